@@ -1,0 +1,252 @@
+"""Charge bookkeeping and the block-sparse two-site H_eff, restated with plain loops over
+charge blocks. Test infrastructure only.
+
+Charges (Sec. II and Sec. III): particle number N (U(1)) and ring momentum K in Z_M, with
+M = Ly in the mixed basis (the onsite rotation T_y = prod exp(i k n_{x,k}) makes K an
+additive onsite charge) and M = 1 in real space. Local charge of orbital momentum m:
+q(s) = (s, s * m mod M) for occupation s.
+
+Tensors are lists of dense blocks, one per allowed charge combination:
+  bond sectors      ((N, K), dim), sorted by (N, K)
+  theta             fused "middle" blocks: for each middle charge q_m (sorted), rows
+                    (s1, a) with q_a + q1(s1) = q_m (s1 = 0 rows first), columns (s2, b) with
+                    q_b - q2(s2) = q_m (s2 = 0 first); block row-major; blocks concatenated
+  left env  L_w     block (w, a) for every channel w and left sector a whose image
+                    q_a + c_w is a left sector; shape d(q_a + c_w) x d(q_a) = [bra][ket];
+                    ordered by w, then a; row-major; concatenated
+  right env R_w     block (w, b) for every channel w and right sector b with q_b + c_w a
+                    right sector; shape d(q_b) x d(q_b + c_w) = [ket][bra]; ordered by w, b
+  MPO site          entries (w, w', s', s, value), nonzero only if
+                    c_{w'} = c_w + q(s') - q(s)
+Complex numbers are stored interleaved (re, im) as complex128.
+
+H_eff (the two-site effective Hamiltonian of DMRG, applied as in the definition):
+  X_w[a', s1, s2, b]      = sum_a L_w[a', a] theta[a, s1, s2, b]
+  Y_{w''}[a', s1', s2', b] = sum W_i[w, w', s1', s1] W_{i+1}[w', w'', s2', s2] X_w[a', s1, s2, b]
+  theta'[a', s1', s2', b'] = sum_{w'', b} Y_{w''}[a', s1', s2', b] R_{w''}[b, b']
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def qadd(q1, q2, mod):
+    return (q1[0] + q2[0], (q1[1] + q2[1]) % mod)
+
+
+def qsub(q1, q2, mod):
+    return (q1[0] - q2[0], (q1[1] - q2[1]) % mod)
+
+
+def qsite(s, m, mod):
+    return (s, (s * m) % mod)
+
+
+class BondSectors:
+    def __init__(self, sectors):
+        self.charges = [tuple(q) for q, _ in sectors]
+        self.dims = [int(d) for _, d in sectors]
+        if self.charges != sorted(self.charges) or len(set(self.charges)) != len(self.charges):
+            raise ValueError("bond sectors must be sorted and distinct")
+        self.index = {q: i for i, q in enumerate(self.charges)}
+
+    def dim(self, q):
+        i = self.index.get(q)
+        return 0 if i is None else self.dims[i]
+
+
+def theta_layout(left, right, m1, m2, mod):
+    """Middle sectors of the fused two-site tensor.
+
+    Returns a list of dicts, sorted by middle charge q, each with
+    rows: [(s1, a_index, d_a, row_offset)], cols: [(s2, b_index, d_b, col_offset)],
+    rowdim, coldim, offset (position of the block in the flat array)."""
+    cand = set()
+    for q in left.charges:
+        for s1 in (0, 1):
+            cand.add(qadd(q, qsite(s1, m1, mod), mod))
+    out = []
+    off = 0
+    for q in sorted(cand):
+        rows, r = [], 0
+        for s1 in (0, 1):
+            a = qsub(q, qsite(s1, m1, mod), mod)
+            if a in left.index:
+                rows.append((s1, left.index[a], left.dim(a), r))
+                r += left.dim(a)
+        cols, c = [], 0
+        for s2 in (0, 1):
+            b = qadd(q, qsite(s2, m2, mod), mod)
+            if b in right.index:
+                cols.append((s2, right.index[b], right.dim(b), c))
+                c += right.dim(b)
+        if r == 0 or c == 0:
+            continue
+        out.append({"q": q, "rows": rows, "cols": cols, "rowdim": r, "coldim": c, "offset": off})
+        off += r * c
+    return out
+
+
+def theta_size(layout):
+    return sum(m["rowdim"] * m["coldim"] for m in layout)
+
+
+def env_left_layout(left, cw, mod):
+    """[(w, a_index, a'_index, offset, d_a', d_a)] for the blocks of L_w."""
+    out, off = [], 0
+    for w, c in enumerate(cw):
+        for ai, qa in enumerate(left.charges):
+            qp = qadd(qa, c, mod)
+            if qp in left.index:
+                dp, da = left.dim(qp), left.dims[ai]
+                out.append((w, ai, left.index[qp], off, dp, da))
+                off += dp * da
+    return out
+
+
+def env_right_layout(right, cw, mod):
+    """[(w, b_index, b'_index, offset, d_b, d_b')] for the blocks of R_w."""
+    out, off = [], 0
+    for w, c in enumerate(cw):
+        for bi, qb in enumerate(right.charges):
+            qp = qadd(qb, c, mod)
+            if qp in right.index:
+                db, dp = right.dims[bi], right.dim(qp)
+                out.append((w, bi, right.index[qp], off, db, dp))
+                off += db * dp
+    return out
+
+
+def env_size(layout):
+    return sum(e[4] * e[5] for e in layout)
+
+
+def theta_blocks(flat, layout):
+    """Flat fused theta -> {(a_index, s1, s2): d_a x d_b array}."""
+    out = {}
+    for m in layout:
+        blk = flat[m["offset"]: m["offset"] + m["rowdim"] * m["coldim"]].reshape(m["rowdim"], m["coldim"])
+        for s1, ai, da, ro in m["rows"]:
+            for s2, bi, db, co in m["cols"]:
+                out[(ai, s1, s2)] = blk[ro:ro + da, co:co + db]
+    return out
+
+
+def theta_flat(blocks, layout):
+    flat = np.zeros(theta_size(layout), dtype=np.complex128)
+    for m in layout:
+        blk = flat[m["offset"]: m["offset"] + m["rowdim"] * m["coldim"]].reshape(m["rowdim"], m["coldim"])
+        for s1, ai, da, ro in m["rows"]:
+            for s2, bi, db, co in m["cols"]:
+                if (ai, s1, s2) in blocks:
+                    blk[ro:ro + da, co:co + db] = blocks[(ai, s1, s2)]
+    return flat
+
+
+def heff_apply(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, tflat):
+    """theta' = H_eff theta, block by block, in the order of the definition above.
+
+    left/right: BondSectors of the bonds left of site i and right of site i+1; m1, m2:
+    momenta of the two sites; cl, cm, cr: channel charges of the MPO bonds left of i,
+    between i and i+1, right of i+1; wi, wj: MPO entry lists; lflat, rflat, tflat: flat
+    complex128 arrays in the layouts above."""
+    lay = theta_layout(left, right, m1, m2, mod)
+    theta = theta_blocks(tflat, lay)
+    lblk = {(w, ai): lflat[off: off + dp * da].reshape(dp, da)
+            for w, ai, api, off, dp, da in env_left_layout(left, cl, mod)}
+    rblk = {(w, bi): rflat[off: off + db * dp].reshape(db, dp)
+            for w, bi, bpi, off, db, dp in env_right_layout(right, cr, mod)}
+    # X_w = L_w theta
+    x = {}
+    for (ai, s1, s2), blk in theta.items():
+        qa = left.charges[ai]
+        for w, c in enumerate(cl):
+            key = (w, ai)
+            if key not in lblk:
+                continue
+            api = left.index[qadd(qa, c, mod)]
+            x[(w, api, s1, s2, ai)] = lblk[key] @ blk
+    # Y_{w''} = sum W_i W_{i+1} X_w
+    wj_by_mid = {}
+    for (wp, wpp, s2p, s2, val) in wj:
+        wj_by_mid.setdefault(wp, []).append((wpp, s2p, s2, val))
+    x_by = {}
+    for (w, api, s1, s2, ai), xb in x.items():
+        x_by.setdefault((w, s1), []).append((api, s2, ai, xb))
+    y = {}
+    for (w, wp, s1p, s1, vi) in wi:
+        for (wpp, s2p, s2, vj) in wj_by_mid.get(wp, []):
+            for (api, xs2, ai, xb) in x_by.get((w, s1), []):
+                if xs2 != s2:
+                    continue
+                qb = qadd(qadd(left.charges[ai], qsite(s1, m1, mod), mod), qsite(s2, m2, mod), mod)
+                bi = right.index[qb]
+                k = (wpp, api, s1p, s2p, bi)
+                y[k] = y.get(k, 0) + (vi * vj) * xb
+    # theta' = sum Y_{w''} R_{w''}
+    out = {}
+    for (wpp, api, s1p, s2p, bi), yb in y.items():
+        key = (wpp, bi)
+        if key not in rblk:
+            continue
+        qbp = qadd(right.charges[bi], cr[wpp], mod)
+        expect = qadd(qadd(left.charges[api], qsite(s1p, m1, mod), mod), qsite(s2p, m2, mod), mod)
+        if qbp != expect:
+            raise AssertionError("charge conservation violated")
+        k = (api, s1p, s2p)
+        out[k] = out.get(k, 0) + yb @ rblk[key]
+    return theta_flat(out, lay)
+
+
+def heff_flops(left, right, m1, m2, mod, cl, cm, cr, wi, wj):
+    """Real flops of heff_apply in the order of the definition: 8 per complex
+    multiply-add in the L step, the W step (one scaled block add per matching pair of
+    MPO entries) and the R step. This count depends only on the workload."""
+    lay = theta_layout(left, right, m1, m2, mod)
+    blocks = []
+    for m in lay:
+        for s1, ai, da, ro in m["rows"]:
+            for s2, bi, db, co in m["cols"]:
+                blocks.append((ai, s1, s2, da, db, bi))
+    fl = 0
+    xkeys = {}
+    for ai, s1, s2, da, db, bi in blocks:
+        for w, c in enumerate(cl):
+            q = qadd(left.charges[ai], c, mod)
+            if q in left.index:
+                dp = left.dim(q)
+                fl += 8 * dp * da * db
+                xkeys.setdefault((w, s1, s2), []).append((left.index[q], bi, dp, db))
+    wj_by_mid = {}
+    for (wp, wpp, s2p, s2, val) in wj:
+        wj_by_mid.setdefault(wp, []).append((wpp, s2p, s2))
+    ykeys = set()
+    for (w, wp, s1p, s1, vi) in wi:
+        for (wpp, s2p, s2) in wj_by_mid.get(wp, []):
+            for api, bi, dp, db in xkeys.get((w, s1, s2), []):
+                fl += 8 * dp * db
+                ykeys.add((wpp, api, s1p, s2p, bi, dp, db))
+    for wpp, api, s1p, s2p, bi, dp, db in ykeys:
+        q = qadd(right.charges[bi], cr[wpp], mod)
+        if q in right.index:
+            fl += 8 * dp * db * right.dim(q)
+    return fl
+
+
+def random_env_from_layout(layout_size, seed):
+    import synth
+    return synth.complex_pm1(seed, layout_size)
+
+
+def fused_bond_sectors(site_ms, mod):
+    """Exact sectors of the left block spanned by orbitals with momenta site_ms: fusing one
+    orbital with local charges q(0) = (0, 0), q(1) = (1, m) at a time (dims add up)."""
+    sec = {(0, 0): 1}
+    for m in site_ms:
+        nxt = {}
+        for q, d in sec.items():
+            for s in (0, 1):
+                q2 = qadd(q, qsite(s, m, mod), mod)
+                nxt[q2] = nxt.get(q2, 0) + d
+        sec = nxt
+    return sorted(sec.items())
