@@ -1,0 +1,151 @@
+/*
+ * mrdmrg.h -- C ABI of the GB300 (sm_103a) hot path of two-site DMRG on a cylinder in
+ * mixed real and momentum space (Motruk, Zaletel, Mong, Pollmann, arXiv:1512.03318).
+ *
+ * Problem statement (Sec. III.A, Eq. H; Sec. IV.D, Eqs. H_kin and H_k_int): spinless
+ * fermions on an Lx x Ly cylinder (open along x, periodic around y) with hopping t, flux
+ * phi = 2 pi p / q per plaquette in Landau gauge and nearest-neighbour repulsion V. The
+ * orbitals around each ring are Fourier transformed, so the chain runs over orbitals
+ * (x, k) with k = 2 pi m / Ly (Sec. II, Fig. 1b) and the rotation of the cylinder becomes
+ * an onsite Z_Ly charge K next to the particle number N (Sec. II).
+ *
+ * Conventions shared by every call
+ *   charge      (N, K) with K in [0, modulus); modulus = Ly in the mixed basis, 1 in real
+ *               space. Local charge of an orbital with momentum index m and occupation s:
+ *               q(s) = (s, s*m mod modulus).
+ *   sectors     int32 triplets (N, K, dim), strictly increasing in (N, K), dim > 0.
+ *   channels    MPO channel charges, int32 pairs (dN, dK); an MPO entry W[w, w', s', s]
+ *               (s' bra, s ket) is allowed only if c_{w'} = c_w + q(s') - q(s).
+ *   complex     interleaved (re, im) doubles (complex128); lengths below count complex
+ *               elements.
+ *   theta       two-site tensor, fused by middle charge q_m: for each q_m (sorted) a dense
+ *               block with rows (s1, a), q_a + q1(s1) = q_m, s1 = 0 rows first, and columns
+ *               (s2, b), q_b - q2(s2) = q_m, s2 = 0 first; row-major; blocks back to back.
+ *   left env    L_w blocks for every (w, a) with q_a + c_w a left sector, shape
+ *               d(q_a + c_w) x d(q_a) ([bra][ket]); ordered by w then a; row-major.
+ *   right env   R_w blocks for every (w, b) with q_b + c_w a right sector, shape
+ *               d(q_b) x d(q_b + c_w) ([ket][bra]); ordered by w then b; row-major.
+ *   H_eff       theta'[a',s1',s2',b'] = sum L_w[a',a] W_i[w,w',s1',s1] W_{i+1}[w',w'',s2',s2]
+ *               R_{w''}[b,b'] theta[a,s1,s2,b]  (the two-site effective Hamiltonian of
+ *               DMRG; the paper relies on standard DMRG, its refs. W92, S2005, S2011).
+ *
+ * Pointers: "dev" arguments are device pointers on the context's device, owned by the
+ * caller and only read or written during the call (or until the stream work it enqueued
+ * completes). Host arrays are read during the call only. Handles are owned by the library
+ * and released by the matching *_free. Every call returns 0 or a negative MRD_E_* code and
+ * never aborts; mrd_last_error() gives a message. Calls on one context are not
+ * thread-safe. All device work is enqueued on the context's stream.
+ */
+#ifndef MRDMRG_H
+#define MRDMRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRD_OK 0
+#define MRD_E_ARG (-1)      /* invalid argument (sizes, ordering, null pointer)           */
+#define MRD_E_CHARGE (-2)   /* an MPO entry or block violates charge conservation          */
+#define MRD_E_NOCONV (-3)   /* an iterative solver did not converge                       */
+#define MRD_E_OOM (-4)      /* device allocation failed                                   */
+#define MRD_E_CUDA (-5)     /* a CUDA runtime call failed                                 */
+#define MRD_E_NAN (-6)      /* a non-finite value was produced                            */
+#define MRD_E_TIMEOUT (-7)  /* a bounded device wait gave up                              */
+#define MRD_E_STATE (-8)    /* call out of order (e.g. apply before set_env)              */
+
+#define MRD_PREC_FP64 0     /* complex128 operands, FP64 arithmetic                       */
+
+#define MRD_BASIS_MIXED 0   /* orbitals (x, k_m), charges (N, K mod Ly)                   */
+#define MRD_BASIS_REAL 1    /* orbitals (x, y), charge N only (modulus 1)                 */
+
+typedef struct mrd_ctx mrd_ctx;
+typedef struct mrd_mpo mrd_mpo;
+typedef struct mrd_heff mrd_heff;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`. `stream` is a cudaStream_t borrowed from the
+ * caller (NULL = the legacy default stream); the library never destroys it. */
+int mrd_create(mrd_ctx** out, int device, void* stream);
+int mrd_destroy(mrd_ctx* ctx);
+int mrd_set_stream(mrd_ctx* ctx, void* stream);
+/* Message of the last failing call on this context (static storage of the context). */
+const char* mrd_last_error(const mrd_ctx* ctx);
+/* Library version as major*10000 + minor*100 + patch. */
+int mrd_version(void);
+
+/* ------------------------------------------------------------------ MPO (Sec. IV) */
+
+typedef struct {
+  int32_t lx, ly;          /* rings along the cylinder, orbitals per ring (ly >= 2)      */
+  int32_t flux_p, flux_q;  /* flux per plaquette phi = 2 pi p / q (q > 0)                */
+  double t, v;             /* hopping and nearest-neighbour repulsion                    */
+  int32_t basis;           /* MRD_BASIS_MIXED or MRD_BASIS_REAL                          */
+} mrd_model;
+
+/* Build the Hamiltonian MPO from its finite-state machine (Sec. IV.A-B): intermediate
+ * nodes carry the set of operators already placed and, in the mixed basis, the cumulative
+ * momentum (the momentum-labelled nodes of Sec. IV.D, Figs. 9-10); unreachable nodes are
+ * trimmed (Sec. IV.D) and nodes with proportional pasts or futures are fused. Host
+ * computation; the result lives in host memory of the handle. ctx may be NULL (no device
+ * is touched; errors are then reported by the return code only). */
+int mrd_mpo_build(mrd_ctx* ctx, const mrd_model* model, mrd_mpo** out);
+int mrd_mpo_free(mrd_mpo* mpo);
+/* Number of sites (lx*ly) and charge modulus. */
+int mrd_mpo_info(const mrd_mpo* mpo, int32_t* n_sites, int32_t* modulus);
+/* Dimension of MPO bond `bond` (0..n_sites); if charges != NULL, writes 2*dim int32
+ * (dN, dK) channel charges. */
+int mrd_mpo_bond(const mrd_mpo* mpo, int32_t bond, int32_t* dim, int32_t* charges);
+/* Nonzero entries of site `site`: if idx != NULL writes 4*nnz int32 (w, w', s', s) and if
+ * val != NULL 2*nnz doubles (re, im), ordered by (w, w', s', s). */
+int mrd_mpo_site(const mrd_mpo* mpo, int32_t site, int32_t* nnz, int32_t* idx, double* val);
+
+/* ------------------------------------------------------------------ two-site H_eff */
+
+typedef struct {
+  int32_t n_left;  const int32_t* left;    /* sectors of the bond left of site i         */
+  int32_t n_right; const int32_t* right;   /* sectors of the bond right of site i+1      */
+  int32_t m1, m2, modulus;                 /* momentum indices of sites i, i+1; modulus  */
+  int32_t d_l, d_m, d_r;                   /* MPO bond dims left of i, between, right    */
+  const int32_t* c_l; const int32_t* c_m; const int32_t* c_r;   /* channel charges       */
+  int32_t nnz_i; const int32_t* wi_idx; const double* wi_val;   /* W_i entries           */
+  int32_t nnz_j; const int32_t* wj_idx; const double* wj_val;   /* W_{i+1} entries       */
+} mrd_heff_desc;
+
+/* Validate the description and build, on the device, the charge tables of the two-site
+ * problem: fused middle sectors with block offsets, environment block layouts, and the
+ * task lists of the contraction. Host arrays are copied. */
+int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out);
+int mrd_heff_free(mrd_heff* h);
+/* Lengths (complex elements) of theta, the left env and the right env. */
+int mrd_heff_sizes(const mrd_heff* h, int64_t* theta_len, int64_t* lenv_len, int64_t* renv_len);
+/* Load the environments (device pointers, complex128, layouts above). They are folded
+ * with the MPO into internal operands LW_{w'} = sum_w W_i[w,w'] L_w and
+ * WR_{w'} = sum_{w''} W_{i+1}[w',w''] R_{w''}; the caller's buffers are not retained. */
+int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev);
+/* theta_out = H_eff theta_in (device pointers; must not overlap). */
+int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev, int32_t prec);
+/* Real flops of one H_eff application (8 per complex multiply-add), written to flops4:
+ * [0] in the order of the definition (L step, W step, R step); [1] as executed by the
+ * library, no padding counted; [2] and [3] the executed share of its step-1
+ * (Z = LW theta) and step-2 (theta' = sum Z WR) grouped GEMMs. */
+int mrd_heff_flops(const mrd_heff* h, double* flops4);
+/* Kernel timing. With on != 0 every mrd_heff_apply records CUDA events around its two
+ * grouped-GEMM launches on the context stream (no synchronisation). collect() waits for
+ * the recorded work, returns the summed durations in ms of the step-1 and step-2 launches
+ * and the number of applies recorded, and clears the record. */
+int mrd_heff_timing(mrd_heff* h, int32_t on);
+int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls);
+
+/* Table export for bit-exact checks. which = 0: middle sectors, 8 int64 per row
+ * (N, K, rowdim, coldim, offset, row_off_s1=1, col_off_s2=1, flags); which = 1: left-env
+ * blocks, 6 int64 (w, a, a', offset, rows, cols); which = 2: right-env blocks, 6 int64
+ * (w, b, b', offset, rows, cols). If rows == NULL only *count is set. */
+int mrd_heff_table(const mrd_heff* h, int32_t which, int64_t* rows, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRDMRG_H */

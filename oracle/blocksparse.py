@@ -143,13 +143,15 @@ def theta_flat(blocks, layout):
     return flat
 
 
-def heff_apply(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, tflat):
+def heff_apply(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, tflat, rows=None):
     """theta' = H_eff theta, block by block, in the order of the definition above.
 
     left/right: BondSectors of the bonds left of site i and right of site i+1; m1, m2:
     momenta of the two sites; cl, cm, cr: channel charges of the MPO bonds left of i,
     between i and i+1, right of i+1; wi, wj: MPO entry lists; lflat, rflat, tflat: flat
-    complex128 arrays in the layouts above."""
+    complex128 arrays in the layouts above. rows: optional set of left-sector indices a';
+    if given, only output blocks with those a' are computed (others stay zero), which is
+    the same arithmetic on a subset (used to bound the CPU timing sample)."""
     lay = theta_layout(left, right, m1, m2, mod)
     theta = theta_blocks(tflat, lay)
     lblk = {(w, ai): lflat[off: off + dp * da].reshape(dp, da)
@@ -165,6 +167,8 @@ def heff_apply(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, tflat
             if key not in lblk:
                 continue
             api = left.index[qadd(qa, c, mod)]
+            if rows is not None and api not in rows:
+                continue
             x[(w, api, s1, s2, ai)] = lblk[key] @ blk
     # Y_{w''} = sum W_i W_{i+1} X_w
     wj_by_mid = {}
@@ -198,10 +202,11 @@ def heff_apply(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, tflat
     return theta_flat(out, lay)
 
 
-def heff_flops(left, right, m1, m2, mod, cl, cm, cr, wi, wj):
+def heff_flops(left, right, m1, m2, mod, cl, cm, cr, wi, wj, rows=None):
     """Real flops of heff_apply in the order of the definition: 8 per complex
     multiply-add in the L step, the W step (one scaled block add per matching pair of
-    MPO entries) and the R step. This count depends only on the workload."""
+    MPO entries) and the R step. This count depends only on the workload (and on the
+    optional row subset, as in heff_apply)."""
     lay = theta_layout(left, right, m1, m2, mod)
     blocks = []
     for m in lay:
@@ -214,6 +219,8 @@ def heff_flops(left, right, m1, m2, mod, cl, cm, cr, wi, wj):
         for w, c in enumerate(cl):
             q = qadd(left.charges[ai], c, mod)
             if q in left.index:
+                if rows is not None and left.index[q] not in rows:
+                    continue
                 dp = left.dim(q)
                 fl += 8 * dp * da * db
                 xkeys.setdefault((w, s1, s2), []).append((left.index[q], bi, dp, db))
@@ -250,3 +257,41 @@ def fused_bond_sectors(site_ms, mod):
                 nxt[q2] = nxt.get(q2, 0) + d
         sec = nxt
     return sorted(sec.items())
+
+
+def heff_apply_block(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, tflat, out_key):
+    """One output block theta'[(a', s1', s2')] of H_eff theta, by the same definition as
+    heff_apply restricted to that block (for sampled checks at sizes where the full
+    product is too slow). out_key = (a'_index, s1', s2'); returns a d_a' x d_b' array."""
+    api, s1p, s2p = out_key
+    lay = theta_layout(left, right, m1, m2, mod)
+    theta = theta_blocks(tflat, lay)
+    lblk = {(w, ai): (apx, lflat[off: off + dp * da].reshape(dp, da))
+            for w, ai, apx, off, dp, da in env_left_layout(left, cl, mod)}
+    rblk = {(w, bi): (bpx, rflat[off: off + db * dp].reshape(db, dp))
+            for w, bi, bpx, off, db, dp in env_right_layout(right, cr, mod)}
+    qbp = qadd(qadd(left.charges[api], qsite(s1p, m1, mod), mod), qsite(s2p, m2, mod), mod)
+    bpi = right.index[qbp]
+    wi_by_w = {}
+    for (w, wp, a1, a2, v) in wi:
+        if a1 == s1p:
+            wi_by_w.setdefault(wp, []).append((w, a2, v))
+    out = np.zeros((left.dims[api], right.dims[bpi]), dtype=np.complex128)
+    for (wp, wpp, b1, b2, vj) in wj:
+        if b1 != s2p:
+            continue
+        for (w, s1, vi) in wi_by_w.get(wp, []):
+            s2 = b2
+            # X_w[a', s1, s2, b] for this a'
+            for (ai, t1, t2), blk in theta.items():
+                if t1 != s1 or t2 != s2 or (w, ai) not in lblk:
+                    continue
+                apx, lb = lblk[(w, ai)]
+                if apx != api:
+                    continue
+                qb = qadd(qadd(left.charges[ai], qsite(s1, m1, mod), mod), qsite(s2, m2, mod), mod)
+                bi = right.index[qb]
+                if (wpp, bi) not in rblk or rblk[(wpp, bi)][0] != bpi:
+                    continue
+                out += (vi * vj) * ((lb @ blk) @ rblk[(wpp, bi)][1])
+    return out

@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) hot path of two-site DMRG on a cylinder in mixed real and momentum space
+(arXiv:1512.03318): Python binding of libmrdmrg (see include/mrdmrg.h).
+
+The binding only marshals arguments: every step runs in the library's CUDA kernels (or its
+host MPO builder). Importing this package never falls back to another implementation: if
+the shared library is missing, `lib()` raises.
+"""
+from .binding import (  # noqa: F401
+    MRD_BASIS_MIXED, MRD_BASIS_REAL, MRD_PREC_FP64, Context, Heff, MPO, MrdError, lib, lib_path)

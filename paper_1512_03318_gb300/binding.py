@@ -1,0 +1,260 @@
+"""ctypes binding of libmrdmrg with the C names; argument marshalling only.
+
+Device buffers are passed as raw pointers: torch tensors (their data_ptr()) or integers.
+Host arrays are numpy arrays converted to the C types of the header."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MRD_PREC_FP64 = 0
+MRD_BASIS_MIXED = 0
+MRD_BASIS_REAL = 1
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+class MrdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mrdmrg error {code}: {msg}")
+        self.code = code
+
+
+class mrd_model(C.Structure):
+    _fields_ = [("lx", C.c_int32), ("ly", C.c_int32), ("flux_p", C.c_int32), ("flux_q", C.c_int32),
+                ("t", C.c_double), ("v", C.c_double), ("basis", C.c_int32)]
+
+
+class mrd_heff_desc(C.Structure):
+    _fields_ = [("n_left", C.c_int32), ("left", C.POINTER(C.c_int32)),
+                ("n_right", C.c_int32), ("right", C.POINTER(C.c_int32)),
+                ("m1", C.c_int32), ("m2", C.c_int32), ("modulus", C.c_int32),
+                ("d_l", C.c_int32), ("d_m", C.c_int32), ("d_r", C.c_int32),
+                ("c_l", C.POINTER(C.c_int32)), ("c_m", C.POINTER(C.c_int32)), ("c_r", C.POINTER(C.c_int32)),
+                ("nnz_i", C.c_int32), ("wi_idx", C.POINTER(C.c_int32)), ("wi_val", C.POINTER(C.c_double)),
+                ("nnz_j", C.c_int32), ("wj_idx", C.POINTER(C.c_int32)), ("wj_val", C.POINTER(C.c_double))]
+
+
+_SIGS = {
+    "mrd_version": (C.c_int, []),
+    "mrd_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
+    "mrd_destroy": (C.c_int, [C.c_void_p]),
+    "mrd_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mrd_last_error": (C.c_char_p, [C.c_void_p]),
+    "mrd_mpo_build": (C.c_int, [C.c_void_p, C.POINTER(mrd_model), C.POINTER(C.c_void_p)]),
+    "mrd_mpo_free": (C.c_int, [C.c_void_p]),
+    "mrd_mpo_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mrd_mpo_bond": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mrd_mpo_site": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_double)]),
+    "mrd_heff_create": (C.c_int, [C.c_void_p, C.POINTER(mrd_heff_desc), C.POINTER(C.c_void_p)]),
+    "mrd_heff_free": (C.c_int, [C.c_void_p]),
+    "mrd_heff_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mrd_heff_set_env": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrd_heff_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "mrd_heff_flops": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mrd_heff_table": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int32)]),
+}
+
+
+def declared_symbols():
+    """Function names declared in include/mrdmrg.h (parsed from the header text)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mrdmrg.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(mrd_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmrdmrg not built ({path}); run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(x):
+    """Raw device pointer of a torch tensor, or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+
+
+def _p32(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _p64f(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        h = C.c_void_p()
+        rc = lib().mrd_create(C.byref(h), device, _stream_ptr(stream))
+        if rc != 0:
+            raise MrdError(rc, "mrd_create failed")
+        self.h = h
+        self.device = device
+
+    def check(self, rc):
+        if rc != 0:
+            raise MrdError(rc, lib().mrd_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        self.check(lib().mrd_set_stream(self.h, _stream_ptr(stream)))
+
+    def close(self):
+        if self.h:
+            lib().mrd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class MPO:
+    """Handle of a host-built MPO (mrd_mpo_build). ctx may be None (host only)."""
+
+    def __init__(self, ctx, lx, ly, flux_p, flux_q, t, v, basis=MRD_BASIS_MIXED):
+        m = mrd_model(lx, ly, flux_p, flux_q, t, v, basis)
+        h = C.c_void_p()
+        rc = lib().mrd_mpo_build(ctx.h if ctx is not None else None, C.byref(m), C.byref(h))
+        if rc != 0:
+            msg = lib().mrd_last_error(ctx.h).decode() if ctx is not None else "mrd_mpo_build failed"
+            raise MrdError(rc, msg)
+        self.h = h
+        n, mod = C.c_int32(), C.c_int32()
+        lib().mrd_mpo_info(h, C.byref(n), C.byref(mod))
+        self.n_sites, self.modulus, self.ly = n.value, mod.value, ly
+
+    def bond(self, b):
+        d = C.c_int32()
+        lib().mrd_mpo_bond(self.h, b, C.byref(d), None)
+        ch = np.zeros(2 * d.value, dtype=np.int32)
+        lib().mrd_mpo_bond(self.h, b, C.byref(d), _p32(ch))
+        return ch.reshape(-1, 2)
+
+    def site(self, j):
+        nnz = C.c_int32()
+        lib().mrd_mpo_site(self.h, j, C.byref(nnz), None, None)
+        idx = np.zeros(4 * nnz.value, dtype=np.int32)
+        val = np.zeros(2 * nnz.value, dtype=np.float64)
+        lib().mrd_mpo_site(self.h, j, C.byref(nnz), _p32(idx), _p64f(val))
+        return idx.reshape(-1, 4), val[0::2] + 1j * val[1::2]
+
+    def __del__(self):
+        try:
+            lib().mrd_mpo_free(self.h)
+        except Exception:
+            pass
+
+
+class Heff:
+    """Two-site H_eff problem (mrd_heff_create / set_env / apply)."""
+
+    def __init__(self, ctx: Context, left, right, m1, m2, modulus, cl, cm, cr, wi_idx, wi_val, wj_idx, wj_val):
+        self.ctx = ctx
+        keep = {}
+        keep["left"] = _i32(left)
+        keep["right"] = _i32(right)
+        keep["cl"], keep["cm"], keep["cr"] = _i32(cl), _i32(cm), _i32(cr)
+        keep["wi_idx"], keep["wj_idx"] = _i32(wi_idx), _i32(wj_idx)
+        wv = np.asarray(wi_val, dtype=np.complex128).reshape(-1)
+        keep["wi_val"] = _f64(np.stack([wv.real, wv.imag], axis=1))
+        wv = np.asarray(wj_val, dtype=np.complex128).reshape(-1)
+        keep["wj_val"] = _f64(np.stack([wv.real, wv.imag], axis=1))
+        d = mrd_heff_desc()
+        d.n_left, d.left = len(keep["left"]) // 3, _p32(keep["left"])
+        d.n_right, d.right = len(keep["right"]) // 3, _p32(keep["right"])
+        d.m1, d.m2, d.modulus = m1, m2, modulus
+        d.d_l, d.d_m, d.d_r = len(keep["cl"]) // 2, len(keep["cm"]) // 2, len(keep["cr"]) // 2
+        d.c_l, d.c_m, d.c_r = _p32(keep["cl"]), _p32(keep["cm"]), _p32(keep["cr"])
+        d.nnz_i, d.wi_idx, d.wi_val = len(keep["wi_idx"]) // 4, _p32(keep["wi_idx"]), _p64f(keep["wi_val"])
+        d.nnz_j, d.wj_idx, d.wj_val = len(keep["wj_idx"]) // 4, _p32(keep["wj_idx"]), _p64f(keep["wj_val"])
+        h = C.c_void_p()
+        ctx.check(lib().mrd_heff_create(ctx.h, C.byref(d), C.byref(h)))
+        self.h = h
+        t, l, r = C.c_int64(), C.c_int64(), C.c_int64()
+        lib().mrd_heff_sizes(h, C.byref(t), C.byref(l), C.byref(r))
+        self.theta_len, self.lenv_len, self.renv_len = t.value, l.value, r.value
+
+    def set_env(self, lenv, renv):
+        self.ctx.check(lib().mrd_heff_set_env(self.h, _ptr(lenv), _ptr(renv)))
+
+    def apply(self, theta_in, theta_out, prec=MRD_PREC_FP64):
+        self.ctx.check(lib().mrd_heff_apply(self.h, _ptr(theta_in), _ptr(theta_out), prec))
+
+    def flops(self):
+        """(definition-order, executed, executed step 1, executed step 2) real flops."""
+        f = (C.c_double * 4)()
+        self.ctx.check(lib().mrd_heff_flops(self.h, f))
+        return f[0], f[1], f[2], f[3]
+
+    def timing(self, on=True):
+        self.ctx.check(lib().mrd_heff_timing(self.h, 1 if on else 0))
+
+    def timing_collect(self):
+        a, b, n = C.c_double(), C.c_double(), C.c_int32()
+        self.ctx.check(lib().mrd_heff_timing_collect(self.h, C.byref(a), C.byref(b), C.byref(n)))
+        return a.value, b.value, n.value
+
+    def table(self, which):
+        n = C.c_int64()
+        self.ctx.check(lib().mrd_heff_table(self.h, which, None, C.byref(n)))
+        width = 8 if which == 0 else 6
+        rows = np.zeros(max(1, n.value) * width, dtype=np.int64)
+        self.ctx.check(lib().mrd_heff_table(self.h, which, rows.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(n)))
+        return rows[: n.value * width].reshape(-1, width)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrd_heff_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,579 @@
+// C ABI entry points (include/mrdmrg.h): argument checks, device memory, launches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <tuple>
+#include <string>
+#include <vector>
+
+#include "mrd_internal.h"
+#include "plan.cuh"
+
+namespace mrd {
+cudaError_t launch_plan(const PlanDims& d, const PlanPtrs& p, cudaStream_t s);
+cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
+                              const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                              int n_sm, cudaStream_t s);
+cudaError_t launch_fold_env(const double2* env, double2* out, const int64_t* rows, int64_t nrows,
+                            const int64_t* env_map, int n_sec, const int32_t* perm, const int32_t* idx,
+                            const double* val, int chan_field, cudaStream_t s);
+}  // namespace mrd
+
+using namespace mrd;
+
+int mrd_fail(mrd_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int mrd_cuda_fail(mrd_ctx* ctx, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return mrd_fail(ctx, e == cudaErrorMemoryAllocation ? MRD_E_OOM : MRD_E_CUDA, m);
+}
+
+namespace {
+
+// Device arena: a list of allocations freed together.
+struct Arena {
+  std::vector<void*> ptrs;
+  ~Arena() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  template <class T>
+  cudaError_t alloc(T** out, size_t count) {
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(p);
+    *out = (T*)p;
+    return cudaSuccess;
+  }
+};
+
+struct Guard {  // switches to a device for the scope
+  int prev = -1;
+  explicit Guard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Guard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int kmod(int k, int m) { return ((k % m) + m) % m; }
+
+}  // namespace
+
+struct mrd_heff {
+  mrd_ctx* ctx = nullptr;
+  PlanDims d{};
+  PlanPtrs p{};
+  Arena plan_mem;   // tables
+  Arena data_mem;   // LW, WR, Z
+  int64_t counts[C_NCOUNTS] = {0};
+  double* wi_val = nullptr;
+  double* wj_val = nullptr;
+  double2* lw = nullptr;
+  double2* wr = nullptr;
+  double2* z = nullptr;
+  bool env_loaded = false;
+  double def_flops = 0.0;
+  int n_sm = 152;
+  std::vector<int32_t> left, right, cl, cm, cr, wi_idx, wj_idx;
+  std::vector<double> wi_v, wj_v;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;   // 3 per recorded apply: before step 1, between, after step 2
+  std::vector<cudaEvent_t> ev_pool;
+  ~mrd_heff() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+};
+
+static cudaEvent_t take_event(mrd_heff* h) {
+  cudaEvent_t e = nullptr;
+  if (!h->ev_pool.empty()) {
+    e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  h->ev.push_back(e);
+  return e;
+}
+
+extern "C" {
+
+int mrd_version(void) { return 100; }
+
+int mrd_create(mrd_ctx** out, int device, void* stream) {
+  if (!out) return MRD_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return MRD_E_ARG;
+  mrd_ctx* c = new mrd_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  *out = c;
+  return MRD_OK;
+}
+
+int mrd_destroy(mrd_ctx* ctx) {
+  delete ctx;
+  return MRD_OK;
+}
+
+int mrd_set_stream(mrd_ctx* ctx, void* stream) {
+  if (!ctx) return MRD_E_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return MRD_OK;
+}
+
+const char* mrd_last_error(const mrd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// ------------------------------------------------------------------ MPO
+
+int mrd_mpo_build(mrd_ctx* ctx, const mrd_model* model, mrd_mpo** out) {
+  // host-only: ctx may be NULL (then no message is recorded)
+  if (!model || !out) return mrd_fail(ctx, MRD_E_ARG, "mrd_mpo_build: null argument");
+  *out = nullptr;
+  mrd_mpo* m = new mrd_mpo();
+  m->ctx = ctx;
+  std::string err;
+  int rc = build_mpo_host(*model, &m->h, &err);
+  if (rc != MRD_OK) {
+    delete m;
+    return mrd_fail(ctx, rc, err);
+  }
+  *out = m;
+  return MRD_OK;
+}
+
+int mrd_mpo_free(mrd_mpo* mpo) {
+  delete mpo;
+  return MRD_OK;
+}
+
+int mrd_mpo_info(const mrd_mpo* mpo, int32_t* n_sites, int32_t* modulus) {
+  if (!mpo) return MRD_E_ARG;
+  if (n_sites) *n_sites = mpo->h.n_sites;
+  if (modulus) *modulus = mpo->h.modulus;
+  return MRD_OK;
+}
+
+int mrd_mpo_bond(const mrd_mpo* mpo, int32_t bond, int32_t* dim, int32_t* charges) {
+  if (!mpo || !dim || bond < 0 || bond > mpo->h.n_sites) return MRD_E_ARG;
+  const auto& c = mpo->h.bond_charges[bond];
+  *dim = (int32_t)(c.size() / 2);
+  if (charges) std::memcpy(charges, c.data(), c.size() * sizeof(int32_t));
+  return MRD_OK;
+}
+
+int mrd_mpo_site(const mrd_mpo* mpo, int32_t site, int32_t* nnz, int32_t* idx, double* val) {
+  if (!mpo || !nnz || site < 0 || site >= mpo->h.n_sites) return MRD_E_ARG;
+  const auto& i = mpo->h.site_idx[site];
+  const auto& v = mpo->h.site_val[site];
+  *nnz = (int32_t)(i.size() / 4);
+  if (idx) std::memcpy(idx, i.data(), i.size() * sizeof(int32_t));
+  if (val) std::memcpy(val, v.data(), v.size() * sizeof(double));
+  return MRD_OK;
+}
+
+// ------------------------------------------------------------------ H_eff
+
+static int validate_sectors(mrd_ctx* ctx, const int32_t* s, int n, int mod, const char* what) {
+  if (n < 0 || (n > 0 && !s)) return mrd_fail(ctx, MRD_E_ARG, std::string("mrd_heff_create: bad ") + what);
+  for (int i = 0; i < n; ++i) {
+    if (s[3 * i + 2] <= 0 || s[3 * i + 1] < 0 || s[3 * i + 1] >= mod)
+      return mrd_fail(ctx, MRD_E_ARG, std::string("mrd_heff_create: ") + what + " sector with dim <= 0 or K out of range");
+    if (i > 0 && qkey(s[3 * i - 3], s[3 * i - 2]) >= qkey(s[3 * i], s[3 * i + 1]))
+      return mrd_fail(ctx, MRD_E_ARG, std::string("mrd_heff_create: ") + what + " sectors not strictly increasing in (N, K)");
+  }
+  return MRD_OK;
+}
+
+static int validate_entries(mrd_ctx* ctx, const int32_t* idx, const double* val, int nnz, int d0, int d1,
+                            const int32_t* c0, const int32_t* c1, int m, int mod, const char* what) {
+  if (nnz < 0 || (nnz > 0 && (!idx || !val))) return mrd_fail(ctx, MRD_E_ARG, std::string("mrd_heff_create: bad ") + what);
+  for (int e = 0; e < nnz; ++e) {
+    int w = idx[4 * e], wp = idx[4 * e + 1], sp = idx[4 * e + 2], s = idx[4 * e + 3];
+    if (w < 0 || w >= d0 || wp < 0 || wp >= d1 || (sp & ~1) || (s & ~1))
+      return mrd_fail(ctx, MRD_E_ARG, std::string("mrd_heff_create: ") + what + " entry index out of range");
+    if (c1[2 * wp] != c0[2 * w] + sp - s || kmod(c1[2 * wp + 1], mod) != kmod(c0[2 * w + 1] + (sp - s) * m, mod))
+      return mrd_fail(ctx, MRD_E_CHARGE, std::string("mrd_heff_create: ") + what + " entry violates charge conservation");
+  }
+  // duplicates would be summed twice by nobody: reject them
+  std::vector<int64_t> keys(nnz);
+  for (int e = 0; e < nnz; ++e)
+    keys[e] = (((int64_t)idx[4 * e] * d1 + idx[4 * e + 1]) * 2 + idx[4 * e + 2]) * 2 + idx[4 * e + 3];
+  std::sort(keys.begin(), keys.end());
+  for (int e = 1; e < nnz; ++e)
+    if (keys[e] == keys[e - 1]) return mrd_fail(ctx, MRD_E_ARG, std::string("mrd_heff_create: duplicate ") + what + " entry");
+  return MRD_OK;
+}
+
+int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
+  if (!ctx || !desc || !out) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_create: null argument");
+  *out = nullptr;
+  const mrd_heff_desc& D = *desc;
+  if (D.modulus < 1 || D.d_l < 1 || D.d_m < 1 || D.d_r < 1 || !D.c_l || !D.c_m || !D.c_r || D.m1 < 0 || D.m2 < 0)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_create: bad modulus, MPO dims or channel charges");
+  int rc;
+  if ((rc = validate_sectors(ctx, D.left, D.n_left, D.modulus, "left")) != MRD_OK) return rc;
+  if ((rc = validate_sectors(ctx, D.right, D.n_right, D.modulus, "right")) != MRD_OK) return rc;
+  if ((rc = validate_entries(ctx, D.wi_idx, D.wi_val, D.nnz_i, D.d_l, D.d_m, D.c_l, D.c_m, D.m1, D.modulus, "W_i")) != MRD_OK) return rc;
+  if ((rc = validate_entries(ctx, D.wj_idx, D.wj_val, D.nnz_j, D.d_m, D.d_r, D.c_m, D.c_r, D.m2, D.modulus, "W_i+1")) != MRD_OK) return rc;
+  if (D.n_left == 0 || D.n_right == 0) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_create: empty bond");
+
+  Guard g(ctx->device);
+  mrd_heff* h = new mrd_heff();
+  h->ctx = ctx;
+  cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  h->left.assign(D.left, D.left + 3 * D.n_left);
+  h->right.assign(D.right, D.right + 3 * D.n_right);
+  h->cl.assign(D.c_l, D.c_l + 2 * D.d_l);
+  h->cm.assign(D.c_m, D.c_m + 2 * D.d_m);
+  h->cr.assign(D.c_r, D.c_r + 2 * D.d_r);
+  for (auto* v : {&h->cl, &h->cm, &h->cr})
+    for (size_t i = 1; i < v->size(); i += 2) (*v)[i] = kmod((*v)[i], D.modulus);
+  h->wi_idx.assign(D.wi_idx, D.wi_idx + 4 * D.nnz_i);
+  h->wj_idx.assign(D.wj_idx, D.wj_idx + 4 * D.nnz_j);
+  h->wi_v.assign(D.wi_val, D.wi_val + 2 * D.nnz_i);
+  h->wj_v.assign(D.wj_val, D.wj_val + 2 * D.nnz_j);
+
+  PlanDims& d = h->d;
+  d.n_l = D.n_left; d.n_r = D.n_right; d.d_l = D.d_l; d.d_m = D.d_m; d.d_r = D.d_r;
+  d.nnz_i = D.nnz_i; d.nnz_j = D.nnz_j; d.m1 = D.m1 % D.modulus; d.m2 = D.m2 % D.modulus; d.mod = D.modulus;
+  d.mid_cap = 2 * (int64_t)D.n_left;
+  d.lw_cap = (int64_t)D.d_m * 4 * D.n_left;
+  d.wr_cap = (int64_t)D.d_m * 4 * D.n_right;
+  d.z_cap = (int64_t)D.d_m * d.mid_cap;
+  d.t1_cap = d.z_cap * 2;
+  d.t2_cap = d.mid_cap * 4;
+  d.seg2_stride = 2 * (int64_t)D.d_m;
+  int64_t sl = d.mid_cap;
+  for (int64_t v : {(int64_t)D.d_l * D.n_left, (int64_t)D.d_r * D.n_right, d.lw_cap, d.wr_cap, d.z_cap, d.t1_cap, d.t2_cap})
+    sl = v > sl ? v : sl;
+  d.scratch_len = sl + 1;
+
+  Arena& A = h->plan_mem;
+  PlanPtrs& p = h->p;
+  int32_t *left = nullptr, *right = nullptr, *cl = nullptr, *cm = nullptr, *cr = nullptr, *wi = nullptr, *wj = nullptr;
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, n) if (e == cudaSuccess) e = A.alloc(&(ptr), (size_t)(n))
+  ALLOC(left, 3 * d.n_l); ALLOC(right, 3 * d.n_r); ALLOC(cl, 2 * d.d_l); ALLOC(cm, 2 * d.d_m); ALLOC(cr, 2 * d.d_r);
+  ALLOC(wi, 4 * d.nnz_i); ALLOC(wj, 4 * d.nnz_j); ALLOC(h->wi_val, 2 * d.nnz_i); ALLOC(h->wj_val, 2 * d.nnz_j);
+  ALLOC(p.wi_perm, d.nnz_i); ALLOC(p.wj_perm, d.nnz_j); ALLOC(p.trip_i, 8 * d.d_m); ALLOC(p.trip_j, 8 * d.d_m);
+  ALLOC(p.mid, MIDF * d.mid_cap); ALLOC(p.counts, C_NCOUNTS);
+  ALLOC(p.lmap, (int64_t)d.d_l * d.n_l); ALLOC(p.rmap, (int64_t)d.d_r * d.n_r);
+  ALLOC(p.lwmap, d.lw_cap); ALLOC(p.lw, LWF * d.lw_cap); ALLOC(p.wrmap, d.wr_cap); ALLOC(p.wr, WRF * d.wr_cap);
+  ALLOC(p.zmap, d.z_cap); ALLOC(p.z, ZF * d.z_cap); ALLOC(p.s1mask, d.z_cap);
+  ALLOC(p.t1, TF * d.t1_cap); ALLOC(p.seg1, SF * 2 * d.t1_cap); ALLOC(p.tile1, d.t1_cap + 1);
+  ALLOC(p.t2, TF * d.t2_cap); ALLOC(p.seg2, SF * d.t2_cap * d.seg2_stride); ALLOC(p.tile2, d.t2_cap + 1);
+  ALLOC(p.scr_a, d.scratch_len); ALLOC(p.scr_b, d.scratch_len);
+#undef ALLOC
+  if (e != cudaSuccess) {
+    delete h;
+    return mrd_cuda_fail(ctx, e, "mrd_heff_create: cudaMalloc");
+  }
+  p.left = left; p.right = right; p.cl = cl; p.cm = cm; p.cr = cr; p.wi_idx = wi; p.wj_idx = wj;
+  cudaStream_t s = ctx->stream;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  up(left, h->left.data(), h->left.size() * 4); up(right, h->right.data(), h->right.size() * 4);
+  up(cl, h->cl.data(), h->cl.size() * 4); up(cm, h->cm.data(), h->cm.size() * 4); up(cr, h->cr.data(), h->cr.size() * 4);
+  up(wi, h->wi_idx.data(), h->wi_idx.size() * 4); up(wj, h->wj_idx.data(), h->wj_idx.size() * 4);
+  up(h->wi_val, h->wi_v.data(), h->wi_v.size() * 8); up(h->wj_val, h->wj_v.data(), h->wj_v.size() * 8);
+  if (e == cudaSuccess) e = launch_plan(d, p, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->counts, p.counts, sizeof(h->counts), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete h;
+    return mrd_cuda_fail(ctx, e, "mrd_heff_create: plan");
+  }
+  // Host check of the device-built tables before any kernel reads through them: every
+  // GEMM segment and output block, and every fold source, must lie inside its buffer.
+  {
+    const int64_t* c = h->counts;
+    auto dl = [&](std::vector<int64_t>& v, const int64_t* src, size_t n) {
+      v.resize(n);
+      if (e == cudaSuccess && n) e = cudaMemcpy(v.data(), src, n * 8, cudaMemcpyDeviceToHost);
+    };
+    std::vector<int64_t> t1, s1, t2, s2, lw, wr, lmap, rmap;
+    std::vector<int32_t> wperm_i(d.nnz_i), wperm_j(d.nnz_j);
+    dl(t1, p.t1, (size_t)TF * c[C_NT1]); dl(s1, p.seg1, (size_t)SF * 2 * c[C_NT1]);
+    dl(t2, p.t2, (size_t)TF * c[C_NT2]); dl(s2, p.seg2, (size_t)SF * c[C_NT2] * d.seg2_stride);
+    dl(lw, p.lw, (size_t)LWF * c[C_NLW]); dl(wr, p.wr, (size_t)WRF * c[C_NWR]);
+    dl(lmap, p.lmap, (size_t)d.d_l * d.n_l); dl(rmap, p.rmap, (size_t)d.d_r * d.n_r);
+    if (e == cudaSuccess && d.nnz_i) e = cudaMemcpy(wperm_i.data(), p.wi_perm, d.nnz_i * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && d.nnz_j) e = cudaMemcpy(wperm_j.data(), p.wj_perm, d.nnz_j * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { delete h; return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
+    bool ok = c[C_NMID] <= d.mid_cap && c[C_NLW] <= d.lw_cap && c[C_NWR] <= d.wr_cap && c[C_NZ] <= d.z_cap;
+    auto in = [](int64_t off, int64_t rows, int64_t cols, int64_t ld, int64_t len) {
+      if (rows == 0 || cols == 0) return true;
+      return off >= 0 && ld >= cols && off + (rows - 1) * ld + cols <= len;
+    };
+    auto check_tasks = [&](const std::vector<int64_t>& t, const std::vector<int64_t>& sg, int64_t nt, int64_t alen,
+                           int64_t blen, int64_t clen) {
+      for (int64_t i = 0; i < nt && ok; ++i) {
+        const int64_t* r = &t[TF * i];
+        if (r[0] == 0 || r[1] == 0) continue;
+        ok = ok && in(r[2], r[0], r[1], r[3], clen);
+        for (int64_t k = 0; k < r[5] && ok; ++k) {
+          const int64_t* q = &sg[SF * (r[4] + k)];
+          ok = ok && q[4] > 0 && in(q[0], r[0], q[4], q[1], alen) && in(q[2], q[4], r[1], q[3], blen);
+        }
+      }
+    };
+    check_tasks(t1, s1, c[C_NT1], c[C_LWLEN], c[C_THETA], c[C_ZLEN]);
+    check_tasks(t2, s2, c[C_NT2], c[C_ZLEN], c[C_WRLEN], c[C_THETA]);
+    for (int64_t i = 0; i < c[C_NLW] && ok; ++i) {
+      const int64_t* r = &lw[LWF * i];
+      ok = ok && r[7] >= 0 && r[7] + r[5] * r[6] <= c[C_LWLEN];
+      for (int64_t k = r[8]; k < r[9] && ok; ++k) {
+        int w = h->wi_idx[4 * wperm_i[k]];
+        int64_t off = lmap[(size_t)w * d.n_l + r[3]];
+        ok = ok && off >= 0 && off + r[5] * r[6] <= c[C_LENV];
+      }
+    }
+    for (int64_t i = 0; i < c[C_NWR] && ok; ++i) {
+      const int64_t* r = &wr[WRF * i];
+      ok = ok && r[7] >= 0 && r[7] + r[5] * r[6] <= c[C_WRLEN];
+      for (int64_t k = r[8]; k < r[9] && ok; ++k) {
+        int wpp = h->wj_idx[4 * wperm_j[k] + 1];
+        int64_t off = rmap[(size_t)wpp * d.n_r + r[3]];
+        ok = ok && off >= 0 && off + r[5] * r[6] <= c[C_RENV];
+      }
+    }
+    if (!ok) {
+      delete h;
+      return mrd_fail(ctx, MRD_E_STATE, "mrd_heff_create: internal table check failed (out-of-range block)");
+    }
+  }
+  Arena& B = h->data_mem;
+  if (e == cudaSuccess) e = B.alloc(&h->lw, (size_t)h->counts[C_LWLEN]);
+  if (e == cudaSuccess) e = B.alloc(&h->wr, (size_t)h->counts[C_WRLEN]);
+  if (e == cudaSuccess) e = B.alloc(&h->z, (size_t)h->counts[C_ZLEN]);
+  if (e != cudaSuccess) {
+    delete h;
+    return mrd_cuda_fail(ctx, e, "mrd_heff_create: operand buffers");
+  }
+
+  // flops in the order of the definition (host arithmetic on the device-built tables)
+  {
+    std::vector<int64_t> mid(MIDF * h->counts[C_NMID]);
+    e = cudaMemcpy(mid.data(), p.mid, mid.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { delete h; return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
+    // theta blocks (a, s1, s2) -> (d_a, d_b, b)
+    struct TB { int a, s1, s2, b; int64_t da, db; };
+    std::vector<TB> tb;
+    for (int64_t m = 0; m < h->counts[C_NMID]; ++m) {
+      const int64_t* r = &mid[MIDF * m];
+      for (int s1 = 0; s1 < 2; ++s1)
+        for (int s2 = 0; s2 < 2; ++s2) {
+          if (r[5 + s1] < 0 || r[8 + s2] < 0) continue;
+          int a = (int)r[5 + s1], b = (int)r[8 + s2];
+          tb.push_back({a, s1, s2, b, h->left[3 * a + 2], h->right[3 * b + 2]});
+        }
+    }
+    auto find = [&](const std::vector<int32_t>& sec, int N, int K) {
+      int n = (int)sec.size() / 3;
+      for (int i = 0; i < n; ++i) if (sec[3 * i] == N && sec[3 * i + 1] == K) return i;
+      return -1;
+    };
+    double fl = 0.0;
+    std::vector<std::vector<std::vector<std::tuple<int, int, int64_t, int64_t>>>> xk(
+        d.d_l, std::vector<std::vector<std::tuple<int, int, int64_t, int64_t>>>(4));
+    for (const TB& t : tb)
+      for (int w = 0; w < d.d_l; ++w) {
+        int ap = find(h->left, h->left[3 * t.a] + h->cl[2 * w], kmod(h->left[3 * t.a + 1] + h->cl[2 * w + 1], d.mod));
+        if (ap < 0) continue;
+        int64_t dp = h->left[3 * ap + 2];
+        fl += 8.0 * dp * t.da * t.db;
+        xk[w][t.s1 * 2 + t.s2].emplace_back(ap, t.b, dp, t.db);
+      }
+    std::vector<std::vector<std::tuple<int, int, int, double>>> wj_by(d.d_m);
+    for (int e2 = 0; e2 < d.nnz_j; ++e2)
+      wj_by[h->wj_idx[4 * e2]].emplace_back(h->wj_idx[4 * e2 + 1], h->wj_idx[4 * e2 + 2], h->wj_idx[4 * e2 + 3], 0.0);
+    std::set<std::tuple<int, int, int, int, int>> ykeys;
+    std::vector<std::tuple<int, int, int, int, int, int64_t, int64_t>> ylist;
+    for (int e1 = 0; e1 < d.nnz_i; ++e1) {
+      int w = h->wi_idx[4 * e1], wp = h->wi_idx[4 * e1 + 1], s1p = h->wi_idx[4 * e1 + 2], s1 = h->wi_idx[4 * e1 + 3];
+      for (const auto& j : wj_by[wp]) {
+        int wpp = std::get<0>(j), s2p = std::get<1>(j), s2 = std::get<2>(j);
+        for (const auto& x : xk[w][s1 * 2 + s2]) {
+          fl += 8.0 * std::get<2>(x) * std::get<3>(x);
+          auto key = std::make_tuple(wpp, std::get<0>(x), s1p, s2p, std::get<1>(x));
+          if (ykeys.insert(key).second) ylist.emplace_back(wpp, std::get<0>(x), s1p, s2p, std::get<1>(x), std::get<2>(x), std::get<3>(x));
+        }
+      }
+    }
+    for (const auto& y : ylist) {
+      int wpp = std::get<0>(y), bi = std::get<4>(y);
+      int bp = find(h->right, h->right[3 * bi] + h->cr[2 * wpp], kmod(h->right[3 * bi + 1] + h->cr[2 * wpp + 1], d.mod));
+      if (bp >= 0) fl += 8.0 * std::get<5>(y) * std::get<6>(y) * h->right[3 * bp + 2];
+    }
+    h->def_flops = fl;
+  }
+  *out = h;
+  return MRD_OK;
+}
+
+int mrd_heff_free(mrd_heff* h) {
+  if (!h) return MRD_OK;
+  Guard g(h->ctx->device);
+  cudaStreamSynchronize(h->ctx->stream);
+  delete h;
+  return MRD_OK;
+}
+
+int mrd_heff_sizes(const mrd_heff* h, int64_t* theta_len, int64_t* lenv_len, int64_t* renv_len) {
+  if (!h) return MRD_E_ARG;
+  if (theta_len) *theta_len = h->counts[C_THETA];
+  if (lenv_len) *lenv_len = h->counts[C_LENV];
+  if (renv_len) *renv_len = h->counts[C_RENV];
+  return MRD_OK;
+}
+
+int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev) {
+  if (!h) return MRD_E_ARG;
+  mrd_ctx* ctx = h->ctx;
+  if ((!lenv_dev && h->counts[C_LENV] > 0) || (!renv_dev && h->counts[C_RENV] > 0))
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_set_env: null environment");
+  Guard g(ctx->device);
+  cudaError_t e = launch_fold_env((const double2*)lenv_dev, h->lw, h->p.lw, h->counts[C_NLW], h->p.lmap, h->d.n_l,
+                                  h->p.wi_perm, h->p.wi_idx, h->wi_val, 0, ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_fold_env((const double2*)renv_dev, h->wr, h->p.wr, h->counts[C_NWR], h->p.rmap, h->d.n_r,
+                        h->p.wj_perm, h->p.wj_idx, h->wj_val, 1, ctx->stream);
+  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_set_env");
+  h->env_loaded = true;
+  return MRD_OK;
+}
+
+int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev, int32_t prec) {
+  if (!h) return MRD_E_ARG;
+  mrd_ctx* ctx = h->ctx;
+  if (!h->env_loaded) return mrd_fail(ctx, MRD_E_STATE, "mrd_heff_apply: environments not loaded");
+  if (prec != MRD_PREC_FP64) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: unsupported precision");
+  const int64_t n = h->counts[C_THETA];
+  if (n > 0 && (!theta_in_dev || !theta_out_dev)) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: null theta");
+  const char* a = (const char*)theta_in_dev;
+  const char* b = (const char*)theta_out_dev;
+  if (n > 0 && a < b + n * 16 && b < a + n * 16) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: theta_in and theta_out overlap");
+  Guard g(ctx->device);
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (h->timing) {
+    e0 = take_event(h); e1 = take_event(h); e2 = take_event(h);
+    if (!e0 || !e1 || !e2) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
+  }
+  cudaError_t e = cudaMemsetAsync(theta_out_dev, 0, (size_t)n * 16, s);
+  if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess)
+    e = launch_cgemm_fp64(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1, h->p.seg1, h->p.tile1,
+                          h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s);
+  if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess)
+    e = launch_cgemm_fp64(h->z, h->wr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
+                          h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s);
+  if (e == cudaSuccess && e2) e = cudaEventRecord(e2, s);
+  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply");
+  return MRD_OK;
+}
+
+int mrd_heff_flops(const mrd_heff* h, double* flops4) {
+  if (!h || !flops4) return MRD_E_ARG;
+  flops4[0] = h->def_flops;
+  flops4[1] = (double)h->counts[C_FLOPS1] + (double)h->counts[C_FLOPS2];
+  flops4[2] = (double)h->counts[C_FLOPS1];
+  flops4[3] = (double)h->counts[C_FLOPS2];
+  return MRD_OK;
+}
+
+int mrd_heff_timing(mrd_heff* h, int32_t on) {
+  if (!h) return MRD_E_ARG;
+  h->timing = on != 0;
+  return MRD_OK;
+}
+
+int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls) {
+  if (!h) return MRD_E_ARG;
+  mrd_ctx* ctx = h->ctx;
+  Guard g(ctx->device);
+  double a = 0.0, b = 0.0;
+  const size_t n = h->ev.size() / 3;
+  if (n) MRD_CUDA(ctx, cudaEventSynchronize(h->ev.back()));
+  for (size_t i = 0; i < n; ++i) {
+    float x = 0.f, y = 0.f;
+    MRD_CUDA(ctx, cudaEventElapsedTime(&x, h->ev[3 * i], h->ev[3 * i + 1]));
+    MRD_CUDA(ctx, cudaEventElapsedTime(&y, h->ev[3 * i + 1], h->ev[3 * i + 2]));
+    a += x;
+    b += y;
+  }
+  for (cudaEvent_t e : h->ev) h->ev_pool.push_back(e);
+  h->ev.clear();
+  if (ms_step1) *ms_step1 = a;
+  if (ms_step2) *ms_step2 = b;
+  if (n_calls) *n_calls = (int32_t)n;
+  return MRD_OK;
+}
+
+int mrd_heff_table(const mrd_heff* h, int32_t which, int64_t* rows, int64_t* count) {
+  if (!h || !count) return MRD_E_ARG;
+  mrd_ctx* ctx = h->ctx;
+  Guard g(ctx->device);
+  if (which == 0) {
+    const int64_t n = h->counts[C_NMID];
+    *count = n;
+    if (!rows) return MRD_OK;
+    std::vector<int64_t> mid(MIDF * n);
+    MRD_CUDA(ctx, cudaMemcpy(mid.data(), h->p.mid, mid.size() * 8, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t* r = &mid[MIDF * i];
+      int64_t* o = rows + 8 * i;
+      int64_t flags = (r[5] >= 0 ? 1 : 0) | (r[6] >= 0 ? 2 : 0) | (r[8] >= 0 ? 4 : 0) | (r[9] >= 0 ? 8 : 0);
+      o[0] = r[0]; o[1] = r[1]; o[2] = r[2]; o[3] = r[3]; o[4] = r[4];
+      o[5] = r[6] >= 0 ? r[7] : -1; o[6] = r[9] >= 0 ? r[10] : -1; o[7] = flags;
+    }
+    return MRD_OK;
+  }
+  if (which == 1 || which == 2) {
+    const bool lft = which == 1;
+    const int nsec = lft ? h->d.n_l : h->d.n_r, nch = lft ? h->d.d_l : h->d.d_r;
+    std::vector<int64_t> map((size_t)nsec * nch);
+    MRD_CUDA(ctx, cudaMemcpy(map.data(), lft ? h->p.lmap : h->p.rmap, map.size() * 8, cudaMemcpyDeviceToHost));
+    const std::vector<int32_t>& sec = lft ? h->left : h->right;
+    const std::vector<int32_t>& ch = lft ? h->cl : h->cr;
+    int64_t k = 0;
+    for (int w = 0; w < nch; ++w)
+      for (int x = 0; x < nsec; ++x) {
+        int64_t off = map[(size_t)w * nsec + x];
+        if (off < 0) continue;
+        if (rows) {
+          int N = sec[3 * x] + ch[2 * w], K = kmod(sec[3 * x + 1] + ch[2 * w + 1], h->d.mod);
+          int xp = -1;
+          for (int i = 0; i < nsec; ++i) if (sec[3 * i] == N && sec[3 * i + 1] == K) xp = i;
+          int64_t* o = rows + 6 * k;
+          o[0] = w; o[1] = x; o[2] = xp; o[3] = off;
+          o[4] = lft ? sec[3 * xp + 2] : sec[3 * x + 2];
+          o[5] = lft ? sec[3 * x + 2] : sec[3 * xp + 2];
+        }
+        ++k;
+      }
+    *count = k;
+    return MRD_OK;
+  }
+  return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_table: unknown table");
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// Internal declarations shared by the translation units of libmrdmrg.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mrdmrg.h"
+
+namespace mrd {
+
+struct HostMPO {
+  int n_sites = 0;
+  int modulus = 1;
+  std::vector<std::vector<int32_t>> bond_charges;  // per bond: 2*dim
+  std::vector<std::vector<int32_t>> site_idx;      // per site: 4*nnz
+  std::vector<std::vector<double>> site_val;       // per site: 2*nnz
+};
+
+int build_mpo_host(const mrd_model& m, HostMPO* out, std::string* err);
+
+// Packed charge key: lexicographic in (N, K).
+__host__ __device__ inline int64_t qkey(int32_t n, int32_t k) {
+  return ((int64_t)(n + (1 << 29)) << 32) | (int64_t)(uint32_t)k;
+}
+
+// A device buffer owned by the library.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace mrd
+
+struct mrd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+};
+
+struct mrd_mpo {
+  mrd_ctx* ctx = nullptr;
+  mrd::HostMPO h;
+};
+
+// Status helpers: set the context's message and return a code.
+int mrd_fail(mrd_ctx* ctx, int code, const std::string& msg);
+int mrd_cuda_fail(mrd_ctx* ctx, cudaError_t e, const char* where);
+
+#define MRD_CUDA(ctx, call)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return mrd_cuda_fail(ctx, e_, #call); \
+  } while (0)

@@ -11,7 +11,8 @@ mix(seed + (i + 1) * GOLDEN). Doubles are the top 53 bits scaled by 2**-53.
 Bond-sector recipe (stand-in for the sector-size histogram of a converged Hofstadter run,
 whose figures the paper does not print): sectors (N_rel, K) with N_rel in [-3, 3] around
 the mean filling of the bond and K in Z_{L_y}; weight exp(-N_rel^2 / (2 sigma^2)) *
-(1 + 0.25 u), u uniform in [-1, 1); dim = max(4, floor(chi * w / sum w)); the largest
+(1 + 0.25 u), u uniform in [-1, 1); every sector first gets the minimum dim 4 and the
+remaining chi - 4 * n_sectors is split in proportion to the weights (floor); the largest
 sector absorbs the remainder so that the dims sum to chi exactly.
 """
 from __future__ import annotations
@@ -65,7 +66,10 @@ def bond_sectors(chi: int, ly: int, n_mean: int, seed: int, sigma_n: float = 0.6
     keys = [(n_mean + dn, k) for dn in range(-n_rel_max, n_rel_max + 1) for k in range(ly)]
     u = uniform_pm1(seed, len(keys))
     w = np.array([np.exp(-((n - n_mean) ** 2) / (2 * sigma_n ** 2)) for n, _ in keys]) * (1 + 0.25 * u)
-    dims = np.maximum(min_dim, np.floor(chi * w / w.sum()).astype(np.int64))
+    spare = chi - min_dim * len(keys)
+    if spare < 0:
+        raise ValueError("chi too small for the sector recipe")
+    dims = min_dim + np.floor(spare * w / w.sum()).astype(np.int64)
     big = int(np.argmax(dims))
     dims[big] += chi - int(dims.sum())
     if dims[big] < max(min_dim, 1):
