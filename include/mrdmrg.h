@@ -139,6 +139,29 @@ int mrd_heff_flops(const mrd_heff* h, double* flops4);
 int mrd_heff_timing(mrd_heff* h, int32_t on);
 int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls);
 
+/* Capacity of the static scratch used by mrd_heff_apply_noalloc, in complex128 elements
+ * (64 MiB). */
+#define MRD_NOALLOC_Z_MAX_ELEMS (4194304)
+
+/* theta_out = H_eff theta_in like mrd_heff_apply with MRD_PREC_FP64, but this call
+ * allocates nothing: no cudaMalloc, cudaFree or other allocating routine. It is for callers
+ * that may not allocate device memory when they need the product, for instance code whose
+ * device memory is owned by an external pool that must see every allocation, or a thread
+ * that must not touch the CUDA allocator while work is being captured elsewhere. (The paper
+ * has no counterpart; this is an interface convenience.)
+ *
+ * The step-1 intermediate Z (normally a buffer allocated by mrd_heff_create) lives instead in
+ * a static device array of MRD_NOALLOC_Z_MAX_ELEMS complex128 elements that every GPU which
+ * loads this library keeps until the process exits. Problems whose Z is larger are rejected
+ * with MRD_E_ARG and a message naming both sizes; use mrd_heff_apply for them. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current), so make that first call before any stream capture. All calls share the one
+ * array: two calls whose device work overlaps in time (different streams or contexts) race
+ * and give wrong results; calls ordered on one stream are safe. theta_out is cleared by the
+ * call; Z needs no clearing because step 2 reads only what step 1 of the same call wrote.
+ * The handle must have its environments loaded (mrd_heff_set_env). */
+int mrd_heff_apply_noalloc(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev);
+
 /* Table export for bit-exact checks. which = 0: middle sectors, 8 int64 per row
  * (N, K, rowdim, coldim, offset, row_off_s1=1, col_off_s2=1, flags); which = 1: left-env
  * blocks, 6 int64 (w, a, a', offset, rows, cols); which = 2: right-env blocks, 6 int64

@@ -62,6 +62,7 @@ _SIGS = {
     "mrd_heff_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "mrd_heff_flops": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_heff_table": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mrd_heff_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
@@ -225,6 +226,10 @@ class Heff:
 
     def apply(self, theta_in, theta_out, prec=MRD_PREC_FP64):
         self.ctx.check(lib().mrd_heff_apply(self.h, _ptr(theta_in), _ptr(theta_out), prec))
+
+    def apply_noalloc(self, theta_in, theta_out):
+        """mrd_heff_apply_noalloc: same product, no device allocation (static scratch)."""
+        self.ctx.check(lib().mrd_heff_apply_noalloc(self.h, _ptr(theta_in), _ptr(theta_out)))
 
     def flops(self):
         """(definition-order, executed, executed step 1, executed step 2) real flops."""

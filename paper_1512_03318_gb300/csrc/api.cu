@@ -577,3 +577,20 @@ int mrd_heff_table(const mrd_heff* h, int32_t which, int64_t* rows, int64_t* cou
 }
 
 }  // extern "C"
+
+namespace mrd {
+
+// Read-only view of a handle for mrd_heff_apply_noalloc (heff_noalloc.cu).
+int mrd_heff_internal_noalloc_view(const mrd_heff* h, PlanPtrs* p, int64_t* counts, const double2** lw,
+                                   const double2** wr, int* n_sm, mrd_ctx** ctx, bool* env_loaded) {
+  *p = h->p;
+  for (int i = 0; i < C_NCOUNTS; ++i) counts[i] = h->counts[i];
+  *lw = h->lw;
+  *wr = h->wr;
+  *n_sm = h->n_sm;
+  *ctx = h->ctx;
+  *env_loaded = h->env_loaded;
+  return MRD_OK;
+}
+
+}  // namespace mrd
