@@ -139,6 +139,24 @@ int mrd_heff_flops(const mrd_heff* h, double* flops4);
 int mrd_heff_timing(mrd_heff* h, int32_t on);
 int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls);
 
+/* ------------------------------------------------------------------ eigensolver */
+
+#define MRD_LANCZOS_MAX_ITER 60
+
+/* Lowest eigenpair of H_eff by Lanczos with full reorthogonalisation (two classical
+ * Gram-Schmidt passes per step), the standard DMRG eigensolver. theta_dev: start vector
+ * on entry, normalised ground vector on exit (device, complex128, theta layout). Stops when
+ * the lowest Ritz value changes by less than tol * |E|, when the Krylov space is exhausted,
+ * or after max_iter (1..MRD_LANCZOS_MAX_ITER) matvecs. The matvecs use precision `prec`;
+ * all vector arithmetic and the tridiagonal eigenproblem are FP64 on the device. Writes the
+ * Ritz value to *energy and the number of matvecs to *iters. The workspace ((max+1)
+ * vectors) is allocated on the first call and kept by the handle. */
+int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, int32_t prec, double* energy,
+                int32_t* iters);
+/* Rayleigh quotient E = <theta, H theta> / <theta, theta> with one matvec of precision
+ * `prec` (FP64 on the device), and the relative residual |H theta - E theta| / |theta|. */
+int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double* energy, double* residual);
+
 /* Capacity of the static scratch used by mrd_heff_apply_noalloc, in complex128 elements
  * (64 MiB). */
 #define MRD_NOALLOC_Z_MAX_ELEMS (4194304)

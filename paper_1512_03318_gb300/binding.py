@@ -16,6 +16,27 @@ MRD_BASIS_MIXED = 0
 MRD_BASIS_REAL = 1
 
 _LIB = None
+_LIVE = []        # weak references to open handles, closed in creation-reverse order at exit
+
+
+def _register(obj):
+    import weakref
+    _LIVE.append(weakref.ref(obj))
+
+
+def _close_all():
+    for r in reversed(_LIVE):
+        o = r()
+        if o is not None:
+            try:
+                o.close()
+            except Exception:
+                pass
+    _LIVE.clear()
+
+
+import atexit  # noqa: E402
+atexit.register(_close_all)
 
 
 def lib_path() -> str:
@@ -63,6 +84,10 @@ _SIGS = {
     "mrd_heff_flops": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_heff_table": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mrd_heff_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrd_lanczos": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.POINTER(C.c_double),
+                              C.POINTER(C.c_int32)]),
+    "mrd_heff_rayleigh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
@@ -127,6 +152,7 @@ class Context:
             raise MrdError(rc, "mrd_create failed")
         self.h = h
         self.device = device
+        _register(self)
 
     def check(self, rc):
         if rc != 0:
@@ -166,6 +192,7 @@ class MPO:
             msg = lib().mrd_last_error(ctx.h).decode() if ctx is not None else "mrd_mpo_build failed"
             raise MrdError(rc, msg)
         self.h = h
+        _register(self)
         n, mod = C.c_int32(), C.c_int32()
         lib().mrd_mpo_info(h, C.byref(n), C.byref(mod))
         self.n_sites, self.modulus, self.ly = n.value, mod.value, ly
@@ -185,9 +212,14 @@ class MPO:
         lib().mrd_mpo_site(self.h, j, C.byref(nnz), _p32(idx), _p64f(val))
         return idx.reshape(-1, 4), val[0::2] + 1j * val[1::2]
 
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrd_mpo_free(self.h)
+            self.h = None
+
     def __del__(self):
         try:
-            lib().mrd_mpo_free(self.h)
+            self.close()
         except Exception:
             pass
 
@@ -217,6 +249,7 @@ class Heff:
         h = C.c_void_p()
         ctx.check(lib().mrd_heff_create(ctx.h, C.byref(d), C.byref(h)))
         self.h = h
+        _register(self)
         t, l, r = C.c_int64(), C.c_int64(), C.c_int64()
         lib().mrd_heff_sizes(h, C.byref(t), C.byref(l), C.byref(r))
         self.theta_len, self.lenv_len, self.renv_len = t.value, l.value, r.value
@@ -226,6 +259,17 @@ class Heff:
 
     def apply(self, theta_in, theta_out, prec=MRD_PREC_FP64):
         self.ctx.check(lib().mrd_heff_apply(self.h, _ptr(theta_in), _ptr(theta_out), prec))
+
+    def lanczos(self, theta, max_iter=30, tol=1e-13, prec=MRD_PREC_FP64):
+        """In place: theta (device) -> ground vector; returns (energy, matvecs)."""
+        e, it = C.c_double(), C.c_int32()
+        self.ctx.check(lib().mrd_lanczos(self.h, _ptr(theta), max_iter, tol, prec, C.byref(e), C.byref(it)))
+        return e.value, it.value
+
+    def rayleigh(self, theta, prec=MRD_PREC_FP64):
+        e, r = C.c_double(), C.c_double()
+        self.ctx.check(lib().mrd_heff_rayleigh(self.h, _ptr(theta), prec, C.byref(e), C.byref(r)))
+        return e.value, r.value
 
     def apply_noalloc(self, theta_in, theta_out):
         """mrd_heff_apply_noalloc: same product, no device allocation (static scratch)."""

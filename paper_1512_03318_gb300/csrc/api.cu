@@ -1,5 +1,6 @@
 // C ABI entry points (include/mrdmrg.h): argument checks, device memory, launches.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <set>
@@ -18,9 +19,25 @@ cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, co
 cudaError_t launch_fold_env(const double2* env, double2* out, const int64_t* rows, int64_t nrows,
                             const int64_t* env_map, int n_sec, const int32_t* perm, const int32_t* idx,
                             const double* val, int chan_field, cudaStream_t s);
+struct Lanczos;
+void lanczos_free(Lanczos* L);
+cudaError_t lanczos_alloc(Lanczos** out, int64_t n);
+int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, double2*), void* op, double2* theta,
+                int max_iter, double tol, double* energy, int* iters, double* beta_last);
+int vdot(Lanczos* L, mrd_ctx* ctx, const double2* u, const double2* v, double* re, double* im);
+double2* lanczos_work(Lanczos* L);
 }  // namespace mrd
 
 using namespace mrd;
+
+void mrd_ctx_retain(mrd_ctx* ctx) {
+  if (ctx) ++ctx->refs;
+}
+
+void mrd_ctx_release(mrd_ctx* ctx) {
+  if (!ctx) return;
+  if (--ctx->refs == 0 && ctx->destroyed) delete ctx;
+}
 
 int mrd_fail(mrd_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -92,9 +109,11 @@ struct mrd_heff {
   bool timing = false;
   std::vector<cudaEvent_t> ev;   // 3 per recorded apply: before step 1, between, after step 2
   std::vector<cudaEvent_t> ev_pool;
+  Lanczos* lz = nullptr;
   ~mrd_heff() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    lanczos_free(lz);
   }
 };
 
@@ -127,7 +146,9 @@ int mrd_create(mrd_ctx** out, int device, void* stream) {
 }
 
 int mrd_destroy(mrd_ctx* ctx) {
-  delete ctx;
+  if (!ctx) return MRD_OK;
+  ctx->destroyed = true;
+  if (ctx->refs == 0) delete ctx;
   return MRD_OK;
 }
 
@@ -236,6 +257,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
   Guard g(ctx->device);
   mrd_heff* h = new mrd_heff();
   h->ctx = ctx;
+  mrd_ctx_retain(ctx);
   cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   h->left.assign(D.left, D.left + 3 * D.n_left);
   h->right.assign(D.right, D.right + 3 * D.n_right);
@@ -282,6 +304,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
 #undef ALLOC
   if (e != cudaSuccess) {
     delete h;
+    mrd_ctx_release(ctx);
     return mrd_cuda_fail(ctx, e, "mrd_heff_create: cudaMalloc");
   }
   p.left = left; p.right = right; p.cl = cl; p.cm = cm; p.cr = cr; p.wi_idx = wi; p.wj_idx = wj;
@@ -298,6 +321,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     delete h;
+    mrd_ctx_release(ctx);
     return mrd_cuda_fail(ctx, e, "mrd_heff_create: plan");
   }
   // Host check of the device-built tables before any kernel reads through them: every
@@ -316,7 +340,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
     dl(lmap, p.lmap, (size_t)d.d_l * d.n_l); dl(rmap, p.rmap, (size_t)d.d_r * d.n_r);
     if (e == cudaSuccess && d.nnz_i) e = cudaMemcpy(wperm_i.data(), p.wi_perm, d.nnz_i * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && d.nnz_j) e = cudaMemcpy(wperm_j.data(), p.wj_perm, d.nnz_j * 4, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) { delete h; return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
+    if (e != cudaSuccess) { delete h; mrd_ctx_release(ctx); return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
     bool ok = c[C_NMID] <= d.mid_cap && c[C_NLW] <= d.lw_cap && c[C_NWR] <= d.wr_cap && c[C_NZ] <= d.z_cap;
     auto in = [](int64_t off, int64_t rows, int64_t cols, int64_t ld, int64_t len) {
       if (rows == 0 || cols == 0) return true;
@@ -356,6 +380,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
     }
     if (!ok) {
       delete h;
+      mrd_ctx_release(ctx);
       return mrd_fail(ctx, MRD_E_STATE, "mrd_heff_create: internal table check failed (out-of-range block)");
     }
   }
@@ -365,6 +390,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
   if (e == cudaSuccess) e = B.alloc(&h->z, (size_t)h->counts[C_ZLEN]);
   if (e != cudaSuccess) {
     delete h;
+    mrd_ctx_release(ctx);
     return mrd_cuda_fail(ctx, e, "mrd_heff_create: operand buffers");
   }
 
@@ -372,7 +398,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
   {
     std::vector<int64_t> mid(MIDF * h->counts[C_NMID]);
     e = cudaMemcpy(mid.data(), p.mid, mid.size() * 8, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) { delete h; return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
+    if (e != cudaSuccess) { delete h; mrd_ctx_release(ctx); return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
     // theta blocks (a, s1, s2) -> (d_a, d_b, b)
     struct TB { int a, s1, s2, b; int64_t da, db; };
     std::vector<TB> tb;
@@ -430,9 +456,13 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
 
 int mrd_heff_free(mrd_heff* h) {
   if (!h) return MRD_OK;
-  Guard g(h->ctx->device);
-  cudaStreamSynchronize(h->ctx->stream);
-  delete h;
+  mrd_ctx* ctx = h->ctx;
+  {
+    Guard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    delete h;
+  }
+  mrd_ctx_release(ctx);
   return MRD_OK;
 }
 
@@ -497,6 +527,65 @@ int mrd_heff_flops(const mrd_heff* h, double* flops4) {
   flops4[1] = (double)h->counts[C_FLOPS1] + (double)h->counts[C_FLOPS2];
   flops4[2] = (double)h->counts[C_FLOPS1];
   flops4[3] = (double)h->counts[C_FLOPS2];
+  return MRD_OK;
+}
+
+struct ApplyArg {
+  mrd_heff* h;
+  int32_t prec;
+};
+
+static int apply_cb(void* op, const double2* in, double2* out) {
+  ApplyArg* a = (ApplyArg*)op;
+  return mrd_heff_apply(a->h, (const double*)in, (double*)out, a->prec);
+}
+
+static int ensure_lanczos(mrd_heff* h) {
+  if (h->lz) return MRD_OK;
+  cudaError_t e = lanczos_alloc(&h->lz, h->counts[C_THETA]);
+  if (e != cudaSuccess) return mrd_cuda_fail(h->ctx, e, "Lanczos workspace");
+  return MRD_OK;
+}
+
+int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, int32_t prec, double* energy,
+                int32_t* iters) {
+  if (!h || !energy || !iters) return MRD_E_ARG;
+  mrd_ctx* ctx = h->ctx;
+  if (!h->env_loaded) return mrd_fail(ctx, MRD_E_STATE, "mrd_lanczos: environments not loaded");
+  if (!theta_dev || h->counts[C_THETA] == 0) return mrd_fail(ctx, MRD_E_ARG, "mrd_lanczos: empty or null theta");
+  Guard g(ctx->device);
+  int rc = ensure_lanczos(h);
+  if (rc != MRD_OK) return rc;
+  ApplyArg arg{h, prec};
+  int it = 0;
+  rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr);
+  *iters = it;
+  return rc;
+}
+
+int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double* energy, double* residual) {
+  if (!h || !energy) return MRD_E_ARG;
+  mrd_ctx* ctx = h->ctx;
+  if (!theta_dev || h->counts[C_THETA] == 0) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_rayleigh: empty theta");
+  Guard g(ctx->device);
+  int rc = ensure_lanczos(h);
+  if (rc != MRD_OK) return rc;
+  double2* hv = lanczos_work(h->lz);   // the workspace's spare vector
+  rc = mrd_heff_apply(h, theta_dev, (double*)hv, prec);
+  if (rc != MRD_OK) return rc;
+  double nn, ni, en, ei;
+  if ((rc = vdot(h->lz, ctx, (const double2*)theta_dev, (const double2*)theta_dev, &nn, &ni)) != MRD_OK) return rc;
+  if ((rc = vdot(h->lz, ctx, (const double2*)theta_dev, hv, &en, &ei)) != MRD_OK) return rc;
+  if (!(nn > 0)) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_rayleigh: zero vector");
+  const double e = en / nn;
+  *energy = e;
+  if (residual) {
+    double hh, hi;
+    if ((rc = vdot(h->lz, ctx, hv, hv, &hh, &hi)) != MRD_OK) return rc;
+    // |Hv - E v|^2 = <Hv,Hv> - 2 E Re<v,Hv> + E^2 <v,v>
+    double r2 = hh - 2.0 * e * en + e * e * nn;
+    *residual = std::sqrt(r2 > 0 ? r2 : 0.0) / std::sqrt(nn);
+  }
   return MRD_OK;
 }
 

@@ -37,7 +37,13 @@ struct mrd_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   std::string err;
+  int refs = 0;            // live handles created on this context
+  bool destroyed = false;  // mrd_destroy called; deleted when refs drops to 0
 };
+
+// Reference counting so that handles and contexts may be released in any order.
+void mrd_ctx_retain(mrd_ctx* ctx);
+void mrd_ctx_release(mrd_ctx* ctx);
 
 struct mrd_mpo {
   mrd_ctx* ctx = nullptr;

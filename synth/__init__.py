@@ -128,3 +128,13 @@ def random_channel_charges(d_left: int, d_mid: int, d_right: int, m1: int, m2: i
     cm = grow(cl, d_mid, m1)
     cr = grow(cm, d_right, m2)
     return cl, cm, cr
+
+
+def hermitian_blocks(dims, seed):
+    """Random Hermitian blocks X + X^+ (X entries complex U[-1, 1)), one per dim, flattened
+    row-major and concatenated."""
+    out = []
+    for i, d in enumerate(dims):
+        x = complex_pm1(substream(seed, i), d * d).reshape(d, d)
+        out.append((x + x.conj().T).reshape(-1))
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.complex128)
