@@ -63,6 +63,7 @@ extern "C" {
 typedef struct mrd_ctx mrd_ctx;
 typedef struct mrd_mpo mrd_mpo;
 typedef struct mrd_heff mrd_heff;
+typedef struct mrd_dmrg mrd_dmrg;
 
 /* ------------------------------------------------------------------ context */
 
@@ -156,6 +157,52 @@ int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, in
 /* Rayleigh quotient E = <theta, H theta> / <theta, theta> with one matvec of precision
  * `prec` (FP64 on the device), and the relative residual |H theta - E theta| / |theta|. */
 int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double* energy, double* residual);
+
+/* ------------------------------------------------------------------ two-site DMRG */
+
+typedef struct {
+  int32_t chi;               /* bond dimension: keep at most chi Schmidt values per bond     */
+  double svd_cutoff;         /* drop Schmidt values below svd_cutoff * largest (e.g. 1e-14)  */
+  int32_t lanczos_max_iter;  /* 1 .. MRD_LANCZOS_MAX_ITER                                    */
+  double lanczos_tol;        /* relative change of the Ritz value that stops Lanczos         */
+  int32_t prec;              /* MRD_PREC_* of the Lanczos matvecs                            */
+} mrd_dmrg_params;
+
+/* Finite two-site DMRG state on the device for the MPO `mpo` (which must outlive it) in the
+ * charge sector (N = n_part, K = k_tot mod modulus). Starts from a seeded random MPS whose
+ * entries are SplitMix64 draws (counter-based, seed `seed`): sites left of `center` are
+ * left-canonical, the others right-canonical (orthonormalised by the block SVD), and the
+ * left environments up to bond `center` and right environments from bond center+2 are
+ * built. Bond sectors are the exactly reachable charges, each of dimension at most its exact
+ * state count and chi (scaled down so every bond sums to at most chi); if caps/caps_off are
+ * given, bond j only keeps the sectors listed in caps[3*caps_off[j] .. 3*caps_off[j+1]) as
+ * (N, K, max dim) triplets (bonds with an empty list use the default). */
+int mrd_dmrg_create(mrd_ctx* ctx, const mrd_mpo* mpo, int32_t n_part, int32_t k_tot, int32_t chi, uint64_t seed,
+                    int32_t center, const int32_t* caps, const int64_t* caps_off, mrd_dmrg** out);
+int mrd_dmrg_free(mrd_dmrg* d);
+/* One two-site update at sites (i, i+1) (standard two-site DMRG): theta = M_i M_{i+1}, ground
+ * state of H_eff by Lanczos, block SVD of theta by middle charge (the Schmidt decomposition,
+ * Sec. III.C), truncation to chi with cutoff, renormalised Schmidt values; direction +1
+ * moves the orthogonality centre right (A_i = U, M_{i+1} = S V^+, then L_{i+1}) and -1 left
+ * (M_i = U S, B_{i+1} = V^+, then R_{i+1}). Needs L_i and R_{i+2}. Writes the Ritz energy
+ * and the discarded weight. */
+int mrd_two_site_update(mrd_dmrg* d, int32_t i, int32_t direction, const mrd_dmrg_params* p, double* energy,
+                        double* trunc_err);
+/* One sweep: two-site updates left to right over all bonds, then right to left (requires the
+ * centre at site 0). Writes the last energy. */
+int mrd_sweep(mrd_dmrg* d, const mrd_dmrg_params* p, double* energy);
+/* Sectors of MPS bond `bond` (0..n) as (N, K, dim) triplets (sectors may be NULL). */
+int mrd_dmrg_bond(const mrd_dmrg* d, int32_t bond, int32_t* n_sectors, int32_t* sectors);
+/* Copy of MPS tensor `site` to the host (complex128). mode 0: blocks grouped by right
+ * sector r, each a (rows (s, l) with l = r - q(s), s = 0 first) x d_r row-major matrix;
+ * mode 1: grouped by left sector l, each a d_l x (columns (s, r), r = l + q(s)) matrix.
+ * host may be NULL (only *mode and *len are set). */
+int mrd_dmrg_site(mrd_dmrg* d, int32_t site, int32_t* mode, int64_t* len, double* host);
+/* Copy of the left (side 0) or right (side 1) environment at `bond` in the layouts of this
+ * header; *len = -1 if it is not built. */
+int mrd_dmrg_env(mrd_dmrg* d, int32_t bond, int32_t side, int64_t* len, double* host);
+/* Energy, discarded weight and Lanczos matvecs of the last two-site update. */
+int mrd_dmrg_stats(const mrd_dmrg* d, double* energy, double* trunc_err, int32_t* lanczos_iters);
 
 /* Capacity of the static scratch used by mrd_heff_apply_noalloc, in complex128 elements
  * (64 MiB). */

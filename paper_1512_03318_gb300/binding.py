@@ -88,6 +88,17 @@ _SIGS = {
                               C.POINTER(C.c_int32)]),
     "mrd_heff_rayleigh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
+    "mrd_dmrg_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_int32,
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_void_p)]),
+    "mrd_dmrg_free": (C.c_int, [C.c_void_p]),
+    "mrd_two_site_update": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]),
+    "mrd_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "mrd_dmrg_bond": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mrd_dmrg_site": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_double)]),
+    "mrd_dmrg_env": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "mrd_dmrg_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
@@ -215,6 +226,81 @@ class MPO:
     def close(self):
         if getattr(self, "h", None):
             lib().mrd_mpo_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class mrd_dmrg_params(C.Structure):
+    _fields_ = [("chi", C.c_int32), ("svd_cutoff", C.c_double), ("lanczos_max_iter", C.c_int32),
+                ("lanczos_tol", C.c_double), ("prec", C.c_int32)]
+
+
+class DMRG:
+    """Finite two-site DMRG state on the device (mrd_dmrg_*)."""
+
+    def __init__(self, ctx, mpo, n_part, k_tot, chi, seed=1234, center=0, caps=None):
+        self.ctx, self.mpo = ctx, mpo
+        h = C.c_void_p()
+        cp = co = None
+        if caps is not None:     # list over bonds of lists of (N, K, dim)
+            flat = [x for bond in caps for t in bond for x in t]
+            offs = np.cumsum([0] + [len(b) for b in caps]).astype(np.int64)
+            self._caps = (np.array(flat, dtype=np.int32), offs)
+            cp, co = _p32(self._caps[0]), self._caps[1].ctypes.data_as(C.POINTER(C.c_int64))
+        ctx.check(lib().mrd_dmrg_create(ctx.h, mpo.h, n_part, k_tot, chi, seed, center, cp, co, C.byref(h)))
+        self.h = h
+        _register(self)
+
+    @staticmethod
+    def params(chi, cutoff=1e-14, max_iter=30, tol=1e-13, prec=MRD_PREC_FP64):
+        return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec)
+
+    def update(self, i, direction, params):
+        e, t = C.c_double(), C.c_double()
+        self.ctx.check(lib().mrd_two_site_update(self.h, i, direction, C.byref(params), C.byref(e), C.byref(t)))
+        return e.value, t.value
+
+    def sweep(self, params):
+        e = C.c_double()
+        self.ctx.check(lib().mrd_sweep(self.h, C.byref(params), C.byref(e)))
+        return e.value
+
+    def bond(self, b):
+        n = C.c_int32()
+        lib().mrd_dmrg_bond(self.h, b, C.byref(n), None)
+        out = np.zeros(3 * max(n.value, 1), dtype=np.int32)
+        lib().mrd_dmrg_bond(self.h, b, C.byref(n), _p32(out))
+        return out[: 3 * n.value].reshape(-1, 3)
+
+    def site(self, j):
+        mode, ln = C.c_int32(), C.c_int64()
+        self.ctx.check(lib().mrd_dmrg_site(self.h, j, C.byref(mode), C.byref(ln), None))
+        buf = np.zeros(2 * max(ln.value, 1), dtype=np.float64)
+        self.ctx.check(lib().mrd_dmrg_site(self.h, j, C.byref(mode), C.byref(ln), _p64f(buf)))
+        return mode.value, (buf[0::2] + 1j * buf[1::2])[: ln.value]
+
+    def env(self, b, side):
+        ln = C.c_int64()
+        self.ctx.check(lib().mrd_dmrg_env(self.h, b, side, C.byref(ln), None))
+        if ln.value < 0:
+            return None
+        buf = np.zeros(2 * max(ln.value, 1), dtype=np.float64)
+        self.ctx.check(lib().mrd_dmrg_env(self.h, b, side, C.byref(ln), _p64f(buf)))
+        return (buf[0::2] + 1j * buf[1::2])[: ln.value]
+
+    def stats(self):
+        e, t, it = C.c_double(), C.c_double(), C.c_int32()
+        lib().mrd_dmrg_stats(self.h, C.byref(e), C.byref(t), C.byref(it))
+        return e.value, t.value, it.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrd_dmrg_free(self.h)
             self.h = None
 
     def __del__(self):

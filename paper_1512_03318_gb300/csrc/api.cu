@@ -8,8 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "mrd_internal.h"
-#include "plan.cuh"
+#include "heff_internal.h"
 
 namespace mrd {
 cudaError_t launch_plan(const PlanDims& d, const PlanPtrs& p, cudaStream_t s);
@@ -47,86 +46,6 @@ int mrd_fail(mrd_ctx* ctx, int code, const std::string& msg) {
 int mrd_cuda_fail(mrd_ctx* ctx, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorString(e);
   return mrd_fail(ctx, e == cudaErrorMemoryAllocation ? MRD_E_OOM : MRD_E_CUDA, m);
-}
-
-namespace {
-
-// Device arena: a list of allocations freed together.
-struct Arena {
-  std::vector<void*> ptrs;
-  ~Arena() { release(); }
-  void release() {
-    for (void* p : ptrs) cudaFree(p);
-    ptrs.clear();
-  }
-  template <class T>
-  cudaError_t alloc(T** out, size_t count) {
-    void* p = nullptr;
-    size_t bytes = count * sizeof(T);
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) return e;
-    ptrs.push_back(p);
-    *out = (T*)p;
-    return cudaSuccess;
-  }
-};
-
-struct Guard {  // switches to a device for the scope
-  int prev = -1;
-  explicit Guard(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~Guard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-int kmod(int k, int m) { return ((k % m) + m) % m; }
-
-}  // namespace
-
-struct mrd_heff {
-  mrd_ctx* ctx = nullptr;
-  PlanDims d{};
-  PlanPtrs p{};
-  Arena plan_mem;   // tables
-  Arena data_mem;   // LW, WR, Z
-  int64_t counts[C_NCOUNTS] = {0};
-  double* wi_val = nullptr;
-  double* wj_val = nullptr;
-  double2* lw = nullptr;
-  double2* wr = nullptr;
-  double2* z = nullptr;
-  bool env_loaded = false;
-  double def_flops = 0.0;
-  int n_sm = 152;
-  std::vector<int32_t> left, right, cl, cm, cr, wi_idx, wj_idx;
-  std::vector<double> wi_v, wj_v;
-  bool timing = false;
-  std::vector<cudaEvent_t> ev;   // 3 per recorded apply: before step 1, between, after step 2
-  std::vector<cudaEvent_t> ev_pool;
-  Lanczos* lz = nullptr;
-  ~mrd_heff() {
-    for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    lanczos_free(lz);
-  }
-};
-
-static cudaEvent_t take_event(mrd_heff* h) {
-  cudaEvent_t e = nullptr;
-  if (!h->ev_pool.empty()) {
-    e = h->ev_pool.back();
-    h->ev_pool.pop_back();
-  } else if (cudaEventCreate(&e) != cudaSuccess) {
-    return nullptr;
-  }
-  h->ev.push_back(e);
-  return e;
 }
 
 extern "C" {
@@ -332,7 +251,11 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
       v.resize(n);
       if (e == cudaSuccess && n) e = cudaMemcpy(v.data(), src, n * 8, cudaMemcpyDeviceToHost);
     };
-    std::vector<int64_t> t1, s1, t2, s2, lw, wr, lmap, rmap;
+    std::vector<int64_t> t1, s1, t2, s2;
+    std::vector<int64_t>& lw = h->lw_host;
+    std::vector<int64_t>& wr = h->wr_host;
+    std::vector<int64_t>& lmap = h->lmap_host;
+    std::vector<int64_t>& rmap = h->rmap_host;
     std::vector<int32_t> wperm_i(d.nnz_i), wperm_j(d.nnz_j);
     dl(t1, p.t1, (size_t)TF * c[C_NT1]); dl(s1, p.seg1, (size_t)SF * 2 * c[C_NT1]);
     dl(t2, p.t2, (size_t)TF * c[C_NT2]); dl(s2, p.seg2, (size_t)SF * c[C_NT2] * d.seg2_stride);
@@ -396,7 +319,8 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
 
   // flops in the order of the definition (host arithmetic on the device-built tables)
   {
-    std::vector<int64_t> mid(MIDF * h->counts[C_NMID]);
+    std::vector<int64_t>& mid = h->mid_host;
+    mid.resize(MIDF * h->counts[C_NMID]);
     e = cudaMemcpy(mid.data(), p.mid, mid.size() * 8, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { delete h; mrd_ctx_release(ctx); return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
     // theta blocks (a, s1, s2) -> (d_a, d_b, b)

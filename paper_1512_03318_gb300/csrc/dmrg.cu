@@ -1,0 +1,922 @@
+// Two-site DMRG on the device: block-sparse MPS, environments, two-site update and sweep.
+//
+// The paper applies standard finite/infinite DMRG (its refs. W92, S2005, S2011, M08) to the
+// mixed-basis MPO; this file is the finite two-site algorithm on an open cylinder:
+//   theta = M_i M_{i+1}; ground state of H_eff = L W_i W_{i+1} R by Lanczos; block SVD of
+//   theta by middle charge (the Schmidt decomposition, Sec. III.C) truncated to chi;
+//   left- or right-canonical factors; environment update L' = A^+ (L W) A or
+//   R' = B (W R) B^+; sweep left to right and back.
+// Block-sparse MPS tensor M[l, s, r] (r = l + q(s)) is stored either grouped by right sector
+// (mode 0: rows (s, l) stacked per r, the layout of U from the SVD) or grouped by left
+// sector (mode 1: columns (s, r) side by side per l, the layout of V^+). Both are addressed
+// through sub-blocks (l, s) of shape d_l x d_r with a leading dimension.
+// All contractions are grouped complex GEMMs (the FP64 kernel of heff_fp64.cu) over task
+// lists built here from the sector tables; every output block has one owner task.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "heff_internal.h"
+
+namespace mrd {
+
+cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
+                              const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                              int n_sm, cudaStream_t s);
+cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* src_off, int nblk, double2* work,
+                     cudaStream_t s);
+cudaError_t svd_round(double2* work, const int64_t* blk, const int64_t* pair_prefix, int nblk, int64_t npairs,
+                      int round, double tol, int* rotated, cudaStream_t s);
+cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
+                       double* S_sorted, int* order_scratch, cudaStream_t s);
+cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
+                         int* keep, double* info, int* flat_block, cudaStream_t s);
+enum { SVF = 10 };
+
+namespace {
+
+constexpr int kTile = 32;
+
+struct Sec {
+  int32_t N, K, d;
+};
+using Secs = std::vector<Sec>;
+
+int find_sec(const Secs& s, int N, int K) {
+  const int64_t key = qkey(N, K);
+  int lo = 0, hi = (int)s.size() - 1;
+  while (lo <= hi) {
+    const int m = (lo + hi) >> 1;
+    const int64_t k = qkey(s[m].N, s[m].K);
+    if (k == key) return m;
+    if (k < key) lo = m + 1; else hi = m - 1;
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------- device buffers
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~Buf() { if (p) cudaFree(p); }
+  cudaError_t need(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t nb = std::max<size_t>(b, 256);
+    cudaError_t e = cudaMalloc(&p, nb);
+    if (e == cudaSuccess) bytes = nb;
+    return e;
+  }
+  template <class T>
+  T* as() const { return (T*)p; }
+};
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  // SplitMix64 finaliser (Steele, Lea & Flood 2014) of state x
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Counter-based uniform [-1, 1) complex entries: element e of stream `seed`.
+__global__ void k_fill_random(double2* out, int64_t n, uint64_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed + 2 * (uint64_t)e * 0x9E3779B97F4A7C15ull);
+    const uint64_t b = splitmix64(seed + (2 * (uint64_t)e + 1) * 0x9E3779B97F4A7C15ull);
+    out[e] = make_double2(2.0 * (double)(a >> 11) * 0x1.0p-53 - 1.0, 2.0 * (double)(b >> 11) * 0x1.0p-53 - 1.0);
+  }
+}
+
+// Strided block copies with optional scaling by singular values:
+// task: src_off src_ld dst_off dst_ld rows cols scale_mode(0 none, 1 by column, 2 by row) s_off
+enum { CPF = 8 };
+__global__ void k_copy_blocks(const double2* __restrict__ src, double2* __restrict__ dst,
+                              const int64_t* __restrict__ tasks, int ntasks, const double* __restrict__ S,
+                              const double* __restrict__ sscale) {
+  const double g = sscale ? *sscale : 1.0;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const int64_t* d = tasks + CPF * t;
+    const int64_t rows = d[4], cols = d[5], mode = d[6];
+    for (int64_t e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int64_t r = e / cols, c = e % cols;
+      double2 v = src[d[0] + r * d[1] + c];
+      if (mode) {
+        const double f = g * S[d[7] + (mode == 1 ? c : r)];
+        v.x *= f;
+        v.y *= f;
+      }
+      dst[d[2] + r * d[3] + c] = v;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- tensors
+
+struct SiteT {
+  Secs left, right;
+  int m = 0, mod = 1;
+  int mode = 1;
+  std::vector<int64_t> goff, gext;
+  std::vector<std::array<int64_t, 2>> sub;
+  int64_t size = 0;
+  Buf data;
+
+  void layout() {
+    goff.clear(); gext.clear(); sub.clear(); size = 0;
+    if (mode == 0) {
+      for (const Sec& r : right) {
+        std::array<int64_t, 2> so{-1, -1};
+        int64_t rows = 0;
+        for (int s = 0; s < 2; ++s) {
+          const int li = find_sec(left, r.N - s, kmod(r.K - s * m, mod));
+          if (li >= 0) { so[s] = rows; rows += left[li].d; }
+        }
+        goff.push_back(size); gext.push_back(rows); sub.push_back(so);
+        size += rows * r.d;
+      }
+    } else {
+      for (const Sec& l : left) {
+        std::array<int64_t, 2> so{-1, -1};
+        int64_t cols = 0;
+        for (int s = 0; s < 2; ++s) {
+          const int ri = find_sec(right, l.N + s, kmod(l.K + s * m, mod));
+          if (ri >= 0) { so[s] = cols; cols += right[ri].d; }
+        }
+        goff.push_back(size); gext.push_back(cols); sub.push_back(so);
+        size += (int64_t)l.d * cols;
+      }
+    }
+  }
+  // sub-block (li, s): offset and leading dimension; false if absent
+  bool subblock(int li, int s, int64_t* off, int64_t* ld, int* ri_out) const {
+    const Sec& l = left[li];
+    const int ri = find_sec(right, l.N + s, kmod(l.K + s * m, mod));
+    if (ri < 0) return false;
+    if (ri_out) *ri_out = ri;
+    if (mode == 0) {
+      if (sub[ri][s] < 0) return false;
+      *off = goff[ri] + sub[ri][s] * right[ri].d;
+      *ld = right[ri].d;
+    } else {
+      if (sub[li][s] < 0) return false;
+      *off = goff[li] + sub[li][s];
+      *ld = gext[li];
+    }
+    return true;
+  }
+};
+
+struct EnvT {
+  Secs sec;
+  std::vector<std::array<int, 2>> ch;
+  bool left = true;
+  std::vector<int64_t> off;
+  int64_t size = 0;
+  Buf data;
+  void layout(int mod) {
+    off.assign(ch.size() * sec.size(), -1);
+    size = 0;
+    for (size_t w = 0; w < ch.size(); ++w)
+      for (size_t x = 0; x < sec.size(); ++x) {
+        const int xp = find_sec(sec, sec[x].N + ch[w][0], kmod(sec[x].K + ch[w][1], mod));
+        if (xp < 0) continue;
+        off[w * sec.size() + x] = size;
+        size += (int64_t)sec[x].d * sec[xp].d;
+      }
+  }
+};
+
+struct GemmList {
+  std::vector<int64_t> t, s;
+  void task(int64_t M, int64_t N, int64_t c_off, int64_t ldc) {
+    t.insert(t.end(), {M, N, c_off, ldc, (int64_t)(s.size() / SF), 0});
+  }
+  void seg(int64_t a_off, int64_t lda, int64_t b_off, int64_t ldb, int64_t K, int64_t flags) {
+    s.insert(s.end(), {a_off, lda, b_off, ldb, K, flags});
+    t.back() += 1;
+  }
+  void drop_empty_last() {
+    if (!t.empty() && t.back() == 0) t.resize(t.size() - TF);
+  }
+};
+
+}  // namespace mrd
+
+using namespace mrd;
+
+struct mrd_dmrg {
+  mrd_ctx* ctx = nullptr;
+  HostMPO mpo;
+  int n = 0, ly = 0, mod = 1;
+  int n_sm = 152;
+  int target_N = 0, target_K = 0;
+  std::vector<SiteT> A;
+  std::vector<EnvT> L, R;
+  Buf gtask, gseg, gpref, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
+      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, tbuf, zeros;
+  double last_energy = 0.0, last_trunc = 0.0;
+  int last_iters = 0;
+};
+
+namespace {
+
+int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const double2* Bop, int64_t blen, double2* C,
+             int64_t clen) {
+  mrd_ctx* ctx = D->ctx;
+  g.drop_empty_last();
+  const int64_t nt = (int64_t)g.t.size() / TF;
+  if (nt == 0) return MRD_OK;
+  std::vector<int64_t> pref(nt + 1, 0);
+  auto in = [](int64_t off, int64_t rows, int64_t cols, int64_t ld, int64_t len) {
+    if (rows == 0 || cols == 0) return true;
+    return off >= 0 && ld >= cols && off + (rows - 1) * ld + cols <= len;
+  };
+  for (int64_t i = 0; i < nt; ++i) {
+    const int64_t* r = &g.t[TF * i];
+    if (!in(r[2], r[0], r[1], r[3], clen)) return mrd_fail(ctx, MRD_E_STATE, "internal: GEMM output out of range");
+    for (int64_t k = 0; k < r[5]; ++k) {
+      const int64_t* q = &g.s[SF * (r[4] + k)];
+      const bool ta = q[5] & 1, tb = q[5] & 2;
+      bool ok = ta ? in(q[0], q[4], r[0], q[1], alen) : in(q[0], r[0], q[4], q[1], alen);
+      ok = ok && (tb ? in(q[2], r[1], q[4], q[3], blen) : in(q[2], q[4], r[1], q[3], blen));
+      if (!ok) return mrd_fail(ctx, MRD_E_STATE, "internal: GEMM operand out of range");
+    }
+    pref[i + 1] = pref[i] + ((r[0] + kTile - 1) / kTile) * ((r[1] + kTile - 1) / kTile);
+  }
+  cudaStream_t s = ctx->stream;
+  MRD_CUDA(ctx, D->gtask.need(g.t.size() * 8));
+  MRD_CUDA(ctx, D->gseg.need(std::max<size_t>(g.s.size(), 1) * 8));
+  MRD_CUDA(ctx, D->gpref.need(pref.size() * 8));
+  MRD_CUDA(ctx, cudaMemcpyAsync(D->gtask.p, g.t.data(), g.t.size() * 8, cudaMemcpyHostToDevice, s));
+  if (!g.s.empty()) MRD_CUDA(ctx, cudaMemcpyAsync(D->gseg.p, g.s.data(), g.s.size() * 8, cudaMemcpyHostToDevice, s));
+  MRD_CUDA(ctx, cudaMemcpyAsync(D->gpref.p, pref.data(), pref.size() * 8, cudaMemcpyHostToDevice, s));
+  MRD_CUDA(ctx, launch_cgemm_fp64(Aop, Bop, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
+                                  nt, pref[nt], D->n_sm, s));
+  // the host task arrays must stay valid until the copies completed
+  MRD_CUDA(ctx, cudaStreamSynchronize(s));
+  return MRD_OK;
+}
+
+int run_copies(mrd_dmrg* D, const std::vector<int64_t>& t, const double2* src, double2* dst, const double* S,
+               const double* sscale) {
+  mrd_ctx* ctx = D->ctx;
+  const int nt = (int)(t.size() / CPF);
+  if (nt == 0) return MRD_OK;
+  cudaStream_t s = ctx->stream;
+  MRD_CUDA(ctx, D->ctask.need(t.size() * 8));
+  MRD_CUDA(ctx, cudaMemcpyAsync(D->ctask.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, s));
+  k_copy_blocks<<<std::min(nt, 4096), 256, 0, s>>>(src, dst, D->ctask.as<int64_t>(), nt, S, sscale);
+  MRD_CUDA(ctx, cudaGetLastError());
+  MRD_CUDA(ctx, cudaStreamSynchronize(s));
+  return MRD_OK;
+}
+
+std::vector<std::array<int, 2>> mpo_channels(const HostMPO& m, int bond, int mod) {
+  std::vector<std::array<int, 2>> c;
+  const auto& v = m.bond_charges[bond];
+  for (size_t i = 0; i + 1 < v.size(); i += 2) c.push_back({v[i], kmod(v[i + 1], mod)});
+  return c;
+}
+
+// Build the H_eff handle for sites (i, i+1) from the current bonds; env pointers may be the
+// zero buffer when a side is only needed for its fold with the MPO.
+int make_heff(mrd_dmrg* D, int i, const double2* lenv, const double2* renv, mrd_heff** out) {
+  const SiteT& X = D->A[i];
+  const SiteT& Y = D->A[i + 1];
+  std::vector<int32_t> ls, rs, cl, cm, cr;
+  for (const Sec& s : X.left) ls.insert(ls.end(), {s.N, s.K, s.d});
+  for (const Sec& s : Y.right) rs.insert(rs.end(), {s.N, s.K, s.d});
+  const auto& b0 = D->mpo.bond_charges[i];
+  const auto& b1 = D->mpo.bond_charges[i + 1];
+  const auto& b2 = D->mpo.bond_charges[i + 2];
+  mrd_heff_desc d{};
+  d.n_left = (int32_t)X.left.size(); d.left = ls.data();
+  d.n_right = (int32_t)Y.right.size(); d.right = rs.data();
+  d.m1 = X.m; d.m2 = Y.m;
+  d.modulus = D->mod;
+  d.d_l = (int32_t)(b0.size() / 2); d.d_m = (int32_t)(b1.size() / 2); d.d_r = (int32_t)(b2.size() / 2);
+  d.c_l = b0.data(); d.c_m = b1.data(); d.c_r = b2.data();
+  d.nnz_i = (int32_t)(D->mpo.site_idx[i].size() / 4); d.wi_idx = D->mpo.site_idx[i].data(); d.wi_val = D->mpo.site_val[i].data();
+  d.nnz_j = (int32_t)(D->mpo.site_idx[i + 1].size() / 4); d.wj_idx = D->mpo.site_idx[i + 1].data();
+  d.wj_val = D->mpo.site_val[i + 1].data();
+  int rc = mrd_heff_create(D->ctx, &d, out);
+  if (rc != MRD_OK) return rc;
+  mrd_heff* h = *out;
+  // zero stand-ins for absent environments
+  const int64_t need = std::max(h->counts[C_LENV], h->counts[C_RENV]);
+  if (!lenv || !renv) {
+    MRD_CUDA(D->ctx, D->zeros.need((size_t)std::max<int64_t>(need, 1) * 16));
+    MRD_CUDA(D->ctx, cudaMemsetAsync(D->zeros.p, 0, (size_t)std::max<int64_t>(need, 1) * 16, D->ctx->stream));
+  }
+  rc = mrd_heff_set_env(h, (const double*)(lenv ? lenv : D->zeros.as<double2>()),
+                        (const double*)(renv ? renv : D->zeros.as<double2>()));
+  if (rc != MRD_OK) { mrd_heff_free(h); *out = nullptr; }
+  return rc;
+}
+
+// theta = X * Y in the middle-sector layout of h (zero where the bond has no sector).
+int form_theta(mrd_dmrg* D, mrd_heff* h, const SiteT& X, const SiteT& Y, double2* theta) {
+  mrd_ctx* ctx = D->ctx;
+  const int64_t n = h->counts[C_THETA];
+  MRD_CUDA(ctx, cudaMemsetAsync(theta, 0, (size_t)n * 16, ctx->stream));
+  GemmList g;
+  const std::vector<int64_t>& mid = h->mid_host;
+  for (int64_t q = 0; q < h->counts[C_NMID]; ++q) {
+    const int64_t* r = &mid[MIDF * q];
+    const int ci = find_sec(X.right, (int)r[0], (int)r[1]);   // bond sector between the sites
+    if (ci < 0) continue;
+    const int yi = find_sec(Y.left, (int)r[0], (int)r[1]);
+    if (yi < 0) continue;
+    const int64_t dc = X.right[ci].d;
+    for (int s1 = 0; s1 < 2; ++s1) {
+      if (r[5 + s1] < 0) continue;
+      const int ai = (int)r[5 + s1];
+      int64_t xo, xld;
+      int rr;
+      if (!X.subblock(ai, s1, &xo, &xld, &rr) || rr != ci) continue;
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (r[8 + s2] < 0) continue;
+        int64_t yo, yld;
+        int bi;
+        if (!Y.subblock(yi, s2, &yo, &yld, &bi) || bi != (int)r[8 + s2]) continue;
+        const int64_t roff = s1 ? r[7] : 0, coff = s2 ? r[10] : 0;
+        g.task(X.left[ai].d, Y.right[bi].d, r[4] + roff * r[3] + coff, r[3]);
+        g.seg(xo, xld, yo, yld, dc, 0);
+      }
+    }
+  }
+  // X and Y live in different buffers: run as two operands
+  return run_gemm(D, g, X.data.as<double2>(), X.size, Y.data.as<double2>(), Y.size, theta, n);
+}
+
+// Block SVD of the blocks `blk` (SVF rows) of `src`; returns kept counts per block and info.
+int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>& src_off, const double2* src,
+              int chi, double cutoff, std::vector<int>& keep, double info[3]) {
+  mrd_ctx* ctx = D->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nb = (int)src_off.size();
+  keep.assign(nb, 0);
+  if (nb == 0) { info[0] = 1; info[1] = 0; info[2] = 0; return MRD_OK; }
+  int64_t work = 0, ulen = 0, vlen = 0, slen = 0, maxrr = 0, npairs = 0;
+  std::vector<int64_t> pp(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    int64_t* d = &blk[SVF * b];
+    const int64_t m = d[0], n = d[1];
+    const bool wide = m < n;
+    const int64_t p = wide ? n : m, r = wide ? m : n;
+    d[2] = p; d[3] = r; d[9] = wide;
+    d[4] = work; work += p * r;
+    d[6] = ulen; ulen += m * r;
+    d[7] = vlen; vlen += r * n;
+    d[8] = slen; slen += r;
+    const int64_t rr = r + (r & 1);
+    maxrr = std::max(maxrr, rr);
+    pp[b + 1] = pp[b] + rr / 2;
+  }
+  for (int b = 0; b < nb; ++b) {   // V_X of every block after all X blocks
+    blk[SVF * b + 5] = work;
+    work += blk[SVF * b + 3] * blk[SVF * b + 3];
+  }
+  npairs = pp[nb];
+  MRD_CUDA(ctx, D->svd_blk.need(blk.size() * 8));
+  MRD_CUDA(ctx, D->svd_src.need(src_off.size() * 8));
+  MRD_CUDA(ctx, D->svd_pref.need(pp.size() * 8));
+  MRD_CUDA(ctx, D->svd_work.need((size_t)work * 16));
+  MRD_CUDA(ctx, D->svd_u.need((size_t)ulen * 16));
+  MRD_CUDA(ctx, D->svd_vh.need((size_t)vlen * 16));
+  MRD_CUDA(ctx, D->svd_s.need((size_t)slen * 8));
+  MRD_CUDA(ctx, D->svd_ss.need((size_t)slen * 8));
+  MRD_CUDA(ctx, D->svd_ord.need((size_t)slen * 4));
+  MRD_CUDA(ctx, D->svd_flat.need((size_t)slen * 4));
+  MRD_CUDA(ctx, D->svd_keep.need((size_t)nb * 4));
+  MRD_CUDA(ctx, D->svd_info.need(4 * 8));
+  MRD_CUDA(ctx, D->svd_rot.need(8));
+  MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_blk.p, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice, s));
+  MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_src.p, src_off.data(), src_off.size() * 8, cudaMemcpyHostToDevice, s));
+  MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_pref.p, pp.data(), pp.size() * 8, cudaMemcpyHostToDevice, s));
+  const int64_t* dblk = D->svd_blk.as<int64_t>();
+  MRD_CUDA(ctx, svd_load(src, dblk, D->svd_src.as<int64_t>(), nb, D->svd_work.as<double2>(), s));
+  int* rot = D->svd_rot.as<int>();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
+    for (int rd = 0; rd + 1 < maxrr; ++rd)
+      MRD_CUDA(ctx, svd_round(D->svd_work.as<double2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-15, rot, s));
+    int hrot = 0;
+    MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
+    MRD_CUDA(ctx, cudaStreamSynchronize(s));
+    if (hrot == 0) break;
+    if (sweep == 39) return mrd_fail(ctx, MRD_E_NOCONV, "block SVD: Jacobi sweeps did not converge");
+  }
+  MRD_CUDA(ctx, svd_finish(D->svd_work.as<double2>(), dblk, nb, D->svd_u.as<double2>(), D->svd_vh.as<double2>(),
+                           D->svd_s.as<double>(), D->svd_ss.as<double>(), D->svd_ord.as<int>(), s));
+  MRD_CUDA(ctx, svd_truncate(dblk, nb, D->svd_ss.as<double>(), slen, chi, cutoff, D->svd_keep.as<int>(),
+                             D->svd_info.as<double>(), D->svd_flat.as<int>(), s));
+  MRD_CUDA(ctx, cudaMemcpyAsync(keep.data(), D->svd_keep.p, nb * 4, cudaMemcpyDeviceToHost, s));
+  MRD_CUDA(ctx, cudaMemcpyAsync(info, D->svd_info.p, 3 * 8, cudaMemcpyDeviceToHost, s));
+  MRD_CUDA(ctx, cudaStreamSynchronize(s));
+  return MRD_OK;
+}
+
+// L[i+1] = A^+ (L[i] W_i) A with A = D->A[i] (mode 0) and the LW fold of h (sites i, i+1).
+int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
+  mrd_ctx* ctx = D->ctx;
+  const SiteT& A = D->A[i];
+  const Secs& ls = A.left;   // bond i
+  const Secs& cs = A.right;  // bond i+1
+  auto cm = mpo_channels(D->mpo, i + 1, D->mod);
+  const int m1 = A.m, mod = D->mod;
+  // LW blocks (w', s', s, a) -> offset
+  std::map<std::array<int64_t, 4>, int64_t> lw;
+  for (int64_t k = 0; k < h->counts[C_NLW]; ++k) {
+    const int64_t* r = &h->lw_host[LWF * k];
+    lw[{r[0], r[1], r[2], r[3]}] = r[7];
+  }
+  // step 1: T(w', c, s') = sum_s LW(w', s', s, a) A(a, s -> c)
+  GemmList g1;
+  struct TB { int64_t off, rows; };
+  std::map<std::array<int, 3>, TB> tblk;
+  int64_t tlen = 0;
+  for (int w = 0; w < (int)cm.size(); ++w)
+    for (int c = 0; c < (int)cs.size(); ++c) {
+      const int cp = find_sec(cs, cs[c].N + cm[w][0], kmod(cs[c].K + cm[w][1], mod));
+      if (cp < 0) continue;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int ap = find_sec(ls, cs[cp].N - sp, kmod(cs[cp].K - sp * m1, mod));
+        if (ap < 0) continue;
+        bool started = false;
+        for (int s = 0; s < 2; ++s) {
+          const int a = find_sec(ls, cs[c].N - s, kmod(cs[c].K - s * m1, mod));
+          if (a < 0) continue;
+          auto it = lw.find({w, sp, s, a});
+          if (it == lw.end()) continue;
+          int64_t ao, ald;
+          int rr;
+          if (!A.subblock(a, s, &ao, &ald, &rr) || rr != c) continue;
+          if (!started) {
+            tblk[{w, c, sp}] = {tlen, ls[ap].d};
+            g1.task(ls[ap].d, cs[c].d, tlen, cs[c].d);
+            tlen += (int64_t)ls[ap].d * cs[c].d;
+            started = true;
+          }
+          g1.seg(it->second, ls[a].d, ao, ald, ls[a].d, 0);
+        }
+      }
+    }
+  MRD_CUDA(ctx, D->tbuf.need((size_t)std::max<int64_t>(tlen, 1) * 16));
+  int rc = run_gemm(D, g1, h->lw, h->counts[C_LWLEN], A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen);
+  if (rc != MRD_OK) return rc;
+  // step 2: L'(w', c) = sum_s' A(a', s' -> c')^+ T(w', c, s')
+  EnvT& E = D->L[i + 1];
+  E.sec = cs;
+  E.ch = cm;
+  E.left = true;
+  E.layout(mod);
+  MRD_CUDA(ctx, E.data.need((size_t)std::max<int64_t>(E.size, 1) * 16));
+  MRD_CUDA(ctx, cudaMemsetAsync(E.data.p, 0, (size_t)std::max<int64_t>(E.size, 1) * 16, ctx->stream));
+  GemmList g2;
+  for (int w = 0; w < (int)cm.size(); ++w)
+    for (int c = 0; c < (int)cs.size(); ++c) {
+      const int64_t off = E.off[(size_t)w * cs.size() + c];
+      if (off < 0) continue;
+      const int cp = find_sec(cs, cs[c].N + cm[w][0], kmod(cs[c].K + cm[w][1], mod));
+      bool started = false;
+      for (int sp = 0; sp < 2; ++sp) {
+        auto it = tblk.find({w, c, sp});
+        if (it == tblk.end()) continue;
+        const int ap = find_sec(ls, cs[cp].N - sp, kmod(cs[cp].K - sp * m1, mod));
+        int64_t ao, ald;
+        int rr;
+        if (!A.subblock(ap, sp, &ao, &ald, &rr) || rr != cp) continue;
+        if (!started) { g2.task(cs[cp].d, cs[c].d, off, cs[c].d); started = true; }
+        // A-op: conj-transpose of the d_a' x d_c' sub-block
+        g2.seg(ao, ald, it->second.off, cs[c].d, ls[ap].d, 1);
+      }
+    }
+  return run_gemm(D, g2, A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen, E.data.as<double2>(), E.size);
+}
+
+// R[i+1] = B (W_{i+1} R[i+2]) B^+ with B = D->A[i+1] (mode 1) and the WR fold of h.
+int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
+  mrd_ctx* ctx = D->ctx;
+  const SiteT& B = D->A[i + 1];
+  const Secs& cs = B.left;   // bond i+1
+  const Secs& bs = B.right;  // bond i+2
+  auto cm = mpo_channels(D->mpo, i + 1, D->mod);
+  const int m2 = B.m, mod = D->mod;
+  std::map<std::array<int64_t, 4>, int64_t> wr;
+  for (int64_t k = 0; k < h->counts[C_NWR]; ++k) {
+    const int64_t* r = &h->wr_host[WRF * k];
+    wr[{r[0], r[1], r[2], r[3]}] = r[7];
+  }
+  // step 1: T(w', c, s') = sum_s B(c, s -> b) WR(w', s, s', b)
+  GemmList g1;
+  struct TB { int64_t off, cols; };
+  std::map<std::array<int, 3>, TB> tblk;
+  int64_t tlen = 0;
+  for (int w = 0; w < (int)cm.size(); ++w)
+    for (int c = 0; c < (int)cs.size(); ++c) {
+      const int cp = find_sec(cs, cs[c].N + cm[w][0], kmod(cs[c].K + cm[w][1], mod));
+      if (cp < 0) continue;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int bp = find_sec(bs, cs[cp].N + sp, kmod(cs[cp].K + sp * m2, mod));
+        if (bp < 0) continue;
+        bool started = false;
+        for (int s = 0; s < 2; ++s) {
+          int64_t bo, bld;
+          int b;
+          if (!B.subblock(c, s, &bo, &bld, &b)) continue;
+          auto it = wr.find({w, s, sp, b});
+          if (it == wr.end()) continue;
+          if (!started) {
+            tblk[{w, c, sp}] = {tlen, bs[bp].d};
+            g1.task(cs[c].d, bs[bp].d, tlen, bs[bp].d);
+            tlen += (int64_t)cs[c].d * bs[bp].d;
+            started = true;
+          }
+          g1.seg(bo, bld, it->second, bs[bp].d, bs[b].d, 0);
+        }
+      }
+    }
+  MRD_CUDA(ctx, D->tbuf.need((size_t)std::max<int64_t>(tlen, 1) * 16));
+  int rc = run_gemm(D, g1, B.data.as<double2>(), B.size, h->wr, h->counts[C_WRLEN], D->tbuf.as<double2>(), tlen);
+  if (rc != MRD_OK) return rc;
+  EnvT& E = D->R[i + 1];
+  E.sec = cs;
+  E.ch = cm;
+  E.left = false;
+  E.layout(mod);
+  MRD_CUDA(ctx, E.data.need((size_t)std::max<int64_t>(E.size, 1) * 16));
+  MRD_CUDA(ctx, cudaMemsetAsync(E.data.p, 0, (size_t)std::max<int64_t>(E.size, 1) * 16, ctx->stream));
+  GemmList g2;
+  for (int w = 0; w < (int)cm.size(); ++w)
+    for (int c = 0; c < (int)cs.size(); ++c) {
+      const int64_t off = E.off[(size_t)w * cs.size() + c];
+      if (off < 0) continue;
+      const int cp = find_sec(cs, cs[c].N + cm[w][0], kmod(cs[c].K + cm[w][1], mod));
+      bool started = false;
+      for (int sp = 0; sp < 2; ++sp) {
+        auto it = tblk.find({w, c, sp});
+        if (it == tblk.end()) continue;
+        int64_t bo, bld;
+        int bp;
+        if (!B.subblock(cp, sp, &bo, &bld, &bp)) continue;
+        if (!started) { g2.task(cs[c].d, cs[cp].d, off, cs[cp].d); started = true; }
+        // B-op: conj-transpose of the d_c' x d_b' sub-block
+        g2.seg(it->second.off, it->second.cols, bo, bld, bs[bp].d, 2);
+      }
+    }
+  return run_gemm(D, g2, D->tbuf.as<double2>(), tlen, B.data.as<double2>(), B.size, E.data.as<double2>(), E.size);
+}
+
+int set_trivial_env(mrd_dmrg* D, EnvT& E, const Secs& sec, int bond, bool left) {
+  E.sec = sec;
+  E.ch = mpo_channels(D->mpo, bond, D->mod);
+  E.left = left;
+  E.layout(D->mod);
+  if (E.size != 1) return mrd_fail(D->ctx, MRD_E_STATE, "boundary environment is not 1 x 1");
+  MRD_CUDA(D->ctx, E.data.need(16));
+  const double2 one = make_double2(1.0, 0.0);
+  MRD_CUDA(D->ctx, cudaMemcpy(E.data.p, &one, 16, cudaMemcpyHostToDevice));
+  return MRD_OK;
+}
+
+// Right-orthonormalise the rows of every group of a mode-1 tensor (or the columns of every
+// group of a mode-0 tensor) with the block SVD; the data is replaced by V^+ (or U).
+int orthonormalise(mrd_dmrg* D, SiteT& T) {
+  std::vector<int64_t> blk, src;
+  std::vector<int> gi;
+  for (size_t g = 0; g < T.goff.size(); ++g) {
+    const int64_t rows = T.mode == 1 ? T.left[g].d : T.gext[g];
+    const int64_t cols = T.mode == 1 ? T.gext[g] : T.right[g].d;
+    if (rows == 0 || cols == 0) continue;
+    std::vector<int64_t> d(SVF, 0);
+    d[0] = rows; d[1] = cols;
+    blk.insert(blk.end(), d.begin(), d.end());
+    src.push_back(T.goff[g]);
+    gi.push_back((int)g);
+  }
+  std::vector<int> keep;
+  double info[3];
+  int rc = block_svd(D, blk, src, T.data.as<double2>(), 1 << 30, 0.0, keep, info);
+  if (rc != MRD_OK) return rc;
+  std::vector<int64_t> cp;
+  for (size_t b = 0; b < gi.size(); ++b) {
+    const int64_t* d = &blk[SVF * b];
+    const int g = gi[b];
+    if (T.mode == 1) {   // rows of Vh: r = min(rows, cols) must equal rows
+      if (d[3] != d[0]) return mrd_fail(D->ctx, MRD_E_STATE, "orthonormalise: rank-deficient group");
+      cp.insert(cp.end(), {d[7], d[1], T.goff[g], T.gext[g], d[0], d[1], 0, 0});
+    } else {
+      if (d[3] != d[1]) return mrd_fail(D->ctx, MRD_E_STATE, "orthonormalise: rank-deficient group");
+      cp.insert(cp.end(), {d[6], d[3], T.goff[g], T.right[g].d, d[0], d[1], 0, 0});
+    }
+  }
+  return run_copies(D, cp, T.mode == 1 ? D->svd_vh.as<double2>() : D->svd_u.as<double2>(), T.data.as<double2>(),
+                    nullptr, nullptr);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mrd_dmrg_create(mrd_ctx* ctx, const mrd_mpo* mpo, int32_t n_part, int32_t k_tot, int32_t chi, uint64_t seed,
+                    int32_t center, const int32_t* caps, const int64_t* caps_off, mrd_dmrg** out) {
+  if (!ctx || !mpo || !out || chi < 1) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_create: bad argument");
+  *out = nullptr;
+  const HostMPO& H = mpo->h;
+  const int n = H.n_sites;
+  if (n < 2 || center < 0 || center > n - 2) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_create: need n >= 2, 0 <= center <= n-2");
+  if (H.bond_charges[0].size() != 2 || H.bond_charges[n].size() != 2)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_create: MPO boundary bonds must have dimension 1");
+  Guard g(ctx->device);
+  mrd_dmrg* D = new mrd_dmrg();
+  D->ctx = ctx;
+  mrd_ctx_retain(ctx);
+  D->mpo = H;
+  D->n = n;
+  D->mod = H.modulus;
+  // ly: the site momentum period (orbital j has momentum j mod ly in the mixed basis)
+  D->ly = H.modulus > 1 ? H.modulus : 1;
+  D->target_N = n_part;
+  D->target_K = kmod(k_tot, D->mod);
+  cudaDeviceGetAttribute(&D->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int mod = D->mod;
+  auto site_m = [&](int j) { return mod > 1 ? j % D->ly : 0; };
+  // exact state counts left and right of every bond (log scale to avoid overflow)
+  std::vector<std::map<int64_t, double>> lc(n + 1), rc(n + 1);
+  lc[0][qkey(0, 0)] = 0.0;
+  for (int j = 0; j < n; ++j)
+    for (auto& kv : lc[j]) {
+      const int N = (int)((kv.first >> 32) - (1 << 29)), K = (int)(kv.first & 0xffffffff);
+      for (int s = 0; s < 2; ++s) {
+        const int64_t k2 = qkey(N + s, kmod(K + s * site_m(j), mod));
+        auto it = lc[j + 1].find(k2);
+        if (it == lc[j + 1].end()) lc[j + 1][k2] = kv.second;
+        else it->second = std::max(it->second, kv.second) + std::log1p(std::exp(-std::fabs(it->second - kv.second)));
+      }
+    }
+  rc[n][qkey(n_part, D->target_K)] = 0.0;
+  for (int j = n - 1; j >= 0; --j)
+    for (auto& kv : rc[j + 1]) {
+      const int N = (int)((kv.first >> 32) - (1 << 29)), K = (int)(kv.first & 0xffffffff);
+      for (int s = 0; s < 2; ++s) {
+        const int64_t k2 = qkey(N - s, kmod(K - s * site_m(j), mod));
+        auto it = rc[j].find(k2);
+        if (it == rc[j].end()) rc[j][k2] = kv.second;
+        else it->second = std::max(it->second, kv.second) + std::log1p(std::exp(-std::fabs(it->second - kv.second)));
+      }
+    }
+  if (!lc[n].count(qkey(n_part, D->target_K))) {
+    mrd_dmrg_free(D);
+    return mrd_fail(ctx, MRD_E_CHARGE, "mrd_dmrg_create: target charge unreachable");
+  }
+  // bond sectors: exact counts, capped by the caller's caps (if given) and by chi
+  std::vector<Secs> bond(n + 1);
+  for (int j = 0; j <= n; ++j) {
+    std::map<int64_t, int> capmap;
+    const bool has_cap = caps && caps_off && caps_off[j + 1] > caps_off[j];
+    if (has_cap)
+      for (int64_t k = caps_off[j]; k < caps_off[j + 1]; ++k)
+        capmap[qkey(caps[3 * k], kmod(caps[3 * k + 1], mod))] = caps[3 * k + 2];
+    for (auto& kv : lc[j]) {
+      auto r = rc[j].find(kv.first);
+      if (r == rc[j].end()) continue;
+      double lim = std::min(kv.second, r->second);   // log of the exact dimension bound
+      int64_t d = lim > 40 ? (int64_t)1 << 40 : (int64_t)std::llround(std::exp(lim));
+      d = std::min<int64_t>(d, chi);
+      if (has_cap) {
+        auto c = capmap.find(kv.first);
+        d = c == capmap.end() ? 0 : std::min<int64_t>(d, c->second);
+      }
+      if (d <= 0) continue;
+      const int N = (int)((kv.first >> 32) - (1 << 29)), K = (int)(kv.first & 0xffffffff);
+      bond[j].push_back({N, K, (int32_t)d});
+    }
+    if (!has_cap) {   // keep the total at most chi: scale down proportionally (at least 1 each)
+      int64_t tot = 0;
+      for (auto& s : bond[j]) tot += s.d;
+      if (tot > chi) {
+        for (auto& s : bond[j]) s.d = std::max<int32_t>(1, (int32_t)((double)s.d * chi / tot));
+      }
+    }
+  }
+  // the dims must be realisable from both sides: shrink until every sector fits its
+  // neighbours (d_j(q) <= sum_s d_{j+1}(q + q(s)) and <= sum_s d_{j-1}(q - q(s)))
+  for (int pass = 0, changed = 1; changed && pass < 1000; ++pass) {
+    changed = 0;
+    for (int j = 1; j < n; ++j) {
+      for (auto& s : bond[j]) {
+        int64_t right = 0, left = 0;
+        for (int t = 0; t < 2; ++t) {
+          const int r = find_sec(bond[j + 1], s.N + t, kmod(s.K + t * site_m(j), mod));
+          if (r >= 0) right += bond[j + 1][r].d;
+          const int l = find_sec(bond[j - 1], s.N - t, kmod(s.K - t * site_m(j - 1), mod));
+          if (l >= 0) left += bond[j - 1][l].d;
+        }
+        const int32_t nd = (int32_t)std::min<int64_t>(s.d, std::min(left, right));
+        if (nd != s.d) { s.d = nd; changed = 1; }
+      }
+      bond[j].erase(std::remove_if(bond[j].begin(), bond[j].end(), [](const Sec& s) { return s.d <= 0; }), bond[j].end());
+    }
+  }
+  D->A.resize(n);
+  D->L.resize(n + 1);
+  D->R.resize(n + 1);
+  cudaStream_t s = ctx->stream;
+  for (int j = 0; j < n; ++j) {
+    SiteT& T = D->A[j];
+    T.left = bond[j];
+    T.right = bond[j + 1];
+    T.m = site_m(j);
+    T.mod = mod;
+    T.mode = j < center ? 0 : 1;
+    T.layout();
+    cudaError_t e = T.data.need((size_t)std::max<int64_t>(T.size, 1) * 16);
+    if (e != cudaSuccess) { mrd_dmrg_free(D); return mrd_cuda_fail(ctx, e, "mrd_dmrg_create: MPS"); }
+    if (T.size > 0) {
+      const int64_t grid = std::min<int64_t>((T.size + 255) / 256, 4096);
+      k_fill_random<<<(unsigned)grid, 256, 0, s>>>(T.data.as<double2>(), T.size, seed * 0x100000001B3ull + (uint64_t)j * 0x9E3779B97F4A7C15ull);
+    }
+  }
+  int rcd = MRD_OK;
+  for (int j = 0; j < n && rcd == MRD_OK; ++j)
+    if (j != center) rcd = orthonormalise(D, D->A[j]);
+  if (rcd == MRD_OK) rcd = set_trivial_env(D, D->L[0], bond[0], 0, true);
+  if (rcd == MRD_OK) rcd = set_trivial_env(D, D->R[n], bond[n], n, false);
+  // left environments up to the centre, right environments down to centre + 2
+  for (int j = 0; j < center && rcd == MRD_OK; ++j) {
+    mrd_heff* h = nullptr;
+    rcd = make_heff(D, j, D->L[j].data.as<double2>(), nullptr, &h);
+    if (rcd == MRD_OK) rcd = env_left(D, h, j);
+    if (h) mrd_heff_free(h);
+  }
+  for (int j = n - 1; j >= center + 2 && rcd == MRD_OK; --j) {
+    mrd_heff* h = nullptr;
+    rcd = make_heff(D, j - 1, nullptr, D->R[j + 1].data.as<double2>(), &h);
+    if (rcd == MRD_OK) rcd = env_right(D, h, j - 1);
+    if (h) mrd_heff_free(h);
+  }
+  if (rcd != MRD_OK) {
+    std::string msg = ctx->err;
+    mrd_dmrg_free(D);
+    return mrd_fail(ctx, rcd, msg);
+  }
+  *out = D;
+  return MRD_OK;
+}
+
+int mrd_dmrg_free(mrd_dmrg* D) {
+  if (!D) return MRD_OK;
+  mrd_ctx* ctx = D->ctx;
+  {
+    Guard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    delete D;
+  }
+  mrd_ctx_release(ctx);
+  return MRD_OK;
+}
+
+int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmrg_params* p, double* energy,
+                        double* trunc_err) {
+  if (!D || !p) return MRD_E_ARG;
+  mrd_ctx* ctx = D->ctx;
+  if (i < 0 || i > D->n - 2) return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: site out of range");
+  if (!D->L[i].data.p || !D->R[i + 2].data.p)
+    return mrd_fail(ctx, MRD_E_STATE, "mrd_two_site_update: environments of this bond are not available");
+  Guard g(ctx->device);
+  mrd_heff* h = nullptr;
+  int rc = make_heff(D, i, D->L[i].data.as<double2>(), D->R[i + 2].data.as<double2>(), &h);
+  if (rc != MRD_OK) return rc;
+  struct Free { mrd_heff* h; ~Free() { if (h) mrd_heff_free(h); } } guard{h};
+  const int64_t n = h->counts[C_THETA];
+  MRD_CUDA(ctx, D->theta.need((size_t)std::max<int64_t>(n, 1) * 16));
+  double2* theta = D->theta.as<double2>();
+  if ((rc = form_theta(D, h, D->A[i], D->A[i + 1], theta)) != MRD_OK) return rc;
+  double e = 0.0;
+  int32_t it = 0;
+  if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e, &it)) != MRD_OK) return rc;
+  D->last_iters = it;
+  // block SVD of theta by middle charge
+  std::vector<int64_t> blk, src;
+  std::vector<int> mids;
+  for (int64_t q = 0; q < h->counts[C_NMID]; ++q) {
+    const int64_t* r = &h->mid_host[MIDF * q];
+    std::vector<int64_t> d(SVF, 0);
+    d[0] = r[2]; d[1] = r[3];
+    blk.insert(blk.end(), d.begin(), d.end());
+    src.push_back(r[4]);
+    mids.push_back((int)q);
+  }
+  std::vector<int> keep;
+  double info[3];
+  if ((rc = block_svd(D, blk, src, theta, p->chi, p->svd_cutoff, keep, info)) != MRD_OK) return rc;
+  // new bond i+1
+  Secs nb;
+  for (size_t b = 0; b < mids.size(); ++b)
+    if (keep[b] > 0) {
+      const int64_t* r = &h->mid_host[MIDF * mids[b]];
+      nb.push_back({(int32_t)r[0], (int32_t)r[1], keep[b]});
+    }
+  if (nb.empty()) return mrd_fail(ctx, MRD_E_NAN, "mrd_two_site_update: all singular values vanished");
+  SiteT& X = D->A[i];
+  SiteT& Y = D->A[i + 1];
+  X.right = nb; X.mode = 0; X.layout();
+  Y.left = nb; Y.mode = 1; Y.layout();
+  MRD_CUDA(ctx, X.data.need((size_t)std::max<int64_t>(X.size, 1) * 16));
+  MRD_CUDA(ctx, Y.data.need((size_t)std::max<int64_t>(Y.size, 1) * 16));
+  std::vector<int64_t> cx, cy;
+  int nbi = 0;
+  for (size_t b = 0; b < mids.size(); ++b) {
+    if (keep[b] == 0) continue;
+    const int64_t* d = &blk[SVF * b];
+    const int64_t m = d[0], ncol = d[1], r = d[3], k = keep[b];
+    // X group nbi: rows (s1, a) of the middle sector, k columns = U[:, :k] (times S when moving left)
+    cx.insert(cx.end(), {d[6], r, X.goff[nbi], k, m, k, direction < 0 ? 1 : 0, d[8]});
+    // Y group nbi: k rows = Vh[:k, :] (times S when moving right)
+    cy.insert(cy.end(), {d[7], ncol, Y.goff[nbi], Y.gext[nbi], k, ncol, direction > 0 ? 2 : 0, d[8]});
+    ++nbi;
+  }
+  const double* S = D->svd_ss.as<double>();
+  const double* sscale = D->svd_info.as<double>();
+  if ((rc = run_copies(D, cx, D->svd_u.as<double2>(), X.data.as<double2>(), S, sscale)) != MRD_OK) return rc;
+  if ((rc = run_copies(D, cy, D->svd_vh.as<double2>(), Y.data.as<double2>(), S, sscale)) != MRD_OK) return rc;
+  if (direction > 0) rc = env_left(D, h, i);
+  else rc = env_right(D, h, i);
+  if (rc != MRD_OK) return rc;
+  D->last_energy = e;
+  D->last_trunc = info[1];
+  if (energy) *energy = e;
+  if (trunc_err) *trunc_err = info[1];
+  return MRD_OK;
+}
+
+int mrd_sweep(mrd_dmrg* D, const mrd_dmrg_params* p, double* energy) {
+  if (!D || !p) return MRD_E_ARG;
+  int rc;
+  double e = 0.0;
+  for (int i = 0; i <= D->n - 2; ++i)
+    if ((rc = mrd_two_site_update(D, i, +1, p, &e, nullptr)) != MRD_OK) return rc;
+  for (int i = D->n - 2; i >= 0; --i)
+    if ((rc = mrd_two_site_update(D, i, -1, p, &e, nullptr)) != MRD_OK) return rc;
+  if (energy) *energy = e;
+  return MRD_OK;
+}
+
+int mrd_dmrg_bond(const mrd_dmrg* D, int32_t bond, int32_t* n_sectors, int32_t* sectors) {
+  if (!D || !n_sectors || bond < 0 || bond > D->n) return MRD_E_ARG;
+  const Secs& s = bond < D->n ? D->A[bond].left : D->A[D->n - 1].right;
+  *n_sectors = (int32_t)s.size();
+  if (sectors)
+    for (size_t k = 0; k < s.size(); ++k) {
+      sectors[3 * k] = s[k].N; sectors[3 * k + 1] = s[k].K; sectors[3 * k + 2] = s[k].d;
+    }
+  return MRD_OK;
+}
+
+int mrd_dmrg_site(mrd_dmrg* D, int32_t site, int32_t* mode, int64_t* len, double* host) {
+  if (!D || !len || site < 0 || site >= D->n) return MRD_E_ARG;
+  const SiteT& T = D->A[site];
+  if (mode) *mode = T.mode;
+  *len = T.size;
+  if (host && T.size) {
+    Guard g(D->ctx->device);
+    MRD_CUDA(D->ctx, cudaStreamSynchronize(D->ctx->stream));
+    MRD_CUDA(D->ctx, cudaMemcpy(host, T.data.p, (size_t)T.size * 16, cudaMemcpyDeviceToHost));
+  }
+  return MRD_OK;
+}
+
+int mrd_dmrg_env(mrd_dmrg* D, int32_t bond, int32_t side, int64_t* len, double* host) {
+  if (!D || !len || bond < 0 || bond > D->n) return MRD_E_ARG;
+  EnvT& E = side == 0 ? D->L[bond] : D->R[bond];
+  *len = E.data.p ? E.size : -1;
+  if (host && E.data.p && E.size) {
+    Guard g(D->ctx->device);
+    MRD_CUDA(D->ctx, cudaStreamSynchronize(D->ctx->stream));
+    MRD_CUDA(D->ctx, cudaMemcpy(host, E.data.p, (size_t)E.size * 16, cudaMemcpyDeviceToHost));
+  }
+  return MRD_OK;
+}
+
+int mrd_dmrg_stats(const mrd_dmrg* D, double* energy, double* trunc_err, int32_t* lanczos_iters) {
+  if (!D) return MRD_E_ARG;
+  if (energy) *energy = D->last_energy;
+  if (trunc_err) *trunc_err = D->last_trunc;
+  if (lanczos_iters) *lanczos_iters = D->last_iters;
+  return MRD_OK;
+}
+
+}  // extern "C"

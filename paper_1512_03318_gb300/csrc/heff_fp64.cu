@@ -67,16 +67,33 @@ __global__ void __launch_bounds__(256) k_cgemm_fp64(const double2* __restrict__ 
     for (int64_t s = 0; s < nseg; ++s) {
       const int64_t* sg = segs + SF * (seg0 + s);
       const int64_t a_off = sg[0], lda = sg[1], b_off = sg[2], ldb = sg[3], K = sg[4];
+      const int64_t flags = sg[5];
       for (int64_t k0 = 0; k0 < K; k0 += kK) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int e = tid + r * 256;
-          const int ar = e >> 4, ak = e & 15;           // A tile: 32 rows x 16 k
-          const int64_t gr = m0 + ar, gk = k0 + ak;
-          As[ar][ak] = (gr < M && gk < K) ? A[a_off + gr * lda + gk] : make_double2(0.0, 0.0);
-          const int bk = e >> 5, bc = e & 31;           // B tile: 16 k x 32 cols
-          const int64_t gk2 = k0 + bk, gc = n0 + bc;
-          Bs[bk][bc] = (gk2 < K && gc < N) ? B[b_off + gk2 * ldb + gc] : make_double2(0.0, 0.0);
+          if (!(flags & 1)) {                           // A[m, k] at a_off + m * lda + k
+            const int ar = e >> 4, ak = e & 15;
+            const int64_t gr = m0 + ar, gk = k0 + ak;
+            As[ar][ak] = (gr < M && gk < K) ? A[a_off + gr * lda + gk] : make_double2(0.0, 0.0);
+          } else {                                      // A[m, k] = conj(A[a_off + k * lda + m])
+            const int ar = e & 31, ak = e >> 5;
+            const int64_t gr = m0 + ar, gk = k0 + ak;
+            double2 v = (gr < M && gk < K) ? A[a_off + gk * lda + gr] : make_double2(0.0, 0.0);
+            v.y = -v.y;
+            As[ar][ak] = v;
+          }
+          if (!(flags & 2)) {                           // B[k, n] at b_off + k * ldb + n
+            const int bk = e >> 5, bc = e & 31;
+            const int64_t gk2 = k0 + bk, gc = n0 + bc;
+            Bs[bk][bc] = (gk2 < K && gc < N) ? B[b_off + gk2 * ldb + gc] : make_double2(0.0, 0.0);
+          } else {                                      // B[k, n] = conj(B[b_off + n * ldb + k])
+            const int bk = e & 15, bc = e >> 4;
+            const int64_t gk2 = k0 + bk, gc = n0 + bc;
+            double2 v = (gk2 < K && gc < N) ? B[b_off + gc * ldb + gk2] : make_double2(0.0, 0.0);
+            v.y = -v.y;
+            Bs[bk][bc] = v;
+          }
         }
         __syncthreads();
 #pragma unroll

@@ -1,0 +1,103 @@
+// Internal layout of an H_eff handle, shared by api.cu and the DMRG layer.
+#pragma once
+#include <vector>
+
+#include "mrd_internal.h"
+#include "plan.cuh"
+
+namespace mrd {
+struct Lanczos;
+void lanczos_free(Lanczos* L);
+}  // namespace mrd
+using mrd::Lanczos;
+using mrd::lanczos_free;
+using mrd::PlanDims;
+using mrd::PlanPtrs;
+using namespace mrd;
+
+namespace mrd {
+
+// Device arena: a list of allocations freed together.
+struct Arena {
+  std::vector<void*> ptrs;
+  ~Arena() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  template <class T>
+  cudaError_t alloc(T** out, size_t count) {
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(p);
+    *out = (T*)p;
+    return cudaSuccess;
+  }
+};
+
+struct Guard {  // switches to a device for the scope
+  int prev = -1;
+  explicit Guard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Guard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline int kmod(int k, int m) { return ((k % m) + m) % m; }
+
+}  // namespace mrd
+
+using mrd::Arena;
+using mrd::Guard;
+using mrd::kmod;
+
+struct mrd_heff {
+  mrd_ctx* ctx = nullptr;
+  PlanDims d{};
+  PlanPtrs p{};
+  Arena plan_mem;   // tables
+  Arena data_mem;   // LW, WR, Z
+  int64_t counts[C_NCOUNTS] = {0};
+  double* wi_val = nullptr;
+  double* wj_val = nullptr;
+  double2* lw = nullptr;
+  double2* wr = nullptr;
+  double2* z = nullptr;
+  bool env_loaded = false;
+  double def_flops = 0.0;
+  int n_sm = 152;
+  std::vector<int32_t> left, right, cl, cm, cr, wi_idx, wj_idx;
+  std::vector<double> wi_v, wj_v;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;   // 3 per recorded apply: before step 1, between, after step 2
+  std::vector<cudaEvent_t> ev_pool;
+  Lanczos* lz = nullptr;
+  // host copies of the device-built tables (downloaded once at creation)
+  std::vector<int64_t> mid_host, lw_host, wr_host, lmap_host, rmap_host;
+  ~mrd_heff() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    lanczos_free(lz);
+  }
+};
+
+inline cudaEvent_t take_event(mrd_heff* h) {
+  cudaEvent_t e = nullptr;
+  if (!h->ev_pool.empty()) {
+    e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  h->ev.push_back(e);
+  return e;
+}
+

@@ -371,6 +371,7 @@ __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
         seg[2] = min_[4] + (s1 ? min_[7] : 0) * Ncols;
         seg[3] = Ncols;
         seg[4] = K;
+        seg[5] = 0;
         flops += 8 * Mrows * Ncols * K;
         ++cnt;
       }
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
           seg[2] = p.wr[WRF * wrid + 7];
           seg[3] = Ncols;
           seg[4] = K;
+          seg[5] = 0;
           flops += 8 * Mrows * Ncols * K;
           ++cnt;
         }

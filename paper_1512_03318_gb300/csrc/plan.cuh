@@ -5,13 +5,13 @@
 namespace mrd {
 
 // Row widths of the int64 tables.
-enum { MIDF = 12, LWF = 10, WRF = 10, ZF = 6, TF = 6, SF = 5 };
+enum { MIDF = 12, LWF = 10, WRF = 10, ZF = 6, TF = 6, SF = 6 };
 // MID row: N K rowdim coldim offset row_a0 row_a1 row_off1 col_b0 col_b1 col_off1 pad
 // LW row : w' s1' s1 a a' rows cols offset contrib_begin contrib_end
 // WR row : w' s2 s2' b b' rows cols offset contrib_begin contrib_end
 // Z row  : w' m_in m_out rows cols offset
 // task   : M N c_off ldc seg_begin seg_count
-// segment: a_off lda b_off ldb K
+// segment: a_off lda b_off ldb K flags (bit 0: A conjugate-transposed, bit 1: B conjugate-transposed)
 enum Count {
   C_NMID = 0, C_THETA, C_LENV, C_RENV, C_NLW, C_LWLEN, C_NWR, C_WRLEN, C_NZ, C_ZLEN,
   C_NT1, C_NT2, C_TILES1, C_TILES2, C_FLOPS1, C_FLOPS2, C_ERR, C_NCOUNTS
