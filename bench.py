@@ -1,13 +1,21 @@
-"""Benchmark of the two-site H_eff hot path on GB300 (one JSON line on rank 0).
+"""Benchmark of the two-site DMRG hot path on GB300 (one JSON line on rank 0).
 
-Workload: the Ly = 10 interacting Hofstadter cylinder (flux 1/10, t = 1, V = 1, Lx = 20),
-bond dimension chi = 3200, mixed real/momentum-space MPO built by the library, synthetic
-charge sectors (70 per bond, dims 4..277, seeded recipe of `synth`), environments and theta
-with seeded complex entries. The two sites are in the middle of the ring at the middle of
-the cylinder (the largest MPO bonds). One step = one H_eff application theta' = H_eff theta.
+Step: one two-site update at bond dimension chi = 3200 on the Ly = 10 interacting Hofstadter
+cylinder (flux 1/10, t = 1, V = 1, one particle per ring, Lx = 12), mixed real/momentum-space
+MPO built by the library: H_eff tables, theta, Lanczos with split-BF16 tensor-core matvecs,
+FP64 refinement of the ground vector, block SVD and truncation, environment update.
+The state is a seeded random MPS, left-canonical left of the centre and right-canonical right
+of it, with genuine environments contracted from the ends; bond sectors follow the synthetic
+sector recipe of `synth` (70 sectors of dims 4..277 at chi = 3200). Successive steps move the
+centre one site to the right. `value` is seconds per update (whole job: wall / updates).
 
-Launch: python bench.py [--gpus N --steps K --warmup W] (N > 1 under torchrun: independent
-replicas, one per GPU, weak scaling). --impl reference times the CPU oracle instead.
+Also measured in the same run: the FP64 form of the update at the same accuracy, the energy
+error of the mixed form against a converged FP64 reference of the same H_eff, H_eff
+throughput (TFLOP/s, definition-order flops) in FP64, TF32 and split BF16 on the Lx = 20
+cylinder's mid-ring sites with random environments, and the CPU oracle.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; N > 1 under torchrun runs independent
+replicas (weak scaling). --impl reference times the CPU oracle.
 """
 from __future__ import annotations
 
@@ -28,10 +36,21 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "s per two-site update & H_eff TFLOP/s at χ=3200, mixed-prec vs FP64, ΔE≤1e-9"
-LY, LX, CHI, FLUX_P, FLUX_Q, T_HOP, V_INT = 10, 20, 3200, 1, 10, 1.0, 1.0
-SITE = (LX // 2) * LY + LY // 2 - 1
-SEED = 1234 + 3          # configuration index 3 of the workload list (chi = 3200)
+LY, CHI, FLUX_P, FLUX_Q, T_HOP, V_INT = 10, 3200, 1, 10, 1.0, 1.0
+LX_UPDATE = 12            # cylinder of the update steps
+LX_MATVEC = 20            # cylinder of the matvec throughput measurement
+SEED = 1234 + 3           # workload index 3 (chi = 3200)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "of fallback"
 
 
 def set_chi(chi):
@@ -39,29 +58,19 @@ def set_chi(chi):
     CHI = chi
 
 
-def workload_name():
-    return (f"H_eff matvec FP64, mixed-space Hofstadter cylinder Ly={LY} Lx={LX} flux={FLUX_P}/{FLUX_Q} "
-            f"t={T_HOP} V={V_INT}, chi={CHI}, sites ({SITE},{SITE + 1})")
+def update_centre(lx):
+    return (lx // 2) * LY + LY // 2 - 1
 
 
-def sectors(seed_tag):
-    return synth.bond_sectors(CHI, LY, LX // 2, synth.substream(SEED, seed_tag))
+def update_caps(lx, chi):
+    n = lx * LY
+    return [[(q[0], q[1], d) for q, d in synth.bond_sectors(chi, LY, round(j / LY), synth.substream(SEED, 7, j))]
+            if 2 <= j <= n - 2 else [] for j in range(n + 1)]
 
 
-def sec_array(sec):
-    return np.array([[q[0], q[1], d] for q, d in sec], dtype=np.int32)
-
-
-def build_problem_gpu(P, ctx, rank):
-    mpo = P.MPO(None, LX, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, P.MRD_BASIS_MIXED)
-    i_idx, i_val = mpo.site(SITE)
-    j_idx, j_val = mpo.site(SITE + 1)
-    h = P.Heff(ctx, sec_array(sectors(1)), sec_array(sectors(2)), SITE % LY, (SITE + 1) % LY, mpo.modulus,
-               mpo.bond(SITE), mpo.bond(SITE + 1), mpo.bond(SITE + 2), i_idx, i_val, j_idx, j_val)
-    s = synth.substream(SEED, 100 + rank)
-    return h, (synth.complex_pm1(synth.substream(s, 8), h.lenv_len),
-               synth.complex_pm1(synth.substream(s, 9), h.renv_len),
-               synth.complex_pm1(synth.substream(s, 10), h.theta_len))
+def workload_name(chi):
+    return (f"two-site update, mixed-space Hofstadter cylinder Ly={LY} Lx={LX_UPDATE} flux={FLUX_P}/{FLUX_Q} "
+            f"t={T_HOP} V={V_INT} N={LX_UPDATE}, chi={chi}, random canonical MPS with synthetic sectors")
 
 
 class ClockSampler:
@@ -70,9 +79,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device):
-        self.device = device
-        self.proc = None
-        self.path = None
+        self.device, self.proc, self.path = device, None, None
 
     def __enter__(self):
         try:
@@ -107,37 +114,41 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        num = lambda x: x.replace(".", "").isdigit()
+        sm = [float(r[0]) for r in rows if num(r[0])]
+        mx = [float(r[1]) for r in rows if num(r[1])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
+        pw = [float(r[2]) for r in rows if num(r[2])]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())}
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
 
 def oracle_workload():
-    """The same workload for the CPU oracle: its own MPO, the same seeded sectors and
-    operands (replica 0)."""
+    """The matvec workload for the CPU oracle: its own MPO, the same seeded sectors and
+    operands as the GPU matvec measurement."""
     from oracle import blocksparse as B
     from oracle import mpo as M
-    mp = M.build_mpo(LX, LY, FLUX_P / FLUX_Q, T_HOP, V_INT, "mixed")
-    left, right = B.BondSectors(sectors(1)), B.BondSectors(sectors(2))
-    m1, m2, mod = SITE % LY, (SITE + 1) % LY, LY
-    cl, cm, cr = (mp.bond_charges[SITE], mp.bond_charges[SITE + 1], mp.bond_charges[SITE + 2])
-    wi, wj = mp.entries[SITE], mp.entries[SITE + 1]
+    site = update_centre(LX_MATVEC)
+    mp = M.build_mpo(LX_MATVEC, LY, FLUX_P / FLUX_Q, T_HOP, V_INT, "mixed")
+    left = B.BondSectors(synth.bond_sectors(CHI, LY, LX_MATVEC // 2, synth.substream(SEED, 1)))
+    right = B.BondSectors(synth.bond_sectors(CHI, LY, LX_MATVEC // 2, synth.substream(SEED, 2)))
+    m1, m2, mod = site % LY, (site + 1) % LY, LY
+    cl, cm, cr = mp.bond_charges[site], mp.bond_charges[site + 1], mp.bond_charges[site + 2]
+    wi, wj = mp.entries[site], mp.entries[site + 1]
     lay = B.theta_layout(left, right, m1, m2, mod)
     s = synth.substream(SEED, 100)
     lflat = synth.complex_pm1(synth.substream(s, 8), B.env_size(B.env_left_layout(left, cl, mod)))
     rflat = synth.complex_pm1(synth.substream(s, 9), B.env_size(B.env_right_layout(right, cr, mod)))
     tflat = synth.complex_pm1(synth.substream(s, 10), B.theta_size(lay))
-    args = (left, right, m1, m2, mod, cl, cm, cr, wi, wj)
-    return B, args, (lflat, rflat, tflat)
+    return B, (left, right, m1, m2, mod, cl, cm, cr, wi, wj), (lflat, rflat, tflat)
 
 
 def oracle_step_factory():
-    """One CPU step: the oracle's H_eff restricted to the output blocks of every fourth
-    left sector (a fixed quarter of the output), so that a step takes about a second."""
+    """One CPU step: the oracle's H_eff restricted to the output blocks of every fourth left
+    sector (a fixed quarter of the output), about a second of work."""
     B, args, flats = oracle_workload()
     rows = set(range(0, len(args[0].dims), 4))
     flops = B.heff_flops(*args, rows=rows)
@@ -154,11 +165,10 @@ def cpu_baseline(n_steps=3):
     step()
     times = [step() for _ in range(n_steps)]
     t = statistics.median(times)
-    return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)),
-            "kind": "oracle",
-            "sample": f"oracle H_eff (numpy complex128, plain loops over charge blocks) on the output blocks "
-                      f"of every 4th left sector ({flops / 1e9:.1f} GFLOP), median of {n_steps} after 1 warm-up, "
-                      f"{t:.2f} s each"}
+    return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"oracle H_eff (numpy complex128, plain loops over charge blocks) at chi={CHI}, Ly={LY}, on the "
+                      f"output blocks of every 4th left sector ({flops / 1e9:.1f} GFLOP), median of {n_steps} after "
+                      f"1 warm-up, {t:.2f} s each; compare with heff_tflops"}
 
 
 def run_reference(args):
@@ -171,33 +181,87 @@ def run_reference(args):
     t0 = time.perf_counter()
     times = [step() for _ in range(args.steps)]
     total = time.perf_counter() - t0
-    ms = 1e3 * total / args.steps
     value = flops * args.steps / total / 1e12
     cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": workload_name(), "impl": "CPU oracle (numpy), host cores",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"H_eff matvec, Ly={LY} chi={CHI} (CPU oracle, numpy, host cores)",
                        "sample": "output blocks of every 4th left sector per step"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} steps of the oracle H_eff on a fixed quarter of the "
-                                       f"output blocks ({flops / 1e9:.1f} GFLOP each), median "
+                             "sample": f"{args.steps} steps of the oracle H_eff on a fixed quarter of the output "
+                                       f"blocks ({flops / 1e9:.1f} GFLOP each), median "
                                        f"{1e3 * statistics.median(times):.0f} ms"},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
+# ---------------------------------------------------------------- GPU measurements
+
+def matvec_throughput(P, ctx, torch, dev, stream, reps=10):
+    """H_eff TFLOP/s per precision on the Lx = 20 mid-ring sites, random environments."""
+    site = update_centre(LX_MATVEC)
+    mpo = P.MPO(None, LX_MATVEC, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, P.MRD_BASIS_MIXED)
+    sec = lambda tag: np.array([[q[0], q[1], d] for q, d in synth.bond_sectors(CHI, LY, LX_MATVEC // 2,
+                                                                              synth.substream(SEED, tag))],
+                               dtype=np.int32)
+    i_idx, i_val = mpo.site(site)
+    j_idx, j_val = mpo.site(site + 1)
+    h = P.Heff(ctx, sec(1), sec(2), site % LY, (site + 1) % LY, mpo.modulus, mpo.bond(site), mpo.bond(site + 1),
+               mpo.bond(site + 2), i_idx, i_val, j_idx, j_val)
+    s = synth.substream(SEED, 100)
+    L = torch.from_numpy(synth.complex_pm1(synth.substream(s, 8), h.lenv_len)).to(dev)
+    R = torch.from_numpy(synth.complex_pm1(synth.substream(s, 9), h.renv_len)).to(dev)
+    T = torch.from_numpy(synth.complex_pm1(synth.substream(s, 10), h.theta_len)).to(dev)
+    out = torch.empty_like(T)
+    h.set_env(L, R)
+    f_def, f_exec, f1, f2 = h.flops()
+    res = {}
+    for name, prec in PREC.items():
+        n = reps if prec else 3
+        for _ in range(2):
+            h.apply(T, out, prec=prec)
+        torch.cuda.synchronize(dev)
+        h.timing(True)
+        h.timing_collect()
+        h.timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            h.apply(T, out, prec=prec)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms1, ms2, calls = h.timing_collect()
+        h.timing(False)
+        ms = e0.elapsed_time(e1) / n
+        res[name] = {"tflops": f_def / (ms / 1e3) / 1e12, "ms": ms, "ms_step1": ms1 / max(calls, 1),
+                     "ms_step2": ms2 / max(calls, 1)}
+    res["flops_definition"] = f_def
+    res["flops_executed"] = f_exec
+    res["flops_step1"], res["flops_step2"] = f1, f2
+    res["theta_len"] = h.theta_len
+    h.close()
+    return res
+
+
+def make_state(P, ctx, mpo, chi, caps, seed):
+    return P.DMRG(ctx, mpo, LX_UPDATE, 0, chi, seed=seed, center=update_centre(LX_UPDATE), caps=caps)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--chi", type=int, default=CHI, help="bond dimension (smaller cases for profiling)")
+    ap.add_argument("--chi", type=int, default=CHI)
+    ap.add_argument("--refine", type=int, default=6, help="FP64 refinement matvecs of the mixed form")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fast-restarts", type=int, default=8, help="restarts of the reduced-precision Lanczos")
+    ap.add_argument("--only-matvec", action="store_true", help="H_eff throughput only (profiling runs)")
     args = ap.parse_args()
-    set_chi(args.chi)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -216,98 +280,177 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = P.Context(local, stream)
-    h, (lflat, rflat, tflat) = build_problem_gpu(P, ctx, rank)
-    L = torch.from_numpy(lflat).to(dev)
-    R = torch.from_numpy(rflat).to(dev)
-    T = torch.from_numpy(tflat).to(dev)
-    out = torch.empty_like(T)
-    h.set_env(L, R)
-    f_def, f_exec, f1, f2 = h.flops()
-
-    for _ in range(args.warmup):
-        h.apply(T, out)
-    torch.cuda.synchronize(dev)
+    chi = args.chi
+    n_sites = LX_UPDATE * LY
+    centre = update_centre(LX_UPDATE)
+    if centre + args.warmup + args.steps + 1 > n_sites - 2:
+        raise SystemExit("too many steps for the cylinder length")
+    mpo = P.MPO(None, LX_UPDATE, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, P.MRD_BASIS_MIXED)
+    caps = update_caps(LX_UPDATE, chi)
+    seed = 11 + rank
+    # reduced-precision Lanczos restarted until its Ritz value settles, then FP64 refinement
+    mixed = P.DMRG.params(chi, 1e-14, 30, 1e-10, PREC["bf16x3"], args.refine, 1e-13, restarts=args.fast_restarts)
+    if args.only_matvec:
+        set_chi(chi)
+        mv = matvec_throughput(P, ctx, torch, dev, stream)
+        print(json.dumps({"only_matvec": True, "chi": chi, "heff_tflops": {k: mv[k]["tflops"] for k in PREC},
+                          "heff_ms_steps": {k: [mv[k]["ms_step1"], mv[k]["ms_step2"]] for k in PREC}}))
+        return 0
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # device-resident timed region
-    h.timing(True)
-    h.timing_collect()
-    h.timing(True)
-    barrier()
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- accuracy: mixed form vs converged FP64 reference of the same first H_eff
+    ref_state = make_state(P, ctx, mpo, chi, caps, seed)
+    e_ref, _ = ref_state.update(centre, +1, P.DMRG.params(chi, 1e-14, 30, 1e-13, PREC["bf16x3"], 60, 1e-15))
+    ref_state.close()
+
+    # ---- timed mixed-precision updates (device resident)
+    st = make_state(P, ctx, mpo, chi, caps, seed)
+    energies = []
+    for k in range(args.warmup):
+        e, _ = st.update(centre + k, +1, mixed)
+        energies.append(e)
+    e_mixed_first = energies[0]
     torch.cuda.synchronize(dev)
+    st.timing(True)
+    barrier()
+    phases = np.zeros(6)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = P.launch_count()
+    t_wall = time.perf_counter()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
-            h.apply(T, out)
+        for k in range(args.steps):
+            st.update(centre + args.warmup + k, +1, mixed)
+            phases += np.array(st.phase_ms())
         e1.record(stream)
         torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    launches = P.launch_count() - launches0
     barrier()
-    ms_total = e0.elapsed_time(e1)
-    ms1, ms2, ncalls = h.timing_collect()
-    h.timing(False)
-    ms_max = ms_total
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    ms_step = ms_max / args.steps
-    value = world * f_def * args.steps / (ms_max / 1e3) / 1e12
+    kms, kn = st.timing(False)
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    trunc = st.stats()[1]
+    st.close()
+    s_per_update = ms_total / 1e3 / args.steps / world
 
-    # end to end: host theta in pinned memory -> device -> H_eff -> host, every step
-    th = torch.from_numpy(tflat).pin_memory()
-    oh = torch.empty_like(th).pin_memory()
-    Td = torch.empty_like(T)
-    for _ in range(2):
-        Td.copy_(th, non_blocking=True)
-        h.apply(Td, out)
-        oh.copy_(out, non_blocking=True)
+    # ---- e2e: the two site tensors of every step come from pinned host memory and the updated
+    # tensors go back to the host, through the public API
+    st = make_state(P, ctx, mpo, chi, caps, seed)
+    for k in range(args.warmup):
+        st.update(centre + k, +1, mixed)
+    nmax = max(st.site_len(j) for j in range(n_sites))
+    hbuf = [torch.empty(nmax, dtype=torch.complex128).pin_memory() for _ in range(2)]
+    i0 = centre + args.warmup
+    st.site_into(i0, hbuf[0])
+    st.site_into(i0 + 1, hbuf[1])
     torch.cuda.synchronize(dev)
     barrier()
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    for _ in range(args.steps):
-        Td.copy_(th, non_blocking=True)
-        h.apply(Td, out)
-        oh.copy_(out, non_blocking=True)
-    e3.record(stream)
+    h2d = d2h = 0
+    t_e2e = time.perf_counter()
+    for k in range(args.steps):
+        i = i0 + k
+        h2d += 16 * (st.site_len(i) + st.site_len(i + 1))
+        st.set_site(i, hbuf[0].data_ptr())
+        st.set_site(i + 1, hbuf[1].data_ptr())
+        st.update(i, +1, mixed)
+        d2h += 16 * st.site_into(i, hbuf[0])
+        d2h += 16 * st.site_into(i + 1, hbuf[1])
     torch.cuda.synchronize(dev)
-    barrier()
-    ms_e2e = e2.elapsed_time(e3)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * f_def * args.steps / (ms_e2e / 1e3) / 1e12
-    nbytes = int(th.numel() * th.element_size())
+    t_e2e = max_over_ranks(time.perf_counter() - t_e2e)
+    st.close()
+    e2e_value = t_e2e / args.steps / world
+
+    # ---- FP64 form at the same accuracy (restarted Lanczos until the Ritz value settles)
+    st = make_state(P, ctx, mpo, chi, caps, seed)
+    fp64 = P.DMRG.params(chi, 1e-14, 30, 1e-12, PREC["fp64"], 0, 1e-14, restarts=6)
+    st.timing(True)
+    t64 = time.perf_counter()
+    e_fp64 = None
+    for k in range(args.fp64_steps):
+        e, _ = st.update(centre + k, +1, fp64)
+        if k == 0:
+            e_fp64 = e
+    torch.cuda.synchronize(dev)
+    t64 = (time.perf_counter() - t64) / args.fp64_steps
+    st.timing(False)
+    fp64_matvecs = st.stats()[2]
+    st.close()
+
+    # ---- H_eff throughput per precision (Lx = 20 mid-ring sites, random environments)
+    mv = matvec_throughput(P, ctx, torch, dev, stream)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    dom, dom_ms, dom_flops = ("k_cgemm_fp64 step 2 (theta' = sum_w' Z_w' WR_w')", ms2, f2) if ms2 >= ms1 else \
-        ("k_cgemm_fp64 step 1 (Z_w' = LW_w' theta)", ms1, f1)
-    achieved = dom_flops / (dom_ms / max(ncalls, 1) / 1e3) / 1e12
+    bf16_peak, bf16_sust, peak_src = measured_peaks()
+    tc_ms, f64_ms = kms[0] + kms[1], kms[2] + kms[3]
+    f_exec = mv["flops_executed"]
+    if f64_ms >= tc_ms:
+        ach = f_exec / (mv["fp64"]["ms"] / 1e3) / 1e12
+        roof = {"kernel": "k_cgemm_fp64 (FP64 refinement matvecs, steps 1+2)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 DFMA: 2/clk/SM x 152 SMs x 2.07 GHz (probe: 1.206 TFLOP/s at 1.995 GHz); "
+                               "not in MEASURED_PEAKS.json",
+                "gemm_share": f64_ms / (tc_ms + f64_ms)}
+    else:
+        per = tc_ms / max(kn[0], 1) / 1e3
+        hw = 3 * f_exec / per / 1e12
+        roof = {"kernel": "k_tc_gemm BF16X3 (steps 1+2)", "bound": "tensor", "achieved": hw, "peak": bf16_sust,
+                "unit": "TFLOP/s", "frac": hw / bf16_sust, "traffic": None, "peak_source": f"bf16 sustained {peak_src}",
+                "gemm_share": tc_ms / (tc_ms + f64_ms)}
+    tc = mv["bf16x3"]
+    tc_hw = 3 * f_exec / (tc["ms"] / 1e3) / 1e12
+    tf = mv["tf32"]
+    tf_hw = f_exec / (tf["ms"] / 1e3) / 1e12
     line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(), "chi": CHI, "ly": LY, "lx": LX,
-                   "theta_len": h.theta_len, "lenv_len": h.lenv_len, "renv_len": h.renv_len,
-                   "flops_definition": f_def, "flops_executed": f_exec, "precision": "FP64",
-                   "l2": "working set > L2 (environments folded with the MPO and the Z intermediate, ~2.5 GB)",
+        "metric": METRIC, "value": s_per_update, "unit": "s/update", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+        "config": {"workload": workload_name(chi), "chi": chi, "ly": LY, "lx": LX_UPDATE,
+                   "form": f"split-BF16 tensor-core Lanczos (30 per run, up to {args.fast_restarts} restarts) + "
+                           f"FP64 Lanczos refinement (up to {args.refine} matvecs)",
+                   "l2": "working set > L2 (folded environments, Z intermediate and Lanczos basis, >1 GB)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "FP64 DFMA: 2 per clock per SM x 152 SMs x 2.07 GHz (measured 1.206 TFLOP/s "
-                                    "at 1.995 GHz); not in MEASURED_PEAKS.json"},
-        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "gpu_launches": 2 * args.steps,
+        "s_per_update_fp64": t64,
+        "fp64_form_matvecs": fp64_matvecs,
+        "speedup_vs_fp64": t64 / (ms_total / 1e3 / args.steps),
+        "dE_rel_mixed_vs_converged_fp64": abs(e_mixed_first - e_ref) / abs(e_ref),
+        "dE_rel_fp64_form_vs_converged_fp64": abs(e_fp64 - e_ref) / abs(e_ref),
+        "energy_first_update": {"mixed": e_mixed_first, "fp64_form": e_fp64, "converged_fp64": e_ref},
+        "discarded_weight_last": trunc,
+        "phase_ms_mean": dict(zip(["tables", "theta", "lanczos+refine", "svd", "tensors", "env"],
+                                  (phases / args.steps).round(2).tolist())),
+        "gemm_ms_per_step": {"tc": tc_ms / args.steps, "fp64": f64_ms / args.steps},
+        "heff_tflops": {k: round(mv[k]["tflops"], 3) for k in PREC},
+        "heff_ms": {k: round(mv[k]["ms"], 4) for k in PREC},
+        "heff_ms_steps": {k: [round(mv[k]["ms_step1"], 4), round(mv[k]["ms_step2"], 4)] for k in PREC},
+        "heff_flops": {"definition": mv["flops_definition"], "executed": mv["flops_executed"]},
+        "roofline": roof,
+        "roofline_tc_bf16x3": {"kernel": "k_tc_gemm BF16X3 (steps 1+2), Lx=20 matvec", "bound": "tensor",
+                               "achieved": tc_hw, "peak": bf16_peak, "unit": "TFLOP/s", "frac": tc_hw / bf16_peak,
+                               "traffic": None, "note": "hardware bf16 flops = 3 x executed complex-product flops "
+                                                        f"(split), peak = bf16 burst {peak_src}"},
+        "roofline_tc_tf32": {"kernel": "k_tc_gemm TF32 (steps 1+2), Lx=20 matvec", "bound": "tensor",
+                             "achieved": tf_hw, "peak": bf16_peak / 2, "unit": "TFLOP/s",
+                             "frac": tf_hw / (bf16_peak / 2), "traffic": None,
+                             "note": f"TF32 peak = bf16 burst {peak_src} x 1/2 (nominal ratio)"},
+        "e2e": {"value": e2e_value, "unit": "s/update", "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
         "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

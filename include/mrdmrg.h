@@ -56,6 +56,8 @@ extern "C" {
 #define MRD_E_STATE (-8)    /* call out of order (e.g. apply before set_env)              */
 
 #define MRD_PREC_FP64 0     /* complex128 operands, FP64 arithmetic                       */
+#define MRD_PREC_TF32 1     /* tcgen05 tensor cores, TF32 operands, FP32 accumulation     */
+#define MRD_PREC_BF16X3 2   /* tcgen05, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accum.   */
 
 #define MRD_BASIS_MIXED 0   /* orbitals (x, k_m), charges (N, K mod Ly)                   */
 #define MRD_BASIS_REAL 1    /* orbitals (x, y), charge N only (modulus 1)                 */
@@ -76,6 +78,8 @@ int mrd_set_stream(mrd_ctx* ctx, void* stream);
 const char* mrd_last_error(const mrd_ctx* ctx);
 /* Library version as major*10000 + minor*100 + patch. */
 int mrd_version(void);
+/* Number of CUDA kernels this library has launched so far in this process (all contexts). */
+int64_t mrd_launch_count(void);
 
 /* ------------------------------------------------------------------ MPO (Sec. IV) */
 
@@ -126,7 +130,11 @@ int mrd_heff_sizes(const mrd_heff* h, int64_t* theta_len, int64_t* lenv_len, int
  * with the MPO into internal operands LW_{w'} = sum_w W_i[w,w'] L_w and
  * WR_{w'} = sum_{w''} W_{i+1}[w',w''] R_{w''}; the caller's buffers are not retained. */
 int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev);
-/* theta_out = H_eff theta_in (device pointers; must not overlap). */
+/* theta_out = H_eff theta_in (device pointers, complex128; must not overlap). prec:
+ * MRD_PREC_FP64 runs FP64 grouped GEMMs; MRD_PREC_TF32 and MRD_PREC_BF16X3 run the same
+ * contraction on the tcgen05 tensor cores with FP32 accumulation (complex products as four
+ * real ones), operands repacked into 128-byte swizzled tiles: the folded environments once
+ * after each mrd_heff_set_env, theta on every call; the result is returned in complex128. */
 int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev, int32_t prec);
 /* Real flops of one H_eff application (8 per complex multiply-add), written to flops4:
  * [0] in the order of the definition (L step, W step, R step); [1] as executed by the
@@ -166,9 +174,14 @@ typedef struct {
   int32_t lanczos_max_iter;  /* 1 .. MRD_LANCZOS_MAX_ITER                                    */
   double lanczos_tol;        /* relative change of the Ritz value that stops Lanczos         */
   int32_t prec;              /* MRD_PREC_* of the Lanczos matvecs                            */
+  int32_t refine_iter;       /* > 0 with a reduced prec: FP64 Lanczos polish of the ground   */
+                             /* vector, at most this many FP64 matvecs (iterative refinement) */
+  double refine_tol;         /* relative Ritz-value change that stops the polish              */
+  int32_t lanczos_restarts;  /* extra Lanczos runs restarted from the current ground vector   */
+                             /* while the Ritz value still moves by more than lanczos_tol     */
 } mrd_dmrg_params;
 
-/* Finite two-site DMRG state on the device for the MPO `mpo` (which must outlive it) in the
+/* Finite two-site DMRG state on the device for the MPO `mpo` (copied; it may be freed later) in the
  * charge sector (N = n_part, K = k_tot mod modulus). Starts from a seeded random MPS whose
  * entries are SplitMix64 draws (counter-based, seed `seed`): sites left of `center` are
  * left-canonical, the others right-canonical (orthonormalised by the block SVD), and the
@@ -184,7 +197,9 @@ int mrd_dmrg_free(mrd_dmrg* d);
  * state of H_eff by Lanczos, block SVD of theta by middle charge (the Schmidt decomposition,
  * Sec. III.C), truncation to chi with cutoff, renormalised Schmidt values; direction +1
  * moves the orthogonality centre right (A_i = U, M_{i+1} = S V^+, then L_{i+1}) and -1 left
- * (M_i = U S, B_{i+1} = V^+, then R_{i+1}). Needs L_i and R_{i+2}. Writes the Ritz energy
+ * (M_i = U S, B_{i+1} = V^+, then R_{i+1}). Needs L_i and R_{i+2}. With a reduced-precision
+ * prec and refine_iter > 0 the Lanczos ground vector is polished by FP64 Lanczos started
+ * from it (iterative refinement); the energy is then the FP64 Ritz value. Writes the energy
  * and the discarded weight. */
 int mrd_two_site_update(mrd_dmrg* d, int32_t i, int32_t direction, const mrd_dmrg_params* p, double* energy,
                         double* trunc_err);
@@ -201,7 +216,21 @@ int mrd_dmrg_site(mrd_dmrg* d, int32_t site, int32_t* mode, int64_t* len, double
 /* Copy of the left (side 0) or right (side 1) environment at `bond` in the layouts of this
  * header; *len = -1 if it is not built. */
 int mrd_dmrg_env(mrd_dmrg* d, int32_t bond, int32_t side, int64_t* len, double* host);
-/* Energy, discarded weight and Lanczos matvecs of the last two-site update. */
+/* Replace the data of MPS tensor `site` with host data in the layout mrd_dmrg_site reports
+ * (same sectors and mode; *len complex128 values). The copy is enqueued on the context
+ * stream (pinned host memory makes it asynchronous). */
+int mrd_dmrg_set_site(mrd_dmrg* d, int32_t site, const double* host);
+/* GEMM kernel timing of the updates: returns (and clears) the accumulated CUDA-event times in
+ * ms of the tensor-core step-1 and step-2 launches and of the FP64 step-1 and step-2
+ * launches, and the number of tensor-core and FP64 H_eff applications; then switches the
+ * recording on (on != 0) or off. Arrays may be NULL. */
+int mrd_dmrg_timing(mrd_dmrg* d, int32_t on, double* kernel_ms4, int64_t* applies2);
+/* Wall time in ms of the phases of the last two-site update (each ends with a stream
+ * synchronisation): [0] H_eff tables and environment fold, [1] theta, [2] Lanczos,
+ * [3] block SVD and truncation, [4] new MPS tensors, [5] environment update. */
+int mrd_dmrg_phase_ms(const mrd_dmrg* d, double* ms6);
+/* Energy, discarded weight and matvec count of the last two-site update; the count is the
+ * reduced-precision (or FP64) Lanczos matvecs plus 1000 times the FP64 refinement matvecs. */
 int mrd_dmrg_stats(const mrd_dmrg* d, double* energy, double* trunc_err, int32_t* lanczos_iters);
 
 /* Capacity of the static scratch used by mrd_heff_apply_noalloc, in complex128 elements

@@ -12,6 +12,8 @@ import numpy as np
 from . import build as _build
 
 MRD_PREC_FP64 = 0
+MRD_PREC_TF32 = 1
+MRD_PREC_BF16X3 = 2
 MRD_BASIS_MIXED = 0
 MRD_BASIS_REAL = 1
 
@@ -37,6 +39,11 @@ def _close_all():
 
 import atexit  # noqa: E402
 atexit.register(_close_all)
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().mrd_launch_count())
 
 
 def lib_path() -> str:
@@ -66,6 +73,7 @@ class mrd_heff_desc(C.Structure):
 
 _SIGS = {
     "mrd_version": (C.c_int, []),
+    "mrd_launch_count": (C.c_int64, []),
     "mrd_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     "mrd_destroy": (C.c_int, [C.c_void_p]),
     "mrd_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -99,6 +107,9 @@ _SIGS = {
                                 C.POINTER(C.c_double)]),
     "mrd_dmrg_env": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "mrd_dmrg_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "mrd_dmrg_phase_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mrd_dmrg_set_site": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "mrd_dmrg_timing": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
@@ -237,7 +248,8 @@ class MPO:
 
 class mrd_dmrg_params(C.Structure):
     _fields_ = [("chi", C.c_int32), ("svd_cutoff", C.c_double), ("lanczos_max_iter", C.c_int32),
-                ("lanczos_tol", C.c_double), ("prec", C.c_int32)]
+                ("lanczos_tol", C.c_double), ("prec", C.c_int32), ("refine_iter", C.c_int32),
+                ("refine_tol", C.c_double), ("lanczos_restarts", C.c_int32)]
 
 
 class DMRG:
@@ -257,8 +269,9 @@ class DMRG:
         _register(self)
 
     @staticmethod
-    def params(chi, cutoff=1e-14, max_iter=30, tol=1e-13, prec=MRD_PREC_FP64):
-        return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec)
+    def params(chi, cutoff=1e-14, max_iter=30, tol=1e-13, prec=MRD_PREC_FP64, refine_iter=0, refine_tol=1e-13,
+               restarts=0):
+        return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec, refine_iter, refine_tol, restarts)
 
     def update(self, i, direction, params):
         e, t = C.c_double(), C.c_double()
@@ -292,6 +305,33 @@ class DMRG:
         buf = np.zeros(2 * max(ln.value, 1), dtype=np.float64)
         self.ctx.check(lib().mrd_dmrg_env(self.h, b, side, C.byref(ln), _p64f(buf)))
         return (buf[0::2] + 1j * buf[1::2])[: ln.value]
+
+    def set_site(self, j, host_ptr):
+        """host_ptr: address of complex128 data (e.g. a pinned torch tensor's data_ptr())."""
+        self.ctx.check(lib().mrd_dmrg_set_site(self.h, j, _ptr(host_ptr)))
+
+    def site_into(self, j, host_tensor):
+        """Copy MPS tensor j into a host tensor (complex128, numel >= len)."""
+        mode, ln = C.c_int32(), C.c_int64()
+        self.ctx.check(lib().mrd_dmrg_site(self.h, j, C.byref(mode), C.byref(ln),
+                                           C.cast(C.c_void_p(host_tensor.data_ptr()), C.POINTER(C.c_double))))
+        return ln.value
+
+    def site_len(self, j):
+        mode, ln = C.c_int32(), C.c_int64()
+        self.ctx.check(lib().mrd_dmrg_site(self.h, j, C.byref(mode), C.byref(ln), None))
+        return ln.value
+
+    def timing(self, on=True):
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 2)()
+        self.ctx.check(lib().mrd_dmrg_timing(self.h, 1 if on else 0, ms, n))
+        return list(ms), list(n)
+
+    def phase_ms(self):
+        f = (C.c_double * 6)()
+        self.ctx.check(lib().mrd_dmrg_phase_ms(self.h, f))
+        return list(f)
 
     def stats(self):
         e, t, it = C.c_double(), C.c_double(), C.c_int32()

@@ -1,5 +1,6 @@
 // C ABI entry points (include/mrdmrg.h): argument checks, device memory, launches.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,11 @@ double2* lanczos_work(Lanczos* L);
 
 using namespace mrd;
 
+namespace mrd {
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace mrd
+
 void mrd_ctx_retain(mrd_ctx* ctx) {
   if (ctx) ++ctx->refs;
 }
@@ -51,6 +57,8 @@ int mrd_cuda_fail(mrd_ctx* ctx, cudaError_t e, const char* where) {
 extern "C" {
 
 int mrd_version(void) { return 100; }
+
+int64_t mrd_launch_count(void) { return mrd::g_launches.load(); }
 
 int mrd_create(mrd_ctx** out, int device, void* stream) {
   if (!out) return MRD_E_ARG;
@@ -251,7 +259,10 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
       v.resize(n);
       if (e == cudaSuccess && n) e = cudaMemcpy(v.data(), src, n * 8, cudaMemcpyDeviceToHost);
     };
-    std::vector<int64_t> t1, s1, t2, s2;
+    std::vector<int64_t>& t1 = h->t1_host;
+    std::vector<int64_t>& s1 = h->s1_host;
+    std::vector<int64_t>& t2 = h->t2_host;
+    std::vector<int64_t>& s2 = h->s2_host;
     std::vector<int64_t>& lw = h->lw_host;
     std::vector<int64_t>& wr = h->wr_host;
     std::vector<int64_t>& lmap = h->lmap_host;
@@ -411,6 +422,7 @@ int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev
                         h->p.wj_perm, h->p.wj_idx, h->wj_val, 1, ctx->stream);
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_set_env");
   h->env_loaded = true;
+  tc_env_changed(h);
   return MRD_OK;
 }
 
@@ -418,13 +430,15 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   if (!h) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   if (!h->env_loaded) return mrd_fail(ctx, MRD_E_STATE, "mrd_heff_apply: environments not loaded");
-  if (prec != MRD_PREC_FP64) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: unsupported precision");
+  if (prec != MRD_PREC_FP64 && prec != MRD_PREC_TF32 && prec != MRD_PREC_BF16X3)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: unsupported precision");
   const int64_t n = h->counts[C_THETA];
   if (n > 0 && (!theta_in_dev || !theta_out_dev)) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: null theta");
   const char* a = (const char*)theta_in_dev;
   const char* b = (const char*)theta_out_dev;
   if (n > 0 && a < b + n * 16 && b < a + n * 16) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: theta_in and theta_out overlap");
   Guard g(ctx->device);
+  if (prec != MRD_PREC_FP64) return tc_apply(h, theta_in_dev, theta_out_dev, prec);
   cudaStream_t s = ctx->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (h->timing) {
@@ -484,6 +498,7 @@ int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, in
   int it = 0;
   rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr);
   *iters = it;
+  if (rc == MRD_OK && prec != MRD_PREC_FP64) rc = tc_status(h);
   return rc;
 }
 

@@ -14,6 +14,7 @@
 // lists built here from the sector tables; every output block has one owner task.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -227,7 +228,11 @@ struct mrd_dmrg {
   Buf gtask, gseg, gpref, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
       svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, tbuf, zeros;
   double last_energy = 0.0, last_trunc = 0.0;
-  int last_iters = 0;
+  int last_iters = 0, last_refine = 0;
+  bool timing = false;
+  double kms[4] = {0, 0, 0, 0};   // accumulated GEMM ms: tensor-core step 1, step 2, FP64 step 1, step 2
+  int64_t kcount[2] = {0, 0};     // applies: tensor core, FP64
+  double phase_ms[6] = {0, 0, 0, 0, 0, 0};   // plan, theta, lanczos, svd, tensors, env (last update)
 };
 
 namespace {
@@ -278,6 +283,7 @@ int run_copies(mrd_dmrg* D, const std::vector<int64_t>& t, const double2* src, d
   MRD_CUDA(ctx, D->ctask.need(t.size() * 8));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->ctask.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, s));
   k_copy_blocks<<<std::min(nt, 4096), 256, 0, s>>>(src, dst, D->ctask.as<int64_t>(), nt, S, sscale);
+  mrd::count_launch();
   MRD_CUDA(ctx, cudaGetLastError());
   MRD_CUDA(ctx, cudaStreamSynchronize(s));
   return MRD_OK;
@@ -748,6 +754,7 @@ int mrd_dmrg_create(mrd_ctx* ctx, const mrd_mpo* mpo, int32_t n_part, int32_t k_
     if (T.size > 0) {
       const int64_t grid = std::min<int64_t>((T.size + 255) / 256, 4096);
       k_fill_random<<<(unsigned)grid, 256, 0, s>>>(T.data.as<double2>(), T.size, seed * 0x100000001B3ull + (uint64_t)j * 0x9E3779B97F4A7C15ull);
+      mrd::count_launch();
     }
   }
   int rcd = MRD_OK;
@@ -797,18 +804,57 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   if (!D->L[i].data.p || !D->R[i + 2].data.p)
     return mrd_fail(ctx, MRD_E_STATE, "mrd_two_site_update: environments of this bond are not available");
   Guard g(ctx->device);
+  using clk = std::chrono::steady_clock;
+  auto t0 = clk::now();
+  auto lap = [&](int k) {
+    cudaStreamSynchronize(ctx->stream);
+    auto t1 = clk::now();
+    D->phase_ms[k] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    t0 = t1;
+  };
   mrd_heff* h = nullptr;
   int rc = make_heff(D, i, D->L[i].data.as<double2>(), D->R[i + 2].data.as<double2>(), &h);
   if (rc != MRD_OK) return rc;
   struct Free { mrd_heff* h; ~Free() { if (h) mrd_heff_free(h); } } guard{h};
+  if (D->timing) mrd_heff_timing(h, 1);
+  auto collect = [&](int which) {
+    if (!D->timing) return;
+    double a = 0, b = 0;
+    int32_t n = 0;
+    mrd_heff_timing_collect(h, &a, &b, &n);
+    D->kms[2 * which] += a;
+    D->kms[2 * which + 1] += b;
+    D->kcount[which] += n;
+  };
+  lap(0);
   const int64_t n = h->counts[C_THETA];
   MRD_CUDA(ctx, D->theta.need((size_t)std::max<int64_t>(n, 1) * 16));
   double2* theta = D->theta.as<double2>();
   if ((rc = form_theta(D, h, D->A[i], D->A[i + 1], theta)) != MRD_OK) return rc;
+  lap(1);
   double e = 0.0;
   int32_t it = 0;
   if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e, &it)) != MRD_OK) return rc;
   D->last_iters = it;
+  collect(p->prec == MRD_PREC_FP64 ? 1 : 0);
+  for (int r = 0; r < p->lanczos_restarts && it == p->lanczos_max_iter; ++r) {
+    double e2 = 0.0;
+    if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e2, &it)) != MRD_OK)
+      return rc;
+    D->last_iters += it;
+    const bool done = std::fabs(e2 - e) < p->lanczos_tol * std::fabs(e2);
+    e = e2;
+    if (done) break;
+  }
+  D->last_refine = 0;
+  if (p->prec != MRD_PREC_FP64 && p->refine_iter > 0) {
+    int32_t it2 = 0;
+    if ((rc = mrd_lanczos(h, (double*)theta, p->refine_iter, p->refine_tol, MRD_PREC_FP64, &e, &it2)) != MRD_OK)
+      return rc;
+    D->last_refine = it2;
+  }
+  collect(1);
+  lap(2);
   // block SVD of theta by middle charge
   std::vector<int64_t> blk, src;
   std::vector<int> mids;
@@ -823,6 +869,7 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   std::vector<int> keep;
   double info[3];
   if ((rc = block_svd(D, blk, src, theta, p->chi, p->svd_cutoff, keep, info)) != MRD_OK) return rc;
+  lap(3);
   // new bond i+1
   Secs nb;
   for (size_t b = 0; b < mids.size(); ++b)
@@ -853,9 +900,11 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   const double* sscale = D->svd_info.as<double>();
   if ((rc = run_copies(D, cx, D->svd_u.as<double2>(), X.data.as<double2>(), S, sscale)) != MRD_OK) return rc;
   if ((rc = run_copies(D, cy, D->svd_vh.as<double2>(), Y.data.as<double2>(), S, sscale)) != MRD_OK) return rc;
+  lap(4);
   if (direction > 0) rc = env_left(D, h, i);
   else rc = env_right(D, h, i);
   if (rc != MRD_OK) return rc;
+  lap(5);
   D->last_energy = e;
   D->last_trunc = info[1];
   if (energy) *energy = e;
@@ -911,11 +960,39 @@ int mrd_dmrg_env(mrd_dmrg* D, int32_t bond, int32_t side, int64_t* len, double* 
   return MRD_OK;
 }
 
+int mrd_dmrg_timing(mrd_dmrg* D, int32_t on, double* kernel_ms4, int64_t* applies2) {
+  if (!D) return MRD_E_ARG;
+  if (kernel_ms4)
+    for (int k = 0; k < 4; ++k) kernel_ms4[k] = D->kms[k];
+  if (applies2) { applies2[0] = D->kcount[0]; applies2[1] = D->kcount[1]; }
+  for (int k = 0; k < 4; ++k) D->kms[k] = 0;
+  D->kcount[0] = D->kcount[1] = 0;
+  D->timing = on != 0;
+  return MRD_OK;
+}
+
+int mrd_dmrg_set_site(mrd_dmrg* D, int32_t site, const double* host) {
+  if (!D || site < 0 || site >= D->n) return MRD_E_ARG;
+  SiteT& T = D->A[site];
+  if (T.size && !host) return mrd_fail(D->ctx, MRD_E_ARG, "mrd_dmrg_set_site: null data");
+  if (T.size) {
+    Guard g(D->ctx->device);
+    MRD_CUDA(D->ctx, cudaMemcpyAsync(T.data.p, host, (size_t)T.size * 16, cudaMemcpyHostToDevice, D->ctx->stream));
+  }
+  return MRD_OK;
+}
+
+int mrd_dmrg_phase_ms(const mrd_dmrg* D, double* ms6) {
+  if (!D || !ms6) return MRD_E_ARG;
+  for (int k = 0; k < 6; ++k) ms6[k] = D->phase_ms[k];
+  return MRD_OK;
+}
+
 int mrd_dmrg_stats(const mrd_dmrg* D, double* energy, double* trunc_err, int32_t* lanczos_iters) {
   if (!D) return MRD_E_ARG;
   if (energy) *energy = D->last_energy;
   if (trunc_err) *trunc_err = D->last_trunc;
-  if (lanczos_iters) *lanczos_iters = D->last_iters;
+  if (lanczos_iters) *lanczos_iters = D->last_iters + 1000 * D->last_refine;
   return MRD_OK;
 }
 

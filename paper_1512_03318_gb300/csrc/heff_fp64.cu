@@ -153,6 +153,7 @@ cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, co
   int64_t grid = (int64_t)n_sm * 8;
   if (grid > total_tiles) grid = total_tiles;
   k_cgemm_fp64<<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 
@@ -162,6 +163,7 @@ cudaError_t launch_fold_env(const double2* env, double2* out, const int64_t* row
   if (nrows <= 0) return cudaSuccess;
   int64_t grid = nrows < 65535 ? nrows : 65535;
   k_fold_env<<<(unsigned)grid, 256, 0, s>>>(env, out, rows, nrows, env_map, n_sec, perm, idx, val, chan_field);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 

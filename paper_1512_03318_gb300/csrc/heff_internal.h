@@ -9,6 +9,12 @@ namespace mrd {
 struct Lanczos;
 void lanczos_free(Lanczos* L);
 }  // namespace mrd
+struct Tc;
+void tc_free(Tc* t);
+struct mrd_heff;
+int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec);
+void tc_env_changed(mrd_heff* h);
+int tc_status(mrd_heff* h);
 using mrd::Lanczos;
 using mrd::lanczos_free;
 using mrd::PlanDims;
@@ -81,11 +87,14 @@ struct mrd_heff {
   std::vector<cudaEvent_t> ev_pool;
   Lanczos* lz = nullptr;
   // host copies of the device-built tables (downloaded once at creation)
-  std::vector<int64_t> mid_host, lw_host, wr_host, lmap_host, rmap_host;
+  std::vector<int64_t> mid_host, lw_host, wr_host, lmap_host, rmap_host, t1_host, s1_host, t2_host, s2_host;
+  // tensor-core path state (tc_host.cu)
+  struct Tc* tc = nullptr;
   ~mrd_heff() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     lanczos_free(lz);
+    tc_free(tc);
   }
 };
 

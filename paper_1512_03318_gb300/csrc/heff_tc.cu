@@ -1,0 +1,427 @@
+// Tensor-core (tcgen05 / TMEM) grouped complex GEMMs of the two-site H_eff in reduced
+// precision with FP32 accumulation.
+//
+// Same two steps as the FP64 path (step 1: Z_{w'} = LW_{w'} theta; step 2:
+// theta' = sum_{w'} Z_{w'} WR_{w'}), same task decomposition. A complex product is four real
+// products on real tensor cores, C_re = A_re B_re - A_im B_im and C_im = A_re B_im + A_im B_re,
+// the minus sign coming from the A-negate bit of the instruction descriptor. Precisions:
+//   TF32    operands rounded to TF32 (planes re, im); 4 MMAs per complex product step.
+//   BF16X3  every operand x split as x_hi = bf16(x), x_lo = bf16(x - x_hi) (planes re_hi,
+//           re_lo, im_hi, im_lo); A_hi B_hi + A_hi B_lo + A_lo B_hi per real product, so 12
+//           MMAs per complex step (the split-precision scheme of Henry, Tang & Heinecke 2019).
+//
+// Operands live in HBM as "panels" of UMMA-ready tiles: a tile is R rows x 128 bytes of K
+// (32 TF32 or 64 BF16 values), K-major, 128-byte swizzled, zero padded, with its planes
+// stored back to back, so one cp.async.bulk moves a tile into shared memory unchanged.
+// A panels have 128-row tiles; B panels hold all N rows (padded to 16, at most 256 per tile).
+// LW and WR are packed once per environment load, theta once per matvec, and the step-1
+// epilogue writes Z directly in the packed A format of step 2.
+//
+// Kernel: persistent, one CTA per SM, 6 warps: warp 0 issues the bulk copies, warp 1 owns
+// TMEM (512 columns: C_re at 0, C_im at 256) and issues the MMAs from one thread, warps 2-5
+// drain the accumulators (warp w reads TMEM lanes 32 (w % 4) ..). Shared-memory stages are
+// handed over with mbarriers; every wait is bounded and sets an error flag when it gives up.
+#include <cuda_bf16.h>
+
+#include "mrd_internal.h"
+#include "tc.cuh"
+
+namespace mrd {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t sw128(uint32_t row, uint32_t byte_in_row) {
+  const uint32_t lin = row * 128u + byte_in_row;
+  return lin ^ (((lin >> 7) & 7u) << 4);
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // SBO: 8 rows x 128 bytes
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ uint32_t make_idesc(int prec, int n, bool neg_a) {
+  uint32_t d = 0;
+  d |= 1u << 4;                                        // D: FP32
+  if (prec == TC_TF32) { d |= 2u << 7; d |= 2u << 10; }  // A, B: TF32
+  else { d |= 1u << 7; d |= 1u << 10; }                // A, B: BF16
+  if (neg_a) d |= 1u << 13;
+  d |= (uint32_t)(n >> 3) << 17;
+  d |= (uint32_t)(128 >> 4) << 24;
+  return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  }
+  if (!done) atomicCAS(err, 0, code);
+  return done != 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mma(int prec, uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (prec == TC_TF32)
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  else
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ int64_t find_task(const int64_t* prefix, int64_t n, int64_t item) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Store one value into a packed panel: element (row, k), plane q.
+__device__ __forceinline__ void put_packed(uint8_t* base, const TcPanelGeom& g, int64_t row, int64_t k, int plane,
+                                           int prec, float v) {
+  const int ebytes = prec == TC_TF32 ? 4 : 2;
+  const int kpt = 128 / ebytes;
+  const int64_t rt = row / 128, kt = k / kpt;
+  uint8_t* tile = base + ((rt * g.nkt + kt) * g.planes + plane) * (int64_t)(128 * 128);
+  const uint32_t off = sw128((uint32_t)(row % 128), (uint32_t)((k % kpt) * ebytes));
+  if (prec == TC_TF32) *(float*)(tile + off) = v;
+  else *(__nv_bfloat16*)(tile + off) = __float2bfloat16_rn(v);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- packing kernels
+
+// Pack FP64 complex blocks into panels. Each job: src element offset, src row stride,
+// transpose flag (0: panel row r, col k = src[r * ld + k]; 1: = src[k * ld + r]), rows, K,
+// destination panel byte offset, row tile height (128 for A, padded N for B), nkt.
+__global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ dst, const int64_t* __restrict__ jobs,
+                       int njobs, int prec) {
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const int64_t* d = jobs + TCJ * j;
+    const int64_t s_off = d[0], ld = d[1], trans = d[2], rows = d[3], K = d[4], p_off = d[5], rowtile = d[6],
+                  nkt = d[7], npad = d[8];
+    const int ebytes = prec == TC_TF32 ? 4 : 2;
+    const int kpt = 128 / ebytes;
+    const int planes = prec == TC_TF32 ? 2 : 4;
+    for (int64_t e = threadIdx.x; e < rows * K; e += blockDim.x) {
+      int64_t r, k;
+      double2 v;
+      if (!trans) {
+        r = e / K; k = e % K;
+        v = src[s_off + r * ld + k];
+      } else {
+        k = e / rows; r = e % rows;   // consecutive threads read consecutive source columns
+        v = src[s_off + k * ld + r];
+      }
+      const int64_t rt = r / rowtile, kt = k / kpt;
+      const int64_t nrow = npad - rt * rowtile < rowtile ? npad - rt * rowtile : rowtile;
+      const int64_t tile_bytes = nrow * 128;   // one plane of this row tile
+      uint8_t* tile = dst + p_off + rt * nkt * planes * rowtile * 128 + kt * planes * tile_bytes;
+      const uint32_t off = sw128((uint32_t)(r % rowtile), (uint32_t)((k % kpt) * ebytes));
+      if (prec == TC_TF32) {
+        *(float*)(tile + off) = tf32_rna((float)v.x);
+        *(float*)(tile + tile_bytes + off) = tf32_rna((float)v.y);
+      } else {
+        const __nv_bfloat16 rh = __double2bfloat16(v.x);
+        const __nv_bfloat16 rl = __double2bfloat16(v.x - (double)__bfloat162float(rh));
+        const __nv_bfloat16 ih = __double2bfloat16(v.y);
+        const __nv_bfloat16 il = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+        *(__nv_bfloat16*)(tile + off) = rh;
+        *(__nv_bfloat16*)(tile + tile_bytes + off) = rl;
+        *(__nv_bfloat16*)(tile + 2 * tile_bytes + off) = ih;
+        *(__nv_bfloat16*)(tile + 3 * tile_bytes + off) = il;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- grouped GEMM
+
+struct TcArgs {
+  const uint8_t* a_base;   // packed A panels
+  const uint8_t* b_base;   // packed B panels
+  const int64_t* tasks;    // TCT per task
+  const int64_t* segs;     // TCS per segment
+  const int64_t* prefix;   // tiles prefix (n_tasks + 1)
+  int64_t n_tasks;
+  uint8_t* z_out;          // packed Z output (mode 0)
+  double2* f_out;          // FP64 output (mode 1)
+  int prec;
+  int* err;
+};
+
+constexpr int kStages = kTcStages;
+constexpr int kStageBytes = kTcStageBytes;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
+  extern __shared__ uint8_t dyn[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int prec = g.prec;
+  const int planes = prec == TC_TF32 ? 2 : 4;
+  const int kpt = prec == TC_TF32 ? 32 : 64;       // K values per 128-byte row
+  const int kstep = prec == TC_TF32 ? 8 : 16;      // K per MMA instruction
+  const int ntile = tc_ntile(prec);                // B rows (output columns) per tile
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc_full), 1);
+    mbar_init(smem_u32(&bar_acc_empty), 4);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int64_t total = g.prefix[g.n_tasks];
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+      const int64_t t = find_task(g.prefix, g.n_tasks, item);
+      const int64_t* task = g.tasks + TCT * t;
+      const int64_t N = task[1];
+      const int64_t local = item - g.prefix[t];
+      const int64_t tiles_n = (N + ntile - 1) / ntile;
+      const int64_t rt = local / tiles_n, nt = local % tiles_n;
+      const int64_t npad = ((N + 15) / 16) * 16;
+      const int64_t nrow = npad - nt * ntile < ntile ? npad - nt * ntile : ntile;
+      for (int64_t s = 0; s < task[6] && ok; ++s) {
+        const int64_t* sg = g.segs + TCS * (task[5] + s);
+        const int64_t nkt = sg[2];
+        const uint8_t* a = g.a_base + sg[0] + rt * nkt * planes * (int64_t)(128 * 128);
+        const uint8_t* b = g.b_base + sg[1] + nt * nkt * planes * (int64_t)ntile * 128;
+        for (int64_t kt = 0; kt < nkt && ok; ++kt) {
+          ok = mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1, g.err, 11);
+          if (!ok) break;
+          const uint32_t abytes = planes * 128 * 128, bbytes = (uint32_t)(planes * nrow * 128);
+          const uint32_t sa = smem_u32(smem + stage * kStageBytes);
+          const uint32_t sb = sa + planes * 128 * 128;
+          mbar_expect_tx(smem_u32(&bar_full[stage]), abytes + bbytes);
+          bulk_g2s(sa, a + kt * abytes, abytes, smem_u32(&bar_full[stage]));
+          bulk_g2s(sb, b + kt * (int64_t)bbytes, bbytes, smem_u32(&bar_full[stage]));
+          if (++stage == kStages) { stage = 0; phase ^= 1; }
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    int stage = 0;
+    uint32_t phase = 0, acc_phase = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+      const int64_t t = find_task(g.prefix, g.n_tasks, item);
+      const int64_t* task = g.tasks + TCT * t;
+      const int64_t N = task[1];
+      const int64_t local = item - g.prefix[t];
+      const int64_t tiles_n = (N + ntile - 1) / ntile;
+      const int64_t nt = local % tiles_n;
+      const int64_t npad = ((N + 15) / 16) * 16;
+      const int nrow = (int)(npad - nt * ntile < ntile ? npad - nt * ntile : ntile);
+      // accumulators free?
+      ok = mbar_wait(smem_u32(&bar_acc_empty), acc_phase ^ 1, g.err, 12);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t id_pos = make_idesc(prec, nrow, false), id_neg = make_idesc(prec, nrow, true);
+      bool first = true;
+      for (int64_t s = 0; s < task[6] && ok; ++s) {
+        const int64_t nkt = g.segs[TCS * (task[5] + s) + 2];
+        for (int64_t kt = 0; kt < nkt && ok; ++kt) {
+          ok = mbar_wait(smem_u32(&bar_full[stage]), phase, g.err, 13);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sa = smem_u32(smem + stage * kStageBytes);
+          const uint32_t sb = sa + planes * 128 * 128;
+          const uint32_t pa = 128 * 128, pb = (uint32_t)nrow * 128;
+          for (int ks = 0; ks < kpt / kstep; ++ks) {
+            const uint32_t ko = ks * 32;   // 32 bytes of K per instruction
+            const uint32_t acc = first ? 0u : 1u;
+            if (prec == TC_TF32) {
+              const uint64_t ar = make_desc(sa + ko), ai = make_desc(sa + pa + ko);
+              const uint64_t br = make_desc(sb + ko), bi = make_desc(sb + pb + ko);
+              mma(prec, tmem, ar, br, id_pos, acc);
+              mma(prec, tmem, ai, bi, id_neg, 1u);
+              mma(prec, tmem + 256, ar, bi, id_pos, acc);
+              mma(prec, tmem + 256, ai, br, id_pos, 1u);
+            } else {
+              // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+              uint64_t A[4], B[4];
+              for (int q = 0; q < 4; ++q) {
+                A[q] = make_desc(sa + q * pa + ko);
+                B[q] = make_desc(sb + q * pb + ko);
+              }
+              // C_re += Re(A) Re(B) - Im(A) Im(B), each with hi*hi + hi*lo + lo*hi
+              mma(prec, tmem, A[0], B[0], id_pos, acc);
+              mma(prec, tmem, A[0], B[1], id_pos, 1u);
+              mma(prec, tmem, A[1], B[0], id_pos, 1u);
+              mma(prec, tmem, A[2], B[2], id_neg, 1u);
+              mma(prec, tmem, A[2], B[3], id_neg, 1u);
+              mma(prec, tmem, A[3], B[2], id_neg, 1u);
+              // C_im += Re(A) Im(B) + Im(A) Re(B)
+              mma(prec, tmem + 256, A[0], B[2], id_pos, acc);
+              mma(prec, tmem + 256, A[0], B[3], id_pos, 1u);
+              mma(prec, tmem + 256, A[1], B[2], id_pos, 1u);
+              mma(prec, tmem + 256, A[2], B[0], id_pos, 1u);
+              mma(prec, tmem + 256, A[2], B[1], id_pos, 1u);
+              mma(prec, tmem + 256, A[3], B[0], id_pos, 1u);
+            }
+            first = false;
+          }
+          mma_commit(smem_u32(&bar_empty[stage]));
+          if (++stage == kStages) { stage = 0; phase ^= 1; }
+        }
+      }
+      mma_commit(smem_u32(&bar_acc_full));
+      acc_phase ^= 1;
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    const int quad = warp & 3;            // TMEM lanes 32*quad .. 32*quad+31
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+      const int64_t t = find_task(g.prefix, g.n_tasks, item);
+      const int64_t* task = g.tasks + TCT * t;
+      const int64_t M = task[0], N = task[1];
+      const int64_t local = item - g.prefix[t];
+      const int64_t tiles_n = (N + ntile - 1) / ntile;
+      const int64_t rt = local / tiles_n, nt = local % tiles_n;
+      ok = mbar_wait(smem_u32(&bar_acc_full), acc_phase, g.err, 14);
+      acc_phase ^= 1;
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int64_t row = rt * 128 + quad * 32 + lane;
+      const int64_t c0 = nt * ntile;
+      const int64_t ncols = N - c0 < ntile ? N - c0 : ntile;
+      for (int64_t cb = 0; cb < ncols; cb += 16) {
+        uint32_t vr[16], vi[16];
+        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cb;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
+                       "=r"(vr[7]), "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]),
+                       "=r"(vr[14]), "=r"(vr[15])
+                     : "r"(ta));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
+                       "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]),
+                       "=r"(vi[14]), "=r"(vi[15])
+                     : "r"(ta + 256));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (row < M) {
+          for (int j = 0; j < 16; ++j) {
+            const int64_t c = c0 + cb + j;
+            if (c >= N) break;
+            const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
+            if (task[7] == 1) {
+              g.f_out[task[2] + row * task[3] + c] = make_double2((double)re, (double)im);
+            } else {
+              // packed Z: columns below split go to panel task[2], the rest to task[3]
+              const bool second = c >= task[4];
+              const int64_t k = second ? c - task[4] : c;
+              TcPanelGeom geo;
+              geo.nkt = second ? task[9] : task[8];
+              geo.planes = planes;
+              uint8_t* base = g.z_out + (second ? task[3] : task[2]);
+              if (prec == TC_TF32) {
+                put_packed(base, geo, row, k, 0, prec, tf32_rna(re));
+                put_packed(base, geo, row, k, 1, prec, tf32_rna(im));
+              } else {
+                const float rh = __bfloat162float(__float2bfloat16_rn(re));
+                const float ih = __bfloat162float(__float2bfloat16_rn(im));
+                put_packed(base, geo, row, k, 0, prec, rh);
+                put_packed(base, geo, row, k, 1, prec, re - rh);
+                put_packed(base, geo, row, k, 2, prec, ih);
+                put_packed(base, geo, row, k, 3, prec, im - ih);
+              }
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int prec, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  k_pack<<<njobs < 8192 ? njobs : 8192, 256, 0, s>>>(src, dst, jobs, njobs, prec);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
+                    const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
+                    int prec, int* err, int n_sm, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err};
+  const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
+  k_tc_gemm<<<(unsigned)grid, 192, kSmemBytes, s>>>(g);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace mrd

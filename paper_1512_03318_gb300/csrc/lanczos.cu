@@ -298,7 +298,9 @@ cudaError_t lanczos_alloc(Lanczos** out, int64_t n) {
 
 static cudaError_t dots(Lanczos* L, const double2* V, int nv, const double2* w, double2* out, cudaStream_t s) {
   k_multidot<<<kRedBlocks, kRedThreads, 0, s>>>(V, L->n, nv, w, L->n, L->partial);
+  mrd::count_launch();
   k_finish_dots<<<(nv + 63) / 64, 64, 0, s>>>(L->partial, kRedBlocks, nv, out);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 
@@ -318,6 +320,7 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
   // v_0 = theta / |theta|
   MRD_CUDA(ctx, dots(L, theta, 1, theta, L->scal, s));
   k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(theta, L->V, n, L->scal);
+  mrd::count_launch();
   MRD_CUDA(ctx, cudaGetLastError());
   double e_prev = 0.0;
   int k = 0;
@@ -327,14 +330,20 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
     if (rc != MRD_OK) return rc;
     MRD_CUDA(ctx, dots(L, L->V, j + 1, L->w, L->c1, s));
     k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, j + 1, L->c1, L->w, n);
+    mrd::count_launch();
     MRD_CUDA(ctx, dots(L, L->V, j + 1, L->w, L->c2, s));
     k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, j + 1, L->c2, L->w, n);
+    mrd::count_launch();
     k_record_alpha<<<1, 1, 0, s>>>(L->st, j, L->c1, L->c2);
+    mrd::count_launch();
     MRD_CUDA(ctx, dots(L, L->w, 1, L->w, L->scal, s));
     k_record_beta<<<1, 1, 0, s>>>(L->st, j, L->scal);
+    mrd::count_launch();
     k_tridiag_lowest<<<1, 32, 0, s>>>(L->st, j + 1);
+    mrd::count_launch();
     if (j + 1 < max_iter) {
       k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(L->w, L->V + (int64_t)(j + 1) * n, n, L->scal);
+      mrd::count_launch();
     }
     MRD_CUDA(ctx, cudaGetLastError());
     MRD_CUDA(ctx, cudaMemcpyAsync(L->st_host, L->st, sizeof(LzState), cudaMemcpyDeviceToHost, s));
@@ -350,8 +359,10 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
   }
   // ground vector = V y, normalised
   k_combination_real<<<grid_for(n), 256, 0, s>>>(L->V, n, k, L->st->y, L->w, n);
+  mrd::count_launch();
   MRD_CUDA(ctx, dots(L, L->w, 1, L->w, L->scal, s));
   k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(L->w, theta, n, L->scal);
+  mrd::count_launch();
   MRD_CUDA(ctx, cudaGetLastError());
   MRD_CUDA(ctx, cudaStreamSynchronize(s));
   *energy = L->st_host->energy;

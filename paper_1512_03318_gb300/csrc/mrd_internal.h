@@ -25,6 +25,9 @@ __host__ __device__ inline int64_t qkey(int32_t n, int32_t k) {
   return ((int64_t)(n + (1 << 29)) << 32) | (int64_t)(uint32_t)k;
 }
 
+// Number of kernels this library has launched (all devices, all contexts).
+void count_launch();
+
 // A device buffer owned by the library.
 struct DevBuf {
   void* p = nullptr;

@@ -449,6 +449,7 @@ __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
 
 cudaError_t launch_plan(const PlanDims& d, const PlanPtrs& p, cudaStream_t s) {
   k_plan<<<1, 1024, 0, s>>>(d, p);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 

@@ -273,6 +273,7 @@ cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* sr
   if (nblk == 0) return cudaSuccess;
   dim3 grid(64, nblk);
   k_svd_load<<<grid, 256, 0, s>>>(theta, blk, src_off, nblk, work);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 
@@ -281,6 +282,7 @@ cudaError_t svd_round(double2* work, const int64_t* blk, const int64_t* pair_pre
   if (npairs == 0) return cudaSuccess;
   const int64_t threads = npairs * 32;
   k_svd_round<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(work, blk, pair_prefix, nblk, round, tol, rotated);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 
@@ -288,13 +290,16 @@ cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double
                        double* S_sorted, int* order_scratch, cudaStream_t s) {
   if (nblk == 0) return cudaSuccess;
   k_svd_finish<<<nblk, 256, 0, s>>>(work, blk, nblk, U, Vh, S, order_scratch);
+  mrd::count_launch();
   k_svd_sort_values<<<nblk, 256, 0, s>>>(blk, nblk, S, S_sorted);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
                          int* keep, double* info, int* flat_block, cudaStream_t s) {
   k_truncate<<<1, 1024, 0, s>>>(blk, nblk, S_sorted, total, chi, cutoff, keep, info, flat_block);
+  mrd::count_launch();
   return cudaGetLastError();
 }
 

@@ -1,0 +1,29 @@
+// Shared layout constants of the tensor-core H_eff path (heff_tc.cu, tc_host.cu).
+#pragma once
+#include <stdint.h>
+
+namespace mrd {
+
+enum { TC_TF32 = 1, TC_BF16X3 = 2 };
+// task row (int64): M N out0 out1 split seg0 nseg mode nkt_z0 nkt_z1
+//   mode 0: packed Z output, out0/out1 = byte offsets of the Z panels of the two column
+//           parts (columns < split / >= split), nkt_z0/1 their K-tile counts
+//   mode 1: FP64 output, out0 = element offset, out1 = leading dimension
+enum { TCT = 10 };
+// segment row: a_panel_byte_offset b_panel_byte_offset nkt pad
+enum { TCS = 4 };
+// pack job row: src_off ld trans rows K panel_byte_offset rowtile nkt npad
+enum { TCJ = 9 };
+
+struct TcPanelGeom {
+  int64_t nkt;
+  int planes;
+};
+
+__host__ __device__ inline int tc_planes(int prec) { return prec == TC_TF32 ? 2 : 4; }
+__host__ __device__ inline int tc_kpt(int prec) { return prec == TC_TF32 ? 32 : 64; }   // K per 128-byte row
+__host__ __device__ inline int tc_ntile(int prec) { return prec == TC_TF32 ? 256 : 64; } // B rows per tile
+constexpr int kTcStageBytes = 96 * 1024;   // A: planes x 16 KB, B: planes x ntile x 128 B (both precisions)
+constexpr int kTcStages = 2;
+
+}  // namespace mrd

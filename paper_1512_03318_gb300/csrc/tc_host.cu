@@ -1,0 +1,260 @@
+// Host side of the tensor-core H_eff: packed-panel tables (derived on the host from the
+// device-built charge tables of plan.cu), packing of the folded environments and of theta,
+// and the two grouped-GEMM launches.
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "heff_internal.h"
+#include "tc.cuh"
+
+namespace mrd {
+cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int prec, cudaStream_t s);
+cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
+                    const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
+                    int prec, int* err, int n_sm, cudaStream_t s);
+}  // namespace mrd
+
+struct Tc {
+  int prec = 0;
+  bool env_dirty = true;
+  Arena mem;
+  uint8_t *lw = nullptr, *wr = nullptr, *th = nullptr, *z = nullptr;
+  int64_t lw_bytes = 0, wr_bytes = 0, th_bytes = 0, z_bytes = 0;
+  int64_t *t1 = nullptr, *s1 = nullptr, *p1 = nullptr, *t2 = nullptr, *s2 = nullptr, *p2 = nullptr;
+  int64_t n1 = 0, tiles1 = 0, n2 = 0, tiles2 = 0;
+  int64_t *j_lw = nullptr, *j_wr = nullptr, *j_th = nullptr;
+  int n_lw = 0, n_wr = 0, n_th = 0;
+  int* err = nullptr;
+};
+
+void tc_free(Tc* t) { delete t; }
+
+namespace {
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+struct Panel {
+  int64_t off, nkt;
+};
+
+// bytes of an A panel (128-row tiles) or a B panel (ntile-row tiles, rows padded to 16)
+int64_t a_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 128) * nkt * planes * 128; }
+int64_t b_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 16) * nkt * planes * 128; }
+
+int build(mrd_heff* h, int prec) {
+  mrd_ctx* ctx = h->ctx;
+  Tc* T = h->tc;
+  const int planes = tc_planes(prec), kpt = tc_kpt(prec), ntile = tc_ntile(prec);
+  const int64_t* c = h->counts;
+  std::map<int64_t, Panel> lw_map, wr_map, th_map, z_map;
+  std::vector<int64_t> j_lw, j_wr, j_th;
+  int64_t lw_b = 0, wr_b = 0, th_b = 0, z_b = 0;
+  // folded left operand LW(w', s1', s1, a): A panel, rows d_a', K d_a
+  for (int64_t k = 0; k < c[C_NLW]; ++k) {
+    const int64_t* r = &h->lw_host[LWF * k];
+    const int64_t rows = r[5], K = r[6], nkt = (K + kpt - 1) / kpt;
+    lw_map[r[7]] = {lw_b, nkt};
+    j_lw.insert(j_lw.end(), {r[7], K, 0, rows, K, lw_b, 128, nkt, round_up(rows, 128)});
+    lw_b += a_bytes(rows, nkt, planes);
+  }
+  // folded right operand WR(w', s2, s2', b): B panel of its transpose, rows d_b', K d_b
+  for (int64_t k = 0; k < c[C_NWR]; ++k) {
+    const int64_t* r = &h->wr_host[WRF * k];
+    const int64_t K = r[5], rows = r[6], nkt = (K + kpt - 1) / kpt;
+    wr_map[r[7]] = {wr_b, nkt};
+    j_wr.insert(j_wr.end(), {r[7], rows, 1, rows, K, wr_b, ntile, nkt, round_up(rows, 16)});
+    wr_b += b_bytes(rows, nkt, planes);
+  }
+  // theta rows (s1, a) of every middle sector: B panel of the transpose, rows coldim, K d_a
+  const std::vector<int64_t>& mid = h->mid_host;
+  for (int64_t m = 0; m < c[C_NMID]; ++m) {
+    const int64_t* r = &mid[MIDF * m];
+    for (int s1 = 0; s1 < 2; ++s1) {
+      if (r[5 + s1] < 0) continue;
+      const int64_t K = h->left[3 * r[5 + s1] + 2], rows = r[3], nkt = (K + kpt - 1) / kpt;
+      const int64_t src = r[4] + (s1 ? r[7] : 0) * r[3];
+      th_map[src] = {th_b, nkt};
+      j_th.insert(j_th.end(), {src, rows, 1, rows, K, th_b, ntile, nkt, round_up(rows, 16)});
+      th_b += b_bytes(rows, nkt, planes);
+    }
+  }
+  // Z(w', m_in) rows (s1') x columns (s2): A panels keyed by their FP64 element offset
+  std::vector<int64_t> z(ZF * c[C_NZ]);
+  if (c[C_NZ]) {
+    cudaError_t e = cudaMemcpy(z.data(), h->p.z, z.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: table download");
+  }
+  const int64_t nmid = c[C_NMID];
+  for (int64_t k = 0; k < c[C_NZ]; ++k) {
+    const int64_t* zr = &z[ZF * k];
+    const int64_t wp = zr[0], mi = zr[1], mo = zr[2];
+    const int64_t* rin = &mid[MIDF * mi];
+    const int64_t* rout = &mid[MIDF * mo];
+    for (int s1p = 0; s1p < 2; ++s1p) {
+      const int64_t ti = (wp * nmid + mi) * 2 + s1p;
+      if (h->t1_host[TF * ti + 5] == 0) continue;   // no rows of this part written
+      const int64_t rows = h->left[3 * rout[5 + s1p] + 2];
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (rin[8 + s2] < 0) continue;
+        const int64_t K = h->right[3 * rin[8 + s2] + 2], nkt = (K + kpt - 1) / kpt;
+        const int64_t key = zr[5] + (s1p ? rout[7] : 0) * rin[3] + (s2 ? rin[10] : 0);
+        z_map[key] = {z_b, nkt};
+        z_b += a_bytes(rows, nkt, planes);
+      }
+    }
+  }
+  // step-1 tasks (Z = LW theta)
+  std::vector<int64_t> t1, s1, p1{0}, t2, s2, p2{0};
+  for (int64_t i = 0; i < c[C_NT1]; ++i) {
+    const int64_t* t = &h->t1_host[TF * i];
+    if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
+    const int64_t wp = i / 2 / nmid, mi = (i / 2) % nmid;
+    (void)wp;
+    const int64_t* rin = &mid[MIDF * mi];
+    const int64_t seg0 = (int64_t)s1.size() / TCS;
+    for (int64_t k = 0; k < t[5]; ++k) {
+      const int64_t* sg = &h->s1_host[SF * (t[4] + k)];
+      auto a = lw_map.find(sg[0]);
+      auto b = th_map.find(sg[2]);
+      if (a == lw_map.end() || b == th_map.end() || a->second.nkt != b->second.nkt)
+        return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
+      s1.insert(s1.end(), {a->second.off, b->second.off, a->second.nkt, 0});
+    }
+    const int64_t split = rin[8] >= 0 ? rin[10] : 0;
+    int64_t z0 = 0, z1 = 0, k0 = 0, k1 = 0;
+    if (rin[8] >= 0) {
+      auto q = z_map.find(t[2]);
+      if (q == z_map.end()) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
+      z0 = q->second.off; k0 = q->second.nkt;
+    }
+    if (rin[9] >= 0) {
+      auto q = z_map.find(t[2] + rin[10]);
+      if (q == z_map.end()) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
+      z1 = q->second.off; k1 = q->second.nkt;
+    }
+    t1.insert(t1.end(), {t[0], t[1], z0, z1, split, seg0, t[5], 0, k0, k1});
+    p1.push_back(p1.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
+  }
+  // step-2 tasks (theta' = sum Z WR)
+  for (int64_t i = 0; i < c[C_NT2]; ++i) {
+    const int64_t* t = &h->t2_host[TF * i];
+    if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
+    const int64_t seg0 = (int64_t)s2.size() / TCS;
+    for (int64_t k = 0; k < t[5]; ++k) {
+      const int64_t* sg = &h->s2_host[SF * (t[4] + k)];
+      auto a = z_map.find(sg[0]);
+      auto b = wr_map.find(sg[2]);
+      if (a == z_map.end() || b == wr_map.end() || a->second.nkt != b->second.nkt)
+        return mrd_fail(ctx, MRD_E_STATE, "tc: step-2 operand not packed");
+      s2.insert(s2.end(), {a->second.off, b->second.off, a->second.nkt, 0});
+    }
+    t2.insert(t2.end(), {t[0], t[1], t[2], t[3], 0, seg0, t[5], 1, 0, 0});
+    p2.push_back(p2.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
+  }
+  // every tile the kernel reads or writes must lie inside its buffer
+  {
+    auto chk = [&](const std::vector<int64_t>& tk, const std::vector<int64_t>& sg, int64_t alen, int64_t blen,
+                   bool zout) {
+      for (size_t i = 0; i < tk.size(); i += TCT) {
+        const int64_t M = tk[i], N = tk[i + 1];
+        for (int64_t k = 0; k < tk[i + 6]; ++k) {
+          const int64_t* q = &sg[TCS * (tk[i + 5] + k)];
+          if (q[0] < 0 || q[0] + a_bytes(M, q[2], planes) > alen) return false;
+          if (q[1] < 0 || q[1] + b_bytes(N, q[2], planes) > blen) return false;
+        }
+        if (zout) {
+          const int64_t split = tk[i + 4];
+          if (split > 0 && tk[i + 2] + a_bytes(M, tk[i + 8], planes) > z_b) return false;
+          if (N > split && tk[i + 3] + a_bytes(M, tk[i + 9], planes) > z_b) return false;
+          if (split > 0 && (tk[i + 8] + 0) * kpt < split) return false;
+          if (N > split && tk[i + 9] * kpt < N - split) return false;
+        }
+      }
+      return true;
+    };
+    if (!chk(t1, s1, lw_b, th_b, true) || !chk(t2, s2, z_b, wr_b, false))
+      return mrd_fail(ctx, MRD_E_STATE, "tc: internal panel table check failed");
+    if (planes * 128 * 128 + planes * ntile * 128 > kTcStageBytes)
+      return mrd_fail(ctx, MRD_E_STATE, "tc: stage does not fit");
+  }
+  // device buffers
+  delete h->tc;
+  h->tc = T = new Tc();
+  T->prec = prec;
+  Arena& A = T->mem;
+  cudaError_t e = cudaSuccess;
+#define TALLOC(ptr, n) if (e == cudaSuccess) e = A.alloc(&(ptr), (size_t)std::max<int64_t>((n), 1))
+  TALLOC(T->lw, lw_b); TALLOC(T->wr, wr_b); TALLOC(T->th, th_b); TALLOC(T->z, z_b);
+  TALLOC(T->t1, t1.size()); TALLOC(T->s1, s1.size()); TALLOC(T->p1, p1.size());
+  TALLOC(T->t2, t2.size()); TALLOC(T->s2, s2.size()); TALLOC(T->p2, p2.size());
+  TALLOC(T->j_lw, j_lw.size()); TALLOC(T->j_wr, j_wr.size()); TALLOC(T->j_th, j_th.size());
+  TALLOC(T->err, 1);
+#undef TALLOC
+  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: device buffers");
+  T->lw_bytes = lw_b; T->wr_bytes = wr_b; T->th_bytes = th_b; T->z_bytes = z_b;
+  T->n1 = (int64_t)t1.size() / TCT; T->tiles1 = p1.back();
+  T->n2 = (int64_t)t2.size() / TCT; T->tiles2 = p2.back();
+  T->n_lw = (int)(j_lw.size() / TCJ); T->n_wr = (int)(j_wr.size() / TCJ); T->n_th = (int)(j_th.size() / TCJ);
+  cudaStream_t s = ctx->stream;
+  auto up = [&](int64_t* d, const std::vector<int64_t>& v) {
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpyAsync(d, v.data(), v.size() * 8, cudaMemcpyHostToDevice, s);
+  };
+  up(T->t1, t1); up(T->s1, s1); up(T->p1, p1); up(T->t2, t2); up(T->s2, s2); up(T->p2, p2);
+  up(T->j_lw, j_lw); up(T->j_wr, j_wr); up(T->j_th, j_th);
+  // zero padding everywhere (packing and the Z epilogue only write valid elements)
+  for (auto pr : {std::make_pair(T->lw, lw_b), std::make_pair(T->wr, wr_b), std::make_pair(T->th, th_b),
+                  std::make_pair(T->z, z_b)})
+    if (e == cudaSuccess && pr.second) e = cudaMemsetAsync(pr.first, 0, (size_t)pr.second, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(T->err, 0, 4, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors leave scope
+  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: upload");
+  return MRD_OK;
+}
+
+}  // namespace
+
+void tc_env_changed(mrd_heff* h) {
+  if (h->tc) h->tc->env_dirty = true;
+}
+
+int tc_status(mrd_heff* h) {
+  if (!h->tc) return MRD_OK;
+  int herr = 0;
+  MRD_CUDA(h->ctx, cudaMemcpyAsync(&herr, h->tc->err, 4, cudaMemcpyDeviceToHost, h->ctx->stream));
+  MRD_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  if (herr) return mrd_fail(h->ctx, MRD_E_TIMEOUT, "tensor-core GEMM: a bounded wait gave up (code " +
+                                                       std::to_string(herr) + ")");
+  return MRD_OK;
+}
+
+int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
+  mrd_ctx* ctx = h->ctx;
+  const int tp = prec == MRD_PREC_TF32 ? TC_TF32 : TC_BF16X3;
+  int rc;
+  if (!h->tc || h->tc->prec != tp) {
+    if (!h->tc) h->tc = new Tc();
+    if ((rc = build(h, tp)) != MRD_OK) return rc;
+  }
+  Tc* T = h->tc;
+  cudaStream_t s = ctx->stream;
+  if (T->env_dirty) {
+    MRD_CUDA(ctx, tc_pack(h->lw, T->lw, T->j_lw, T->n_lw, tp, s));
+    MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, tp, s));
+    T->env_dirty = false;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (h->timing) {
+    e0 = take_event(h); e1 = take_event(h); e2 = take_event(h);
+    if (!e0 || !e1 || !e2) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
+  }
+  MRD_CUDA(ctx, cudaMemsetAsync(out, 0, (size_t)h->counts[C_THETA] * 16, s));
+  MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, tp, s));
+  if (e0) MRD_CUDA(ctx, cudaEventRecord(e0, s));
+  MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->tiles1, T->z, nullptr, tp, T->err, h->n_sm, s));
+  if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
+  MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->tiles2, nullptr, (double2*)out, tp, T->err,
+                        h->n_sm, s));
+  if (e2) MRD_CUDA(ctx, cudaEventRecord(e2, s));
+  return MRD_OK;
+}

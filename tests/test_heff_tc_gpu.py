@@ -1,0 +1,84 @@
+"""Tensor-core H_eff (tcgen05, TF32 and split BF16) against the FP64 oracle on the same
+seeded inputs. Reduced precision has no closed form: the bounds below are those of the
+arithmetic (TF32 keeps 11 significant bits, the BF16 pair hi + lo about 16, FP32
+accumulation) with margin; the FP64 path of the library is checked to 1e-12 elsewhere."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import blocksparse as B  # noqa: E402
+from tests import gpu_cases as G  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# relative to max |theta'|. Each operand of the chain (theta, Z, WR) carries a rounding of
+# 2^-11 (TF32) or about 2^-18 (BF16 hi + lo); sums over thousands of terms with partial
+# cancellation amplify it relative to the largest output entry.
+TOL = {1: 2e-3, 2: 5e-5}           # small random blocks
+TOL_MODEL = {1: 1e-2, 2: 2e-4}     # Ly = 10, chi = 3200 model MPO (K up to ~10^4)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1512_03318_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return P.Context(0, torch.cuda.current_stream())
+
+
+CASES = [
+    (1, 4, 40, 44, 1, 2, 5, 6, 7),
+    (7, 6, 150, 170, 5, 3, 4, 8, 6),
+    (21, 2, 300, 280, 1, 0, 4, 4, 4),
+    (35, 1, 600, 500, 0, 0, 4, 4, 4),
+]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("seed,ly,chi_l,chi_r,m1,m2,dl,dm,dr", CASES)
+def test_tc_heff_matches_oracle(ctx, prec, seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr):
+    import paper_1512_03318_gb300 as P
+    case = G.random_case(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr)
+    ref = B.heff_apply(case["left"], case["right"], case["m1"], case["m2"], case["mod"], case["cl"], case["cm"],
+                       case["cr"], case["wi"], case["wj"], case["lflat"], case["rflat"], case["tflat"])
+    h = P.Heff(ctx, **G.heff_args(case))
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    h.set_env(dev(case["lflat"]), dev(case["rflat"]))
+    T = dev(case["tflat"])
+    out = torch.empty_like(T)
+    for _ in range(2):                       # second call reuses the packed environments
+        h.apply(T, out, prec=prec)
+        got = out.cpu().numpy()
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err < TOL[prec], err
+    # packed environments follow a new set_env
+    h.set_env(dev(2 * case["lflat"]), dev(case["rflat"]))
+    h.apply(T, out, prec=prec)
+    err = np.max(np.abs(out.cpu().numpy() - 2 * ref)) / np.max(np.abs(2 * ref))
+    assert err < TOL[prec], err
+
+
+def test_tc_model_mpo_sampled_blocks(ctx):
+    """Ly = 10, chi = 3200 model MPO: sampled output blocks, BF16X3 and TF32."""
+    import synth
+    import paper_1512_03318_gb300 as P
+    from tests.test_heff_gpu import _model_case
+    case = _model_case(10, 3200, 1237, 20)
+    h = P.Heff(ctx, **G.heff_args(case))
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    h.set_env(dev(case["lflat"]), dev(case["rflat"]))
+    T = dev(case["tflat"])
+    out64, out = torch.empty_like(T), torch.empty_like(T)
+    h.apply(T, out64, prec=0)
+    for prec in (2, 1):
+        h.apply(T, out, prec=prec)
+        err = (out - out64).abs().max().item() / out64.abs().max().item()
+        assert err < TOL_MODEL[prec], (prec, err)
+    lay = case["lay"]
+    blocks = B.theta_blocks(out64.cpu().numpy(), lay)
+    keys = sorted(blocks)
+    key = keys[int(synth.splitmix64(5, 1)[0] % np.uint64(len(keys)))]
+    ref = B.heff_apply_block(case["left"], case["right"], case["m1"], case["m2"], case["mod"], case["cl"], case["cm"],
+                             case["cr"], case["wi"], case["wj"], case["lflat"], case["rflat"], case["tflat"], key)
+    assert np.max(np.abs(blocks[key] - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
