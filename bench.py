@@ -257,7 +257,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chi", type=int, default=CHI)
-    ap.add_argument("--refine", type=int, default=6, help="FP64 refinement matvecs of the mixed form")
+    ap.add_argument("--refine", type=int, default=1, help="FP64 refinement matvecs of the mixed form")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fast-restarts", type=int, default=8, help="restarts of the reduced-precision Lanczos")
     ap.add_argument("--only-matvec", action="store_true", help="H_eff throughput only (profiling runs)")

@@ -29,14 +29,18 @@ cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, co
                               const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
                               int n_sm, cudaStream_t s);
 cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* src_off, int nblk, double2* work,
-                     cudaStream_t s);
+                     double* fro2, cudaStream_t s);
 cudaError_t svd_round(double2* work, const int64_t* blk, const int64_t* pair_prefix, int nblk, int64_t npairs,
-                      int round, double tol, int* rotated, cudaStream_t s);
+                      int round, double tol, const double* fro2, int* rotated, cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
-                       double* S_sorted, int* order_scratch, cudaStream_t s);
+                       double* S_sorted, int* order_scratch, const double* fro2, cudaStream_t s);
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
                          int* keep, double* info, int* flat_block, cudaStream_t s);
-enum { SVF = 10 };
+cudaError_t svd_round32(float2* w32, const int64_t* blk, const int64_t* pair_prefix, int nblk, int64_t npairs,
+                        int round, float tol, const double* fro2, int* rotated, cudaStream_t s);
+cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
+cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
+enum { SVF = 12 };
 
 namespace {
 
@@ -118,6 +122,15 @@ __global__ void k_copy_blocks(const double2* __restrict__ src, double2* __restri
       }
       dst[d[2] + r * d[3] + c] = v;
     }
+  }
+}
+
+// x *= g (g read from device memory)
+__global__ void k_scale(double2* __restrict__ x, int64_t n, const double* __restrict__ g) {
+  const double f = *g;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    x[e].x *= f;
+    x[e].y *= f;
   }
 }
 
@@ -226,7 +239,8 @@ struct mrd_dmrg {
   std::vector<SiteT> A;
   std::vector<EnvT> L, R;
   Buf gtask, gseg, gpref, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
-      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, tbuf, zeros;
+      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, tbuf, zeros;
+  int svd_sweeps32 = 0, svd_sweeps64 = 0;
   double last_energy = 0.0, last_trunc = 0.0;
   int last_iters = 0, last_refine = 0;
   bool timing = false;
@@ -369,7 +383,7 @@ int form_theta(mrd_dmrg* D, mrd_heff* h, const SiteT& X, const SiteT& Y, double2
 
 // Block SVD of the blocks `blk` (SVF rows) of `src`; returns kept counts per block and info.
 int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>& src_off, const double2* src,
-              int chi, double cutoff, std::vector<int>& keep, double info[3]) {
+              int side, int chi, double cutoff, std::vector<int>& keep, double info[3]) {
   mrd_ctx* ctx = D->ctx;
   cudaStream_t s = ctx->stream;
   const int nb = (int)src_off.size();
@@ -380,7 +394,7 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   for (int b = 0; b < nb; ++b) {
     int64_t* d = &blk[SVF * b];
     const int64_t m = d[0], n = d[1];
-    const bool wide = m < n;
+    const bool wide = side == 1;   // X = M^+ (orthonormal V) instead of X = M (orthonormal U)
     const int64_t p = wide ? n : m, r = wide ? m : n;
     d[2] = p; d[3] = r; d[9] = wide;
     d[4] = work; work += p * r;
@@ -391,15 +405,25 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     maxrr = std::max(maxrr, rr);
     pp[b + 1] = pp[b] + rr / 2;
   }
+  int64_t xlen = work;
   for (int b = 0; b < nb; ++b) {   // V_X of every block after all X blocks
     blk[SVF * b + 5] = work;
     work += blk[SVF * b + 3] * blk[SVF * b + 3];
+  }
+  int64_t w32 = 0;                 // FP32 copies: X32 then V32 per block
+  for (int b = 0; b < nb; ++b) {
+    blk[SVF * b + 10] = w32;
+    w32 += blk[SVF * b + 2] * blk[SVF * b + 3];
+    blk[SVF * b + 11] = w32;
+    w32 += blk[SVF * b + 3] * blk[SVF * b + 3];
   }
   npairs = pp[nb];
   MRD_CUDA(ctx, D->svd_blk.need(blk.size() * 8));
   MRD_CUDA(ctx, D->svd_src.need(src_off.size() * 8));
   MRD_CUDA(ctx, D->svd_pref.need(pp.size() * 8));
   MRD_CUDA(ctx, D->svd_work.need((size_t)work * 16));
+  MRD_CUDA(ctx, D->svd_w32.need((size_t)std::max<int64_t>(w32, 1) * 8));
+  MRD_CUDA(ctx, D->svd_x2.need((size_t)std::max<int64_t>(xlen, 1) * 16));
   MRD_CUDA(ctx, D->svd_u.need((size_t)ulen * 16));
   MRD_CUDA(ctx, D->svd_vh.need((size_t)vlen * 16));
   MRD_CUDA(ctx, D->svd_s.need((size_t)slen * 8));
@@ -409,24 +433,57 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   MRD_CUDA(ctx, D->svd_keep.need((size_t)nb * 4));
   MRD_CUDA(ctx, D->svd_info.need(4 * 8));
   MRD_CUDA(ctx, D->svd_rot.need(8));
+  MRD_CUDA(ctx, D->svd_fro.need((size_t)nb * 8));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_blk.p, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice, s));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_src.p, src_off.data(), src_off.size() * 8, cudaMemcpyHostToDevice, s));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_pref.p, pp.data(), pp.size() * 8, cudaMemcpyHostToDevice, s));
   const int64_t* dblk = D->svd_blk.as<int64_t>();
-  MRD_CUDA(ctx, svd_load(src, dblk, D->svd_src.as<int64_t>(), nb, D->svd_work.as<double2>(), s));
+  const double* fro = D->svd_fro.as<double>();
+  MRD_CUDA(ctx, svd_load(src, dblk, D->svd_src.as<int64_t>(), nb, D->svd_work.as<double2>(), D->svd_fro.as<double>(), s));
   int* rot = D->svd_rot.as<int>();
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
-    for (int rd = 0; rd + 1 < maxrr; ++rd)
-      MRD_CUDA(ctx, svd_round(D->svd_work.as<double2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-15, rot, s));
-    int hrot = 0;
-    MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
-    MRD_CUDA(ctx, cudaStreamSynchronize(s));
-    if (hrot == 0) break;
-    if (sweep == 39) return mrd_fail(ctx, MRD_E_NOCONV, "block SVD: Jacobi sweeps did not converge");
+  auto sweep_until_done = [&](bool f32, int max_sweeps, int* used) -> int {
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
+      for (int rd = 0; rd + 1 < maxrr; ++rd) {
+        if (f32)
+          MRD_CUDA(ctx, svd_round32(D->svd_w32.as<float2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-6f,
+                                    fro, rot, s));
+        else
+          MRD_CUDA(ctx, svd_round(D->svd_work.as<double2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-15,
+                                  fro, rot, s));
+      }
+      int hrot = 0;
+      MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
+      MRD_CUDA(ctx, cudaStreamSynchronize(s));
+      *used = sweep + 1;
+      if (hrot == 0) return MRD_OK;
+    }
+    return f32 ? MRD_OK : mrd_fail(ctx, MRD_E_NOCONV, "block SVD: Jacobi sweeps did not converge");
+  };
+  // FP32 pre-sweeps orthogonalise the columns to ~1e-6; their rotations V32 are applied to the
+  // FP64 matrix (X <- X V32, one grouped GEMM) and FP64 sweeps finish the job.
+  MRD_CUDA(ctx, svd_to_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
+  int rc = sweep_until_done(true, 30, &D->svd_sweeps32);
+  if (rc != MRD_OK) return rc;
+  MRD_CUDA(ctx, svd_v_from_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
+  {
+    GemmList g;
+    for (int b = 0; b < nb; ++b) {   // X_new^T (r x p) = V^T (r x r) X^T (r x p), all column-major buffers
+      const int64_t* d = &blk[SVF * b];
+      const int64_t p = d[2], r = d[3];
+      if (p == 0 || r == 0) continue;
+      g.task(r, p, d[4], p);
+      g.seg(d[5], r, d[4], p, r, 0);
+    }
+    rc = run_gemm(D, g, D->svd_work.as<double2>(), work, D->svd_work.as<double2>(), work, D->svd_x2.as<double2>(),
+                  xlen);
+    if (rc != MRD_OK) return rc;
+    MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_work.p, D->svd_x2.p, (size_t)xlen * 16, cudaMemcpyDeviceToDevice, s));
   }
+  rc = sweep_until_done(false, 40, &D->svd_sweeps64);
+  if (rc != MRD_OK) return rc;
   MRD_CUDA(ctx, svd_finish(D->svd_work.as<double2>(), dblk, nb, D->svd_u.as<double2>(), D->svd_vh.as<double2>(),
-                           D->svd_s.as<double>(), D->svd_ss.as<double>(), D->svd_ord.as<int>(), s));
+                           D->svd_s.as<double>(), D->svd_ss.as<double>(), D->svd_ord.as<int>(), fro, s));
   MRD_CUDA(ctx, svd_truncate(dblk, nb, D->svd_ss.as<double>(), slen, chi, cutoff, D->svd_keep.as<int>(),
                              D->svd_info.as<double>(), D->svd_flat.as<int>(), s));
   MRD_CUDA(ctx, cudaMemcpyAsync(keep.data(), D->svd_keep.p, nb * 4, cudaMemcpyDeviceToHost, s));
@@ -615,7 +672,7 @@ int orthonormalise(mrd_dmrg* D, SiteT& T) {
   }
   std::vector<int> keep;
   double info[3];
-  int rc = block_svd(D, blk, src, T.data.as<double2>(), 1 << 30, 0.0, keep, info);
+  int rc = block_svd(D, blk, src, T.data.as<double2>(), T.mode == 1 ? 1 : 0, 1 << 30, 0.0, keep, info);
   if (rc != MRD_OK) return rc;
   std::vector<int64_t> cp;
   for (size_t b = 0; b < gi.size(); ++b) {
@@ -868,7 +925,8 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   }
   std::vector<int> keep;
   double info[3];
-  if ((rc = block_svd(D, blk, src, theta, p->chi, p->svd_cutoff, keep, info)) != MRD_OK) return rc;
+  const int side = direction > 0 ? 0 : 1;   // the factor that stays in canonical form
+  if ((rc = block_svd(D, blk, src, theta, side, p->chi, p->svd_cutoff, keep, info)) != MRD_OK) return rc;
   lap(3);
   // new bond i+1
   Secs nb;
@@ -884,22 +942,43 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   Y.left = nb; Y.mode = 1; Y.layout();
   MRD_CUDA(ctx, X.data.need((size_t)std::max<int64_t>(X.size, 1) * 16));
   MRD_CUDA(ctx, Y.data.need((size_t)std::max<int64_t>(Y.size, 1) * 16));
-  std::vector<int64_t> cx, cy;
+  // canonical factor: copy of the orthonormal singular vectors; the other factor: exact
+  // projection of theta (U^+ theta moving right, theta V moving left), then renormalised
+  std::vector<int64_t> cp;
+  GemmList proj;
   int nbi = 0;
   for (size_t b = 0; b < mids.size(); ++b) {
     if (keep[b] == 0) continue;
     const int64_t* d = &blk[SVF * b];
     const int64_t m = d[0], ncol = d[1], r = d[3], k = keep[b];
-    // X group nbi: rows (s1, a) of the middle sector, k columns = U[:, :k] (times S when moving left)
-    cx.insert(cx.end(), {d[6], r, X.goff[nbi], k, m, k, direction < 0 ? 1 : 0, d[8]});
-    // Y group nbi: k rows = Vh[:k, :] (times S when moving right)
-    cy.insert(cy.end(), {d[7], ncol, Y.goff[nbi], Y.gext[nbi], k, ncol, direction > 0 ? 2 : 0, d[8]});
+    if (direction > 0) {
+      cp.insert(cp.end(), {d[6], r, X.goff[nbi], k, m, k, 0, 0});                 // A_i = U[:, :k]
+      proj.task(k, ncol, Y.goff[nbi], Y.gext[nbi]);                                  // M_{i+1} = U_k^+ theta_q
+      proj.seg(d[6], r, src[b], ncol, m, 1);
+    } else {
+      cp.insert(cp.end(), {d[7], ncol, Y.goff[nbi], Y.gext[nbi], k, ncol, 0, 0}); // B_{i+1} = V^+[:k, :]
+      proj.task(m, k, X.goff[nbi], k);                                               // M_i = theta_q V_k
+      proj.seg(src[b], ncol, d[7], ncol, ncol, 2);
+    }
     ++nbi;
   }
-  const double* S = D->svd_ss.as<double>();
-  const double* sscale = D->svd_info.as<double>();
-  if ((rc = run_copies(D, cx, D->svd_u.as<double2>(), X.data.as<double2>(), S, sscale)) != MRD_OK) return rc;
-  if ((rc = run_copies(D, cy, D->svd_vh.as<double2>(), Y.data.as<double2>(), S, sscale)) != MRD_OK) return rc;
+  SiteT& canon = direction > 0 ? X : Y;
+  SiteT& centre = direction > 0 ? Y : X;
+  if ((rc = run_copies(D, cp, direction > 0 ? D->svd_u.as<double2>() : D->svd_vh.as<double2>(),
+                       canon.data.as<double2>(), nullptr, nullptr)) != MRD_OK)
+    return rc;
+  const int64_t svd_ulen = D->svd_u.bytes / 16, svd_vlen = D->svd_vh.bytes / 16;
+  if (direction > 0)
+    rc = run_gemm(D, proj, D->svd_u.as<double2>(), svd_ulen, theta, n, centre.data.as<double2>(), centre.size);
+  else
+    rc = run_gemm(D, proj, theta, n, D->svd_vh.as<double2>(), svd_vlen, centre.data.as<double2>(), centre.size);
+  if (rc != MRD_OK) return rc;
+  if (centre.size > 0) {
+    k_scale<<<(unsigned)std::min<int64_t>((centre.size + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        centre.data.as<double2>(), centre.size, D->svd_info.as<double>());
+    mrd::count_launch();
+    MRD_CUDA(ctx, cudaGetLastError());
+  }
   lap(4);
   if (direction > 0) rc = env_left(D, h, i);
   else rc = env_right(D, h, i);
