@@ -324,6 +324,7 @@ def main():
     st.timing(True)
     barrier()
     phases = np.zeros(6)
+    sweeps = np.zeros(2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = P.launch_count()
     t_wall = time.perf_counter()
@@ -332,6 +333,7 @@ def main():
         for k in range(args.steps):
             st.update(centre + args.warmup + k, +1, mixed)
             phases += np.array(st.phase_ms())
+            sweeps += np.array(st.svd_sweeps())
         e1.record(stream)
         torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall
@@ -432,6 +434,7 @@ def main():
         "discarded_weight_last": trunc,
         "phase_ms_mean": dict(zip(["tables", "theta", "lanczos+refine", "svd", "tensors", "env"],
                                   (phases / args.steps).round(2).tolist())),
+        "svd_jacobi_rounds_mean": dict(zip(["fp32", "fp64"], (sweeps / args.steps).round(1).tolist())),
         "gemm_ms_per_step": {"tc": tc_ms / args.steps, "fp64": f64_ms / args.steps},
         "heff_tflops": {k: round(mv[k]["tflops"], 3) for k in PREC},
         "heff_ms": {k: round(mv[k]["ms"], 4) for k in PREC},

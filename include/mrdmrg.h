@@ -227,8 +227,9 @@ int mrd_dmrg_set_site(mrd_dmrg* d, int32_t site, const double* host);
 int mrd_dmrg_timing(mrd_dmrg* d, int32_t on, double* kernel_ms4, int64_t* applies2);
 /* Wall time in ms of the phases of the last two-site update (each ends with a stream
  * synchronisation): [0] H_eff tables and environment fold, [1] theta, [2] Lanczos,
- * [3] block SVD and truncation, [4] new MPS tensors, [5] environment update. */
-int mrd_dmrg_phase_ms(const mrd_dmrg* d, double* ms6);
+ * [3] block SVD and truncation, [4] new MPS tensors, [5] environment update; then [6] the
+ * FP32 and [7] the FP64 Jacobi sweeps of its block SVD. */
+int mrd_dmrg_phase_ms(const mrd_dmrg* d, double* ms8);
 /* Energy, discarded weight and matvec count of the last two-site update; the count is the
  * reduced-precision (or FP64) Lanczos matvecs plus 1000 times the FP64 refinement matvecs. */
 int mrd_dmrg_stats(const mrd_dmrg* d, double* energy, double* trunc_err, int32_t* lanczos_iters);

@@ -329,9 +329,15 @@ class DMRG:
         return list(ms), list(n)
 
     def phase_ms(self):
-        f = (C.c_double * 6)()
+        """[tables, theta, lanczos, svd, tensors, env] ms of the last update."""
+        f = (C.c_double * 8)()
         self.ctx.check(lib().mrd_dmrg_phase_ms(self.h, f))
-        return list(f)
+        return list(f)[:6]
+
+    def svd_sweeps(self):
+        f = (C.c_double * 8)()
+        self.ctx.check(lib().mrd_dmrg_phase_ms(self.h, f))
+        return int(f[6]), int(f[7])
 
     def stats(self):
         e, t, it = C.c_double(), C.c_double(), C.c_int32()

@@ -446,10 +446,10 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
       MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
       for (int rd = 0; rd + 1 < maxrr; ++rd) {
         if (f32)
-          MRD_CUDA(ctx, svd_round32(D->svd_w32.as<float2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-6f,
+          MRD_CUDA(ctx, svd_round32(D->svd_w32.as<float2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-5f,
                                     fro, rot, s));
         else
-          MRD_CUDA(ctx, svd_round(D->svd_work.as<double2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-15,
+          MRD_CUDA(ctx, svd_round(D->svd_work.as<double2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-14,
                                   fro, rot, s));
       }
       int hrot = 0;
@@ -460,7 +460,8 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     }
     return f32 ? MRD_OK : mrd_fail(ctx, MRD_E_NOCONV, "block SVD: Jacobi sweeps did not converge");
   };
-  // FP32 pre-sweeps orthogonalise the columns to ~1e-6; their rotations V32 are applied to the
+  // FP32 pre-sweeps orthogonalise the columns to ~1e-5 (the resolution of FP32 dot products of
+  // a few hundred terms); their rotations V32 are applied to the
   // FP64 matrix (X <- X V32, one grouped GEMM) and FP64 sweeps finish the job.
   MRD_CUDA(ctx, svd_to_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
   int rc = sweep_until_done(true, 30, &D->svd_sweeps32);
@@ -1061,9 +1062,11 @@ int mrd_dmrg_set_site(mrd_dmrg* D, int32_t site, const double* host) {
   return MRD_OK;
 }
 
-int mrd_dmrg_phase_ms(const mrd_dmrg* D, double* ms6) {
-  if (!D || !ms6) return MRD_E_ARG;
-  for (int k = 0; k < 6; ++k) ms6[k] = D->phase_ms[k];
+int mrd_dmrg_phase_ms(const mrd_dmrg* D, double* ms8) {
+  if (!D || !ms8) return MRD_E_ARG;
+  for (int k = 0; k < 6; ++k) ms8[k] = D->phase_ms[k];
+  ms8[6] = D->svd_sweeps32;
+  ms8[7] = D->svd_sweeps64;
   return MRD_OK;
 }
 

@@ -13,12 +13,13 @@
 // Operands live in HBM as "panels" of UMMA-ready tiles: a tile is R rows x 128 bytes of K
 // (32 TF32 or 64 BF16 values), K-major, 128-byte swizzled, zero padded, with its planes
 // stored back to back, so one cp.async.bulk moves a tile into shared memory unchanged.
-// A panels have 128-row tiles; B panels hold all N rows (padded to 16, at most 256 per tile).
+// A panels have 128-row tiles; B panels hold all N rows (padded to 16), 128 (TF32) or 64
+// (BF16) rows per tile.
 // LW and WR are packed once per environment load, theta once per matvec, and the step-1
 // epilogue writes Z directly in the packed A format of step 2.
 //
 // Kernel: persistent, one CTA per SM, 6 warps: warp 0 issues the bulk copies, warp 1 owns
-// TMEM (512 columns: C_re at 0, C_im at 256) and issues the MMAs from one thread, warps 2-5
+// TMEM (512 columns: two accumulator slots of C_re, C_im) and issues the MMAs from one thread, warps 2-5
 // drain the accumulators (warp w reads TMEM lanes 32 (w % 4) ..). Shared-memory stages are
 // handed over with mbarriers; every wait is bounded and sets an error flag when it gives up.
 #include <cuda_bf16.h>
@@ -113,18 +114,6 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// Store one value into a packed panel: element (row, k), plane q.
-__device__ __forceinline__ void put_packed(uint8_t* base, const TcPanelGeom& g, int64_t row, int64_t k, int plane,
-                                           int prec, float v) {
-  const int ebytes = prec == TC_TF32 ? 4 : 2;
-  const int kpt = 128 / ebytes;
-  const int64_t rt = row / 128, kt = k / kpt;
-  uint8_t* tile = base + ((rt * g.nkt + kt) * g.planes + plane) * (int64_t)(128 * 128);
-  const uint32_t off = sw128((uint32_t)(row % 128), (uint32_t)((k % kpt) * ebytes));
-  if (prec == TC_TF32) *(float*)(tile + off) = v;
-  else *(__nv_bfloat16*)(tile + off) = __float2bfloat16_rn(v);
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- packing kernels
@@ -188,32 +177,83 @@ struct TcArgs {
   int* err;
 };
 
-constexpr int kStages = kTcStages;
-constexpr int kStageBytes = kTcStageBytes;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+// Accumulator slots in TMEM: slot b holds C_re at columns 256 b and C_im at 256 b + 128.
+constexpr int kAccSlots = 2;
+
+// Write 16 consecutive output values of one row into a packed panel (16-byte chunks).
+__device__ __forceinline__ void put_packed16(uint8_t* base, int64_t nkt, int planes, int prec, int64_t row,
+                                             int64_t k0, const float* re, const float* im, int nvalid) {
+  const int kpt = prec == TC_TF32 ? 32 : 64;
+  const int64_t rt = row / 128, kt = k0 / kpt;
+  uint8_t* tile = base + (rt * nkt + kt) * planes * (int64_t)(128 * 128);
+  const uint32_t r = (uint32_t)(row % 128);
+  const int kin = (int)(k0 % kpt);
+  if (prec == TC_TF32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {          // 4 chunks of 4 TF32 values
+      uint4 vr, vi;
+      float* fr = (float*)&vr;
+      float* fi = (float*)&vi;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = 4 * q + e;
+        fr[e] = j < nvalid ? tf32_rna(re[j]) : 0.f;
+        fi[e] = j < nvalid ? tf32_rna(im[j]) : 0.f;
+      }
+      const uint32_t off = sw128(r, (uint32_t)((kin + 4 * q) * 4));
+      *(uint4*)(tile + off) = vr;
+      *(uint4*)(tile + 128 * 128 + off) = vi;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {          // 2 chunks of 8 BF16 values per plane
+      uint4 v[4];
+      __nv_bfloat16* b[4];
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) b[pl] = (__nv_bfloat16*)&v[pl];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int j = 8 * q + e;
+        const float x = j < nvalid ? re[j] : 0.f, y = j < nvalid ? im[j] : 0.f;
+        const __nv_bfloat16 xh = __float2bfloat16_rn(x), yh = __float2bfloat16_rn(y);
+        b[0][e] = xh;
+        b[1][e] = __float2bfloat16_rn(x - __bfloat162float(xh));
+        b[2][e] = yh;
+        b[3][e] = __float2bfloat16_rn(y - __bfloat162float(yh));
+      }
+      const uint32_t off = sw128(r, (uint32_t)((kin + 8 * q) * 2));
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) *(uint4*)(tile + pl * 128 * 128 + off) = v[pl];
+    }
+  }
+}
 
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
   extern __shared__ uint8_t dyn[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty;
+  __shared__ __align__(8) uint64_t bar_full[3], bar_empty[3], bar_acc_full[kAccSlots], bar_acc_empty[kAccSlots];
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int prec = g.prec;
-  const int planes = prec == TC_TF32 ? 2 : 4;
-  const int kpt = prec == TC_TF32 ? 32 : 64;       // K values per 128-byte row
+  const int planes = tc_planes(prec);
+  const int kpt = tc_kpt(prec);                    // K values per 128-byte row
   const int kstep = prec == TC_TF32 ? 8 : 16;      // K per MMA instruction
   const int ntile = tc_ntile(prec);                // B rows (output columns) per tile
+  const int nstages = tc_stages(prec);
+  const int stage_bytes = tc_stage_bytes(prec);
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < nstages; ++s) {
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_acc_full), 1);
-    mbar_init(smem_u32(&bar_acc_empty), 4);
+    for (int b = 0; b < kAccSlots; ++b) {
+      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[b]), 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -245,19 +285,21 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
           ok = mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1, g.err, 11);
           if (!ok) break;
           const uint32_t abytes = planes * 128 * 128, bbytes = (uint32_t)(planes * nrow * 128);
-          const uint32_t sa = smem_u32(smem + stage * kStageBytes);
+          const uint32_t sa = smem_u32(smem + stage * stage_bytes);
           const uint32_t sb = sa + planes * 128 * 128;
           mbar_expect_tx(smem_u32(&bar_full[stage]), abytes + bbytes);
           bulk_g2s(sa, a + kt * abytes, abytes, smem_u32(&bar_full[stage]));
           bulk_g2s(sb, b + kt * (int64_t)bbytes, bbytes, smem_u32(&bar_full[stage]));
-          if (++stage == kStages) { stage = 0; phase ^= 1; }
+          if (++stage == nstages) { stage = 0; phase ^= 1; }
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     int stage = 0;
-    uint32_t phase = 0, acc_phase = 0;
+    uint32_t phase = 0;
+    uint32_t acc_phase = 0;   // bit b: phase of slot b
+    int slot = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
       const int64_t t = find_task(g.prefix, g.n_tasks, item);
@@ -268,10 +310,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       const int64_t nt = local % tiles_n;
       const int64_t npad = ((N + 15) / 16) * 16;
       const int nrow = (int)(npad - nt * ntile < ntile ? npad - nt * ntile : ntile);
-      // accumulators free?
-      ok = mbar_wait(smem_u32(&bar_acc_empty), acc_phase ^ 1, g.err, 12);
+      ok = mbar_wait(smem_u32(&bar_acc_empty[slot]), ((acc_phase >> slot) & 1) ^ 1, g.err, 12);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t t_re = tmem + 256 * slot, t_im = t_re + 128;
       const uint32_t id_pos = make_idesc(prec, nrow, false), id_neg = make_idesc(prec, nrow, true);
       bool first = true;
       for (int64_t s = 0; s < task[6] && ok; ++s) {
@@ -280,7 +322,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
           ok = mbar_wait(smem_u32(&bar_full[stage]), phase, g.err, 13);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t sa = smem_u32(smem + stage * kStageBytes);
+          const uint32_t sa = smem_u32(smem + stage * stage_bytes);
           const uint32_t sb = sa + planes * 128 * 128;
           const uint32_t pa = 128 * 128, pb = (uint32_t)nrow * 128;
           for (int ks = 0; ks < kpt / kstep; ++ks) {
@@ -289,10 +331,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
             if (prec == TC_TF32) {
               const uint64_t ar = make_desc(sa + ko), ai = make_desc(sa + pa + ko);
               const uint64_t br = make_desc(sb + ko), bi = make_desc(sb + pb + ko);
-              mma(prec, tmem, ar, br, id_pos, acc);
-              mma(prec, tmem, ai, bi, id_neg, 1u);
-              mma(prec, tmem + 256, ar, bi, id_pos, acc);
-              mma(prec, tmem + 256, ai, br, id_pos, 1u);
+              mma(prec, t_re, ar, br, id_pos, acc);
+              mma(prec, t_re, ai, bi, id_neg, 1u);
+              mma(prec, t_im, ar, bi, id_pos, acc);
+              mma(prec, t_im, ai, br, id_pos, 1u);
             } else {
               // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
               uint64_t A[4], B[4];
@@ -301,33 +343,35 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
                 B[q] = make_desc(sb + q * pb + ko);
               }
               // C_re += Re(A) Re(B) - Im(A) Im(B), each with hi*hi + hi*lo + lo*hi
-              mma(prec, tmem, A[0], B[0], id_pos, acc);
-              mma(prec, tmem, A[0], B[1], id_pos, 1u);
-              mma(prec, tmem, A[1], B[0], id_pos, 1u);
-              mma(prec, tmem, A[2], B[2], id_neg, 1u);
-              mma(prec, tmem, A[2], B[3], id_neg, 1u);
-              mma(prec, tmem, A[3], B[2], id_neg, 1u);
+              mma(prec, t_re, A[0], B[0], id_pos, acc);
+              mma(prec, t_re, A[0], B[1], id_pos, 1u);
+              mma(prec, t_re, A[1], B[0], id_pos, 1u);
+              mma(prec, t_re, A[2], B[2], id_neg, 1u);
+              mma(prec, t_re, A[2], B[3], id_neg, 1u);
+              mma(prec, t_re, A[3], B[2], id_neg, 1u);
               // C_im += Re(A) Im(B) + Im(A) Re(B)
-              mma(prec, tmem + 256, A[0], B[2], id_pos, acc);
-              mma(prec, tmem + 256, A[0], B[3], id_pos, 1u);
-              mma(prec, tmem + 256, A[1], B[2], id_pos, 1u);
-              mma(prec, tmem + 256, A[2], B[0], id_pos, 1u);
-              mma(prec, tmem + 256, A[2], B[1], id_pos, 1u);
-              mma(prec, tmem + 256, A[3], B[0], id_pos, 1u);
+              mma(prec, t_im, A[0], B[2], id_pos, acc);
+              mma(prec, t_im, A[0], B[3], id_pos, 1u);
+              mma(prec, t_im, A[1], B[2], id_pos, 1u);
+              mma(prec, t_im, A[2], B[0], id_pos, 1u);
+              mma(prec, t_im, A[2], B[1], id_pos, 1u);
+              mma(prec, t_im, A[3], B[0], id_pos, 1u);
             }
             first = false;
           }
           mma_commit(smem_u32(&bar_empty[stage]));
-          if (++stage == kStages) { stage = 0; phase ^= 1; }
+          if (++stage == nstages) { stage = 0; phase ^= 1; }
         }
       }
-      mma_commit(smem_u32(&bar_acc_full));
-      acc_phase ^= 1;
+      mma_commit(smem_u32(&bar_acc_full[slot]));
+      acc_phase ^= 1u << slot;
+      slot ^= 1;
     }
   } else if (warp >= 2) {
     // ---------------- epilogue
     const int quad = warp & 3;            // TMEM lanes 32*quad .. 32*quad+31
-    uint32_t acc_phase = 0;
+    uint32_t acc_phase = 0;   // bit b: phase of slot b
+    int slot = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
       const int64_t t = find_task(g.prefix, g.n_tasks, item);
@@ -336,60 +380,50 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       const int64_t local = item - g.prefix[t];
       const int64_t tiles_n = (N + ntile - 1) / ntile;
       const int64_t rt = local / tiles_n, nt = local % tiles_n;
-      ok = mbar_wait(smem_u32(&bar_acc_full), acc_phase, g.err, 14);
-      acc_phase ^= 1;
+      ok = mbar_wait(smem_u32(&bar_acc_full[slot]), (acc_phase >> slot) & 1, g.err, 14);
+      acc_phase ^= 1u << slot;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int64_t row = rt * 128 + quad * 32 + lane;
       const int64_t c0 = nt * ntile;
       const int64_t ncols = N - c0 < ntile ? N - c0 : ntile;
+      const uint32_t t_re = tmem + 256 * slot + ((uint32_t)(quad * 32) << 16);
       for (int64_t cb = 0; cb < ncols; cb += 16) {
         uint32_t vr[16], vi[16];
-        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cb;
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                      : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
                        "=r"(vr[7]), "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]),
                        "=r"(vr[14]), "=r"(vr[15])
-                     : "r"(ta));
+                     : "r"(t_re + (uint32_t)cb));
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                      : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
                        "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]),
                        "=r"(vi[14]), "=r"(vi[15])
-                     : "r"(ta + 256));
+                     : "r"(t_re + 128u + (uint32_t)cb));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (row < M) {
+          const int nvalid = (int)(ncols - cb < 16 ? ncols - cb : 16);
+          float re[16], im[16];
+#pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int64_t c = c0 + cb + j;
-            if (c >= N) break;
-            const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
-            if (task[7] == 1) {
-              g.f_out[task[2] + row * task[3] + c] = make_double2((double)re, (double)im);
-            } else {
-              // packed Z: columns below split go to panel task[2], the rest to task[3]
-              const bool second = c >= task[4];
-              const int64_t k = second ? c - task[4] : c;
-              TcPanelGeom geo;
-              geo.nkt = second ? task[9] : task[8];
-              geo.planes = planes;
-              uint8_t* base = g.z_out + (second ? task[3] : task[2]);
-              if (prec == TC_TF32) {
-                put_packed(base, geo, row, k, 0, prec, tf32_rna(re));
-                put_packed(base, geo, row, k, 1, prec, tf32_rna(im));
-              } else {
-                const float rh = __bfloat162float(__float2bfloat16_rn(re));
-                const float ih = __bfloat162float(__float2bfloat16_rn(im));
-                put_packed(base, geo, row, k, 0, prec, rh);
-                put_packed(base, geo, row, k, 1, prec, re - rh);
-                put_packed(base, geo, row, k, 2, prec, ih);
-                put_packed(base, geo, row, k, 3, prec, im - ih);
-              }
-            }
+            re[j] = __uint_as_float(vr[j]);
+            im[j] = __uint_as_float(vi[j]);
+          }
+          const int64_t c = c0 + cb;
+          if (task[7] == 1) {
+            double2* dst = g.f_out + task[2] + row * task[3] + c;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (j < nvalid) dst[j] = make_double2((double)re[j], (double)im[j]);
+          } else {
+            put_packed16(g.z_out + task[2], task[8], planes, prec, row, c, re, im, nvalid);
           }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty));
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty[slot]));
+      slot ^= 1;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -413,13 +447,13 @@ cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t*
   if (total_tiles <= 0) return cudaSuccess;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
-  k_tc_gemm<<<(unsigned)grid, 192, kSmemBytes, s>>>(g);
+  k_tc_gemm<<<(unsigned)grid, 192, kTcSmemBytes, s>>>(g);
   mrd::count_launch();
   return cudaGetLastError();
 }

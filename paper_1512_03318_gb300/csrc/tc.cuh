@@ -5,9 +5,8 @@
 namespace mrd {
 
 enum { TC_TF32 = 1, TC_BF16X3 = 2 };
-// task row (int64): M N out0 out1 split seg0 nseg mode nkt_z0 nkt_z1
-//   mode 0: packed Z output, out0/out1 = byte offsets of the Z panels of the two column
-//           parts (columns < split / >= split), nkt_z0/1 their K-tile counts
+// task row (int64): M N out0 out1 pad seg0 nseg mode nkt_z pad
+//   mode 0: packed Z output, out0 = byte offset of the Z panel, nkt_z its K-tile count
 //   mode 1: FP64 output, out0 = element offset, out1 = leading dimension
 enum { TCT = 10 };
 // segment row: a_panel_byte_offset b_panel_byte_offset nkt pad
@@ -22,8 +21,11 @@ struct TcPanelGeom {
 
 __host__ __device__ inline int tc_planes(int prec) { return prec == TC_TF32 ? 2 : 4; }
 __host__ __device__ inline int tc_kpt(int prec) { return prec == TC_TF32 ? 32 : 64; }   // K per 128-byte row
-__host__ __device__ inline int tc_ntile(int prec) { return prec == TC_TF32 ? 256 : 64; } // B rows per tile
-constexpr int kTcStageBytes = 96 * 1024;   // A: planes x 16 KB, B: planes x ntile x 128 B (both precisions)
-constexpr int kTcStages = 2;
+__host__ __device__ inline int tc_ntile(int prec) { return prec == TC_TF32 ? 128 : 64; } // B rows per tile
+// shared-memory stage: A planes x 16 KB + B planes x ntile x 128 B
+__host__ __device__ inline int tc_stage_bytes(int prec) { return prec == TC_TF32 ? 64 * 1024 : 96 * 1024; }
+__host__ __device__ inline int tc_stages(int prec) { return prec == TC_TF32 ? 3 : 2; }
+constexpr int kTcSmemBytes = 192 * 1024 + 1024;
+constexpr int kTcStageBytes = 96 * 1024;   // largest stage (bounds checks)
 
 }  // namespace mrd

@@ -66,17 +66,21 @@ int build(mrd_heff* h, int prec) {
     j_wr.insert(j_wr.end(), {r[7], rows, 1, rows, K, wr_b, ntile, nkt, round_up(rows, 16)});
     wr_b += b_bytes(rows, nkt, planes);
   }
-  // theta rows (s1, a) of every middle sector: B panel of the transpose, rows coldim, K d_a
+  // theta block (s1, a) x (s2, b) of every middle sector: B panel of its transpose, rows d_b, K d_a
   const std::vector<int64_t>& mid = h->mid_host;
   for (int64_t m = 0; m < c[C_NMID]; ++m) {
     const int64_t* r = &mid[MIDF * m];
     for (int s1 = 0; s1 < 2; ++s1) {
       if (r[5 + s1] < 0) continue;
-      const int64_t K = h->left[3 * r[5 + s1] + 2], rows = r[3], nkt = (K + kpt - 1) / kpt;
-      const int64_t src = r[4] + (s1 ? r[7] : 0) * r[3];
-      th_map[src] = {th_b, nkt};
-      j_th.insert(j_th.end(), {src, rows, 1, rows, K, th_b, ntile, nkt, round_up(rows, 16)});
-      th_b += b_bytes(rows, nkt, planes);
+      const int64_t K = h->left[3 * r[5 + s1] + 2], nkt = (K + kpt - 1) / kpt;
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (r[8 + s2] < 0) continue;
+        const int64_t rows = h->right[3 * r[8 + s2] + 2];
+        const int64_t src = r[4] + (s1 ? r[7] : 0) * r[3] + (s2 ? r[10] : 0);
+        th_map[src] = {th_b, nkt};
+        j_th.insert(j_th.end(), {src, r[3], 1, rows, K, th_b, ntile, nkt, round_up(rows, 16)});
+        th_b += b_bytes(rows, nkt, planes);
+      }
     }
   }
   // Z(w', m_in) rows (s1') x columns (s2): A panels keyed by their FP64 element offset
@@ -104,37 +108,30 @@ int build(mrd_heff* h, int prec) {
       }
     }
   }
-  // step-1 tasks (Z = LW theta)
+  // step-1 tasks (Z = LW theta), one per (w', m_in, s1', s2) so that each writes one Z panel
   std::vector<int64_t> t1, s1, p1{0}, t2, s2, p2{0};
   for (int64_t i = 0; i < c[C_NT1]; ++i) {
     const int64_t* t = &h->t1_host[TF * i];
     if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
-    const int64_t wp = i / 2 / nmid, mi = (i / 2) % nmid;
-    (void)wp;
-    const int64_t* rin = &mid[MIDF * mi];
-    const int64_t seg0 = (int64_t)s1.size() / TCS;
-    for (int64_t k = 0; k < t[5]; ++k) {
-      const int64_t* sg = &h->s1_host[SF * (t[4] + k)];
-      auto a = lw_map.find(sg[0]);
-      auto b = th_map.find(sg[2]);
-      if (a == lw_map.end() || b == th_map.end() || a->second.nkt != b->second.nkt)
-        return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
-      s1.insert(s1.end(), {a->second.off, b->second.off, a->second.nkt, 0});
-    }
-    const int64_t split = rin[8] >= 0 ? rin[10] : 0;
-    int64_t z0 = 0, z1 = 0, k0 = 0, k1 = 0;
-    if (rin[8] >= 0) {
-      auto q = z_map.find(t[2]);
+    const int64_t* rin = &mid[MIDF * ((i / 2) % nmid)];
+    for (int s2p = 0; s2p < 2; ++s2p) {
+      if (rin[8 + s2p] < 0) continue;
+      const int64_t N = h->right[3 * rin[8 + s2p] + 2], coff = s2p ? rin[10] : 0;
+      if (N == 0) continue;
+      const int64_t seg0 = (int64_t)s1.size() / TCS;
+      for (int64_t k = 0; k < t[5]; ++k) {
+        const int64_t* sg = &h->s1_host[SF * (t[4] + k)];
+        auto a = lw_map.find(sg[0]);
+        auto b = th_map.find(sg[2] + coff);
+        if (a == lw_map.end() || b == th_map.end() || a->second.nkt != b->second.nkt)
+          return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
+        s1.insert(s1.end(), {a->second.off, b->second.off, a->second.nkt, 0});
+      }
+      auto q = z_map.find(t[2] + coff);
       if (q == z_map.end()) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
-      z0 = q->second.off; k0 = q->second.nkt;
+      t1.insert(t1.end(), {t[0], N, q->second.off, 0, 0, seg0, t[5], 0, q->second.nkt, 0});
+      p1.push_back(p1.back() + ((t[0] + 127) / 128) * ((N + ntile - 1) / ntile));
     }
-    if (rin[9] >= 0) {
-      auto q = z_map.find(t[2] + rin[10]);
-      if (q == z_map.end()) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
-      z1 = q->second.off; k1 = q->second.nkt;
-    }
-    t1.insert(t1.end(), {t[0], t[1], z0, z1, split, seg0, t[5], 0, k0, k1});
-    p1.push_back(p1.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
   }
   // step-2 tasks (theta' = sum Z WR)
   for (int64_t i = 0; i < c[C_NT2]; ++i) {
@@ -163,19 +160,15 @@ int build(mrd_heff* h, int prec) {
           if (q[0] < 0 || q[0] + a_bytes(M, q[2], planes) > alen) return false;
           if (q[1] < 0 || q[1] + b_bytes(N, q[2], planes) > blen) return false;
         }
-        if (zout) {
-          const int64_t split = tk[i + 4];
-          if (split > 0 && tk[i + 2] + a_bytes(M, tk[i + 8], planes) > z_b) return false;
-          if (N > split && tk[i + 3] + a_bytes(M, tk[i + 9], planes) > z_b) return false;
-          if (split > 0 && (tk[i + 8] + 0) * kpt < split) return false;
-          if (N > split && tk[i + 9] * kpt < N - split) return false;
-        }
+        if (zout && (tk[i + 2] < 0 || tk[i + 2] + a_bytes(M, tk[i + 8], planes) > z_b || tk[i + 8] * kpt < N))
+          return false;
       }
       return true;
     };
     if (!chk(t1, s1, lw_b, th_b, true) || !chk(t2, s2, z_b, wr_b, false))
       return mrd_fail(ctx, MRD_E_STATE, "tc: internal panel table check failed");
-    if (planes * 128 * 128 + planes * ntile * 128 > kTcStageBytes)
+    if (planes * 128 * 128 + planes * ntile * 128 > tc_stage_bytes(prec) ||
+        tc_stages(prec) * tc_stage_bytes(prec) > kTcSmemBytes - 1024)
       return mrd_fail(ctx, MRD_E_STATE, "tc: stage does not fit");
   }
   // device buffers
