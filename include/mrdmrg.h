@@ -179,7 +179,16 @@ typedef struct {
   double refine_tol;         /* relative Ritz-value change that stops the polish              */
   int32_t lanczos_restarts;  /* extra Lanczos runs restarted from the current ground vector   */
                              /* while the Ritz value still moves by more than lanczos_tol     */
+  int32_t svd_mode;          /* MRD_SVD_*: arithmetic of the one-sided Jacobi sweeps          */
 } mrd_dmrg_params;
+
+/* Block SVD sweep arithmetic. The final sweeps stop when every column pair is orthogonal to
+ * 1e-14 (FP64) or 5e-13 (float-float: pairs of FP32 numbers, ~48-bit products, on the FP32
+ * pipes); FP32 pre-sweeps (to 1e-5) may precede them. */
+#define MRD_SVD_F32_FF 0   /* FP32 pre-sweeps, float-float sweeps */
+#define MRD_SVD_FF 1       /* float-float sweeps only             */
+#define MRD_SVD_F32_F64 2  /* FP32 pre-sweeps, FP64 sweeps        */
+#define MRD_SVD_F64 3      /* FP64 sweeps only                    */
 
 /* Finite two-site DMRG state on the device for the MPO `mpo` (copied; it may be freed later) in the
  * charge sector (N = n_part, K = k_tot mod modulus). Starts from a seeded random MPS whose

@@ -16,6 +16,10 @@ MRD_PREC_TF32 = 1
 MRD_PREC_BF16X3 = 2
 MRD_BASIS_MIXED = 0
 MRD_BASIS_REAL = 1
+MRD_SVD_F32_FF = 0
+MRD_SVD_FF = 1
+MRD_SVD_F32_F64 = 2
+MRD_SVD_F64 = 3
 
 _LIB = None
 _LIVE = []        # weak references to open handles, closed in creation-reverse order at exit
@@ -249,7 +253,7 @@ class MPO:
 class mrd_dmrg_params(C.Structure):
     _fields_ = [("chi", C.c_int32), ("svd_cutoff", C.c_double), ("lanczos_max_iter", C.c_int32),
                 ("lanczos_tol", C.c_double), ("prec", C.c_int32), ("refine_iter", C.c_int32),
-                ("refine_tol", C.c_double), ("lanczos_restarts", C.c_int32)]
+                ("refine_tol", C.c_double), ("lanczos_restarts", C.c_int32), ("svd_mode", C.c_int32)]
 
 
 class DMRG:
@@ -270,8 +274,10 @@ class DMRG:
 
     @staticmethod
     def params(chi, cutoff=1e-14, max_iter=30, tol=1e-13, prec=MRD_PREC_FP64, refine_iter=0, refine_tol=1e-13,
-               restarts=0):
-        return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec, refine_iter, refine_tol, restarts)
+               restarts=0, svd_mode=None):
+        if svd_mode is None:   # FP64 updates decompose in FP64, reduced-precision ones in float-float
+            svd_mode = MRD_SVD_F64 if prec == MRD_PREC_FP64 else MRD_SVD_FF
+        return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec, refine_iter, refine_tol, restarts, svd_mode)
 
     def update(self, i, direction, params):
         e, t = C.c_double(), C.c_double()

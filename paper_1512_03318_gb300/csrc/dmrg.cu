@@ -30,17 +30,24 @@ cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, co
                               int n_sm, cudaStream_t s);
 cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* src_off, int nblk, double2* work,
                      double* fro2, cudaStream_t s);
-cudaError_t svd_round(double2* work, const int64_t* blk, const int64_t* pair_prefix, int nblk, int64_t npairs,
-                      int round, double tol, const double* fro2, int* rotated, cudaStream_t s);
+int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
+cudaError_t svd_bround(double2* work, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
+                       int round, int W, int64_t smem, double tol, bool ff, const double* fro2, int* rotated,
+                       cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
                        double* S_sorted, int* order_scratch, const double* fro2, cudaStream_t s);
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
                          int* keep, double* info, int* flat_block, cudaStream_t s);
-cudaError_t svd_round32(float2* w32, const int64_t* blk, const int64_t* pair_prefix, int nblk, int64_t npairs,
-                        int round, float tol, const double* fro2, int* rotated, cudaStream_t s);
+cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
+                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 enum { SVF = 12 };
+constexpr int64_t kSvdMaxSmemHost = 220 * 1024;   // dynamic shared memory of a Jacobi CTA
+// orthogonality tolerance |x_i^+ x_j| / (|x_i| |x_j|) of the final sweeps: FP64, and float-float
+// (48-bit products: dot products of a few hundred terms carry ~1e-13 relative noise)
+constexpr double kTolF64 = 1e-14, kTolFF = 5e-13;
+constexpr int kMaxSweeps64 = 60;
 
 namespace {
 
@@ -125,12 +132,47 @@ __global__ void k_copy_blocks(const double2* __restrict__ src, double2* __restri
   }
 }
 
-// x *= g (g read from device memory)
-__global__ void k_scale(double2* __restrict__ x, int64_t n, const double* __restrict__ g) {
-  const double f = *g;
+constexpr int kNormParts = 256;
+
+// partial[blockIdx.x] = sum of |x_e|^2 over a fixed strided subset (fixed reduction order)
+__global__ void __launch_bounds__(256) k_sumsq_partial(const double2* __restrict__ x, int64_t n,
+                                                       double* __restrict__ partial) {
+  __shared__ double sm[256];
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)kNormParts * 256)
+    acc = fma(x[e].x, x[e].x, fma(x[e].y, x[e].y, acc));
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+// Renormalise the centre tensor to unit norm: kept = |x|^2 (the weight captured by the
+// orthonormal canonical factor), info[0] = 1/sqrt(kept), info[1] = discarded weight
+// 1 - kept / |theta|^2 with |theta|^2 = sum of the blocks' fro2.
+__global__ void __launch_bounds__(256) k_scale_unit(double2* __restrict__ x, int64_t n,
+                                                    const double* __restrict__ partial,
+                                                    const double* __restrict__ fro2, int nblk,
+                                                    double* __restrict__ info) {
+  __shared__ double f;
+  if (threadIdx.x == 0) {
+    double kept = 0.0, all = 0.0;
+    for (int q = 0; q < kNormParts; ++q) kept += partial[q];
+    for (int b = 0; b < nblk; ++b) all += fro2[b];
+    f = kept > 0.0 ? 1.0 / sqrt(kept) : 0.0;
+    if (blockIdx.x == 0) {
+      info[0] = f;
+      info[1] = all > 0.0 ? fmax(0.0, (all - kept) / all) : 0.0;
+    }
+  }
+  __syncthreads();
+  const double g = f;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    x[e].x *= f;
-    x[e].y *= f;
+    x[e].x *= g;
+    x[e].y *= g;
   }
 }
 
@@ -383,14 +425,13 @@ int form_theta(mrd_dmrg* D, mrd_heff* h, const SiteT& X, const SiteT& Y, double2
 
 // Block SVD of the blocks `blk` (SVF rows) of `src`; returns kept counts per block and info.
 int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>& src_off, const double2* src,
-              int side, int chi, double cutoff, std::vector<int>& keep, double info[3]) {
+              int side, int chi, double cutoff, int mode, std::vector<int>& keep, double info[3]) {
   mrd_ctx* ctx = D->ctx;
   cudaStream_t s = ctx->stream;
   const int nb = (int)src_off.size();
   keep.assign(nb, 0);
   if (nb == 0) { info[0] = 1; info[1] = 0; info[2] = 0; return MRD_OK; }
-  int64_t work = 0, ulen = 0, vlen = 0, slen = 0, maxrr = 0, npairs = 0;
-  std::vector<int64_t> pp(nb + 1, 0);
+  int64_t work = 0, ulen = 0, vlen = 0, slen = 0;
   for (int b = 0; b < nb; ++b) {
     int64_t* d = &blk[SVF * b];
     const int64_t m = d[0], n = d[1];
@@ -401,9 +442,6 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     d[6] = ulen; ulen += m * r;
     d[7] = vlen; vlen += r * n;
     d[8] = slen; slen += r;
-    const int64_t rr = r + (r & 1);
-    maxrr = std::max(maxrr, rr);
-    pp[b + 1] = pp[b] + rr / 2;
   }
   int64_t xlen = work;
   for (int b = 0; b < nb; ++b) {   // V_X of every block after all X blocks
@@ -417,7 +455,36 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     blk[SVF * b + 11] = w32;
     w32 += blk[SVF * b + 3] * blk[SVF * b + 3];
   }
-  npairs = pp[nb];
+  // block-cyclic Jacobi schedules: column groups of W (FP32 with V: 16, FP64: 8), halved
+  // while a group pair does not fit in shared memory
+  struct Sched {
+    int W = 0, rounds = 0;
+    int64_t ncta = 0, smem = 0;
+  };
+  std::vector<int64_t> pp(2 * (nb + 1), 0);
+  auto schedule = [&](int W, bool f32, int64_t* pre) -> Sched {
+    Sched sc;
+    for (;;) {
+      int64_t sm = 0;
+      for (int b = 0; b < nb; ++b)
+        sm = std::max(sm, svd_bround_smem(W, blk[SVF * b + 2], f32 ? blk[SVF * b + 3] : 0, f32));
+      if (sm <= kSvdMaxSmemHost || W == 2) { sc.smem = sm; break; }
+      W /= 2;
+    }
+    sc.W = W;
+    pre[0] = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int64_t r = blk[SVF * b + 3];
+      const int64_t G = (r + W - 1) / W, Gp = std::max<int64_t>(2, G + (G & 1));
+      pre[b + 1] = pre[b] + (r > 0 ? Gp / 2 : 0);
+      if (r > 0) sc.rounds = std::max<int>(sc.rounds, (int)(Gp - 1));
+    }
+    sc.ncta = pre[nb];
+    return sc;
+  };
+  const Sched s32 = schedule(16, true, pp.data()), s64 = schedule(8, false, pp.data() + nb + 1);
+  if (s32.smem > kSvdMaxSmemHost || s64.smem > kSvdMaxSmemHost)
+    return mrd_fail(ctx, MRD_E_OOM, "block SVD: a block is too large for the shared-memory Jacobi rounds");
   MRD_CUDA(ctx, D->svd_blk.need(blk.size() * 8));
   MRD_CUDA(ctx, D->svd_src.need(src_off.size() * 8));
   MRD_CUDA(ctx, D->svd_pref.need(pp.size() * 8));
@@ -441,16 +508,20 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   const double* fro = D->svd_fro.as<double>();
   MRD_CUDA(ctx, svd_load(src, dblk, D->svd_src.as<int64_t>(), nb, D->svd_work.as<double2>(), D->svd_fro.as<double>(), s));
   int* rot = D->svd_rot.as<int>();
+  const int64_t* pre32 = D->svd_pref.as<int64_t>();
+  const int64_t* pre64 = pre32 + nb + 1;
   auto sweep_until_done = [&](bool f32, int max_sweeps, int* used) -> int {
+    const Sched& sc = f32 ? s32 : s64;
+    const bool ff = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
       MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
-      for (int rd = 0; rd + 1 < maxrr; ++rd) {
+      for (int rd = 0; rd < sc.rounds; ++rd) {
         if (f32)
-          MRD_CUDA(ctx, svd_round32(D->svd_w32.as<float2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-5f,
-                                    fro, rot, s));
+          MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f, fro,
+                                     rot, s));
         else
-          MRD_CUDA(ctx, svd_round(D->svd_work.as<double2>(), dblk, D->svd_pref.as<int64_t>(), nb, npairs, rd, 1e-14,
-                                  fro, rot, s));
+          MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), dblk, pre64, nb, sc.ncta, rd, sc.W, sc.smem,
+                                   ff ? kTolFF : kTolF64, ff, fro, rot, s));
       }
       int hrot = 0;
       MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
@@ -460,11 +531,14 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     }
     return f32 ? MRD_OK : mrd_fail(ctx, MRD_E_NOCONV, "block SVD: Jacobi sweeps did not converge");
   };
-  // FP32 pre-sweeps orthogonalise the columns to ~1e-5 (the resolution of FP32 dot products of
-  // a few hundred terms); their rotations V32 are applied to the
-  // FP64 matrix (X <- X V32, one grouped GEMM) and FP64 sweeps finish the job.
+  // FP32 pre-sweeps (MRD_SVD_F32_*) orthogonalise the columns to ~1e-5 (the resolution of FP32
+  // dot products of a few hundred terms); their rotations V32 are applied to the FP64 matrix
+  // (X <- X V32, one grouped GEMM) and float-float or FP64 sweeps finish the job.
+  int rc = MRD_OK;
+  D->svd_sweeps32 = 0;
+  if (mode == MRD_SVD_F32_FF || mode == MRD_SVD_F32_F64) {
   MRD_CUDA(ctx, svd_to_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
-  int rc = sweep_until_done(true, 30, &D->svd_sweeps32);
+  rc = sweep_until_done(true, 30, &D->svd_sweeps32);
   if (rc != MRD_OK) return rc;
   MRD_CUDA(ctx, svd_v_from_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
   {
@@ -481,7 +555,8 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     if (rc != MRD_OK) return rc;
     MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_work.p, D->svd_x2.p, (size_t)xlen * 16, cudaMemcpyDeviceToDevice, s));
   }
-  rc = sweep_until_done(false, 40, &D->svd_sweeps64);
+  }
+  rc = sweep_until_done(false, kMaxSweeps64, &D->svd_sweeps64);
   if (rc != MRD_OK) return rc;
   MRD_CUDA(ctx, svd_finish(D->svd_work.as<double2>(), dblk, nb, D->svd_u.as<double2>(), D->svd_vh.as<double2>(),
                            D->svd_s.as<double>(), D->svd_ss.as<double>(), D->svd_ord.as<int>(), fro, s));
@@ -673,7 +748,7 @@ int orthonormalise(mrd_dmrg* D, SiteT& T) {
   }
   std::vector<int> keep;
   double info[3];
-  int rc = block_svd(D, blk, src, T.data.as<double2>(), T.mode == 1 ? 1 : 0, 1 << 30, 0.0, keep, info);
+  int rc = block_svd(D, blk, src, T.data.as<double2>(), T.mode == 1 ? 1 : 0, 1 << 30, 0.0, MRD_SVD_FF, keep, info);
   if (rc != MRD_OK) return rc;
   std::vector<int64_t> cp;
   for (size_t b = 0; b < gi.size(); ++b) {
@@ -859,6 +934,8 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   if (!D || !p) return MRD_E_ARG;
   mrd_ctx* ctx = D->ctx;
   if (i < 0 || i > D->n - 2) return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: site out of range");
+  if (p->svd_mode < MRD_SVD_F32_FF || p->svd_mode > MRD_SVD_F64)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: unknown svd_mode");
   if (!D->L[i].data.p || !D->R[i + 2].data.p)
     return mrd_fail(ctx, MRD_E_STATE, "mrd_two_site_update: environments of this bond are not available");
   Guard g(ctx->device);
@@ -927,7 +1004,7 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   std::vector<int> keep;
   double info[3];
   const int side = direction > 0 ? 0 : 1;   // the factor that stays in canonical form
-  if ((rc = block_svd(D, blk, src, theta, side, p->chi, p->svd_cutoff, keep, info)) != MRD_OK) return rc;
+  if ((rc = block_svd(D, blk, src, theta, side, p->chi, p->svd_cutoff, p->svd_mode, keep, info)) != MRD_OK) return rc;
   lap(3);
   // new bond i+1
   Secs nb;
@@ -975,10 +1052,16 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
     rc = run_gemm(D, proj, theta, n, D->svd_vh.as<double2>(), svd_vlen, centre.data.as<double2>(), centre.size);
   if (rc != MRD_OK) return rc;
   if (centre.size > 0) {
-    k_scale<<<(unsigned)std::min<int64_t>((centre.size + 255) / 256, 4096), 256, 0, ctx->stream>>>(
-        centre.data.as<double2>(), centre.size, D->svd_info.as<double>());
+    MRD_CUDA(ctx, D->svd_x2.need((size_t)kNormParts * 8));
+    k_sumsq_partial<<<kNormParts, 256, 0, ctx->stream>>>(centre.data.as<double2>(), centre.size,
+                                                         D->svd_x2.as<double>());
+    mrd::count_launch();
+    k_scale_unit<<<(unsigned)std::min<int64_t>((centre.size + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        centre.data.as<double2>(), centre.size, D->svd_x2.as<double>(), D->svd_fro.as<double>(), (int)mids.size(),
+        D->svd_info.as<double>());
     mrd::count_launch();
     MRD_CUDA(ctx, cudaGetLastError());
+    MRD_CUDA(ctx, cudaMemcpyAsync(info, D->svd_info.p, 2 * 8, cudaMemcpyDeviceToHost, ctx->stream));
   }
   lap(4);
   if (direction > 0) rc = env_left(D, h, i);

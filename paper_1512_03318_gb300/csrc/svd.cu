@@ -9,9 +9,10 @@
 // gives U_q (the "left" side), X = M_q^+ gives V_q (the "right" side); the caller picks the
 // side that must be exactly orthonormal and obtains the other factor by projection
 // (U^+ M or M V, an FP64 GEMM). Sweeps run first in FP32 (cheap, columns orthogonal to
-// ~1e-6), their accumulated rotation is applied to the FP64 X by one GEMM, and FP64 sweeps
-// finish (quadratic convergence, typically 2-3 sweeps). All blocks advance together: one
-// launch per round of the round-robin pair schedule, one warp per column pair.
+// ~1e-5), their accumulated rotation is applied to the FP64 X by one GEMM, and FP64 sweeps
+// finish. All blocks advance together in a block-cyclic order: the columns are grouped, one
+// launch per round of the round-robin schedule on the groups, one CTA per group pair with its
+// columns staged in shared memory, one warp per column pair.
 //
 // Truncation keeps the globally largest chi singular values above cutoff * s_max, ties
 // broken by (value desc, block asc, index asc); the kept values are renormalised to
@@ -24,6 +25,7 @@ namespace mrd {
 
 // Per-block descriptor (int64): m n p r x_off v_off out_u_off out_vh_off s_off wide
 enum { SVF = 12 };   // + field 10: X32 offset, 11: V32 offset (float2 units)
+constexpr int kSvdMaxSmem = 220 * 1024;
 
 namespace {
 
@@ -58,48 +60,22 @@ __global__ void k_svd_load(const double2* __restrict__ theta, const int64_t* __r
     V[e] = make_double2((e / r) == (e % r) ? 1.0 : 0.0, 0.0);
 }
 
-// One round of the round-robin schedule for every block. Warp w handles pair (w - pair_prefix
-// of its block); the block's columns are padded to an even count rr, the dummy column rr-1
-// (when r is odd) is skipped. T is float (pre-sweeps) or double.
+// Rotate the column pair (x_i, x_j) (and the matching columns of V, when given) so that they
+// become orthogonal; one warp, columns of length p (V: r). Returns whether it rotated.
+// A column whose norm is negligible against the block (|x|^2 <= floor2 = zero_rel |M|_F^2)
+// is a numerical zero (rank deficiency): it is neither rotated nor counted as unconverged.
 template <class T, class T2>
-__global__ void k_svd_round(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf, int vf,
-                            const int64_t* __restrict__ pair_prefix, int nblk, int round, T tol,
-                            const double* __restrict__ fro2, double zero_rel, int* __restrict__ rotated) {
-  const int64_t wglob = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wglob >= pair_prefix[nblk]) return;
-  int lo = 0, hi = nblk - 1;   // largest b with pair_prefix[b] <= wglob
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (pair_prefix[mid] <= wglob) lo = mid; else hi = mid - 1;
-  }
-  const int b = lo;
-  const int64_t* d = blk + SVF * b;
-  const int64_t p = d[2], r = d[3];
-  const int64_t rr = r + (r & 1);
-  if (rr < 2 || round >= rr - 1) return;
-  const int64_t k = wglob - pair_prefix[b];
-  int64_t i, j;
-  if (k == 0) {
-    i = round;
-    j = rr - 1;
-  } else {
-    i = (round + k) % (rr - 1);
-    j = (round - k + (rr - 1)) % (rr - 1);
-  }
-  if (i >= r || j >= r) return;   // dummy column
-  T2* X = work + d[xf];
-  T2* V = vf >= 0 ? work + d[vf] : nullptr;
-  T2* xi = X + i * p;
-  T2* xj = X + j * p;
+__device__ __forceinline__ bool jacobi_pair(T2* xi, T2* xj, int p, T2* vi, T2* vj, int r, T tol, double floor2,
+                                            int lane) {
   T a = 0, bb = 0, gr = 0, gi = 0;
-  for (int64_t t = lane; t < p; t += 32) {
+  for (int t = lane; t < p; t += 32) {
     const T2 u = xi[t], v = xj[t];
     a = fma(u.x, u.x, fma(u.y, u.y, a));
     bb = fma(v.x, v.x, fma(v.y, v.y, bb));
     gr = fma(u.x, v.x, fma(u.y, v.y, gr));     // Re(conj(u) v)
     gi = fma(u.x, v.y, fma(-u.y, v.x, gi));    // Im(conj(u) v)
   }
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     bb += __shfl_xor_sync(0xffffffffu, bb, o);
@@ -107,45 +83,276 @@ __global__ void k_svd_round(T2* __restrict__ work, const int64_t* __restrict__ b
     gi += __shfl_xor_sync(0xffffffffu, gi, o);
   }
   const T g = sqrt(gr * gr + gi * gi);
-  // a column whose norm is negligible against the block (|x|^2 <= zero_rel |M|_F^2) is a
-  // numerical zero (rank deficiency): it is neither rotated nor counted as unconverged
-  const double floor2 = zero_rel * fro2[b];
-  if ((double)a <= floor2 || (double)bb <= floor2) return;
-  if (!(g > tol * sqrt(a * bb))) return;
+  if ((double)a <= floor2 || (double)bb <= floor2) return false;
+  if (!(g > tol * sqrt(a * bb))) return false;
   // phase-free real rotation on (x_i, e^{-i phi} x_j), phi = arg(gamma)
   const T ph_r = gr / g, ph_i = -gi / g;          // e^{-i phi}
   const T zeta = (bb - a) / (T(2) * g);
   const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-  const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
-  for (int64_t q = lane; q < p; q += 32) {
-    const T2 u = xi[q], v0 = xj[q];
-    T2 v;
-    v.x = v0.x * ph_r - v0.y * ph_i;
-    v.y = v0.x * ph_i + v0.y * ph_r;
-    T2 o1, o2;
-    o1.x = c * u.x - s * v.x; o1.y = c * u.y - s * v.y;
-    o2.x = s * u.x + c * v.x; o2.y = s * u.y + c * v.y;
-    xi[q] = o1;
-    xj[q] = o2;
+  const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
+  auto rot = [&](T2* ci, T2* cj, int n) {
+    for (int q = lane; q < n; q += 32) {
+      const T2 u = ci[q], v0 = cj[q];
+      T2 v;
+      v.x = v0.x * ph_r - v0.y * ph_i;
+      v.y = v0.x * ph_i + v0.y * ph_r;
+      T2 o1, o2;
+      o1.x = c * u.x - sn * v.x; o1.y = c * u.y - sn * v.y;
+      o2.x = sn * u.x + c * v.x; o2.y = sn * u.y + c * v.y;
+      ci[q] = o1;
+      cj[q] = o2;
+    }
+  };
+  rot(xi, xj, p);
+  if (vi != nullptr) rot(vi, vj, r);
+  return true;
+}
+
+// ---- float-float arithmetic (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2): a value is held as
+// an unevaluated sum hi + lo of two floats, |lo| <= ulp(hi) / 2, about 48 significant bits.
+// Products use the exact FMA residual of hi * hi; sums use TwoSum. All operations below use
+// the explicitly rounded intrinsics so that no multiply-add contraction alters them.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+// accumulator s + c: s collects the rounded partial sums, c their TwoSum errors and the
+// low-order parts of the products
+struct FFAcc {
+  float s, c;
+};
+
+// acc += x * y
+__device__ __forceinline__ void ff_mac(FFAcc& a, FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);         // x.hi * y.hi = p + e exactly
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const float s = __fadd_rn(a.s, p);           // TwoSum(a.s, p)
+  const float bp = __fsub_rn(s, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  a.s = s;
+  a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+}
+__device__ __forceinline__ FF ff_norm(FFAcc a) {  // FastTwoSum(s, c)
+  const float h = __fadd_rn(a.s, a.c);
+  return {h, __fsub_rn(a.c, __fsub_rn(h, a.s))};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+
+// acc += x * c for an FP32 coefficient c (exact product of c with both parts of x)
+__device__ __forceinline__ void ff_mac1(FFAcc& a, FF x, float c) {
+  const float p = __fmul_rn(c, x.hi);
+  float e = __fmaf_rn(c, x.hi, -p);
+  e = __fmaf_rn(c, x.lo, e);
+  const float s = __fadd_rn(a.s, p);
+  const float bp = __fsub_rn(s, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  a.s = s;
+  a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+}
+
+// a + b in float-float (TwoSum of the high parts, low parts added to the error)
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bp = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b.hi, bp));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const FF w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = ff_add(v, w);
   }
-  if (V == nullptr) {
-    if (lane == 0) atomicAdd(rotated, 1);
-    return;
+  return v;
+}
+
+// Float-float version of jacobi_pair: columns of complex float-float values (float4 =
+// re.hi, im.hi, re.lo, im.lo) on the FP32 pipes. Dot products are accumulated and reduced
+// in float-float (~48 bits, so the orthogonality test resolves 5e-13); the rotation
+// coefficients are FP32 numbers derived from them (bb - a formed in float-float), and the
+// rotation with these coefficients is applied exactly in float-float. An FP32 coefficient
+// makes the rotation unitary only to ~1e-7: the pair is left orthogonal to ~1e-7 of its
+// previous overlap (the next sweep removes the rest) and the column norms drift by ~1e-7,
+// which the caller absorbs because it takes the singular vectors of one side from the
+// orthogonalised columns and the other factor by projection.
+__device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, float tol, float floor2, int lane) {
+  FFAcc A = {0.f, 0.f}, B = {0.f, 0.f}, GR = {0.f, 0.f}, GI = {0.f, 0.f};
+  for (int t = lane; t < p; t += 32) {
+    const float4 u4 = xi[t], v4 = xj[t];
+    const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
+    ff_mac(A, ur, ur);
+    ff_mac(A, ui, ui);
+    ff_mac(B, vr, vr);
+    ff_mac(B, vi, vi);
+    ff_mac(GR, ur, vr);                        // Re(conj(u) v)
+    ff_mac(GR, ui, vi);
+    ff_mac(GI, ur, vi);                        // Im(conj(u) v)
+    ff_mac(GI, ff_neg(ui), vr);
   }
-  T2* vi = V + i * r;
-  T2* vj = V + j * r;
-  for (int64_t q = lane; q < r; q += 32) {
-    const T2 u = vi[q], v0 = vj[q];
-    T2 v;
-    v.x = v0.x * ph_r - v0.y * ph_i;
-    v.y = v0.x * ph_i + v0.y * ph_r;
-    T2 o1, o2;
-    o1.x = c * u.x - s * v.x; o1.y = c * u.y - s * v.y;
-    o2.x = s * u.x + c * v.x; o2.y = s * u.y + c * v.y;
-    vi[q] = o1;
-    vj[q] = o2;
+  const FF a2 = ff_warp_sum(ff_norm(A)), b2 = ff_warp_sum(ff_norm(B));
+  const FF gr2 = ff_warp_sum(ff_norm(GR)), gi2 = ff_warp_sum(ff_norm(GI));
+  const float a = a2.hi, bb = b2.hi, gr = gr2.hi, gi = gi2.hi;
+  const float g = hypotf(gr, gi);               // no intermediate underflow
+  if (a <= floor2 || bb <= floor2) return false;
+  if (!(g > tol * (sqrtf(a) * sqrtf(bb)))) return false;
+  const FF dba = ff_add(b2, ff_neg(a2));
+  const float ph_r = gr / g, ph_i = -gi / g;    // e^{-i phi}
+  // columns of very different norms give |zeta| up to ~1e26: take t = 1 / (2 zeta) there
+  // (relative error 1 / (4 zeta^2)) instead of squaring zeta
+  const float zeta = dba.hi / (2.f * g);
+  const float t = fabsf(zeta) > 1e4f ? 0.5f / zeta
+                                     : (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  if (!(fabsf(t) > 0.f) || !isfinite(t)) return false;   // no representable rotation
+  const float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
+  // x_i' = c u - sigma v, x_j' = s u + kappa v with sigma = s e^{-i phi}, kappa = c e^{-i phi}
+  const float sr = sn * ph_r, si = sn * ph_i, kr = c * ph_r, ki = c * ph_i;
+  for (int q = lane; q < p; q += 32) {
+    const float4 u4 = xi[q], v4 = xj[q];
+    const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
+    FFAcc o1r = {0.f, 0.f}, o1i = {0.f, 0.f}, o2r = {0.f, 0.f}, o2i = {0.f, 0.f};
+    ff_mac1(o1r, ur, c); ff_mac1(o1r, vr, -sr); ff_mac1(o1r, vi, si);    // c u_r - (s_r v_r - s_i v_i)
+    ff_mac1(o1i, ui, c); ff_mac1(o1i, vi, -sr); ff_mac1(o1i, vr, -si);   // c u_i - (s_r v_i + s_i v_r)
+    ff_mac1(o2r, ur, sn); ff_mac1(o2r, vr, kr); ff_mac1(o2r, vi, -ki);   // s u_r + k_r v_r - k_i v_i
+    ff_mac1(o2i, ui, sn); ff_mac1(o2i, vi, kr); ff_mac1(o2i, vr, ki);    // s u_i + k_r v_i + k_i v_r
+    const FF a1 = ff_norm(o1r), b1 = ff_norm(o1i), a3 = ff_norm(o2r), b3 = ff_norm(o2i);
+    xi[q] = make_float4(a1.hi, b1.hi, a1.lo, b1.lo);
+    xj[q] = make_float4(a3.hi, b3.hi, a3.lo, b3.lo);
   }
-  if (lane == 0) atomicAdd(rotated, 1);
+  return true;
+}
+
+// pair q of step s of the round-robin schedule on n (even) items
+__device__ __forceinline__ void rr_pair(int n, int s, int q, int& i, int& j) {
+  if (q == 0) {
+    i = s;
+    j = n - 1;
+  } else {
+    i = (s + q) % (n - 1);
+    j = (s - q + (n - 1)) % (n - 1);
+  }
+}
+
+// One round of the block-cyclic schedule for every block. The r columns of a block form
+// G = ceil(r / W) groups of W (padded to an even count Gp with an empty group); round
+// `round` pairs the groups round-robin and CTA k of the block takes group pair k: it stages
+// the (up to) 2W columns of X, and of V when vf >= 0, in shared memory, rotates every cross
+// pair (one pair per warp, W disjoint pairs per step, W steps), in round 0 first every pair
+// inside each of the two groups, and writes the columns back. Over Gp - 1 rounds each
+// column pair is rotated once (one sweep). T is float (pre-sweeps) or double.
+// MODE 0: FP32 columns and V (T2 = float2); 1: FP64 (double2); 2: FP64 columns held in
+// shared memory as float-float (G2 = double2 in global memory, float4 in shared memory).
+template <int MODE, class T, class T2, class S2>
+__global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf, int vf,
+                             const int64_t* __restrict__ grp_prefix, int nblk, int round, int W, T tol,
+                             const double* __restrict__ fro2, double zero_rel, int* __restrict__ rotated) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ int n_rot;
+  const int64_t cta = blockIdx.x;
+  int lo = 0, hi = nblk - 1;   // largest b with grp_prefix[b] <= cta
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (grp_prefix[mid] <= cta) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const int64_t* d = blk + SVF * b;
+  const int p = (int)d[2], r = (int)d[3];
+  const int G = (r + W - 1) / W, Gp = G + (G & 1) < 2 ? 2 : G + (G & 1);
+  if (r == 0 || round >= Gp - 1) return;
+  const int k = (int)(cta - grp_prefix[b]);
+  int gI, gJ;
+  rr_pair(Gp, round, k, gI, gJ);
+  const int nI = gI < G ? min(W, r - gI * W) : 0, nJ = gJ < G ? min(W, r - gJ * W) : 0;
+  if (nI + nJ < 2) return;
+  T2* X = work + d[xf];
+  T2* V = vf >= 0 ? work + d[vf] : nullptr;
+  S2* sx = (S2*)smem_raw;                      // 2W columns of length p
+  S2* sv = sx + (int64_t)2 * W * p;            // 2W columns of length r (V, MODE 0)
+  if (threadIdx.x == 0) n_rot = 0;
+  // float-float columns are staged scaled by a power of two (exact) that brings the block
+  // to unit Frobenius norm, away from the FP32 underflow range
+  const int e2 = MODE == 2 && fro2[b] > 0.0 ? -ilogb(sqrt(fro2[b])) : 0;
+  const double up = ldexp(1.0, e2), down = ldexp(1.0, -e2);
+  // stage: local column c < W is column gI*W + c, c >= W is column gJ*W + c - W
+  for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * p; e += blockDim.x) {
+    const int cc = (int)(e / p), t = (int)(e % p);
+    const int lc = cc < nI ? cc : W + cc - nI;
+    const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
+    const T2 x = X[(int64_t)gc * p + t];
+    if constexpr (MODE == 2) {
+      const FF re = ff_from(x.x * up), im = ff_from(x.y * up);
+      sx[(int64_t)lc * p + t] = make_float4(re.hi, im.hi, re.lo, im.lo);
+    } else {
+      sx[(int64_t)lc * p + t] = x;
+    }
+  }
+  if (V != nullptr)
+    for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * r; e += blockDim.x) {
+      const int cc = (int)(e / r), t = (int)(e % r);
+      const int lc = cc < nI ? cc : W + cc - nI;
+      const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
+      if constexpr (MODE == 0) sv[(int64_t)lc * r + t] = V[(int64_t)gc * r + t];
+    }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double floor2 = zero_rel * fro2[b];
+  int mine = 0;
+  auto do_pair = [&](int i, int j) {
+    bool rot;
+    if constexpr (MODE == 2)
+      rot = jacobi_pair_ff(sx + (int64_t)i * p, sx + (int64_t)j * p, p, (float)tol, (float)(floor2 * up * up), lane);
+    else
+      rot = jacobi_pair<T, T2>(sx + (int64_t)i * p, sx + (int64_t)j * p, p, V ? sv + (int64_t)i * r : nullptr,
+                               V ? sv + (int64_t)j * r : nullptr, r, tol, floor2, lane);
+    if (rot) ++mine;
+  };
+  if (round == 0) {
+    // pairs inside group I (warps 0 .. W/2-1) and inside group J (warps W/2 .. W-1)
+    for (int st = 0; st < W - 1; ++st) {
+      const int grp = warp < W / 2 ? 0 : 1;
+      int i, j;
+      rr_pair(W, st, warp % (W / 2), i, j);
+      const int n = grp ? nJ : nI;
+      if (i < n && j < n) do_pair(grp * W + i, grp * W + j);
+      __syncthreads();
+    }
+  }
+  for (int st = 0; st < W; ++st) {             // cross pairs (I_w, J_{(w + st) mod W})
+    const int i = warp, j = (warp + st) % W;
+    if (i < nI && j < nJ) do_pair(i, W + j);
+    __syncthreads();
+  }
+  if (lane == 0 && mine) atomicAdd(&n_rot, mine);
+  for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * p; e += blockDim.x) {
+    const int cc = (int)(e / p), t = (int)(e % p);
+    const int lc = cc < nI ? cc : W + cc - nI;
+    const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
+    if constexpr (MODE == 2) {
+      const float4 v = sx[(int64_t)lc * p + t];
+      X[(int64_t)gc * p + t] = make_double2(((double)v.x + (double)v.z) * down, ((double)v.y + (double)v.w) * down);
+    } else {
+      X[(int64_t)gc * p + t] = sx[(int64_t)lc * p + t];
+    }
+  }
+  if constexpr (MODE == 0)
+    if (V != nullptr)
+      for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * r; e += blockDim.x) {
+        const int cc = (int)(e / r), t = (int)(e % r);
+        const int lc = cc < nI ? cc : W + cc - nI;
+        const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
+        V[(int64_t)gc * r + t] = sv[(int64_t)lc * r + t];
+      }
+  __syncthreads();
+  if (threadIdx.x == 0 && n_rot) atomicAdd(rotated, n_rot);
 }
 
 // FP32 working copies: X32 (descriptor field 10) from X, V32 (field 11) = identity.
@@ -254,55 +461,87 @@ __global__ void k_svd_sort_values(const int64_t* __restrict__ blk, int nblk, dou
   }
 }
 
-// Global truncation (one CTA): keep[b] = number of kept values of block b; info[0] = scale
-// applied to the kept values (1/sqrt(sum kept s^2)), info[1] = discarded weight
-// (sum of discarded s^2 / total), info[2] = s_max.
-__global__ void k_truncate(const int64_t* __restrict__ blk, int nblk, const double* __restrict__ S_sorted,
-                           int64_t total, int chi, double cutoff, int* __restrict__ keep, double* __restrict__ info,
-                           int* __restrict__ flat_block) {
-  __shared__ double smax_s;
-  const int tid = threadIdx.x;
-  // block of every flat index
-  for (int b = 0; b < nblk; ++b) {
-    const int64_t* d = blk + SVF * b;
-    for (int64_t k = tid; k < d[3]; k += blockDim.x) flat_block[d[8] + k] = b;
+// Global truncation, three launches. keep[b] = number of kept values of block b (the chi
+// largest over all blocks, ties broken by (block, index), and above cutoff * s_max);
+// info[0] = scale applied to the kept values (1/sqrt(sum kept s^2)), info[1] = discarded
+// weight (sum of discarded s^2 / total), info[2] = s_max; info[3] holds s_max as bits while
+// it is being formed (non-negative doubles order like their bit patterns).
+__global__ void k_trunc_prep(const int64_t* __restrict__ blk, int nblk, const double* __restrict__ S_sorted,
+                             int* __restrict__ keep, double* __restrict__ info, int* __restrict__ flat_block) {
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int64_t* d = blk + SVF * b;
+  for (int64_t k = threadIdx.x; k < d[3]; k += blockDim.x) flat_block[d[8] + k] = b;
+  if (threadIdx.x == 0) {
+    keep[b] = 0;
+    if (d[3] > 0)
+      atomicMax((unsigned long long*)&info[3], (unsigned long long)__double_as_longlong(S_sorted[d[8]]));
   }
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-      const int64_t* d = blk + SVF * b;
-      if (d[3] > 0) mx = fmax(mx, S_sorted[d[8]]);
+}
+
+constexpr int kRankTile = 256;
+
+// rank of every value among all values (one thread per value, values staged through shared
+// memory in tiles); a value of rank < chi above the cutoff is kept
+__global__ void __launch_bounds__(kRankTile) k_trunc_rank(const double* __restrict__ S_sorted, int64_t total, int chi,
+                                                          double cutoff, int* __restrict__ keep,
+                                                          const double* __restrict__ info,
+                                                          const int* __restrict__ flat_block) {
+  __shared__ double sv[kRankTile];
+  __shared__ int sb[kRankTile];
+  const int64_t e = blockIdx.x * (int64_t)kRankTile + threadIdx.x;
+  const bool live = e < total;
+  const double v = live ? S_sorted[e] : 0.0;
+  const int be = live ? flat_block[e] : 0;
+  const double smax = __longlong_as_double((long long)__double_as_longlong(info[3]));
+  int64_t rank = 0;
+  for (int64_t f0 = 0; f0 < total; f0 += kRankTile) {
+    const int64_t f = f0 + threadIdx.x;
+    __syncthreads();
+    if (f < total) {
+      sv[threadIdx.x] = S_sorted[f];
+      sb[threadIdx.x] = flat_block[f];
     }
-    smax_s = mx;
-  }
-  for (int b = tid; b < nblk; b += blockDim.x) keep[b] = 0;
-  __syncthreads();
-  const double smax = smax_s;
-  for (int64_t e = tid; e < total; e += blockDim.x) {
-    const double v = S_sorted[e];
-    const int be = flat_block[e];
-    int64_t rank = 0;
-    for (int64_t f = 0; f < total; ++f) {
-      const double w = S_sorted[f];
-      const int bf = flat_block[f];
-      rank += (w > v) || (w == v && (bf < be || (bf == be && f < e)));
-    }
-    if (rank < chi && v > cutoff * smax) atomicAdd(&keep[be], 1);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double kept = 0.0, all = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-      const int64_t* d = blk + SVF * b;
-      for (int64_t k = 0; k < d[3]; ++k) {
-        const double v = S_sorted[d[8] + k];
-        all += v * v;
-        if (k < keep[b]) kept += v * v;
+    __syncthreads();
+    const int n = total - f0 < kRankTile ? (int)(total - f0) : kRankTile;
+    if (live && rank < chi) {
+      for (int q = 0; q < n; ++q) {
+        const double w = sv[q];
+        const int bf = sb[q];
+        rank += (w > v) || (w == v && (bf < be || (bf == be && f0 + q < e)));
       }
     }
-    info[0] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
-    info[1] = all > 0 ? (all - kept) / all : 0.0;
-    info[2] = smax;
+  }
+  if (live && rank < chi && v > cutoff * smax) atomicAdd(&keep[be], 1);
+}
+
+// kept and total weight with a fixed reduction order (one CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) k_trunc_sums(const int64_t* __restrict__ blk, const double* __restrict__ S_sorted,
+                                                     int64_t total, const int* __restrict__ keep,
+                                                     double* __restrict__ info, const int* __restrict__ flat_block) {
+  __shared__ double s_all[1024], s_kept[1024];
+  double all = 0.0, kept = 0.0;
+  for (int64_t e = threadIdx.x; e < total; e += 1024) {
+    const int b = flat_block[e];
+    const double v = S_sorted[e];
+    all += v * v;
+    if (e - blk[SVF * b + 8] < keep[b]) kept += v * v;
+  }
+  s_all[threadIdx.x] = all;
+  s_kept[threadIdx.x] = kept;
+  __syncthreads();
+  for (int h = 512; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      s_all[threadIdx.x] += s_all[threadIdx.x + h];
+      s_kept[threadIdx.x] += s_kept[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double a = s_all[0], k = s_kept[0];
+    info[2] = __longlong_as_double((long long)__double_as_longlong(info[3]));
+    info[0] = k > 0 ? 1.0 / sqrt(k) : 0.0;
+    info[1] = a > 0 ? (a - k) / a : 0.0;
   }
 }
 
@@ -319,23 +558,48 @@ cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* sr
   return cudaGetLastError();
 }
 
-cudaError_t svd_round(double2* work, const int64_t* blk, const int64_t* pair_prefix, int nblk, int64_t npairs,
-                      int round, double tol, const double* fro2, int* rotated, cudaStream_t s) {
-  if (npairs == 0) return cudaSuccess;
-  const int64_t threads = npairs * 32;
-  k_svd_round<double, double2><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(work, blk, 4, -1, pair_prefix,
-                                                                                nblk, round, tol, fro2, 1e-28,
-                                                                                rotated);
+// Shared memory of one CTA of the block rounds for column length p and V length r_v.
+int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32) {
+  return (int64_t)2 * W * (p + r_v) * (f32 ? 8 : 16);
+}
+
+// FP64 (ff = false) or float-float (ff = true) rounds on the FP64 columns X (field 4).
+cudaError_t svd_bround(double2* work, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
+                       int round, int W, int64_t smem, double tol, bool ff, const double* fro2, int* rotated,
+                       cudaStream_t s) {
+  if (ncta == 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_svd_bround<1, double, double2, double2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdMaxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_svd_bround<2, double, double2, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSvdMaxSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (ff)
+    k_svd_bround<2, double, double2, float4><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
+        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated);
+  else
+    k_svd_bround<1, double, double2, double2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
+        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated);
   mrd::count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t svd_round32(float2* w32, const int64_t* blk, const int64_t* pair_prefix, int nblk, int64_t npairs,
-                        int round, float tol, const double* fro2, int* rotated, cudaStream_t s) {
-  if (npairs == 0) return cudaSuccess;
-  const int64_t threads = npairs * 32;
-  k_svd_round<float, float2><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(w32, blk, 10, 11, pair_prefix, nblk,
-                                                                              round, tol, fro2, 1e-12, rotated);
+cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
+                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, cudaStream_t s) {
+  if (ncta == 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_svd_bround<0, float, float2, float2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdMaxSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_svd_bround<0, float, float2, float2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
+      w32, blk, 10, 11, grp_prefix, nblk, round, W, tol, fro2, 1e-12, rotated);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -368,7 +632,17 @@ cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double
 
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
                          int* keep, double* info, int* flat_block, cudaStream_t s) {
-  k_truncate<<<1, 1024, 0, s>>>(blk, nblk, S_sorted, total, chi, cutoff, keep, info, flat_block);
+  if (nblk <= 0) return cudaMemsetAsync(info, 0, 4 * 8, s);
+  cudaError_t e = cudaMemsetAsync(info, 0, 4 * 8, s);
+  if (e != cudaSuccess) return e;
+  k_trunc_prep<<<nblk, 256, 0, s>>>(blk, nblk, S_sorted, keep, info, flat_block);
+  mrd::count_launch();
+  if (total > 0) {
+    k_trunc_rank<<<(unsigned)((total + kRankTile - 1) / kRankTile), kRankTile, 0, s>>>(S_sorted, total, chi, cutoff,
+                                                                                     keep, info, flat_block);
+    mrd::count_launch();
+  }
+  k_trunc_sums<<<1, 1024, 0, s>>>(blk, S_sorted, total, keep, info, flat_block);
   mrd::count_launch();
   return cudaGetLastError();
 }

@@ -32,11 +32,11 @@ def ed_sector(lx, ly, flux, t, v, n, k=None):
     return float(np.linalg.eigvalsh(h)[0])
 
 
-def run_dmrg(ctx, lx, ly, fq, t, v, n, k, chi, basis=0, sweeps=8, seed=7):
+def run_dmrg(ctx, lx, ly, fq, t, v, n, k, chi, basis=0, sweeps=8, seed=7, svd_mode=None):
     import paper_1512_03318_gb300 as P
     mpo = P.MPO(None, lx, ly, 1, fq, t, v, basis)
     d = P.DMRG(ctx, mpo, n, k, chi, seed=seed, center=0)
-    p = P.DMRG.params(chi, 1e-14, 40, 1e-14)
+    p = P.DMRG.params(chi, 1e-14, 40, 1e-14, svd_mode=svd_mode)
     es = []
     for _ in range(sweeps):
         es.append(d.sweep(p))
@@ -65,13 +65,15 @@ def test_dmrg_real_basis_matches_ed(ctx):
     assert abs(es[-1] - e) < 1e-10 * abs(e)
 
 
-def test_dmrg_config1_exact_bond_dimension(ctx):
+@pytest.mark.parametrize("svd_mode", [3, 1, 0, 2])
+def test_dmrg_config1_exact_bond_dimension(ctx, svd_mode):
     """4 x 4 cylinder, flux 1/4, t = V = 1, N = 4: chi = 256 exceeds the largest Schmidt rank
-    (163), so DMRG reaches the ED ground energy of the sector."""
+    (163), so DMRG reaches the ED ground energy of the sector, whatever the arithmetic of the
+    block SVD sweeps (FP64, float-float, FP32 followed by float-float or FP64)."""
     lx, ly, n = 4, 4, 4
     e_ed = [ed_sector(lx, ly, 0.25, 1.0, 1.0, n, k) for k in range(ly)]
     k0 = int(np.argmin(e_ed))
-    es, d = run_dmrg(ctx, lx, ly, 4, 1.0, 1.0, n, k0, 256, sweeps=6)
+    es, d = run_dmrg(ctx, lx, ly, 4, 1.0, 1.0, n, k0, 256, sweeps=6, svd_mode=svd_mode)
     assert abs(es[-1] - e_ed[k0]) < 1e-10 * abs(e_ed[k0])
     assert min(e_ed) == e_ed[k0]
     # the middle bond is not truncated: its total dimension is the exact Schmidt rank bound
@@ -94,3 +96,44 @@ def test_dmrg_free_fermions_closed_form(ctx):
     e0 = model.free_fermion_ground_energy(lx, ly, 1 / 3, 1.0, n)
     best = min(run_dmrg(ctx, lx, ly, 3, 1.0, 0.0, n, k, 64)[0][-1] for k in range(ly))
     assert abs(best - e0) < 1e-10 * abs(e0)
+
+
+def _isometry_error(site, left, right, m, ly):
+    """max |A^+ A - I| over the right-sector blocks of a mode-0 MPS tensor (rows (s, l))."""
+    dl = {(int(a), int(b)): int(c) for a, b, c in left}
+    off, err = 0, 0.0
+    for n_r, k_r, d_r in right:
+        rows = sum(dl.get((int(n_r) - s, (int(k_r) - s * m) % ly), 0) for s in (0, 1))
+        blk = site[off:off + rows * d_r].reshape(rows, d_r)
+        off += rows * d_r
+        err = max(err, float(np.abs(blk.conj().T @ blk - np.eye(d_r)).max()))
+    assert off == site.size
+    return err
+
+
+@pytest.mark.parametrize("prec,svd_mode", [(0, 3), (2, 1), (2, 0), (2, 2)])
+def test_update_canonical_factor_at_production_block_sizes(ctx, prec, svd_mode):
+    """One two-site update at the centre of a 10 x 12 cylinder with chi = 1024 (sector blocks
+    of a few hundred columns, several column groups of the block-cyclic Jacobi): the
+    canonical factor is an isometry to 1e-12, the centre tensor has unit norm and the new bond
+    keeps at most chi states."""
+    import paper_1512_03318_gb300 as P
+    import synth
+    lx, ly, chi = 12, 10, 1024
+    n_sites = lx * ly
+    caps = [[(q[0], q[1], d) for q, d in synth.bond_sectors(chi, ly, round(j / ly), synth.substream(99, 7, j))]
+            if 2 <= j <= n_sites - 2 else [] for j in range(n_sites + 1)]
+    mpo = P.MPO(None, lx, ly, 1, 10, 1.0, 1.0, P.MRD_BASIS_MIXED)
+    i = (lx // 2) * ly + ly // 2 - 1
+    d = P.DMRG(ctx, mpo, lx, 0, chi, seed=5, center=i, caps=caps)
+    p = P.DMRG.params(chi, 1e-14, 30, 1e-10, prec, 1, 1e-13, restarts=4, svd_mode=svd_mode)
+    e, trunc = d.update(i, +1, p)
+    assert math.isfinite(e)
+    mode, a = d.site(i)
+    assert mode == 0
+    assert _isometry_error(a, d.bond(i), d.bond(i + 1), i % ly, ly) < 1e-12
+    _, c = d.site(i + 1)
+    assert abs(np.vdot(c, c).real - 1.0) < 1e-12
+    assert d.bond(i + 1)[:, 2].sum() <= chi
+    assert 0.0 <= trunc < 1e-2
+    d.close()
