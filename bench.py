@@ -41,7 +41,7 @@ LX_UPDATE = 12            # cylinder of the update steps
 LX_MATVEC = 20            # cylinder of the matvec throughput measurement
 SEED = 1234 + 3           # workload index 3 (chi = 3200)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
-PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "ff": 3}
 
 
 def measured_peaks():
@@ -219,7 +219,7 @@ def matvec_throughput(P, ctx, torch, dev, stream, reps=10):
     f_def, f_exec, f1, f2 = h.flops()
     res = {}
     for name, prec in PREC.items():
-        n = reps if prec else 3
+        n = reps if prec in (1, 2) else 3
         for _ in range(2):
             h.apply(T, out, prec=prec)
         torch.cuda.synchronize(dev)
@@ -310,7 +310,8 @@ def main():
 
     # ---- accuracy: mixed form vs converged FP64 reference of the same first H_eff
     ref_state = make_state(P, ctx, mpo, chi, caps, seed)
-    e_ref, _ = ref_state.update(centre, +1, P.DMRG.params(chi, 1e-14, 30, 1e-13, PREC["bf16x3"], 60, 1e-15))
+    e_ref, _ = ref_state.update(centre, +1, P.DMRG.params(chi, 1e-14, 30, 1e-13, PREC["bf16x3"], 60, 1e-15,
+                                                          refine_prec=PREC["fp64"]))
     ref_state.close()
 
     # ---- timed mixed-precision updates (device resident)

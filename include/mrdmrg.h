@@ -58,6 +58,8 @@ extern "C" {
 #define MRD_PREC_FP64 0     /* complex128 operands, FP64 arithmetic                       */
 #define MRD_PREC_TF32 1     /* tcgen05 tensor cores, TF32 operands, FP32 accumulation     */
 #define MRD_PREC_BF16X3 2   /* tcgen05, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accum.   */
+#define MRD_PREC_FF 3       /* complex128 operands split into float-float pairs (~48-bit  */
+                            /* products, TwoSum accumulation) on the FP32 pipes           */
 
 #define MRD_BASIS_MIXED 0   /* orbitals (x, k_m), charges (N, K mod Ly)                   */
 #define MRD_BASIS_REAL 1    /* orbitals (x, y), charge N only (modulus 1)                 */
@@ -131,7 +133,8 @@ int mrd_heff_sizes(const mrd_heff* h, int64_t* theta_len, int64_t* lenv_len, int
  * WR_{w'} = sum_{w''} W_{i+1}[w',w''] R_{w''}; the caller's buffers are not retained. */
 int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev);
 /* theta_out = H_eff theta_in (device pointers, complex128; must not overlap). prec:
- * MRD_PREC_FP64 runs FP64 grouped GEMMs; MRD_PREC_TF32 and MRD_PREC_BF16X3 run the same
+ * MRD_PREC_FP64 runs FP64 grouped GEMMs, MRD_PREC_FF the same grouped GEMMs in float-float
+ * arithmetic (~1e-13 relative); MRD_PREC_TF32 and MRD_PREC_BF16X3 run the same
  * contraction on the tcgen05 tensor cores with FP32 accumulation (complex products as four
  * real ones), operands repacked into 128-byte swizzled tiles: the folded environments once
  * after each mrd_heff_set_env, theta on every call; the result is returned in complex128. */
@@ -180,6 +183,8 @@ typedef struct {
   int32_t lanczos_restarts;  /* extra Lanczos runs restarted from the current ground vector   */
                              /* while the Ritz value still moves by more than lanczos_tol     */
   int32_t svd_mode;          /* MRD_SVD_*: arithmetic of the one-sided Jacobi sweeps          */
+  int32_t refine_prec;       /* MRD_PREC_FP64 or MRD_PREC_FF: arithmetic of the refinement    */
+                             /* matvecs, the environment updates and the GEMMs of the SVD     */
 } mrd_dmrg_params;
 
 /* Block SVD sweep arithmetic. The final sweeps stop when every column pair is orthogonal to

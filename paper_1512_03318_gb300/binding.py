@@ -14,6 +14,7 @@ from . import build as _build
 MRD_PREC_FP64 = 0
 MRD_PREC_TF32 = 1
 MRD_PREC_BF16X3 = 2
+MRD_PREC_FF = 3
 MRD_BASIS_MIXED = 0
 MRD_BASIS_REAL = 1
 MRD_SVD_F32_FF = 0
@@ -253,7 +254,8 @@ class MPO:
 class mrd_dmrg_params(C.Structure):
     _fields_ = [("chi", C.c_int32), ("svd_cutoff", C.c_double), ("lanczos_max_iter", C.c_int32),
                 ("lanczos_tol", C.c_double), ("prec", C.c_int32), ("refine_iter", C.c_int32),
-                ("refine_tol", C.c_double), ("lanczos_restarts", C.c_int32), ("svd_mode", C.c_int32)]
+                ("refine_tol", C.c_double), ("lanczos_restarts", C.c_int32), ("svd_mode", C.c_int32),
+                ("refine_prec", C.c_int32)]
 
 
 class DMRG:
@@ -274,10 +276,15 @@ class DMRG:
 
     @staticmethod
     def params(chi, cutoff=1e-14, max_iter=30, tol=1e-13, prec=MRD_PREC_FP64, refine_iter=0, refine_tol=1e-13,
-               restarts=0, svd_mode=None):
-        if svd_mode is None:   # FP64 updates decompose in FP64, reduced-precision ones in float-float
+               restarts=0, svd_mode=None, refine_prec=None):
+        # FP64 updates stay in FP64 throughout; reduced-precision ones use float-float for the
+        # SVD sweeps, the refinement, the environment updates and the SVD's GEMMs
+        if svd_mode is None:
             svd_mode = MRD_SVD_F64 if prec == MRD_PREC_FP64 else MRD_SVD_FF
-        return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec, refine_iter, refine_tol, restarts, svd_mode)
+        if refine_prec is None:
+            refine_prec = MRD_PREC_FP64 if prec == MRD_PREC_FP64 else MRD_PREC_FF
+        return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec, refine_iter, refine_tol, restarts, svd_mode,
+                               refine_prec)
 
     def update(self, i, direction, params):
         e, t = C.c_double(), C.c_double()

@@ -13,6 +13,8 @@
 
 namespace mrd {
 cudaError_t launch_plan(const PlanDims& d, const PlanPtrs& p, cudaStream_t s);
+cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
+                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
                               const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
                               int n_sm, cudaStream_t s);
@@ -430,7 +432,7 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   if (!h) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   if (!h->env_loaded) return mrd_fail(ctx, MRD_E_STATE, "mrd_heff_apply: environments not loaded");
-  if (prec != MRD_PREC_FP64 && prec != MRD_PREC_TF32 && prec != MRD_PREC_BF16X3)
+  if (prec != MRD_PREC_FP64 && prec != MRD_PREC_TF32 && prec != MRD_PREC_BF16X3 && prec != MRD_PREC_FF)
     return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: unsupported precision");
   const int64_t n = h->counts[C_THETA];
   if (n > 0 && (!theta_in_dev || !theta_out_dev)) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: null theta");
@@ -438,7 +440,8 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   const char* b = (const char*)theta_out_dev;
   if (n > 0 && a < b + n * 16 && b < a + n * 16) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: theta_in and theta_out overlap");
   Guard g(ctx->device);
-  if (prec != MRD_PREC_FP64) return tc_apply(h, theta_in_dev, theta_out_dev, prec);
+  if (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3) return tc_apply(h, theta_in_dev, theta_out_dev, prec);
+  auto gemm = prec == MRD_PREC_FF ? launch_cgemm_ff : launch_cgemm_fp64;
   cudaStream_t s = ctx->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (h->timing) {
@@ -448,12 +451,12 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   cudaError_t e = cudaMemsetAsync(theta_out_dev, 0, (size_t)n * 16, s);
   if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
   if (e == cudaSuccess)
-    e = launch_cgemm_fp64(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1, h->p.seg1, h->p.tile1,
-                          h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s);
+    e = gemm(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1, h->p.seg1, h->p.tile1, h->counts[C_NT1],
+             h->counts[C_TILES1], h->n_sm, s);
   if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
   if (e == cudaSuccess)
-    e = launch_cgemm_fp64(h->z, h->wr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
-                          h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s);
+    e = gemm(h->z, h->wr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2, h->counts[C_NT2],
+             h->counts[C_TILES2], h->n_sm, s);
   if (e == cudaSuccess && e2) e = cudaEventRecord(e2, s);
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply");
   return MRD_OK;
@@ -498,7 +501,7 @@ int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, in
   int it = 0;
   rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr);
   *iters = it;
-  if (rc == MRD_OK && prec != MRD_PREC_FP64) rc = tc_status(h);
+  if (rc == MRD_OK && (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3)) rc = tc_status(h);
   return rc;
 }
 

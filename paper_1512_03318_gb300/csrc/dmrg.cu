@@ -25,6 +25,8 @@
 
 namespace mrd {
 
+cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
+                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
                               const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
                               int n_sm, cudaStream_t s);
@@ -283,6 +285,7 @@ struct mrd_dmrg {
   Buf gtask, gseg, gpref, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
       svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, tbuf, zeros;
   int svd_sweeps32 = 0, svd_sweeps64 = 0;
+  bool gemm_ff = false;   // grouped GEMMs of the update in float-float (refine_prec MRD_PREC_FF)
   double last_energy = 0.0, last_trunc = 0.0;
   int last_iters = 0, last_refine = 0;
   bool timing = false;
@@ -323,8 +326,9 @@ int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const d
   MRD_CUDA(ctx, cudaMemcpyAsync(D->gtask.p, g.t.data(), g.t.size() * 8, cudaMemcpyHostToDevice, s));
   if (!g.s.empty()) MRD_CUDA(ctx, cudaMemcpyAsync(D->gseg.p, g.s.data(), g.s.size() * 8, cudaMemcpyHostToDevice, s));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->gpref.p, pref.data(), pref.size() * 8, cudaMemcpyHostToDevice, s));
-  MRD_CUDA(ctx, launch_cgemm_fp64(Aop, Bop, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
-                                  nt, pref[nt], D->n_sm, s));
+  MRD_CUDA(ctx, (D->gemm_ff ? launch_cgemm_ff : launch_cgemm_fp64)(Aop, Bop, C, D->gtask.as<int64_t>(),
+                                                                   D->gseg.as<int64_t>(), D->gpref.as<int64_t>(), nt,
+                                                                   pref[nt], D->n_sm, s));
   // the host task arrays must stay valid until the copies completed
   MRD_CUDA(ctx, cudaStreamSynchronize(s));
   return MRD_OK;
@@ -936,6 +940,11 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   if (i < 0 || i > D->n - 2) return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: site out of range");
   if (p->svd_mode < MRD_SVD_F32_FF || p->svd_mode > MRD_SVD_F64)
     return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: unknown svd_mode");
+  if (p->refine_prec != MRD_PREC_FP64 && p->refine_prec != MRD_PREC_FF)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: refine_prec must be MRD_PREC_FP64 or MRD_PREC_FF");
+  if (p->prec < MRD_PREC_FP64 || p->prec > MRD_PREC_FF)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: unknown prec");
+  D->gemm_ff = p->refine_prec == MRD_PREC_FF;
   if (!D->L[i].data.p || !D->R[i + 2].data.p)
     return mrd_fail(ctx, MRD_E_STATE, "mrd_two_site_update: environments of this bond are not available");
   Guard g(ctx->device);
@@ -971,7 +980,7 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   int32_t it = 0;
   if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e, &it)) != MRD_OK) return rc;
   D->last_iters = it;
-  collect(p->prec == MRD_PREC_FP64 ? 1 : 0);
+  collect(p->prec == MRD_PREC_FP64 || p->prec == MRD_PREC_FF ? 1 : 0);
   for (int r = 0; r < p->lanczos_restarts && it == p->lanczos_max_iter; ++r) {
     double e2 = 0.0;
     if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e2, &it)) != MRD_OK)
@@ -982,9 +991,9 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
     if (done) break;
   }
   D->last_refine = 0;
-  if (p->prec != MRD_PREC_FP64 && p->refine_iter > 0) {
+  if ((p->prec == MRD_PREC_TF32 || p->prec == MRD_PREC_BF16X3) && p->refine_iter > 0) {
     int32_t it2 = 0;
-    if ((rc = mrd_lanczos(h, (double*)theta, p->refine_iter, p->refine_tol, MRD_PREC_FP64, &e, &it2)) != MRD_OK)
+    if ((rc = mrd_lanczos(h, (double*)theta, p->refine_iter, p->refine_tol, p->refine_prec, &e, &it2)) != MRD_OK)
       return rc;
     D->last_refine = it2;
   }

@@ -1,0 +1,151 @@
+// Grouped complex GEMM in float-float arithmetic (~48-bit products and sums on the FP32 pipes).
+//
+// Same task and segment tables as the FP64 grouped GEMM (plan.cuh: task = M N c_off ldc
+// seg_begin seg_count; segment = a_off lda b_off ldb K flags, flag bit 0: A conjugate-
+// transposed, bit 1: B conjugate-transposed), same result layout (FP64 complex). Operands are
+// read as FP64 and split into float-float pairs when staged in shared memory; every output
+// accumulates its products with exact FMA residuals and TwoSum, renormalised every 16
+// terms, so the result carries ~1e-13 relative error (dot products of up to ~10^4 terms)
+// against ~1e-16 for FP64, at several times the FP64 rate of GB300. Each output block is
+// owned by one task, as in FP64: no atomics, deterministic results.
+#include "ff.cuh"
+#include "mrd_internal.h"
+#include "plan.cuh"
+
+namespace mrd {
+
+namespace {
+
+constexpr int kT = 32;   // output tile (complex elements per side), 2 x 2 per thread
+constexpr int kK = 16;   // K chunk
+
+__device__ __forceinline__ int64_t find_task_ff(const int64_t* prefix, int64_t n, int64_t item) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// complex float-float value (re, im), staged as float4 {re.hi, im.hi, re.lo, im.lo}
+__device__ __forceinline__ float4 cff_from(double2 v) {
+  const FF r = ff_from(v.x), i = ff_from(v.y);
+  return make_float4(r.hi, i.hi, r.lo, i.lo);
+}
+
+struct CAcc {
+  FFAcc re, im;
+};
+
+// c += a * b (complex)
+__device__ __forceinline__ void cff_mac(CAcc& c, float4 a, float4 b) {
+  const FF ar = {a.x, a.z}, ai = {a.y, a.w}, br = {b.x, b.z}, bi = {b.y, b.w};
+  ff_mac(c.re, ar, br);
+  ff_mac(c.re, ff_neg(ai), bi);
+  ff_mac(c.im, ar, bi);
+  ff_mac(c.im, ai, br);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_cgemm_ff(const double2* __restrict__ A, const double2* __restrict__ B,
+                                                  double2* __restrict__ C, const int64_t* __restrict__ tasks,
+                                                  const int64_t* __restrict__ segs,
+                                                  const int64_t* __restrict__ prefix, int64_t n_tasks) {
+  __shared__ float4 As[kT][kK + 1];
+  __shared__ float4 Bs[kK][kT + 1];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int64_t total = prefix[n_tasks];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int64_t t = find_task_ff(prefix, n_tasks, item);
+    const int64_t* task = tasks + TF * t;
+    const int64_t M = task[0], N = task[1], c_off = task[2], ldc = task[3];
+    const int64_t seg0 = task[4], nseg = task[5];
+    const int64_t tiles_n = (N + kT - 1) / kT;
+    const int64_t local = item - prefix[t];
+    const int64_t m0 = (local / tiles_n) * kT, n0 = (local % tiles_n) * kT;
+    CAcc acc[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) acc[i][j] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int64_t s = 0; s < nseg; ++s) {
+      const int64_t* sg = segs + SF * (seg0 + s);
+      const int64_t a_off = sg[0], lda = sg[1], b_off = sg[2], ldb = sg[3], K = sg[4];
+      const int64_t flags = sg[5];
+      for (int64_t k0 = 0; k0 < K; k0 += kK) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int e = tid + r * 256;
+          if (!(flags & 1)) {                           // A[m, k] at a_off + m * lda + k
+            const int ar = e >> 4, ak = e & 15;
+            const int64_t gr = m0 + ar, gk = k0 + ak;
+            As[ar][ak] = cff_from((gr < M && gk < K) ? A[a_off + gr * lda + gk] : make_double2(0.0, 0.0));
+          } else {                                      // A[m, k] = conj(A[a_off + k * lda + m])
+            const int ar = e & 31, ak = e >> 5;
+            const int64_t gr = m0 + ar, gk = k0 + ak;
+            double2 v = (gr < M && gk < K) ? A[a_off + gk * lda + gr] : make_double2(0.0, 0.0);
+            v.y = -v.y;
+            As[ar][ak] = cff_from(v);
+          }
+          if (!(flags & 2)) {                           // B[k, n] at b_off + k * ldb + n
+            const int bk = e >> 5, bc = e & 31;
+            const int64_t gk2 = k0 + bk, gc = n0 + bc;
+            Bs[bk][bc] = cff_from((gk2 < K && gc < N) ? B[b_off + gk2 * ldb + gc] : make_double2(0.0, 0.0));
+          } else {                                      // B[k, n] = conj(B[b_off + n * ldb + k])
+            const int bk = e & 15, bc = e >> 4;
+            const int64_t gk2 = k0 + bk, gc = n0 + bc;
+            double2 v = (gk2 < K && gc < N) ? B[b_off + gc * ldb + gk2] : make_double2(0.0, 0.0);
+            v.y = -v.y;
+            Bs[bk][bc] = cff_from(v);
+          }
+        }
+        __syncthreads();
+        const int kn = K - k0 < kK ? (int)(K - k0) : kK;   // zero padding adds nothing: skip it
+        for (int k = 0; k < kn; ++k) {
+          const float4 a0 = As[2 * ty][k], a1 = As[2 * ty + 1][k];
+          const float4 b0 = Bs[k][2 * tx], b1 = Bs[k][2 * tx + 1];
+          cff_mac(acc[0][0], a0, b0);
+          cff_mac(acc[0][1], a0, b1);
+          cff_mac(acc[1][0], a1, b0);
+          cff_mac(acc[1][1], a1, b1);
+        }
+        // renormalise every accumulator (s, c) <- FastTwoSum(s, c) once per K chunk: the
+        // error term c then holds at most 16 products' residuals, and its own FP32 rounding
+        // stays ~2^-46 of s instead of growing with K
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const FF r = ff_norm(acc[i][j].re), m = ff_norm(acc[i][j].im);
+            acc[i][j].re = {r.hi, r.lo};
+            acc[i][j].im = {m.hi, m.lo};
+          }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int64_t r = m0 + 2 * ty + i, c = n0 + 2 * tx + j;
+        if (r < M && c < N)
+          C[c_off + r * ldc + c] = make_double2((double)acc[i][j].re.s + (double)acc[i][j].re.c,
+                                                (double)acc[i][j].im.s + (double)acc[i][j].im.c);
+      }
+  }
+}
+
+cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
+                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  int64_t grid = (int64_t)n_sm * 8;
+  if (grid > total_tiles) grid = total_tiles;
+  k_cgemm_ff<<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace mrd
