@@ -149,6 +149,16 @@ int mrd_heff_flops(const mrd_heff* h, double* flops4);
  * the recorded work, returns the summed durations in ms of the step-1 and step-2 launches
  * and the number of applies recorded, and clears the record. */
 int mrd_heff_timing(mrd_heff* h, int32_t on);
+/* Execution options of an H_eff (value per option; returns MRD_E_ARG for an unknown option):
+ *   MRD_OPT_GRAPH           1 (default): mrd_lanczos captures one Lanczos step (matvec,
+ *                           reorthogonalisation, tridiagonal solve) as a CUDA graph and
+ *                           replays it; 0: launches every kernel of every step.
+ *   MRD_OPT_PER_TASK_LAUNCH 0 (default): each GEMM step of mrd_heff_apply is one grouped
+ *                           persistent launch over all charge blocks; 1: one launch per task
+ *                           (output block), the per-block baseline the grouped launch replaces. */
+#define MRD_OPT_GRAPH 1
+#define MRD_OPT_PER_TASK_LAUNCH 2
+int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value);
 int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls);
 
 /* ------------------------------------------------------------------ eigensolver */

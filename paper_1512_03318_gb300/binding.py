@@ -17,6 +17,8 @@ MRD_PREC_BF16X3 = 2
 MRD_PREC_FF = 3
 MRD_BASIS_MIXED = 0
 MRD_BASIS_REAL = 1
+MRD_OPT_GRAPH = 1
+MRD_OPT_PER_TASK_LAUNCH = 2
 MRD_SVD_F32_FF = 0
 MRD_SVD_FF = 1
 MRD_SVD_F32_F64 = 2
@@ -116,6 +118,7 @@ _SIGS = {
     "mrd_dmrg_set_site": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "mrd_dmrg_timing": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mrd_heff_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
 }
@@ -401,6 +404,10 @@ class Heff:
 
     def set_env(self, lenv, renv):
         self.ctx.check(lib().mrd_heff_set_env(self.h, _ptr(lenv), _ptr(renv)))
+
+    def set_option(self, option, value):
+        """mrd_heff_set_option (MRD_OPT_GRAPH, MRD_OPT_PER_TASK_LAUNCH)."""
+        self.ctx.check(lib().mrd_heff_set_option(self.h, option, int(value)))
 
     def apply(self, theta_in, theta_out, prec=MRD_PREC_FP64):
         self.ctx.check(lib().mrd_heff_apply(self.h, _ptr(theta_in), _ptr(theta_out), prec))

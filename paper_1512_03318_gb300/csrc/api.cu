@@ -13,8 +13,10 @@
 
 namespace mrd {
 cudaError_t launch_plan(const PlanDims& d, const PlanPtrs& p, cudaStream_t s);
-cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
-                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s);
+cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
+                                   const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                                   int n_sm, cudaStream_t s);
+cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
                               const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
                               int n_sm, cudaStream_t s);
@@ -23,9 +25,9 @@ cudaError_t launch_fold_env(const double2* env, double2* out, const int64_t* row
                             const double* val, int chan_field, cudaStream_t s);
 struct Lanczos;
 void lanczos_free(Lanczos* L);
-cudaError_t lanczos_alloc(Lanczos** out, int64_t n);
+cudaError_t lanczos_alloc(Lanczos** out, int64_t n, cudaStream_t stream);
 int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, double2*), void* op, double2* theta,
-                int max_iter, double tol, double* energy, int* iters, double* beta_last);
+                int max_iter, double tol, double* energy, int* iters, double* beta_last, uint64_t graph_key);
 int vdot(Lanczos* L, mrd_ctx* ctx, const double2* u, const double2* v, double* re, double* im);
 double2* lanczos_work(Lanczos* L);
 }  // namespace mrd
@@ -35,6 +37,9 @@ using namespace mrd;
 namespace mrd {
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(int64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+int64_t launch_count_total() { return g_launches.load(); }
 }  // namespace mrd
 
 void mrd_ctx_retain(mrd_ctx* ctx) {
@@ -216,6 +221,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
   d.scratch_len = sl + 1;
 
   Arena& A = h->plan_mem;
+  A.stream = ctx->stream;
   PlanPtrs& p = h->p;
   int32_t *left = nullptr, *right = nullptr, *cl = nullptr, *cm = nullptr, *cr = nullptr, *wi = nullptr, *wj = nullptr;
   cudaError_t e = cudaSuccess;
@@ -321,6 +327,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
     }
   }
   Arena& B = h->data_mem;
+  B.stream = ctx->stream;
   if (e == cudaSuccess) e = B.alloc(&h->lw, (size_t)h->counts[C_LWLEN]);
   if (e == cudaSuccess) e = B.alloc(&h->wr, (size_t)h->counts[C_WRLEN]);
   if (e == cudaSuccess) e = B.alloc(&h->z, (size_t)h->counts[C_ZLEN]);
@@ -425,6 +432,73 @@ int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_set_env");
   h->env_loaded = true;
   tc_env_changed(h);
+  h->ff_dirty = true;
+  return MRD_OK;
+}
+
+// Per-task launch tables of the FP64 / float-float GEMM steps (32 x 32 tiles).
+static int ensure_per_task(mrd_heff* h) {
+  if (h->pt_pref1) return MRD_OK;
+  mrd_ctx* ctx = h->ctx;
+  const int64_t n1 = h->counts[C_NT1], n2 = h->counts[C_NT2];
+  std::vector<int64_t> p1(2 * std::max<int64_t>(n1, 1), 0), p2(2 * std::max<int64_t>(n2, 1), 0);
+  h->pt_tiles1.assign(n1, 0);
+  h->pt_tiles2.assign(n2, 0);
+  for (int64_t t = 0; t < n1; ++t) {
+    const int64_t* r = &h->t1_host[TF * t];
+    h->pt_tiles1[t] = r[5] > 0 ? ((r[0] + 31) / 32) * ((r[1] + 31) / 32) : 0;
+    p1[2 * t + 1] = h->pt_tiles1[t];
+  }
+  for (int64_t t = 0; t < n2; ++t) {
+    const int64_t* r = &h->t2_host[TF * t];
+    h->pt_tiles2[t] = r[5] > 0 ? ((r[0] + 31) / 32) * ((r[1] + 31) / 32) : 0;
+    p2[2 * t + 1] = h->pt_tiles2[t];
+  }
+  Arena& A = h->pt_mem;
+  A.stream = ctx->stream;
+  int64_t *d1 = nullptr, *d2 = nullptr;
+  cudaError_t e = A.alloc(&d1, p1.size());
+  if (e == cudaSuccess) e = A.alloc(&d2, p2.size());
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d1, p1.data(), p1.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d2, p2.data(), p2.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "per-task launch tables");
+  h->pt_pref1 = d1;
+  h->pt_pref2 = d2;
+  ++h->gen;
+  return MRD_OK;
+}
+
+// Everything an application of `prec` needs beyond launching its kernels: tensor-core panel
+// tables and packed environments, float-float copies of the folded environments. Allocates
+// and may synchronise; a no-op once done (until the environments or the precision change).
+// h->gen counts the (re)allocations, which invalidate captured Lanczos steps.
+static int heff_prepare(mrd_heff* h, int32_t prec) {
+  mrd_ctx* ctx = h->ctx;
+  cudaStream_t s = ctx->stream;
+  if (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3) return tc_prepare(h, prec);
+  if (h->per_task) {
+    int rc = ensure_per_task(h);
+    if (rc != MRD_OK) return rc;
+  }
+  if (prec != MRD_PREC_FF) return MRD_OK;
+  // float-float operands: LW and WR converted once per environment load, theta per call;
+  // Z is written and read in float-float (it reuses the FP64 Z buffer: 16 bytes either way)
+  if (!h->lw_ff) {
+    Arena& A = h->ff_mem;
+    A.stream = s;
+    cudaError_t e = A.alloc(&h->lw_ff, (size_t)std::max<int64_t>(h->counts[C_LWLEN], 1));
+    if (e == cudaSuccess) e = A.alloc(&h->wr_ff, (size_t)std::max<int64_t>(h->counts[C_WRLEN], 1));
+    if (e == cudaSuccess) e = A.alloc(&h->th_ff, (size_t)std::max<int64_t>(h->counts[C_THETA], 1));
+    if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply: float-float buffers");
+    h->ff_dirty = true;
+    ++h->gen;
+  }
+  if (h->ff_dirty) {
+    MRD_CUDA(ctx, to_ff(h->lw, h->lw_ff, h->counts[C_LWLEN], s));
+    MRD_CUDA(ctx, to_ff(h->wr, h->wr_ff, h->counts[C_WRLEN], s));
+    h->ff_dirty = false;
+  }
   return MRD_OK;
 }
 
@@ -441,7 +515,8 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   if (n > 0 && a < b + n * 16 && b < a + n * 16) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_apply: theta_in and theta_out overlap");
   Guard g(ctx->device);
   if (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3) return tc_apply(h, theta_in_dev, theta_out_dev, prec);
-  auto gemm = prec == MRD_PREC_FF ? launch_cgemm_ff : launch_cgemm_fp64;
+  int rc = heff_prepare(h, prec);
+  if (rc != MRD_OK) return rc;
   cudaStream_t s = ctx->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (h->timing) {
@@ -449,14 +524,51 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
     if (!e0 || !e1 || !e2) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
   }
   cudaError_t e = cudaMemsetAsync(theta_out_dev, 0, (size_t)n * 16, s);
-  if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
-  if (e == cudaSuccess)
-    e = gemm(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1, h->p.seg1, h->p.tile1, h->counts[C_NT1],
-             h->counts[C_TILES1], h->n_sm, s);
-  if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
-  if (e == cudaSuccess)
-    e = gemm(h->z, h->wr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2, h->counts[C_NT2],
-             h->counts[C_TILES2], h->n_sm, s);
+  if (prec == MRD_PREC_FF) {
+    float4* z_ff = (float4*)h->z;
+    if (e == cudaSuccess) e = to_ff((const double2*)theta_in_dev, h->th_ff, n, s);
+    if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
+    if (!h->per_task) {
+      if (e == cudaSuccess)
+        e = launch_cgemm_ff_packed(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1, h->p.seg1, h->p.tile1,
+                                   h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s);
+      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess)
+        e = launch_cgemm_ff_packed(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
+                                   h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s);
+    } else {
+      for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT1]; ++t)
+        if (h->pt_tiles1[t])
+          e = launch_cgemm_ff_packed(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1 + TF * t, h->p.seg1,
+                                     h->pt_pref1 + 2 * t, 1, h->pt_tiles1[t], h->n_sm, s);
+      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT2]; ++t)
+        if (h->pt_tiles2[t])
+          e = launch_cgemm_ff_packed(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2 + TF * t, h->p.seg2,
+                                     h->pt_pref2 + 2 * t, 1, h->pt_tiles2[t], h->n_sm, s);
+    }
+  } else {
+    if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
+    if (!h->per_task) {
+      if (e == cudaSuccess)
+        e = launch_cgemm_fp64(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1, h->p.seg1, h->p.tile1,
+                              h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s);
+      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess)
+        e = launch_cgemm_fp64(h->z, h->wr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
+                              h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s);
+    } else {
+      for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT1]; ++t)
+        if (h->pt_tiles1[t])
+          e = launch_cgemm_fp64(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1 + TF * t, h->p.seg1,
+                                h->pt_pref1 + 2 * t, 1, h->pt_tiles1[t], h->n_sm, s);
+      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT2]; ++t)
+        if (h->pt_tiles2[t])
+          e = launch_cgemm_fp64(h->z, h->wr, (double2*)theta_out_dev, h->p.t2 + TF * t, h->p.seg2,
+                                h->pt_pref2 + 2 * t, 1, h->pt_tiles2[t], h->n_sm, s);
+    }
+  }
   if (e == cudaSuccess && e2) e = cudaEventRecord(e2, s);
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply");
   return MRD_OK;
@@ -483,7 +595,7 @@ static int apply_cb(void* op, const double2* in, double2* out) {
 
 static int ensure_lanczos(mrd_heff* h) {
   if (h->lz) return MRD_OK;
-  cudaError_t e = lanczos_alloc(&h->lz, h->counts[C_THETA]);
+  cudaError_t e = lanczos_alloc(&h->lz, h->counts[C_THETA], h->ctx->stream);
   if (e != cudaSuccess) return mrd_cuda_fail(h->ctx, e, "Lanczos workspace");
   return MRD_OK;
 }
@@ -497,9 +609,15 @@ int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, in
   Guard g(ctx->device);
   int rc = ensure_lanczos(h);
   if (rc != MRD_OK) return rc;
+  if (prec != MRD_PREC_FP64 && prec != MRD_PREC_TF32 && prec != MRD_PREC_BF16X3 && prec != MRD_PREC_FF)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_lanczos: unsupported precision");
+  if ((rc = heff_prepare(h, prec)) != MRD_OK) return rc;
   ApplyArg arg{h, prec};
   int it = 0;
-  rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr);
+  // one Lanczos step is captured as a CUDA graph and replayed (not while GEMM timing records
+  // events); the key changes whenever the operator's buffers are reallocated
+  const uint64_t key = h->use_graph && !h->timing ? ((uint64_t)h->gen << 8 | (uint64_t)(prec + 1)) : 0;
+  rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr, key);
   *iters = it;
   if (rc == MRD_OK && (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3)) rc = tc_status(h);
   return rc;
@@ -527,6 +645,20 @@ int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double
     // |Hv - E v|^2 = <Hv,Hv> - 2 E Re<v,Hv> + E^2 <v,v>
     double r2 = hh - 2.0 * e * en + e * e * nn;
     *residual = std::sqrt(r2 > 0 ? r2 : 0.0) / std::sqrt(nn);
+  }
+  return MRD_OK;
+}
+
+int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) {
+  if (!h) return MRD_E_ARG;
+  if (option == MRD_OPT_GRAPH) {
+    h->use_graph = value != 0;
+  } else if (option == MRD_OPT_PER_TASK_LAUNCH) {
+    h->per_task = value != 0;
+    if (h->tc) tc_env_changed(h);   // tensor-core per-task tables are built with the panels
+    ++h->gen;
+  } else {
+    return mrd_fail(h->ctx, MRD_E_ARG, "mrd_heff_set_option: unknown option");
   }
   return MRD_OK;
 }

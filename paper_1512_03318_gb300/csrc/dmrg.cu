@@ -33,9 +33,11 @@ cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, co
 cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* src_off, int nblk, double2* work,
                      double* fro2, cudaStream_t s);
 int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
-cudaError_t svd_bround(double2* work, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
-                       int round, int W, int64_t smem, double tol, bool ff, const double* fro2, int* rotated,
+cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
+                       int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
                        cudaStream_t s);
+cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
+                      cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
                        double* S_sorted, int* order_scratch, const double* fro2, cudaStream_t s);
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
@@ -524,8 +526,8 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
           MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f, fro,
                                      rot, s));
         else
-          MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), dblk, pre64, nb, sc.ncta, rd, sc.W, sc.smem,
-                                   ff ? kTolFF : kTolF64, ff, fro, rot, s));
+          MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, nb,
+                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, s));
       }
       int hrot = 0;
       MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
@@ -560,8 +562,12 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_work.p, D->svd_x2.p, (size_t)xlen * 16, cudaMemcpyDeviceToDevice, s));
   }
   }
+  // float-float sweeps work on a float-float copy of X in svd_x2 (16 bytes per element either way)
+  const bool ffm = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
+  if (ffm) MRD_CUDA(ctx, svd_ff_io(D->svd_work.as<double2>(), D->svd_x2.as<float4>(), dblk, nb, fro, true, s));
   rc = sweep_until_done(false, kMaxSweeps64, &D->svd_sweeps64);
   if (rc != MRD_OK) return rc;
+  if (ffm) MRD_CUDA(ctx, svd_ff_io(D->svd_work.as<double2>(), D->svd_x2.as<float4>(), dblk, nb, fro, false, s));
   MRD_CUDA(ctx, svd_finish(D->svd_work.as<double2>(), dblk, nb, D->svd_u.as<double2>(), D->svd_vh.as<double2>(),
                            D->svd_s.as<double>(), D->svd_ss.as<double>(), D->svd_ord.as<int>(), fro, s));
   MRD_CUDA(ctx, svd_truncate(dblk, nb, D->svd_ss.as<double>(), slen, chi, cutoff, D->svd_keep.as<int>(),

@@ -38,6 +38,28 @@ struct CAcc {
   FFAcc re, im;
 };
 
+// operand element as staged float-float: FP64 operands are split on load, float-float
+// operands (float4 {re.hi, im.hi, re.lo, im.lo}, prepared once) are read as they are
+__device__ __forceinline__ float4 ld_op(const double2* p, int64_t i, bool conj) {
+  if (i < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+  double2 v = p[i];
+  if (conj) v.y = -v.y;
+  return cff_from(v);
+}
+__device__ __forceinline__ float4 ld_op(const float4* p, int64_t i, bool conj) {
+  if (i < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 v = p[i];
+  if (conj) { v.y = -v.y; v.w = -v.w; }
+  return v;
+}
+__device__ __forceinline__ void st_out(double2* c, int64_t i, const CAcc& a) {
+  c[i] = make_double2((double)a.re.s + (double)a.re.c, (double)a.im.s + (double)a.im.c);
+}
+__device__ __forceinline__ void st_out(float4* c, int64_t i, const CAcc& a) {
+  const FF r = ff_norm(a.re), m = ff_norm(a.im);
+  c[i] = make_float4(r.hi, m.hi, r.lo, m.lo);
+}
+
 // c += a * b (complex)
 __device__ __forceinline__ void cff_mac(CAcc& c, float4 a, float4 b) {
   const FF ar = {a.x, a.z}, ai = {a.y, a.w}, br = {b.x, b.z}, bi = {b.y, b.w};
@@ -49,8 +71,9 @@ __device__ __forceinline__ void cff_mac(CAcc& c, float4 a, float4 b) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_cgemm_ff(const double2* __restrict__ A, const double2* __restrict__ B,
-                                                  double2* __restrict__ C, const int64_t* __restrict__ tasks,
+template <class TA, class TB, class TC>
+__global__ void __launch_bounds__(256) k_cgemm_ff(const TA* __restrict__ A, const TB* __restrict__ B,
+                                                  TC* __restrict__ C, const int64_t* __restrict__ tasks,
                                                   const int64_t* __restrict__ segs,
                                                   const int64_t* __restrict__ prefix, int64_t n_tasks) {
   __shared__ float4 As[kT][kK + 1];
@@ -82,24 +105,20 @@ __global__ void __launch_bounds__(256) k_cgemm_ff(const double2* __restrict__ A,
           if (!(flags & 1)) {                           // A[m, k] at a_off + m * lda + k
             const int ar = e >> 4, ak = e & 15;
             const int64_t gr = m0 + ar, gk = k0 + ak;
-            As[ar][ak] = cff_from((gr < M && gk < K) ? A[a_off + gr * lda + gk] : make_double2(0.0, 0.0));
+            As[ar][ak] = ld_op(A, (gr < M && gk < K) ? a_off + gr * lda + gk : -1, false);
           } else {                                      // A[m, k] = conj(A[a_off + k * lda + m])
             const int ar = e & 31, ak = e >> 5;
             const int64_t gr = m0 + ar, gk = k0 + ak;
-            double2 v = (gr < M && gk < K) ? A[a_off + gk * lda + gr] : make_double2(0.0, 0.0);
-            v.y = -v.y;
-            As[ar][ak] = cff_from(v);
+            As[ar][ak] = ld_op(A, (gr < M && gk < K) ? a_off + gk * lda + gr : -1, true);
           }
           if (!(flags & 2)) {                           // B[k, n] at b_off + k * ldb + n
             const int bk = e >> 5, bc = e & 31;
             const int64_t gk2 = k0 + bk, gc = n0 + bc;
-            Bs[bk][bc] = cff_from((gk2 < K && gc < N) ? B[b_off + gk2 * ldb + gc] : make_double2(0.0, 0.0));
+            Bs[bk][bc] = ld_op(B, (gk2 < K && gc < N) ? b_off + gk2 * ldb + gc : -1, false);
           } else {                                      // B[k, n] = conj(B[b_off + n * ldb + k])
             const int bk = e & 15, bc = e >> 4;
             const int64_t gk2 = k0 + bk, gc = n0 + bc;
-            double2 v = (gk2 < K && gc < N) ? B[b_off + gc * ldb + gk2] : make_double2(0.0, 0.0);
-            v.y = -v.y;
-            Bs[bk][bc] = cff_from(v);
+            Bs[bk][bc] = ld_op(B, (gk2 < K && gc < N) ? b_off + gc * ldb + gk2 : -1, true);
           }
         }
         __syncthreads();
@@ -131,19 +150,45 @@ __global__ void __launch_bounds__(256) k_cgemm_ff(const double2* __restrict__ A,
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int64_t r = m0 + 2 * ty + i, c = n0 + 2 * tx + j;
-        if (r < M && c < N)
-          C[c_off + r * ldc + c] = make_double2((double)acc[i][j].re.s + (double)acc[i][j].re.c,
-                                                (double)acc[i][j].im.s + (double)acc[i][j].im.c);
+        if (r < M && c < N) st_out(C, c_off + r * ldc + c, acc[i][j]);
       }
   }
 }
 
-cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
-                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
+// x (FP64 complex) -> float-float operand layout
+__global__ void k_to_ff(const double2* __restrict__ x, float4* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = cff_from(x[i]);
+}
+
+template <class TA, class TB, class TC>
+static cudaError_t launch_ff(const TA* A, const TB* B, TC* C, const int64_t* tasks, const int64_t* segs,
+                             const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   int64_t grid = (int64_t)n_sm * 8;
   if (grid > total_tiles) grid = total_tiles;
-  k_cgemm_ff<<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks);
+  k_cgemm_ff<TA, TB, TC><<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
+                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
+  return launch_ff(A, B, C, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s);
+}
+
+// operands already in float-float layout; result in float-float (c_ff) or FP64 (c64)
+cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
+                                   const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                                   int n_sm, cudaStream_t s) {
+  if (c_ff) return launch_ff(A, B, c_ff, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s);
+  return launch_ff(A, B, c64, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s);
+}
+
+cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_to_ff<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(x, y, n);
   mrd::count_launch();
   return cudaGetLastError();
 }

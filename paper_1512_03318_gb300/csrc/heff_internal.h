@@ -13,6 +13,7 @@ struct Tc;
 void tc_free(Tc* t);
 struct mrd_heff;
 int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec);
+int tc_prepare(mrd_heff* h, int32_t prec);
 void tc_env_changed(mrd_heff* h);
 int tc_status(mrd_heff* h);
 using mrd::Lanczos;
@@ -23,20 +24,20 @@ using namespace mrd;
 
 namespace mrd {
 
-// Device arena: a list of allocations freed together.
+// Device arena: a list of allocations freed together, through the library's memory cache
+// (released blocks are reused by later arenas on the same stream).
 struct Arena {
   std::vector<void*> ptrs;
+  cudaStream_t stream = nullptr;   // stream of the work that uses the arena's memory
   ~Arena() { release(); }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cache_free(p, stream);
     ptrs.clear();
   }
   template <class T>
   cudaError_t alloc(T** out, size_t count) {
     void* p = nullptr;
-    size_t bytes = count * sizeof(T);
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = cache_alloc(&p, count * sizeof(T), stream);
     if (e != cudaSuccess) return e;
     ptrs.push_back(p);
     *out = (T*)p;
@@ -90,6 +91,20 @@ struct mrd_heff {
   std::vector<int64_t> mid_host, lw_host, wr_host, lmap_host, rmap_host, t1_host, s1_host, t2_host, s2_host;
   // tensor-core path state (tc_host.cu)
   struct Tc* tc = nullptr;
+  // float-float path: LW, WR in float-float layout (prepared after each environment load) and
+  // theta staging
+  Arena ff_mem;
+  float4 *lw_ff = nullptr, *wr_ff = nullptr, *th_ff = nullptr;
+  bool ff_dirty = true;
+  uint64_t gen = 1;          // bumped when apply buffers are reallocated (captured graphs go stale)
+  bool use_graph = true;     // capture Lanczos steps as CUDA graphs (MRD_OPT_GRAPH)
+  bool per_task = false;     // one GEMM launch per task (MRD_OPT_PER_TASK_LAUNCH)
+  // per-task launches: [0, tiles of task t] for every task of step 1 and step 2 (device),
+  // tiles per task (host), for the FP64 / float-float tiles and for the tensor-core tiles
+  Arena pt_mem;
+  int64_t* pt_pref1 = nullptr;
+  int64_t* pt_pref2 = nullptr;
+  std::vector<int64_t> pt_tiles1, pt_tiles2;
   ~mrd_heff() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);

@@ -434,6 +434,17 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
   }
 }
 
+// Kernel attributes (dynamic shared memory above 48 KB); called before any capture.
+cudaError_t tc_gemm_init() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int prec, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   k_pack<<<njobs < 8192 ? njobs : 8192, 256, 0, s>>>(src, dst, jobs, njobs, prec);
@@ -445,12 +456,8 @@ cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t*
                     const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
                     int prec, int* err, int n_sm, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t ea = tc_gemm_init();
+  if (ea != cudaSuccess) return ea;
   TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
   k_tc_gemm<<<(unsigned)grid, 192, kTcSmemBytes, s>>>(g);

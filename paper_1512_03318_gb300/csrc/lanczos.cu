@@ -30,59 +30,96 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Device state of one Lanczos run. j is the current step: the kernels of a step read it,
+// so that one captured CUDA graph of a step serves every step.
+struct LzState {
+  double alpha[MRD_LANCZOS_MAX_ITER + 1];
+  double beta[MRD_LANCZOS_MAX_ITER + 1];
+  double y[MRD_LANCZOS_MAX_ITER + 1];
+  double energy;
+  double beta_last;
+  int flags;
+  int j;
+};
+
+// number of vectors of a reduction: nv >= 0 as given, nv < 0 means v_0 .. v_j of the state
+__device__ __forceinline__ int eff_nv(int nv, const LzState* st) { return nv >= 0 ? nv : st->j + 1; }
+
+constexpr int kJB = 4;   // vectors per pass of k_multidot (w is read once per pass)
+
 // partial[b * nv + j] = sum over this CTA's share of conj(V_j) . w, j < nv (re, im interleaved)
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const double2* __restrict__ V, int64_t ldv, int nv,
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const double2* __restrict__ V, int64_t ldv, int nv_arg,
+                                                          const LzState* __restrict__ st,
                                                           const double2* __restrict__ w, int64_t n,
                                                           double2* __restrict__ partial) {
-  __shared__ double sre[kRedThreads / 32], sim[kRedThreads / 32];
+  __shared__ double sre[kJB][kRedThreads / 32], sim[kJB][kRedThreads / 32];
+  const int nv = eff_nv(nv_arg, st);
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b = blockIdx.x * chunk;
   const int64_t e = b + chunk < n ? b + chunk : n;
-  for (int j = 0; j < nv; ++j) {
-    const double2* v = V + (int64_t)j * ldv;
-    double re = 0.0, im = 0.0;
+  for (int j0 = 0; j0 < nv; j0 += kJB) {
+    double re[kJB], im[kJB];
+#pragma unroll
+    for (int q = 0; q < kJB; ++q) re[q] = im[q] = 0.0;
     for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-      const double2 x = v[i], y = w[i];
-      re = fma(x.x, y.x, re);
-      re = fma(x.y, y.y, re);
-      im = fma(x.x, y.y, im);
-      im = fma(-x.y, y.x, im);
+      const double2 y = w[i];
+#pragma unroll
+      for (int q = 0; q < kJB; ++q) {
+        if (j0 + q < nv) {
+          const double2 x = V[(int64_t)(j0 + q) * ldv + i];
+          re[q] = fma(x.x, y.x, re[q]);
+          re[q] = fma(x.y, y.y, re[q]);
+          im[q] = fma(x.x, y.y, im[q]);
+          im[q] = fma(-x.y, y.x, im[q]);
+        }
+      }
     }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if ((threadIdx.x & 31) == 0) {
-      sre[threadIdx.x >> 5] = re;
-      sim[threadIdx.x >> 5] = im;
+#pragma unroll
+    for (int q = 0; q < kJB; ++q) {
+      re[q] = warp_sum(re[q]);
+      im[q] = warp_sum(im[q]);
+      if ((threadIdx.x & 31) == 0) {
+        sre[q][threadIdx.x >> 5] = re[q];
+        sim[q][threadIdx.x >> 5] = im[q];
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < kJB && j0 + (int)threadIdx.x < nv) {
+      const int q = threadIdx.x;
       double a = 0.0, c = 0.0;
       for (int k = 0; k < kRedThreads / 32; ++k) {
-        a += sre[k];
-        c += sim[k];
+        a += sre[q][k];
+        c += sim[q][k];
       }
-      partial[(int64_t)blockIdx.x * nv + j] = make_double2(a, c);
+      partial[(int64_t)blockIdx.x * nv + j0 + q] = make_double2(a, c);
     }
     __syncthreads();
   }
 }
 
-// out[j] = sum_b partial[b * nv + j]; one thread per j, fixed order.
-__global__ void k_finish_dots(const double2* __restrict__ partial, int nblocks, int nv, double2* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// out[j] = sum_b partial[b * nv + j]; one warp per j, fixed order (lane-strided sums, then
+// a shuffle tree).
+__global__ void k_finish_dots(const double2* __restrict__ partial, int nblocks, int nv_arg,
+                              const LzState* __restrict__ st, double2* __restrict__ out) {
+  const int nv = eff_nv(nv_arg, st);
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (j >= nv) return;
   double a = 0.0, c = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
+  for (int b = lane; b < nblocks; b += 32) {
     const double2 p = partial[(int64_t)b * nv + j];
     a += p.x;
     c += p.y;
   }
-  out[j] = make_double2(a, c);
+  a = warp_sum(a);
+  c = warp_sum(c);
+  if (lane == 0) out[j] = make_double2(a, c);
 }
 
 // w -= sum_j c[j] V_j
-__global__ void k_sub_combination(const double2* __restrict__ V, int64_t ldv, int nv, const double2* __restrict__ c,
+__global__ void k_sub_combination(const double2* __restrict__ V, int64_t ldv, int nv_arg,
+                                  const LzState* __restrict__ st, const double2* __restrict__ c,
                                   double2* __restrict__ w, int64_t n) {
+  const int nv = eff_nv(nv_arg, st);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double2 acc = w[i];
     for (int j = 0; j < nv; ++j) {
@@ -119,23 +156,38 @@ __global__ void k_scale_by_invnorm(const double2* __restrict__ src, double2* __r
 }
 
 // Lanczos bookkeeping after the two Gram-Schmidt passes of step j (single thread):
-// alpha_j += Re(c1_j) + Re(c2_j) is accumulated in state.
-struct LzState {
-  double alpha[MRD_LANCZOS_MAX_ITER + 1];
-  double beta[MRD_LANCZOS_MAX_ITER + 1];
-  double y[MRD_LANCZOS_MAX_ITER + 1];
-  double energy;
-  double beta_last;
-  int flags;
-};
-
-__global__ void k_record_alpha(LzState* st, int j, const double2* __restrict__ c1, const double2* __restrict__ c2) {
+// alpha_j = Re(c1_j) + Re(c2_j).
+__global__ void k_record_alpha(LzState* st, const double2* __restrict__ c1, const double2* __restrict__ c2) {
+  const int j = st->j;
   st->alpha[j] = c1[j].x + c2[j].x;
 }
 
-__global__ void k_record_beta(LzState* st, int j, const double2* __restrict__ nrm2) {
+__global__ void k_record_beta(LzState* st, const double2* __restrict__ nrm2) {
+  const int j = st->j;
   st->beta[j] = sqrt(nrm2->x);
   st->beta_last = st->beta[j];
+}
+
+__global__ void k_set_step(LzState* st, int j) { st->j = j; }
+__global__ void k_next_step(LzState* st) { st->j += 1; }
+
+// vin = v_j (j read from the state: one captured iteration serves every j)
+__global__ void k_copy_vj(const double2* __restrict__ V, int64_t n, const LzState* __restrict__ st,
+                          double2* __restrict__ vin) {
+  const double2* v = V + (int64_t)st->j * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    vin[i] = v[i];
+}
+
+// v_{j+1} = w / |w|
+__global__ void k_scale_next(const double2* __restrict__ w, double2* __restrict__ V, int64_t n,
+                             const double2* __restrict__ nrm2, const LzState* __restrict__ st) {
+  const double sc = nrm2->x > 0.0 ? 1.0 / sqrt(nrm2->x) : 0.0;
+  double2* dst = V + (int64_t)(st->j + 1) * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = w[i];
+    dst[i] = make_double2(v.x * sc, v.y * sc);
+  }
 }
 
 __device__ int sturm_count(const double* a, const double* b, int k, double x) {
@@ -151,8 +203,9 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
   return cnt;
 }
 
-// Lowest eigenpair of the k x k tridiagonal Lanczos matrix; one warp.
-__global__ void k_tridiag_lowest(LzState* st, int k) {
+// Lowest eigenpair of the k x k tridiagonal Lanczos matrix, k = j + 1; one warp.
+__global__ void k_tridiag_lowest(LzState* st) {
+  const int k = st->j + 1;
   const double* a = st->alpha;
   const double* b = st->beta;
   const int lane = threadIdx.x;
@@ -260,34 +313,47 @@ struct Lanczos {
   int64_t n = 0;
   double2* V = nullptr;        // (MRD_LANCZOS_MAX_ITER + 1) vectors of length n
   double2* w = nullptr;
+  double2* vin = nullptr;      // v_j staged for the operator (fixed address: graph-capturable)
   double2* partial = nullptr;  // kRedBlocks * (MRD_LANCZOS_MAX_ITER + 1)
   double2* c1 = nullptr;
   double2* c2 = nullptr;
   double2* scal = nullptr;
   LzState* st = nullptr;
   LzState* st_host = nullptr;  // pinned
+  cudaStream_t stream = nullptr;   // stream of the memory cache the buffers return to
+  // captured Lanczos step: valid while the operator's key is unchanged
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  uint64_t step_key = 0;
+  int step_kernels = 0;
 };
 
 void lanczos_free(Lanczos* L) {
   if (!L) return;
-  cudaFree(L->V); cudaFree(L->w); cudaFree(L->partial); cudaFree(L->c1); cudaFree(L->c2); cudaFree(L->scal);
-  cudaFree(L->st);
-  if (L->st_host) cudaFreeHost(L->st_host);
+  for (void* p : {(void*)L->V, (void*)L->w, (void*)L->vin, (void*)L->partial, (void*)L->c1, (void*)L->c2,
+                  (void*)L->scal, (void*)L->st})
+    cache_free(p, L->stream);
+  if (L->st_host) cache_free_host(L->st_host);
+  if (L->step_exec) cudaGraphExecDestroy(L->step_exec);
+  if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
   delete L;
 }
 
-cudaError_t lanczos_alloc(Lanczos** out, int64_t n) {
+cudaError_t lanczos_alloc(Lanczos** out, int64_t n, cudaStream_t stream) {
   Lanczos* L = new Lanczos();
   L->n = n;
+  L->stream = stream;
   const int kv = MRD_LANCZOS_MAX_ITER + 1;
-  cudaError_t e = cudaMalloc(&L->V, (size_t)kv * (n > 0 ? n : 1) * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&L->w, (size_t)(n > 0 ? n : 1) * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&L->partial, (size_t)kRedBlocks * kv * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&L->c1, kv * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&L->c2, kv * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&L->scal, 4 * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&L->st, sizeof(LzState));
-  if (e == cudaSuccess) e = cudaMallocHost(&L->st_host, sizeof(LzState));
+  auto dev = [&](auto** p, size_t bytes) { return cache_alloc((void**)p, bytes, stream); };
+  cudaError_t e = dev(&L->V, (size_t)kv * (n > 0 ? n : 1) * 16);
+  if (e == cudaSuccess) e = dev(&L->w, (size_t)(n > 0 ? n : 1) * 16);
+  if (e == cudaSuccess) e = dev(&L->vin, (size_t)(n > 0 ? n : 1) * 16);
+  if (e == cudaSuccess) e = dev(&L->partial, (size_t)kRedBlocks * kv * 16);
+  if (e == cudaSuccess) e = dev(&L->c1, kv * 16);
+  if (e == cudaSuccess) e = dev(&L->c2, kv * 16);
+  if (e == cudaSuccess) e = dev(&L->scal, 4 * 16);
+  if (e == cudaSuccess) e = dev(&L->st, sizeof(LzState));
+  if (e == cudaSuccess) e = cache_alloc_host((void**)&L->st_host, sizeof(LzState));
   if (e != cudaSuccess) {
     lanczos_free(L);
     return e;
@@ -296,10 +362,12 @@ cudaError_t lanczos_alloc(Lanczos** out, int64_t n) {
   return cudaSuccess;
 }
 
+// nv >= 0: dots of v_0 .. v_{nv-1}; nv < 0: of v_0 .. v_j (j from the device state)
 static cudaError_t dots(Lanczos* L, const double2* V, int nv, const double2* w, double2* out, cudaStream_t s) {
-  k_multidot<<<kRedBlocks, kRedThreads, 0, s>>>(V, L->n, nv, w, L->n, L->partial);
+  k_multidot<<<kRedBlocks, kRedThreads, 0, s>>>(V, L->n, nv, L->st, w, L->n, L->partial);
   mrd::count_launch();
-  k_finish_dots<<<(nv + 63) / 64, 64, 0, s>>>(L->partial, kRedBlocks, nv, out);
+  const int nmax = nv >= 0 ? nv : MRD_LANCZOS_MAX_ITER + 1;
+  k_finish_dots<<<(nmax + 3) / 4, 128, 0, s>>>(L->partial, kRedBlocks, nv, L->st, out);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -309,10 +377,91 @@ static unsigned grid_for(int64_t n) {
   return (unsigned)(g < 1216 ? (g > 0 ? g : 1) : 1216);
 }
 
+// One Lanczos step j (j in the device state) on the context stream, ending with the copy of
+// the state to pinned host memory; no host synchronisation, so it can be captured.
+static int lanczos_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, double2*), void* op) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = L->n;
+  k_copy_vj<<<grid_for(n), 256, 0, s>>>(L->V, n, L->st, L->vin);
+  mrd::count_launch();
+  int rc = apply(op, L->vin, L->w);
+  if (rc != MRD_OK) return rc;
+  s = ctx->stream;
+  MRD_CUDA(ctx, dots(L, L->V, -1, L->w, L->c1, s));
+  k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -1, L->st, L->c1, L->w, n);
+  mrd::count_launch();
+  MRD_CUDA(ctx, dots(L, L->V, -1, L->w, L->c2, s));
+  k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -1, L->st, L->c2, L->w, n);
+  mrd::count_launch();
+  k_record_alpha<<<1, 1, 0, s>>>(L->st, L->c1, L->c2);
+  mrd::count_launch();
+  MRD_CUDA(ctx, dots(L, L->w, 1, L->w, L->scal, s));
+  k_record_beta<<<1, 1, 0, s>>>(L->st, L->scal);
+  mrd::count_launch();
+  k_tridiag_lowest<<<1, 32, 0, s>>>(L->st);
+  mrd::count_launch();
+  k_scale_next<<<grid_for(n), 256, 0, s>>>(L->w, L->V, n, L->scal, L->st);
+  mrd::count_launch();
+  k_next_step<<<1, 1, 0, s>>>(L->st);
+  mrd::count_launch();
+  MRD_CUDA(ctx, cudaGetLastError());
+  MRD_CUDA(ctx, cudaMemcpyAsync(L->st_host, L->st, sizeof(LzState), cudaMemcpyDeviceToHost, s));
+  return MRD_OK;
+}
+
+// Capture one step as a CUDA graph on a private stream (the context stream may be the legacy
+// default stream, which cannot be captured). Returns false (and leaves no graph) if the
+// operator could not be captured; the caller then launches the steps directly.
+static bool capture_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, double2*), void* op,
+                         uint64_t key) {
+  if (L->step_exec) {
+    cudaGraphExecDestroy(L->step_exec);
+    L->step_exec = nullptr;
+  }
+  if (!L->cap_stream && cudaStreamCreateWithFlags(&L->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    L->cap_stream = nullptr;
+    return false;
+  }
+  cudaStream_t saved = ctx->stream;
+  const int64_t c0 = mrd::launch_count_total();
+  if (cudaStreamBeginCapture(L->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->stream = L->cap_stream;
+  const std::string err_saved = ctx->err;
+  const int rc = lanczos_step(L, ctx, apply, op);
+  ctx->stream = saved;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(L->cap_stream, &g);
+  const int64_t kernels = mrd::launch_count_total() - c0;
+  mrd::uncount_launches(kernels);          // counted again at every replay
+  if (rc != MRD_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    ctx->err = err_saved;
+    return false;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&L->step_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    L->step_exec = nullptr;
+    return false;
+  }
+  L->step_key = key;
+  L->step_kernels = (int)kernels;
+  return true;
+}
+
 // Runs Lanczos on the operator `apply` (theta_out = H theta_in on stream s). theta: start
-// vector in, ground vector out. Host reads one small state record per iteration.
+// vector in, ground vector out. Host reads one small state record per iteration. With
+// graph_key != 0 the step is captured once as a CUDA graph (kept while the key is unchanged)
+// and replayed; the operator must then be ready (buffers built, operands packed) and free of
+// host synchronisation.
 int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, double2*), void* op, double2* theta,
-                int max_iter, double tol, double* energy, int* iters, double* beta_last) {
+                int max_iter, double tol, double* energy, int* iters, double* beta_last, uint64_t graph_key) {
   cudaStream_t s = ctx->stream;
   const int64_t n = L->n;
   if (max_iter < 1 || max_iter > MRD_LANCZOS_MAX_ITER)
@@ -321,32 +470,21 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
   MRD_CUDA(ctx, dots(L, theta, 1, theta, L->scal, s));
   k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(theta, L->V, n, L->scal);
   mrd::count_launch();
+  k_set_step<<<1, 1, 0, s>>>(L->st, 0);
+  mrd::count_launch();
   MRD_CUDA(ctx, cudaGetLastError());
+  bool graph = graph_key != 0 && (L->step_exec && L->step_key == graph_key);
+  if (graph_key != 0 && !graph) graph = capture_step(L, ctx, apply, op, graph_key);
   double e_prev = 0.0;
   int k = 0;
   for (int j = 0; j < max_iter; ++j) {
-    double2* vj = L->V + (int64_t)j * n;
-    int rc = apply(op, vj, L->w);
-    if (rc != MRD_OK) return rc;
-    MRD_CUDA(ctx, dots(L, L->V, j + 1, L->w, L->c1, s));
-    k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, j + 1, L->c1, L->w, n);
-    mrd::count_launch();
-    MRD_CUDA(ctx, dots(L, L->V, j + 1, L->w, L->c2, s));
-    k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, j + 1, L->c2, L->w, n);
-    mrd::count_launch();
-    k_record_alpha<<<1, 1, 0, s>>>(L->st, j, L->c1, L->c2);
-    mrd::count_launch();
-    MRD_CUDA(ctx, dots(L, L->w, 1, L->w, L->scal, s));
-    k_record_beta<<<1, 1, 0, s>>>(L->st, j, L->scal);
-    mrd::count_launch();
-    k_tridiag_lowest<<<1, 32, 0, s>>>(L->st, j + 1);
-    mrd::count_launch();
-    if (j + 1 < max_iter) {
-      k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(L->w, L->V + (int64_t)(j + 1) * n, n, L->scal);
-      mrd::count_launch();
+    if (graph) {
+      MRD_CUDA(ctx, cudaGraphLaunch(L->step_exec, s));
+      mrd::count_launches(L->step_kernels);
+    } else {
+      int rc = lanczos_step(L, ctx, apply, op);
+      if (rc != MRD_OK) return rc;
     }
-    MRD_CUDA(ctx, cudaGetLastError());
-    MRD_CUDA(ctx, cudaMemcpyAsync(L->st_host, L->st, sizeof(LzState), cudaMemcpyDeviceToHost, s));
     MRD_CUDA(ctx, cudaStreamSynchronize(s));
     k = j + 1;
     const double e = L->st_host->energy;

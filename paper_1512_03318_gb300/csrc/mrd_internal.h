@@ -25,8 +25,21 @@ __host__ __device__ inline int64_t qkey(int32_t n, int32_t k) {
   return ((int64_t)(n + (1 << 29)) << 32) | (int64_t)(uint32_t)k;
 }
 
-// Number of kernels this library has launched (all devices, all contexts).
+// Number of kernels this library has launched (all devices, all contexts); a replayed CUDA
+// graph counts the kernels it holds.
 void count_launch();
+void count_launches(int64_t n);
+void uncount_launches(int64_t n);
+int64_t launch_count_total();
+
+// Device memory cache (pool.cu): cache_alloc hands out a block of at least `bytes`, reusing
+// one that was released on the same stream; cache_free returns it; cache_trim frees the
+// cached blocks of a device.
+cudaError_t cache_alloc(void** out, size_t bytes, cudaStream_t s);
+void cache_free(void* p, cudaStream_t s);
+void cache_trim(int device);
+cudaError_t cache_alloc_host(void** out, size_t bytes);   // pinned host memory, reused by size
+void cache_free_host(void* p);
 
 // A device buffer owned by the library.
 struct DevBuf {

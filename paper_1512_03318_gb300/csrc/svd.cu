@@ -164,6 +164,34 @@ __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, fl
   return true;
 }
 
+// Power of two (exact scaling) that brings a block of squared Frobenius norm fro2 to unit
+// norm, away from the FP32 underflow range, while its columns are held in float-float.
+__device__ __forceinline__ double ff_scale(double fro2) {
+  return fro2 > 0.0 ? ldexp(1.0, -ilogb(sqrt(fro2))) : 1.0;
+}
+
+// X (FP64, field 4) <-> its float-float copy (float4 {re.hi, im.hi, re.lo, im.lo}, same
+// offsets), scaled by ff_scale: to_ff = true converts X -> copy, false copy -> X.
+__global__ void k_svd_ff_io(double2* __restrict__ work, float4* __restrict__ xff, const int64_t* __restrict__ blk,
+                            int nblk, const double* __restrict__ fro2, bool to_ff) {
+  const int b = blockIdx.y;
+  if (b >= nblk) return;
+  const int64_t* d = blk + SVF * b;
+  const int64_t len = d[2] * d[3];
+  double2* X = work + d[4];
+  float4* F = xff + d[4];
+  const double up = ff_scale(fro2[b]), down = 1.0 / up;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    if (to_ff) {
+      const FF re = ff_from(X[e].x * up), im = ff_from(X[e].y * up);
+      F[e] = make_float4(re.hi, im.hi, re.lo, im.lo);
+    } else {
+      const float4 v = F[e];
+      X[e] = make_double2(((double)v.x + (double)v.z) * down, ((double)v.y + (double)v.w) * down);
+    }
+  }
+}
+
 // pair q of step s of the round-robin schedule on n (even) items
 __device__ __forceinline__ void rr_pair(int n, int s, int q, int& i, int& j) {
   if (q == 0) {
@@ -182,8 +210,8 @@ __device__ __forceinline__ void rr_pair(int n, int s, int q, int& i, int& j) {
 // pair (one pair per warp, W disjoint pairs per step, W steps), in round 0 first every pair
 // inside each of the two groups, and writes the columns back. Over Gp - 1 rounds each
 // column pair is rotated once (one sweep). T is float (pre-sweeps) or double.
-// MODE 0: FP32 columns and V (T2 = float2); 1: FP64 (double2); 2: FP64 columns held in
-// shared memory as float-float (G2 = double2 in global memory, float4 in shared memory).
+// MODE 0: FP32 columns and V (T2 = float2); 1: FP64 (double2); 2: float-float columns
+// (float4, scaled by ff_scale).
 template <int MODE, class T, class T2, class S2>
 __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf, int vf,
                              const int64_t* __restrict__ grp_prefix, int nblk, int round, int W, T tol,
@@ -211,22 +239,14 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
   S2* sx = (S2*)smem_raw;                      // 2W columns of length p
   S2* sv = sx + (int64_t)2 * W * p;            // 2W columns of length r (V, MODE 0)
   if (threadIdx.x == 0) n_rot = 0;
-  // float-float columns are staged scaled by a power of two (exact) that brings the block
-  // to unit Frobenius norm, away from the FP32 underflow range
-  const int e2 = MODE == 2 && fro2[b] > 0.0 ? -ilogb(sqrt(fro2[b])) : 0;
-  const double up = ldexp(1.0, e2), down = ldexp(1.0, -e2);
+  // float-float columns are held scaled by ff_scale(fro2) (svd_ff_io)
+  const double up = MODE == 2 ? ff_scale(fro2[b]) : 1.0;
   // stage: local column c < W is column gI*W + c, c >= W is column gJ*W + c - W
   for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * p; e += blockDim.x) {
     const int cc = (int)(e / p), t = (int)(e % p);
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
-    const T2 x = X[(int64_t)gc * p + t];
-    if constexpr (MODE == 2) {
-      const FF re = ff_from(x.x * up), im = ff_from(x.y * up);
-      sx[(int64_t)lc * p + t] = make_float4(re.hi, im.hi, re.lo, im.lo);
-    } else {
-      sx[(int64_t)lc * p + t] = x;
-    }
+    sx[(int64_t)lc * p + t] = X[(int64_t)gc * p + t];
   }
   if (V != nullptr)
     for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * r; e += blockDim.x) {
@@ -269,12 +289,7 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     const int cc = (int)(e / p), t = (int)(e % p);
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
-    if constexpr (MODE == 2) {
-      const float4 v = sx[(int64_t)lc * p + t];
-      X[(int64_t)gc * p + t] = make_double2(((double)v.x + (double)v.z) * down, ((double)v.y + (double)v.w) * down);
-    } else {
-      X[(int64_t)gc * p + t] = sx[(int64_t)lc * p + t];
-    }
+    X[(int64_t)gc * p + t] = sx[(int64_t)lc * p + t];
   }
   if constexpr (MODE == 0)
     if (V != nullptr)
@@ -496,9 +511,10 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32) {
   return (int64_t)2 * W * (p + r_v) * (f32 ? 8 : 16);
 }
 
-// FP64 (ff = false) or float-float (ff = true) rounds on the FP64 columns X (field 4).
-cudaError_t svd_bround(double2* work, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
-                       int round, int W, int64_t smem, double tol, bool ff, const double* fro2, int* rotated,
+// FP64 rounds on X (field 4 of work) or, with xff != nullptr, float-float rounds on the
+// float-float copy xff (same offsets, see svd_ff_io).
+cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
+                       int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
                        cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
   static bool attr = false;
@@ -506,17 +522,26 @@ cudaError_t svd_bround(double2* work, const int64_t* blk, const int64_t* grp_pre
     cudaError_t e = cudaFuncSetAttribute(k_svd_bround<1, double, double2, double2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdMaxSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_svd_bround<2, double, double2, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_svd_bround<2, double, float4, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kSvdMaxSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (ff)
-    k_svd_bround<2, double, double2, float4><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated);
+  if (xff)
+    k_svd_bround<2, double, float4, float4><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
+        xff, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated);
   else
     k_svd_bround<1, double, double2, double2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
         work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
+                      cudaStream_t s) {
+  if (nblk == 0) return cudaSuccess;
+  dim3 grid(32, nblk);
+  k_svd_ff_io<<<grid, 256, 0, s>>>(work, xff, blk, nblk, fro2, to_ff);
   mrd::count_launch();
   return cudaGetLastError();
 }

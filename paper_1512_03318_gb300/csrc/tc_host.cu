@@ -10,6 +10,7 @@
 
 namespace mrd {
 cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int prec, cudaStream_t s);
+cudaError_t tc_gemm_init();
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
                     const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
                     int prec, int* err, int n_sm, cudaStream_t s);
@@ -22,9 +23,12 @@ struct Tc {
   uint8_t *lw = nullptr, *wr = nullptr, *th = nullptr, *z = nullptr;
   int64_t lw_bytes = 0, wr_bytes = 0, th_bytes = 0, z_bytes = 0;
   int64_t *t1 = nullptr, *s1 = nullptr, *p1 = nullptr, *t2 = nullptr, *s2 = nullptr, *p2 = nullptr;
-  int64_t n1 = 0, tiles1 = 0, n2 = 0, tiles2 = 0;
+  int64_t n1 = 0, ntiles1 = 0, n2 = 0, ntiles2 = 0;
   int64_t *j_lw = nullptr, *j_wr = nullptr, *j_th = nullptr;
   int n_lw = 0, n_wr = 0, n_th = 0;
+  // per-task launches: [0, tiles of task t] pairs (device) and tiles per task (host)
+  int64_t *pt1 = nullptr, *pt2 = nullptr;
+  std::vector<int64_t> tiles1, tiles2;
   int* err = nullptr;
 };
 
@@ -176,6 +180,7 @@ int build(mrd_heff* h, int prec) {
   h->tc = T = new Tc();
   T->prec = prec;
   Arena& A = T->mem;
+  A.stream = ctx->stream;
   cudaError_t e = cudaSuccess;
 #define TALLOC(ptr, n) if (e == cudaSuccess) e = A.alloc(&(ptr), (size_t)std::max<int64_t>((n), 1))
   TALLOC(T->lw, lw_b); TALLOC(T->wr, wr_b); TALLOC(T->th, th_b); TALLOC(T->z, z_b);
@@ -183,11 +188,15 @@ int build(mrd_heff* h, int prec) {
   TALLOC(T->t2, t2.size()); TALLOC(T->s2, s2.size()); TALLOC(T->p2, p2.size());
   TALLOC(T->j_lw, j_lw.size()); TALLOC(T->j_wr, j_wr.size()); TALLOC(T->j_th, j_th.size());
   TALLOC(T->err, 1);
+  std::vector<int64_t> q1(2 * std::max<size_t>(p1.size() - 1, 1), 0), q2(2 * std::max<size_t>(p2.size() - 1, 1), 0);
+  for (size_t t = 0; t + 1 < p1.size(); ++t) q1[2 * t + 1] = p1[t + 1] - p1[t];
+  for (size_t t = 0; t + 1 < p2.size(); ++t) q2[2 * t + 1] = p2[t + 1] - p2[t];
+  TALLOC(T->pt1, q1.size()); TALLOC(T->pt2, q2.size());
 #undef TALLOC
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: device buffers");
   T->lw_bytes = lw_b; T->wr_bytes = wr_b; T->th_bytes = th_b; T->z_bytes = z_b;
-  T->n1 = (int64_t)t1.size() / TCT; T->tiles1 = p1.back();
-  T->n2 = (int64_t)t2.size() / TCT; T->tiles2 = p2.back();
+  T->n1 = (int64_t)t1.size() / TCT; T->ntiles1 = p1.back();
+  T->n2 = (int64_t)t2.size() / TCT; T->ntiles2 = p2.back();
   T->n_lw = (int)(j_lw.size() / TCJ); T->n_wr = (int)(j_wr.size() / TCJ); T->n_th = (int)(j_th.size() / TCJ);
   cudaStream_t s = ctx->stream;
   auto up = [&](int64_t* d, const std::vector<int64_t>& v) {
@@ -195,6 +204,11 @@ int build(mrd_heff* h, int prec) {
   };
   up(T->t1, t1); up(T->s1, s1); up(T->p1, p1); up(T->t2, t2); up(T->s2, s2); up(T->p2, p2);
   up(T->j_lw, j_lw); up(T->j_wr, j_wr); up(T->j_th, j_th);
+  up(T->pt1, q1); up(T->pt2, q2);
+  T->tiles1.resize(p1.size() - 1);
+  T->tiles2.resize(p2.size() - 1);
+  for (size_t t = 0; t < T->tiles1.size(); ++t) T->tiles1[t] = q1[2 * t + 1];
+  for (size_t t = 0; t < T->tiles2.size(); ++t) T->tiles2[t] = q2[2 * t + 1];
   // zero padding everywhere (packing and the Z epilogue only write valid elements)
   for (auto pr : {std::make_pair(T->lw, lw_b), std::make_pair(T->wr, wr_b), std::make_pair(T->th, th_b),
                   std::make_pair(T->z, z_b)})
@@ -221,13 +235,17 @@ int tc_status(mrd_heff* h) {
   return MRD_OK;
 }
 
-int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
+// Panel tables and buffers for `prec` (host work, allocation, synchronisation) and the packed
+// environments; a no-op when both are current.
+int tc_prepare(mrd_heff* h, int32_t prec) {
   mrd_ctx* ctx = h->ctx;
   const int tp = prec == MRD_PREC_TF32 ? TC_TF32 : TC_BF16X3;
   int rc;
+  MRD_CUDA(ctx, tc_gemm_init());
   if (!h->tc || h->tc->prec != tp) {
     if (!h->tc) h->tc = new Tc();
     if ((rc = build(h, tp)) != MRD_OK) return rc;
+    ++h->gen;
   }
   Tc* T = h->tc;
   cudaStream_t s = ctx->stream;
@@ -236,6 +254,16 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
     MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, tp, s));
     T->env_dirty = false;
   }
+  return MRD_OK;
+}
+
+int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
+  mrd_ctx* ctx = h->ctx;
+  const int tp = prec == MRD_PREC_TF32 ? TC_TF32 : TC_BF16X3;
+  int rc = tc_prepare(h, prec);
+  if (rc != MRD_OK) return rc;
+  Tc* T = h->tc;
+  cudaStream_t s = ctx->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (h->timing) {
     e0 = take_event(h); e1 = take_event(h); e2 = take_event(h);
@@ -244,10 +272,21 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   MRD_CUDA(ctx, cudaMemsetAsync(out, 0, (size_t)h->counts[C_THETA] * 16, s));
   MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, tp, s));
   if (e0) MRD_CUDA(ctx, cudaEventRecord(e0, s));
-  MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->tiles1, T->z, nullptr, tp, T->err, h->n_sm, s));
-  if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
-  MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->tiles2, nullptr, (double2*)out, tp, T->err,
-                        h->n_sm, s));
+  if (!h->per_task) {
+    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->ntiles1, T->z, nullptr, tp, T->err, h->n_sm,
+                          s));
+    if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
+    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->err,
+                          h->n_sm, s));
+  } else {   // one launch per task: the per-block baseline of the grouped persistent launch
+    for (int64_t t = 0; t < T->n1; ++t)
+      MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, 1, T->tiles1[t], T->z, nullptr, tp,
+                            T->err, h->n_sm, s));
+    if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
+    for (int64_t t = 0; t < T->n2; ++t)
+      MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, 1, T->tiles2[t], nullptr,
+                            (double2*)out, tp, T->err, h->n_sm, s));
+  }
   if (e2) MRD_CUDA(ctx, cudaEventRecord(e2, s));
   return MRD_OK;
 }

@@ -82,3 +82,48 @@ def test_lanczos_fixed_iterations_match_oracle(ctx):
         assert it == k and it_or == k
         assert abs(e_gpu - e_or) < 1e-11 * abs(e_or)
         assert abs(abs(np.vdot(th.cpu().numpy(), v_or)) - 1) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 2, 3])
+def test_lanczos_graph_replay_is_bitwise_the_direct_launch(ctx, prec):
+    """A Lanczos step captured once as a CUDA graph and replayed for every step gives the
+    same Ritz values and ground vector, bit for bit, as launching every kernel (all kernels
+    are deterministic), and the library's launch counter counts the replayed kernels."""
+    import paper_1512_03318_gb300 as P
+    case = _hermitian_case(47, 4, 40, 44, 1, 2)
+    res = []
+    for graph in (1, 0, 1):
+        h = P.Heff(ctx, **G.heff_args(case))
+        h.set_option(P.MRD_OPT_GRAPH, graph)
+        h.set_env(torch.from_numpy(case["lflat"]).cuda(), torch.from_numpy(case["rflat"]).cuda())
+        th = torch.from_numpy(case["tflat"].copy()).cuda()
+        c0 = P.launch_count()
+        e, it = h.lanczos(th, max_iter=25, tol=1e-14, prec=prec)
+        res.append((e, it, th.cpu().numpy(), P.launch_count() - c0))
+        h.close()
+    (e1, it1, v1, n1), (e0, it0, v0, n0), (e2, it2, v2, n2) = res
+    assert it1 == it0 == it2 and it1 > 3
+    assert e1 == e0 == e2
+    assert np.array_equal(v1, v0) and np.array_equal(v1, v2)
+    assert n1 == n0 == n2 > 10 * it1
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_per_task_launch_equals_grouped_launch(ctx, prec):
+    """The per-block baseline (one GEMM launch per output task) computes exactly what the
+    grouped persistent launch computes."""
+    import paper_1512_03318_gb300 as P
+    case = G.random_case(7, 6, 150, 170, 5, 3, 4, 8, 6)
+    h = P.Heff(ctx, **G.heff_args(case))
+    h.set_env(torch.from_numpy(case["lflat"]).cuda(), torch.from_numpy(case["rflat"]).cuda())
+    T = torch.from_numpy(case["tflat"]).cuda()
+    a, b = torch.empty_like(T), torch.empty_like(T)
+    h.apply(T, a, prec)
+    h.set_option(P.MRD_OPT_PER_TASK_LAUNCH, 1)
+    c0 = P.launch_count()
+    h.apply(T, b, prec)
+    n_per_task = P.launch_count() - c0
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert n_per_task > 10
+    h.close()
