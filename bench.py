@@ -237,6 +237,21 @@ def matvec_throughput(P, ctx, torch, dev, stream, reps=10):
         ms = e0.elapsed_time(e1) / n
         res[name] = {"tflops": f_def / (ms / 1e3) / 1e12, "ms": ms, "ms_step1": ms1 / max(calls, 1),
                      "ms_step2": ms2 / max(calls, 1)}
+        if prec in (1, 2):
+            res[name]["tile_config"] = dict(zip(["cols_per_tile", "stages", "task_order", "source"], h.tc_config()))
+    # the per-block baseline: one GEMM launch per output task instead of the grouped launch
+    h.set_option(P.MRD_OPT_PER_TASK_LAUNCH, 1)
+    for name in ("bf16x3",):
+        h.apply(T, out, prec=PREC[name])
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            h.apply(T, out, prec=PREC[name])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name]["ms_per_task_launches"] = e0.elapsed_time(e1) / 2
+    h.set_option(P.MRD_OPT_PER_TASK_LAUNCH, 0)
     res["flops_definition"] = f_def
     res["flops_executed"] = f_exec
     res["flops_step1"], res["flops_step2"] = f1, f2
@@ -440,6 +455,9 @@ def main():
         "heff_tflops": {k: round(mv[k]["tflops"], 3) for k in PREC},
         "heff_ms": {k: round(mv[k]["ms"], 4) for k in PREC},
         "heff_ms_steps": {k: [round(mv[k]["ms_step1"], 4), round(mv[k]["ms_step2"], 4)] for k in PREC},
+        "heff_tile_config": {k: mv[k].get("tile_config") for k in ("tf32", "bf16x3")},
+        "heff_bf16x3_ms_grouped_vs_per_task": [round(mv["bf16x3"]["ms"], 4),
+                                               round(mv["bf16x3"]["ms_per_task_launches"], 3)],
         "heff_flops": {"definition": mv["flops_definition"], "executed": mv["flops_executed"]},
         "roofline": roof,
         "roofline_tc_bf16x3": {"kernel": "k_tc_gemm BF16X3 (steps 1+2), Lx=20 matvec", "bound": "tensor",

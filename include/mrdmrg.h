@@ -155,10 +155,20 @@ int mrd_heff_timing(mrd_heff* h, int32_t on);
  *                           replays it; 0: launches every kernel of every step.
  *   MRD_OPT_PER_TASK_LAUNCH 0 (default): each GEMM step of mrd_heff_apply is one grouped
  *                           persistent launch over all charge blocks; 1: one launch per task
- *                           (output block), the per-block baseline the grouped launch replaces. */
+ *                           (output block), the per-block baseline the grouped launch replaces.
+ *   MRD_OPT_AUTOTUNE        1 (default): the first tensor-core application of a problem
+ *                           class (precision, size of theta, number of tasks) times every
+ *                           candidate tile configuration (columns per tile, pipeline stages,
+ *                           task order) and keeps the fastest for the context; later H_effs
+ *                           of the class reuse it; 0: the default configuration. */
 #define MRD_OPT_GRAPH 1
 #define MRD_OPT_PER_TASK_LAUNCH 2
+#define MRD_OPT_AUTOTUNE 3
 int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value);
+/* Tensor-core tile configuration in use: cfg4 = {columns per tile, pipeline stages, task
+ * order (0: charge order, 1: largest work first), source (0: default, 1: tuned on this
+ * H_eff, 2: tuned earlier on the context)}; all -1 before the first tensor-core application. */
+int mrd_heff_tc_config(const mrd_heff* h, int32_t* cfg4);
 int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls);
 
 /* ------------------------------------------------------------------ eigensolver */

@@ -19,6 +19,7 @@ MRD_BASIS_MIXED = 0
 MRD_BASIS_REAL = 1
 MRD_OPT_GRAPH = 1
 MRD_OPT_PER_TASK_LAUNCH = 2
+MRD_OPT_AUTOTUNE = 3
 MRD_SVD_F32_FF = 0
 MRD_SVD_FF = 1
 MRD_SVD_F32_F64 = 2
@@ -119,6 +120,7 @@ _SIGS = {
     "mrd_dmrg_timing": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "mrd_heff_tc_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
 }
@@ -408,6 +410,12 @@ class Heff:
     def set_option(self, option, value):
         """mrd_heff_set_option (MRD_OPT_GRAPH, MRD_OPT_PER_TASK_LAUNCH)."""
         self.ctx.check(lib().mrd_heff_set_option(self.h, option, int(value)))
+
+    def tc_config(self):
+        """(columns per tile, stages, task order, source) of the tensor-core GEMM (mrd_heff_tc_config)."""
+        c = (C.c_int32 * 4)()
+        self.ctx.check(lib().mrd_heff_tc_config(self.h, c))
+        return tuple(c)
 
     def apply(self, theta_in, theta_out, prec=MRD_PREC_FP64):
         self.ctx.check(lib().mrd_heff_apply(self.h, _ptr(theta_in), _ptr(theta_out), prec))

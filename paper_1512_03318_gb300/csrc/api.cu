@@ -653,6 +653,8 @@ int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) {
   if (!h) return MRD_E_ARG;
   if (option == MRD_OPT_GRAPH) {
     h->use_graph = value != 0;
+  } else if (option == MRD_OPT_AUTOTUNE) {
+    h->autotune = value != 0;
   } else if (option == MRD_OPT_PER_TASK_LAUNCH) {
     h->per_task = value != 0;
     if (h->tc) tc_env_changed(h);   // tensor-core per-task tables are built with the panels
@@ -661,6 +663,11 @@ int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) {
     return mrd_fail(h->ctx, MRD_E_ARG, "mrd_heff_set_option: unknown option");
   }
   return MRD_OK;
+}
+
+int mrd_heff_tc_config(const mrd_heff* h, int32_t* cfg4) {
+  if (!h || !cfg4) return MRD_E_ARG;
+  return tc_config(h, cfg4);
 }
 
 int mrd_heff_timing(mrd_heff* h, int32_t on) {

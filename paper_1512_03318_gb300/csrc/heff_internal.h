@@ -14,6 +14,8 @@ void tc_free(Tc* t);
 struct mrd_heff;
 int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec);
 int tc_prepare(mrd_heff* h, int32_t prec);
+int tc_config(const mrd_heff* h, int32_t* cfg4);
+int autotune(mrd_heff* h, int prec);
 void tc_env_changed(mrd_heff* h);
 int tc_status(mrd_heff* h);
 using mrd::Lanczos;
@@ -99,6 +101,7 @@ struct mrd_heff {
   uint64_t gen = 1;          // bumped when apply buffers are reallocated (captured graphs go stale)
   bool use_graph = true;     // capture Lanczos steps as CUDA graphs (MRD_OPT_GRAPH)
   bool per_task = false;     // one GEMM launch per task (MRD_OPT_PER_TASK_LAUNCH)
+  bool autotune = true;      // time the tensor-core tile configurations (MRD_OPT_AUTOTUNE)
   // per-task launches: [0, tiles of task t] for every task of step 1 and step 2 (device),
   // tiles per task (host), for the FP64 / float-float tiles and for the tensor-core tiles
   Arena pt_mem;

@@ -175,6 +175,9 @@ struct TcArgs {
   double2* f_out;          // FP64 output (mode 1)
   int prec;
   int* err;
+  int ntile;               // B rows per tile (multiple of 16, at most 128)
+  int nstages;             // shared-memory pipeline depth (at most kTcMaxStages)
+  int stage_bytes;
 };
 
 // Accumulator slots in TMEM: slot b holds C_re at columns 256 b and C_im at 256 b + 128.
@@ -231,16 +234,17 @@ __device__ __forceinline__ void put_packed16(uint8_t* base, int64_t nkt, int pla
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
   extern __shared__ uint8_t dyn[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bar_full[3], bar_empty[3], bar_acc_full[kAccSlots], bar_acc_empty[kAccSlots];
+  __shared__ __align__(8) uint64_t bar_full[kTcMaxStages], bar_empty[kTcMaxStages], bar_acc_full[kAccSlots],
+      bar_acc_empty[kAccSlots];
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int prec = g.prec;
   const int planes = tc_planes(prec);
   const int kpt = tc_kpt(prec);                    // K values per 128-byte row
   const int kstep = prec == TC_TF32 ? 8 : 16;      // K per MMA instruction
-  const int ntile = tc_ntile(prec);                // B rows (output columns) per tile
-  const int nstages = tc_stages(prec);
-  const int stage_bytes = tc_stage_bytes(prec);
+  const int ntile = g.ntile;                       // B rows (output columns) per tile
+  const int nstages = g.nstages;
+  const int stage_bytes = g.stage_bytes;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -438,7 +442,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
 cudaError_t tc_gemm_init() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -454,13 +458,18 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
 
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
                     const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
-                    int prec, int* err, int n_sm, cudaStream_t s) {
+                    int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   cudaError_t ea = tc_gemm_init();
   if (ea != cudaSuccess) return ea;
-  TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err};
+  const int smem = tc_smem_bytes(prec, cfg);
+  if (cfg.stages < 1 || cfg.stages > kTcMaxStages || cfg.ntile < 16 || cfg.ntile > 128 || cfg.ntile % 16 ||
+      smem > kTcMaxSmem)
+    return cudaErrorInvalidValue;
+  TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, cfg.ntile, cfg.stages,
+           tc_stage_bytes(prec, cfg.ntile)};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
-  k_tc_gemm<<<(unsigned)grid, 192, kTcSmemBytes, s>>>(g);
+  k_tc_gemm<<<(unsigned)grid, 192, smem, s>>>(g);
   mrd::count_launch();
   return cudaGetLastError();
 }

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -55,6 +57,8 @@ struct mrd_ctx {
   std::string err;
   int refs = 0;            // live handles created on this context
   bool destroyed = false;  // mrd_destroy called; deleted when refs drops to 0
+  // autotuner decisions: problem class -> tensor-core tile configuration (ntile, stages, order)
+  std::map<uint64_t, std::array<int, 3>> tc_tuned;
 };
 
 // Reference counting so that handles and contexts may be released in any order.

@@ -21,11 +21,20 @@ struct TcPanelGeom {
 
 __host__ __device__ inline int tc_planes(int prec) { return prec == TC_TF32 ? 2 : 4; }
 __host__ __device__ inline int tc_kpt(int prec) { return prec == TC_TF32 ? 32 : 64; }   // K per 128-byte row
-__host__ __device__ inline int tc_ntile(int prec) { return prec == TC_TF32 ? 128 : 64; } // B rows per tile
+// Tile configuration of the grouped GEMM, picked per problem class by the autotuner
+// (tc_host.cu): B rows (output columns) per tile, pipeline stages, task order (0: charge
+// order, 1: largest work first).
+struct TcCfg {
+  int ntile, stages, order;
+};
+constexpr int kTcMaxStages = 4;
+constexpr int kTcMaxSmem = 220 * 1024;   // dynamic; the kernel's static shared memory comes on top
 // shared-memory stage: A planes x 16 KB + B planes x ntile x 128 B
-__host__ __device__ inline int tc_stage_bytes(int prec) { return prec == TC_TF32 ? 64 * 1024 : 96 * 1024; }
-__host__ __device__ inline int tc_stages(int prec) { return prec == TC_TF32 ? 3 : 2; }
-constexpr int kTcSmemBytes = 192 * 1024 + 1024;
-constexpr int kTcStageBytes = 96 * 1024;   // largest stage (bounds checks)
+__host__ __device__ inline int tc_stage_bytes(int prec, int ntile) {
+  return tc_planes(prec) * (128 * 128 + ntile * 128);
+}
+__host__ __device__ inline int tc_smem_bytes(int prec, TcCfg c) { return c.stages * tc_stage_bytes(prec, c.ntile) + 1024; }
+// default configuration (also the first candidate of the autotuner)
+inline TcCfg tc_default_cfg(int prec) { return prec == TC_TF32 ? TcCfg{128, 3, 0} : TcCfg{64, 2, 0}; }
 
 }  // namespace mrd

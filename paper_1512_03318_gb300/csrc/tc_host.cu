@@ -13,11 +13,13 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
 cudaError_t tc_gemm_init();
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
                     const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
-                    int prec, int* err, int n_sm, cudaStream_t s);
+                    int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s);
 }  // namespace mrd
 
 struct Tc {
   int prec = 0;
+  TcCfg cfg{0, 0, 0};
+  int cfg_source = 0;   // 0: default, 1: tuned on this H_eff, 2: tuned earlier on this context
   bool env_dirty = true;
   Arena mem;
   uint8_t *lw = nullptr, *wr = nullptr, *th = nullptr, *z = nullptr;
@@ -46,10 +48,10 @@ struct Panel {
 int64_t a_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 128) * nkt * planes * 128; }
 int64_t b_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 16) * nkt * planes * 128; }
 
-int build(mrd_heff* h, int prec) {
+int build(mrd_heff* h, int prec, TcCfg cfg) {
   mrd_ctx* ctx = h->ctx;
   Tc* T = h->tc;
-  const int planes = tc_planes(prec), kpt = tc_kpt(prec), ntile = tc_ntile(prec);
+  const int planes = tc_planes(prec), kpt = tc_kpt(prec), ntile = cfg.ntile;
   const int64_t* c = h->counts;
   std::map<int64_t, Panel> lw_map, wr_map, th_map, z_map;
   std::vector<int64_t> j_lw, j_wr, j_th;
@@ -153,6 +155,30 @@ int build(mrd_heff* h, int prec) {
     t2.insert(t2.end(), {t[0], t[1], t[2], t[3], 0, seg0, t[5], 1, 0, 0});
     p2.push_back(p2.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
   }
+  // block schedule: tiles are dealt to the persistent CTAs in task order; order 1 puts the
+  // tasks with the most work (tiles x K tiles) first so that the long ones start early
+  if (cfg.order == 1) {
+    auto reorder = [&](std::vector<int64_t>& tk, const std::vector<int64_t>& sg, std::vector<int64_t>& pf) {
+      const size_t nt = tk.size() / TCT;
+      std::vector<int64_t> work(nt), idx(nt);
+      for (size_t i = 0; i < nt; ++i) {
+        int64_t kt = 0;
+        for (int64_t k = 0; k < tk[TCT * i + 6]; ++k) kt += sg[TCS * (tk[TCT * i + 5] + k) + 2];
+        work[i] = (pf[i + 1] - pf[i]) * kt;
+        idx[i] = (int64_t)i;
+      }
+      std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return work[a] > work[b]; });
+      std::vector<int64_t> t2v(tk.size()), p2v(nt + 1, 0);
+      for (size_t i = 0; i < nt; ++i) {
+        std::copy(tk.begin() + TCT * idx[i], tk.begin() + TCT * (idx[i] + 1), t2v.begin() + TCT * i);
+        p2v[i + 1] = p2v[i] + (pf[idx[i] + 1] - pf[idx[i]]);
+      }
+      tk.swap(t2v);
+      pf.swap(p2v);
+    };
+    reorder(t1, s1, p1);
+    reorder(t2, s2, p2);
+  }
   // every tile the kernel reads or writes must lie inside its buffer
   {
     auto chk = [&](const std::vector<int64_t>& tk, const std::vector<int64_t>& sg, int64_t alen, int64_t blen,
@@ -171,14 +197,14 @@ int build(mrd_heff* h, int prec) {
     };
     if (!chk(t1, s1, lw_b, th_b, true) || !chk(t2, s2, z_b, wr_b, false))
       return mrd_fail(ctx, MRD_E_STATE, "tc: internal panel table check failed");
-    if (planes * 128 * 128 + planes * ntile * 128 > tc_stage_bytes(prec) ||
-        tc_stages(prec) * tc_stage_bytes(prec) > kTcSmemBytes - 1024)
+    if (tc_smem_bytes(prec, cfg) > kTcMaxSmem || cfg.stages < 1 || cfg.stages > kTcMaxStages)
       return mrd_fail(ctx, MRD_E_STATE, "tc: stage does not fit");
   }
   // device buffers
   delete h->tc;
   h->tc = T = new Tc();
   T->prec = prec;
+  T->cfg = cfg;
   Arena& A = T->mem;
   A.stream = ctx->stream;
   cudaError_t e = cudaSuccess;
@@ -221,6 +247,95 @@ int build(mrd_heff* h, int prec) {
 
 }  // namespace
 
+namespace {
+
+// Candidate tile configurations per precision (all fit the 227 KB of shared memory).
+std::vector<TcCfg> candidates(int prec) {
+  if (prec == TC_TF32) return {{128, 3, 0}, {64, 4, 0}, {128, 3, 1}, {64, 4, 1}};
+  return {{64, 2, 0}, {32, 2, 0}, {64, 2, 1}, {32, 2, 1}};
+}
+
+// Problem class of an H_eff for the tuning cache: precision, size of theta (powers of two)
+// and number of tensor-core step-2 tasks (powers of two).
+uint64_t tune_key(const mrd_heff* h, int prec) {
+  auto lg = [](int64_t v) { uint64_t b = 0; while (v > 1) { v >>= 1; ++b; } return b; };
+  return (uint64_t)prec << 56 | lg(h->counts[C_THETA]) << 40 | lg(h->counts[C_NT2]) << 24 | (uint64_t)h->n_sm;
+}
+
+// Kernel time (ms) of steps 1 and 2 with the built configuration, on the packed operands
+// (values do not change the time): 1 warm-up, 3 timed applications.
+int time_cfg(mrd_heff* h, double* ms) {
+  mrd_ctx* ctx = h->ctx;
+  Tc* T = h->tc;
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  MRD_CUDA(ctx, cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&b);
+  if (e != cudaSuccess) { cudaEventDestroy(a); return mrd_cuda_fail(ctx, e, "autotune: event"); }
+  double2* out = nullptr;   // scratch output of the timing runs
+  e = cache_alloc((void**)&out, (size_t)std::max<int64_t>(h->counts[C_THETA], 1) * 16, s);
+  for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+    if (r == 1) e = cudaEventRecord(a, s);
+    if (e == cudaSuccess)
+      e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
+                  h->n_sm, s);
+    if (e == cudaSuccess)
+      e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
+                  s);
+  }
+  float f = 0.f;
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&f, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cache_free(out, s);
+  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "autotune: timing");
+  *ms = f / 3.0;
+  return tc_status(h);
+}
+
+}  // namespace
+
+// Pick the tile configuration: from the context's tuning cache for this problem class, else
+// by timing every candidate on this H_eff (MRD_OPT_AUTOTUNE, default on), else the default.
+int autotune(mrd_heff* h, int prec) {
+  mrd_ctx* ctx = h->ctx;
+  const uint64_t key = tune_key(h, prec);
+  if (!h->autotune) {
+    int rc = build(h, prec, tc_default_cfg(prec));
+    if (rc == MRD_OK) h->tc->cfg_source = 0;
+    return rc;
+  }
+  auto it = ctx->tc_tuned.find(key);
+  if (it != ctx->tc_tuned.end()) {
+    int rc = build(h, prec, TcCfg{it->second[0], it->second[1], it->second[2]});
+    if (rc == MRD_OK) h->tc->cfg_source = 2;
+    return rc;
+  }
+  TcCfg best{0, 0, 0};
+  double best_ms = 1e300;
+  for (const TcCfg& c : candidates(prec)) {
+    int rc = build(h, prec, c);
+    if (rc != MRD_OK) return rc;
+    Tc* T = h->tc;
+    MRD_CUDA(ctx, tc_pack(h->lw, T->lw, T->j_lw, T->n_lw, prec, ctx->stream));
+    MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, prec, ctx->stream));
+    double ms = 0.0;
+    if ((rc = time_cfg(h, &ms)) != MRD_OK) return rc;
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  ctx->tc_tuned[key] = {best.ntile, best.stages, best.order};
+  const TcCfg last = candidates(prec).back();
+  if (best.ntile != last.ntile || best.stages != last.stages || best.order != last.order) {
+    int rc = build(h, prec, best);
+    if (rc != MRD_OK) return rc;
+  }
+  h->tc->cfg_source = 1;
+  h->tc->env_dirty = true;
+  return MRD_OK;
+}
+
 void tc_env_changed(mrd_heff* h) {
   if (h->tc) h->tc->env_dirty = true;
 }
@@ -244,7 +359,7 @@ int tc_prepare(mrd_heff* h, int32_t prec) {
   MRD_CUDA(ctx, tc_gemm_init());
   if (!h->tc || h->tc->prec != tp) {
     if (!h->tc) h->tc = new Tc();
-    if ((rc = build(h, tp)) != MRD_OK) return rc;
+    if ((rc = autotune(h, tp)) != MRD_OK) return rc;
     ++h->gen;
   }
   Tc* T = h->tc;
@@ -254,6 +369,18 @@ int tc_prepare(mrd_heff* h, int32_t prec) {
     MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, tp, s));
     T->env_dirty = false;
   }
+  return MRD_OK;
+}
+
+int tc_config(const mrd_heff* h, int32_t* cfg4) {
+  if (!h->tc) {
+    cfg4[0] = cfg4[1] = cfg4[2] = cfg4[3] = -1;
+    return MRD_OK;
+  }
+  cfg4[0] = h->tc->cfg.ntile;
+  cfg4[1] = h->tc->cfg.stages;
+  cfg4[2] = h->tc->cfg.order;
+  cfg4[3] = h->tc->cfg_source;
   return MRD_OK;
 }
 
@@ -273,19 +400,19 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, tp, s));
   if (e0) MRD_CUDA(ctx, cudaEventRecord(e0, s));
   if (!h->per_task) {
-    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->ntiles1, T->z, nullptr, tp, T->err, h->n_sm,
-                          s));
-    if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
-    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->err,
+    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
                           h->n_sm, s));
+    if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
+    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
+                          T->err, h->n_sm, s));
   } else {   // one launch per task: the per-block baseline of the grouped persistent launch
     for (int64_t t = 0; t < T->n1; ++t)
       MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, 1, T->tiles1[t], T->z, nullptr, tp,
-                            T->err, h->n_sm, s));
+                            T->cfg, T->err, h->n_sm, s));
     if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
     for (int64_t t = 0; t < T->n2; ++t)
       MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, 1, T->tiles2[t], nullptr,
-                            (double2*)out, tp, T->err, h->n_sm, s));
+                            (double2*)out, tp, T->cfg, T->err, h->n_sm, s));
   }
   if (e2) MRD_CUDA(ctx, cudaEventRecord(e2, s));
   return MRD_OK;

@@ -82,3 +82,29 @@ def test_tc_model_mpo_sampled_blocks(ctx):
     ref = B.heff_apply_block(case["left"], case["right"], case["m1"], case["m2"], case["mod"], case["cl"], case["cm"],
                              case["cr"], case["wi"], case["wj"], case["lflat"], case["rflat"], case["tflat"], key)
     assert np.max(np.abs(blocks[key] - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_autotuned_tile_configuration(ctx, prec):
+    """The autotuner times the candidate tile configurations on the first application of a
+    problem class, keeps the fastest for the context (a second H_eff of the class reuses it),
+    and every configuration computes the same result bit for bit: tiling the output columns
+    and reordering the tasks do not change any element's accumulation order."""
+    import paper_1512_03318_gb300 as P
+    case = G.random_case(21, 2, 300, 280, 1, 0, 4, 4, 4)
+    outs, cfgs = [], []
+    for tune in (0, 1, 1):
+        h = P.Heff(ctx, **G.heff_args(case))
+        h.set_option(P.MRD_OPT_AUTOTUNE, tune)
+        h.set_env(torch.from_numpy(case["lflat"]).cuda(), torch.from_numpy(case["rflat"]).cuda())
+        T = torch.from_numpy(case["tflat"]).cuda()
+        out = torch.empty_like(T)
+        h.apply(T, out, prec)
+        torch.cuda.synchronize()
+        outs.append(out.cpu())
+        cfgs.append(h.tc_config())
+        h.close()
+    assert cfgs[0][3] == 0 and cfgs[1][3] in (1, 2) and cfgs[2][3] == 2
+    assert cfgs[1][:3] == cfgs[2][:3]
+    assert cfgs[1][0] in (32, 64, 128) and cfgs[1][1] in (2, 3, 4) and cfgs[1][2] in (0, 1)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])

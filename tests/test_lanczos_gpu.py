@@ -95,6 +95,7 @@ def test_lanczos_graph_replay_is_bitwise_the_direct_launch(ctx, prec):
     for graph in (1, 0, 1):
         h = P.Heff(ctx, **G.heff_args(case))
         h.set_option(P.MRD_OPT_GRAPH, graph)
+        h.set_option(P.MRD_OPT_AUTOTUNE, 0)   # no tuning launches in the counts
         h.set_env(torch.from_numpy(case["lflat"]).cuda(), torch.from_numpy(case["rflat"]).cuda())
         th = torch.from_numpy(case["tflat"].copy()).cuda()
         c0 = P.launch_count()
