@@ -35,7 +35,7 @@ cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* sr
 int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
                        int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
-                       cudaStream_t s);
+                       int* last_rot, int sweep, cudaStream_t s);
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
                       cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
@@ -43,7 +43,8 @@ cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
                          int* keep, double* info, int* flat_block, cudaStream_t s);
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
-                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, cudaStream_t s);
+                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
+                         int sweep, cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 enum { SVF = 12 };
@@ -285,7 +286,7 @@ struct mrd_dmrg {
   std::vector<SiteT> A;
   std::vector<EnvT> L, R;
   Buf gtask, gseg, gpref, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
-      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, tbuf, zeros;
+      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, svd_last, tbuf, zeros;
   int svd_sweeps32 = 0, svd_sweeps64 = 0;
   bool gemm_ff = false;   // grouped GEMMs of the update in float-float (refine_prec MRD_PREC_FF)
   double last_energy = 0.0, last_trunc = 0.0;
@@ -503,6 +504,7 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   MRD_CUDA(ctx, D->svd_ss.need((size_t)slen * 8));
   MRD_CUDA(ctx, D->svd_ord.need((size_t)slen * 4));
   MRD_CUDA(ctx, D->svd_flat.need((size_t)slen * 4));
+  MRD_CUDA(ctx, D->svd_last.need((size_t)std::max<int64_t>(slen, 1) * 4));
   MRD_CUDA(ctx, D->svd_keep.need((size_t)nb * 4));
   MRD_CUDA(ctx, D->svd_info.need(4 * 8));
   MRD_CUDA(ctx, D->svd_rot.need(8));
@@ -519,15 +521,17 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   auto sweep_until_done = [&](bool f32, int max_sweeps, int* used) -> int {
     const Sched& sc = f32 ? s32 : s64;
     const bool ff = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
+    int* last = D->svd_last.as<int>();
+    MRD_CUDA(ctx, cudaMemsetAsync(last, 0, (size_t)slen * 4, s));
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
       MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
       for (int rd = 0; rd < sc.rounds; ++rd) {
         if (f32)
           MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f, fro,
-                                     rot, s));
+                                     rot, last, sweep, s));
         else
           MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, nb,
-                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, s));
+                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, s));
       }
       int hrot = 0;
       MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));

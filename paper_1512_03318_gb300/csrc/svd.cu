@@ -118,27 +118,23 @@ __device__ __forceinline__ bool jacobi_pair(T2* xi, T2* xj, int p, T2* vi, T2* v
 // previous overlap (the next sweep removes the rest) and the column norms drift by ~1e-7,
 // which the caller absorbs because it takes the singular vectors of one side from the
 // orthogonalised columns and the other factor by projection.
-__device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, float tol, float floor2, int lane) {
-  FFAcc A = {0.f, 0.f}, B = {0.f, 0.f}, GR = {0.f, 0.f}, GI = {0.f, 0.f};
+__device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, float tol, float floor2, FF& na, FF& nb,
+                                               int lane) {
+  FFAcc GR = {0.f, 0.f}, GI = {0.f, 0.f};
   for (int t = lane; t < p; t += 32) {
     const float4 u4 = xi[t], v4 = xj[t];
     const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
-    ff_mac(A, ur, ur);
-    ff_mac(A, ui, ui);
-    ff_mac(B, vr, vr);
-    ff_mac(B, vi, vi);
     ff_mac(GR, ur, vr);                        // Re(conj(u) v)
     ff_mac(GR, ui, vi);
     ff_mac(GI, ur, vi);                        // Im(conj(u) v)
     ff_mac(GI, ff_neg(ui), vr);
   }
-  const FF a2 = ff_warp_sum(ff_norm(A)), b2 = ff_warp_sum(ff_norm(B));
   const FF gr2 = ff_warp_sum(ff_norm(GR)), gi2 = ff_warp_sum(ff_norm(GI));
-  const float a = a2.hi, bb = b2.hi, gr = gr2.hi, gi = gi2.hi;
+  const float a = na.hi, bb = nb.hi, gr = gr2.hi, gi = gi2.hi;
   const float g = hypotf(gr, gi);               // no intermediate underflow
   if (a <= floor2 || bb <= floor2) return false;
   if (!(g > tol * (sqrtf(a) * sqrtf(bb)))) return false;
-  const FF dba = ff_add(b2, ff_neg(a2));
+  const FF dba = ff_add(nb, ff_neg(na));
   const float ph_r = gr / g, ph_i = -gi / g;    // e^{-i phi}
   // columns of very different norms give |zeta| up to ~1e26: take t = 1 / (2 zeta) there
   // (relative error 1 / (4 zeta^2)) instead of squaring zeta
@@ -149,6 +145,7 @@ __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, fl
   const float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
   // x_i' = c u - sigma v, x_j' = s u + kappa v with sigma = s e^{-i phi}, kappa = c e^{-i phi}
   const float sr = sn * ph_r, si = sn * ph_i, kr = c * ph_r, ki = c * ph_i;
+  FFAcc A = {0.f, 0.f}, B = {0.f, 0.f};          // norms of the rotated columns
   for (int q = lane; q < p; q += 32) {
     const float4 u4 = xi[q], v4 = xj[q];
     const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
@@ -160,7 +157,13 @@ __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, fl
     const FF a1 = ff_norm(o1r), b1 = ff_norm(o1i), a3 = ff_norm(o2r), b3 = ff_norm(o2i);
     xi[q] = make_float4(a1.hi, b1.hi, a1.lo, b1.lo);
     xj[q] = make_float4(a3.hi, b3.hi, a3.lo, b3.lo);
+    ff_mac(A, a1, a1);
+    ff_mac(A, b1, b1);
+    ff_mac(B, a3, a3);
+    ff_mac(B, b3, b3);
   }
+  na = ff_warp_sum(ff_norm(A));
+  nb = ff_warp_sum(ff_norm(B));
   return true;
 }
 
@@ -215,9 +218,12 @@ __device__ __forceinline__ void rr_pair(int n, int s, int q, int& i, int& j) {
 template <int MODE, class T, class T2, class S2>
 __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf, int vf,
                              const int64_t* __restrict__ grp_prefix, int nblk, int round, int W, T tol,
-                             const double* __restrict__ fro2, double zero_rel, int* __restrict__ rotated) {
+                             const double* __restrict__ fro2, double zero_rel, int* __restrict__ rotated,
+                             int* __restrict__ last_rot, int sweep) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ int n_rot;
+  __shared__ int s_last[32];   // sweep in which each staged column last rotated
+  __shared__ FF s_norm[32];    // float-float column norms (MODE 2)
   const int64_t cta = blockIdx.x;
   int lo = 0, hi = nblk - 1;   // largest b with grp_prefix[b] <= cta
   while (lo < hi) {
@@ -255,18 +261,53 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
       const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
       if constexpr (MODE == 0) sv[(int64_t)lc * r + t] = V[(int64_t)gc * r + t];
     }
+  for (int cc = threadIdx.x; cc < nI + nJ; cc += blockDim.x) {
+    const int lc = cc < nI ? cc : W + cc - nI;
+    const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
+    s_last[lc] = last_rot[d[8] + gc];
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (MODE == 2) {   // norms of the staged columns, one warp per column
+    for (int cc = warp; cc < nI + nJ; cc += blockDim.x >> 5) {
+      const int lc = cc < nI ? cc : W + cc - nI;
+      const float4* x = sx + (int64_t)lc * p;
+      FFAcc A = {0.f, 0.f};
+      for (int t = lane; t < p; t += 32) {
+        const float4 u = x[t];
+        ff_mac(A, FF{u.x, u.z}, FF{u.x, u.z});
+        ff_mac(A, FF{u.y, u.w}, FF{u.y, u.w});
+      }
+      const FF nrm = ff_warp_sum(ff_norm(A));
+      if (lane == 0) s_norm[lc] = nrm;
+    }
+    __syncthreads();
+  }
   const double floor2 = zero_rel * fro2[b];
   int mine = 0;
+  // A pair found orthogonal in the previous sweep stays orthogonal while neither column
+  // rotates: pairs whose columns last rotated before the previous sweep are skipped (the
+  // first two sweeps test every pair, last_rot starting at 0).
   auto do_pair = [&](int i, int j) {
+    if (s_last[i] < sweep - 1 && s_last[j] < sweep - 1) return;
     bool rot;
-    if constexpr (MODE == 2)
-      rot = jacobi_pair_ff(sx + (int64_t)i * p, sx + (int64_t)j * p, p, (float)tol, (float)(floor2 * up * up), lane);
-    else
+    if constexpr (MODE == 2) {
+      FF na = s_norm[i], nb = s_norm[j];
+      rot = jacobi_pair_ff(sx + (int64_t)i * p, sx + (int64_t)j * p, p, (float)tol, (float)(floor2 * up * up), na,
+                           nb, lane);
+      if (rot && lane == 0) {
+        s_norm[i] = na;
+        s_norm[j] = nb;
+      }
+    } else {
       rot = jacobi_pair<T, T2>(sx + (int64_t)i * p, sx + (int64_t)j * p, p, V ? sv + (int64_t)i * r : nullptr,
                                V ? sv + (int64_t)j * r : nullptr, r, tol, floor2, lane);
-    if (rot) ++mine;
+    }
+    if (rot) {
+      ++mine;
+      if (lane == 0) s_last[i] = s_last[j] = sweep;
+    }
+    __syncwarp();
   };
   if (round == 0) {
     // pairs inside group I (warps 0 .. W/2-1) and inside group J (warps W/2 .. W-1)
@@ -299,6 +340,11 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
         const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
         V[(int64_t)gc * r + t] = sv[(int64_t)lc * r + t];
       }
+  for (int cc = threadIdx.x; cc < nI + nJ; cc += blockDim.x) {
+    const int lc = cc < nI ? cc : W + cc - nI;
+    const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
+    last_rot[d[8] + gc] = s_last[lc];
+  }
   __syncthreads();
   if (threadIdx.x == 0 && n_rot) atomicAdd(rotated, n_rot);
 }
@@ -515,7 +561,7 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32) {
 // float-float copy xff (same offsets, see svd_ff_io).
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
                        int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
-                       cudaStream_t s) {
+                       int* last_rot, int sweep, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -529,10 +575,10 @@ cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int
   }
   if (xff)
     k_svd_bround<2, double, float4, float4><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        xff, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated);
+        xff, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep);
   else
     k_svd_bround<1, double, double2, double2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated);
+        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -547,7 +593,8 @@ cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, 
 }
 
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
-                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, cudaStream_t s) {
+                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
+                         int sweep, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -557,7 +604,7 @@ cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_pre
     attr = true;
   }
   k_svd_bround<0, float, float2, float2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-      w32, blk, 10, 11, grp_prefix, nblk, round, W, tol, fro2, 1e-12, rotated);
+      w32, blk, 10, 11, grp_prefix, nblk, round, W, tol, fro2, 1e-12, rotated, last_rot, sweep);
   mrd::count_launch();
   return cudaGetLastError();
 }
