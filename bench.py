@@ -41,6 +41,7 @@ LX_UPDATE = 12            # cylinder of the update steps
 LX_MATVEC = 20            # cylinder of the matvec throughput measurement
 SEED = 1234 + 3           # workload index 3 (chi = 3200)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+FP32_ISSUE_TINSTR = 128 * 152 * 2.070e9 / 1e12     # FP32 instructions per second (lanes x SMs x clock)
 PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "ff": 3}
 
 
@@ -304,7 +305,7 @@ def main():
     caps = update_caps(LX_UPDATE, chi)
     seed = 11 + rank
     # reduced-precision Lanczos restarted until its Ritz value settles, then FP64 refinement
-    mixed = P.DMRG.params(chi, 1e-14, 30, 1e-10, PREC["bf16x3"], args.refine, 1e-13, restarts=args.fast_restarts)
+    mixed = P.DMRG.params(chi, 1e-14, 60, 1e-10, PREC["bf16x3"], args.refine, 1e-13, restarts=args.fast_restarts)
     if args.only_matvec:
         set_chi(chi)
         mv = matvec_throughput(P, ctx, torch, dev, stream)
@@ -341,6 +342,7 @@ def main():
     barrier()
     phases = np.zeros(6)
     sweeps = np.zeros(2)
+    svd_work = np.zeros(6)   # summed mrd_dmrg_svd_stats of the timed updates
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = P.launch_count()
     t_wall = time.perf_counter()
@@ -350,6 +352,7 @@ def main():
             st.update(centre + args.warmup + k, +1, mixed)
             phases += np.array(st.phase_ms())
             sweeps += np.array(st.svd_sweeps())
+            svd_work += np.array(st.svd_stats())
         e1.record(stream)
         torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall
@@ -413,21 +416,36 @@ def main():
         return 0
 
     bf16_peak, bf16_sust, peak_src = measured_peaks()
-    tc_ms, f64_ms = kms[0] + kms[1], kms[2] + kms[3]
+    tc_ms, hp_ms = kms[0] + kms[1], kms[2] + kms[3]   # tensor-core and float-float H_eff GEMMs
+    svd_ms = svd_work[0] + svd_work[4]                 # Jacobi rounds
     f_exec = mv["flops_executed"]
-    if f64_ms >= tc_ms:
-        ach = f_exec / (mv["fp64"]["ms"] / 1e3) / 1e12
-        roof = {"kernel": "k_cgemm_fp64 (FP64 refinement matvecs, steps 1+2)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 DFMA: 2/clk/SM x 152 SMs x 2.07 GHz (probe: 1.206 TFLOP/s at 1.995 GHz); "
-                               "not in MEASURED_PEAKS.json",
-                "gemm_share": f64_ms / (tc_ms + f64_ms)}
-    else:
+    # the dominant kernel of the timed updates by GPU time
+    shares = {"k_svd_bround (Jacobi rounds)": svd_ms, "k_tc_gemm (Lanczos matvecs)": tc_ms,
+              "k_cgemm_ff (refinement matvecs)": hp_ms}
+    dominant = max(shares, key=shares.get)
+    if dominant.startswith("k_svd_bround"):
+        # float-float Jacobi: FP32 instructions of the work done (per element of a tested pair:
+        # 4 float-float multiply-adds of 12 instructions; per element of a rotated pair: 12 of
+        # 11, 4 FastTwoSums of 3 and 4 of 12), against the FP32 issue rate
+        instr = svd_work[1] * 48 + svd_work[2] * 192
+        ach = instr / (svd_work[0] / 1e3) / 1e12
+        roof = {"kernel": "k_svd_bround<float-float> (block-cyclic Jacobi rounds)", "bound": "alu", "achieved": ach,
+                "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
+                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived, DESIGN.md)",
+                "ms_per_step": svd_work[0] / args.steps, "share_of_measured_kernels": svd_ms / sum(shares.values())}
+    elif dominant.startswith("k_tc_gemm"):
         per = tc_ms / max(kn[0], 1) / 1e3
         hw = 3 * f_exec / per / 1e12
         roof = {"kernel": "k_tc_gemm BF16X3 (steps 1+2)", "bound": "tensor", "achieved": hw, "peak": bf16_sust,
                 "unit": "TFLOP/s", "frac": hw / bf16_sust, "traffic": None, "peak_source": f"bf16 sustained {peak_src}",
-                "gemm_share": tc_ms / (tc_ms + f64_ms)}
+                "ms_per_step": tc_ms / args.steps, "share_of_measured_kernels": tc_ms / sum(shares.values())}
+    else:
+        per = hp_ms / max(kn[1], 1) / 1e3
+        ach = f_exec / 8 * 48 / per / 1e12
+        roof = {"kernel": "k_cgemm_ff (float-float refinement matvec, steps 1+2)", "bound": "alu", "achieved": ach,
+                "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
+                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived, DESIGN.md)",
+                "ms_per_step": hp_ms / args.steps, "share_of_measured_kernels": hp_ms / sum(shares.values())}
     tc = mv["bf16x3"]
     tc_hw = 3 * f_exec / (tc["ms"] / 1e3) / 1e12
     tf = mv["tf32"]
@@ -435,10 +453,11 @@ def main():
     line = {
         "metric": METRIC, "value": s_per_update, "unit": "s/update", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x3+f32x2", "data": "synthetic",
         "config": {"workload": workload_name(chi), "chi": chi, "ly": LY, "lx": LX_UPDATE,
-                   "form": f"split-BF16 tensor-core Lanczos (30 per run, up to {args.fast_restarts} restarts) + "
-                           f"FP64 Lanczos refinement (up to {args.refine} matvecs)",
+                   "form": f"split-BF16 tensor-core Lanczos (60 per run, up to {args.fast_restarts} restarts) + "
+                           f"float-float Rayleigh-quotient refinement ({args.refine} matvec), float-float "
+                           f"Jacobi SVD and environment updates",
                    "l2": "working set > L2 (folded environments, Z intermediate and Lanczos basis, >1 GB)",
                    "parallelism": f"replicas x{world}"},
         "s_per_update_fp64": t64,
@@ -451,7 +470,8 @@ def main():
         "phase_ms_mean": dict(zip(["tables", "theta", "lanczos+refine", "svd", "tensors", "env"],
                                   (phases / args.steps).round(2).tolist())),
         "svd_jacobi_rounds_mean": dict(zip(["fp32", "fp64"], (sweeps / args.steps).round(1).tolist())),
-        "gemm_ms_per_step": {"tc": tc_ms / args.steps, "fp64": f64_ms / args.steps},
+        "kernel_ms_per_step": {k: round(v / args.steps, 3) for k, v in shares.items()},
+        "svd_elem_pairs_per_step": {"tested": svd_work[1] / args.steps, "rotated": svd_work[2] / args.steps},
         "heff_tflops": {k: round(mv[k]["tflops"], 3) for k in PREC},
         "heff_ms": {k: round(mv[k]["ms"], 4) for k in PREC},
         "heff_ms_steps": {k: [round(mv[k]["ms_step1"], 4), round(mv[k]["ms_step2"], 4)] for k in PREC},
@@ -464,6 +484,11 @@ def main():
                                "achieved": tc_hw, "peak": bf16_peak, "unit": "TFLOP/s", "frac": tc_hw / bf16_peak,
                                "traffic": None, "note": "hardware bf16 flops = 3 x executed complex-product flops "
                                                         f"(split), peak = bf16 burst {peak_src}"},
+        "roofline_ff_gemm": {"kernel": "k_cgemm_ff (steps 1+2), Lx=20 matvec", "bound": "alu",
+                             "achieved": f_exec / 8 * 48 / (mv["ff"]["ms"] / 1e3) / 1e12, "peak": FP32_ISSUE_TINSTR,
+                             "unit": "T FP32-instr/s",
+                             "frac": f_exec / 8 * 48 / (mv["ff"]["ms"] / 1e3) / 1e12 / FP32_ISSUE_TINSTR,
+                             "traffic": None, "note": "48 FP32 instructions per complex multiply-add (4 float-float)"},
         "roofline_tc_tf32": {"kernel": "k_tc_gemm TF32 (steps 1+2), Lx=20 matvec", "bound": "tensor",
                              "achieved": tf_hw, "peak": bf16_peak / 2, "unit": "TFLOP/s",
                              "frac": tf_hw / (bf16_peak / 2), "traffic": None,

@@ -264,6 +264,11 @@ int mrd_dmrg_timing(mrd_dmrg* d, int32_t on, double* kernel_ms4, int64_t* applie
  * [3] block SVD and truncation, [4] new MPS tensors, [5] environment update; then [6] the
  * FP32 and [7] the FP64 Jacobi sweeps of its block SVD. */
 int mrd_dmrg_phase_ms(const mrd_dmrg* d, double* ms8);
+/* Block SVD of the last two-site update: out6 = {ms of the final (float-float or FP64) Jacobi
+ * sweeps (CUDA events around them), column element-pairs whose overlap was tested (sum of the
+ * column length over tested pairs), element-pairs rotated, final sweeps, ms of the FP32
+ * pre-sweeps (0 without), svd_mode}. */
+int mrd_dmrg_svd_stats(const mrd_dmrg* d, double* out6);
 /* Energy, discarded weight and matvec count of the last two-site update; the count is the
  * reduced-precision (or FP64) Lanczos matvecs plus 1000 times the FP64 refinement matvecs. */
 int mrd_dmrg_stats(const mrd_dmrg* d, double* energy, double* trunc_err, int32_t* lanczos_iters);

@@ -121,6 +121,7 @@ _SIGS = {
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "mrd_heff_tc_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "mrd_dmrg_svd_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
 }
@@ -356,6 +357,12 @@ class DMRG:
         f = (C.c_double * 8)()
         self.ctx.check(lib().mrd_dmrg_phase_ms(self.h, f))
         return int(f[6]), int(f[7])
+
+    def svd_stats(self):
+        """(sweep ms, element-pairs tested, element-pairs rotated, sweeps, FP32 pre-sweep ms, svd_mode)."""
+        f = (C.c_double * 6)()
+        self.ctx.check(lib().mrd_dmrg_svd_stats(self.h, f))
+        return tuple(f)
 
     def stats(self):
         e, t, it = C.c_double(), C.c_double(), C.c_int32()

@@ -35,7 +35,7 @@ cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* sr
 int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
                        int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
-                       int* last_rot, int sweep, cudaStream_t s);
+                       int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s);
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
                       cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
@@ -44,7 +44,7 @@ cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, i
                          int* keep, double* info, int* flat_block, cudaStream_t s);
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
                          int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
-                         int sweep, cudaStream_t s);
+                         int sweep, unsigned long long* wctr, cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 enum { SVF = 12 };
@@ -286,7 +286,12 @@ struct mrd_dmrg {
   std::vector<SiteT> A;
   std::vector<EnvT> L, R;
   Buf gtask, gseg, gpref, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
-      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, svd_last, tbuf, zeros;
+      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, svd_last, svd_ctr, tbuf,
+      zeros;
+  cudaEvent_t svd_ev[2] = {nullptr, nullptr};
+  // last block SVD: [0] ms of the final sweeps, [1] element-pairs tested, [2] rotated, [3] sweeps,
+  // [4] ms of the FP32 pre-sweeps, [5] svd_mode
+  double svd_stats[6] = {0, 0, 0, 0, 0, 0};
   int svd_sweeps32 = 0, svd_sweeps64 = 0;
   bool gemm_ff = false;   // grouped GEMMs of the update in float-float (refine_prec MRD_PREC_FF)
   double last_energy = 0.0, last_trunc = 0.0;
@@ -518,28 +523,56 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   int* rot = D->svd_rot.as<int>();
   const int64_t* pre32 = D->svd_pref.as<int64_t>();
   const int64_t* pre64 = pre32 + nb + 1;
+  // per phase: the rounds' time (events around the sweeps) and work (element-pairs tested and
+  // rotated, counted by the kernels), reported by mrd_dmrg_svd_stats
+  if (!D->svd_ev[0]) {
+    MRD_CUDA(ctx, cudaEventCreate(&D->svd_ev[0]));
+    MRD_CUDA(ctx, cudaEventCreate(&D->svd_ev[1]));
+  }
+  MRD_CUDA(ctx, D->svd_ctr.need(2 * 8));
+  for (double& v : D->svd_stats) v = 0.0;
+  D->svd_stats[5] = mode;
   auto sweep_until_done = [&](bool f32, int max_sweeps, int* used) -> int {
     const Sched& sc = f32 ? s32 : s64;
     const bool ff = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
     int* last = D->svd_last.as<int>();
+    unsigned long long* wctr = D->svd_ctr.as<unsigned long long>();
     MRD_CUDA(ctx, cudaMemsetAsync(last, 0, (size_t)slen * 4, s));
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    MRD_CUDA(ctx, cudaMemsetAsync(wctr, 0, 2 * 8, s));
+    MRD_CUDA(ctx, cudaEventRecord(D->svd_ev[0], s));
+    bool done = false;
+    for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
       MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
       for (int rd = 0; rd < sc.rounds; ++rd) {
         if (f32)
           MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f, fro,
-                                     rot, last, sweep, s));
+                                     rot, last, sweep, wctr, s));
         else
           MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, nb,
-                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, s));
+                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, wctr, s));
       }
       int hrot = 0;
       MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
       MRD_CUDA(ctx, cudaStreamSynchronize(s));
       *used = sweep + 1;
-      if (hrot == 0) return MRD_OK;
+      done = hrot == 0;
     }
-    return f32 ? MRD_OK : mrd_fail(ctx, MRD_E_NOCONV, "block SVD: Jacobi sweeps did not converge");
+    MRD_CUDA(ctx, cudaEventRecord(D->svd_ev[1], s));
+    unsigned long long cnt[2] = {0, 0};
+    MRD_CUDA(ctx, cudaMemcpyAsync(cnt, wctr, 2 * 8, cudaMemcpyDeviceToHost, s));
+    MRD_CUDA(ctx, cudaStreamSynchronize(s));
+    float ms = 0.f;
+    MRD_CUDA(ctx, cudaEventElapsedTime(&ms, D->svd_ev[0], D->svd_ev[1]));
+    if (f32) {
+      D->svd_stats[4] = ms;
+    } else {
+      D->svd_stats[0] = ms;
+      D->svd_stats[1] = (double)cnt[0];
+      D->svd_stats[2] = (double)cnt[1];
+      D->svd_stats[3] = *used;
+    }
+    if (done || f32) return MRD_OK;
+    return mrd_fail(ctx, MRD_E_NOCONV, "block SVD: Jacobi sweeps did not converge");
   };
   // FP32 pre-sweeps (MRD_SVD_F32_*) orthogonalise the columns to ~1e-5 (the resolution of FP32
   // dot products of a few hundred terms); their rotations V32 are applied to the FP64 matrix
@@ -937,6 +970,8 @@ int mrd_dmrg_free(mrd_dmrg* D) {
   {
     Guard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t e : D->svd_ev)
+      if (e) cudaEventDestroy(e);
     delete D;
   }
   mrd_ctx_release(ctx);
@@ -990,7 +1025,6 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   int32_t it = 0;
   if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e, &it)) != MRD_OK) return rc;
   D->last_iters = it;
-  collect(p->prec == MRD_PREC_FP64 || p->prec == MRD_PREC_FF ? 1 : 0);
   for (int r = 0; r < p->lanczos_restarts && it == p->lanczos_max_iter; ++r) {
     double e2 = 0.0;
     if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e2, &it)) != MRD_OK)
@@ -1000,6 +1034,7 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
     e = e2;
     if (done) break;
   }
+  collect(p->prec == MRD_PREC_FP64 || p->prec == MRD_PREC_FF ? 1 : 0);
   D->last_refine = 0;
   if ((p->prec == MRD_PREC_TF32 || p->prec == MRD_PREC_BF16X3) && p->refine_iter > 0) {
     int32_t it2 = 0;
@@ -1169,6 +1204,12 @@ int mrd_dmrg_phase_ms(const mrd_dmrg* D, double* ms8) {
   for (int k = 0; k < 6; ++k) ms8[k] = D->phase_ms[k];
   ms8[6] = D->svd_sweeps32;
   ms8[7] = D->svd_sweeps64;
+  return MRD_OK;
+}
+
+int mrd_dmrg_svd_stats(const mrd_dmrg* D, double* out6) {
+  if (!D || !out6) return MRD_E_ARG;
+  for (int k = 0; k < 6; ++k) out6[k] = D->svd_stats[k];
   return MRD_OK;
 }
 

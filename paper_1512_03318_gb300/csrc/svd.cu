@@ -219,9 +219,10 @@ template <int MODE, class T, class T2, class S2>
 __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf, int vf,
                              const int64_t* __restrict__ grp_prefix, int nblk, int round, int W, T tol,
                              const double* __restrict__ fro2, double zero_rel, int* __restrict__ rotated,
-                             int* __restrict__ last_rot, int sweep) {
+                             int* __restrict__ last_rot, int sweep, unsigned long long* __restrict__ wctr) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ int n_rot;
+  __shared__ unsigned long long n_tested, n_rotated;   // element-pairs tested / rotated
   __shared__ int s_last[32];   // sweep in which each staged column last rotated
   __shared__ FF s_norm[32];    // float-float column norms (MODE 2)
   const int64_t cta = blockIdx.x;
@@ -244,7 +245,10 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
   T2* V = vf >= 0 ? work + d[vf] : nullptr;
   S2* sx = (S2*)smem_raw;                      // 2W columns of length p
   S2* sv = sx + (int64_t)2 * W * p;            // 2W columns of length r (V, MODE 0)
-  if (threadIdx.x == 0) n_rot = 0;
+  if (threadIdx.x == 0) {
+    n_rot = 0;
+    n_tested = n_rotated = 0;
+  }
   // float-float columns are held scaled by ff_scale(fro2) (svd_ff_io)
   const double up = MODE == 2 ? ff_scale(fro2[b]) : 1.0;
   // stage: local column c < W is column gI*W + c, c >= W is column gJ*W + c - W
@@ -303,9 +307,13 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
       rot = jacobi_pair<T, T2>(sx + (int64_t)i * p, sx + (int64_t)j * p, p, V ? sv + (int64_t)i * r : nullptr,
                                V ? sv + (int64_t)j * r : nullptr, r, tol, floor2, lane);
     }
+    if (lane == 0) atomicAdd(&n_tested, (unsigned long long)p);
     if (rot) {
       ++mine;
-      if (lane == 0) s_last[i] = s_last[j] = sweep;
+      if (lane == 0) {
+        s_last[i] = s_last[j] = sweep;
+        atomicAdd(&n_rotated, (unsigned long long)p);
+      }
     }
     __syncwarp();
   };
@@ -346,7 +354,11 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     last_rot[d[8] + gc] = s_last[lc];
   }
   __syncthreads();
-  if (threadIdx.x == 0 && n_rot) atomicAdd(rotated, n_rot);
+  if (threadIdx.x == 0) {
+    if (n_rot) atomicAdd(rotated, n_rot);
+    atomicAdd(&wctr[0], n_tested);
+    atomicAdd(&wctr[1], n_rotated);
+  }
 }
 
 // FP32 working copies: X32 (descriptor field 10) from X, V32 (field 11) = identity.
@@ -561,7 +573,7 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32) {
 // float-float copy xff (same offsets, see svd_ff_io).
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
                        int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
-                       int* last_rot, int sweep, cudaStream_t s) {
+                       int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -575,10 +587,10 @@ cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int
   }
   if (xff)
     k_svd_bround<2, double, float4, float4><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        xff, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep);
+        xff, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
   else
     k_svd_bround<1, double, double2, double2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep);
+        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -594,7 +606,7 @@ cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, 
 
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
                          int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
-                         int sweep, cudaStream_t s) {
+                         int sweep, unsigned long long* wctr, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -604,7 +616,7 @@ cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_pre
     attr = true;
   }
   k_svd_bround<0, float, float2, float2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-      w32, blk, 10, 11, grp_prefix, nblk, round, W, tol, fro2, 1e-12, rotated, last_rot, sweep);
+      w32, blk, 10, 11, grp_prefix, nblk, round, W, tol, fro2, 1e-12, rotated, last_rot, sweep, wctr);
   mrd::count_launch();
   return cudaGetLastError();
 }
