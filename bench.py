@@ -277,6 +277,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fast-restarts", type=int, default=8, help="restarts of the reduced-precision Lanczos")
     ap.add_argument("--only-matvec", action="store_true", help="H_eff throughput only (profiling runs)")
+    ap.add_argument("--profile-update", action="store_true",
+                    help="warm-up updates, then one update inside a CUDA profiler range (ncu --profile-from-start off)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -311,6 +313,20 @@ def main():
         mv = matvec_throughput(P, ctx, torch, dev, stream)
         print(json.dumps({"only_matvec": True, "chi": chi, "heff_tflops": {k: mv[k]["tflops"] for k in PREC},
                           "heff_ms_steps": {k: [mv[k]["ms_step1"], mv[k]["ms_step2"]] for k in PREC}}))
+        return 0
+
+    if args.profile_update:
+        st = make_state(P, ctx, mpo, chi, caps, seed)
+        for k in range(args.warmup):
+            st.update(centre + k, +1, mixed)
+        torch.cuda.synchronize(dev)
+        torch.cuda.cudart().cudaProfilerStart()
+        e, trunc = st.update(centre + args.warmup, +1, mixed)
+        torch.cuda.synchronize(dev)
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"profile_update": True, "chi": chi, "energy": e, "discarded_weight": trunc,
+                          "phase_ms": st.phase_ms(), "svd_stats": st.svd_stats(), "lanczos_stats": st.stats()}))
+        st.close()
         return 0
 
     def barrier():
