@@ -494,7 +494,8 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     sc.ncta = pre[nb];
     return sc;
   };
-  const Sched s32 = schedule(16, true, pp.data()), s64 = schedule(8, false, pp.data() + nb + 1);
+  const bool ff_cols = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
+  const Sched s32 = schedule(16, true, pp.data()), s64 = schedule(ff_cols ? 16 : 8, false, pp.data() + nb + 1);
   if (s32.smem > kSvdMaxSmemHost || s64.smem > kSvdMaxSmemHost)
     return mrd_fail(ctx, MRD_E_OOM, "block SVD: a block is too large for the shared-memory Jacobi rounds");
   MRD_CUDA(ctx, D->svd_blk.need(blk.size() * 8));

@@ -175,10 +175,24 @@ struct TcArgs {
   double2* f_out;          // FP64 output (mode 1)
   int prec;
   int* err;
+  const int2* items;       // per tile item: (task, tile within the task), or null: search the prefix
   int ntile;               // B rows per tile (multiple of 16, at most 128)
   int nstages;             // shared-memory pipeline depth (at most kTcMaxStages)
   int stage_bytes;
 };
+
+// Task and tile of a work item: one load from the host-built item table, else a binary
+// search over the tile prefix (per-task launches, one task).
+__device__ __forceinline__ void item_of(const TcArgs& g, int64_t item, int64_t& t, int64_t& local) {
+  if (g.items) {
+    const int2 v = g.items[item];
+    t = v.x;
+    local = v.y;
+  } else {
+    t = find_task(g.prefix, g.n_tasks, item);
+    local = item - g.prefix[t];
+  }
+}
 
 // Accumulator slots in TMEM: slot b holds C_re at columns 256 b and C_im at 256 b + 128.
 constexpr int kAccSlots = 2;
@@ -272,10 +286,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
     uint32_t phase = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-      const int64_t t = find_task(g.prefix, g.n_tasks, item);
+      int64_t t, local;
+      item_of(g, item, t, local);
       const int64_t* task = g.tasks + TCT * t;
       const int64_t N = task[1];
-      const int64_t local = item - g.prefix[t];
       const int64_t tiles_n = (N + ntile - 1) / ntile;
       const int64_t rt = local / tiles_n, nt = local % tiles_n;
       const int64_t npad = ((N + 15) / 16) * 16;
@@ -306,10 +320,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
     int slot = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-      const int64_t t = find_task(g.prefix, g.n_tasks, item);
+      int64_t t, local;
+      item_of(g, item, t, local);
       const int64_t* task = g.tasks + TCT * t;
       const int64_t N = task[1];
-      const int64_t local = item - g.prefix[t];
       const int64_t tiles_n = (N + ntile - 1) / ntile;
       const int64_t nt = local % tiles_n;
       const int64_t npad = ((N + 15) / 16) * 16;
@@ -378,10 +392,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
     int slot = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-      const int64_t t = find_task(g.prefix, g.n_tasks, item);
+      int64_t t, local;
+      item_of(g, item, t, local);
       const int64_t* task = g.tasks + TCT * t;
       const int64_t M = task[0], N = task[1];
-      const int64_t local = item - g.prefix[t];
       const int64_t tiles_n = (N + ntile - 1) / ntile;
       const int64_t rt = local / tiles_n, nt = local % tiles_n;
       ok = mbar_wait(smem_u32(&bar_acc_full[slot]), (acc_phase >> slot) & 1, g.err, 14);
@@ -457,8 +471,8 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
 }
 
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
-                    const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
-                    int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s) {
+                    const int64_t* prefix, const int2* items, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out,
+                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   cudaError_t ea = tc_gemm_init();
   if (ea != cudaSuccess) return ea;
@@ -466,7 +480,7 @@ cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t*
   if (cfg.stages < 1 || cfg.stages > kTcMaxStages || cfg.ntile < 16 || cfg.ntile > 128 || cfg.ntile % 16 ||
       smem > kTcMaxSmem)
     return cudaErrorInvalidValue;
-  TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, cfg.ntile, cfg.stages,
+  TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, items, cfg.ntile, cfg.stages,
            tc_stage_bytes(prec, cfg.ntile)};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
   k_tc_gemm<<<(unsigned)grid, 192, smem, s>>>(g);

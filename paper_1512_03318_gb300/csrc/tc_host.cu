@@ -12,8 +12,8 @@ namespace mrd {
 cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int prec, cudaStream_t s);
 cudaError_t tc_gemm_init();
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
-                    const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out,
-                    int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s);
+                    const int64_t* prefix, const int2* items, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out,
+                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s);
 }  // namespace mrd
 
 struct Tc {
@@ -31,6 +31,7 @@ struct Tc {
   // per-task launches: [0, tiles of task t] pairs (device) and tiles per task (host)
   int64_t *pt1 = nullptr, *pt2 = nullptr;
   std::vector<int64_t> tiles1, tiles2;
+  int2 *it1 = nullptr, *it2 = nullptr;   // item tables of the grouped launches
   int* err = nullptr;
 };
 
@@ -218,6 +219,13 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   for (size_t t = 0; t + 1 < p1.size(); ++t) q1[2 * t + 1] = p1[t + 1] - p1[t];
   for (size_t t = 0; t + 1 < p2.size(); ++t) q2[2 * t + 1] = p2[t + 1] - p2[t];
   TALLOC(T->pt1, q1.size()); TALLOC(T->pt2, q2.size());
+  // item tables: (task, tile within task) of every tile, in launch order
+  std::vector<int2> i1, i2;
+  for (size_t t = 0; t + 1 < p1.size(); ++t)
+    for (int64_t l = 0; l < p1[t + 1] - p1[t]; ++l) i1.push_back(make_int2((int)t, (int)l));
+  for (size_t t = 0; t + 1 < p2.size(); ++t)
+    for (int64_t l = 0; l < p2[t + 1] - p2[t]; ++l) i2.push_back(make_int2((int)t, (int)l));
+  TALLOC(T->it1, i1.size()); TALLOC(T->it2, i2.size());
 #undef TALLOC
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: device buffers");
   T->lw_bytes = lw_b; T->wr_bytes = wr_b; T->th_bytes = th_b; T->z_bytes = z_b;
@@ -231,6 +239,8 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   up(T->t1, t1); up(T->s1, s1); up(T->p1, p1); up(T->t2, t2); up(T->s2, s2); up(T->p2, p2);
   up(T->j_lw, j_lw); up(T->j_wr, j_wr); up(T->j_th, j_th);
   up(T->pt1, q1); up(T->pt2, q2);
+  if (e == cudaSuccess && !i1.empty()) e = cudaMemcpyAsync(T->it1, i1.data(), i1.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !i2.empty()) e = cudaMemcpyAsync(T->it2, i2.data(), i2.size() * 8, cudaMemcpyHostToDevice, s);
   T->tiles1.resize(p1.size() - 1);
   T->tiles2.resize(p2.size() - 1);
   for (size_t t = 0; t < T->tiles1.size(); ++t) T->tiles1[t] = q1[2 * t + 1];
@@ -277,10 +287,10 @@ int time_cfg(mrd_heff* h, double* ms) {
   for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
     if (r == 1) e = cudaEventRecord(a, s);
     if (e == cudaSuccess)
-      e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
+      e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
                   h->n_sm, s);
     if (e == cudaSuccess)
-      e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
+      e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
                   s);
   }
   float f = 0.f;
@@ -400,18 +410,18 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, tp, s));
   if (e0) MRD_CUDA(ctx, cudaEventRecord(e0, s));
   if (!h->per_task) {
-    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
+    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
                           h->n_sm, s));
     if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
-    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
+    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
                           T->err, h->n_sm, s));
   } else {   // one launch per task: the per-block baseline of the grouped persistent launch
     for (int64_t t = 0; t < T->n1; ++t)
-      MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, 1, T->tiles1[t], T->z, nullptr, tp,
+      MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, nullptr, 1, T->tiles1[t], T->z, nullptr, tp,
                             T->cfg, T->err, h->n_sm, s));
     if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
     for (int64_t t = 0; t < T->n2; ++t)
-      MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, 1, T->tiles2[t], nullptr,
+      MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, nullptr, 1, T->tiles2[t], nullptr,
                             (double2*)out, tp, T->cfg, T->err, h->n_sm, s));
   }
   if (e2) MRD_CUDA(ctx, cudaEventRecord(e2, s));
