@@ -3,19 +3,20 @@
 Step: one two-site update at bond dimension chi = 3200 on the Ly = 10 interacting Hofstadter
 cylinder (flux 1/10, t = 1, V = 1, one particle per ring, Lx = 12), mixed real/momentum-space
 MPO built by the library: H_eff tables, theta, Lanczos with split-BF16 tensor-core matvecs,
-FP64 refinement of the ground vector, block SVD and truncation, environment update.
-The state is a seeded random MPS, left-canonical left of the centre and right-canonical right
-of it, with genuine environments contracted from the ends; bond sectors follow the synthetic
-sector recipe of `synth` (70 sectors of dims 4..277 at chi = 3200). Successive steps move the
-centre one site to the right. `value` is seconds per update (whole job: wall / updates).
+float-float Rayleigh-quotient refinement of the ground vector, float-float block SVD and
+truncation, float-float environment update. The state is a seeded random MPS, left-canonical
+left of the centre and right-canonical right of it, with genuine environments contracted from
+the ends; bond sectors follow the synthetic sector recipe of `synth` (70 sectors of dims 4..277
+at chi = 3200). Successive steps move the centre one site to the right. `value` is seconds per
+update (lower is better).
 
-Also measured in the same run: the FP64 form of the update at the same accuracy, the energy
-error of the mixed form against a converged FP64 reference of the same H_eff, H_eff
-throughput (TFLOP/s, definition-order flops) in FP64, TF32 and split BF16 on the Lx = 20
-cylinder's mid-ring sites with random environments, and the CPU oracle.
+Also measured in the same run: the plain FP64 form of the update, the energy error of the
+mixed form against a converged FP64 reference of the same H_eff, H_eff throughput (TFLOP/s,
+definition-order flops) in FP64, float-float, TF32 and split BF16 on the Lx = 20 cylinder's
+mid-ring sites with random environments, and the CPU oracle (s/update from a bounded sample).
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; N > 1 under torchrun runs independent
-replicas (weak scaling). --impl reference times the CPU oracle.
+replicas (weak scaling). --impl reference times the CPU oracle in the same unit.
 """
 from __future__ import annotations
 
@@ -128,72 +129,93 @@ class ClockSampler:
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
 
 def oracle_workload():
-    """The matvec workload for the CPU oracle: its own MPO, the same seeded sectors and
-    operands as the GPU matvec measurement."""
+    """The first H_eff of the timed updates for the CPU oracle: the oracle's own MPO of the
+    10 x 12 cylinder at the centre sites, the seeded bond sectors that cap the centre bonds of
+    the GPU state, random environments and theta of those shapes."""
     from oracle import blocksparse as B
     from oracle import mpo as M
-    site = update_centre(LX_MATVEC)
-    mp = M.build_mpo(LX_MATVEC, LY, FLUX_P / FLUX_Q, T_HOP, V_INT, "mixed")
-    left = B.BondSectors(synth.bond_sectors(CHI, LY, LX_MATVEC // 2, synth.substream(SEED, 1)))
-    right = B.BondSectors(synth.bond_sectors(CHI, LY, LX_MATVEC // 2, synth.substream(SEED, 2)))
+    site = update_centre(LX_UPDATE)
+    caps = update_caps(LX_UPDATE, CHI)
+    mp = M.build_mpo(LX_UPDATE, LY, FLUX_P / FLUX_Q, T_HOP, V_INT, "mixed")
+    left = B.BondSectors([((n, k), d) for n, k, d in caps[site]])
+    right = B.BondSectors([((n, k), d) for n, k, d in caps[site + 2]])
     m1, m2, mod = site % LY, (site + 1) % LY, LY
     cl, cm, cr = mp.bond_charges[site], mp.bond_charges[site + 1], mp.bond_charges[site + 2]
     wi, wj = mp.entries[site], mp.entries[site + 1]
     lay = B.theta_layout(left, right, m1, m2, mod)
-    s = synth.substream(SEED, 100)
+    s = synth.substream(SEED, 200)
     lflat = synth.complex_pm1(synth.substream(s, 8), B.env_size(B.env_left_layout(left, cl, mod)))
     rflat = synth.complex_pm1(synth.substream(s, 9), B.env_size(B.env_right_layout(right, cr, mod)))
     tflat = synth.complex_pm1(synth.substream(s, 10), B.theta_size(lay))
     return B, (left, right, m1, m2, mod, cl, cm, cr, wi, wj), (lflat, rflat, tflat)
 
 
+ORACLE_MATVECS = 30   # matvecs of one oracle update: its Lanczos step cap
+
+
 def oracle_step_factory():
     """One CPU step: the oracle's H_eff restricted to the output blocks of every fourth left
-    sector (a fixed quarter of the output), about a second of work."""
+    sector (a fixed quarter of the output, a second or so of work). Returns the step, its flops
+    and the flops of the full H_eff."""
     B, args, flats = oracle_workload()
     rows = set(range(0, len(args[0].dims), 4))
     flops = B.heff_flops(*args, rows=rows)
+    full = B.heff_flops(*args)
 
     def step():
         t0 = time.perf_counter()
         B.heff_apply(*args, *flats, rows=rows)
         return time.perf_counter() - t0
-    return step, flops
+    return step, flops, full
+
+
+def oracle_s_per_update(t_sample, flops, full):
+    """Seconds per two-site update of the oracle, from one sample step: the full matvec time
+    (sample time x full / sample flops) times ORACLE_MATVECS. The oracle's SVD and environment
+    update are left out, so this is a lower bound."""
+    return t_sample * full / flops * ORACLE_MATVECS
+
+
+def oracle_sample_text(flops, full, t):
+    return (f"oracle block-sparse H_eff (numpy complex128, loops over charge blocks) of the first update's H_eff "
+            f"(Ly={LY}, Lx={LX_UPDATE}, chi={CHI}) on the output blocks of every 4th left sector "
+            f"({flops / 1e9:.1f} of {full / 1e9:.1f} GFLOP, {t:.2f} s), scaled to the full matvec and to "
+            f"{ORACLE_MATVECS} matvecs per update (the oracle Lanczos cap); SVD and environment update not "
+            f"included: a lower bound")
 
 
 def cpu_baseline(n_steps=3):
-    step, flops = oracle_step_factory()
+    step, flops, full = oracle_step_factory()
     step()
     times = [step() for _ in range(n_steps)]
     t = statistics.median(times)
-    return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"oracle H_eff (numpy complex128, plain loops over charge blocks) at chi={CHI}, Ly={LY}, on the "
-                      f"output blocks of every 4th left sector ({flops / 1e9:.1f} GFLOP), median of {n_steps} after "
-                      f"1 warm-up, {t:.2f} s each; compare with heff_tflops"}
+    return {"value": oracle_s_per_update(t, flops, full), "unit": "s/update", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": oracle_sample_text(flops, full, t) + f"; median of {n_steps} after 1 warm-up"}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, timed on the host cores on bounded samples of the
+    update workload, in the bench's own metric (s/update, lower is better)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    step, flops = oracle_step_factory()
+    step, flops, full = oracle_step_factory()
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
     times = [step() for _ in range(args.steps)]
     total = time.perf_counter() - t0
-    value = flops * args.steps / total / 1e12
+    value = oracle_s_per_update(total / args.steps, flops, full)
     cores = len(os.sched_getaffinity(0))
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/update", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": f"H_eff matvec, Ly={LY} chi={CHI} (CPU oracle, numpy, host cores)",
-                       "sample": "output blocks of every 4th left sector per step"},
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} steps of the oracle H_eff on a fixed quarter of the output "
-                                       f"blocks ({flops / 1e9:.1f} GFLOP each), median "
-                                       f"{1e3 * statistics.median(times):.0f} ms"},
-            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": workload_name(CHI), "chi": CHI, "ly": LY, "lx": LX_UPDATE,
+                       "sample": "each step: the oracle H_eff on every 4th left sector's output blocks"},
+            "cpu_baseline": {"value": value, "unit": "s/update", "cores": cores, "kind": "oracle",
+                             "sample": oracle_sample_text(flops, full, statistics.median(times)) +
+                                       f"; {args.steps} steps after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": "s/update", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
