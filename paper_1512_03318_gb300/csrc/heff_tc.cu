@@ -120,43 +120,65 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // Pack FP64 complex blocks into panels. Each job: src element offset, src row stride,
 // transpose flag (0: panel row r, col k = src[r * ld + k]; 1: = src[k * ld + r]), rows, K,
-// destination panel byte offset, row tile height (128 for A, padded N for B), nkt.
+// destination panel byte offset, row tile height (128 for A, the tile column count for B), nkt.
+// One thread writes one 16-byte chunk of a panel row in every plane: 4 consecutive K values
+// (TF32) or 8 (BF16). For transposed sources consecutive threads take consecutive panel rows,
+// so each of the chunk's reads is coalesced; K beyond the block is written as zero padding.
 __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ dst, const int64_t* __restrict__ jobs,
                        int njobs, int prec) {
+  const bool tf32 = prec == TC_TF32;
+  const int kc = tf32 ? 4 : 8;                   // K values per 16-byte chunk
+  const int kpt = tf32 ? 32 : 64;                // K values per 128-byte row
+  const int planes = tf32 ? 2 : 4;
   for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
     const int64_t* d = jobs + TCJ * j;
     const int64_t s_off = d[0], ld = d[1], trans = d[2], rows = d[3], K = d[4], p_off = d[5], rowtile = d[6],
                   nkt = d[7], npad = d[8];
-    const int ebytes = prec == TC_TF32 ? 4 : 2;
-    const int kpt = 128 / ebytes;
-    const int planes = prec == TC_TF32 ? 2 : 4;
-    for (int64_t e = threadIdx.x; e < rows * K; e += blockDim.x) {
-      int64_t r, k;
-      double2 v;
-      if (!trans) {
-        r = e / K; k = e % K;
-        v = src[s_off + r * ld + k];
-      } else {
-        k = e / rows; r = e % rows;   // consecutive threads read consecutive source columns
-        v = src[s_off + k * ld + r];
-      }
-      const int64_t rt = r / rowtile, kt = k / kpt;
+    const int64_t nch = (K + kc - 1) / kc;       // chunks per row
+    for (int64_t e = threadIdx.x; e < rows * nch; e += blockDim.x) {
+      int64_t r, ch;
+      if (trans) { ch = e / rows; r = e % rows; }   // consecutive threads: consecutive rows
+      else { r = e / nch; ch = e % nch; }           // consecutive threads: consecutive chunks
+      const int64_t k0 = ch * kc;
+      const int64_t rt = r / rowtile, kt = k0 / kpt;
       const int64_t nrow = npad - rt * rowtile < rowtile ? npad - rt * rowtile : rowtile;
-      const int64_t tile_bytes = nrow * 128;   // one plane of this row tile
+      const int64_t tile_bytes = nrow * 128;       // one plane of this row tile
       uint8_t* tile = dst + p_off + rt * nkt * planes * rowtile * 128 + kt * planes * tile_bytes;
-      const uint32_t off = sw128((uint32_t)(r % rowtile), (uint32_t)((k % kpt) * ebytes));
-      if (prec == TC_TF32) {
-        *(float*)(tile + off) = tf32_rna((float)v.x);
-        *(float*)(tile + tile_bytes + off) = tf32_rna((float)v.y);
+      const uint32_t off = sw128((uint32_t)(r % rowtile), (uint32_t)((k0 % kpt) * (tf32 ? 4 : 2)));
+      if (tf32) {
+        float4 re, im;
+        float* pr = (float*)&re;
+        float* pi = (float*)&im;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t k = k0 + q;
+          double2 v = make_double2(0.0, 0.0);
+          if (k < K) v = trans ? src[s_off + k * ld + r] : src[s_off + r * ld + k];
+          pr[q] = tf32_rna((float)v.x);
+          pi[q] = tf32_rna((float)v.y);
+        }
+        *(float4*)(tile + off) = re;
+        *(float4*)(tile + tile_bytes + off) = im;
       } else {
-        const __nv_bfloat16 rh = __double2bfloat16(v.x);
-        const __nv_bfloat16 rl = __double2bfloat16(v.x - (double)__bfloat162float(rh));
-        const __nv_bfloat16 ih = __double2bfloat16(v.y);
-        const __nv_bfloat16 il = __double2bfloat16(v.y - (double)__bfloat162float(ih));
-        *(__nv_bfloat16*)(tile + off) = rh;
-        *(__nv_bfloat16*)(tile + tile_bytes + off) = rl;
-        *(__nv_bfloat16*)(tile + 2 * tile_bytes + off) = ih;
-        *(__nv_bfloat16*)(tile + 3 * tile_bytes + off) = il;
+        uint4 pl[4];
+        __nv_bfloat16* b0 = (__nv_bfloat16*)&pl[0];
+        __nv_bfloat16* b1 = (__nv_bfloat16*)&pl[1];
+        __nv_bfloat16* b2 = (__nv_bfloat16*)&pl[2];
+        __nv_bfloat16* b3 = (__nv_bfloat16*)&pl[3];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int64_t k = k0 + q;
+          double2 v = make_double2(0.0, 0.0);
+          if (k < K) v = trans ? src[s_off + k * ld + r] : src[s_off + r * ld + k];
+          const __nv_bfloat16 rh = __double2bfloat16(v.x);
+          const __nv_bfloat16 ih = __double2bfloat16(v.y);
+          b0[q] = rh;
+          b1[q] = __double2bfloat16(v.x - (double)__bfloat162float(rh));
+          b2[q] = ih;
+          b3[q] = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) *(uint4*)(tile + q * tile_bytes + off) = pl[q];
       }
     }
   }
