@@ -283,6 +283,61 @@ def matvec_throughput(P, ctx, torch, dev, stream, reps=10):
     return res
 
 
+def real_vs_mixed(P, ctx, torch, dev, stream):
+    """The paper's comparison of the two bases (Sec. III.B, Fig. 3) on this build's own code:
+    the same Hofstadter cylinder (Lx = 20, mid-ring sites) at the same chi, with the mixed
+    basis (charges N and K mod Ly, the library's mixed-space MPO) and with the real-space basis
+    (charge N only, the real-space MPO, D = 3 Ly + 2). Reports the H_eff time per application
+    (BF16X3 and FP64), the definition-order flops and the sizes of theta and of the two
+    environments. Operand values are seeded random numbers (timing does not depend on them)."""
+    site = update_centre(LX_MATVEC)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(SEED)
+    out = {}
+    for name, basis, ly_q in (("mixed", P.MRD_BASIS_MIXED, LY), ("real", P.MRD_BASIS_REAL, 1)):
+        mpo = P.MPO(None, LX_MATVEC, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, basis)
+        sec = lambda tag: np.array([[q[0], q[1], d] for q, d in synth.bond_sectors(CHI, ly_q, LX_MATVEC // 2,
+                                                                                  synth.substream(SEED, tag))],
+                                   dtype=np.int32)
+        i_idx, i_val = mpo.site(site)
+        j_idx, j_val = mpo.site(site + 1)
+        m1, m2 = (site % LY, (site + 1) % LY) if basis == P.MRD_BASIS_MIXED else (0, 0)
+        h = P.Heff(ctx, sec(1), sec(2), m1, m2, mpo.modulus, mpo.bond(site), mpo.bond(site + 1), mpo.bond(site + 2),
+                   i_idx, i_val, j_idx, j_val)
+        rnd = lambda n: torch.randn(n, dtype=torch.complex128, device=dev, generator=gen)
+        L, R, T = rnd(h.lenv_len), rnd(h.renv_len), rnd(h.theta_len)
+        o = torch.empty_like(T)
+        h.set_env(L, R)
+        f_def = h.flops()[0]
+        res = {"theta_elems": h.theta_len, "env_bytes": 16 * (h.lenv_len + h.renv_len), "flops_definition": f_def,
+               "mpo_bond_dim": int(len(mpo.bond(site + 1)))}
+        for pname, n in (("bf16x3", 5), ("fp64", 1)):
+            prec = PREC[pname]
+            h.apply(T, o, prec)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                h.apply(T, o, prec)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            res[f"ms_{pname}"] = e0.elapsed_time(e1) / n
+        h.close()
+        del L, R, T, o
+        out[name] = res
+    out["ratio_real_over_mixed"] = {k: out["real"][k] / out["mixed"][k]
+                                    for k in ("ms_bf16x3", "ms_fp64", "flops_definition", "env_bytes", "theta_elems")}
+    return out
+
+
+def real_vs_mixed_or_note(P, ctx, torch, dev, stream):
+    try:
+        return real_vs_mixed(P, ctx, torch, dev, stream)
+    except (P.MrdError, torch.cuda.OutOfMemoryError) as e:   # the real-space problem is ~20x larger
+        torch.cuda.empty_cache()
+        return {"skipped": f"{type(e).__name__}: {e}"}
+
+
 def make_state(P, ctx, mpo, chi, caps, seed):
     return P.DMRG(ctx, mpo, LX_UPDATE, 0, chi, seed=seed, center=update_centre(LX_UPDATE), caps=caps)
 
@@ -447,6 +502,7 @@ def main():
 
     # ---- H_eff throughput per precision (Lx = 20 mid-ring sites, random environments)
     mv = matvec_throughput(P, ctx, torch, dev, stream)
+    rvm = real_vs_mixed_or_note(P, ctx, torch, dev, stream)
 
     if rank != 0:
         if dist is not None:
@@ -517,6 +573,7 @@ def main():
         "heff_bf16x3_ms_grouped_vs_per_task": [round(mv["bf16x3"]["ms"], 4),
                                                round(mv["bf16x3"]["ms_per_task_launches"], 3)],
         "heff_flops": {"definition": mv["flops_definition"], "executed": mv["flops_executed"]},
+        "real_vs_mixed_heff": rvm,
         "roofline": roof,
         "roofline_tc_bf16x3": {"kernel": "k_tc_gemm BF16X3 (steps 1+2), Lx=20 matvec", "bound": "tensor",
                                "achieved": tc_hw, "peak": bf16_peak, "unit": "TFLOP/s", "frac": tc_hw / bf16_peak,
