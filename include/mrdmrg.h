@@ -269,6 +269,13 @@ int mrd_dmrg_phase_ms(const mrd_dmrg* d, double* ms8);
  * column length over tested pairs), element-pairs rotated, final sweeps, ms of the FP32
  * pre-sweeps (0 without), svd_mode}. */
 int mrd_dmrg_svd_stats(const mrd_dmrg* d, double* out6);
+/* Momentum-resolved entanglement spectrum (Sec. III.C): the Schmidt values lambda of the
+ * bond cut by the last two-site update (*bond = i + 1 for an update of sites i, i+1), one per
+ * kept Schmidt state, with the charges (N, K) of its left part in nk (2 per value). The values
+ * of one sector are consecutive, sectors in increasing (N, K); sum lambda^2 = 1. They are the
+ * norms of the centre tensor's rows (or columns, moving left) against the isometric canonical
+ * factor; entanglement energies are -2 ln lambda. Call with nk = values = NULL for *n. */
+int mrd_dmrg_schmidt(const mrd_dmrg* d, int32_t* bond, int64_t* n, int32_t* nk, double* values);
 /* Energy, discarded weight and matvec count of the last two-site update; the count is the
  * reduced-precision (or FP64) Lanczos matvecs plus 1000 times the FP64 refinement matvecs. */
 int mrd_dmrg_stats(const mrd_dmrg* d, double* energy, double* trunc_err, int32_t* lanczos_iters);

@@ -122,6 +122,8 @@ _SIGS = {
     "mrd_heff_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "mrd_heff_tc_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "mrd_dmrg_svd_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mrd_dmrg_schmidt": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_double)]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
 }
@@ -357,6 +359,19 @@ class DMRG:
         f = (C.c_double * 8)()
         self.ctx.check(lib().mrd_dmrg_phase_ms(self.h, f))
         return int(f[6]), int(f[7])
+
+    def schmidt(self):
+        """(bond, {(N, K): Schmidt values}) of the bond cut by the last update (mrd_dmrg_schmidt)."""
+        b, n = C.c_int32(), C.c_int64()
+        self.ctx.check(lib().mrd_dmrg_schmidt(self.h, C.byref(b), C.byref(n), None, None))
+        nk = np.zeros(2 * max(n.value, 1), dtype=np.int32)
+        val = np.zeros(max(n.value, 1), dtype=np.float64)
+        self.ctx.check(lib().mrd_dmrg_schmidt(self.h, C.byref(b), C.byref(n), _p32(nk),
+                                              val.ctypes.data_as(C.POINTER(C.c_double))))
+        out = {}
+        for j in range(n.value):
+            out.setdefault((int(nk[2 * j]), int(nk[2 * j + 1])), []).append(val[j])
+        return b.value, {k: np.sort(np.array(v))[::-1] for k, v in out.items()}
 
     def svd_stats(self):
         """(sweep ms, element-pairs tested, element-pairs rotated, sweeps, FP32 pre-sweep ms, svd_mode)."""

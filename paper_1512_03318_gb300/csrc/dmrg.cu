@@ -158,6 +158,27 @@ __global__ void __launch_bounds__(256) k_sumsq_partial(const double2* __restrict
 // Renormalise the centre tensor to unit norm: kept = |x|^2 (the weight captured by the
 // orthonormal canonical factor), info[0] = 1/sqrt(kept), info[1] = discarded weight
 // 1 - kept / |theta|^2 with |theta|^2 = sum of the blocks' fro2.
+// Schmidt values of the bond an update cut (Sec. III.C): per kept bond sector, the norms of the
+// centre tensor's rows (moving right: the centre is (a) x (s2, b)) or columns (moving left:
+// (s1, a) x (b)). The canonical factor is an isometry, so these are the weights of the
+// kept Schmidt states. Table row: offset, values, length of a row/column, leading dimension,
+// by_rows, output offset. One CTA per bond sector, fixed summation order.
+__global__ void k_schmidt(const double2* __restrict__ c, const int64_t* __restrict__ tab, int nblk,
+                          double* __restrict__ out) {
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int64_t* t = tab + 6 * b;
+  const int64_t off = t[0], nv = t[1], len = t[2], ld = t[3], by_rows = t[4], o = t[5];
+  for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+    double acc = 0.0;
+    for (int64_t q = 0; q < len; ++q) {
+      const double2 x = by_rows ? c[off + v * ld + q] : c[off + q * ld + v];
+      acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    }
+    out[o + v] = sqrt(acc);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_scale_unit(double2* __restrict__ x, int64_t n,
                                                     const double* __restrict__ partial,
                                                     const double* __restrict__ fro2, int nblk,
@@ -295,6 +316,11 @@ struct mrd_dmrg {
   int svd_sweeps32 = 0, svd_sweeps64 = 0;
   bool gemm_ff = false;   // grouped GEMMs of the update in float-float (refine_prec MRD_PREC_FF)
   double last_energy = 0.0, last_trunc = 0.0;
+  // Schmidt values of the bond cut by the last update: bond index, (N, K) and value per state
+  int schmidt_bond = -1;
+  std::vector<int32_t> schmidt_nk;
+  std::vector<double> schmidt_val;
+  Buf schmidt_tab, schmidt_out;
   int last_iters = 0, last_refine = 0;
   bool timing = false;
   double kms[4] = {0, 0, 0, 0};   // accumulated GEMM ms: tensor-core step 1, step 2, FP64 step 1, step 2
@@ -1118,6 +1144,38 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
     MRD_CUDA(ctx, cudaGetLastError());
     MRD_CUDA(ctx, cudaMemcpyAsync(info, D->svd_info.p, 2 * 8, cudaMemcpyDeviceToHost, ctx->stream));
   }
+  {
+    // Schmidt values of the new bond i+1
+    std::vector<int64_t> tab;
+    int64_t nvals = 0;
+    int nbi = 0;
+    for (size_t b = 0; b < mids.size(); ++b) {
+      if (keep[b] == 0) continue;
+      const int64_t* d = &blk[SVF * b];
+      const int64_t k = keep[b];
+      if (direction > 0) tab.insert(tab.end(), {Y.goff[nbi], k, d[1], Y.gext[nbi], 1, nvals});
+      else tab.insert(tab.end(), {X.goff[nbi], k, d[0], k, 0, nvals});
+      nvals += k;
+      ++nbi;
+    }
+    MRD_CUDA(ctx, D->schmidt_tab.need(std::max<size_t>(tab.size(), 1) * 8));
+    MRD_CUDA(ctx, D->schmidt_out.need((size_t)std::max<int64_t>(nvals, 1) * 8));
+    D->schmidt_val.assign(nvals, 0.0);
+    if (nbi > 0) {
+      MRD_CUDA(ctx, cudaMemcpyAsync(D->schmidt_tab.p, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+      k_schmidt<<<nbi, 128, 0, ctx->stream>>>(centre.data.as<double2>(), D->schmidt_tab.as<int64_t>(), nbi,
+                                              D->schmidt_out.as<double>());
+      mrd::count_launch();
+      MRD_CUDA(ctx, cudaGetLastError());
+      MRD_CUDA(ctx, cudaMemcpyAsync(D->schmidt_val.data(), D->schmidt_out.p, (size_t)nvals * 8,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+      MRD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // tab and the host copy
+    }
+    D->schmidt_nk.clear();
+    for (const Sec& q : nb)
+      for (int v = 0; v < q.d; ++v) D->schmidt_nk.insert(D->schmidt_nk.end(), {q.N, q.K});
+    D->schmidt_bond = i + 1;
+  }
   lap(4);
   if (direction > 0) rc = env_left(D, h, i);
   else rc = env_right(D, h, i);
@@ -1205,6 +1263,15 @@ int mrd_dmrg_phase_ms(const mrd_dmrg* D, double* ms8) {
   for (int k = 0; k < 6; ++k) ms8[k] = D->phase_ms[k];
   ms8[6] = D->svd_sweeps32;
   ms8[7] = D->svd_sweeps64;
+  return MRD_OK;
+}
+
+int mrd_dmrg_schmidt(const mrd_dmrg* D, int32_t* bond, int64_t* n, int32_t* nk, double* values) {
+  if (!D || !n) return MRD_E_ARG;
+  if (bond) *bond = D->schmidt_bond;
+  *n = (int64_t)D->schmidt_val.size();
+  if (nk && !D->schmidt_nk.empty()) std::copy(D->schmidt_nk.begin(), D->schmidt_nk.end(), nk);
+  if (values && !D->schmidt_val.empty()) std::copy(D->schmidt_val.begin(), D->schmidt_val.end(), values);
   return MRD_OK;
 }
 

@@ -137,3 +137,62 @@ def test_update_canonical_factor_at_production_block_sizes(ctx, prec, svd_mode):
     assert d.bond(i + 1)[:, 2].sum() <= chi
     assert 0.0 <= trunc < 1e-2
     d.close()
+
+
+def _schmidt_after_sweeps(ctx, lx, ly, fq, v, n, k, chi, bond):
+    es, d = run_dmrg(ctx, lx, ly, fq, 1.0, v, n, k, chi, sweeps=8)
+    import paper_1512_03318_gb300 as P
+    p = P.DMRG.params(chi, 1e-14, 40, 1e-14)
+    for i in range(bond):                   # centre back to the bond, moving right
+        d.update(i, +1, p)
+    b, spec = d.schmidt()
+    d.close()
+    assert b == bond
+    return es[-1], spec
+
+
+def _compare_spectra(got, ref, tol):
+    keep = lambda sp: {key: val[val > 1e-4] for key, val in sp.items() if np.any(val > 1e-4)}
+    got, ref = keep(got), keep(ref)
+    assert set(got) == set(ref), (sorted(got), sorted(ref))
+    for key in ref:
+        assert len(got[key]) == len(ref[key]), key
+        assert np.max(np.abs(got[key] - ref[key])) < tol, key
+
+
+def test_entanglement_spectrum_matches_ed(ctx):
+    """Momentum-resolved Schmidt values of the middle bond of the 4 x 4 cylinder (flux 1/4,
+    V = 1, N = 4) at exact bond dimension equal those of the ED ground state, sector by
+    sector (N, K of the left half)."""
+    from oracle import entanglement as E
+    lx, ly, n = 4, 4, 4
+    e_ed = [ed_sector(lx, ly, 0.25, 1.0, 1.0, n, k) for k in range(ly)]
+    k0 = int(np.argmin(e_ed))
+    basis = model.fock_basis(lx * ly, n)
+    basis = np.array([s for s in basis if model.total_momentum(lx, ly, int(s)) == k0], dtype=np.uint64)
+    h = model.mixed_space_hamiltonian(lx, ly, 0.25, 1.0, 1.0, n, basis=basis)
+    w, vec = np.linalg.eigh(h)
+    ref = E.schmidt_spectrum(vec[:, 0], basis, 8, ly)
+    e, got = _schmidt_after_sweeps(ctx, lx, ly, 4, 1.0, n, k0, 256, 8)
+    assert abs(e - w[0]) < 1e-10 * abs(w[0])
+    assert abs(sum(np.sum(v ** 2) for v in got.values()) - 1.0) < 1e-12
+    _compare_spectra(got, ref, 1e-5)
+
+
+def test_entanglement_spectrum_free_fermions(ctx):
+    """V = 0 (3 x 3, flux 1/3, N = 3): the GPU Schmidt values equal the correlation-matrix
+    closed form of the Slater determinant."""
+    from oracle import entanglement as E
+    lx, ly, n = 3, 3, 3
+    e0 = model.free_fermion_ground_energy(lx, ly, 1 / 3, 1.0, n)
+    ref = E.free_fermion_spectrum(lx, ly, 1 / 3, 1.0, n, 4)
+    best = None
+    for k in range(ly):
+        try:
+            e, got = _schmidt_after_sweeps(ctx, lx, ly, 3, 0.0, n, k, 64, 4)
+        except Exception:   # sectors without states of this N
+            continue
+        if best is None or e < best[0]:
+            best = (e, got)
+    assert abs(best[0] - e0) < 1e-10 * abs(e0)
+    _compare_spectra(best[1], ref, 1e-6)
