@@ -3,8 +3,8 @@
 Step: one two-site update at bond dimension chi = 3200 on the Ly = 10 interacting Hofstadter
 cylinder (flux 1/10, t = 1, V = 1, one particle per ring, Lx = 12), mixed real/momentum-space
 MPO built by the library: H_eff tables, theta, Lanczos with split-BF16 tensor-core matvecs,
-float-float Rayleigh-quotient refinement of the ground vector, float-float block SVD and
-truncation, float-float environment update. The state is a seeded random MPS, left-canonical
+float-float Rayleigh-quotient refinement of the ground vector, block SVD (FP32 pre-sweeps,
+float-float Jacobi sweeps) and truncation, float-float environment update. The state is a seeded random MPS, left-canonical
 left of the centre and right-canonical right of it, with genuine environments contracted from
 the ends; bond sectors follow the synthetic sector recipe of `synth` (70 sectors of dims 4..277
 at chi = 3200). Successive steps move the centre one site to the right. `value` is seconds per
@@ -550,8 +550,8 @@ def main():
         "vs_baseline": None, "dtype": "bf16x3+f32x2", "data": "synthetic",
         "config": {"workload": workload_name(chi), "chi": chi, "ly": LY, "lx": LX_UPDATE,
                    "form": f"split-BF16 tensor-core Lanczos (60 per run, up to {args.fast_restarts} restarts) + "
-                           f"float-float Rayleigh-quotient refinement ({args.refine} matvec), float-float "
-                           f"Jacobi SVD and environment updates",
+                           f"float-float Rayleigh-quotient refinement ({args.refine} matvec), block SVD by "
+                           f"FP32 pre-sweeps + float-float Jacobi sweeps, float-float environment update",
                    "l2": "working set > L2 (folded environments, Z intermediate and Lanczos basis, >1 GB)",
                    "parallelism": f"replicas x{world}"},
         "s_per_update_fp64": t64,

@@ -209,7 +209,7 @@ typedef struct {
 
 /* Block SVD sweep arithmetic. The final sweeps stop when every column pair is orthogonal to
  * 1e-14 (FP64) or 5e-13 (float-float: pairs of FP32 numbers, ~48-bit products, on the FP32
- * pipes); FP32 pre-sweeps (to 1e-5) may precede them. */
+ * pipes); FP32 pre-sweeps (to 1e-5, at most 8 sweeps) may precede them. */
 #define MRD_SVD_F32_FF 0   /* FP32 pre-sweeps, float-float sweeps */
 #define MRD_SVD_FF 1       /* float-float sweeps only             */
 #define MRD_SVD_F32_F64 2  /* FP32 pre-sweeps, FP64 sweeps        */

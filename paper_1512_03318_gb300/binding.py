@@ -285,10 +285,11 @@ class DMRG:
     @staticmethod
     def params(chi, cutoff=1e-14, max_iter=30, tol=1e-13, prec=MRD_PREC_FP64, refine_iter=0, refine_tol=1e-13,
                restarts=0, svd_mode=None, refine_prec=None):
-        # FP64 updates stay in FP64 throughout; reduced-precision ones use float-float for the
-        # SVD sweeps, the refinement, the environment updates and the SVD's GEMMs
+        # FP64 updates stay in FP64 throughout; reduced-precision ones use FP32 pre-sweeps and
+        # float-float sweeps for the SVD, and float-float for the refinement, the environment
+        # updates and the SVD's GEMMs
         if svd_mode is None:
-            svd_mode = MRD_SVD_F64 if prec == MRD_PREC_FP64 else MRD_SVD_FF
+            svd_mode = MRD_SVD_F64 if prec == MRD_PREC_FP64 else MRD_SVD_F32_FF
         if refine_prec is None:
             refine_prec = MRD_PREC_FP64 if prec == MRD_PREC_FP64 else MRD_PREC_FF
         return mrd_dmrg_params(chi, cutoff, max_iter, tol, prec, refine_iter, refine_tol, restarts, svd_mode,
