@@ -25,8 +25,10 @@
 
 namespace mrd {
 
-cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
-                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s);
+cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
+                                   const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                                   int n_sm, cudaStream_t s);
+cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
                               const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
                               int n_sm, cudaStream_t s);
@@ -326,6 +328,7 @@ struct mrd_dmrg {
   std::vector<int32_t> schmidt_nk;
   std::vector<double> schmidt_val;
   Buf schmidt_tab, schmidt_out;
+  Buf ff_a, ff_b;   // float-float copies of the operands of a grouped GEMM
   int last_iters = 0, last_refine = 0;
   bool timing = false;
   double kms[4] = {0, 0, 0, 0};   // accumulated GEMM ms: tensor-core step 1, step 2, FP64 step 1, step 2
@@ -365,9 +368,19 @@ int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const d
   MRD_CUDA(ctx, cudaMemcpyAsync(D->gtask.p, g.t.data(), g.t.size() * 8, cudaMemcpyHostToDevice, s));
   if (!g.s.empty()) MRD_CUDA(ctx, cudaMemcpyAsync(D->gseg.p, g.s.data(), g.s.size() * 8, cudaMemcpyHostToDevice, s));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->gpref.p, pref.data(), pref.size() * 8, cudaMemcpyHostToDevice, s));
-  MRD_CUDA(ctx, (D->gemm_ff ? launch_cgemm_ff : launch_cgemm_fp64)(Aop, Bop, C, D->gtask.as<int64_t>(),
-                                                                   D->gseg.as<int64_t>(), D->gpref.as<int64_t>(), nt,
-                                                                   pref[nt], D->n_sm, s));
+  if (D->gemm_ff) {
+    // float-float: split each operand once (one pass over it) instead of on every tile load,
+    // where the FP64 -> float conversions would run on the slow FP64 pipe; same results
+    MRD_CUDA(ctx, D->ff_a.need((size_t)std::max<int64_t>(alen, 1) * 16));
+    MRD_CUDA(ctx, D->ff_b.need((size_t)std::max<int64_t>(blen, 1) * 16));
+    MRD_CUDA(ctx, to_ff(Aop, D->ff_a.as<float4>(), alen, s));
+    MRD_CUDA(ctx, to_ff(Bop, D->ff_b.as<float4>(), blen, s));
+    MRD_CUDA(ctx, launch_cgemm_ff_packed(D->ff_a.as<float4>(), D->ff_b.as<float4>(), nullptr, C, D->gtask.as<int64_t>(),
+                                         D->gseg.as<int64_t>(), D->gpref.as<int64_t>(), nt, pref[nt], D->n_sm, s));
+  } else {
+    MRD_CUDA(ctx, launch_cgemm_fp64(Aop, Bop, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
+                                    nt, pref[nt], D->n_sm, s));
+  }
   // the host task arrays must stay valid until the copies completed
   MRD_CUDA(ctx, cudaStreamSynchronize(s));
   return MRD_OK;
