@@ -2,8 +2,10 @@
 // relies on DMRG as in its refs. W92, S2005, S2011 without restating it).
 //
 // Krylov recursion with full reorthogonalisation: for j = 0, 1, ...
-//   w = H v_j;  two classical Gram-Schmidt passes c = V^+ w, w -= V c  (V = [v_0 .. v_j]);
-//   alpha_j = Re(c_j) summed over both passes;  beta_j = |w|;  v_{j+1} = w / beta_j;
+//   w = H v_j;  a local pass c1 = [v_{j-1} v_j]^+ w, w -= [v_{j-1} v_j] c1 (the three-term
+//   recurrence), then one full classical Gram-Schmidt pass c2 = V^+ w, w -= V c2
+//   (V = [v_0 .. v_j]); alpha_j = Re of v_j's coefficient summed over both passes;
+//   beta_j = |w|;  v_{j+1} = w / beta_j;
 //   lowest eigenpair (E_j, y) of the tridiagonal T_j = tridiag(beta, alpha, beta).
 // Stops when |E_j - E_{j-1}| < tol |E_j|, when beta_j vanishes (invariant subspace) or at
 // max_iter; the ground vector is V y, normalised.
@@ -43,7 +45,12 @@ struct LzState {
 };
 
 // number of vectors of a reduction: nv >= 0 as given, nv < 0 means v_0 .. v_j of the state
-__device__ __forceinline__ int eff_nv(int nv, const LzState* st) { return nv >= 0 ? nv : st->j + 1; }
+// Vectors of a reduction or combination: nv >= 0: v_0 .. v_{nv-1}; nv = -1: v_0 .. v_j (all);
+// nv = -2: v_{j-1}, v_j (the two the three-term recurrence involves; v_0 alone at j = 0).
+__device__ __forceinline__ int eff_nv(int nv, const LzState* st) {
+  return nv >= 0 ? nv : (nv == -1 ? st->j + 1 : (st->j > 0 ? 2 : 1));
+}
+__device__ __forceinline__ int first_v(int nv, const LzState* st) { return nv == -2 && st->j > 0 ? st->j - 1 : 0; }
 
 constexpr int kJB = 4;   // vectors per pass of k_multidot (w is read once per pass)
 
@@ -54,6 +61,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double2* __restr
                                                           double2* __restrict__ partial) {
   __shared__ double sre[kJB][kRedThreads / 32], sim[kJB][kRedThreads / 32];
   const int nv = eff_nv(nv_arg, st);
+  V += (int64_t)first_v(nv_arg, st) * ldv;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b = blockIdx.x * chunk;
   const int64_t e = b + chunk < n ? b + chunk : n;
@@ -120,6 +128,7 @@ __global__ void k_sub_combination(const double2* __restrict__ V, int64_t ldv, in
                                   const LzState* __restrict__ st, const double2* __restrict__ c,
                                   double2* __restrict__ w, int64_t n) {
   const int nv = eff_nv(nv_arg, st);
+  V += (int64_t)first_v(nv_arg, st) * ldv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double2 acc = w[i];
     for (int j = 0; j < nv; ++j) {
@@ -155,11 +164,12 @@ __global__ void k_scale_by_invnorm(const double2* __restrict__ src, double2* __r
   }
 }
 
-// Lanczos bookkeeping after the two Gram-Schmidt passes of step j (single thread):
+// Lanczos bookkeeping after the local and the full Gram-Schmidt pass of step j (single thread):
 // alpha_j = Re(c1_j) + Re(c2_j).
+// c1: coefficients of the local pass (v_{j-1}, v_j), c2: of the full pass (v_0 .. v_j)
 __global__ void k_record_alpha(LzState* st, const double2* __restrict__ c1, const double2* __restrict__ c2) {
   const int j = st->j;
-  st->alpha[j] = c1[j].x + c2[j].x;
+  st->alpha[j] = c1[j > 0 ? 1 : 0].x + c2[j].x;
 }
 
 __global__ void k_record_beta(LzState* st, const double2* __restrict__ nrm2) {
@@ -387,8 +397,10 @@ static int lanczos_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const doub
   int rc = apply(op, L->vin, L->w);
   if (rc != MRD_OK) return rc;
   s = ctx->stream;
-  MRD_CUDA(ctx, dots(L, L->V, -1, L->w, L->c1, s));
-  k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -1, L->st, L->c1, L->w, n);
+  // local pass against v_{j-1}, v_j (the three-term recurrence), then one full classical
+  // Gram-Schmidt pass against v_0 .. v_j that removes what rounding left
+  MRD_CUDA(ctx, dots(L, L->V, -2, L->w, L->c1, s));
+  k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -2, L->st, L->c1, L->w, n);
   mrd::count_launch();
   MRD_CUDA(ctx, dots(L, L->V, -1, L->w, L->c2, s));
   k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -1, L->st, L->c2, L->w, n);
