@@ -86,14 +86,46 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void mma(int prec, uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (prec == TC_TF32)
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  else
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+// The MMAs of one K step of a complex product, issued from one asm block with the accumulate
+// predicate set once. TF32: C_re += Re(A) Re(B) - Im(A) Im(B) (negated A), C_im += Re(A) Im(B)
+// + Im(A) Re(B). acc = 0 starts the accumulators of the tile.
+__device__ __forceinline__ void mma4_tf32(uint32_t t_re, uint32_t t_im, uint64_t ar, uint64_t ai, uint64_t br,
+                                          uint64_t bi, uint32_t id_pos, uint32_t id_neg, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %8, 0;\nsetp.eq.b32 q, 0, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %2, %4, %6, p;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %3, %5, %7, q;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%1], %2, %5, %6, p;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%1], %3, %4, %6, q;\n}\n"
+      ::"r"(t_re), "r"(t_im), "l"(ar), "l"(ai), "l"(br), "l"(bi), "r"(id_pos), "r"(id_neg), "r"(acc));
 }
+
+// Split BF16 (planes 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo at plane strides pa, pb in descriptor
+// units): each real product is hi*hi + hi*lo + lo*hi, 12 MMAs per complex K step.
+__device__ __forceinline__ void mma12_bf16x3(uint32_t t_re, uint32_t t_im, uint64_t a, uint64_t pa, uint64_t b,
+                                             uint64_t pb, uint32_t id_pos, uint32_t id_neg, uint32_t acc) {
+  const uint64_t A0 = a, A1 = a + pa, A2 = a + 2 * pa, A3 = a + 3 * pa;
+  const uint64_t B0 = b, B1 = b + pb, B2 = b + 2 * pb, B3 = b + 3 * pb;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %12, 0;\nsetp.eq.b32 q, 0, 0;\n"
+      // C_re += Re(A) Re(B) - Im(A) Im(B)
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %6, %10, p;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %7, %10, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %6, %10, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %8, %11, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %9, %11, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %8, %11, q;\n"
+      // C_im += Re(A) Im(B) + Im(A) Re(B)
+      "tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %8, %10, p;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %9, %10, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %8, %10, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %6, %10, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %7, %10, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%1], %5, %6, %10, q;\n}\n"
+      ::"r"(t_re), "r"(t_im), "l"(A0), "l"(A1), "l"(A2), "l"(A3), "l"(B0), "l"(B1), "l"(B2), "l"(B3),
+        "r"(id_pos), "r"(id_neg), "r"(acc));
+}
+
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -364,39 +396,19 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t sa = smem_u32(smem + stage * stage_bytes);
           const uint32_t sb = sa + planes * 128 * 128;
-          const uint32_t pa = 128 * 128, pb = (uint32_t)nrow * 128;
-          for (int ks = 0; ks < kpt / kstep; ++ks) {
-            const uint32_t ko = ks * 32;   // 32 bytes of K per instruction
+          // descriptors of the stage's planes; a K step of 32 bytes adds 2 to the address field
+          // (smem address / 16 in bits 0-13, no carry below 256 KB), so each instruction's
+          // descriptors are one 64-bit add away from these
+          const uint64_t a0 = make_desc(sa), b0 = make_desc(sb);
+          const uint64_t pa = (128 * 128) >> 4, pb = ((uint32_t)nrow * 128) >> 4;
+          const int nks = kpt / kstep;
+          for (int ks = 0; ks < nks; ++ks) {
+            const uint64_t ko = 2 * ks;
             const uint32_t acc = first ? 0u : 1u;
-            if (prec == TC_TF32) {
-              const uint64_t ar = make_desc(sa + ko), ai = make_desc(sa + pa + ko);
-              const uint64_t br = make_desc(sb + ko), bi = make_desc(sb + pb + ko);
-              mma(prec, t_re, ar, br, id_pos, acc);
-              mma(prec, t_re, ai, bi, id_neg, 1u);
-              mma(prec, t_im, ar, bi, id_pos, acc);
-              mma(prec, t_im, ai, br, id_pos, 1u);
-            } else {
-              // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-              uint64_t A[4], B[4];
-              for (int q = 0; q < 4; ++q) {
-                A[q] = make_desc(sa + q * pa + ko);
-                B[q] = make_desc(sb + q * pb + ko);
-              }
-              // C_re += Re(A) Re(B) - Im(A) Im(B), each with hi*hi + hi*lo + lo*hi
-              mma(prec, t_re, A[0], B[0], id_pos, acc);
-              mma(prec, t_re, A[0], B[1], id_pos, 1u);
-              mma(prec, t_re, A[1], B[0], id_pos, 1u);
-              mma(prec, t_re, A[2], B[2], id_neg, 1u);
-              mma(prec, t_re, A[2], B[3], id_neg, 1u);
-              mma(prec, t_re, A[3], B[2], id_neg, 1u);
-              // C_im += Re(A) Im(B) + Im(A) Re(B)
-              mma(prec, t_im, A[0], B[2], id_pos, acc);
-              mma(prec, t_im, A[0], B[3], id_pos, 1u);
-              mma(prec, t_im, A[1], B[2], id_pos, 1u);
-              mma(prec, t_im, A[2], B[0], id_pos, 1u);
-              mma(prec, t_im, A[2], B[1], id_pos, 1u);
-              mma(prec, t_im, A[3], B[0], id_pos, 1u);
-            }
+            if (prec == TC_TF32)
+              mma4_tf32(t_re, t_im, a0 + ko, a0 + pa + ko, b0 + ko, b0 + pb + ko, id_pos, id_neg, acc);
+            else
+              mma12_bf16x3(t_re, t_im, a0 + ko, pa, b0 + ko, pb, id_pos, id_neg, acc);
             first = false;
           }
           mma_commit(smem_u32(&bar_empty[stage]));
