@@ -462,11 +462,12 @@ def main():
     st = make_state(P, ctx, mpo, chi, caps, seed)
     for k in range(args.warmup):
         st.update(centre + k, +1, mixed)
-    nmax = max(st.site_len(j) for j in range(n_sites))
-    hbuf = [torch.empty(nmax, dtype=torch.complex128).pin_memory() for _ in range(2)]
+    # one pinned host buffer per site of the timed steps, holding that site's current tensor
     i0 = centre + args.warmup
-    st.site_into(i0, hbuf[0])
-    st.site_into(i0 + 1, hbuf[1])
+    nmax = max(st.site_len(j) for j in range(n_sites))
+    hsite = {j: torch.empty(2 * nmax, dtype=torch.complex128).pin_memory() for j in range(i0, i0 + args.steps + 1)}
+    for j in hsite:
+        st.site_into(j, hsite[j])
     torch.cuda.synchronize(dev)
     barrier()
     h2d = d2h = 0
@@ -474,11 +475,11 @@ def main():
     for k in range(args.steps):
         i = i0 + k
         h2d += 16 * (st.site_len(i) + st.site_len(i + 1))
-        st.set_site(i, hbuf[0].data_ptr())
-        st.set_site(i + 1, hbuf[1].data_ptr())
+        st.set_site(i, hsite[i].data_ptr())
+        st.set_site(i + 1, hsite[i + 1].data_ptr())
         st.update(i, +1, mixed)
-        d2h += 16 * st.site_into(i, hbuf[0])
-        d2h += 16 * st.site_into(i + 1, hbuf[1])
+        d2h += 16 * st.site_into(i, hsite[i])
+        d2h += 16 * st.site_into(i + 1, hsite[i + 1])
     torch.cuda.synchronize(dev)
     t_e2e = max_over_ranks(time.perf_counter() - t_e2e)
     st.close()

@@ -335,6 +335,9 @@ class DMRG:
     def site_into(self, j, host_tensor):
         """Copy MPS tensor j into a host tensor (complex128, numel >= len)."""
         mode, ln = C.c_int32(), C.c_int64()
+        self.ctx.check(lib().mrd_dmrg_site(self.h, j, C.byref(mode), C.byref(ln), None))
+        if host_tensor.numel() < ln.value:
+            raise ValueError(f"site {j} has {ln.value} elements; the host tensor holds {host_tensor.numel()}")
         self.ctx.check(lib().mrd_dmrg_site(self.h, j, C.byref(mode), C.byref(ln),
                                            C.cast(C.c_void_p(host_tensor.data_ptr()), C.POINTER(C.c_double))))
         return ln.value
