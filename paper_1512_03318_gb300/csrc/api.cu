@@ -27,7 +27,8 @@ struct Lanczos;
 void lanczos_free(Lanczos* L);
 cudaError_t lanczos_alloc(Lanczos** out, int64_t n, cudaStream_t stream);
 int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, double2*), void* op, double2* theta,
-                int max_iter, double tol, double* energy, int* iters, double* beta_last, uint64_t graph_key);
+                int max_iter, double tol, double* energy, int* iters, double* beta_last, uint64_t graph_key,
+                int (*replayed)(void*) = nullptr);
 int vdot(Lanczos* L, mrd_ctx* ctx, const double2* u, const double2* v, double* re, double* im);
 double2* lanczos_work(Lanczos* L);
 }  // namespace mrd
@@ -518,21 +519,20 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   int rc = heff_prepare(h, prec);
   if (rc != MRD_OK) return rc;
   cudaStream_t s = ctx->stream;
-  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-  if (h->timing) {
-    e0 = take_event(h); e1 = take_event(h); e2 = take_event(h);
-    if (!e0 || !e1 || !e2) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
-  }
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool cap = false;
+  if (h->timing && !apply_events(h, s, ev, &cap)) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
+  const cudaEvent_t e0 = ev[0], e1 = ev[1], e2 = ev[2];
   cudaError_t e = cudaMemsetAsync(theta_out_dev, 0, (size_t)n * 16, s);
   if (prec == MRD_PREC_FF) {
     float4* z_ff = (float4*)h->z;
     if (e == cudaSuccess) e = to_ff((const double2*)theta_in_dev, h->th_ff, n, s);
-    if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess && e0) e = record_event(e0, s, cap);
     if (!h->per_task) {
       if (e == cudaSuccess)
         e = launch_cgemm_ff_packed(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1, h->p.seg1, h->p.tile1,
                                    h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s);
-      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess && e1) e = record_event(e1, s, cap);
       if (e == cudaSuccess)
         e = launch_cgemm_ff_packed(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
                                    h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s);
@@ -541,19 +541,19 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
         if (h->pt_tiles1[t])
           e = launch_cgemm_ff_packed(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1 + TF * t, h->p.seg1,
                                      h->pt_pref1 + 2 * t, 1, h->pt_tiles1[t], h->n_sm, s);
-      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess && e1) e = record_event(e1, s, cap);
       for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT2]; ++t)
         if (h->pt_tiles2[t])
           e = launch_cgemm_ff_packed(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2 + TF * t, h->p.seg2,
                                      h->pt_pref2 + 2 * t, 1, h->pt_tiles2[t], h->n_sm, s);
     }
   } else {
-    if (e == cudaSuccess && e0) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess && e0) e = record_event(e0, s, cap);
     if (!h->per_task) {
       if (e == cudaSuccess)
         e = launch_cgemm_fp64(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1, h->p.seg1, h->p.tile1,
                               h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s);
-      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess && e1) e = record_event(e1, s, cap);
       if (e == cudaSuccess)
         e = launch_cgemm_fp64(h->z, h->wr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
                               h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s);
@@ -562,14 +562,14 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
         if (h->pt_tiles1[t])
           e = launch_cgemm_fp64(h->lw, (const double2*)theta_in_dev, h->z, h->p.t1 + TF * t, h->p.seg1,
                                 h->pt_pref1 + 2 * t, 1, h->pt_tiles1[t], h->n_sm, s);
-      if (e == cudaSuccess && e1) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess && e1) e = record_event(e1, s, cap);
       for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT2]; ++t)
         if (h->pt_tiles2[t])
           e = launch_cgemm_fp64(h->z, h->wr, (double2*)theta_out_dev, h->p.t2 + TF * t, h->p.seg2,
                                 h->pt_pref2 + 2 * t, 1, h->pt_tiles2[t], h->n_sm, s);
     }
   }
-  if (e == cudaSuccess && e2) e = cudaEventRecord(e2, s);
+  if (e == cudaSuccess && e2) e = record_event(e2, s, cap);
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply");
   return MRD_OK;
 }
@@ -593,6 +593,18 @@ static int apply_cb(void* op, const double2* in, double2* out) {
   return mrd_heff_apply(a->h, (const double*)in, (double*)out, a->prec);
 }
 
+// after each replay of a step graph captured with timing: the GEMM times of its apply
+static int replay_timing_cb(void* op) {
+  mrd_heff* h = static_cast<ApplyArg*>(op)->h;
+  float a = 0.f, b = 0.f;
+  MRD_CUDA(h->ctx, cudaEventElapsedTime(&a, h->gev[0], h->gev[1]));
+  MRD_CUDA(h->ctx, cudaEventElapsedTime(&b, h->gev[1], h->gev[2]));
+  h->gms[0] += a;
+  h->gms[1] += b;
+  ++h->gcalls;
+  return MRD_OK;
+}
+
 static int ensure_lanczos(mrd_heff* h) {
   if (h->lz) return MRD_OK;
   cudaError_t e = lanczos_alloc(&h->lz, h->counts[C_THETA], h->ctx->stream);
@@ -614,10 +626,16 @@ int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, in
   if ((rc = heff_prepare(h, prec)) != MRD_OK) return rc;
   ApplyArg arg{h, prec};
   int it = 0;
-  // one Lanczos step is captured as a CUDA graph and replayed (not while GEMM timing records
-  // events); the key changes whenever the operator's buffers are reallocated
-  const uint64_t key = h->use_graph && !h->timing ? ((uint64_t)h->gen << 8 | (uint64_t)(prec + 1)) : 0;
-  rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr, key);
+  // one Lanczos step is captured as a CUDA graph and replayed; the key changes whenever the
+  // operator's buffers are reallocated, and a graph captured with GEMM timing records the
+  // apply's events at every replay (read back after each one)
+  if (h->timing)
+    for (cudaEvent_t& ev : h->gev)
+      if (!ev) MRD_CUDA(ctx, cudaEventCreate(&ev));
+  const uint64_t key =
+      h->use_graph ? ((uint64_t)h->gen << 8 | (h->timing ? 0x80u : 0u) | (uint64_t)(prec + 1)) : 0;
+  rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr, key,
+                   h->timing ? replay_timing_cb : nullptr);
   *iters = it;
   if (rc == MRD_OK && (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3)) rc = tc_status(h);
   return rc;
@@ -692,9 +710,14 @@ int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int
   }
   for (cudaEvent_t e : h->ev) h->ev_pool.push_back(e);
   h->ev.clear();
+  a += h->gms[0];
+  b += h->gms[1];
+  const int32_t calls = (int32_t)n + h->gcalls;
+  h->gms[0] = h->gms[1] = 0.0;
+  h->gcalls = 0;
   if (ms_step1) *ms_step1 = a;
   if (ms_step2) *ms_step2 = b;
-  if (n_calls) *n_calls = (int32_t)n;
+  if (n_calls) *n_calls = calls;
   return MRD_OK;
 }
 

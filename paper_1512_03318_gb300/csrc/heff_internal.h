@@ -88,6 +88,11 @@ struct mrd_heff {
   bool timing = false;
   std::vector<cudaEvent_t> ev;   // 3 per recorded apply: before step 1, between, after step 2
   std::vector<cudaEvent_t> ev_pool;
+  // the three events of the apply captured in the Lanczos step graph: recorded by the graph at
+  // every replay and read back after each one into gms / gcalls
+  cudaEvent_t gev[3] = {nullptr, nullptr, nullptr};
+  double gms[2] = {0.0, 0.0};
+  int32_t gcalls = 0;
   Lanczos* lz = nullptr;
   // host copies of the device-built tables (downloaded once at creation)
   std::vector<int64_t> mid_host, lw_host, wr_host, lmap_host, rmap_host, t1_host, s1_host, t2_host, s2_host;
@@ -111,10 +116,17 @@ struct mrd_heff {
   ~mrd_heff() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : gev)
+      if (e) cudaEventDestroy(e);
     lanczos_free(lz);
     tc_free(tc);
   }
 };
+
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t s, bool captured) {
+  if (!e) return cudaSuccess;
+  return captured ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
 
 inline cudaEvent_t take_event(mrd_heff* h) {
   cudaEvent_t e = nullptr;
@@ -126,5 +138,26 @@ inline cudaEvent_t take_event(mrd_heff* h) {
   }
   h->ev.push_back(e);
   return e;
+}
+
+// The timing events of one apply on stream s: three pooled events, or, while s is being
+// captured into the Lanczos step graph, the graph's own three (external event nodes, so that
+// each replay records them). *captured tells which.
+inline bool apply_events(mrd_heff* h, cudaStream_t s, cudaEvent_t ev[3], bool* captured) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  *captured = cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
+  if (!*captured) {
+    for (int k = 0; k < 3; ++k)
+      if (!(ev[k] = take_event(h))) return false;
+    return true;
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (!h->gev[k] && cudaEventCreate(&h->gev[k]) != cudaSuccess) {
+      h->gev[k] = nullptr;
+      return false;
+    }
+    ev[k] = h->gev[k];
+  }
+  return true;
 }
 

@@ -471,9 +471,10 @@ static bool capture_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const dou
 // vector in, ground vector out. Host reads one small state record per iteration. With
 // graph_key != 0 the step is captured once as a CUDA graph (kept while the key is unchanged)
 // and replayed; the operator must then be ready (buffers built, operands packed) and free of
-// host synchronisation.
+// host synchronisation. `replayed(op)`, if given, runs after every replay of the graph.
 int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, double2*), void* op, double2* theta,
-                int max_iter, double tol, double* energy, int* iters, double* beta_last, uint64_t graph_key) {
+                int max_iter, double tol, double* energy, int* iters, double* beta_last, uint64_t graph_key,
+                int (*replayed)(void*)) {
   cudaStream_t s = ctx->stream;
   const int64_t n = L->n;
   if (max_iter < 1 || max_iter > MRD_LANCZOS_MAX_ITER)
@@ -498,6 +499,10 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
       if (rc != MRD_OK) return rc;
     }
     MRD_CUDA(ctx, cudaStreamSynchronize(s));
+    if (graph && replayed) {
+      const int rc = replayed(op);
+      if (rc != MRD_OK) return rc;
+    }
     k = j + 1;
     const double e = L->st_host->energy;
     const double b = L->st_host->beta_last;

@@ -401,29 +401,28 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   if (rc != MRD_OK) return rc;
   Tc* T = h->tc;
   cudaStream_t s = ctx->stream;
-  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-  if (h->timing) {
-    e0 = take_event(h); e1 = take_event(h); e2 = take_event(h);
-    if (!e0 || !e1 || !e2) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
-  }
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool cap = false;
+  if (h->timing && !apply_events(h, s, ev, &cap)) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
+  const cudaEvent_t e0 = ev[0], e1 = ev[1], e2 = ev[2];
   MRD_CUDA(ctx, cudaMemsetAsync(out, 0, (size_t)h->counts[C_THETA] * 16, s));
   MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, tp, s));
-  if (e0) MRD_CUDA(ctx, cudaEventRecord(e0, s));
+  MRD_CUDA(ctx, record_event(e0, s, cap));
   if (!h->per_task) {
     MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
                           h->n_sm, s));
-    if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
+    MRD_CUDA(ctx, record_event(e1, s, cap));
     MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
                           T->err, h->n_sm, s));
   } else {   // one launch per task: the per-block baseline of the grouped persistent launch
     for (int64_t t = 0; t < T->n1; ++t)
       MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, nullptr, 1, T->tiles1[t], T->z, nullptr, tp,
                             T->cfg, T->err, h->n_sm, s));
-    if (e1) MRD_CUDA(ctx, cudaEventRecord(e1, s));
+    MRD_CUDA(ctx, record_event(e1, s, cap));
     for (int64_t t = 0; t < T->n2; ++t)
       MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, nullptr, 1, T->tiles2[t], nullptr,
                             (double2*)out, tp, T->cfg, T->err, h->n_sm, s));
   }
-  if (e2) MRD_CUDA(ctx, cudaEventRecord(e2, s));
+  MRD_CUDA(ctx, record_event(e2, s, cap));
   return MRD_OK;
 }

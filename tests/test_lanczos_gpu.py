@@ -109,6 +109,33 @@ def test_lanczos_graph_replay_is_bitwise_the_direct_launch(ctx, prec):
     assert n1 == n0 == n2 > 10 * it1
 
 
+@pytest.mark.parametrize("prec", [0, 2, 3])
+def test_gemm_timing_inside_the_step_graph(ctx, prec):
+    """With GEMM timing on, the step graph still runs: its apply records its events at every
+    replay, so the timed calls equal the Lanczos steps, as with direct launches, and the
+    result is the same bits."""
+    import paper_1512_03318_gb300 as P
+    case = _hermitian_case(53, 4, 40, 44, 1, 2)
+    res = []
+    for graph in (1, 0):
+        h = P.Heff(ctx, **G.heff_args(case))
+        h.set_option(P.MRD_OPT_GRAPH, graph)
+        h.set_option(P.MRD_OPT_AUTOTUNE, 0)
+        h.set_env(torch.from_numpy(case["lflat"]).cuda(), torch.from_numpy(case["rflat"]).cuda())
+        h.timing(True)
+        th = torch.from_numpy(case["tflat"].copy()).cuda()
+        e, it = h.lanczos(th, max_iter=25, tol=1e-14, prec=prec)
+        ms1, ms2, n = h.timing_collect()
+        res.append((e, it, th.cpu().numpy(), n, ms1, ms2))
+        assert h.timing_collect()[2] == 0   # collected once
+        h.close()
+    (e1, it1, v1, n1, a1, b1), (e0, it0, v0, n0, a0, b0) = res
+    assert it1 == it0 > 3
+    assert n1 == n0 == it1
+    assert e1 == e0 and np.array_equal(v1, v0)
+    assert a1 > 0 and b1 > 0 and a0 > 0 and b0 > 0
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_per_task_launch_equals_grouped_launch(ctx, prec):
     """The per-block baseline (one GEMM launch per output task) computes exactly what the
