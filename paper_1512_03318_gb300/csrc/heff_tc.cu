@@ -156,18 +156,30 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // One thread writes one 16-byte chunk of a panel row in every plane: 4 consecutive K values
 // (TF32) or 8 (BF16). For transposed sources consecutive threads take consecutive panel rows,
 // so each of the chunk's reads is coalesced; K beyond the block is written as zero padding.
+// A CTA takes one piece (kPackPiece chunks of one job) at a time, so large blocks spread over
+// the whole grid. The BF16 split is done in FP32 after one conversion of each value (hi =
+// bf16(x), lo = bf16(x - hi), with x - hi exact in FP32): the split's error, ~2^-17 |x| from
+// rounding lo, is the same as splitting in FP64, and the FP64 pipe (2 ops per clock per SM)
+// only converts.
 __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ dst, const int64_t* __restrict__ jobs,
-                       int njobs, int prec) {
+                       int njobs, int64_t npieces, int prec) {
   const bool tf32 = prec == TC_TF32;
   const int kc = tf32 ? 4 : 8;                   // K values per 16-byte chunk
   const int kpt = tf32 ? 32 : 64;                // K values per 128-byte row
   const int planes = tf32 ? 2 : 4;
-  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
-    const int64_t* d = jobs + TCJ * j;
+  for (int64_t pc = blockIdx.x; pc < npieces; pc += gridDim.x) {
+    int lo = 0, hi = njobs - 1;                  // the last job whose first piece is <= pc
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[TCJ * mid + 9] <= pc) lo = mid; else hi = mid - 1;
+    }
+    const int64_t* d = jobs + TCJ * lo;
     const int64_t s_off = d[0], ld = d[1], trans = d[2], rows = d[3], K = d[4], p_off = d[5], rowtile = d[6],
                   nkt = d[7], npad = d[8];
     const int64_t nch = (K + kc - 1) / kc;       // chunks per row
-    for (int64_t e = threadIdx.x; e < rows * nch; e += blockDim.x) {
+    const int64_t e0 = (pc - d[9]) * kPackPiece;
+    const int64_t e1 = e0 + kPackPiece < rows * nch ? e0 + kPackPiece : rows * nch;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       int64_t r, ch;
       if (trans) { ch = e / rows; r = e % rows; }   // consecutive threads: consecutive rows
       else { r = e / nch; ch = e % nch; }           // consecutive threads: consecutive chunks
@@ -202,12 +214,13 @@ __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ ds
           const int64_t k = k0 + q;
           double2 v = make_double2(0.0, 0.0);
           if (k < K) v = trans ? src[s_off + k * ld + r] : src[s_off + r * ld + k];
-          const __nv_bfloat16 rh = __double2bfloat16(v.x);
-          const __nv_bfloat16 ih = __double2bfloat16(v.y);
+          const float xr = __double2float_rn(v.x), xi = __double2float_rn(v.y);
+          const __nv_bfloat16 rh = __float2bfloat16_rn(xr);
+          const __nv_bfloat16 ih = __float2bfloat16_rn(xi);
           b0[q] = rh;
-          b1[q] = __double2bfloat16(v.x - (double)__bfloat162float(rh));
+          b1[q] = __float2bfloat16_rn(__fsub_rn(xr, __bfloat162float(rh)));
           b2[q] = ih;
-          b3[q] = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+          b3[q] = __float2bfloat16_rn(__fsub_rn(xi, __bfloat162float(ih)));
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) *(uint4*)(tile + q * tile_bytes + off) = pl[q];
@@ -497,9 +510,10 @@ cudaError_t tc_gemm_init() {
   return cudaSuccess;
 }
 
-cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int prec, cudaStream_t s) {
-  if (njobs <= 0) return cudaSuccess;
-  k_pack<<<njobs < 8192 ? njobs : 8192, 256, 0, s>>>(src, dst, jobs, njobs, prec);
+cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int64_t npieces, int prec,
+                    cudaStream_t s) {
+  if (njobs <= 0 || npieces <= 0) return cudaSuccess;
+  k_pack<<<(unsigned)(npieces < 8192 ? npieces : 8192), 256, 0, s>>>(src, dst, jobs, njobs, npieces, prec);
   mrd::count_launch();
   return cudaGetLastError();
 }

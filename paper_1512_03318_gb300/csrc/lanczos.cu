@@ -200,15 +200,32 @@ __global__ void k_scale_next(const double2* __restrict__ w, double2* __restrict_
   }
 }
 
-__device__ int sturm_count(const double* a, const double* b, int k, double x) {
-  // number of eigenvalues of tridiag(b, a, b) smaller than x
-  int cnt = 0;
-  double q = a[0] - x;
-  if (q < 0) ++cnt;
+// Number of eigenvalues of the leading k x k block of tridiag(b, a, b) below x: the sign
+// changes of its leading principal minors p_i = det(T_i - x I), from the Sturm recurrence
+// p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2} (b2 holds the squares). It needs no division:
+// three FP64 operations per row, where the pivot-ratio form q_i = p_i / p_{i-1} divides once
+// per row, and FP64 division is a long instruction sequence on a part with 2 FP64 operations
+// per clock per SM. Both minors are rescaled by 2^-+600 when p_i leaves [2^-600, 2^600]; their
+// ratio (a pivot) stays within 2^+-200, so neither leaves the FP64 range. A zero minor is
+// replaced by 2^-200 times the one before, the same as a tiny positive pivot.
+__device__ int sturm_count(const double* a, const double* b2, int k, double x) {
+  double pm = 1.0, p = a[0] - x;
+  if (p == 0.0) p = 0x1p-200;
+  int cnt = p < 0.0;
   for (int i = 1; i < k; ++i) {
-    double qq = q != 0.0 ? q : 1e-300;
-    q = (a[i] - x) - b[i - 1] * b[i - 1] / qq;
-    if (q < 0) ++cnt;
+    double pn = fma(a[i] - x, p, -b2[i - 1] * pm);
+    if (pn == 0.0) pn = p * 0x1p-200;
+    cnt += (pn < 0.0) != (p < 0.0);
+    pm = p;
+    p = pn;
+    const double m = fabs(p);
+    if (m > 0x1p600) {
+      p *= 0x1p-600;
+      pm *= 0x1p-600;
+    } else if (m < 0x1p-600) {
+      p *= 0x1p600;
+      pm *= 0x1p600;
+    }
   }
   return cnt;
 }
@@ -220,12 +237,19 @@ __global__ void k_tridiag_lowest(LzState* st) {
   const double* b = st->beta;
   const int lane = threadIdx.x;
   __shared__ double lo_s, hi_s;
+  __shared__ double a_s[MRD_LANCZOS_MAX_ITER + 1], b2_s[MRD_LANCZOS_MAX_ITER + 1];
+  for (int i = lane; i < k; i += 32) {
+    a_s[i] = a[i];
+    b2_s[i] = b[i] * b[i];
+  }
   if (lane == 0) {
-    double lo = 1e300, hi = -1e300;
+    // the lowest eigenvalue lies between the lowest Gershgorin bound and the smallest
+    // diagonal element (a Rayleigh quotient of a unit vector)
+    double lo = 1e300, hi = 1e300;
     for (int i = 0; i < k; ++i) {
       double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
       lo = fmin(lo, a[i] - r);
-      hi = fmax(hi, a[i] + r);
+      hi = fmin(hi, a[i]);
     }
     double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
     lo_s = lo - pad;
@@ -236,7 +260,7 @@ __global__ void k_tridiag_lowest(LzState* st) {
     const double lo = lo_s, hi = hi_s;
     if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
     const double x = lo + (hi - lo) * (lane + 1) / 33.0;
-    const int c = sturm_count(a, b, k, x);
+    const int c = sturm_count(a_s, b2_s, k, x);
     const unsigned m = __ballot_sync(0xffffffffu, c >= 1);
     __syncwarp();
     if (lane == 0) {

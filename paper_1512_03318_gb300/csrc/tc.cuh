@@ -11,8 +11,11 @@ enum { TC_TF32 = 1, TC_BF16X3 = 2 };
 enum { TCT = 10 };
 // segment row: a_panel_byte_offset b_panel_byte_offset nkt pad
 enum { TCS = 4 };
-// pack job row: src_off ld trans rows K panel_byte_offset rowtile nkt npad
-enum { TCJ = 9 };
+// pack job row: src_off ld trans rows K panel_byte_offset rowtile nkt npad first_piece, where
+// the job's 16-byte chunks (rows x ceil(K / chunk K)) are cut into pieces of kPackPiece and
+// first_piece is the prefix of the earlier jobs' pieces
+enum { TCJ = 10 };
+constexpr int kPackPiece = 1024;
 
 struct TcPanelGeom {
   int64_t nkt;

@@ -9,7 +9,8 @@
 #include "tc.cuh"
 
 namespace mrd {
-cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int prec, cudaStream_t s);
+cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int njobs, int64_t npieces, int prec,
+                    cudaStream_t s);
 cudaError_t tc_gemm_init();
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
                     const int64_t* prefix, const int2* items, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out,
@@ -28,6 +29,7 @@ struct Tc {
   int64_t n1 = 0, ntiles1 = 0, n2 = 0, ntiles2 = 0;
   int64_t *j_lw = nullptr, *j_wr = nullptr, *j_th = nullptr;
   int n_lw = 0, n_wr = 0, n_th = 0;
+  int64_t pc_lw = 0, pc_wr = 0, pc_th = 0;   // pack pieces of each job list
   // per-task launches: [0, tiles of task t] pairs (device) and tiles per task (host)
   int64_t *pt1 = nullptr, *pt2 = nullptr;
   std::vector<int64_t> tiles1, tiles2;
@@ -62,7 +64,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     const int64_t* r = &h->lw_host[LWF * k];
     const int64_t rows = r[5], K = r[6], nkt = (K + kpt - 1) / kpt;
     lw_map[r[7]] = {lw_b, nkt};
-    j_lw.insert(j_lw.end(), {r[7], K, 0, rows, K, lw_b, 128, nkt, round_up(rows, 128)});
+    j_lw.insert(j_lw.end(), {r[7], K, 0, rows, K, lw_b, 128, nkt, round_up(rows, 128), 0});
     lw_b += a_bytes(rows, nkt, planes);
   }
   // folded right operand WR(w', s2, s2', b): B panel of its transpose, rows d_b', K d_b
@@ -70,7 +72,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     const int64_t* r = &h->wr_host[WRF * k];
     const int64_t K = r[5], rows = r[6], nkt = (K + kpt - 1) / kpt;
     wr_map[r[7]] = {wr_b, nkt};
-    j_wr.insert(j_wr.end(), {r[7], rows, 1, rows, K, wr_b, ntile, nkt, round_up(rows, 16)});
+    j_wr.insert(j_wr.end(), {r[7], rows, 1, rows, K, wr_b, ntile, nkt, round_up(rows, 16), 0});
     wr_b += b_bytes(rows, nkt, planes);
   }
   // theta block (s1, a) x (s2, b) of every middle sector: B panel of its transpose, rows d_b, K d_a
@@ -85,7 +87,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
         const int64_t rows = h->right[3 * r[8 + s2] + 2];
         const int64_t src = r[4] + (s1 ? r[7] : 0) * r[3] + (s2 ? r[10] : 0);
         th_map[src] = {th_b, nkt};
-        j_th.insert(j_th.end(), {src, r[3], 1, rows, K, th_b, ntile, nkt, round_up(rows, 16)});
+        j_th.insert(j_th.end(), {src, r[3], 1, rows, K, th_b, ntile, nkt, round_up(rows, 16), 0});
         th_b += b_bytes(rows, nkt, planes);
       }
     }
@@ -232,6 +234,17 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   T->n1 = (int64_t)t1.size() / TCT; T->ntiles1 = p1.back();
   T->n2 = (int64_t)t2.size() / TCT; T->ntiles2 = p2.back();
   T->n_lw = (int)(j_lw.size() / TCJ); T->n_wr = (int)(j_wr.size() / TCJ); T->n_th = (int)(j_th.size() / TCJ);
+  // first piece of every pack job (field 9) and the pieces of each list
+  const int kc = prec == TC_TF32 ? 4 : 8;
+  auto pieces = [&](std::vector<int64_t>& j) {
+    int64_t n = 0;
+    for (size_t k = 0; k < j.size(); k += TCJ) {
+      j[k + 9] = n;
+      n += (j[k + 3] * ((j[k + 4] + kc - 1) / kc) + kPackPiece - 1) / kPackPiece;
+    }
+    return n;
+  };
+  T->pc_lw = pieces(j_lw); T->pc_wr = pieces(j_wr); T->pc_th = pieces(j_th);
   cudaStream_t s = ctx->stream;
   auto up = [&](int64_t* d, const std::vector<int64_t>& v) {
     if (e == cudaSuccess && !v.empty()) e = cudaMemcpyAsync(d, v.data(), v.size() * 8, cudaMemcpyHostToDevice, s);
@@ -329,8 +342,8 @@ int autotune(mrd_heff* h, int prec) {
     int rc = build(h, prec, c);
     if (rc != MRD_OK) return rc;
     Tc* T = h->tc;
-    MRD_CUDA(ctx, tc_pack(h->lw, T->lw, T->j_lw, T->n_lw, prec, ctx->stream));
-    MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, prec, ctx->stream));
+    MRD_CUDA(ctx, tc_pack(h->lw, T->lw, T->j_lw, T->n_lw, T->pc_lw, prec, ctx->stream));
+    MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, T->pc_wr, prec, ctx->stream));
     double ms = 0.0;
     if ((rc = time_cfg(h, &ms)) != MRD_OK) return rc;
     if (ms < best_ms) { best_ms = ms; best = c; }
@@ -375,8 +388,8 @@ int tc_prepare(mrd_heff* h, int32_t prec) {
   Tc* T = h->tc;
   cudaStream_t s = ctx->stream;
   if (T->env_dirty) {
-    MRD_CUDA(ctx, tc_pack(h->lw, T->lw, T->j_lw, T->n_lw, tp, s));
-    MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, tp, s));
+    MRD_CUDA(ctx, tc_pack(h->lw, T->lw, T->j_lw, T->n_lw, T->pc_lw, tp, s));
+    MRD_CUDA(ctx, tc_pack(h->wr, T->wr, T->j_wr, T->n_wr, T->pc_wr, tp, s));
     T->env_dirty = false;
   }
   return MRD_OK;
@@ -406,7 +419,7 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   if (h->timing && !apply_events(h, s, ev, &cap)) return mrd_fail(ctx, MRD_E_CUDA, "mrd_heff_apply: cudaEventCreate");
   const cudaEvent_t e0 = ev[0], e1 = ev[1], e2 = ev[2];
   MRD_CUDA(ctx, cudaMemsetAsync(out, 0, (size_t)h->counts[C_THETA] * 16, s));
-  MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, tp, s));
+  MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, T->pc_th, tp, s));
   MRD_CUDA(ctx, record_event(e0, s, cap));
   if (!h->per_task) {
     MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
