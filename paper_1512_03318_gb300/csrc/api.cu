@@ -30,6 +30,7 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
                 int max_iter, double tol, double* energy, int* iters, double* beta_last, uint64_t graph_key,
                 int (*replayed)(void*) = nullptr);
 int vdot(Lanczos* L, mrd_ctx* ctx, const double2* u, const double2* v, double* re, double* im);
+cudaError_t lanczos_set_fp32_full(Lanczos* L, bool on);
 double2* lanczos_work(Lanczos* L);
 }  // namespace mrd
 
@@ -632,6 +633,9 @@ int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, in
   if (h->timing)
     for (cudaEvent_t& ev : h->gev)
       if (!ev) MRD_CUDA(ctx, cudaEventCreate(&ev));
+  // with tensor-core matvecs (~1e-5 .. 1e-3 relative) the full reorthogonalisation pass runs
+  // in FP32; FP64 and float-float runs keep it in FP64
+  MRD_CUDA(ctx, lanczos_set_fp32_full(h->lz, prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3));
   const uint64_t key =
       h->use_graph ? ((uint64_t)h->gen << 8 | (h->timing ? 0x80u : 0u) | (uint64_t)(prec + 1)) : 0;
   rc = lanczos_run(h->lz, ctx, apply_cb, &arg, (double2*)theta_dev, max_iter, tol, energy, &it, nullptr, key,

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_cgemm_ff(const TA* __restrict__ A, cons
   __shared__ float4 As[kT][kK + 1];
   __shared__ float4 Bs[kK][kT + 1];
   const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;
+  const int warp = tid >> 5, lane = tid & 31;
   const int64_t total = prefix[n_tasks];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int64_t t = find_task_ff(prefix, n_tasks, item);
@@ -89,6 +89,16 @@ __global__ void __launch_bounds__(256) k_cgemm_ff(const TA* __restrict__ A, cons
     const int64_t tiles_n = (N + kT - 1) / kT;
     const int64_t local = item - prefix[t];
     const int64_t m0 = (local / tiles_n) * kT, n0 = (local % tiles_n) * kT;
+    // Each thread owns 2 x 2 outputs, each warp a 4 x 32 strip of the tile. The strips run
+    // along the tile's shorter valid side, so that a warp whose strip lies wholly in the
+    // padding of a small block (e.g. 4 rows of 32) skips the products and leaves its issue
+    // slots to the other CTAs of the SM. Which thread computes an output changes nothing in
+    // how it is computed: the results are the same bits either way.
+    const int rv = M - m0 < kT ? (int)(M - m0) : kT, cv = N - n0 < kT ? (int)(N - n0) : kT;
+    const bool by_col = cv < rv;
+    const int ws = 4 * warp, ls = 2 * (lane >> 4), lt = 2 * (lane & 15);
+    const int r0 = by_col ? lt : ws + ls, c0 = by_col ? ws + ls : lt;   // first row / column of the thread
+    const bool active = (by_col ? cv : rv) > ws;
     CAcc acc[2][2];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -122,10 +132,10 @@ __global__ void __launch_bounds__(256) k_cgemm_ff(const TA* __restrict__ A, cons
           }
         }
         __syncthreads();
-        const int kn = K - k0 < kK ? (int)(K - k0) : kK;   // zero padding adds nothing: skip it
+        const int kn = !active ? 0 : K - k0 < kK ? (int)(K - k0) : kK;   // zero padding adds nothing: skip it
         for (int k = 0; k < kn; ++k) {
-          const float4 a0 = As[2 * ty][k], a1 = As[2 * ty + 1][k];
-          const float4 b0 = Bs[k][2 * tx], b1 = Bs[k][2 * tx + 1];
+          const float4 a0 = As[r0][k], a1 = As[r0 + 1][k];
+          const float4 b0 = Bs[k][c0], b1 = Bs[k][c0 + 1];
           cff_mac(acc[0][0], a0, b0);
           cff_mac(acc[0][1], a0, b1);
           cff_mac(acc[1][0], a1, b0);
@@ -149,7 +159,7 @@ __global__ void __launch_bounds__(256) k_cgemm_ff(const TA* __restrict__ A, cons
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const int64_t r = m0 + 2 * ty + i, c = n0 + 2 * tx + j;
+        const int64_t r = m0 + r0 + i, c = n0 + c0 + j;
         if (r < M && c < N) st_out(C, c_off + r * ldc + c, acc[i][j]);
       }
   }

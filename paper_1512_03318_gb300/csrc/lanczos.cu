@@ -140,6 +140,97 @@ __global__ void k_sub_combination(const double2* __restrict__ V, int64_t ldv, in
   }
 }
 
+// FP32 form of the full Gram-Schmidt pass, for Lanczos runs whose matvec is itself a
+// reduced-precision product (TF32 or split BF16, ~1e-5 .. 1e-3 relative). After the FP64
+// local pass the remaining coefficients <v_i, w> are the small residue of rounding; computed
+// from FP32 copies of v_i and w their error is ~2^-24 |w| / sqrt(n) (random rounding over n
+// terms), which keeps the basis orthogonal to ~1e-10 relative, far inside the sqrt(eps)
+// (semi-orthogonality) level that keeps the Ritz values exact to working precision. FP32
+// halves the bytes and moves the products off the FP64 pipe (2 operations per clock per SM),
+// which bounds the FP64 pass at ~2.5 TB/s.
+constexpr int kJB32 = 8;   // vectors per pass of k_multidot32
+
+__global__ void k_to_f32(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    y[i] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  }
+}
+
+// partial[b * nv + j] = sum over this CTA's share of conj(V32_j) . w32, j <= st->j: FP32
+// products and per-thread sums, FP64 from the warp reduction on (layout of k_multidot)
+__global__ void __launch_bounds__(kRedThreads) k_multidot32(const float2* __restrict__ V32, int64_t ldv,
+                                                            const LzState* __restrict__ st,
+                                                            const float2* __restrict__ w32, int64_t n,
+                                                            double2* __restrict__ partial) {
+  __shared__ double sre[kJB32][kRedThreads / 32], sim[kJB32][kRedThreads / 32];
+  const int nv = st->j + 1;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t b = blockIdx.x * chunk;
+  const int64_t e = b + chunk < n ? b + chunk : n;
+  for (int j0 = 0; j0 < nv; j0 += kJB32) {
+    float re[kJB32], im[kJB32];
+#pragma unroll
+    for (int q = 0; q < kJB32; ++q) re[q] = im[q] = 0.f;
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+      const float2 y = w32[i];
+#pragma unroll
+      for (int q = 0; q < kJB32; ++q) {
+        if (j0 + q < nv) {
+          const float2 x = V32[(int64_t)(j0 + q) * ldv + i];
+          re[q] = __fmaf_rn(x.x, y.x, re[q]);
+          re[q] = __fmaf_rn(x.y, y.y, re[q]);
+          im[q] = __fmaf_rn(x.x, y.y, im[q]);
+          im[q] = __fmaf_rn(-x.y, y.x, im[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kJB32; ++q) {
+      const double r = warp_sum((double)re[q]), m = warp_sum((double)im[q]);
+      if ((threadIdx.x & 31) == 0) {
+        sre[q][threadIdx.x >> 5] = r;
+        sim[q][threadIdx.x >> 5] = m;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kJB32 && j0 + (int)threadIdx.x < nv) {
+      const int q = threadIdx.x;
+      double a = 0.0, c = 0.0;
+      for (int k = 0; k < kRedThreads / 32; ++k) {
+        a += sre[q][k];
+        c += sim[q][k];
+      }
+      partial[(int64_t)blockIdx.x * nv + j0 + q] = make_double2(a, c);
+    }
+    __syncthreads();
+  }
+}
+
+// w -= sum_{j <= st->j} c_j V32_j: the correction is summed in FP32 (coefficients rounded to
+// FP32 once per CTA) and subtracted from the FP64 vector
+__global__ void k_sub_combination32(const float2* __restrict__ V32, int64_t ldv, const LzState* __restrict__ st,
+                                    const double2* __restrict__ c, double2* __restrict__ w, int64_t n) {
+  __shared__ float2 cs[MRD_LANCZOS_MAX_ITER + 1];
+  const int nv = st->j + 1;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = make_float2(__double2float_rn(c[j].x), __double2float_rn(c[j].y));
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float ax = 0.f, ay = 0.f;
+    for (int j = 0; j < nv; ++j) {
+      const float2 v = V32[(int64_t)j * ldv + i], cj = cs[j];
+      ax = __fmaf_rn(cj.x, v.x, ax);
+      ax = __fmaf_rn(-cj.y, v.y, ax);
+      ay = __fmaf_rn(cj.x, v.y, ay);
+      ay = __fmaf_rn(cj.y, v.x, ay);
+    }
+    double2 o = w[i];
+    o.x -= (double)ax;
+    o.y -= (double)ay;
+    w[i] = o;
+  }
+}
+
 // out = sum_j y[j] V_j with real coefficients y
 __global__ void k_combination_real(const double2* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ y,
                                    double2* __restrict__ out, int64_t n) {
@@ -155,12 +246,15 @@ __global__ void k_combination_real(const double2* __restrict__ V, int64_t ldv, i
 }
 
 // dst = src * (1 / sqrt(norm2)), norm2 read from device memory (real part of *nrm)
+// (and its FP32 copy into dst32 when given)
 __global__ void k_scale_by_invnorm(const double2* __restrict__ src, double2* __restrict__ dst, int64_t n,
-                                   const double2* __restrict__ nrm2) {
+                                   const double2* __restrict__ nrm2, float2* __restrict__ dst32) {
   const double s = nrm2->x > 0.0 ? 1.0 / sqrt(nrm2->x) : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = src[i];
-    dst[i] = make_double2(v.x * s, v.y * s);
+    const double2 o = make_double2(v.x * s, v.y * s);
+    dst[i] = o;
+    if (dst32) dst32[i] = make_float2(__double2float_rn(o.x), __double2float_rn(o.y));
   }
 }
 
@@ -191,12 +285,16 @@ __global__ void k_copy_vj(const double2* __restrict__ V, int64_t n, const LzStat
 
 // v_{j+1} = w / |w|
 __global__ void k_scale_next(const double2* __restrict__ w, double2* __restrict__ V, int64_t n,
-                             const double2* __restrict__ nrm2, const LzState* __restrict__ st) {
+                             const double2* __restrict__ nrm2, const LzState* __restrict__ st,
+                             float2* __restrict__ V32) {
   const double sc = nrm2->x > 0.0 ? 1.0 / sqrt(nrm2->x) : 0.0;
   double2* dst = V + (int64_t)(st->j + 1) * n;
+  float2* dst32 = V32 ? V32 + (int64_t)(st->j + 1) * n : nullptr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = w[i];
-    dst[i] = make_double2(v.x * sc, v.y * sc);
+    const double2 o = make_double2(v.x * sc, v.y * sc);
+    dst[i] = o;
+    if (dst32) dst32[i] = make_float2(__double2float_rn(o.x), __double2float_rn(o.y));
   }
 }
 
@@ -352,6 +450,9 @@ struct Lanczos {
   double2* c1 = nullptr;
   double2* c2 = nullptr;
   double2* scal = nullptr;
+  float2* V32 = nullptr;       // FP32 copies of the basis and of w for the FP32 full pass
+  float2* w32 = nullptr;
+  bool fp32_full = false;      // full Gram-Schmidt pass in FP32 (reduced-precision matvecs)
   LzState* st = nullptr;
   LzState* st_host = nullptr;  // pinned
   cudaStream_t stream = nullptr;   // stream of the memory cache the buffers return to
@@ -365,7 +466,7 @@ struct Lanczos {
 void lanczos_free(Lanczos* L) {
   if (!L) return;
   for (void* p : {(void*)L->V, (void*)L->w, (void*)L->vin, (void*)L->partial, (void*)L->c1, (void*)L->c2,
-                  (void*)L->scal, (void*)L->st})
+                  (void*)L->scal, (void*)L->st, (void*)L->V32, (void*)L->w32})
     cache_free(p, L->stream);
   if (L->st_host) cache_free_host(L->st_host);
   if (L->step_exec) cudaGraphExecDestroy(L->step_exec);
@@ -393,6 +494,24 @@ cudaError_t lanczos_alloc(Lanczos** out, int64_t n, cudaStream_t stream) {
     return e;
   }
   *out = L;
+  return cudaSuccess;
+}
+
+// Selects the FP32 full Gram-Schmidt pass (for reduced-precision matvecs) or the FP64 one;
+// the FP32 copies of the basis are allocated on first use.
+cudaError_t lanczos_set_fp32_full(Lanczos* L, bool on) {
+  if (on && !L->V32) {
+    const size_t n = (size_t)(L->n > 0 ? L->n : 1);
+    cudaError_t e = cache_alloc((void**)&L->V32, (size_t)(MRD_LANCZOS_MAX_ITER + 1) * n * 8, L->stream);
+    if (e == cudaSuccess) e = cache_alloc((void**)&L->w32, n * 8, L->stream);
+    if (e != cudaSuccess) {
+      cache_free(L->V32, L->stream);
+      L->V32 = nullptr;
+      L->fp32_full = false;
+      return e;
+    }
+  }
+  L->fp32_full = on;
   return cudaSuccess;
 }
 
@@ -426,9 +545,17 @@ static int lanczos_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const doub
   MRD_CUDA(ctx, dots(L, L->V, -2, L->w, L->c1, s));
   k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -2, L->st, L->c1, L->w, n);
   mrd::count_launch();
-  MRD_CUDA(ctx, dots(L, L->V, -1, L->w, L->c2, s));
-  k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -1, L->st, L->c2, L->w, n);
-  mrd::count_launch();
+  if (L->fp32_full) {
+    k_to_f32<<<grid_for(n), 256, 0, s>>>(L->w, L->w32, n);
+    k_multidot32<<<kRedBlocks, kRedThreads, 0, s>>>(L->V32, n, L->st, L->w32, n, L->partial);
+    k_finish_dots<<<(MRD_LANCZOS_MAX_ITER + 1 + 3) / 4, 128, 0, s>>>(L->partial, kRedBlocks, -1, L->st, L->c2);
+    k_sub_combination32<<<grid_for(n), 256, 0, s>>>(L->V32, n, L->st, L->c2, L->w, n);
+    mrd::count_launches(4);
+  } else {
+    MRD_CUDA(ctx, dots(L, L->V, -1, L->w, L->c2, s));
+    k_sub_combination<<<grid_for(n), 256, 0, s>>>(L->V, n, -1, L->st, L->c2, L->w, n);
+    mrd::count_launch();
+  }
   k_record_alpha<<<1, 1, 0, s>>>(L->st, L->c1, L->c2);
   mrd::count_launch();
   MRD_CUDA(ctx, dots(L, L->w, 1, L->w, L->scal, s));
@@ -436,7 +563,7 @@ static int lanczos_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const doub
   mrd::count_launch();
   k_tridiag_lowest<<<1, 32, 0, s>>>(L->st);
   mrd::count_launch();
-  k_scale_next<<<grid_for(n), 256, 0, s>>>(L->w, L->V, n, L->scal, L->st);
+  k_scale_next<<<grid_for(n), 256, 0, s>>>(L->w, L->V, n, L->scal, L->st, L->fp32_full ? L->V32 : nullptr);
   mrd::count_launch();
   k_next_step<<<1, 1, 0, s>>>(L->st);
   mrd::count_launch();
@@ -505,7 +632,7 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
     return mrd_fail(ctx, MRD_E_ARG, "mrd_lanczos: max_iter out of range");
   // v_0 = theta / |theta|
   MRD_CUDA(ctx, dots(L, theta, 1, theta, L->scal, s));
-  k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(theta, L->V, n, L->scal);
+  k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(theta, L->V, n, L->scal, L->fp32_full ? L->V32 : nullptr);
   mrd::count_launch();
   k_set_step<<<1, 1, 0, s>>>(L->st, 0);
   mrd::count_launch();
@@ -540,7 +667,7 @@ int lanczos_run(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const double2*, do
   k_combination_real<<<grid_for(n), 256, 0, s>>>(L->V, n, k, L->st->y, L->w, n);
   mrd::count_launch();
   MRD_CUDA(ctx, dots(L, L->w, 1, L->w, L->scal, s));
-  k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(L->w, theta, n, L->scal);
+  k_scale_by_invnorm<<<grid_for(n), 256, 0, s>>>(L->w, theta, n, L->scal, nullptr);
   mrd::count_launch();
   MRD_CUDA(ctx, cudaGetLastError());
   MRD_CUDA(ctx, cudaStreamSynchronize(s));
