@@ -49,6 +49,20 @@ __device__ __forceinline__ void ff_mac1(FFAcc& a, FF x, float c) {
   a.c = __fadd_rn(a.c, __fadd_rn(err, e));
 }
 
+// x * c for an FP32 coefficient c as an accumulator (the exact product: no sum to form yet)
+__device__ __forceinline__ FFAcc ff_prod1(FF x, float c) {
+  const float p = __fmul_rn(c, x.hi);
+  float e = __fmaf_rn(c, x.hi, -p);
+  e = __fmaf_rn(c, x.lo, e);
+  return {p, e};
+}
+
+// a * b of two FP32 numbers, exactly, as a float-float value
+__device__ __forceinline__ FF ff_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
 __device__ __forceinline__ FF ff_norm(FFAcc a) {  // FastTwoSum(s, c)
   const float h = __fadd_rn(a.s, a.c);
   return {h, __fsub_rn(a.c, __fsub_rn(h, a.s))};

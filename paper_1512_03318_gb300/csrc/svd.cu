@@ -145,25 +145,42 @@ __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, fl
   const float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
   // x_i' = c u - sigma v, x_j' = s u + kappa v with sigma = s e^{-i phi}, kappa = c e^{-i phi}
   const float sr = sn * ph_r, si = sn * ph_i, kr = c * ph_r, ki = c * ph_i;
-  FFAcc A = {0.f, 0.f}, B = {0.f, 0.f};          // norms of the rotated columns
   for (int q = lane; q < p; q += 32) {
     const float4 u4 = xi[q], v4 = xj[q];
     const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
-    FFAcc o1r = {0.f, 0.f}, o1i = {0.f, 0.f}, o2r = {0.f, 0.f}, o2i = {0.f, 0.f};
-    ff_mac1(o1r, ur, c); ff_mac1(o1r, vr, -sr); ff_mac1(o1r, vi, si);    // c u_r - (s_r v_r - s_i v_i)
-    ff_mac1(o1i, ui, c); ff_mac1(o1i, vi, -sr); ff_mac1(o1i, vr, -si);   // c u_i - (s_r v_i + s_i v_r)
-    ff_mac1(o2r, ur, sn); ff_mac1(o2r, vr, kr); ff_mac1(o2r, vi, -ki);   // s u_r + k_r v_r - k_i v_i
-    ff_mac1(o2i, ui, sn); ff_mac1(o2i, vi, kr); ff_mac1(o2i, vr, ki);    // s u_i + k_r v_i + k_i v_r
+    FFAcc o1r = ff_prod1(ur, c), o1i = ff_prod1(ui, c), o2r = ff_prod1(ur, sn), o2i = ff_prod1(ui, sn);
+    ff_mac1(o1r, vr, -sr); ff_mac1(o1r, vi, si);    // c u_r - (s_r v_r - s_i v_i)
+    ff_mac1(o1i, vi, -sr); ff_mac1(o1i, vr, -si);   // c u_i - (s_r v_i + s_i v_r)
+    ff_mac1(o2r, vr, kr); ff_mac1(o2r, vi, -ki);    // s u_r + k_r v_r - k_i v_i
+    ff_mac1(o2i, vi, kr); ff_mac1(o2i, vr, ki);     // s u_i + k_r v_i + k_i v_r
     const FF a1 = ff_norm(o1r), b1 = ff_norm(o1i), a3 = ff_norm(o2r), b3 = ff_norm(o2i);
     xi[q] = make_float4(a1.hi, b1.hi, a1.lo, b1.lo);
     xj[q] = make_float4(a3.hi, b3.hi, a3.lo, b3.lo);
-    ff_mac(A, a1, a1);
-    ff_mac(A, b1, b1);
-    ff_mac(B, a3, a3);
-    ff_mac(B, b3, b3);
   }
-  na = ff_warp_sum(ff_norm(A));
-  nb = ff_warp_sum(ff_norm(B));
+  // Norms of the rotated columns from the pair's own values, with the coefficients that were
+  // applied (exact FP32 numbers, whether or not they form an exactly unitary rotation), g =
+  // conj(u) . v:
+  //   |c u - sigma v|^2 = c^2 a + |sigma|^2 b - 2 c Re(sigma g),
+  //   |s u + kappa v|^2 = s^2 a + |kappa|^2 b + 2 s Re(kappa g).
+  // The identities hold for any c, sigma, kappa; in float-float they give the norms to ~1e-14
+  // (as summing the rotated elements would), for ~20 operations per pair instead of 4
+  // multiply-adds per element and two warp reductions.
+  {
+    const FF a = na, b = nb;
+    FFAcc A = {0.f, 0.f}, B = {0.f, 0.f};
+    const FF sig2 = ff_add(ff_two_prod(sr, sr), ff_two_prod(si, si));
+    const FF kap2 = ff_add(ff_two_prod(kr, kr), ff_two_prod(ki, ki));
+    ff_mac(A, ff_two_prod(c, c), a);
+    ff_mac(A, sig2, b);
+    ff_mac(A, ff_two_prod(-2.f * c, sr), gr2);         // -2 c (s_r g_r - s_i g_i)
+    ff_mac(A, ff_two_prod(2.f * c, si), gi2);
+    ff_mac(B, ff_two_prod(sn, sn), a);
+    ff_mac(B, kap2, b);
+    ff_mac(B, ff_two_prod(2.f * sn, kr), gr2);         // 2 s (k_r g_r - k_i g_i)
+    ff_mac(B, ff_two_prod(-2.f * sn, ki), gi2);
+    na = ff_norm(A);
+    nb = ff_norm(B);
+  }
   return true;
 }
 
@@ -251,27 +268,28 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
   }
   // float-float columns are held scaled by ff_scale(fro2) (svd_ff_io)
   const double up = MODE == 2 ? ff_scale(fro2[b]) : 1.0;
-  // stage: local column c < W is column gI*W + c, c >= W is column gJ*W + c - W
-  for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * p; e += blockDim.x) {
-    const int cc = (int)(e / p), t = (int)(e % p);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  // stage: local column c < W is column gI*W + c, c >= W is column gJ*W + c - W (one warp
+  // per column, lanes along it)
+  for (int cc = warp; cc < nI + nJ; cc += nwarp) {
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
-    sx[(int64_t)lc * p + t] = X[(int64_t)gc * p + t];
+    const T2* src = X + (int64_t)gc * p;
+    S2* dst = sx + (int64_t)lc * p;
+    for (int t = lane; t < p; t += 32) dst[t] = src[t];
+    if constexpr (MODE == 0)
+      if (V != nullptr) {
+        const T2* vs = V + (int64_t)gc * r;
+        S2* vd = sv + (int64_t)lc * r;
+        for (int t = lane; t < r; t += 32) vd[t] = vs[t];
+      }
   }
-  if (V != nullptr)
-    for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * r; e += blockDim.x) {
-      const int cc = (int)(e / r), t = (int)(e % r);
-      const int lc = cc < nI ? cc : W + cc - nI;
-      const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
-      if constexpr (MODE == 0) sv[(int64_t)lc * r + t] = V[(int64_t)gc * r + t];
-    }
   for (int cc = threadIdx.x; cc < nI + nJ; cc += blockDim.x) {
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
     s_last[lc] = last_rot[d[8] + gc];
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if constexpr (MODE == 2) {   // norms of the staged columns, one warp per column
     for (int cc = warp; cc < nI + nJ; cc += blockDim.x >> 5) {
       const int lc = cc < nI ? cc : W + cc - nI;
@@ -334,20 +352,19 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     __syncthreads();
   }
   if (lane == 0 && mine) atomicAdd(&n_rot, mine);
-  for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * p; e += blockDim.x) {
-    const int cc = (int)(e / p), t = (int)(e % p);
+  for (int cc = warp; cc < nI + nJ; cc += nwarp) {
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
-    X[(int64_t)gc * p + t] = sx[(int64_t)lc * p + t];
-  }
-  if constexpr (MODE == 0)
-    if (V != nullptr)
-      for (int64_t e = threadIdx.x; e < (int64_t)(nI + nJ) * r; e += blockDim.x) {
-        const int cc = (int)(e / r), t = (int)(e % r);
-        const int lc = cc < nI ? cc : W + cc - nI;
-        const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
-        V[(int64_t)gc * r + t] = sv[(int64_t)lc * r + t];
+    T2* dst = X + (int64_t)gc * p;
+    const S2* src = sx + (int64_t)lc * p;
+    for (int t = lane; t < p; t += 32) dst[t] = src[t];
+    if constexpr (MODE == 0)
+      if (V != nullptr) {
+        T2* vd = V + (int64_t)gc * r;
+        const S2* vs = sv + (int64_t)lc * r;
+        for (int t = lane; t < r; t += 32) vd[t] = vs[t];
       }
+  }
   for (int cc = threadIdx.x; cc < nI + nJ; cc += blockDim.x) {
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
