@@ -43,6 +43,7 @@ LX_MATVEC = 20            # cylinder of the matvec throughput measurement
 SEED = 1234 + 3           # workload index 3 (chi = 3200)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 FP32_ISSUE_TINSTR = 128 * 152 * 2.070e9 / 1e12     # FP32 instructions per second (lanes x SMs x clock)
+FF_INSTR_PER_CMAC = 36   # FP32 instructions of a float-float complex multiply-add (3 products of 12)
 PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "ff": 3}
 
 
@@ -533,9 +534,10 @@ def main():
     dominant = max(shares, key=shares.get)
     if dominant.startswith("k_svd_bround"):
         # float-float Jacobi: FP32 instructions of the work done (per element of a tested pair:
-        # 4 float-float multiply-adds of 12 instructions; per element of a rotated pair: 12 of
-        # 11, 4 FastTwoSums of 3 and 4 of 12), against the FP32 issue rate
-        instr = svd_work[1] * 48 + svd_work[2] * 192
+        # 4 float-float multiply-adds of 12 instructions; per element of a rotated pair: 4
+        # exact products of 3, 8 multiply-adds of 11 and 4 FastTwoSums of 3; the rotated
+        # norms are per pair, not per element), against the FP32 issue rate
+        instr = svd_work[1] * 48 + svd_work[2] * 112
         ach = instr / (svd_work[0] / 1e3) / 1e12
         roof = {"kernel": "k_svd_bround<float-float> (block-cyclic Jacobi rounds)", "bound": "alu", "achieved": ach,
                 "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
@@ -549,7 +551,7 @@ def main():
                 "ms_per_step": tc_ms / args.steps, "share_of_measured_kernels": tc_ms / sum(shares.values())}
     else:
         per = hp_ms / max(kn[1], 1) / 1e3
-        ach = f_exec / 8 * 48 / per / 1e12
+        ach = f_exec / 8 * FF_INSTR_PER_CMAC / per / 1e12
         roof = {"kernel": "k_cgemm_ff (float-float refinement matvec, steps 1+2)", "bound": "alu", "achieved": ach,
                 "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
                 "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived, DESIGN.md)",
@@ -594,10 +596,10 @@ def main():
                                "traffic": None, "note": "hardware bf16 flops = 3 x executed complex-product flops "
                                                         f"(split), peak = bf16 burst {peak_src}"},
         "roofline_ff_gemm": {"kernel": "k_cgemm_ff (steps 1+2), Lx=20 matvec", "bound": "alu",
-                             "achieved": f_exec / 8 * 48 / (mv["ff"]["ms"] / 1e3) / 1e12, "peak": FP32_ISSUE_TINSTR,
+                             "achieved": f_exec / 8 * FF_INSTR_PER_CMAC / (mv["ff"]["ms"] / 1e3) / 1e12, "peak": FP32_ISSUE_TINSTR,
                              "unit": "T FP32-instr/s",
-                             "frac": f_exec / 8 * 48 / (mv["ff"]["ms"] / 1e3) / 1e12 / FP32_ISSUE_TINSTR,
-                             "traffic": None, "note": "48 FP32 instructions per complex multiply-add (4 float-float)"},
+                             "frac": f_exec / 8 * FF_INSTR_PER_CMAC / (mv["ff"]["ms"] / 1e3) / 1e12 / FP32_ISSUE_TINSTR,
+                             "traffic": None, "note": "36 FP32 instructions per complex multiply-add (3 float-float products of 12)"},
         "roofline_tc_tf32": {"kernel": "k_tc_gemm TF32 (steps 1+2), Lx=20 matvec", "bound": "tensor",
                              "achieved": tf_hw, "peak": bf16_peak / 2, "unit": "TFLOP/s",
                              "frac": tf_hw / (bf16_peak / 2), "traffic": None,
