@@ -35,8 +35,8 @@ cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, co
 cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* src_off, int nblk, double2* work,
                      double* fro2, cudaStream_t s);
 int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
-cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
-                       int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
+cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
+                       const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
                        int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s);
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
                       cudaStream_t s);
@@ -44,7 +44,8 @@ cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double
                        double* S_sorted, int* order_scratch, const double* fro2, cudaStream_t s);
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
                          int* keep, double* info, int* flat_block, cudaStream_t s);
-cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
+cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
+                         int64_t ncta,
                          int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
                          int sweep, unsigned long long* wctr, cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
@@ -517,7 +518,15 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     int W = 0, rounds = 0;
     int64_t ncta = 0, smem = 0;
   };
-  std::vector<int64_t> pp(2 * (nb + 1), 0);
+  // pp: CTA prefix of the FP32 rounds, of the final rounds (nb + 1 each), then the block order
+  // of both: longest sweep first (columns x rows, the per-sweep chain of a block's rounds), so
+  // that the CTAs of the largest blocks take the lowest indices and spread over the SMs first
+  std::vector<int64_t> pp(3 * nb + 2, 0);
+  int64_t* order = pp.data() + 2 * (nb + 1);
+  for (int b = 0; b < nb; ++b) order[b] = b;
+  std::stable_sort(order, order + nb, [&](int64_t x, int64_t y) {
+    return blk[SVF * x + 3] * blk[SVF * x + 2] > blk[SVF * y + 3] * blk[SVF * y + 2];
+  });
   auto schedule = [&](int W, bool f32, int64_t* pre) -> Sched {
     Sched sc;
     for (;;) {
@@ -529,17 +538,17 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     }
     sc.W = W;
     pre[0] = 0;
-    for (int b = 0; b < nb; ++b) {
-      const int64_t r = blk[SVF * b + 3];
+    for (int k = 0; k < nb; ++k) {
+      const int64_t r = blk[SVF * order[k] + 3];
       const int64_t G = (r + W - 1) / W, Gp = std::max<int64_t>(2, G + (G & 1));
-      pre[b + 1] = pre[b] + (r > 0 ? Gp / 2 : 0);
+      pre[k + 1] = pre[k] + (r > 0 ? Gp / 2 : 0);
       if (r > 0) sc.rounds = std::max<int>(sc.rounds, (int)(Gp - 1));
     }
     sc.ncta = pre[nb];
     return sc;
   };
   const bool ff_cols = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
-  const Sched s32 = schedule(16, true, pp.data()), s64 = schedule(ff_cols ? 16 : 8, false, pp.data() + nb + 1);
+  const Sched s32 = schedule(8, true, pp.data()), s64 = schedule(ff_cols ? 16 : 8, false, pp.data() + nb + 1);
   if (s32.smem > kSvdMaxSmemHost || s64.smem > kSvdMaxSmemHost)
     return mrd_fail(ctx, MRD_E_OOM, "block SVD: a block is too large for the shared-memory Jacobi rounds");
   MRD_CUDA(ctx, D->svd_blk.need(blk.size() * 8));
@@ -568,6 +577,7 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   int* rot = D->svd_rot.as<int>();
   const int64_t* pre32 = D->svd_pref.as<int64_t>();
   const int64_t* pre64 = pre32 + nb + 1;
+  const int64_t* ord = pre32 + 2 * (nb + 1);
   // per phase: the rounds' time (events around the sweeps) and work (element-pairs tested and
   // rotated, counted by the kernels), reported by mrd_dmrg_svd_stats
   if (!D->svd_ev[0]) {
@@ -590,10 +600,10 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
       MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
       for (int rd = 0; rd < sc.rounds; ++rd) {
         if (f32)
-          MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f, fro,
+          MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, ord, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f, fro,
                                      rot, last, sweep, wctr, s));
         else
-          MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, nb,
+          MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, ord, nb,
                                    sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, wctr, s));
       }
       int hrot = 0;

@@ -234,7 +234,8 @@ __device__ __forceinline__ void rr_pair(int n, int s, int q, int& i, int& j) {
 // (float4, scaled by ff_scale).
 template <int MODE, class T, class T2, class S2>
 __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf, int vf,
-                             const int64_t* __restrict__ grp_prefix, int nblk, int round, int W, T tol,
+                             const int64_t* __restrict__ grp_prefix, const int64_t* __restrict__ order, int nblk,
+                             int round, int W, T tol,
                              const double* __restrict__ fro2, double zero_rel, int* __restrict__ rotated,
                              int* __restrict__ last_rot, int sweep, unsigned long long* __restrict__ wctr) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -243,17 +244,17 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
   __shared__ int s_last[32];   // sweep in which each staged column last rotated
   __shared__ FF s_norm[32];    // float-float column norms (MODE 2)
   const int64_t cta = blockIdx.x;
-  int lo = 0, hi = nblk - 1;   // largest b with grp_prefix[b] <= cta
-  while (lo < hi) {
+  int lo = 0, hi = nblk - 1;   // largest k with grp_prefix[k] <= cta; the CTAs run over the
+  while (lo < hi) {            // blocks in the order `order` (longest sweeps first)
     const int mid = (lo + hi + 1) >> 1;
     if (grp_prefix[mid] <= cta) lo = mid; else hi = mid - 1;
   }
-  const int b = lo;
+  const int b = (int)order[lo];
   const int64_t* d = blk + SVF * b;
   const int p = (int)d[2], r = (int)d[3];
   const int G = (r + W - 1) / W, Gp = G + (G & 1) < 2 ? 2 : G + (G & 1);
   if (r == 0 || round >= Gp - 1) return;
-  const int k = (int)(cta - grp_prefix[b]);
+  const int k = (int)(cta - grp_prefix[lo]);
   int gI, gJ;
   rr_pair(Gp, round, k, gI, gJ);
   const int nI = gI < G ? min(W, r - gI * W) : 0, nJ = gJ < G ? min(W, r - gJ * W) : 0;
@@ -588,8 +589,8 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32) {
 
 // FP64 rounds on X (field 4 of work) or, with xff != nullptr, float-float rounds on the
 // float-float copy xff (same offsets, see svd_ff_io).
-cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix, int nblk,
-                       int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
+cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
+                       const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
                        int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
   static bool attr = false;
@@ -604,10 +605,10 @@ cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int
   }
   if (xff)
     k_svd_bround<2, double, float4, float4><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        xff, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
+        xff, blk, 4, -1, grp_prefix, order, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
   else
     k_svd_bround<1, double, double2, double2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        work, blk, 4, -1, grp_prefix, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
+        work, blk, 4, -1, grp_prefix, order, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -621,7 +622,8 @@ cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, 
   return cudaGetLastError();
 }
 
-cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, int nblk, int64_t ncta,
+cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
+                         int64_t ncta,
                          int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
                          int sweep, unsigned long long* wctr, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
@@ -633,7 +635,7 @@ cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_pre
     attr = true;
   }
   k_svd_bround<0, float, float2, float2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-      w32, blk, 10, 11, grp_prefix, nblk, round, W, tol, fro2, 1e-12, rotated, last_rot, sweep, wctr);
+      w32, blk, 10, 11, grp_prefix, order, nblk, round, W, tol, fro2, 1e-12, rotated, last_rot, sweep, wctr);
   mrd::count_launch();
   return cudaGetLastError();
 }
