@@ -339,6 +339,21 @@ def real_vs_mixed_or_note(P, ctx, torch, dev, stream):
         return {"skipped": f"{type(e).__name__}: {e}"}
 
 
+def mpo_diagnostics(P):
+    """Mean and largest MPO bond dimension and mean fill over a bulk ring (the second of three),
+    real-space and mixed machines, against the real-space 3L + 2 (Sec. IV.C-D). Host only."""
+    out = {}
+    for ly in (4, 6, 8, 10, 12):
+        row = {"3L+2": 3 * ly + 2}
+        for name, basis in (("real", P.MRD_BASIS_REAL), ("mixed", P.MRD_BASIS_MIXED)):
+            m = P.MPO(None, 3, ly, 1, ly, T_HOP, V_INT, basis)
+            mean_d, max_d, fill, _ = m.stats(ly, ly)
+            row[name] = {"mean_D": round(mean_d, 3), "max_D": max_d, "fill": round(fill, 4)}
+            m.close()
+        out[str(ly)] = row
+    return out
+
+
 def make_state(P, ctx, mpo, chi, caps, seed):
     return P.DMRG(ctx, mpo, LX_UPDATE, 0, chi, seed=seed, center=update_centre(LX_UPDATE), caps=caps)
 
@@ -590,6 +605,7 @@ def main():
                                                round(mv["bf16x3"]["ms_per_task_launches"], 3)],
         "heff_flops": {"definition": mv["flops_definition"], "executed": mv["flops_executed"]},
         "real_vs_mixed_heff": rvm,
+        "mpo_diagnostics": mpo_diagnostics(P),
         "roofline": roof,
         "roofline_tc_bf16x3": {"kernel": "k_tc_gemm BF16X3 (steps 1+2), Lx=20 matvec", "bound": "tensor",
                                "achieved": tc_hw, "peak": bf16_peak, "unit": "TFLOP/s", "frac": tc_hw / bf16_peak,

@@ -108,6 +108,13 @@ int mrd_mpo_bond(const mrd_mpo* mpo, int32_t bond, int32_t* dim, int32_t* charge
 /* Nonzero entries of site `site`: if idx != NULL writes 4*nnz int32 (w, w', s', s) and if
  * val != NULL 2*nnz doubles (re, im), ordered by (w, w', s', s). */
 int mrd_mpo_site(const mrd_mpo* mpo, int32_t site, int32_t* nnz, int32_t* idx, double* val);
+/* MPO diagnostics of Sec. IV.D (its figure of the mean bond dimension <D> against the
+ * circumference, and of the fraction of nonzero MPO entries), over the `count` sites
+ * first .. first+count-1 (e.g. one ring, first = x*ly, count = ly) and the bonds
+ * first .. first+count-1 to their left: out4 = {mean bond dimension, largest bond dimension,
+ * mean fill (nonzero entries of site j / (D_j * D_{j+1} * 4)), total nonzero entries}.
+ * MRD_E_ARG unless 0 <= first and 1 <= count and first + count <= n_sites. Host only. */
+int mrd_mpo_stats(const mrd_mpo* mpo, int32_t first, int32_t count, double* out4);
 
 /* ------------------------------------------------------------------ two-site H_eff */
 

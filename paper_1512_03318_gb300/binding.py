@@ -92,6 +92,7 @@ _SIGS = {
     "mrd_mpo_bond": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mrd_mpo_site": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_double)]),
+    "mrd_mpo_stats": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "mrd_heff_create": (C.c_int, [C.c_void_p, C.POINTER(mrd_heff_desc), C.POINTER(C.c_void_p)]),
     "mrd_heff_free": (C.c_int, [C.c_void_p]),
     "mrd_heff_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -246,6 +247,15 @@ class MPO:
         val = np.zeros(2 * nnz.value, dtype=np.float64)
         lib().mrd_mpo_site(self.h, j, C.byref(nnz), _p32(idx), _p64f(val))
         return idx.reshape(-1, 4), val[0::2] + 1j * val[1::2]
+
+    def stats(self, first, count):
+        """(mean bond dimension, largest, mean fill, nonzero entries) of sites first ..
+        first+count-1 and the bonds to their left (mrd_mpo_stats)."""
+        out = (C.c_double * 4)()
+        rc = lib().mrd_mpo_stats(self.h, first, count, out)
+        if rc != 0:
+            raise MrdError(rc, "mrd_mpo_stats: bad site range")
+        return out[0], int(out[1]), out[2], int(out[3])
 
     def close(self):
         if getattr(self, "h", None):

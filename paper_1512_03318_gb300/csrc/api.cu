@@ -144,6 +144,25 @@ int mrd_mpo_site(const mrd_mpo* mpo, int32_t site, int32_t* nnz, int32_t* idx, d
   return MRD_OK;
 }
 
+int mrd_mpo_stats(const mrd_mpo* mpo, int32_t first, int32_t count, double* out4) {
+  if (!mpo || !out4 || first < 0 || count < 1 || first > mpo->h.n_sites - count) return MRD_E_ARG;
+  double dsum = 0.0, fsum = 0.0, nnz = 0.0;
+  int64_t dmax = 0;
+  for (int32_t j = first; j < first + count; ++j) {
+    const int64_t dl = (int64_t)mpo->h.bond_charges[j].size() / 2, dr = (int64_t)mpo->h.bond_charges[j + 1].size() / 2;
+    const double n = (double)(mpo->h.site_idx[j].size() / 4);
+    dsum += (double)dl;
+    dmax = std::max(dmax, dl);
+    fsum += dl * dr > 0 ? n / (4.0 * (double)dl * (double)dr) : 0.0;
+    nnz += n;
+  }
+  out4[0] = dsum / count;
+  out4[1] = (double)dmax;
+  out4[2] = fsum / count;
+  out4[3] = nnz;
+  return MRD_OK;
+}
+
 // ------------------------------------------------------------------ H_eff
 
 static int validate_sectors(mrd_ctx* ctx, const int32_t* s, int n, int mod, const char* what) {

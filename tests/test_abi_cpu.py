@@ -47,3 +47,27 @@ def test_mpo_build_rejects_bad_model():
         P.MPO(None, 2, 1, 1, 4, 1.0, 1.0, P.MRD_BASIS_MIXED)
     with pytest.raises(P.MrdError):
         P.MPO(None, 2, 4, 1, 0, 1.0, 1.0, P.MRD_BASIS_MIXED)
+
+
+@pytest.mark.parametrize("basis,b", [("mixed", P.MRD_BASIS_MIXED), ("real", P.MRD_BASIS_REAL)])
+@pytest.mark.parametrize("lx,ly", [(3, 4), (3, 6), (3, 8)])
+def test_mpo_stats(basis, b, lx, ly):
+    """mrd_mpo_stats over the middle ring equals the bookkeeping of the oracle's MPO (bond
+    dimensions and nonzero entries counted here); the real-space ring has D = 3L + 2 on every
+    bond (Sec. IV.C) and the mixed one stays under the crude bound 26 L + 9 (Sec. IV.D)."""
+    m = P.MPO(None, lx, ly, 1, ly, 1.0, 1.0, b)
+    o = M.build_mpo(lx, ly, 1 / ly, 1.0, 1.0, basis)
+    first, count = ly, ly
+    dims = o.dims()
+    mean_d, max_d, fill, nnz = m.stats(first, count)
+    want_fill = np.mean([len(o.entries[j]) / (4 * dims[j] * dims[j + 1]) for j in range(first, first + count)])
+    assert mean_d == pytest.approx(np.mean(dims[first:first + count]), abs=1e-12)
+    assert max_d == max(dims[first:first + count])
+    assert fill == pytest.approx(want_fill, abs=1e-12)
+    assert nnz == sum(len(o.entries[j]) for j in range(first, first + count))
+    if basis == "real":
+        assert mean_d == 3 * ly + 2 and max_d == 3 * ly + 2
+    else:
+        assert max_d <= 26 * ly + 9
+    with pytest.raises(P.MrdError):
+        m.stats(m.n_sites - 1, 2)

@@ -104,3 +104,35 @@ def test_eq_m_example():
     for r in range(4):
         for c in range(4):
             assert np.allclose(w[r, c], expect[r][c], atol=1e-15)
+
+
+def _operator_schmidt_rank(mpo, b):
+    """Rank of the Hamiltonian across bond b: the left block's operators per channel (sites
+    0..b-1) and the right block's (sites b..n-1), both as vectors of operator entries; the
+    rank of left x right^T is that of the product of their QR triangles."""
+    L = np.ones((1, 1, 1), dtype=complex)
+    for j in range(b):
+        W = mpo.dense_site(j)                                   # [w, w', s', s]
+        L = np.einsum("abw,wvps->apbsv", L, W).reshape(2 * L.shape[0], 2 * L.shape[1], W.shape[1])
+    R = np.ones((1, 1, 1), dtype=complex)
+    for j in range(mpo.n_sites - 1, b - 1, -1):
+        W = mpo.dense_site(j)
+        R = np.einsum("wvps,abv->pasbw", W, R).reshape(2 * R.shape[0], 2 * R.shape[1], W.shape[0])
+    d = L.shape[2]
+    rl = np.linalg.qr(L.reshape(-1, d))[1]
+    rr = np.linalg.qr(R.reshape(-1, d))[1]
+    sv = np.linalg.svd(rl @ rr.T, compute_uv=False)
+    return d, int(np.sum(sv > 1e-10 * sv[0]))
+
+
+@pytest.mark.parametrize("ly", [4, 5])
+def test_bond_dimension_against_operator_schmidt_rank(ly):
+    """The real-space machine is minimal (D = rank = 3L + 2, Sec. IV.C). The mixed machine is
+    within one of the Hamiltonian's operator Schmidt rank in the middle of a ring, and that
+    rank is above 3L + 2: the trimmed mixed D cannot fall below the real-space one there."""
+    b = ly + ly // 2
+    d, r = _operator_schmidt_rank(M.build_mpo(3, ly, 1 / ly, 1.0, 1.0, "real"), b)
+    assert d == r == 3 * ly + 2
+    d, r = _operator_schmidt_rank(M.build_mpo(3, ly, 1 / ly, 1.0, 1.0, "mixed"), b)
+    assert r <= d <= r + 1
+    assert r > 3 * ly + 2
