@@ -358,62 +358,12 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
     return mrd_cuda_fail(ctx, e, "mrd_heff_create: operand buffers");
   }
 
-  // flops in the order of the definition (host arithmetic on the device-built tables)
+  // middle-sector table on the host (tensor-core panel tables, flop counts)
   {
     std::vector<int64_t>& mid = h->mid_host;
     mid.resize(MIDF * h->counts[C_NMID]);
     e = cudaMemcpy(mid.data(), p.mid, mid.size() * 8, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { delete h; mrd_ctx_release(ctx); return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }
-    // theta blocks (a, s1, s2) -> (d_a, d_b, b)
-    struct TB { int a, s1, s2, b; int64_t da, db; };
-    std::vector<TB> tb;
-    for (int64_t m = 0; m < h->counts[C_NMID]; ++m) {
-      const int64_t* r = &mid[MIDF * m];
-      for (int s1 = 0; s1 < 2; ++s1)
-        for (int s2 = 0; s2 < 2; ++s2) {
-          if (r[5 + s1] < 0 || r[8 + s2] < 0) continue;
-          int a = (int)r[5 + s1], b = (int)r[8 + s2];
-          tb.push_back({a, s1, s2, b, h->left[3 * a + 2], h->right[3 * b + 2]});
-        }
-    }
-    auto find = [&](const std::vector<int32_t>& sec, int N, int K) {
-      int n = (int)sec.size() / 3;
-      for (int i = 0; i < n; ++i) if (sec[3 * i] == N && sec[3 * i + 1] == K) return i;
-      return -1;
-    };
-    double fl = 0.0;
-    std::vector<std::vector<std::vector<std::tuple<int, int, int64_t, int64_t>>>> xk(
-        d.d_l, std::vector<std::vector<std::tuple<int, int, int64_t, int64_t>>>(4));
-    for (const TB& t : tb)
-      for (int w = 0; w < d.d_l; ++w) {
-        int ap = find(h->left, h->left[3 * t.a] + h->cl[2 * w], kmod(h->left[3 * t.a + 1] + h->cl[2 * w + 1], d.mod));
-        if (ap < 0) continue;
-        int64_t dp = h->left[3 * ap + 2];
-        fl += 8.0 * dp * t.da * t.db;
-        xk[w][t.s1 * 2 + t.s2].emplace_back(ap, t.b, dp, t.db);
-      }
-    std::vector<std::vector<std::tuple<int, int, int, double>>> wj_by(d.d_m);
-    for (int e2 = 0; e2 < d.nnz_j; ++e2)
-      wj_by[h->wj_idx[4 * e2]].emplace_back(h->wj_idx[4 * e2 + 1], h->wj_idx[4 * e2 + 2], h->wj_idx[4 * e2 + 3], 0.0);
-    std::set<std::tuple<int, int, int, int, int>> ykeys;
-    std::vector<std::tuple<int, int, int, int, int, int64_t, int64_t>> ylist;
-    for (int e1 = 0; e1 < d.nnz_i; ++e1) {
-      int w = h->wi_idx[4 * e1], wp = h->wi_idx[4 * e1 + 1], s1p = h->wi_idx[4 * e1 + 2], s1 = h->wi_idx[4 * e1 + 3];
-      for (const auto& j : wj_by[wp]) {
-        int wpp = std::get<0>(j), s2p = std::get<1>(j), s2 = std::get<2>(j);
-        for (const auto& x : xk[w][s1 * 2 + s2]) {
-          fl += 8.0 * std::get<2>(x) * std::get<3>(x);
-          auto key = std::make_tuple(wpp, std::get<0>(x), s1p, s2p, std::get<1>(x));
-          if (ykeys.insert(key).second) ylist.emplace_back(wpp, std::get<0>(x), s1p, s2p, std::get<1>(x), std::get<2>(x), std::get<3>(x));
-        }
-      }
-    }
-    for (const auto& y : ylist) {
-      int wpp = std::get<0>(y), bi = std::get<4>(y);
-      int bp = find(h->right, h->right[3 * bi] + h->cr[2 * wpp], kmod(h->right[3 * bi + 1] + h->cr[2 * wpp + 1], d.mod));
-      if (bp >= 0) fl += 8.0 * std::get<5>(y) * std::get<6>(y) * h->right[3 * bp + 2];
-    }
-    h->def_flops = fl;
   }
   *out = h;
   return MRD_OK;
@@ -594,8 +544,69 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   return MRD_OK;
 }
 
+// Flops of one application in the order of the definition (L, then W_i W_{i+1}, then R, as
+// the oracle counts them): host arithmetic on the tables, computed on the first request only.
+static double definition_flops(const mrd_heff* h) {
+  const std::vector<int64_t>& mid = h->mid_host;
+  const PlanDims& d = h->d;
+  // theta blocks (a, s1, s2) -> (d_a, d_b, b)
+  struct TB { int a, s1, s2, b; int64_t da, db; };
+  std::vector<TB> tb;
+  for (int64_t m = 0; m < h->counts[C_NMID]; ++m) {
+    const int64_t* r = &mid[MIDF * m];
+    for (int s1 = 0; s1 < 2; ++s1)
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (r[5 + s1] < 0 || r[8 + s2] < 0) continue;
+        int a = (int)r[5 + s1], b = (int)r[8 + s2];
+        tb.push_back({a, s1, s2, b, h->left[3 * a + 2], h->right[3 * b + 2]});
+      }
+  }
+  auto find = [&](const std::vector<int32_t>& sec, int N, int K) {
+    int n = (int)sec.size() / 3;
+    for (int i = 0; i < n; ++i) if (sec[3 * i] == N && sec[3 * i + 1] == K) return i;
+    return -1;
+  };
+  double fl = 0.0;
+  std::vector<std::vector<std::vector<std::tuple<int, int, int64_t, int64_t>>>> xk(
+      d.d_l, std::vector<std::vector<std::tuple<int, int, int64_t, int64_t>>>(4));
+  for (const TB& t : tb)
+    for (int w = 0; w < d.d_l; ++w) {
+      int ap = find(h->left, h->left[3 * t.a] + h->cl[2 * w], kmod(h->left[3 * t.a + 1] + h->cl[2 * w + 1], d.mod));
+      if (ap < 0) continue;
+      int64_t dp = h->left[3 * ap + 2];
+      fl += 8.0 * dp * t.da * t.db;
+      xk[w][t.s1 * 2 + t.s2].emplace_back(ap, t.b, dp, t.db);
+    }
+  std::vector<std::vector<std::tuple<int, int, int, double>>> wj_by(d.d_m);
+  for (int e2 = 0; e2 < d.nnz_j; ++e2)
+    wj_by[h->wj_idx[4 * e2]].emplace_back(h->wj_idx[4 * e2 + 1], h->wj_idx[4 * e2 + 2], h->wj_idx[4 * e2 + 3], 0.0);
+  std::set<std::tuple<int, int, int, int, int>> ykeys;
+  std::vector<std::tuple<int, int, int, int, int, int64_t, int64_t>> ylist;
+  for (int e1 = 0; e1 < d.nnz_i; ++e1) {
+    int w = h->wi_idx[4 * e1], wp = h->wi_idx[4 * e1 + 1], s1p = h->wi_idx[4 * e1 + 2], s1 = h->wi_idx[4 * e1 + 3];
+    for (const auto& j : wj_by[wp]) {
+      int wpp = std::get<0>(j), s2p = std::get<1>(j), s2 = std::get<2>(j);
+      for (const auto& x : xk[w][s1 * 2 + s2]) {
+        fl += 8.0 * std::get<2>(x) * std::get<3>(x);
+        auto key = std::make_tuple(wpp, std::get<0>(x), s1p, s2p, std::get<1>(x));
+        if (ykeys.insert(key).second) ylist.emplace_back(wpp, std::get<0>(x), s1p, s2p, std::get<1>(x), std::get<2>(x), std::get<3>(x));
+      }
+    }
+  }
+  for (const auto& y : ylist) {
+    int wpp = std::get<0>(y), bi = std::get<4>(y);
+    int bp = find(h->right, h->right[3 * bi] + h->cr[2 * wpp], kmod(h->right[3 * bi + 1] + h->cr[2 * wpp + 1], d.mod));
+    if (bp >= 0) fl += 8.0 * std::get<5>(y) * std::get<6>(y) * h->right[3 * bp + 2];
+  }
+  return fl;
+}
+
 int mrd_heff_flops(const mrd_heff* h, double* flops4) {
   if (!h || !flops4) return MRD_E_ARG;
+  if (!h->def_flops_done) {
+    h->def_flops = definition_flops(h);
+    h->def_flops_done = true;
+  }
   flops4[0] = h->def_flops;
   flops4[1] = (double)h->counts[C_FLOPS1] + (double)h->counts[C_FLOPS2];
   flops4[2] = (double)h->counts[C_FLOPS1];

@@ -81,7 +81,8 @@ struct mrd_heff {
   double2* wr = nullptr;
   double2* z = nullptr;
   bool env_loaded = false;
-  double def_flops = 0.0;
+  mutable double def_flops = 0.0;   // definition-order flops, computed on first request
+  mutable bool def_flops_done = false;
   int n_sm = 152;
   std::vector<int32_t> left, right, cl, cm, cr, wi_idx, wj_idx;
   std::vector<double> wi_v, wj_v;

@@ -47,6 +47,26 @@ struct Panel {
   int64_t off, nkt;
 };
 
+// Panels keyed by the FP64 element offset of their block: appended in build order, sorted once
+// (stably, so that of equal keys, e.g. an empty block and the one after it, the last appended
+// wins), then found by binary search. Tens of thousands of lookups per H_eff: a sorted vector
+// avoids the per-node allocations and pointer chasing of a tree map.
+struct PanelIndex {
+  std::vector<std::pair<int64_t, Panel>> v;
+  void add(int64_t key, Panel p) { v.push_back({key, p}); }
+  void finish() {
+    auto lt = [](const std::pair<int64_t, Panel>& a, const std::pair<int64_t, Panel>& b) { return a.first < b.first; };
+    if (!std::is_sorted(v.begin(), v.end(), lt)) std::stable_sort(v.begin(), v.end(), lt);
+  }
+  const Panel* find(int64_t key) const {
+    auto it = std::upper_bound(v.begin(), v.end(), key,
+                               [](int64_t k, const std::pair<int64_t, Panel>& e) { return k < e.first; });
+    if (it == v.begin()) return nullptr;
+    --it;
+    return it->first == key ? &it->second : nullptr;
+  }
+};
+
 // bytes of an A panel (128-row tiles) or a B panel (ntile-row tiles, rows padded to 16)
 int64_t a_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 128) * nkt * planes * 128; }
 int64_t b_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 16) * nkt * planes * 128; }
@@ -56,14 +76,16 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   Tc* T = h->tc;
   const int planes = tc_planes(prec), kpt = tc_kpt(prec), ntile = cfg.ntile;
   const int64_t* c = h->counts;
-  std::map<int64_t, Panel> lw_map, wr_map, th_map, z_map;
+  PanelIndex lw_map, wr_map, th_map, z_map;
+  lw_map.v.reserve(c[C_NLW]);
+  wr_map.v.reserve(c[C_NWR]);
   std::vector<int64_t> j_lw, j_wr, j_th;
   int64_t lw_b = 0, wr_b = 0, th_b = 0, z_b = 0;
   // folded left operand LW(w', s1', s1, a): A panel, rows d_a', K d_a
   for (int64_t k = 0; k < c[C_NLW]; ++k) {
     const int64_t* r = &h->lw_host[LWF * k];
     const int64_t rows = r[5], K = r[6], nkt = (K + kpt - 1) / kpt;
-    lw_map[r[7]] = {lw_b, nkt};
+    lw_map.add(r[7], {lw_b, nkt});
     j_lw.insert(j_lw.end(), {r[7], K, 0, rows, K, lw_b, 128, nkt, round_up(rows, 128), 0});
     lw_b += a_bytes(rows, nkt, planes);
   }
@@ -71,7 +93,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   for (int64_t k = 0; k < c[C_NWR]; ++k) {
     const int64_t* r = &h->wr_host[WRF * k];
     const int64_t K = r[5], rows = r[6], nkt = (K + kpt - 1) / kpt;
-    wr_map[r[7]] = {wr_b, nkt};
+    wr_map.add(r[7], {wr_b, nkt});
     j_wr.insert(j_wr.end(), {r[7], rows, 1, rows, K, wr_b, ntile, nkt, round_up(rows, 16), 0});
     wr_b += b_bytes(rows, nkt, planes);
   }
@@ -86,7 +108,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
         if (r[8 + s2] < 0) continue;
         const int64_t rows = h->right[3 * r[8 + s2] + 2];
         const int64_t src = r[4] + (s1 ? r[7] : 0) * r[3] + (s2 ? r[10] : 0);
-        th_map[src] = {th_b, nkt};
+        th_map.add(src, {th_b, nkt});
         j_th.insert(j_th.end(), {src, r[3], 1, rows, K, th_b, ntile, nkt, round_up(rows, 16), 0});
         th_b += b_bytes(rows, nkt, planes);
       }
@@ -112,11 +134,15 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
         if (rin[8 + s2] < 0) continue;
         const int64_t K = h->right[3 * rin[8 + s2] + 2], nkt = (K + kpt - 1) / kpt;
         const int64_t key = zr[5] + (s1p ? rout[7] : 0) * rin[3] + (s2 ? rin[10] : 0);
-        z_map[key] = {z_b, nkt};
+        z_map.add(key, {z_b, nkt});
         z_b += a_bytes(rows, nkt, planes);
       }
     }
   }
+  lw_map.finish();
+  wr_map.finish();
+  th_map.finish();
+  z_map.finish();
   // step-1 tasks (Z = LW theta), one per (w', m_in, s1', s2) so that each writes one Z panel
   std::vector<int64_t> t1, s1, p1{0}, t2, s2, p2{0};
   for (int64_t i = 0; i < c[C_NT1]; ++i) {
@@ -130,15 +156,14 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
       const int64_t seg0 = (int64_t)s1.size() / TCS;
       for (int64_t k = 0; k < t[5]; ++k) {
         const int64_t* sg = &h->s1_host[SF * (t[4] + k)];
-        auto a = lw_map.find(sg[0]);
-        auto b = th_map.find(sg[2] + coff);
-        if (a == lw_map.end() || b == th_map.end() || a->second.nkt != b->second.nkt)
-          return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
-        s1.insert(s1.end(), {a->second.off, b->second.off, a->second.nkt, 0});
+        const Panel* a = lw_map.find(sg[0]);
+        const Panel* b = th_map.find(sg[2] + coff);
+        if (!a || !b || a->nkt != b->nkt) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
+        s1.insert(s1.end(), {a->off, b->off, a->nkt, 0});
       }
-      auto q = z_map.find(t[2] + coff);
-      if (q == z_map.end()) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
-      t1.insert(t1.end(), {t[0], N, q->second.off, 0, 0, seg0, t[5], 0, q->second.nkt, 0});
+      const Panel* q = z_map.find(t[2] + coff);
+      if (!q) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
+      t1.insert(t1.end(), {t[0], N, q->off, 0, 0, seg0, t[5], 0, q->nkt, 0});
       p1.push_back(p1.back() + ((t[0] + 127) / 128) * ((N + ntile - 1) / ntile));
     }
   }
@@ -149,11 +174,10 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     const int64_t seg0 = (int64_t)s2.size() / TCS;
     for (int64_t k = 0; k < t[5]; ++k) {
       const int64_t* sg = &h->s2_host[SF * (t[4] + k)];
-      auto a = z_map.find(sg[0]);
-      auto b = wr_map.find(sg[2]);
-      if (a == z_map.end() || b == wr_map.end() || a->second.nkt != b->second.nkt)
-        return mrd_fail(ctx, MRD_E_STATE, "tc: step-2 operand not packed");
-      s2.insert(s2.end(), {a->second.off, b->second.off, a->second.nkt, 0});
+      const Panel* a = z_map.find(sg[0]);
+      const Panel* b = wr_map.find(sg[2]);
+      if (!a || !b || a->nkt != b->nkt) return mrd_fail(ctx, MRD_E_STATE, "tc: step-2 operand not packed");
+      s2.insert(s2.end(), {a->off, b->off, a->nkt, 0});
     }
     t2.insert(t2.end(), {t[0], t[1], t[2], t[3], 0, seg0, t[5], 1, 0, 0});
     p2.push_back(p2.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
