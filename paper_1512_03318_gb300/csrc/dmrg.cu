@@ -339,8 +339,13 @@ struct mrd_dmrg {
 
 namespace {
 
+// Grouped GEMM C += sum over segments A . B on the context stream, FP64 or float-float
+// (D->gemm_ff). a_ff / b_ff: the operands already split into float-float (e.g. the H_eff's
+// own copies of LW / WR), used instead of converting Aop / Bop again. Asynchronous: the task
+// tables are copied from pageable host memory (consumed when the copy call returns) into
+// device buffers that later calls reuse in stream order.
 int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const double2* Bop, int64_t blen, double2* C,
-             int64_t clen) {
+             int64_t clen, const float4* a_ff = nullptr, const float4* b_ff = nullptr) {
   mrd_ctx* ctx = D->ctx;
   g.drop_empty_last();
   const int64_t nt = (int64_t)g.t.size() / TF;
@@ -372,18 +377,22 @@ int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const d
   if (D->gemm_ff) {
     // float-float: split each operand once (one pass over it) instead of on every tile load,
     // where the FP64 -> float conversions would run on the slow FP64 pipe; same results
-    MRD_CUDA(ctx, D->ff_a.need((size_t)std::max<int64_t>(alen, 1) * 16));
-    MRD_CUDA(ctx, D->ff_b.need((size_t)std::max<int64_t>(blen, 1) * 16));
-    MRD_CUDA(ctx, to_ff(Aop, D->ff_a.as<float4>(), alen, s));
-    MRD_CUDA(ctx, to_ff(Bop, D->ff_b.as<float4>(), blen, s));
-    MRD_CUDA(ctx, launch_cgemm_ff_packed(D->ff_a.as<float4>(), D->ff_b.as<float4>(), nullptr, C, D->gtask.as<int64_t>(),
-                                         D->gseg.as<int64_t>(), D->gpref.as<int64_t>(), nt, pref[nt], D->n_sm, s));
+    if (!a_ff) {
+      MRD_CUDA(ctx, D->ff_a.need((size_t)std::max<int64_t>(alen, 1) * 16));
+      MRD_CUDA(ctx, to_ff(Aop, D->ff_a.as<float4>(), alen, s));
+      a_ff = D->ff_a.as<float4>();
+    }
+    if (!b_ff) {
+      MRD_CUDA(ctx, D->ff_b.need((size_t)std::max<int64_t>(blen, 1) * 16));
+      MRD_CUDA(ctx, to_ff(Bop, D->ff_b.as<float4>(), blen, s));
+      b_ff = D->ff_b.as<float4>();
+    }
+    MRD_CUDA(ctx, launch_cgemm_ff_packed(a_ff, b_ff, nullptr, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(),
+                                         D->gpref.as<int64_t>(), nt, pref[nt], D->n_sm, s));
   } else {
     MRD_CUDA(ctx, launch_cgemm_fp64(Aop, Bop, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
                                     nt, pref[nt], D->n_sm, s));
   }
-  // the host task arrays must stay valid until the copies completed
-  MRD_CUDA(ctx, cudaStreamSynchronize(s));
   return MRD_OK;
 }
 
@@ -716,7 +725,8 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
       }
     }
   MRD_CUDA(ctx, D->tbuf.need((size_t)std::max<int64_t>(tlen, 1) * 16));
-  int rc = run_gemm(D, g1, h->lw, h->counts[C_LWLEN], A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen);
+  int rc = run_gemm(D, g1, h->lw, h->counts[C_LWLEN], A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen,
+                    heff_ff_lw(h));
   if (rc != MRD_OK) return rc;
   // step 2: L'(w', c) = sum_s' A(a', s' -> c')^+ T(w', c, s')
   EnvT& E = D->L[i + 1];
@@ -791,7 +801,8 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
       }
     }
   MRD_CUDA(ctx, D->tbuf.need((size_t)std::max<int64_t>(tlen, 1) * 16));
-  int rc = run_gemm(D, g1, B.data.as<double2>(), B.size, h->wr, h->counts[C_WRLEN], D->tbuf.as<double2>(), tlen);
+  int rc = run_gemm(D, g1, B.data.as<double2>(), B.size, h->wr, h->counts[C_WRLEN], D->tbuf.as<double2>(), tlen,
+                    nullptr, heff_ff_wr(h));
   if (rc != MRD_OK) return rc;
   EnvT& E = D->R[i + 1];
   E.sec = cs;

@@ -124,6 +124,11 @@ struct mrd_heff {
   }
 };
 
+// The H_eff's float-float copies of LW / WR when they are current (prepared by a float-float
+// application since the last environment load), else nullptr.
+inline const float4* heff_ff_lw(const mrd_heff* h) { return h->lw_ff && !h->ff_dirty ? h->lw_ff : nullptr; }
+inline const float4* heff_ff_wr(const mrd_heff* h) { return h->wr_ff && !h->ff_dirty ? h->wr_ff : nullptr; }
+
 inline cudaError_t record_event(cudaEvent_t e, cudaStream_t s, bool captured) {
   if (!e) return cudaSuccess;
   return captured ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
