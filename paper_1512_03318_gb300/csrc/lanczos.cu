@@ -185,12 +185,20 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot32(const float2* __rest
         }
       }
     }
+    // the warp reductions stay in FP32 (a warp's 32 partial sums hold ~400 elements' products;
+    // their rounding adds ~1e-10 |w| to a coefficient) and turn FP64 per warp, not per lane:
+    // FP64 shuffles and adds would cost 16 issue cycles per warp instruction on this part
 #pragma unroll
     for (int q = 0; q < kJB32; ++q) {
-      const double r = warp_sum((double)re[q]), m = warp_sum((double)im[q]);
+      float r = re[q], m = im[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+      }
       if ((threadIdx.x & 31) == 0) {
-        sre[q][threadIdx.x >> 5] = r;
-        sim[q][threadIdx.x >> 5] = m;
+        sre[q][threadIdx.x >> 5] = (double)r;
+        sim[q][threadIdx.x >> 5] = (double)m;
       }
     }
     __syncthreads();
@@ -375,18 +383,21 @@ __global__ void k_tridiag_lowest(LzState* st) {
   if (lane != 0) return;
   const double lam = 0.5 * (lo_s + hi_s);
   st->energy = lam;
-  // inverse iteration: (T - lam I) y = y_prev with a pivoted LU of the tridiagonal matrix
-  double d[MRD_LANCZOS_MAX_ITER + 1], du[MRD_LANCZOS_MAX_ITER + 1], du2[MRD_LANCZOS_MAX_ITER + 1];
-  double dl[MRD_LANCZOS_MAX_ITER + 1];
-  int piv[MRD_LANCZOS_MAX_ITER + 1];
-  double* y = st->y;
+  // inverse iteration: (T - lam I) y = y_prev with a pivoted LU of the tridiagonal matrix. One
+  // thread: the factors and y live in shared memory (not the thread's stack or global memory,
+  // whose latency the serial recurrences would pay on every access), and the k pivots are
+  // inverted once instead of dividing in each of the three solves
+  __shared__ double d[MRD_LANCZOS_MAX_ITER + 1], du[MRD_LANCZOS_MAX_ITER + 1], du2[MRD_LANCZOS_MAX_ITER + 1];
+  __shared__ double dl[MRD_LANCZOS_MAX_ITER + 1], y[MRD_LANCZOS_MAX_ITER + 1];
+  __shared__ int piv[MRD_LANCZOS_MAX_ITER + 1];
   const double shift = lam + 1e-14 * fmax(1.0, fabs(lam));
+  const double y0 = 1.0 / sqrt((double)k);
   for (int i = 0; i < k; ++i) {
-    d[i] = a[i] - shift;
+    d[i] = a_s[i] - shift;
     du[i] = i + 1 < k ? b[i] : 0.0;
-    dl[i] = i + 1 < k ? b[i] : 0.0;
+    dl[i] = du[i];
     du2[i] = 0.0;
-    y[i] = 1.0 / sqrt((double)k);
+    y[i] = y0;
   }
   for (int i = 0; i + 1 < k; ++i) {  // LU with partial pivoting (LAPACK gttrf layout)
     if (fabs(d[i]) >= fabs(dl[i])) {
@@ -411,6 +422,7 @@ __global__ void k_tridiag_lowest(LzState* st) {
   }
   piv[k - 1] = k - 1;
   const double tiny = 1e-300;
+  for (int i = 0; i < k; ++i) d[i] = 1.0 / (fabs(d[i]) > tiny ? d[i] : tiny);   // pivots, inverted
   for (int rep = 0; rep < 3; ++rep) {
     for (int i = 0; i + 1 < k; ++i) {  // forward: L
       if (piv[i] == i) {
@@ -425,18 +437,18 @@ __global__ void k_tridiag_lowest(LzState* st) {
       double v = y[i];
       if (i + 1 < k) v -= du[i] * y[i + 1];
       if (i + 2 < k) v -= du2[i] * y[i + 2];
-      y[i] = v / (fabs(d[i]) > tiny ? d[i] : tiny);
+      y[i] = v * d[i];
     }
-    double s = 0.0;
-    for (int i = 0; i < k; ++i) s += y[i] * y[i];
-    s = 1.0 / sqrt(s);
-    for (int i = 0; i < k; ++i) y[i] *= s;
+    double sq = 0.0;
+    for (int i = 0; i < k; ++i) sq += y[i] * y[i];
+    sq = 1.0 / sqrt(sq);
+    for (int i = 0; i < k; ++i) y[i] *= sq;
   }
   // fix the sign: first nonzero component positive (deterministic ground vector)
   double sg = 1.0;
   for (int i = 0; i < k; ++i)
     if (y[i] != 0.0) { sg = y[i] > 0 ? 1.0 : -1.0; break; }
-  for (int i = 0; i < k; ++i) y[i] *= sg;
+  for (int i = 0; i < k; ++i) st->y[i] = y[i] * sg;
 }
 
 }  // namespace
