@@ -805,6 +805,13 @@ int mrd_heff_table(const mrd_heff* h, int32_t which, int64_t* rows, int64_t* cou
 
 }  // extern "C"
 
+// Start the float-float conversion of LW / WR (asynchronous device work) ahead of a
+// float-float application, e.g. so that it runs while the host builds the tensor-core tables.
+int heff_prefetch_ff(mrd_heff* h) {
+  Guard g(h->ctx->device);
+  return heff_prepare(h, MRD_PREC_FF);
+}
+
 namespace mrd {
 
 // Read-only view of a handle for mrd_heff_apply_noalloc (heff_noalloc.cu).

@@ -1089,6 +1089,10 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   lap(1);
   double e = 0.0;
   int32_t it = 0;
+  // the float-float refinement's operand conversion runs on the device while the host builds
+  // the tensor-core tables of the Lanczos matvecs
+  const bool tc = p->prec == MRD_PREC_TF32 || p->prec == MRD_PREC_BF16X3;
+  if (tc && p->refine_iter > 0 && p->refine_prec == MRD_PREC_FF && (rc = heff_prefetch_ff(h)) != MRD_OK) return rc;
   if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e, &it)) != MRD_OK) return rc;
   D->last_iters = it;
   for (int r = 0; r < p->lanczos_restarts && it == p->lanczos_max_iter; ++r) {

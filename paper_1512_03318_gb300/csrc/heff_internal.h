@@ -18,6 +18,7 @@ int tc_config(const mrd_heff* h, int32_t* cfg4);
 int autotune(mrd_heff* h, int prec);
 void tc_env_changed(mrd_heff* h);
 int tc_status(mrd_heff* h);
+int heff_prefetch_ff(mrd_heff* h);
 using mrd::Lanczos;
 using mrd::lanczos_free;
 using mrd::PlanDims;

@@ -3,6 +3,7 @@
 // and the two grouped-GEMM launches.
 #include <algorithm>
 #include <map>
+#include <thread>
 #include <vector>
 
 #include "heff_internal.h"
@@ -143,8 +144,34 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   wr_map.finish();
   th_map.finish();
   z_map.finish();
-  // step-1 tasks (Z = LW theta), one per (w', m_in, s1', s2) so that each writes one Z panel
   std::vector<int64_t> t1, s1, p1{0}, t2, s2, p2{0};
+  // step-2 tasks (theta' = sum Z WR), built on a second host thread while this one builds the
+  // step-1 tasks: the two loops share only the finished (read-only) panel indexes
+  bool step2_ok = true;
+  std::thread step2([&] {
+    for (int64_t i = 0; i < c[C_NT2]; ++i) {
+      const int64_t* t = &h->t2_host[TF * i];
+      if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
+      const int64_t seg0 = (int64_t)s2.size() / TCS;
+      for (int64_t k = 0; k < t[5]; ++k) {
+        const int64_t* sg = &h->s2_host[SF * (t[4] + k)];
+        const Panel* a = z_map.find(sg[0]);
+        const Panel* b = wr_map.find(sg[2]);
+        if (!a || !b || a->nkt != b->nkt) {
+          step2_ok = false;
+          return;
+        }
+        s2.insert(s2.end(), {a->off, b->off, a->nkt, 0});
+      }
+      t2.insert(t2.end(), {t[0], t[1], t[2], t[3], 0, seg0, t[5], 1, 0, 0});
+      p2.push_back(p2.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
+    }
+  });
+  struct Join {
+    std::thread& t;
+    ~Join() { if (t.joinable()) t.join(); }
+  } join_step2{step2};
+  // step-1 tasks (Z = LW theta), one per (w', m_in, s1', s2) so that each writes one Z panel
   for (int64_t i = 0; i < c[C_NT1]; ++i) {
     const int64_t* t = &h->t1_host[TF * i];
     if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
@@ -167,21 +194,8 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
       p1.push_back(p1.back() + ((t[0] + 127) / 128) * ((N + ntile - 1) / ntile));
     }
   }
-  // step-2 tasks (theta' = sum Z WR)
-  for (int64_t i = 0; i < c[C_NT2]; ++i) {
-    const int64_t* t = &h->t2_host[TF * i];
-    if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
-    const int64_t seg0 = (int64_t)s2.size() / TCS;
-    for (int64_t k = 0; k < t[5]; ++k) {
-      const int64_t* sg = &h->s2_host[SF * (t[4] + k)];
-      const Panel* a = z_map.find(sg[0]);
-      const Panel* b = wr_map.find(sg[2]);
-      if (!a || !b || a->nkt != b->nkt) return mrd_fail(ctx, MRD_E_STATE, "tc: step-2 operand not packed");
-      s2.insert(s2.end(), {a->off, b->off, a->nkt, 0});
-    }
-    t2.insert(t2.end(), {t[0], t[1], t[2], t[3], 0, seg0, t[5], 1, 0, 0});
-    p2.push_back(p2.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
-  }
+  step2.join();
+  if (!step2_ok) return mrd_fail(ctx, MRD_E_STATE, "tc: step-2 operand not packed");
   // block schedule: tiles are dealt to the persistent CTAs in task order; order 1 puts the
   // tasks with the most work (tiles x K tiles) first so that the long ones start early
   if (cfg.order == 1) {
