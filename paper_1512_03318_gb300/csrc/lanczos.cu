@@ -148,7 +148,8 @@ __global__ void k_sub_combination(const double2* __restrict__ V, int64_t ldv, in
 // (semi-orthogonality) level that keeps the Ritz values exact to working precision. FP32
 // halves the bytes and moves the products off the FP64 pipe (2 operations per clock per SM),
 // which bounds the FP64 pass at ~2.5 TB/s.
-constexpr int kJB32 = 8;   // vectors per pass of k_multidot32
+constexpr int kMD32Chunk = 1024;   // elements of w per CTA of k_multidot32
+inline int64_t md32_blocks(int64_t n) { return n > 0 ? (n + kMD32Chunk - 1) / kMD32Chunk : 1; }
 
 __global__ void k_to_f32(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -157,61 +158,47 @@ __global__ void k_to_f32(const double2* __restrict__ x, float2* __restrict__ y, 
   }
 }
 
-// partial[b * nv + j] = sum over this CTA's share of conj(V32_j) . w32, j <= st->j: FP32
-// products and per-thread sums, FP64 from the warp reduction on (layout of k_multidot)
-__global__ void __launch_bounds__(kRedThreads) k_multidot32(const float2* __restrict__ V32, int64_t ldv,
-                                                            const LzState* __restrict__ st,
-                                                            const float2* __restrict__ w32, int64_t n,
-                                                            double2* __restrict__ partial) {
-  __shared__ double sre[kJB32][kRedThreads / 32], sim[kJB32][kRedThreads / 32];
+// partial[b * nv + j] = conj(V32_j) . w32 over the b-th chunk of kMD32Chunk elements, j <= st->j:
+// a skinny GEMV. The CTA stages its chunk of w32 in shared memory; its warps take the basis
+// vectors in turn and stream that chunk of each with 8 independent loads per lane. Products
+// and sums in FP32 (a warp's sum covers one chunk), stored as FP64 for the cross-chunk sum.
+__global__ void __launch_bounds__(256) k_multidot32(const float2* __restrict__ V32, int64_t ldv,
+                                                    const LzState* __restrict__ st,
+                                                    const float2* __restrict__ w32, int64_t n,
+                                                    double2* __restrict__ partial) {
+  __shared__ float2 ws[kMD32Chunk];
   const int nv = st->j + 1;
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t b = blockIdx.x * chunk;
-  const int64_t e = b + chunk < n ? b + chunk : n;
-  for (int j0 = 0; j0 < nv; j0 += kJB32) {
-    float re[kJB32], im[kJB32];
+  const int64_t b0 = (int64_t)blockIdx.x * kMD32Chunk;
+  const int len = n - b0 < kMD32Chunk ? (int)(n - b0) : kMD32Chunk;
+  for (int t = threadIdx.x; t < kMD32Chunk; t += blockDim.x) ws[t] = t < len ? w32[b0 + t] : make_float2(0.f, 0.f);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  constexpr int kU = 8;
+  for (int q = warp; q < nv; q += nwarp) {
+    const float2* v = V32 + (int64_t)q * ldv + b0;
+    float re = 0.f, im = 0.f;
+    for (int t0 = lane; t0 < len; t0 += 32 * kU) {
+      float2 x[kU];
 #pragma unroll
-    for (int q = 0; q < kJB32; ++q) re[q] = im[q] = 0.f;
-    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-      const float2 y = w32[i];
+      for (int u = 0; u < kU; ++u) {
+        const int t = t0 + 32 * u;
+        x[u] = t < len ? v[t] : make_float2(0.f, 0.f);
+      }
 #pragma unroll
-      for (int q = 0; q < kJB32; ++q) {
-        if (j0 + q < nv) {
-          const float2 x = V32[(int64_t)(j0 + q) * ldv + i];
-          re[q] = __fmaf_rn(x.x, y.x, re[q]);
-          re[q] = __fmaf_rn(x.y, y.y, re[q]);
-          im[q] = __fmaf_rn(x.x, y.y, im[q]);
-          im[q] = __fmaf_rn(-x.y, y.x, im[q]);
-        }
+      for (int u = 0; u < kU; ++u) {
+        const float2 y = ws[t0 + 32 * u < kMD32Chunk ? t0 + 32 * u : 0];
+        re = __fmaf_rn(x[u].x, y.x, re);
+        re = __fmaf_rn(x[u].y, y.y, re);
+        im = __fmaf_rn(x[u].x, y.y, im);
+        im = __fmaf_rn(-x[u].y, y.x, im);
       }
     }
-    // the warp reductions stay in FP32 (a warp's 32 partial sums hold ~400 elements' products;
-    // their rounding adds ~1e-10 |w| to a coefficient) and turn FP64 per warp, not per lane:
-    // FP64 shuffles and adds would cost 16 issue cycles per warp instruction on this part
 #pragma unroll
-    for (int q = 0; q < kJB32; ++q) {
-      float r = re[q], m = im[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        r += __shfl_xor_sync(0xffffffffu, r, o);
-        m += __shfl_xor_sync(0xffffffffu, m, o);
-      }
-      if ((threadIdx.x & 31) == 0) {
-        sre[q][threadIdx.x >> 5] = (double)r;
-        sim[q][threadIdx.x >> 5] = (double)m;
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    __syncthreads();
-    if (threadIdx.x < kJB32 && j0 + (int)threadIdx.x < nv) {
-      const int q = threadIdx.x;
-      double a = 0.0, c = 0.0;
-      for (int k = 0; k < kRedThreads / 32; ++k) {
-        a += sre[q][k];
-        c += sim[q][k];
-      }
-      partial[(int64_t)blockIdx.x * nv + j0 + q] = make_double2(a, c);
-    }
-    __syncthreads();
+    if (lane == 0) partial[(int64_t)blockIdx.x * nv + q] = make_double2((double)re, (double)im);
   }
 }
 
@@ -219,18 +206,26 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot32(const float2* __rest
 // FP32 once per CTA) and subtracted from the FP64 vector
 __global__ void k_sub_combination32(const float2* __restrict__ V32, int64_t ldv, const LzState* __restrict__ st,
                                     const double2* __restrict__ c, double2* __restrict__ w, int64_t n) {
-  __shared__ float2 cs[MRD_LANCZOS_MAX_ITER + 1];
+  constexpr int kU = 8;   // basis vectors per step of the loop: 8 independent loads in flight
+  __shared__ float2 cs[MRD_LANCZOS_MAX_ITER + 1 + kU];
   const int nv = st->j + 1;
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = make_float2(__double2float_rn(c[j].x), __double2float_rn(c[j].y));
+  for (int j = threadIdx.x; j < nv + kU; j += blockDim.x)
+    cs[j] = j < nv ? make_float2(__double2float_rn(c[j].x), __double2float_rn(c[j].y)) : make_float2(0.f, 0.f);
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float ax = 0.f, ay = 0.f;
-    for (int j = 0; j < nv; ++j) {
-      const float2 v = V32[(int64_t)j * ldv + i], cj = cs[j];
-      ax = __fmaf_rn(cj.x, v.x, ax);
-      ax = __fmaf_rn(-cj.y, v.y, ax);
-      ay = __fmaf_rn(cj.x, v.y, ay);
-      ay = __fmaf_rn(cj.y, v.x, ay);
+    for (int j0 = 0; j0 < nv; j0 += kU) {
+      float2 v[kU];
+#pragma unroll
+      for (int q = 0; q < kU; ++q) v[q] = j0 + q < nv ? V32[(int64_t)(j0 + q) * ldv + i] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const float2 cj = cs[j0 + q];
+        ax = __fmaf_rn(cj.x, v[q].x, ax);
+        ax = __fmaf_rn(-cj.y, v[q].y, ax);
+        ay = __fmaf_rn(cj.x, v[q].y, ay);
+        ay = __fmaf_rn(cj.y, v[q].x, ay);
+      }
     }
     double2 o = w[i];
     o.x -= (double)ax;
@@ -311,26 +306,29 @@ __global__ void k_scale_next(const double2* __restrict__ w, double2* __restrict_
 // p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2} (b2 holds the squares). It needs no division:
 // three FP64 operations per row, where the pivot-ratio form q_i = p_i / p_{i-1} divides once
 // per row, and FP64 division is a long instruction sequence on a part with 2 FP64 operations
-// per clock per SM. Both minors are rescaled by 2^-+600 when p_i leaves [2^-600, 2^600]; their
-// ratio (a pivot) stays within 2^+-200, so neither leaves the FP64 range. A zero minor is
-// replaced by 2^-200 times the one before, the same as a tiny positive pivot.
+// per clock per SM. A zero minor is replaced by 2^-50 times the one before (a tiny positive
+// pivot). A row then changes the minors' scale by at most ~2^50 (the guard) and otherwise by
+// |a_i - x| + b_{i-1}^2, so every 8 rows both are rescaled by 2^-+500 when p_i has left
+// [2^-500, 2^500], and neither leaves the FP64 range in between.
 __device__ int sturm_count(const double* a, const double* b2, int k, double x) {
   double pm = 1.0, p = a[0] - x;
-  if (p == 0.0) p = 0x1p-200;
+  if (p == 0.0) p = 0x1p-50;
   int cnt = p < 0.0;
   for (int i = 1; i < k; ++i) {
     double pn = fma(a[i] - x, p, -b2[i - 1] * pm);
-    if (pn == 0.0) pn = p * 0x1p-200;
+    if (pn == 0.0) pn = p * 0x1p-50;
     cnt += (pn < 0.0) != (p < 0.0);
     pm = p;
     p = pn;
-    const double m = fabs(p);
-    if (m > 0x1p600) {
-      p *= 0x1p-600;
-      pm *= 0x1p-600;
-    } else if (m < 0x1p-600) {
-      p *= 0x1p600;
-      pm *= 0x1p600;
+    if ((i & 7) == 0) {
+      const double m = fabs(p);
+      if (m > 0x1p500) {
+        p *= 0x1p-500;
+        pm *= 0x1p-500;
+      } else if (m < 0x1p-500) {
+        p *= 0x1p500;
+        pm *= 0x1p500;
+      }
     }
   }
   return cnt;
@@ -362,9 +360,13 @@ __global__ void k_tridiag_lowest(LzState* st) {
     hi_s = hi + pad;
   }
   __syncwarp();
+  // multisection to 1e-14 relative width (the Ritz value is compared to 1e-10 and refined
+  // afterwards), or until a subdivision no longer shrinks the interval in FP64
+  double prev_w = 0.0;
   for (int it = 0; it < 40; ++it) {
     const double lo = lo_s, hi = hi_s;
-    if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
+    if (!(hi - lo > 1e-14 * fmax(fabs(lo), fabs(hi))) || hi - lo == prev_w) break;
+    prev_w = hi - lo;
     const double x = lo + (hi - lo) * (lane + 1) / 33.0;
     const int c = sturm_count(a_s, b2_s, k, x);
     const unsigned m = __ballot_sync(0xffffffffu, c >= 1);
@@ -459,6 +461,7 @@ struct Lanczos {
   double2* w = nullptr;
   double2* vin = nullptr;      // v_j staged for the operator (fixed address: graph-capturable)
   double2* partial = nullptr;  // kRedBlocks * (MRD_LANCZOS_MAX_ITER + 1)
+  double2* partial32 = nullptr;   // md32_blocks(n) * (MRD_LANCZOS_MAX_ITER + 1), FP32 full pass
   double2* c1 = nullptr;
   double2* c2 = nullptr;
   double2* scal = nullptr;
@@ -478,7 +481,7 @@ struct Lanczos {
 void lanczos_free(Lanczos* L) {
   if (!L) return;
   for (void* p : {(void*)L->V, (void*)L->w, (void*)L->vin, (void*)L->partial, (void*)L->c1, (void*)L->c2,
-                  (void*)L->scal, (void*)L->st, (void*)L->V32, (void*)L->w32})
+                  (void*)L->scal, (void*)L->st, (void*)L->V32, (void*)L->w32, (void*)L->partial32})
     cache_free(p, L->stream);
   if (L->st_host) cache_free_host(L->st_host);
   if (L->step_exec) cudaGraphExecDestroy(L->step_exec);
@@ -516,9 +519,13 @@ cudaError_t lanczos_set_fp32_full(Lanczos* L, bool on) {
     const size_t n = (size_t)(L->n > 0 ? L->n : 1);
     cudaError_t e = cache_alloc((void**)&L->V32, (size_t)(MRD_LANCZOS_MAX_ITER + 1) * n * 8, L->stream);
     if (e == cudaSuccess) e = cache_alloc((void**)&L->w32, n * 8, L->stream);
+    if (e == cudaSuccess)
+      e = cache_alloc((void**)&L->partial32, (size_t)md32_blocks(L->n) * (MRD_LANCZOS_MAX_ITER + 1) * 16, L->stream);
     if (e != cudaSuccess) {
-      cache_free(L->V32, L->stream);
-      L->V32 = nullptr;
+      for (void** q : {(void**)&L->V32, (void**)&L->w32, (void**)&L->partial32}) {
+        cache_free(*q, L->stream);
+        *q = nullptr;
+      }
       L->fp32_full = false;
       return e;
     }
@@ -559,8 +566,9 @@ static int lanczos_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const doub
   mrd::count_launch();
   if (L->fp32_full) {
     k_to_f32<<<grid_for(n), 256, 0, s>>>(L->w, L->w32, n);
-    k_multidot32<<<kRedBlocks, kRedThreads, 0, s>>>(L->V32, n, L->st, L->w32, n, L->partial);
-    k_finish_dots<<<(MRD_LANCZOS_MAX_ITER + 1 + 3) / 4, 128, 0, s>>>(L->partial, kRedBlocks, -1, L->st, L->c2);
+    k_multidot32<<<(unsigned)md32_blocks(n), 256, 0, s>>>(L->V32, n, L->st, L->w32, n, L->partial32);
+    k_finish_dots<<<(MRD_LANCZOS_MAX_ITER + 1 + 3) / 4, 128, 0, s>>>(L->partial32, (int)md32_blocks(n), -1, L->st,
+                                                                      L->c2);
     k_sub_combination32<<<grid_for(n), 256, 0, s>>>(L->V32, n, L->st, L->c2, L->w, n);
     mrd::count_launches(4);
   } else {
