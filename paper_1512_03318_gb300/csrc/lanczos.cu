@@ -65,20 +65,34 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double2* __restr
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b = blockIdx.x * chunk;
   const int64_t e = b + chunk < n ? b + chunk : n;
+  constexpr int kE = 4;   // elements per thread and step: their loads are in flight together
   for (int j0 = 0; j0 < nv; j0 += kJB) {
     double re[kJB], im[kJB];
 #pragma unroll
     for (int q = 0; q < kJB; ++q) re[q] = im[q] = 0.0;
-    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-      const double2 y = w[i];
+    for (int64_t i0 = b + threadIdx.x; i0 < e; i0 += (int64_t)kE * blockDim.x) {
+      double2 y[kE];
+#pragma unroll
+      for (int u = 0; u < kE; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        y[u] = i < e ? w[i] : make_double2(0.0, 0.0);
+      }
 #pragma unroll
       for (int q = 0; q < kJB; ++q) {
         if (j0 + q < nv) {
-          const double2 x = V[(int64_t)(j0 + q) * ldv + i];
-          re[q] = fma(x.x, y.x, re[q]);
-          re[q] = fma(x.y, y.y, re[q]);
-          im[q] = fma(x.x, y.y, im[q]);
-          im[q] = fma(-x.y, y.x, im[q]);
+          double2 x[kE];
+#pragma unroll
+          for (int u = 0; u < kE; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            x[u] = i < e ? V[(int64_t)(j0 + q) * ldv + i] : make_double2(0.0, 0.0);
+          }
+#pragma unroll
+          for (int u = 0; u < kE; ++u) {
+            re[q] = fma(x[u].x, y[u].x, re[q]);
+            re[q] = fma(x[u].y, y[u].y, re[q]);
+            im[q] = fma(x[u].x, y[u].y, im[q]);
+            im[q] = fma(-x[u].y, y[u].x, im[q]);
+          }
         }
       }
     }
@@ -544,9 +558,11 @@ static cudaError_t dots(Lanczos* L, const double2* V, int nv, const double2* w, 
   return cudaGetLastError();
 }
 
+// Grid of the elementwise kernels (256 threads): one element per thread up to ~1M elements,
+// so that every thread's loads are issued at once instead of one grid-stride step at a time.
 static unsigned grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
-  return (unsigned)(g < 1216 ? (g > 0 ? g : 1) : 1216);
+  return (unsigned)(g < 4096 ? (g > 0 ? g : 1) : 4096);
 }
 
 // One Lanczos step j (j in the device state) on the context stream, ending with the copy of
