@@ -38,8 +38,10 @@ struct LzState {
   double alpha[MRD_LANCZOS_MAX_ITER + 1];
   double beta[MRD_LANCZOS_MAX_ITER + 1];
   double y[MRD_LANCZOS_MAX_ITER + 1];
+  double ritz[MRD_LANCZOS_MAX_ITER + 1];   // lowest Ritz value after each step of the run
   double energy;
   double beta_last;
+  double inv_beta;                         // 1 / beta_j of the current step
   int flags;
   int j;
 };
@@ -266,7 +268,10 @@ __global__ void k_combination_real(const double2* __restrict__ V, int64_t ldv, i
 // (and its FP32 copy into dst32 when given)
 __global__ void k_scale_by_invnorm(const double2* __restrict__ src, double2* __restrict__ dst, int64_t n,
                                    const double2* __restrict__ nrm2, float2* __restrict__ dst32) {
-  const double s = nrm2->x > 0.0 ? 1.0 / sqrt(nrm2->x) : 0.0;
+  __shared__ double s_sh;   // one FP64 square root and division per CTA, not per thread
+  if (threadIdx.x == 0) s_sh = nrm2->x > 0.0 ? 1.0 / sqrt(nrm2->x) : 0.0;
+  __syncthreads();
+  const double s = s_sh;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = src[i];
     const double2 o = make_double2(v.x * s, v.y * s);
@@ -287,6 +292,7 @@ __global__ void k_record_beta(LzState* st, const double2* __restrict__ nrm2) {
   const int j = st->j;
   st->beta[j] = sqrt(nrm2->x);
   st->beta_last = st->beta[j];
+  st->inv_beta = nrm2->x > 0.0 ? 1.0 / st->beta[j] : 0.0;
 }
 
 __global__ void k_set_step(LzState* st, int j) { st->j = j; }
@@ -302,9 +308,8 @@ __global__ void k_copy_vj(const double2* __restrict__ V, int64_t n, const LzStat
 
 // v_{j+1} = w / |w|
 __global__ void k_scale_next(const double2* __restrict__ w, double2* __restrict__ V, int64_t n,
-                             const double2* __restrict__ nrm2, const LzState* __restrict__ st,
-                             float2* __restrict__ V32) {
-  const double sc = nrm2->x > 0.0 ? 1.0 / sqrt(nrm2->x) : 0.0;
+                             const LzState* __restrict__ st, float2* __restrict__ V32) {
+  const double sc = st->inv_beta;   // formed once by k_record_beta
   double2* dst = V + (int64_t)(st->j + 1) * n;
   float2* dst32 = V32 ? V32 + (int64_t)(st->j + 1) * n : nullptr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -360,6 +365,7 @@ __global__ void k_tridiag_lowest(LzState* st) {
     a_s[i] = a[i];
     b2_s[i] = b[i] * b[i];
   }
+  __syncwarp();
   if (lane == 0) {
     // the lowest eigenvalue lies between the lowest Gershgorin bound and the smallest
     // diagonal element (a Rayleigh quotient of a unit vector)
@@ -370,8 +376,23 @@ __global__ void k_tridiag_lowest(LzState* st) {
       hi = fmin(hi, a[i]);
     }
     double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
-    lo_s = lo - pad;
-    hi_s = hi + pad;
+    lo -= pad;
+    hi += pad;
+    // warm start: by interlacing the lowest eigenvalue of T_k is at most that of T_{k-1};
+    // late in a run it moves little, so try [E_{k-1} - 4|E_{k-1} - E_{k-2}|, E_{k-1}], padded,
+    // and keep it where Sturm counts confirm it (no eigenvalue below, at least one below the
+    // top); otherwise the Gershgorin bracket
+    if (k >= 3) {
+      const double e1 = st->ritz[k - 2], e2 = st->ritz[k - 3];
+      const double tol = 1e-13 * fmax(fabs(e1), 1.0);
+      const double wlo = e1 - 4.0 * fabs(e1 - e2) - tol, whi = e1 + tol;
+      if (wlo > lo && whi < hi && sturm_count(a_s, b2_s, k, wlo) == 0 && sturm_count(a_s, b2_s, k, whi) >= 1) {
+        lo = wlo;
+        hi = whi;
+      }
+    }
+    lo_s = lo;
+    hi_s = hi;
   }
   __syncwarp();
   // multisection to 1e-14 relative width (the Ritz value is compared to 1e-10 and refined
@@ -399,6 +420,7 @@ __global__ void k_tridiag_lowest(LzState* st) {
   if (lane != 0) return;
   const double lam = 0.5 * (lo_s + hi_s);
   st->energy = lam;
+  st->ritz[k - 1] = lam;
   // inverse iteration: (T - lam I) y = y_prev with a pivoted LU of the tridiagonal matrix. One
   // thread: the factors and y live in shared memory (not the thread's stack or global memory,
   // whose latency the serial recurrences would pay on every access), and the k pivots are
@@ -599,7 +621,7 @@ static int lanczos_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const doub
   mrd::count_launch();
   k_tridiag_lowest<<<1, 32, 0, s>>>(L->st);
   mrd::count_launch();
-  k_scale_next<<<grid_for(n), 256, 0, s>>>(L->w, L->V, n, L->scal, L->st, L->fp32_full ? L->V32 : nullptr);
+  k_scale_next<<<grid_for(n), 256, 0, s>>>(L->w, L->V, n, L->st, L->fp32_full ? L->V32 : nullptr);
   mrd::count_launch();
   k_next_step<<<1, 1, 0, s>>>(L->st);
   mrd::count_launch();
