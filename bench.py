@@ -556,7 +556,7 @@ def main():
         ach = instr / (svd_work[0] / 1e3) / 1e12
         roof = {"kernel": "k_svd_bround<float-float> (block-cyclic Jacobi rounds)", "bound": "alu", "achieved": ach,
                 "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
-                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived, DESIGN.md)",
+                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived from unit counts and the maximum SM clock)",
                 "ms_per_step": svd_work[0] / args.steps, "share_of_measured_kernels": svd_ms / sum(shares.values())}
     elif dominant.startswith("k_tc_gemm"):
         per = tc_ms / max(kn[0], 1) / 1e3
@@ -569,7 +569,7 @@ def main():
         ach = f_exec / 8 * FF_INSTR_PER_CMAC / per / 1e12
         roof = {"kernel": "k_cgemm_ff (float-float refinement matvec, steps 1+2)", "bound": "alu", "achieved": ach,
                 "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
-                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived, DESIGN.md)",
+                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived from unit counts and the maximum SM clock)",
                 "ms_per_step": hp_ms / args.steps, "share_of_measured_kernels": hp_ms / sum(shares.values())}
     tc = mv["bf16x3"]
     tc_hw = 3 * f_exec / (tc["ms"] / 1e3) / 1e12
