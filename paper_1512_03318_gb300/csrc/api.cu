@@ -15,7 +15,8 @@ namespace mrd {
 cudaError_t launch_plan(const PlanDims& d, const PlanPtrs& p, cudaStream_t s);
 cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
                                    const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
-                                   int n_sm, cudaStream_t s);
+                                   int n_sm, cudaStream_t s, const int2* items = nullptr);
+std::vector<int2> ff_item_order(const int64_t* tasks, const int64_t* segs, int64_t n_tasks);
 cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
                               const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
@@ -470,6 +471,21 @@ static int heff_prepare(mrd_heff* h, int32_t prec) {
     MRD_CUDA(ctx, to_ff(h->wr, h->wr_ff, h->counts[C_WRLEN], s));
     h->ff_dirty = false;
   }
+  // launch order of the grouped float-float steps (longest K first), once per H_eff; kept
+  // only if its tiles add up to the device-built tile prefix
+  if (!h->ff_items_built) {
+    h->ff_items_built = true;
+    const std::vector<int2> i1 = ff_item_order(h->t1_host.data(), h->s1_host.data(), h->counts[C_NT1]);
+    const std::vector<int2> i2 = ff_item_order(h->t2_host.data(), h->s2_host.data(), h->counts[C_NT2]);
+    if ((int64_t)i1.size() == h->counts[C_TILES1] && (int64_t)i2.size() == h->counts[C_TILES2]) {
+      Arena& A = h->ff_mem;
+      cudaError_t e = A.alloc(&h->ff_it1, std::max<size_t>(i1.size(), 1));
+      if (e == cudaSuccess) e = A.alloc(&h->ff_it2, std::max<size_t>(i2.size(), 1));
+      if (e == cudaSuccess && !i1.empty()) e = cudaMemcpyAsync(h->ff_it1, i1.data(), i1.size() * 8, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && !i2.empty()) e = cudaMemcpyAsync(h->ff_it2, i2.data(), i2.size() * 8, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply: float-float item tables");
+    }
+  }
   return MRD_OK;
 }
 
@@ -501,11 +517,11 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
     if (!h->per_task) {
       if (e == cudaSuccess)
         e = launch_cgemm_ff_packed(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1, h->p.seg1, h->p.tile1,
-                                   h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s);
+                                   h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s, h->ff_it1);
       if (e == cudaSuccess && e1) e = record_event(e1, s, cap);
       if (e == cudaSuccess)
         e = launch_cgemm_ff_packed(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
-                                   h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s);
+                                   h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s, h->ff_it2);
     } else {
       for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT1]; ++t)
         if (h->pt_tiles1[t])

@@ -27,7 +27,8 @@ namespace mrd {
 
 cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
                                    const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
-                                   int n_sm, cudaStream_t s);
+                                   int n_sm, cudaStream_t s, const int2* items = nullptr);
+std::vector<int2> ff_item_order(const int64_t* tasks, const int64_t* segs, int64_t n_tasks);
 cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
                               const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
@@ -314,7 +315,7 @@ struct mrd_dmrg {
   int target_N = 0, target_K = 0;
   std::vector<SiteT> A;
   std::vector<EnvT> L, R;
-  Buf gtask, gseg, gpref, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
+  Buf gtask, gseg, gpref, gitems, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
       svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, svd_last, svd_ctr, tbuf,
       zeros;
   cudaEvent_t svd_ev[2] = {nullptr, nullptr};
@@ -387,8 +388,16 @@ int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const d
       MRD_CUDA(ctx, to_ff(Bop, D->ff_b.as<float4>(), blen, s));
       b_ff = D->ff_b.as<float4>();
     }
+    // tiles in launch order, longest K first (the tile prefix above uses the same 32 x 32 tiles)
+    const std::vector<int2> items = ff_item_order(g.t.data(), g.s.data(), nt);
+    const int2* it = nullptr;
+    if ((int64_t)items.size() == pref[nt] && !items.empty()) {
+      MRD_CUDA(ctx, D->gitems.need(items.size() * 8));
+      MRD_CUDA(ctx, cudaMemcpyAsync(D->gitems.p, items.data(), items.size() * 8, cudaMemcpyHostToDevice, s));
+      it = D->gitems.as<int2>();
+    }
     MRD_CUDA(ctx, launch_cgemm_ff_packed(a_ff, b_ff, nullptr, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(),
-                                         D->gpref.as<int64_t>(), nt, pref[nt], D->n_sm, s));
+                                         D->gpref.as<int64_t>(), nt, pref[nt], D->n_sm, s, it));
   } else {
     MRD_CUDA(ctx, launch_cgemm_fp64(Aop, Bop, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
                                     nt, pref[nt], D->n_sm, s));

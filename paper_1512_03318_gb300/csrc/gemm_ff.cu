@@ -8,6 +8,9 @@
 // terms, so the result carries ~1e-13 relative error (dot products of up to ~10^4 terms)
 // against ~1e-16 for FP64, at several times the FP64 rate of GB300. Each output block is
 // owned by one task, as in FP64: no atomics, deterministic results.
+#include <algorithm>
+#include <vector>
+
 #include "ff.cuh"
 #include "mrd_internal.h"
 #include "plan.cuh"
@@ -95,11 +98,15 @@ __device__ __forceinline__ FFAcc ff_renorm(FFAcc a) {
 
 }  // namespace
 
+// items (optional): (task, tile within task) of every tile in launch order, longest K first
+// (ff_item_order), so that no long tile starts at the end of the grid; without it tiles run in
+// task order and the task is found by binary search over the tile prefix.
 template <class TA, class TB, class TC>
 __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, const TB* __restrict__ B,
                                                   TC* __restrict__ C, const int64_t* __restrict__ tasks,
                                                   const int64_t* __restrict__ segs,
-                                                  const int64_t* __restrict__ prefix, int64_t n_tasks) {
+                                                  const int64_t* __restrict__ prefix, int64_t n_tasks,
+                                                  const int2* __restrict__ items) {
   __shared__ float4 As[kT][kK + 1];
   __shared__ float4 Bs[kK][kT + 1];
   __shared__ float2 Ass[kT][kK + 1];   // a_r + a_i
@@ -108,12 +115,19 @@ __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, c
   const int warp = tid >> 5, lane = tid & 31;
   const int64_t total = prefix[n_tasks];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
-    const int64_t t = find_task_ff(prefix, n_tasks, item);
+    int64_t t, local;
+    if (items) {
+      const int2 it = items[item];
+      t = it.x;
+      local = it.y;
+    } else {
+      t = find_task_ff(prefix, n_tasks, item);
+      local = item - prefix[t];
+    }
     const int64_t* task = tasks + TF * t;
     const int64_t M = task[0], N = task[1], c_off = task[2], ldc = task[3];
     const int64_t seg0 = task[4], nseg = task[5];
     const int64_t tiles_n = (N + kT - 1) / kT;
-    const int64_t local = item - prefix[t];
     const int64_t m0 = (local / tiles_n) * kT, n0 = (local % tiles_n) * kT;
     // Each thread owns 2 x 2 outputs, each warp a 4 x 32 strip of the tile. The strips run
     // along the tile's shorter valid side, so that a warp whose strip lies wholly in the
@@ -209,26 +223,49 @@ __global__ void k_to_ff(const double2* __restrict__ x, float4* __restrict__ y, i
 
 template <class TA, class TB, class TC>
 static cudaError_t launch_ff(const TA* A, const TB* B, TC* C, const int64_t* tasks, const int64_t* segs,
-                             const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
+                             const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s,
+                             const int2* items) {
   if (total_tiles <= 0) return cudaSuccess;
   int64_t grid = (int64_t)n_sm * 8;
   if (grid > total_tiles) grid = total_tiles;
-  k_cgemm_ff<TA, TB, TC><<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks);
+  k_cgemm_ff<TA, TB, TC><<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks, items);
   mrd::count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
                             const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
-  return launch_ff(A, B, C, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s);
+  return launch_ff(A, B, C, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s, nullptr);
 }
 
 // operands already in float-float layout; result in float-float (c_ff) or FP64 (c64)
 cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
                                    const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
-                                   int n_sm, cudaStream_t s) {
-  if (c_ff) return launch_ff(A, B, c_ff, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s);
-  return launch_ff(A, B, c64, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s);
+                                   int n_sm, cudaStream_t s, const int2* items) {
+  if (c_ff) return launch_ff(A, B, c_ff, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s, items);
+  return launch_ff(A, B, c64, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s, items);
+}
+
+// Launch order of the tiles of a grouped GEMM (host): (task, tile within task) for every tile
+// of 32 x 32 outputs, tasks in decreasing order of their inner dimension (the sum of their
+// segments' K, which sets the time of each of their tiles), ties in task order.
+std::vector<int2> ff_item_order(const int64_t* tasks, const int64_t* segs, int64_t n_tasks) {
+  std::vector<int64_t> cost(n_tasks), idx(n_tasks);
+  for (int64_t t = 0; t < n_tasks; ++t) {
+    const int64_t* r = tasks + TF * t;
+    int64_t k = 0;
+    for (int64_t q = 0; q < r[5]; ++q) k += segs[SF * (r[4] + q) + 4];
+    cost[t] = k;
+    idx[t] = t;
+  }
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+  std::vector<int2> items;
+  for (int64_t t : idx) {
+    const int64_t* r = tasks + TF * t;
+    const int64_t n = ((r[0] + kT - 1) / kT) * ((r[1] + kT - 1) / kT);
+    for (int64_t l = 0; l < n; ++l) items.push_back(make_int2((int)t, (int)l));
+  }
+  return items;
 }
 
 cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s) {

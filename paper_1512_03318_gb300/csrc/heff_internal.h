@@ -104,6 +104,8 @@ struct mrd_heff {
   // theta staging
   Arena ff_mem;
   float4 *lw_ff = nullptr, *wr_ff = nullptr, *th_ff = nullptr;
+  int2 *ff_it1 = nullptr, *ff_it2 = nullptr;   // launch order of the float-float steps (longest K first)
+  bool ff_items_built = false;
   bool ff_dirty = true;
   uint64_t gen = 1;          // bumped when apply buffers are reallocated (captured graphs go stale)
   bool use_graph = true;     // capture Lanczos steps as CUDA graphs (MRD_OPT_GRAPH)
