@@ -197,8 +197,7 @@ def cpu_baseline(n_steps=3):
 def run_reference(args):
     """The reference arm: the CPU oracle, timed on the host cores on bounded samples of the
     update workload, in the bench's own metric (s/update, lower is better)."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if rank_env()[0] != 0:   # under torchrun rank 0 alone runs the reference arm
         return 0
     step, flops, full = oracle_step_factory()
     for _ in range(args.warmup):
@@ -354,6 +353,39 @@ def mpo_diagnostics(P):
     return out
 
 
+# ---------------------------------------------------------------- replicas (N > 1)
+
+def rank_env(env=None):
+    """(rank, world size, local rank) of this process, from the torchrun environment."""
+    env = os.environ if env is None else env
+    return int(env.get("RANK", "0")), int(env.get("WORLD_SIZE", "1")), int(env.get("LOCAL_RANK", "0"))
+
+
+def replica_seed(rank):
+    """Each replica runs its own seeded problem (no data-path collective)."""
+    return 11 + rank
+
+
+def ranks_barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def ranks_max(x, dist, device):
+    """The largest of the ranks' values of x (every rank gets it); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_update_value(seconds, steps, world):
+    """Whole-job seconds per update: the slowest rank's time over all ranks' updates."""
+    return seconds / steps / world
+
+
 def make_state(P, ctx, mpo, chi, caps, seed):
     return P.DMRG(ctx, mpo, LX_UPDATE, 0, chi, seed=seed, center=update_centre(LX_UPDATE), caps=caps)
 
@@ -380,9 +412,7 @@ def main():
     import torch
     import paper_1512_03318_gb300 as P
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -398,7 +428,7 @@ def main():
         raise SystemExit("too many steps for the cylinder length")
     mpo = P.MPO(None, LX_UPDATE, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, P.MRD_BASIS_MIXED)
     caps = update_caps(LX_UPDATE, chi)
-    seed = 11 + rank
+    seed = replica_seed(rank)
     # reduced-precision Lanczos restarted until its Ritz value settles, then FP64 refinement
     mixed = P.DMRG.params(chi, 1e-14, 60, 1e-10, PREC["bf16x3"], args.refine, 1e-13, restarts=args.fast_restarts)
     if args.only_matvec:
@@ -427,15 +457,10 @@ def main():
         return 0
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        ranks_barrier(dist)
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks_max(x, dist, dev)
 
     # ---- accuracy: mixed form vs converged FP64 reference of the same first H_eff
     ref_state = make_state(P, ctx, mpo, chi, caps, seed)
@@ -484,7 +509,7 @@ def main():
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     trunc = st.stats()[1]
     st.close()
-    s_per_update = ms_total / 1e3 / args.steps / world
+    s_per_update = per_update_value(ms_total / 1e3, args.steps, world)
 
     # ---- e2e: the two site tensors of every step come from pinned host memory and the updated
     # tensors go back to the host, through the public API
@@ -512,7 +537,7 @@ def main():
     torch.cuda.synchronize(dev)
     t_e2e = max_over_ranks(time.perf_counter() - t_e2e)
     st.close()
-    e2e_value = t_e2e / args.steps / world
+    e2e_value = per_update_value(t_e2e, args.steps, world)
 
     # ---- FP64 form at the same accuracy (restarted Lanczos until the Ritz value settles)
     st = make_state(P, ctx, mpo, chi, caps, seed)
