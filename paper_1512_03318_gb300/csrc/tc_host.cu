@@ -148,7 +148,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   // step-2 tasks (theta' = sum Z WR), built on a second host thread while this one builds the
   // step-1 tasks: the two loops share only the finished (read-only) panel indexes
   bool step2_ok = true;
-  std::thread step2([&] {
+  auto build_step2 = [&] {
     for (int64_t i = 0; i < c[C_NT2]; ++i) {
       const int64_t* t = &h->t2_host[TF * i];
       if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
@@ -166,7 +166,13 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
       t2.insert(t2.end(), {t[0], t[1], t[2], t[3], 0, seg0, t[5], 1, 0, 0});
       p2.push_back(p2.back() + ((t[0] + 127) / 128) * ((t[1] + ntile - 1) / ntile));
     }
-  });
+  };
+  std::thread step2;
+  try {
+    step2 = std::thread(build_step2);
+  } catch (...) {   // no thread to be had: build it here, before step 1
+    build_step2();
+  }
   struct Join {
     std::thread& t;
     ~Join() { if (t.joinable()) t.join(); }
@@ -194,7 +200,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
       p1.push_back(p1.back() + ((t[0] + 127) / 128) * ((N + ntile - 1) / ntile));
     }
   }
-  step2.join();
+  if (step2.joinable()) step2.join();
   if (!step2_ok) return mrd_fail(ctx, MRD_E_STATE, "tc: step-2 operand not packed");
   // block schedule: tiles are dealt to the persistent CTAs in task order; order 1 puts the
   // tasks with the most work (tiles x K tiles) first so that the long ones start early
