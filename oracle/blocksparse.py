@@ -295,3 +295,69 @@ def heff_apply_block(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat,
                     continue
                 out += (vi * vj) * ((lb @ blk) @ rblk[(wpp, bi)][1])
     return out
+
+
+def env_left_update_block(sec_l, sec_r, m, mod, cl, cm, w_entries, lflat, a_blocks, out_key):
+    """One block of the left environment update of standard two-site DMRG,
+        L'_{w'}[c', c] = sum_{w, a', a, s', s} conj(A[a', s', c']) L_w[a', a] W[w, w', s', s] A[a, s, c],
+    restated with loops over charge blocks. sec_l / sec_r: BondSectors of the bonds left and
+    right of the site (momentum index m); cl / cm: channel charges of the MPO bonds left and
+    right of it; w_entries: the site's (w, w', s', s, value) list; lflat: L in the
+    env_left_layout(sec_l, cl) layout; a_blocks: {(a_index, s): d_a x d_c array} of the MPS
+    tensor, c the sector q_a + q(s). out_key = (w', c_index); returns the d(c + c_{w'}) x d(c)
+    block ([bra][ket]), zero if no term reaches it."""
+    wp, ci = out_key
+    qc = sec_r.charges[ci]
+    qcp = qadd(qc, cm[wp], mod)
+    out = np.zeros((sec_r.dim(qcp), sec_r.dims[ci]), dtype=np.complex128)
+    if qcp not in sec_r.index:
+        return out
+    lblk = {(w, ai): (api, lflat[off: off + dp * da].reshape(dp, da))
+            for w, ai, api, off, dp, da in env_left_layout(sec_l, cl, mod)}
+    for (w, wq, sp, s, v) in w_entries:
+        if wq != wp:
+            continue
+        qa = qsub(qc, qsite(s, m, mod), mod)
+        qap = qsub(qcp, qsite(sp, m, mod), mod)
+        if qa not in sec_l.index or qap not in sec_l.index:
+            continue
+        ai, api = sec_l.index[qa], sec_l.index[qap]
+        if (w, ai) not in lblk or lblk[(w, ai)][0] != api:
+            continue
+        if (ai, s) not in a_blocks or (api, sp) not in a_blocks:
+            continue
+        out += v * (a_blocks[(api, sp)].conj().T @ lblk[(w, ai)][1] @ a_blocks[(ai, s)])
+    return out
+
+
+def env_right_update_block(sec_l, sec_r, m, mod, cl, cm, w_entries, rflat, b_blocks, out_key):
+    """One block of the right environment update of standard two-site DMRG,
+        R'_w[c, c'] = sum_{w', b, b', s', s} B[c, s, b] R_{w'}[b, b'] conj(B[c', s', b']) W[w, w', s', s],
+    restated with loops over charge blocks. sec_l / sec_r: BondSectors left and right of the
+    site (momentum index m); cl / cm: channel charges of the MPO bonds left and right of it;
+    rflat: R in the env_right_layout(sec_r, cm) layout; b_blocks: {(c_index, s): d_c x d_b
+    array}, b the sector q_c + q(s). out_key = (w, c_index); returns the d(c) x d(c + c_w)
+    block ([ket][bra])."""
+    w, ci = out_key
+    qc = sec_l.charges[ci]
+    qcp = qadd(qc, cl[w], mod)
+    out = np.zeros((sec_l.dims[ci], sec_l.dim(qcp)), dtype=np.complex128)
+    if qcp not in sec_l.index:
+        return out
+    cpi = sec_l.index[qcp]
+    rblk = {(wq, bi): (bpi, rflat[off: off + db * dp].reshape(db, dp))
+            for wq, bi, bpi, off, db, dp in env_right_layout(sec_r, cm, mod)}
+    for (wq, wp, sp, s, v) in w_entries:
+        if wq != w:
+            continue
+        qb = qadd(qc, qsite(s, m, mod), mod)
+        qbp = qadd(qcp, qsite(sp, m, mod), mod)
+        if qb not in sec_r.index or qbp not in sec_r.index:
+            continue
+        bi, bpi = sec_r.index[qb], sec_r.index[qbp]
+        if (wp, bi) not in rblk or rblk[(wp, bi)][0] != bpi:
+            continue
+        if (ci, s) not in b_blocks or (cpi, sp) not in b_blocks:
+            continue
+        out += v * (b_blocks[(ci, s)] @ rblk[(wp, bi)][1] @ b_blocks[(cpi, sp)].conj().T)
+    return out

@@ -103,3 +103,222 @@ def test_empty_overlap_gives_empty_theta():
     left = B.BondSectors([((0, 0), 3)])
     right = B.BondSectors([((5, 0), 2)])
     assert B.theta_layout(left, right, 0, 0, 1) == []
+
+
+_CASES = [(1, 4, 40, 44, 1, 2, 5, 6, 7), (3, 5, 60, 50, 4, 0, 6, 5, 8), (5, 3, 36, 30, 2, 1, 9, 7, 4),
+          (7, 6, 50, 70, 5, 3, 4, 8, 6)]
+
+
+def _offsets(dims):
+    return np.concatenate([[0], np.cumsum(dims)]).astype(int)
+
+
+@pytest.mark.parametrize("seed,ly,chi_l,chi_r,m1,m2,dl,dm,dr", _CASES)
+def test_heff_apply_block_equals_dense_block(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr):
+    """heff_apply_block (the sampled reference of the production-size GPU checks) against the
+    dense symmetry-free contraction, output block by output block: every allowed block
+    (a', s1', s2') of the dense H_eff theta, sliced by the sector offsets, equals the single
+    block the function computes."""
+    case = _random_case(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr)
+    left, right, cl, cm, cr, wi, wj, lay, ll, rl, lflat, rflat, tflat = case
+    L, Wi, Wj, R, to_dense = _dense(left, right, m1, m2, ly, cl, cm, cr, wi, wj, lay, ll, rl, lflat, rflat, tflat)
+    ref = D.heff_apply_dense(L, Wi, Wj, R, to_dense(tflat))
+    ol, orr = _offsets(left.dims), _offsets(right.dims)
+    scale = np.max(np.abs(ref))
+    n_checked = 0
+    for m in lay:
+        for s1p, api, dap, _ in m["rows"]:
+            for s2p, bpi, dbp, _ in m["cols"]:
+                got = B.heff_apply_block(left, right, m1, m2, ly, cl, cm, cr, wi, wj, lflat, rflat, tflat,
+                                         (api, s1p, s2p))
+                want = ref[ol[api]:ol[api] + dap, s1p, s2p, orr[bpi]:orr[bpi] + dbp]
+                assert got.shape == want.shape
+                assert np.max(np.abs(got - want), initial=0.0) < 1e-13 * scale
+                n_checked += 1
+    assert n_checked >= 20
+
+
+def _nonzero_blocks(arr, axes_offsets):
+    """Index tuples of the sector blocks of a dense array that hold a nonzero entry. axes_offsets:
+    per axis, the list of block boundaries (sector offsets, or [0, 1, ..] for plain indices)."""
+    import itertools
+    out = []
+    ranges = [range(len(o) - 1) for o in axes_offsets]
+    for idx in itertools.product(*ranges):
+        sl = tuple(slice(o[i], o[i + 1]) for o, i in zip(axes_offsets, idx))
+        if np.any(arr[sl] != 0):
+            out.append(idx)
+    return out
+
+
+@pytest.mark.parametrize("seed,ly,chi_l,chi_r,m1,m2,dl,dm,dr", _CASES[:3])
+def test_heff_flops_equals_count_from_dense_blocks(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr):
+    """heff_flops (the flop count behind every H_eff TFLOP/s figure) against a count taken from
+    the dense arrays alone: 8 real flops per complex multiply-add of every product of nonzero
+    blocks in the definition order L -> W_i W_{i+1} -> R, the nonzero blocks being found in the
+    dense L, theta, X = L theta, Y = W W X and R, sliced by the sector offsets (no layout
+    function involved)."""
+    case = _random_case(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr)
+    left, right, cl, cm, cr, wi, wj, lay, ll, rl, lflat, rflat, tflat = case
+    L, Wi, Wj, R, to_dense = _dense(left, right, m1, m2, ly, cl, cm, cr, wi, wj, lay, ll, rl, lflat, rflat, tflat)
+    T = to_dense(tflat)
+    ol, orr = _offsets(left.dims), _offsets(right.dims)
+    dlf, drt = np.diff(ol), np.diff(orr)
+    chan_l, chan_r, two = list(range(len(cl) + 1)), list(range(len(cr) + 1)), [0, 1, 2]
+    # L step: X_w[a', s1, s2, b] += L_w[a', a] theta[a, s1, s2, b]
+    lnz = _nonzero_blocks(L, [chan_l, ol, ol])
+    tnz = set(_nonzero_blocks(T, [ol, two, two, orr]))
+    fl = 0
+    for w, ap, a in lnz:
+        for s1 in (0, 1):
+            for s2 in (0, 1):
+                for b in range(len(right.dims)):
+                    if (a, s1, s2, b) in tnz:
+                        fl += 8 * dlf[ap] * dlf[a] * drt[b]
+    # W step: one scaled block add per pair of MPO entries (W_i[w,w',s1',s1], W_{i+1}[w',w'',s2',s2])
+    # and nonzero block X_w[a', s1, s2, b]
+    X = np.einsum("wpa,asub->wpsub", L, T)
+    xnz = _nonzero_blocks(X, [chan_l, ol, two, two, orr])
+    xby = {}
+    for w, ap, s1, s2, b in xnz:
+        xby.setdefault((w, s1, s2), []).append((ap, b))
+    for (w, wp, s1p, s1, _) in wi:
+        for (wq, wpp, s2p, s2, _) in wj:
+            if wq != wp:
+                continue
+            for ap, b in xby.get((w, s1, s2), []):
+                fl += 8 * dlf[ap] * drt[b]
+    # R step: theta'[a', s1', s2', b'] += Y_{w''}[a', s1', s2', b] R_{w''}[b, b']
+    Y = np.einsum("zptrb->zptrb", np.einsum("vzru,vptub->zptrb", Wj, np.einsum("wvts,wpsub->vptub", Wi, X)))
+    ynz = _nonzero_blocks(Y, [chan_r, ol, two, two, orr])
+    rnz = _nonzero_blocks(R, [chan_r, orr, orr])
+    rby = {}
+    for w, b, bp in rnz:
+        rby.setdefault((w, b), []).append(bp)
+    for w, ap, s1p, s2p, b in ynz:
+        for bp in rby.get((w, b), []):
+            fl += 8 * dlf[ap] * drt[b] * drt[bp]
+    assert B.heff_flops(left, right, m1, m2, ly, cl, cm, cr, wi, wj) == fl
+
+
+def _random_site(sec_l, sec_r, m, mod, seed):
+    """Dense random MPS tensor A[a, s, c] that is nonzero only on charge-allowed blocks
+    q_a + q(s) = q_c (entries complex U[-1, 1))."""
+    ol, orr = _offsets(sec_l.dims), _offsets(sec_r.dims)
+    A = np.zeros((ol[-1], 2, orr[-1]), complex)
+    k = 0
+    for ai, qa in enumerate(sec_l.charges):
+        for s in (0, 1):
+            qc = B.qadd(qa, B.qsite(s, m, mod), mod)
+            if qc in sec_r.index:
+                ci = sec_r.index[qc]
+                blk = synth.complex_pm1(synth.substream(seed, k), sec_l.dims[ai] * sec_r.dims[ci])
+                A[ol[ai]:ol[ai + 1], s, orr[ci]:orr[ci + 1]] = blk.reshape(sec_l.dims[ai], sec_r.dims[ci])
+                k += 1
+    return A
+
+
+def _env_dense(sec, layout, nchan, flat, left):
+    """Dense environment [w, bra, ket] (left) or [w, ket, bra] (right) from a flat one in its layout."""
+    o = _offsets(sec.dims)
+    env = np.zeros((nchan, o[-1], o[-1]), complex)
+    for w, xi, xpi, off, d0, d1 in layout:
+        blk = flat[off:off + d0 * d1].reshape(d0, d1)
+        if left:
+            env[w, o[xpi]:o[xpi] + d0, o[xi]:o[xi] + d1] = blk
+        else:
+            env[w, o[xi]:o[xi] + d0, o[xpi]:o[xpi] + d1] = blk
+    return env
+
+
+def _layout_mask(sec, layout, nchan, left):
+    o = _offsets(sec.dims)
+    mask = np.zeros((nchan, o[-1], o[-1]), bool)
+    for w, xi, xpi, off, d0, d1 in layout:
+        if left:   # L_w block [bra a' = xpi][ket a = xi]
+            mask[w, o[xpi]:o[xpi] + d0, o[xi]:o[xi] + d1] = True
+        else:      # R_w block [ket b = xi][bra b' = xpi]
+            mask[w, o[xi]:o[xi] + d0, o[xpi]:o[xpi] + d1] = True
+    return mask
+
+
+@pytest.mark.parametrize("seed,ly,m,dl,dr", [(2, 4, 1, 5, 7), (4, 5, 3, 6, 4), (6, 3, 2, 8, 5)])
+def test_env_contraction_stays_in_layout(seed, ly, m, dl, dr):
+    """An environment contracted (dense, oracle.dmrg) from a charge-conserving environment, a
+    random charge-allowed MPS tensor and a random charge-conserving MPO site has no weight
+    outside the blocks env_left_layout / env_right_layout list for the new bond (a block the
+    layouts left out would be dropped by every block-sparse environment, on both sides of a
+    comparison that reads them through these layouts)."""
+    sec0 = B.BondSectors(synth.bond_sectors(40, ly, 10, synth.substream(seed, 1), min_dim=0))
+    # the sectors reachable from sec0 through one orbital of momentum m, random dims
+    cand = sorted({B.qadd(q, B.qsite(s, m, ly), ly) for q in sec0.charges for s in (0, 1)})
+    u = synth.uniform01(synth.substream(seed, 2), len(cand))
+    sec1 = B.BondSectors([(q, 1 + int(5 * x)) for q, x in zip(cand, u)])
+    cl, cm, _ = synth.random_channel_charges(dl, dr, 1, m, m, ly, seed)
+    W = synth.random_mpo_site(cl, cm, ly, m, synth.substream(seed, 3), 0.8)
+    Wd = np.zeros((len(cl), len(cm), 2, 2), complex)
+    for a, b, sp, s, v in W:
+        Wd[a, b, sp, s] += v
+    A = _random_site(sec0, sec1, m, ly, synth.substream(seed, 4))
+    # left: L at bond 0 (channels cl) -> L' at bond 1 (channels cm)
+    lay0 = B.env_left_layout(sec0, cl, ly)
+    L0 = np.zeros((len(cl), A.shape[0], A.shape[0]), complex)
+    L0[_layout_mask(sec0, lay0, len(cl), True)] = synth.complex_pm1(synth.substream(seed, 5), B.env_size(lay0))
+    L1 = D.env_left_update(L0, A, Wd)
+    mask = _layout_mask(sec1, B.env_left_layout(sec1, cm, ly), len(cm), True)
+    assert np.max(np.abs(L1)) > 0
+    assert np.max(np.abs(L1[~mask]), initial=0.0) == 0.0
+    # right: R at bond 1 (channels cm) -> R' at bond 0 (channels cl)
+    lay1 = B.env_right_layout(sec1, cm, ly)
+    R1 = np.zeros((len(cm), A.shape[2], A.shape[2]), complex)
+    R1[_layout_mask(sec1, lay1, len(cm), False)] = synth.complex_pm1(synth.substream(seed, 6), B.env_size(lay1))
+    R0 = D.env_right_update(R1, A, Wd)
+    mask = _layout_mask(sec0, B.env_right_layout(sec0, cl, ly), len(cl), False)
+    assert np.max(np.abs(R0)) > 0
+    assert np.max(np.abs(R0[~mask]), initial=0.0) == 0.0
+
+
+@pytest.mark.parametrize("seed,ly,m,dl,dr", [(2, 4, 1, 5, 7), (4, 5, 3, 6, 4), (6, 3, 2, 8, 5)])
+def test_env_update_blocks_equal_dense(seed, ly, m, dl, dr):
+    """env_left_update_block / env_right_update_block (the block-by-block environment updates
+    that sample the production-size GPU environments) against the dense symmetry-free
+    contractions of oracle.dmrg, block by block over the whole layout of the new bond."""
+    sec0 = B.BondSectors(synth.bond_sectors(40, ly, 10, synth.substream(seed, 1), min_dim=0))
+    cand = sorted({B.qadd(q, B.qsite(s, m, ly), ly) for q in sec0.charges for s in (0, 1)})
+    u = synth.uniform01(synth.substream(seed, 2), len(cand))
+    sec1 = B.BondSectors([(q, 1 + int(5 * x)) for q, x in zip(cand, u)])
+    cl, cm, _ = synth.random_channel_charges(dl, dr, 1, m, m, ly, seed)
+    W = synth.random_mpo_site(cl, cm, ly, m, synth.substream(seed, 3), 0.8)
+    Wd = np.zeros((len(cl), len(cm), 2, 2), complex)
+    for a, b, sp, s, v in W:
+        Wd[a, b, sp, s] += v
+    A = _random_site(sec0, sec1, m, ly, synth.substream(seed, 4))
+    o0, o1 = _offsets(sec0.dims), _offsets(sec1.dims)
+    blocks = {}
+    for ai, qa in enumerate(sec0.charges):
+        for s in (0, 1):
+            qc = B.qadd(qa, B.qsite(s, m, ly), ly)
+            if qc in sec1.index:
+                ci = sec1.index[qc]
+                blocks[(ai, s)] = A[o0[ai]:o0[ai + 1], s, o1[ci]:o1[ci + 1]]
+    # left
+    lay0 = B.env_left_layout(sec0, cl, ly)
+    lflat = synth.complex_pm1(synth.substream(seed, 5), B.env_size(lay0))
+    L0 = _env_dense(sec0, lay0, len(cl), lflat, True)
+    L1 = D.env_left_update(L0, A, Wd)
+    scale = np.max(np.abs(L1))
+    for w, ci, cpi, off, d0, d1 in B.env_left_layout(sec1, cm, ly):
+        got = B.env_left_update_block(sec0, sec1, m, ly, cl, cm, W, lflat, blocks, (w, ci))
+        want = L1[w, o1[cpi]:o1[cpi] + d0, o1[ci]:o1[ci] + d1]
+        assert np.max(np.abs(got - want), initial=0.0) < 1e-13 * scale
+    # right
+    lay1 = B.env_right_layout(sec1, cm, ly)
+    rflat = synth.complex_pm1(synth.substream(seed, 6), B.env_size(lay1))
+    R1 = _env_dense(sec1, lay1, len(cm), rflat, False)
+    R0 = D.env_right_update(R1, A, Wd)
+    bblocks = {(ai, s): blk for (ai, s), blk in blocks.items()}
+    scale = np.max(np.abs(R0))
+    for w, ci, cpi, off, d0, d1 in B.env_right_layout(sec0, cl, ly):
+        got = B.env_right_update_block(sec0, sec1, m, ly, cl, cm, W, rflat, bblocks, (w, ci))
+        want = R0[w, o0[ci]:o0[ci] + d0, o0[cpi]:o0[cpi] + d1]
+        assert np.max(np.abs(got - want), initial=0.0) < 1e-13 * scale
