@@ -168,10 +168,23 @@ int mrd_heff_timing(mrd_heff* h, int32_t on);
  *                           candidate tile configuration (columns per tile, pipeline stages,
  *                           task order) and keeps the fastest for the context; later H_effs
  *                           of the class reuse it; 0: the default configuration. */
+/*   MRD_OPT_WAIT_LIMIT_US   1000000 (default): how long, in microseconds, a wait inside a
+ *                           tensor-core GEMM (for a shared-memory stage, an accumulator or
+ *                           the other warp roles) may last before the kernel gives up: it then
+ *                           sets an error flag, waits for its own copies and MMAs in flight,
+ *                           frees its tensor memory and returns. 0 gives up at the first wait,
+ *                           before any copy or MMA is issued (a test of the error path).
+ *                           Range 0 .. 60,000,000; MRD_E_ARG outside it. The flag is reported
+ *                           as MRD_E_TIMEOUT by the next mrd_lanczos, mrd_heff_rayleigh or
+ *                           mrd_heff_status, which clear it; the context stays usable. */
 #define MRD_OPT_GRAPH 1
 #define MRD_OPT_PER_TASK_LAUNCH 2
 #define MRD_OPT_AUTOTUNE 3
+#define MRD_OPT_WAIT_LIMIT_US 4
 int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value);
+/* Wait for the context stream and report a device-side wait of a tensor-core GEMM that gave
+ * up since the last check: MRD_E_TIMEOUT (the flag is then cleared), else 0. */
+int mrd_heff_status(mrd_heff* h);
 /* Tensor-core tile configuration in use: cfg4 = {columns per tile, pipeline stages, task
  * order (0: charge order, 1: largest work first), source (0: default, 1: tuned on this
  * H_eff, 2: tuned earlier on the context)}; all -1 before the first tensor-core application. */
@@ -247,6 +260,22 @@ int mrd_two_site_update(mrd_dmrg* d, int32_t i, int32_t direction, const mrd_dmr
 /* One sweep: two-site updates left to right over all bonds, then right to left (requires the
  * centre at site 0). Writes the last energy. */
 int mrd_sweep(mrd_dmrg* d, const mrd_dmrg_params* p, double* energy);
+/* Environment update of two-site DMRG (the paper relies on standard DMRG, its refs. W92,
+ * S2005): with direction +1 the left environment of bond site+1 is rebuilt from that of bond
+ * `site`, the MPS tensor A = site and the MPO site W:
+ *   L'_{w'}[c', c] = sum_{w, a', a, s', s} conj(A[a', s', c']) L_w[a', a] W[w, w', s', s] A[a, s, c];
+ * with direction -1 the right environment of bond `site` is rebuilt from that of bond site+1
+ * and B = site:
+ *   R'_w[c, c'] = sum_{w', b, b', s', s} B[c, s, b] R_{w'}[b, b'] conj(B[c', s', b']) W[w, w', s', s].
+ * Block-sparse in the charges: only blocks with q_{c'} = q_c + c_{w'} (left) or
+ * q_{c'} = q_c + c_w (right) exist, in the env layouts of this header. The tensor is used as it
+ * is (an update leaves it left-canonical moving right and right-canonical moving left, which
+ * makes the environment the projected Hamiltonian). The result replaces the state's
+ * environment of that bond, readable with mrd_dmrg_env; two-site updates call the same code.
+ * prec: MRD_PREC_FP64 (FP64 grouped GEMMs) or MRD_PREC_FF (float-float, ~1e-13 relative).
+ * MRD_E_ARG for a site outside 0..n-2 (+1) or 1..n-1 (-1), MRD_E_STATE if the input
+ * environment has not been built. */
+int mrd_env_update(mrd_dmrg* d, int32_t site, int32_t direction, int32_t prec);
 /* Sectors of MPS bond `bond` (0..n) as (N, K, dim) triplets (sectors may be NULL). */
 int mrd_dmrg_bond(const mrd_dmrg* d, int32_t bond, int32_t* n_sectors, int32_t* sectors);
 /* Copy of MPS tensor `site` to the host (complex128). mode 0: blocks grouped by right
@@ -303,7 +332,8 @@ int mrd_dmrg_stats(const mrd_dmrg* d, double* energy, double* trunc_err, int32_t
  * loads this library keeps until the process exits. Problems whose Z is larger are rejected
  * with MRD_E_ARG and a message naming both sizes; use mrd_heff_apply for them. The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress, with that device
- * current), so make that first call before any stream capture. All calls share the one
+ * current), so make that first call before any stream capture; the address is kept for the
+ * life of the process and is not valid after a cudaDeviceReset (nor is any other handle). All calls share the one
  * array: two calls whose device work overlaps in time (different streams or contexts) race
  * and give wrong results; calls ordered on one stream are safe. theta_out is cleared by the
  * call; Z needs no clearing because step 2 reads only what step 1 of the same call wrote.

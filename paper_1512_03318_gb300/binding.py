@@ -20,6 +20,7 @@ MRD_BASIS_REAL = 1
 MRD_OPT_GRAPH = 1
 MRD_OPT_PER_TASK_LAUNCH = 2
 MRD_OPT_AUTOTUNE = 3
+MRD_OPT_WAIT_LIMIT_US = 4
 MRD_SVD_F32_FF = 0
 MRD_SVD_FF = 1
 MRD_SVD_F32_F64 = 2
@@ -111,6 +112,7 @@ _SIGS = {
     "mrd_two_site_update": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]),
     "mrd_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "mrd_env_update": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "mrd_dmrg_bond": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mrd_dmrg_site": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_double)]),
@@ -121,6 +123,7 @@ _SIGS = {
     "mrd_dmrg_timing": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "mrd_heff_status": (C.c_int, [C.c_void_p]),
     "mrd_heff_tc_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "mrd_dmrg_svd_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_dmrg_schmidt": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -315,6 +318,11 @@ class DMRG:
         self.ctx.check(lib().mrd_sweep(self.h, C.byref(params), C.byref(e)))
         return e.value
 
+    def env_update(self, site, direction, prec=MRD_PREC_FP64):
+        """mrd_env_update: rebuild the left environment of bond site+1 (direction +1) or the right
+        environment of bond site (direction -1) from the neighbouring one."""
+        self.ctx.check(lib().mrd_env_update(self.h, site, direction, prec))
+
     def bond(self, b):
         n = C.c_int32()
         lib().mrd_dmrg_bond(self.h, b, C.byref(n), None)
@@ -444,8 +452,13 @@ class Heff:
         self.ctx.check(lib().mrd_heff_set_env(self.h, _ptr(lenv), _ptr(renv)))
 
     def set_option(self, option, value):
-        """mrd_heff_set_option (MRD_OPT_GRAPH, MRD_OPT_PER_TASK_LAUNCH)."""
+        """mrd_heff_set_option (MRD_OPT_GRAPH, MRD_OPT_PER_TASK_LAUNCH, MRD_OPT_AUTOTUNE,
+        MRD_OPT_WAIT_LIMIT_US)."""
         self.ctx.check(lib().mrd_heff_set_option(self.h, option, int(value)))
+
+    def status(self):
+        """mrd_heff_status: raises MrdError (MRD_E_TIMEOUT) if a tensor-core wait gave up."""
+        self.ctx.check(lib().mrd_heff_status(self.h))
 
     def tc_config(self):
         """(columns per tile, stages, task order, source) of the tensor-core GEMM (mrd_heff_tc_config)."""

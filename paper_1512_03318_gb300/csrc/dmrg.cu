@@ -1252,6 +1252,32 @@ int mrd_sweep(mrd_dmrg* D, const mrd_dmrg_params* p, double* energy) {
   return MRD_OK;
 }
 
+int mrd_env_update(mrd_dmrg* D, int32_t site, int32_t direction, int32_t prec) {
+  if (!D) return MRD_E_ARG;
+  mrd_ctx* ctx = D->ctx;
+  if (direction != 1 && direction != -1) return mrd_fail(ctx, MRD_E_ARG, "mrd_env_update: direction must be +1 or -1");
+  if (prec != MRD_PREC_FP64 && prec != MRD_PREC_FF)
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_env_update: prec must be MRD_PREC_FP64 or MRD_PREC_FF");
+  // the fold with the MPO comes from the H_eff of a bond that contains `site`: (site, site+1)
+  // for a left environment, (site-1, site) for a right one
+  if (direction > 0 && (site < 0 || site > D->n - 2))
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_env_update: a left update needs 0 <= site <= n-2");
+  if (direction < 0 && (site < 1 || site > D->n - 1))
+    return mrd_fail(ctx, MRD_E_ARG, "mrd_env_update: a right update needs 1 <= site <= n-1");
+  const EnvT& src = direction > 0 ? D->L[site] : D->R[site + 1];
+  if (!src.data.p) return mrd_fail(ctx, MRD_E_STATE, "mrd_env_update: the input environment is not built");
+  Guard g(ctx->device);
+  D->gemm_ff = prec == MRD_PREC_FF;
+  mrd_heff* h = nullptr;
+  const int i = direction > 0 ? site : site - 1;
+  int rc = direction > 0 ? make_heff(D, i, D->L[i].data.as<double2>(), nullptr, &h)
+                         : make_heff(D, i, nullptr, D->R[i + 2].data.as<double2>(), &h);
+  if (rc != MRD_OK) return rc;
+  rc = direction > 0 ? env_left(D, h, i) : env_right(D, h, i);
+  mrd_heff_free(h);
+  return rc;
+}
+
 int mrd_dmrg_bond(const mrd_dmrg* D, int32_t bond, int32_t* n_sectors, int32_t* sectors) {
   if (!D || !n_sectors || bond < 0 || bond > D->n) return MRD_E_ARG;
   const Secs& s = bond < D->n ? D->A[bond].left : D->A[D->n - 1].right;
