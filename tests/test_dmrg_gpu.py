@@ -32,11 +32,11 @@ def ed_sector(lx, ly, flux, t, v, n, k=None):
     return float(np.linalg.eigvalsh(h)[0])
 
 
-def run_dmrg(ctx, lx, ly, fq, t, v, n, k, chi, basis=0, sweeps=8, seed=7, svd_mode=None):
+def run_dmrg(ctx, lx, ly, fq, t, v, n, k, chi, basis=0, sweeps=8, seed=7, svd_mode=None, params=None):
     import paper_1512_03318_gb300 as P
     mpo = P.MPO(None, lx, ly, 1, fq, t, v, basis)
     d = P.DMRG(ctx, mpo, n, k, chi, seed=seed, center=0)
-    p = P.DMRG.params(chi, 1e-14, 40, 1e-14, svd_mode=svd_mode)
+    p = P.DMRG.params(chi, 1e-14, 40, 1e-14, svd_mode=svd_mode) if params is None else params
     es = []
     for _ in range(sweeps):
         es.append(d.sweep(p))
@@ -139,10 +139,10 @@ def test_update_canonical_factor_at_production_block_sizes(ctx, prec, svd_mode):
     d.close()
 
 
-def _schmidt_after_sweeps(ctx, lx, ly, fq, v, n, k, chi, bond):
-    es, d = run_dmrg(ctx, lx, ly, fq, 1.0, v, n, k, chi, sweeps=8)
+def _schmidt_after_sweeps(ctx, lx, ly, fq, v, n, k, chi, bond, params=None):
+    es, d = run_dmrg(ctx, lx, ly, fq, 1.0, v, n, k, chi, sweeps=8, params=params)
     import paper_1512_03318_gb300 as P
-    p = P.DMRG.params(chi, 1e-14, 40, 1e-14)
+    p = P.DMRG.params(chi, 1e-14, 40, 1e-14) if params is None else params
     for i in range(bond):                   # centre back to the bond, moving right
         d.update(i, +1, p)
     b, spec = d.schmidt()
@@ -196,3 +196,56 @@ def test_entanglement_spectrum_free_fermions(ctx):
             best = (e, got)
     assert abs(best[0] - e0) < 1e-10 * abs(e0)
     _compare_spectra(best[1], ref, 1e-6)
+
+
+# The reduced-precision forms of the update: Lanczos matvecs on the tensor cores (split BF16 or
+# TF32 with FP32 accumulation), the ground vector refined with float-float or FP64 matvecs.
+# (prec, refine_iter, refine_prec, svd_mode); the first row is the form the benchmark times
+# (60 Lanczos steps per run, up to 8 restarts, one float-float Rayleigh quotient, FP32
+# pre-sweeps then float-float Jacobi sweeps, float-float environments).
+REDUCED_FORMS = {
+    "bf16x3+ff (bench form)": (2, 1, 3, 0),
+    "tf32+ff": (1, 20, 3, 0),
+    "bf16x3+fp64": (2, 1, 0, 3),
+    "tf32+fp64": (1, 20, 0, 2),
+}
+
+
+def reduced_params(P, chi, form):
+    prec, refine_iter, refine_prec, svd_mode = REDUCED_FORMS[form]
+    return P.DMRG.params(chi, 1e-14, 60, 1e-10, prec, refine_iter, 1e-13, restarts=8, svd_mode=svd_mode,
+                         refine_prec=refine_prec)
+
+
+@pytest.mark.parametrize("form", list(REDUCED_FORMS))
+def test_reduced_precision_forms_match_ed(ctx, form):
+    """The 1e-9 energy gate of the reduced-precision forms, against exact diagonalisation: on the
+    4 x 4 cylinder (flux 1/4, t = V = 1, N = 4) at chi = 256 (no truncation), sweeps of each form
+    reach the ED ground energy of the sector within 1e-9 relative."""
+    import paper_1512_03318_gb300 as P
+    lx, ly, n = 4, 4, 4
+    e_ed = [ed_sector(lx, ly, 0.25, 1.0, 1.0, n, k) for k in range(ly)]
+    k0 = int(np.argmin(e_ed))
+    es, d = run_dmrg(ctx, lx, ly, 4, 1.0, 1.0, n, k0, 256, sweeps=6, params=reduced_params(P, 256, form))
+    d.close()
+    assert abs(es[-1] - e_ed[k0]) <= 1e-9 * abs(e_ed[k0]), (form, es, e_ed[k0])
+
+
+def test_bench_form_entanglement_spectrum_matches_ed(ctx):
+    """Schmidt values of the middle bond after sweeps of the benchmarked reduced-precision form
+    equal those of the ED ground state, sector by sector (4 x 4, V = 1, exact chi)."""
+    import paper_1512_03318_gb300 as P
+    from oracle import entanglement as E
+    lx, ly, n = 4, 4, 4
+    e_ed = [ed_sector(lx, ly, 0.25, 1.0, 1.0, n, k) for k in range(ly)]
+    k0 = int(np.argmin(e_ed))
+    basis = model.fock_basis(lx * ly, n)
+    basis = np.array([s for s in basis if model.total_momentum(lx, ly, int(s)) == k0], dtype=np.uint64)
+    h = model.mixed_space_hamiltonian(lx, ly, 0.25, 1.0, 1.0, n, basis=basis)
+    w, vec = np.linalg.eigh(h)
+    ref = E.schmidt_spectrum(vec[:, 0], basis, 8, ly)
+    e, got = _schmidt_after_sweeps(ctx, lx, ly, 4, 1.0, n, k0, 256, 8,
+                                   params=reduced_params(P, 256, "bf16x3+ff (bench form)"))
+    assert abs(e - w[0]) <= 1e-9 * abs(w[0])
+    assert abs(sum(np.sum(v ** 2) for v in got.values()) - 1.0) < 1e-12
+    _compare_spectra(got, ref, 1e-5)
