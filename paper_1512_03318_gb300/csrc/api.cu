@@ -700,6 +700,7 @@ int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double
   if (rc != MRD_OK) return rc;
   double2* hv = lanczos_work(h->lz);   // the workspace's spare vector
   rc = mrd_heff_apply(h, theta_dev, (double*)hv, prec);
+  if (rc == MRD_OK && (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3)) rc = tc_status(h);
   if (rc != MRD_OK) return rc;
   double nn, ni, en, ei;
   if ((rc = vdot(h->lz, ctx, (const double2*)theta_dev, (const double2*)theta_dev, &nn, &ni)) != MRD_OK) return rc;
@@ -727,10 +728,21 @@ int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) {
     h->per_task = value != 0;
     if (h->tc) tc_env_changed(h);   // tensor-core per-task tables are built with the panels
     ++h->gen;
+  } else if (option == MRD_OPT_WAIT_LIMIT_US) {
+    if (value < 0 || value > 60000000) return mrd_fail(h->ctx, MRD_E_ARG, "mrd_heff_set_option: wait limit outside 0 .. 60 s");
+    h->wait_ns = (uint64_t)value * 1000ull;
+    ++h->gen;   // captured step graphs hold the old limit in their launch arguments
   } else {
     return mrd_fail(h->ctx, MRD_E_ARG, "mrd_heff_set_option: unknown option");
   }
   return MRD_OK;
+}
+
+int mrd_heff_status(mrd_heff* h) {
+  if (!h) return MRD_E_ARG;
+  Guard g(h->ctx->device);
+  MRD_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  return tc_status(h);
 }
 
 int mrd_heff_tc_config(const mrd_heff* h, int32_t* cfg4) {

@@ -9,6 +9,8 @@
 //
 // The array is a host-side symbol in host code; its device address is obtained once per
 // device with cudaGetSymbolAddress while that device is current, and passed to the kernels.
+// The cached address belongs to the device's primary context: after cudaDeviceReset it is
+// stale (as is every handle of this library created before the reset).
 #include <mutex>
 
 #include "mrd_internal.h"
@@ -60,7 +62,8 @@ extern "C" int mrd_heff_apply_noalloc(mrd_heff* h, const double* theta_in_dev, d
   int n_sm = 0;
   mrd_ctx* ctx = nullptr;
   bool env_loaded = false;
-  mrd::mrd_heff_internal_noalloc_view(h, &p, c, &lw, &wr, &n_sm, &ctx, &env_loaded);
+  const int vrc = mrd::mrd_heff_internal_noalloc_view(h, &p, c, &lw, &wr, &n_sm, &ctx, &env_loaded);
+  if (vrc != MRD_OK) return vrc;
   if (!env_loaded) return mrd_fail(ctx, MRD_E_STATE, "mrd_heff_apply_noalloc: environments not loaded");
   if (c[mrd::C_ZLEN] > (int64_t)MRD_NOALLOC_Z_MAX_ELEMS)
     return mrd_fail(ctx, MRD_E_ARG,

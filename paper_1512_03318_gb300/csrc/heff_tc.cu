@@ -21,7 +21,10 @@
 // Kernel: persistent, one CTA per SM, 6 warps: warp 0 issues the bulk copies, warp 1 owns
 // TMEM (512 columns: two accumulator slots of C_re, C_im) and issues the MMAs from one thread, warps 2-5
 // drain the accumulators (warp w reads TMEM lanes 32 (w % 4) ..). Shared-memory stages are
-// handed over with mbarriers; every wait is bounded and sets an error flag when it gives up.
+// handed over with mbarriers; every wait is bounded (global-timer limit set by the host) and
+// sets an error flag when it gives up. Before the CTA frees its tensor memory and exits, the
+// producer waits for the last fill of every stage and the MMA thread for all its MMAs (commit
+// to a drain barrier), so a CTA whose waits gave up leaves no copy or MMA in flight.
 #include <cuda_bf16.h>
 
 #include "mrd_internal.h"
@@ -59,15 +62,36 @@ __device__ __forceinline__ uint32_t make_idesc(int prec, int n, bool neg_a) {
   return d;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 24) && !done; ++it) {
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-  }
-  if (!done) atomicCAS(err, 0, code);
-  return done != 0;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
+
+__device__ __forceinline__ uint32_t mbar_probe(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done;
+}
+
+// Wait for the phase of `parity` of an mbarrier to complete, for at most limit_ns nanoseconds
+// of the global timer; limit_ns = 0 gives up without probing. On giving up, records `code` in
+// the error flag (first failure wins) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, uint64_t limit_ns) {
+  if (limit_ns > 0) {
+    if (mbar_probe(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (global_ns() - t0 < limit_ns)
+      if (mbar_probe(bar, parity)) return true;
+  }
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+// Limit of the waits that drain a CTA's own copies and MMAs before it frees its tensor memory
+// and exits, whatever limit the work's waits had.
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
@@ -246,6 +270,7 @@ struct TcArgs {
   int ntile;               // B rows per tile (multiple of 16, at most 128)
   int nstages;             // shared-memory pipeline depth (at most kTcMaxStages)
   int stage_bytes;
+  uint64_t wait_ns;        // limit of each pipeline wait (ns); 0: the first wait gives up
 };
 
 // Task and tile of a work item: one load from the host-built item table, else a binary
@@ -316,7 +341,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
   extern __shared__ uint8_t dyn[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t bar_full[kTcMaxStages], bar_empty[kTcMaxStages], bar_acc_full[kAccSlots],
-      bar_acc_empty[kAccSlots];
+      bar_acc_empty[kAccSlots], bar_drain;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int prec = g.prec;
@@ -339,6 +364,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
       mbar_init(smem_u32(&bar_acc_empty[b]), 4);
     }
+    mbar_init(smem_u32(&bar_drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -352,6 +378,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
+    int64_t fills = 0;   // stage fills issued
     for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
       int64_t t, local;
       item_of(g, item, t, local);
@@ -367,7 +394,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
         const uint8_t* a = g.a_base + sg[0] + rt * nkt * planes * (int64_t)(128 * 128);
         const uint8_t* b = g.b_base + sg[1] + nt * nkt * planes * (int64_t)ntile * 128;
         for (int64_t kt = 0; kt < nkt && ok; ++kt) {
-          ok = mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1, g.err, 11);
+          ok = mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1, g.err, 11, g.wait_ns);
           if (!ok) break;
           const uint32_t abytes = planes * 128 * 128, bbytes = (uint32_t)(planes * nrow * 128);
           const uint32_t sa = smem_u32(smem + stage * stage_bytes);
@@ -375,10 +402,15 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
           mbar_expect_tx(smem_u32(&bar_full[stage]), abytes + bbytes);
           bulk_g2s(sa, a + kt * abytes, abytes, smem_u32(&bar_full[stage]));
           bulk_g2s(sb, b + kt * (int64_t)bbytes, bbytes, smem_u32(&bar_full[stage]));
+          ++fills;
           if (++stage == nstages) { stage = 0; phase ^= 1; }
         }
       }
     }
+    // drain: the last fills of every stage have landed before the CTA may exit (after normal
+    // work they have, since the MMAs consumed them; after a wait gave up they may not have)
+    for (int64_t f = fills - 1; f >= 0 && f >= fills - nstages; --f)
+      mbar_wait(smem_u32(&bar_full[f % nstages]), (uint32_t)((f / nstages) & 1), g.err, 15, kDrainNs);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     int stage = 0;
@@ -395,7 +427,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       const int64_t nt = local % tiles_n;
       const int64_t npad = ((N + 15) / 16) * 16;
       const int nrow = (int)(npad - nt * ntile < ntile ? npad - nt * ntile : ntile);
-      ok = mbar_wait(smem_u32(&bar_acc_empty[slot]), ((acc_phase >> slot) & 1) ^ 1, g.err, 12);
+      ok = mbar_wait(smem_u32(&bar_acc_empty[slot]), ((acc_phase >> slot) & 1) ^ 1, g.err, 12, g.wait_ns);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t t_re = tmem + 256 * slot, t_im = t_re + 128;
@@ -404,7 +436,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       for (int64_t s = 0; s < task[6] && ok; ++s) {
         const int64_t nkt = g.segs[TCS * (task[5] + s) + 2];
         for (int64_t kt = 0; kt < nkt && ok; ++kt) {
-          ok = mbar_wait(smem_u32(&bar_full[stage]), phase, g.err, 13);
+          ok = mbar_wait(smem_u32(&bar_full[stage]), phase, g.err, 13, g.wait_ns);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t sa = smem_u32(smem + stage * stage_bytes);
@@ -432,6 +464,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       acc_phase ^= 1u << slot;
       slot ^= 1;
     }
+    // drain: every MMA this thread issued has completed before the tensor memory is freed
+    mma_commit(smem_u32(&bar_drain));
+    mbar_wait(smem_u32(&bar_drain), 0, g.err, 16, kDrainNs);
   } else if (warp >= 2) {
     // ---------------- epilogue
     const int quad = warp & 3;            // TMEM lanes 32*quad .. 32*quad+31
@@ -445,7 +480,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       const int64_t M = task[0], N = task[1];
       const int64_t tiles_n = (N + ntile - 1) / ntile;
       const int64_t rt = local / tiles_n, nt = local % tiles_n;
-      ok = mbar_wait(smem_u32(&bar_acc_full[slot]), (acc_phase >> slot) & 1, g.err, 14);
+      ok = mbar_wait(smem_u32(&bar_acc_full[slot]), (acc_phase >> slot) & 1, g.err, 14, g.wait_ns);
       acc_phase ^= 1u << slot;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -520,7 +555,7 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
 
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
                     const int64_t* prefix, const int2* items, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out,
-                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s) {
+                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, uint64_t wait_ns, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   cudaError_t ea = tc_gemm_init();
   if (ea != cudaSuccess) return ea;
@@ -529,7 +564,7 @@ cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t*
       smem > kTcMaxSmem)
     return cudaErrorInvalidValue;
   TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, items, cfg.ntile, cfg.stages,
-           tc_stage_bytes(prec, cfg.ntile)};
+           tc_stage_bytes(prec, cfg.ntile), wait_ns};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
   k_tc_gemm<<<(unsigned)grid, 192, smem, s>>>(g);
   mrd::count_launch();

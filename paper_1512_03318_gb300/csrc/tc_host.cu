@@ -15,7 +15,7 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
 cudaError_t tc_gemm_init();
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
                     const int64_t* prefix, const int2* items, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out,
-                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, cudaStream_t s);
+                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, uint64_t wait_ns, cudaStream_t s);
 }  // namespace mrd
 
 struct Tc {
@@ -345,10 +345,10 @@ int time_cfg(mrd_heff* h, double* ms) {
     if (r == 1) e = cudaEventRecord(a, s);
     if (e == cudaSuccess)
       e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
-                  h->n_sm, s);
+                  h->n_sm, h->wait_ns, s);
     if (e == cudaSuccess)
       e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
-                  s);
+                  h->wait_ns, s);
   }
   float f = 0.f;
   if (e == cudaSuccess) e = cudaEventRecord(b, s);
@@ -412,8 +412,11 @@ int tc_status(mrd_heff* h) {
   int herr = 0;
   MRD_CUDA(h->ctx, cudaMemcpyAsync(&herr, h->tc->err, 4, cudaMemcpyDeviceToHost, h->ctx->stream));
   MRD_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
-  if (herr) return mrd_fail(h->ctx, MRD_E_TIMEOUT, "tensor-core GEMM: a bounded wait gave up (code " +
-                                                       std::to_string(herr) + ")");
+  if (herr) {   // reported once: the flag is cleared for the next launches
+    MRD_CUDA(h->ctx, cudaMemsetAsync(h->tc->err, 0, 4, h->ctx->stream));
+    MRD_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+    return mrd_fail(h->ctx, MRD_E_TIMEOUT, "tensor-core GEMM: a bounded wait gave up (code " + std::to_string(herr) + ")");
+  }
   return MRD_OK;
 }
 
@@ -467,18 +470,18 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   MRD_CUDA(ctx, record_event(e0, s, cap));
   if (!h->per_task) {
     MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
-                          h->n_sm, s));
+                          h->n_sm, h->wait_ns, s));
     MRD_CUDA(ctx, record_event(e1, s, cap));
     MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
-                          T->err, h->n_sm, s));
+                          T->err, h->n_sm, h->wait_ns, s));
   } else {   // one launch per task: the per-block baseline of the grouped persistent launch
     for (int64_t t = 0; t < T->n1; ++t)
       MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, nullptr, 1, T->tiles1[t], T->z, nullptr, tp,
-                            T->cfg, T->err, h->n_sm, s));
+                            T->cfg, T->err, h->n_sm, h->wait_ns, s));
     MRD_CUDA(ctx, record_event(e1, s, cap));
     for (int64_t t = 0; t < T->n2; ++t)
       MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, nullptr, 1, T->tiles2[t], nullptr,
-                            (double2*)out, tp, T->cfg, T->err, h->n_sm, s));
+                            (double2*)out, tp, T->cfg, T->err, h->n_sm, h->wait_ns, s));
   }
   MRD_CUDA(ctx, record_event(e2, s, cap));
   return MRD_OK;

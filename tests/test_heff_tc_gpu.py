@@ -108,3 +108,35 @@ def test_autotuned_tile_configuration(ctx, prec):
     assert cfgs[1][:3] == cfgs[2][:3]
     assert cfgs[1][0] in (32, 64, 128) and cfgs[1][1] in (2, 3, 4) and cfgs[1][2] in (0, 1)
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_wait_limit_reports_timeout_and_context_recovers(ctx, prec):
+    """Device-side failure detection without a fault: with the wait limit set to zero every
+    wait of the tensor-core GEMM gives up before any copy or MMA is issued, the kernel returns
+    and the host reads MRD_E_TIMEOUT; with the default limit restored, the next application on
+    the same context is correct again."""
+    import paper_1512_03318_gb300 as P
+    case = G.random_case(7, 6, 150, 170, 5, 3, 4, 8, 6)
+    ref = B.heff_apply(case["left"], case["right"], case["m1"], case["m2"], case["mod"], case["cl"], case["cm"],
+                       case["cr"], case["wi"], case["wj"], case["lflat"], case["rflat"], case["tflat"])
+    h = P.Heff(ctx, **G.heff_args(case))
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    h.set_env(dev(case["lflat"]), dev(case["rflat"]))
+    T = dev(case["tflat"])
+    out = torch.empty_like(T)
+    h.apply(T, out, prec=prec)               # tables and tile configuration with the default limit
+    h.status()
+    h.set_option(P.MRD_OPT_WAIT_LIMIT_US, 0)
+    h.apply(T, out, prec=prec)
+    with pytest.raises(P.MrdError) as ex:
+        h.status()
+    assert ex.value.code == -7
+    h.status()                               # reported once, then cleared
+    with pytest.raises(P.MrdError):
+        h.set_option(P.MRD_OPT_WAIT_LIMIT_US, -1)
+    h.set_option(P.MRD_OPT_WAIT_LIMIT_US, 1000000)
+    h.apply(T, out, prec=prec)
+    h.status()
+    err = np.max(np.abs(out.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < TOL[prec], err
