@@ -111,45 +111,41 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 // The MMAs of one K step of a complex product, issued from one asm block with the accumulate
-// predicate set once. TF32: C_re += Re(A) Re(B) - Im(A) Im(B) (negated A), C_im += Re(A) Im(B)
-// + Im(A) Re(B). acc = 0 starts the accumulators of the tile.
-__device__ __forceinline__ void mma4_tf32(uint32_t t_re, uint32_t t_im, uint64_t ar, uint64_t ai, uint64_t br,
-                                          uint64_t bi, uint32_t id_pos, uint32_t id_neg, uint32_t acc) {
+// predicate set once (acc = 0 starts the accumulator of the tile). Each MMA multiplies one A
+// plane by a window of consecutive B planes (tc.cuh), so that its N spans every column group
+// of the output at once: TF32 C[re | im] += A_re x [re | im] + A_im x [-im | re] (2 MMAs of
+// N = 2 nrow); split BF16 C[re_hi | re_lo | im_hi | im_lo] += (A_re_hi + A_re_lo) x
+// [re_hi | re_lo | im_hi | im_lo] + (A_im_hi + A_im_lo) x [-im_hi | -im_lo | re_hi | re_lo]
+// (4 MMAs of N = 4 nrow; the lo x lo product comes with the windows and is kept).
+__device__ __forceinline__ void mma_cplx_tf32(uint32_t tacc, uint64_t a_re, uint64_t a_im, uint64_t b_s0,
+                                              uint64_t b_s1, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %8, 0;\nsetp.eq.b32 q, 0, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %2, %4, %6, p;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %3, %5, %7, q;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%1], %2, %5, %6, p;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%1], %3, %4, %6, q;\n}\n"
-      ::"r"(t_re), "r"(t_im), "l"(ar), "l"(ai), "l"(br), "l"(bi), "r"(id_pos), "r"(id_neg), "r"(acc));
+      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %5, 0;\nsetp.eq.b32 q, 0, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %4, %6, p;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %2, %3, %6, q;\n}\n"
+      ::"r"(tacc), "l"(a_re), "l"(a_im), "l"(b_s0), "l"(b_s1), "r"(acc), "r"(idesc));
 }
 
-// Split BF16 (planes 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo at plane strides pa, pb in descriptor
-// units): each real product is hi*hi + hi*lo + lo*hi, 12 MMAs per complex K step.
-__device__ __forceinline__ void mma12_bf16x3(uint32_t t_re, uint32_t t_im, uint64_t a, uint64_t pa, uint64_t b,
-                                             uint64_t pb, uint32_t id_pos, uint32_t id_neg, uint32_t acc) {
-  const uint64_t A0 = a, A1 = a + pa, A2 = a + 2 * pa, A3 = a + 3 * pa;
-  const uint64_t B0 = b, B1 = b + pb, B2 = b + 2 * pb, B3 = b + 3 * pb;
+__device__ __forceinline__ void mma_cplx_bf16x3(uint32_t tacc, uint64_t a_rh, uint64_t a_rl, uint64_t a_ih,
+                                                uint64_t a_il, uint64_t b_s0, uint64_t b_s2, uint32_t idesc,
+                                                uint32_t acc) {
   asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %12, 0;\nsetp.eq.b32 q, 0, 0;\n"
-      // C_re += Re(A) Re(B) - Im(A) Im(B)
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %6, %10, p;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %7, %10, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %6, %10, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %8, %11, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %9, %11, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %8, %11, q;\n"
-      // C_im += Re(A) Im(B) + Im(A) Re(B)
-      "tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %8, %10, p;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %9, %10, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %8, %10, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %6, %10, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %7, %10, q;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%1], %5, %6, %10, q;\n}\n"
-      ::"r"(t_re), "r"(t_im), "l"(A0), "l"(A1), "l"(A2), "l"(A3), "l"(B0), "l"(B1), "l"(B2), "l"(B3),
-        "r"(id_pos), "r"(id_neg), "r"(acc));
+      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %7, 0;\nsetp.eq.b32 q, 0, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %6, %8, p;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %6, %8, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %5, %8, q;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %5, %8, q;\n}\n"
+      ::"r"(tacc), "l"(a_rh), "l"(a_rl), "l"(a_ih), "l"(a_il), "l"(b_s0), "l"(b_s2), "r"(acc), "r"(idesc));
 }
 
+// 16 consecutive FP32 columns of the warp's 32 TMEM lanes (one row per lane); the caller waits
+// with tcgen05.wait::ld before reading the registers.
+__device__ __forceinline__ void tmem_ld16(uint32_t* v, uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+               : "r"(taddr));
+}
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -176,21 +172,22 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // Pack FP64 complex blocks into panels. Each job: src element offset, src row stride,
 // transpose flag (0: panel row r, col k = src[r * ld + k]; 1: = src[k * ld + r]), rows, K,
-// destination panel byte offset, row tile height (128 for A, the tile column count for B), nkt.
-// One thread writes one 16-byte chunk of a panel row in every plane: 4 consecutive K values
-// (TF32) or 8 (BF16). For transposed sources consecutive threads take consecutive panel rows,
-// so each of the chunk's reads is coalesced; K beyond the block is written as zero padding.
-// A CTA takes one piece (kPackPiece chunks of one job) at a time, so large blocks spread over
-// the whole grid. The BF16 split is done in FP32 after one conversion of each value (hi =
-// bf16(x), lo = bf16(x - hi), with x - hi exact in FP32): the split's error, ~2^-17 |x| from
-// rounding lo, is the same as splitting in FP64, and the FP64 pipe (2 ops per clock per SM)
-// only converts.
+// destination panel byte offset, row tile height (128 for A, the tile column count for B), nkt,
+// padded panel rows, first piece, format (0: A planes, 1: B planes with the negated imaginary
+// parts), and the block's first row and first K inside the panel (row0, k0; k0 a multiple of
+// the chunk's K). One thread writes one 16-byte chunk of a panel row in every plane: 4
+// consecutive K values (TF32) or 8 (BF16). For transposed sources consecutive threads take
+// consecutive panel rows, so each of the chunk's reads is coalesced; K beyond the block is
+// written as zero padding. A CTA takes one piece (kPackPiece chunks of one job) at a time, so
+// large blocks spread over the whole grid. The BF16 split is done in FP32 after one
+// conversion of each value (hi = bf16(x), lo = bf16(x - hi), with x - hi exact in FP32): the
+// split's error, ~2^-17 |x| from rounding lo, is the same as splitting in FP64, and the FP64
+// pipe (2 ops per clock per SM) only converts. Negation is exact in both formats.
 __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ dst, const int64_t* __restrict__ jobs,
                        int njobs, int64_t npieces, int prec) {
   const bool tf32 = prec == TC_TF32;
   const int kc = tf32 ? 4 : 8;                   // K values per 16-byte chunk
   const int kpt = tf32 ? 32 : 64;                // K values per 128-byte row
-  const int planes = tf32 ? 2 : 4;
   for (int64_t pc = blockIdx.x; pc < npieces; pc += gridDim.x) {
     int lo = 0, hi = njobs - 1;                  // the last job whose first piece is <= pc
     while (lo < hi) {
@@ -199,7 +196,8 @@ __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ ds
     }
     const int64_t* d = jobs + TCJ * lo;
     const int64_t s_off = d[0], ld = d[1], trans = d[2], rows = d[3], K = d[4], p_off = d[5], rowtile = d[6],
-                  nkt = d[7], npad = d[8];
+                  nkt = d[7], npad = d[8], bfmt = d[10], row0 = d[11], kbase = d[12];
+    const int planes = bfmt ? tc_bplanes(prec) : tc_aplanes(prec);
     const int64_t nch = (K + kc - 1) / kc;       // chunks per row
     const int64_t e0 = (pc - d[9]) * kPackPiece;
     const int64_t e1 = e0 + kPackPiece < rows * nch ? e0 + kPackPiece : rows * nch;
@@ -207,32 +205,39 @@ __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ ds
       int64_t r, ch;
       if (trans) { ch = e / rows; r = e % rows; }   // consecutive threads: consecutive rows
       else { r = e / nch; ch = e % nch; }           // consecutive threads: consecutive chunks
-      const int64_t k0 = ch * kc;
-      const int64_t rt = r / rowtile, kt = k0 / kpt;
+      const int64_t k0 = ch * kc;                   // within the block
+      const int64_t pr = row0 + r, pk = kbase + k0; // within the panel
+      const int64_t rt = pr / rowtile, kt = pk / kpt;
       const int64_t nrow = npad - rt * rowtile < rowtile ? npad - rt * rowtile : rowtile;
       const int64_t tile_bytes = nrow * 128;       // one plane of this row tile
       uint8_t* tile = dst + p_off + rt * nkt * planes * rowtile * 128 + kt * planes * tile_bytes;
-      const uint32_t off = sw128((uint32_t)(r % rowtile), (uint32_t)((k0 % kpt) * (tf32 ? 4 : 2)));
+      const uint32_t off = sw128((uint32_t)(pr % rowtile), (uint32_t)((pk % kpt) * (tf32 ? 4 : 2)));
       if (tf32) {
         float4 re, im;
-        float* pr = (float*)&re;
-        float* pi = (float*)&im;
+        float* pre = (float*)&re;
+        float* pim = (float*)&im;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int64_t k = k0 + q;
           double2 v = make_double2(0.0, 0.0);
           if (k < K) v = trans ? src[s_off + k * ld + r] : src[s_off + r * ld + k];
-          pr[q] = tf32_rna((float)v.x);
-          pi[q] = tf32_rna((float)v.y);
+          pre[q] = tf32_rna((float)v.x);
+          pim[q] = tf32_rna((float)v.y);
         }
-        *(float4*)(tile + off) = re;
-        *(float4*)(tile + tile_bytes + off) = im;
+        if (bfmt) {    // [-im, re, im]
+          const float4 nim = make_float4(-im.x, -im.y, -im.z, -im.w);
+          *(float4*)(tile + off) = nim;
+          *(float4*)(tile + tile_bytes + off) = re;
+          *(float4*)(tile + 2 * tile_bytes + off) = im;
+        } else {       // [re, im]
+          *(float4*)(tile + off) = re;
+          *(float4*)(tile + tile_bytes + off) = im;
+        }
       } else {
-        uint4 pl[4];
-        __nv_bfloat16* b0 = (__nv_bfloat16*)&pl[0];
-        __nv_bfloat16* b1 = (__nv_bfloat16*)&pl[1];
-        __nv_bfloat16* b2 = (__nv_bfloat16*)&pl[2];
-        __nv_bfloat16* b3 = (__nv_bfloat16*)&pl[3];
+        uint4 pl[6];   // re_hi, re_lo, im_hi, im_lo, -im_hi, -im_lo
+        __nv_bfloat16* b[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) b[q] = (__nv_bfloat16*)&pl[q];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int64_t k = k0 + q;
@@ -241,13 +246,23 @@ __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ ds
           const float xr = __double2float_rn(v.x), xi = __double2float_rn(v.y);
           const __nv_bfloat16 rh = __float2bfloat16_rn(xr);
           const __nv_bfloat16 ih = __float2bfloat16_rn(xi);
-          b0[q] = rh;
-          b1[q] = __float2bfloat16_rn(__fsub_rn(xr, __bfloat162float(rh)));
-          b2[q] = ih;
-          b3[q] = __float2bfloat16_rn(__fsub_rn(xi, __bfloat162float(ih)));
+          const __nv_bfloat16 rl = __float2bfloat16_rn(__fsub_rn(xr, __bfloat162float(rh)));
+          const __nv_bfloat16 il = __float2bfloat16_rn(__fsub_rn(xi, __bfloat162float(ih)));
+          b[0][q] = rh;
+          b[1][q] = rl;
+          b[2][q] = ih;
+          b[3][q] = il;
+          b[4][q] = __hneg(ih);
+          b[5][q] = __hneg(il);
         }
+        if (bfmt) {    // [-im_hi, -im_lo, re_hi, re_lo, im_hi, im_lo]
+          const int order[6] = {4, 5, 0, 1, 2, 3};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) *(uint4*)(tile + q * tile_bytes + off) = pl[q];
+          for (int q = 0; q < 6; ++q) *(uint4*)(tile + q * tile_bytes + off) = pl[order[q]];
+        } else {       // [re_hi, re_lo, im_hi, im_lo]
+#pragma unroll
+          for (int q = 0; q < 4; ++q) *(uint4*)(tile + q * tile_bytes + off) = pl[q];
+        }
       }
     }
   }
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int prec = g.prec;
-  const int planes = tc_planes(prec);
+  const int aplanes = tc_aplanes(prec), bplanes = tc_bplanes(prec), groups = tc_groups(prec);
   const int kpt = tc_kpt(prec);                    // K values per 128-byte row
   const int kstep = prec == TC_TF32 ? 8 : 16;      // K per MMA instruction
   const int ntile = g.ntile;                       // B rows (output columns) per tile
@@ -391,14 +406,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       for (int64_t s = 0; s < task[6] && ok; ++s) {
         const int64_t* sg = g.segs + TCS * (task[5] + s);
         const int64_t nkt = sg[2];
-        const uint8_t* a = g.a_base + sg[0] + rt * nkt * planes * (int64_t)(128 * 128);
-        const uint8_t* b = g.b_base + sg[1] + nt * nkt * planes * (int64_t)ntile * 128;
+        const uint8_t* a = g.a_base + sg[0] + rt * nkt * aplanes * (int64_t)(128 * 128);
+        const uint8_t* b = g.b_base + sg[1] + nt * nkt * bplanes * (int64_t)ntile * 128;
         for (int64_t kt = 0; kt < nkt && ok; ++kt) {
           ok = mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1, g.err, 11, g.wait_ns);
           if (!ok) break;
-          const uint32_t abytes = planes * 128 * 128, bbytes = (uint32_t)(planes * nrow * 128);
+          const uint32_t abytes = aplanes * 128 * 128, bbytes = (uint32_t)(bplanes * nrow * 128);
           const uint32_t sa = smem_u32(smem + stage * stage_bytes);
-          const uint32_t sb = sa + planes * 128 * 128;
+          const uint32_t sb = sa + abytes;
           mbar_expect_tx(smem_u32(&bar_full[stage]), abytes + bbytes);
           bulk_g2s(sa, a + kt * abytes, abytes, smem_u32(&bar_full[stage]));
           bulk_g2s(sb, b + kt * (int64_t)bbytes, bbytes, smem_u32(&bar_full[stage]));
@@ -430,8 +445,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       ok = mbar_wait(smem_u32(&bar_acc_empty[slot]), ((acc_phase >> slot) & 1) ^ 1, g.err, 12, g.wait_ns);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t t_re = tmem + 256 * slot, t_im = t_re + 128;
-      const uint32_t id_pos = make_idesc(prec, nrow, false), id_neg = make_idesc(prec, nrow, true);
+      const uint32_t tacc = tmem + 256 * slot;   // groups x nrow <= 256 columns
+      const uint32_t idesc = make_idesc(prec, groups * nrow, false);
       bool first = true;
       for (int64_t s = 0; s < task[6] && ok; ++s) {
         const int64_t nkt = g.segs[TCS * (task[5] + s) + 2];
@@ -440,7 +455,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t sa = smem_u32(smem + stage * stage_bytes);
-          const uint32_t sb = sa + planes * 128 * 128;
+          const uint32_t sb = sa + aplanes * 128 * 128;
           // descriptors of the stage's planes; a K step of 32 bytes adds 2 to the address field
           // (smem address / 16 in bits 0-13, no carry below 256 KB), so each instruction's
           // descriptors are one 64-bit add away from these
@@ -451,9 +466,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
             const uint64_t ko = 2 * ks;
             const uint32_t acc = first ? 0u : 1u;
             if (prec == TC_TF32)
-              mma4_tf32(t_re, t_im, a0 + ko, a0 + pa + ko, b0 + ko, b0 + pb + ko, id_pos, id_neg, acc);
+              mma_cplx_tf32(tacc, a0 + ko, a0 + pa + ko, b0 + ko, b0 + pb + ko, idesc, acc);
             else
-              mma12_bf16x3(t_re, t_im, a0 + ko, pa, b0 + ko, pb, id_pos, id_neg, acc);
+              mma_cplx_bf16x3(tacc, a0 + ko, a0 + pa + ko, a0 + 2 * pa + ko, a0 + 3 * pa + ko, b0 + ko,
+                              b0 + 2 * pb + ko, idesc, acc);
             first = false;
           }
           mma_commit(smem_u32(&bar_empty[stage]));
@@ -487,19 +503,23 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       const int64_t row = rt * 128 + quad * 32 + lane;
       const int64_t c0 = nt * ntile;
       const int64_t ncols = N - c0 < ntile ? N - c0 : ntile;
-      const uint32_t t_re = tmem + 256 * slot + ((uint32_t)(quad * 32) << 16);
+      const uint32_t tacc = tmem + 256 * slot + ((uint32_t)(quad * 32) << 16);
+      const int64_t npad = ((N + 15) / 16) * 16;
+      const uint32_t nrow = (uint32_t)(npad - c0 < ntile ? npad - c0 : ntile);   // columns of a group
       for (int64_t cb = 0; cb < ncols; cb += 16) {
-        uint32_t vr[16], vi[16];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                     : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
-                       "=r"(vr[7]), "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]),
-                       "=r"(vr[14]), "=r"(vr[15])
-                     : "r"(t_re + (uint32_t)cb));
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                     : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
-                       "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]),
-                       "=r"(vi[14]), "=r"(vi[15])
-                     : "r"(t_re + 128u + (uint32_t)cb));
+        // group g of the accumulator sits at columns g * nrow; split BF16 adds the hi and lo
+        // groups of each part
+        uint32_t vr[16], vi[16], wr[16], wi[16];
+        const uint32_t c = (uint32_t)cb;
+        if (groups == 2) {
+          tmem_ld16(vr, tacc + c);
+          tmem_ld16(vi, tacc + nrow + c);
+        } else {
+          tmem_ld16(vr, tacc + c);
+          tmem_ld16(wr, tacc + nrow + c);
+          tmem_ld16(vi, tacc + 2 * nrow + c);
+          tmem_ld16(wi, tacc + 3 * nrow + c);
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (row < M) {
           const int nvalid = (int)(ncols - cb < 16 ? ncols - cb : 16);
@@ -509,14 +529,21 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
             re[j] = __uint_as_float(vr[j]);
             im[j] = __uint_as_float(vi[j]);
           }
-          const int64_t c = c0 + cb;
+          if (groups == 4) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              re[j] = __fadd_rn(re[j], __uint_as_float(wr[j]));
+              im[j] = __fadd_rn(im[j], __uint_as_float(wi[j]));
+            }
+          }
+          const int64_t col = c0 + cb;
           if (task[7] == 1) {
-            double2* dst = g.f_out + task[2] + row * task[3] + c;
+            double2* dst = g.f_out + task[2] + row * task[3] + col;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
               if (j < nvalid) dst[j] = make_double2((double)re[j], (double)im[j]);
           } else {
-            put_packed16(g.z_out + task[2], task[8], planes, prec, row, c, re, im, nvalid);
+            put_packed16(g.z_out + task[2], task[8], aplanes, prec, row, col, re, im, nvalid);
           }
         }
       }
@@ -560,9 +587,7 @@ cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t*
   cudaError_t ea = tc_gemm_init();
   if (ea != cudaSuccess) return ea;
   const int smem = tc_smem_bytes(prec, cfg);
-  if (cfg.stages < 1 || cfg.stages > kTcMaxStages || cfg.ntile < 16 || cfg.ntile > 128 || cfg.ntile % 16 ||
-      smem > kTcMaxSmem)
-    return cudaErrorInvalidValue;
+  if (!tc_cfg_ok(prec, cfg) || smem > kTcMaxSmem) return cudaErrorInvalidValue;
   TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, items, cfg.ntile, cfg.stages,
            tc_stage_bytes(prec, cfg.ntile), wait_ns};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;

@@ -11,18 +11,26 @@ enum { TC_TF32 = 1, TC_BF16X3 = 2 };
 enum { TCT = 10 };
 // segment row: a_panel_byte_offset b_panel_byte_offset nkt pad
 enum { TCS = 4 };
-// pack job row: src_off ld trans rows K panel_byte_offset rowtile nkt npad first_piece, where
-// the job's 16-byte chunks (rows x ceil(K / chunk K)) are cut into pieces of kPackPiece and
-// first_piece is the prefix of the earlier jobs' pieces
-enum { TCJ = 10 };
+// pack job row: src_off ld trans rows K panel_byte_offset rowtile nkt npad first_piece format
+// row0 k0, where the job's 16-byte chunks (rows x ceil(K / chunk K)) are cut into pieces of
+// kPackPiece and first_piece is the prefix of the earlier jobs' pieces; format 0 writes the
+// A planes, 1 the B planes; row0 / k0 place the block inside a larger panel (multiples of
+// the chunk's K for k0)
+enum { TCJ = 13 };
 constexpr int kPackPiece = 1024;
 
-struct TcPanelGeom {
-  int64_t nkt;
-  int planes;
-};
-
-__host__ __device__ inline int tc_planes(int prec) { return prec == TC_TF32 ? 2 : 4; }
+// Planes of a packed tile. A operands (LW, Z): re, im (TF32) or re_hi, re_lo, im_hi, im_lo
+// (split BF16). B operands (theta, WR) carry their imaginary planes negated as well, ordered
+// so that two windows of consecutive planes are the B operands of one complex product:
+//   TF32    S = [-im, re, im]:  C += A_re x S[1..2] + A_im x S[0..1]
+//   BF16X3  S = [-im_hi, -im_lo, re_hi, re_lo, im_hi, im_lo]:
+//           C += (A_re_hi + A_re_lo) x S[2..5] + (A_im_hi + A_im_lo) x S[0..3]
+// The accumulator then holds the column groups (re, im) or (re_hi, re_lo, im_hi, im_lo) of
+// the output side by side, and the epilogue adds each part's pieces.
+__host__ __device__ inline int tc_aplanes(int prec) { return prec == TC_TF32 ? 2 : 4; }
+__host__ __device__ inline int tc_bplanes(int prec) { return prec == TC_TF32 ? 3 : 6; }
+// accumulator column groups of one output tile (one per B plane of a window)
+__host__ __device__ inline int tc_groups(int prec) { return prec == TC_TF32 ? 2 : 4; }
 __host__ __device__ inline int tc_kpt(int prec) { return prec == TC_TF32 ? 32 : 64; }   // K per 128-byte row
 // Tile configuration of the grouped GEMM, picked per problem class by the autotuner
 // (tc_host.cu): B rows (output columns) per tile, pipeline stages, task order (0: charge
@@ -31,13 +39,21 @@ struct TcCfg {
   int ntile, stages, order;
 };
 constexpr int kTcMaxStages = 4;
-constexpr int kTcMaxSmem = 220 * 1024;   // dynamic; the kernel's static shared memory comes on top
+// dynamic shared memory; with the kernel's ~120 bytes of static shared memory it stays below
+// the 227 KB a block may use
+constexpr int kTcMaxSmem = 225 * 1024;
 // shared-memory stage: A planes x 16 KB + B planes x ntile x 128 B
 __host__ __device__ inline int tc_stage_bytes(int prec, int ntile) {
-  return tc_planes(prec) * (128 * 128 + ntile * 128);
+  return tc_aplanes(prec) * 128 * 128 + tc_bplanes(prec) * ntile * 128;
 }
 __host__ __device__ inline int tc_smem_bytes(int prec, TcCfg c) { return c.stages * tc_stage_bytes(prec, c.ntile) + 1024; }
+// the accumulator of one tile spans groups x ntile FP32 columns: at most 256, so that two
+// tiles (two slots) fit the 512 columns of tensor memory
+__host__ __device__ inline bool tc_cfg_ok(int prec, TcCfg c) {
+  return c.stages >= 1 && c.stages <= kTcMaxStages && c.ntile >= 16 && c.ntile % 16 == 0 &&
+         tc_groups(prec) * c.ntile <= 256 && tc_smem_bytes(prec, c) <= kTcMaxSmem;
+}
 // default configuration (also the first candidate of the autotuner)
-inline TcCfg tc_default_cfg(int prec) { return prec == TC_TF32 ? TcCfg{128, 3, 0} : TcCfg{64, 2, 0}; }
+inline TcCfg tc_default_cfg(int prec) { return prec == TC_TF32 ? TcCfg{128, 2, 0} : TcCfg{64, 2, 0}; }
 
 }  // namespace mrd

@@ -75,7 +75,7 @@ int64_t b_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 1
 int build(mrd_heff* h, int prec, TcCfg cfg) {
   mrd_ctx* ctx = h->ctx;
   Tc* T = h->tc;
-  const int planes = tc_planes(prec), kpt = tc_kpt(prec), ntile = cfg.ntile;
+  const int aplanes = tc_aplanes(prec), bplanes = tc_bplanes(prec), kpt = tc_kpt(prec), ntile = cfg.ntile;
   const int64_t* c = h->counts;
   PanelIndex lw_map, wr_map, th_map, z_map;
   lw_map.v.reserve(c[C_NLW]);
@@ -87,16 +87,16 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     const int64_t* r = &h->lw_host[LWF * k];
     const int64_t rows = r[5], K = r[6], nkt = (K + kpt - 1) / kpt;
     lw_map.add(r[7], {lw_b, nkt});
-    j_lw.insert(j_lw.end(), {r[7], K, 0, rows, K, lw_b, 128, nkt, round_up(rows, 128), 0});
-    lw_b += a_bytes(rows, nkt, planes);
+    j_lw.insert(j_lw.end(), {r[7], K, 0, rows, K, lw_b, 128, nkt, round_up(rows, 128), 0, 0, 0, 0});
+    lw_b += a_bytes(rows, nkt, aplanes);
   }
   // folded right operand WR(w', s2, s2', b): B panel of its transpose, rows d_b', K d_b
   for (int64_t k = 0; k < c[C_NWR]; ++k) {
     const int64_t* r = &h->wr_host[WRF * k];
     const int64_t K = r[5], rows = r[6], nkt = (K + kpt - 1) / kpt;
     wr_map.add(r[7], {wr_b, nkt});
-    j_wr.insert(j_wr.end(), {r[7], rows, 1, rows, K, wr_b, ntile, nkt, round_up(rows, 16), 0});
-    wr_b += b_bytes(rows, nkt, planes);
+    j_wr.insert(j_wr.end(), {r[7], rows, 1, rows, K, wr_b, ntile, nkt, round_up(rows, 16), 0, 1, 0, 0});
+    wr_b += b_bytes(rows, nkt, bplanes);
   }
   // theta block (s1, a) x (s2, b) of every middle sector: B panel of its transpose, rows d_b, K d_a
   const std::vector<int64_t>& mid = h->mid_host;
@@ -110,8 +110,8 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
         const int64_t rows = h->right[3 * r[8 + s2] + 2];
         const int64_t src = r[4] + (s1 ? r[7] : 0) * r[3] + (s2 ? r[10] : 0);
         th_map.add(src, {th_b, nkt});
-        j_th.insert(j_th.end(), {src, r[3], 1, rows, K, th_b, ntile, nkt, round_up(rows, 16), 0});
-        th_b += b_bytes(rows, nkt, planes);
+        j_th.insert(j_th.end(), {src, r[3], 1, rows, K, th_b, ntile, nkt, round_up(rows, 16), 0, 1, 0, 0});
+        th_b += b_bytes(rows, nkt, bplanes);
       }
     }
   }
@@ -136,7 +136,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
         const int64_t K = h->right[3 * rin[8 + s2] + 2], nkt = (K + kpt - 1) / kpt;
         const int64_t key = zr[5] + (s1p ? rout[7] : 0) * rin[3] + (s2 ? rin[10] : 0);
         z_map.add(key, {z_b, nkt});
-        z_b += a_bytes(rows, nkt, planes);
+        z_b += a_bytes(rows, nkt, aplanes);
       }
     }
   }
@@ -234,18 +234,17 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
         const int64_t M = tk[i], N = tk[i + 1];
         for (int64_t k = 0; k < tk[i + 6]; ++k) {
           const int64_t* q = &sg[TCS * (tk[i + 5] + k)];
-          if (q[0] < 0 || q[0] + a_bytes(M, q[2], planes) > alen) return false;
-          if (q[1] < 0 || q[1] + b_bytes(N, q[2], planes) > blen) return false;
+          if (q[0] < 0 || q[0] + a_bytes(M, q[2], aplanes) > alen) return false;
+          if (q[1] < 0 || q[1] + b_bytes(N, q[2], bplanes) > blen) return false;
         }
-        if (zout && (tk[i + 2] < 0 || tk[i + 2] + a_bytes(M, tk[i + 8], planes) > z_b || tk[i + 8] * kpt < N))
+        if (zout && (tk[i + 2] < 0 || tk[i + 2] + a_bytes(M, tk[i + 8], aplanes) > z_b || tk[i + 8] * kpt < N))
           return false;
       }
       return true;
     };
     if (!chk(t1, s1, lw_b, th_b, true) || !chk(t2, s2, z_b, wr_b, false))
       return mrd_fail(ctx, MRD_E_STATE, "tc: internal panel table check failed");
-    if (tc_smem_bytes(prec, cfg) > kTcMaxSmem || cfg.stages < 1 || cfg.stages > kTcMaxStages)
-      return mrd_fail(ctx, MRD_E_STATE, "tc: stage does not fit");
+    if (!tc_cfg_ok(prec, cfg)) return mrd_fail(ctx, MRD_E_STATE, "tc: tile configuration does not fit");
   }
   // device buffers
   delete h->tc;
@@ -318,8 +317,8 @@ namespace {
 
 // Candidate tile configurations per precision (all fit the 227 KB of shared memory).
 std::vector<TcCfg> candidates(int prec) {
-  if (prec == TC_TF32) return {{128, 3, 0}, {64, 4, 0}, {128, 3, 1}, {64, 4, 1}};
-  return {{64, 2, 0}, {32, 2, 0}, {64, 2, 1}, {32, 2, 1}};
+  if (prec == TC_TF32) return {{128, 2, 0}, {64, 4, 0}, {128, 2, 1}, {64, 4, 1}};
+  return {{64, 2, 0}, {48, 2, 0}, {64, 2, 1}, {48, 2, 1}};
 }
 
 // Problem class of an H_eff for the tuning cache: precision, size of theta (powers of two)

@@ -106,7 +106,7 @@ def test_autotuned_tile_configuration(ctx, prec):
         h.close()
     assert cfgs[0][3] == 0 and cfgs[1][3] in (1, 2) and cfgs[2][3] == 2
     assert cfgs[1][:3] == cfgs[2][:3]
-    assert cfgs[1][0] in (32, 64, 128) and cfgs[1][1] in (2, 3, 4) and cfgs[1][2] in (0, 1)
+    assert cfgs[1][0] in (32, 48, 64, 128) and cfgs[1][1] in (2, 3, 4) and cfgs[1][2] in (0, 1)
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
 
 
