@@ -361,3 +361,60 @@ def env_right_update_block(sec_l, sec_r, m, mod, cl, cm, w_entries, rflat, b_blo
             continue
         out += v * (b_blocks[(ci, s)] @ rblk[(wp, bi)][1] @ b_blocks[(cpi, sp)].conj().T)
     return out
+
+
+def two_site_update(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, tflat, chi, cutoff=1e-14,
+                    kmax=30, tol=1e-13, lanczos=None):
+    """One two-site update of standard two-site DMRG (the paper defers the algorithm to its
+    refs. W92, S2005, S2011), block by block, moving the centre to the right:
+      1. the lowest eigenpair of H_eff (heff_apply) by Lanczos from theta
+         (oracle.dmrg.lanczos_ground, or the `lanczos(matvec, v0)` given);
+      2. the SVD of every middle-charge block of the ground vector (the Schmidt decomposition
+         across the centre bond, Sec. III.C);
+      3. the global truncation to at most chi singular values above cutoff * s_max, taken in
+         the order (value descending, block ascending, index ascending), renormalised so that
+         sum s^2 = 1;
+      4. the new left-canonical tensor A = U (rows (s1, a) of each block) and the left
+         environment of the new bond, L' = A^+ L W_i A (env_left_update_block).
+    Returns a dict: energy, matvecs, discarded weight, the new bond's BondSectors, the
+    Schmidt values per new sector, A as {(a_index, s1): block}, and L' in the
+    env_left_layout(new bond, cm) layout."""
+    from oracle import dmrg as D
+    lay = theta_layout(left, right, m1, m2, mod)
+
+    def mv(v):
+        return heff_apply(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, v)
+    if lanczos is None:
+        e, g, nmv = D.lanczos_ground(mv, tflat, kmax=kmax, tol=tol)
+    else:
+        e, g, nmv = lanczos(mv, tflat)
+    svds = []
+    for bi, m in enumerate(lay):
+        blk = g[m["offset"]: m["offset"] + m["rowdim"] * m["coldim"]].reshape(m["rowdim"], m["coldim"])
+        u, s, vh = np.linalg.svd(blk, full_matrices=False)
+        svds.append((u, s, vh))
+    allv = [(-s[k], bi, k) for bi, (u, s, vh) in enumerate(svds) for k in range(len(s))]
+    allv.sort()
+    smax = -allv[0][0]
+    kept = [t for t in allv[:chi] if -t[0] > cutoff * smax]
+    total = sum(t[0] ** 2 for t in allv)
+    keep_w = sum(t[0] ** 2 for t in kept)
+    nkeep = {}
+    for _, bi, k in kept:
+        nkeep[bi] = max(nkeep.get(bi, 0), k + 1)
+    new_secs = [(lay[bi]["q"], nkeep[bi]) for bi in sorted(nkeep)]
+    bond = BondSectors(new_secs)
+    norm = np.sqrt(keep_w)
+    schmidt = {lay[bi]["q"]: svds[bi][1][:nkeep[bi]] / norm for bi in sorted(nkeep)}
+    a_blocks = {}
+    for bi in sorted(nkeep):
+        u = svds[bi][0][:, :nkeep[bi]]
+        for s1, ai, da, ro in lay[bi]["rows"]:
+            a_blocks[(ai, s1)] = u[ro:ro + da]
+    lay_new = env_left_layout(bond, cm, mod)
+    lnew = np.zeros(env_size(lay_new), dtype=np.complex128)
+    for w, ci, cpi, off, d0, d1 in lay_new:
+        lnew[off:off + d0 * d1] = env_left_update_block(left, bond, m1, mod, cl, cm, wi, lflat, a_blocks,
+                                                        (w, ci)).reshape(-1)
+    return {"energy": e, "matvecs": nmv, "discarded": 1.0 - keep_w / total, "bond": bond, "schmidt": schmidt,
+            "a_blocks": a_blocks, "lenv": lnew}

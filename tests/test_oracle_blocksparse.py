@@ -322,3 +322,60 @@ def test_env_update_blocks_equal_dense(seed, ly, m, dl, dr):
         got = B.env_right_update_block(sec0, sec1, m, ly, cl, cm, W, rflat, bblocks, (w, ci))
         want = R0[w, o0[ci]:o0[ci] + d0, o0[cpi]:o0[cpi] + d1]
         assert np.max(np.abs(got - want), initial=0.0) < 1e-13 * scale
+
+
+def test_two_site_update_matches_dense_restatement():
+    """oracle.blocksparse.two_site_update against the dense symmetry-free steps of
+    oracle.dmrg on the same operands: the Lanczos energy equals <g|H_eff|g> of the returned
+    ground vector in the dense contraction; the kept Schmidt values are the chi largest
+    singular values of the dense theta matrix (rows (a, s1), columns (s2, b)) renormalised;
+    the projector A A^+ equals that of the dense SVD truncated to chi (phase-free); and the new
+    left environment equals the dense env_left_update of the densified A."""
+    seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr = 3, 5, 60, 50, 4, 0, 6, 5, 8
+    case = _random_case(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr)
+    left, right, cl, cm, cr, wi, wj, lay, ll, rl, lflat, rflat, tflat = case
+    L, Wi, Wj, R, to_dense = _dense(left, right, m1, m2, ly, cl, cm, cr, wi, wj, lay, ll, rl, lflat, rflat, tflat)
+    # Hermitian operator: H_eff + H_eff^+ as a dense matrix, applied through the block code as
+    # (H + H^+) v = H v + (H^+ v); the symmetrisation keeps the Lanczos recurrence meaningful
+    n = B.theta_size(lay)
+    hmat = np.stack([B.heff_apply(left, right, m1, m2, ly, cl, cm, cr, wi, wj, lflat, rflat, e)
+                     for e in np.eye(n, dtype=complex)], axis=1)
+    herm = hmat + hmat.conj().T
+
+    def lanczos(mv, v0):
+        return D.lanczos_ground(lambda v: herm @ v, v0, kmax=30, tol=1e-13)
+    chi = 40
+    out = B.two_site_update(left, right, m1, m2, ly, cl, cm, cr, wi, wj, lflat, rflat, tflat, chi, lanczos=lanczos)
+    w = np.linalg.eigvalsh(herm)
+    e_ref, g, _ = lanczos(None, tflat)
+    # the energy is the Ritz value of the returned vector, variational
+    assert abs(out["energy"] - np.vdot(g, herm @ g).real) < 1e-10 * abs(w[0])
+    assert out["energy"] >= w[0] - 1e-10 * abs(w[0])
+    # dense theta matrix of the ground vector: rows (a, s1), columns (s2, b)
+    ol, orr = _offsets(left.dims), _offsets(right.dims)
+    T = to_dense(g)                                   # [a, s1, s2, b]
+    tm = T.reshape(ol[-1] * 2, 2 * orr[-1])
+    u, s, vh = np.linalg.svd(tm, full_matrices=False)
+    kept = s[:chi] / np.linalg.norm(s[:chi])
+    got = np.sort(np.concatenate(list(out["schmidt"].values())))[::-1]
+    assert len(got) == chi
+    assert np.max(np.abs(got - kept)) < 1e-12
+    assert abs(out["discarded"] - (1 - np.sum(s[:chi] ** 2) / np.sum(s ** 2))) < 1e-12
+    # densified A[a, s1, c] on the new bond
+    bond = out["bond"]
+    ob = _offsets(bond.dims)
+    A = np.zeros((ol[-1], 2, ob[-1]), complex)
+    for (ai, s1), blk in out["a_blocks"].items():
+        qc = B.qadd(left.charges[ai], B.qsite(s1, m1, ly), ly)
+        ci = bond.index[qc]
+        A[ol[ai]:ol[ai + 1], s1, ob[ci]:ob[ci + 1]] = blk
+    am = A.reshape(ol[-1] * 2, ob[-1])
+    # the truncated projector is as well defined as the gap at the cut allows
+    tol_p = 1e-12 + 1e-14 * s[0] / (s[chi - 1] - s[chi])
+    assert np.max(np.abs(am @ am.conj().T - u[:, :chi] @ u[:, :chi].conj().T)) < tol_p
+    lnew = D.env_left_update(L, A, Wi)
+    lay_new = B.env_left_layout(bond, cm, ly)
+    want = np.zeros(B.env_size(lay_new), complex)
+    for wq, ci, cpi, off, d0, d1 in lay_new:
+        want[off:off + d0 * d1] = lnew[wq, ob[cpi]:ob[cpi] + d0, ob[ci]:ob[ci] + d1].reshape(-1)
+    assert np.max(np.abs(out["lenv"] - want)) < 1e-12 * np.max(np.abs(want))
