@@ -222,7 +222,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU measurements
 
-def matvec_throughput(P, ctx, torch, dev, stream, reps=10):
+def matvec_throughput(P, ctx, torch, dev, stream, reps=10, precs=None):
     """H_eff TFLOP/s per precision on the Lx = 20 mid-ring sites, random environments."""
     site = update_centre(LX_MATVEC)
     mpo = P.MPO(None, LX_MATVEC, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, P.MRD_BASIS_MIXED)
@@ -242,6 +242,8 @@ def matvec_throughput(P, ctx, torch, dev, stream, reps=10):
     f_def, f_exec, f1, f2 = h.flops()
     res = {}
     for name, prec in PREC.items():
+        if precs and name not in precs:
+            continue
         n = reps if prec in (1, 2) else 3
         for _ in range(2):
             h.apply(T, out, prec=prec)
@@ -264,7 +266,7 @@ def matvec_throughput(P, ctx, torch, dev, stream, reps=10):
             res[name]["tile_config"] = dict(zip(["cols_per_tile", "stages", "task_order", "source"], h.tc_config()))
     # the per-block baseline: one GEMM launch per output task instead of the grouped launch
     h.set_option(P.MRD_OPT_PER_TASK_LAUNCH, 1)
-    for name in ("bf16x3",):
+    for name in ("bf16x3",) if "bf16x3" in res else ():
         h.apply(T, out, prec=PREC[name])
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -402,6 +404,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fast-restarts", type=int, default=8, help="restarts of the reduced-precision Lanczos")
     ap.add_argument("--only-matvec", action="store_true", help="H_eff throughput only (profiling runs)")
+    ap.add_argument("--precs", default="", help="with --only-matvec: comma-separated precisions (default all)")
     ap.add_argument("--profile-update", action="store_true",
                     help="warm-up updates, then one update inside a CUDA profiler range (ncu --profile-from-start off)")
     args = ap.parse_args()
@@ -433,9 +436,11 @@ def main():
     mixed = P.DMRG.params(chi, 1e-14, 60, 1e-10, PREC["bf16x3"], args.refine, 1e-13, restarts=args.fast_restarts)
     if args.only_matvec:
         set_chi(chi)
-        mv = matvec_throughput(P, ctx, torch, dev, stream)
-        print(json.dumps({"only_matvec": True, "chi": chi, "heff_tflops": {k: mv[k]["tflops"] for k in PREC},
-                          "heff_ms_steps": {k: [mv[k]["ms_step1"], mv[k]["ms_step2"]] for k in PREC}}))
+        precs = [p for p in args.precs.split(",") if p]
+        mv = matvec_throughput(P, ctx, torch, dev, stream, precs=precs)
+        done = [k for k in PREC if k in mv]
+        print(json.dumps({"only_matvec": True, "chi": chi, "heff_tflops": {k: mv[k]["tflops"] for k in done},
+                          "heff_ms_steps": {k: [mv[k]["ms_step1"], mv[k]["ms_step2"]] for k in done}}))
         return 0
 
     if args.profile_update:

@@ -316,6 +316,14 @@ int mrd_dmrg_schmidt(const mrd_dmrg* d, int32_t* bond, int64_t* n, int32_t* nk, 
  * reduced-precision (or FP64) Lanczos matvecs plus 1000 times the FP64 refinement matvecs. */
 int mrd_dmrg_stats(const mrd_dmrg* d, double* energy, double* trunc_err, int32_t* lanczos_iters);
 
+/* Issue rates measured on the context's device, for roofline fractions of the kernels that
+ * run on the CUDA-core pipes (the float-float GEMM and Jacobi sweeps on FP32, the FP64 forms):
+ * out4 = {FP32 fused multiply-add instructions per second, FP64 fused multiply-add
+ * instructions per second, SM count, maximum SM clock in Hz}. Each rate is the best of 5
+ * timed launches of independent multiply-add chains filling every SM; takes a few ms.
+ * (The paper has no counterpart; this supports the measurements.) */
+int mrd_measure_peaks(mrd_ctx* ctx, double* out4);
+
 /* Capacity of the static scratch used by mrd_heff_apply_noalloc, in complex128 elements
  * (64 MiB). */
 #define MRD_NOALLOC_Z_MAX_ELEMS (4194304)

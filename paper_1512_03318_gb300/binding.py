@@ -124,6 +124,7 @@ _SIGS = {
     "mrd_heff_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "mrd_heff_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "mrd_heff_status": (C.c_int, [C.c_void_p]),
+    "mrd_measure_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_heff_tc_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "mrd_dmrg_svd_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_dmrg_schmidt": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -196,6 +197,12 @@ class Context:
     def check(self, rc):
         if rc != 0:
             raise MrdError(rc, lib().mrd_last_error(self.h).decode())
+
+    def measure_peaks(self):
+        """mrd_measure_peaks: (FP32 FMA instr/s, FP64 FMA instr/s, SMs, max SM clock Hz)."""
+        out = (C.c_double * 4)()
+        self.check(lib().mrd_measure_peaks(self.h, out))
+        return tuple(out)
 
     def set_stream(self, stream):
         self.check(lib().mrd_set_stream(self.h, _stream_ptr(stream)))
