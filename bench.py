@@ -185,13 +185,46 @@ def oracle_sample_text(flops, full, t):
             f"included: a lower bound")
 
 
+def oracle_full_update_ly8(chi=1024, matvecs=ORACLE_MATVECS):
+    """Seconds of one complete oracle two-site update (oracle.blocksparse.two_site_update:
+    Lanczos with `matvecs` block-sparse H_eff applications, block SVD, truncation, new left
+    environment) on the Ly = 8 cylinder at chi = 1024 (flux 1/8, t = V = 1, Lx = 16, the centre
+    sites), with the oracle's MPO and seeded random environments and theta of those shapes."""
+    from oracle import blocksparse as B
+    from oracle import dmrg as D
+    from oracle import mpo as M
+    ly, lx, seed = 8, 16, 1234 + 1
+    n = lx * ly
+    site = (lx // 2) * ly + ly // 2 - 1
+    caps = {j: synth.bond_sectors(chi, ly, round(j / ly), synth.substream(seed, 7, j)) for j in (site, site + 2)}
+    mp = M.build_mpo(lx, ly, 1 / 8, T_HOP, V_INT, "mixed")
+    left, right = B.BondSectors(caps[site]), B.BondSectors(caps[site + 2])
+    m1, m2 = site % ly, (site + 1) % ly
+    cl, cm, cr = mp.bond_charges[site], mp.bond_charges[site + 1], mp.bond_charges[site + 2]
+    lay = B.theta_layout(left, right, m1, m2, ly)
+    s = synth.substream(seed, 200)
+    lflat = synth.complex_pm1(synth.substream(s, 8), B.env_size(B.env_left_layout(left, cl, ly)))
+    rflat = synth.complex_pm1(synth.substream(s, 9), B.env_size(B.env_right_layout(right, cr, ly)))
+    tflat = synth.complex_pm1(synth.substream(s, 10), B.theta_size(lay))
+    # a fixed number of Lanczos steps (random environments: the stopping rule plays no part)
+    lz = lambda mv, v0: D.lanczos_ground(mv, v0, kmax=matvecs, tol=0.0)
+    t0 = time.perf_counter()
+    out = B.two_site_update(left, right, m1, m2, ly, cl, cm, cr, mp.entries[site], mp.entries[site + 1], lflat, rflat,
+                            tflat, chi, lanczos=lz)
+    return time.perf_counter() - t0, out["matvecs"], n
+
+
 def cpu_baseline(n_steps=3):
     step, flops, full = oracle_step_factory()
     step()
     times = [step() for _ in range(n_steps)]
     t = statistics.median(times)
+    t8, mv8, _ = oracle_full_update_ly8()
     return {"value": oracle_s_per_update(t, flops, full), "unit": "s/update", "cores": len(os.sched_getaffinity(0)),
-            "kind": "oracle", "sample": oracle_sample_text(flops, full, t) + f"; median of {n_steps} after 1 warm-up"}
+            "kind": "oracle", "sample": oracle_sample_text(flops, full, t) + f"; median of {n_steps} after 1 warm-up",
+            "full_update_ly8_chi1024_s": t8, "full_update_ly8_matvecs": mv8,
+            "full_update_note": "one complete oracle update (Lanczos, block SVD, truncation, environment) at Ly=8 "
+                                "chi=1024, timed as it is"}
 
 
 def run_reference(args):
@@ -388,8 +421,148 @@ def per_update_value(seconds, steps, world):
     return seconds / steps / world
 
 
-def make_state(P, ctx, mpo, chi, caps, seed):
-    return P.DMRG(ctx, mpo, LX_UPDATE, 0, chi, seed=seed, center=update_centre(LX_UPDATE), caps=caps)
+def make_state(P, ctx, mpo, chi, caps, seed, lx=None, center=None):
+    lx = LX_UPDATE if lx is None else lx
+    return P.DMRG(ctx, mpo, lx, 0, chi, seed=seed, center=update_centre(lx) if center is None else center, caps=caps)
+
+
+def mixed_params(P, chi, refine=1, restarts=8, refine_prec=None, svd_mode=None, prec=None):
+    """The benchmarked reduced-precision form: split-BF16 tensor-core Lanczos (60 steps per run,
+    restarted while the Ritz value moves by more than 1e-10), the ground vector refined with
+    float-float matvecs, FP32 + float-float Jacobi SVD, float-float environments."""
+    return P.DMRG.params(chi, 1e-14, 60, 1e-10, PREC["bf16x3"] if prec is None else prec, refine, 1e-13,
+                         restarts=restarts, svd_mode=svd_mode, refine_prec=refine_prec)
+
+
+def fp64_params(P, chi, tol=1e-12, restarts=6):
+    """The plain FP64 form: FP64 Lanczos restarted until the Ritz value settles to tol, FP64
+    Jacobi SVD, FP64 environments."""
+    return P.DMRG.params(chi, 1e-14, 30, tol, PREC["fp64"], 0, 1e-14, restarts=restarts)
+
+
+def heff_of_bonds(P, ctx, mpo, i, left, right):
+    """The H_eff handle of an update of sites (i, i+1) whose outer bonds have these sectors
+    (no environments: used for its tables and flop counts)."""
+    ly = mpo.modulus if mpo.modulus > 1 else 1
+    i_idx, i_val = mpo.site(i)
+    j_idx, j_val = mpo.site(i + 1)
+    return P.Heff(ctx, left, right, i % ly if ly > 1 else 0, (i + 1) % ly if ly > 1 else 0, mpo.modulus,
+                  mpo.bond(i), mpo.bond(i + 1), mpo.bond(i + 2), i_idx, i_val, j_idx, j_val)
+
+
+def traffic_from_profile(kernel_sources):
+    """DRAM bytes per H_eff application of the tensor-core GEMM from the committed ncu summary,
+    if that summary was taken from the current sources (hash of the kernel files), else None."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "k_tc_gemm_bf16x3_ly10_chi3200_dram.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no ncu summary"
+    h = hashlib.sha256()
+    for f in kernel_sources:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    m_sha = re.search(r"sources sha256: ([0-9a-f]{16})", text)
+    m_b = re.search(r"DRAM bytes per H_eff application: ([0-9.e+]+)", text)
+    if not m_sha or not m_b:
+        return None, "summary without figures"
+    if m_sha.group(1) != h.hexdigest()[:16]:
+        return None, "kernel changed since the ncu capture"
+    return float(m_b.group(1)), path
+
+
+def ly8_forms(P, ctx, torch, dev, details):
+    """Workloads on the Ly = 8 cylinder (flux 1/8, t = V = 1, one particle per ring, Lx = 16,
+    the centre bond): at chi = 1024 the plain FP64 form (s per update) and the FP64 H_eff
+    against the oracle on sampled output blocks; at chi = 2048 the raw matvec error of TF32 and
+    split BF16 against the FP64 H_eff on the same operands, and the first update's energy of
+    each reduced-precision form (refined) against the converged plain FP64 form."""
+    from oracle import blocksparse as B
+    ly, lx = 8, 16
+    mpo = P.MPO(None, lx, ly, 1, 8, T_HOP, V_INT, P.MRD_BASIS_MIXED)
+    c = (lx // 2) * ly + ly // 2 - 1
+    n = lx * ly
+    out = {}
+    for chi, seed in ((1024, 1234 + 1), (2048, 1234 + 2)):
+        caps = [[(q[0], q[1], d) for q, d in synth.bond_sectors(chi, ly, round(j / ly), synth.substream(seed, 7, j))]
+                if 2 <= j <= n - 2 else [] for j in range(n + 1)]
+        res = {}
+        # matvec on seeded random operands of the update's shapes
+        left = np.array(caps[c], dtype=np.int32)
+        right = np.array(caps[c + 2], dtype=np.int32)
+        h = heff_of_bonds(P, ctx, mpo, c, left, right)
+        s = synth.substream(seed, 100)
+        L = torch.from_numpy(synth.complex_pm1(synth.substream(s, 8), h.lenv_len)).to(dev)
+        R = torch.from_numpy(synth.complex_pm1(synth.substream(s, 9), h.renv_len)).to(dev)
+        T = torch.from_numpy(synth.complex_pm1(synth.substream(s, 10), h.theta_len)).to(dev)
+        h.set_env(L, R)
+        o64 = torch.empty_like(T)
+        h.apply(T, o64, PREC["fp64"])
+        ref = o64.cpu().numpy()
+        scale = float(np.max(np.abs(ref)))
+        res["heff_flops_definition"] = h.flops()[0]
+        if chi == 1024:
+            # sampled output blocks against the oracle (the blocks of the two largest left sectors)
+            lb = B.BondSectors([((int(a), int(b)), int(d)) for a, b, d in left])
+            rb = B.BondSectors([((int(a), int(b)), int(d)) for a, b, d in right])
+            i_idx, i_val = mpo.site(c)
+            j_idx, j_val = mpo.site(c + 1)
+            wi = [(int(a), int(b), int(x), int(y), complex(v)) for (a, b, x, y), v in zip(i_idx, i_val)]
+            wj = [(int(a), int(b), int(x), int(y), complex(v)) for (a, b, x, y), v in zip(j_idx, j_val)]
+            ch = lambda b: [(int(x), int(y) % ly) for x, y in mpo.bond(b)]
+            args = (lb, rb, c % ly, (c + 1) % ly, ly, ch(c), ch(c + 1), ch(c + 2), wi, wj)
+            flats = (synth.complex_pm1(synth.substream(s, 8), h.lenv_len),
+                     synth.complex_pm1(synth.substream(s, 9), h.renv_len), T.cpu().numpy())
+            lay = B.theta_layout(lb, rb, c % ly, (c + 1) % ly, ly)
+            big = set(np.argsort(lb.dims)[-2:].tolist())
+            err = 0.0
+            for m in lay:
+                blk = ref[m["offset"]: m["offset"] + m["rowdim"] * m["coldim"]].reshape(m["rowdim"], m["coldim"])
+                for s1p, api, dap, ro in m["rows"]:
+                    if api not in big:
+                        continue
+                    for s2p, bpi, dbp, co in m["cols"]:
+                        want = B.heff_apply_block(*args, *flats, (api, s1p, s2p))
+                        err = max(err, float(np.max(np.abs(blk[ro:ro + dap, co:co + dbp] - want))))
+            res["heff_fp64_rel_err_vs_oracle_sampled"] = err / scale
+        else:
+            for name in ("tf32", "bf16x3"):
+                o = torch.empty_like(T)
+                h.apply(T, o, PREC[name])
+                res[f"heff_{name}_rel_err_vs_fp64"] = float(np.max(np.abs(o.cpu().numpy() - ref))) / scale
+        h.close()
+        del L, R, T, o64
+        # plain FP64 form, converged reference and timed form
+        st = make_state(P, ctx, mpo, chi, caps, 11, lx=lx, center=c)
+        e_ref, _ = st.update(c, +1, fp64_params(P, chi, tol=1e-14, restarts=8))
+        st.close()
+        st = make_state(P, ctx, mpo, chi, caps, 11, lx=lx, center=c)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e64, _ = st.update(c, +1, fp64_params(P, chi))
+        torch.cuda.synchronize(dev)
+        res["s_per_update_fp64"] = time.perf_counter() - t0
+        res["dE_rel_fp64_form"] = abs(e64 - e_ref) / abs(e_ref)
+        st.close()
+        if chi == 2048:
+            forms = {"bf16x3+ff": mixed_params(P, chi), "tf32+ff": mixed_params(P, chi, refine=20, prec=PREC["tf32"]),
+                     "bf16x3+fp64": mixed_params(P, chi, refine_prec=PREC["fp64"], svd_mode=P.MRD_SVD_F32_F64)}
+            for name, prm in forms.items():
+                st = make_state(P, ctx, mpo, chi, caps, 11, lx=lx, center=c)
+                st.update(c, +1, prm)            # tuning pass for this problem class
+                st.close()
+                st = make_state(P, ctx, mpo, chi, caps, 11, lx=lx, center=c)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                e, _ = st.update(c, +1, prm)
+                torch.cuda.synchronize(dev)
+                res[f"form_{name}"] = {"s_per_update": time.perf_counter() - t0, "dE_rel_vs_fp64": abs(e - e_ref) / abs(e_ref)}
+                st.close()
+        res["energy_fp64_converged"] = e_ref
+        out[f"chi{chi}"] = res
+    details["ly8"] = out
+    return out
 
 
 def main():
@@ -400,13 +573,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chi", type=int, default=CHI)
-    ap.add_argument("--refine", type=int, default=1, help="FP64 refinement matvecs of the mixed form")
+    ap.add_argument("--refine", type=int, default=1, help="float-float refinement matvecs of the mixed form")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fast-restarts", type=int, default=8, help="restarts of the reduced-precision Lanczos")
     ap.add_argument("--only-matvec", action="store_true", help="H_eff throughput only (profiling runs)")
     ap.add_argument("--precs", default="", help="with --only-matvec: comma-separated precisions (default all)")
     ap.add_argument("--profile-update", action="store_true",
                     help="warm-up updates, then one update inside a CUDA profiler range (ncu --profile-from-start off)")
+    ap.add_argument("--details", default="bench_details.json", help="file for the per-workload details")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements (Ly = 8 forms, real vs mixed)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -432,8 +607,7 @@ def main():
     mpo = P.MPO(None, LX_UPDATE, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, P.MRD_BASIS_MIXED)
     caps = update_caps(LX_UPDATE, chi)
     seed = replica_seed(rank)
-    # reduced-precision Lanczos restarted until its Ritz value settles, then FP64 refinement
-    mixed = P.DMRG.params(chi, 1e-14, 60, 1e-10, PREC["bf16x3"], args.refine, 1e-13, restarts=args.fast_restarts)
+    mixed = mixed_params(P, chi, args.refine, args.fast_restarts)
     if args.only_matvec:
         set_chi(chi)
         precs = [p for p in args.precs.split(",") if p]
@@ -467,16 +641,20 @@ def main():
     def max_over_ranks(x):
         return ranks_max(x, dist, dev)
 
-    # ---- accuracy: mixed form vs converged FP64 reference of the same first H_eff
+    details = {}
+    peaks = ctx.measure_peaks()   # FP32 / FP64 FMA instructions per second, SMs, clock
+    fp32_peak = peaks[0] / 1e12
+
+    # ---- accuracy reference: the plain FP64 form converged (FP64 Lanczos restarted to 1e-14,
+    # FP64 Jacobi SVD) on the first timed H_eff (same state, same environments)
     ref_state = make_state(P, ctx, mpo, chi, caps, seed)
-    e_ref, _ = ref_state.update(centre, +1, P.DMRG.params(chi, 1e-14, 30, 1e-13, PREC["bf16x3"], 60, 1e-15,
-                                                          refine_prec=PREC["fp64"]))
+    e_ref, _ = ref_state.update(centre, +1, fp64_params(P, chi, tol=1e-14, restarts=8))
+    ref_matvecs = ref_state.stats()[2]
     ref_state.close()
 
     # ---- warm-up pass over every site of the timed updates on a throwaway state: the tile
-    # autotuner times its candidates once per problem class (precision, log2 |theta|, log2
-    # tasks) and keeps only the chosen configuration, so the timed updates hold no tuning
-    # launches but still do all their work
+    # autotuner times its candidates once per problem class and keeps only the chosen
+    # configuration, so the timed updates hold no tuning launches but still do all their work
     st = make_state(P, ctx, mpo, chi, caps, seed)
     for k in range(args.warmup + args.steps):
         st.update(centre + k, +1, mixed)
@@ -495,13 +673,17 @@ def main():
     phases = np.zeros(6)
     sweeps = np.zeros(2)
     svd_work = np.zeros(6)   # summed mrd_dmrg_svd_stats of the timed updates
+    bonds, counts = [], []   # outer bonds and matvec counts of each timed update's H_eff
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = P.launch_count()
     t_wall = time.perf_counter()
     with ClockSampler(local) as clk:
         e0.record(stream)
         for k in range(args.steps):
-            st.update(centre + args.warmup + k, +1, mixed)
+            i = centre + args.warmup + k
+            bonds.append((i, st.bond(i), st.bond(i + 2)))
+            st.update(i, +1, mixed)
+            counts.append(st.stats()[2])
             phases += np.array(st.phase_ms())
             sweeps += np.array(st.svd_sweeps())
             svd_work += np.array(st.svd_stats())
@@ -521,7 +703,6 @@ def main():
     st = make_state(P, ctx, mpo, chi, caps, seed)
     for k in range(args.warmup):
         st.update(centre + k, +1, mixed)
-    # one pinned host buffer per site of the timed steps, holding that site's current tensor
     i0 = centre + args.warmup
     nmax = max(st.site_len(j) for j in range(n_sites))
     hsite = {j: torch.empty(2 * nmax, dtype=torch.complex128).pin_memory() for j in range(i0, i0 + args.steps + 1)}
@@ -544,25 +725,62 @@ def main():
     st.close()
     e2e_value = per_update_value(t_e2e, args.steps, world)
 
-    # ---- FP64 form at the same accuracy (restarted Lanczos until the Ritz value settles)
+    # ---- the plain FP64 form at the gate's accuracy (FP64 Lanczos restarted until the Ritz
+    # value settles to 1e-12)
     st = make_state(P, ctx, mpo, chi, caps, seed)
-    fp64 = P.DMRG.params(chi, 1e-14, 30, 1e-12, PREC["fp64"], 0, 1e-14, restarts=6)
-    st.timing(True)
+    torch.cuda.synchronize(dev)
     t64 = time.perf_counter()
     e_fp64 = None
     for k in range(args.fp64_steps):
-        e, _ = st.update(centre + k, +1, fp64)
+        e, _ = st.update(centre + k, +1, fp64_params(P, chi))
         if k == 0:
             e_fp64 = e
     torch.cuda.synchronize(dev)
     t64 = (time.perf_counter() - t64) / args.fp64_steps
-    st.timing(False)
     fp64_matvecs = st.stats()[2]
     st.close()
 
-    # ---- H_eff throughput per precision (Lx = 20 mid-ring sites, random environments)
+    # ---- the reduced-precision form with FP64 refinement, FP64 Jacobi sweeps after the FP32
+    # pre-sweeps and FP64 environments (the FP64-polished variant), two updates
+    f64r = mixed_params(P, chi, args.refine, args.fast_restarts, refine_prec=PREC["fp64"],
+                        svd_mode=P.MRD_SVD_F32_F64)
+    st = make_state(P, ctx, mpo, chi, caps, seed)
+    torch.cuda.synchronize(dev)
+    t_f64r = time.perf_counter()
+    e_f64r = None
+    for k in range(2):
+        e, _ = st.update(centre + k, +1, f64r)
+        if k == 0:
+            e_f64r = e
+    torch.cuda.synchronize(dev)
+    t_f64r = (time.perf_counter() - t_f64r) / 2
+    st.close()
+
+    # ---- flops of the timed updates' own H_effs (tables rebuilt from the recorded bonds)
+    f_def = f_exec = f_exec_ff = 0.0
+    n_tc = n_ff = 0
+    for (i, lb, rb), cnt in zip(bonds, counts):
+        h = heff_of_bonds(P, ctx, mpo, i, lb, rb)
+        fd, fe, _, _ = h.flops()
+        h.close()
+        ntc, nff = cnt % 1000, cnt // 1000
+        f_def += fd * ntc
+        f_exec += fe * ntc
+        f_exec_ff += fe * nff
+        n_tc += ntc
+        n_ff += nff
+
+    # ---- side measurements
+    set_chi(chi)
     mv = matvec_throughput(P, ctx, torch, dev, stream)
-    rvm = real_vs_mixed_or_note(P, ctx, torch, dev, stream)
+    details["heff_lx20_mid_ring"] = mv
+    if not args.quick:
+        details["real_vs_mixed_heff"] = real_vs_mixed_or_note(P, ctx, torch, dev, stream)
+        try:
+            ly8_forms(P, ctx, torch, dev, details)
+        except (P.MrdError, torch.cuda.OutOfMemoryError) as e:
+            details["ly8"] = {"skipped": f"{type(e).__name__}: {e}"}
+    details["mpo_diagnostics"] = mpo_diagnostics(P)
 
     if rank != 0:
         if dist is not None:
@@ -570,94 +788,93 @@ def main():
         return 0
 
     bf16_peak, bf16_sust, peak_src = measured_peaks()
-    tc_ms, hp_ms = kms[0] + kms[1], kms[2] + kms[3]   # tensor-core and float-float H_eff GEMMs
-    svd_ms = svd_work[0] + svd_work[4]                 # Jacobi rounds
-    f_exec = mv["flops_executed"]
-    # the dominant kernel of the timed updates by GPU time
-    shares = {"k_svd_bround (Jacobi rounds)": svd_ms, "k_tc_gemm (Lanczos matvecs)": tc_ms,
-              "k_cgemm_ff (refinement matvecs)": hp_ms}
-    dominant = max(shares, key=shares.get)
-    if dominant.startswith("k_svd_bround"):
-        # float-float Jacobi: FP32 instructions of the work done (per element of a tested pair:
-        # 4 float-float multiply-adds of 12 instructions; per element of a rotated pair: 4
-        # exact products of 3, 8 multiply-adds of 11 and 4 FastTwoSums of 3; the rotated
-        # norms are per pair, not per element), against the FP32 issue rate
-        instr = svd_work[1] * 48 + svd_work[2] * 112
-        ach = instr / (svd_work[0] / 1e3) / 1e12
-        roof = {"kernel": "k_svd_bround<float-float> (block-cyclic Jacobi rounds)", "bound": "alu", "achieved": ach,
-                "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
-                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived from unit counts and the maximum SM clock)",
-                "ms_per_step": svd_work[0] / args.steps, "share_of_measured_kernels": svd_ms / sum(shares.values())}
-    elif dominant.startswith("k_tc_gemm"):
-        per = tc_ms / max(kn[0], 1) / 1e3
-        hw = 3 * f_exec / per / 1e12
-        roof = {"kernel": "k_tc_gemm BF16X3 (steps 1+2)", "bound": "tensor", "achieved": hw, "peak": bf16_sust,
-                "unit": "TFLOP/s", "frac": hw / bf16_sust, "traffic": None, "peak_source": f"bf16 sustained {peak_src}",
-                "ms_per_step": tc_ms / args.steps, "share_of_measured_kernels": tc_ms / sum(shares.values())}
-    else:
-        per = hp_ms / max(kn[1], 1) / 1e3
-        ach = f_exec / 8 * FF_INSTR_PER_CMAC / per / 1e12
-        roof = {"kernel": "k_cgemm_ff (float-float refinement matvec, steps 1+2)", "bound": "alu", "achieved": ach,
-                "peak": FP32_ISSUE_TINSTR, "unit": "T FP32-instr/s", "frac": ach / FP32_ISSUE_TINSTR,
-                "traffic": None, "peak_source": "128 FP32 lanes/SM x 152 SMs x 2.07 GHz (derived from unit counts and the maximum SM clock)",
-                "ms_per_step": hp_ms / args.steps, "share_of_measured_kernels": hp_ms / sum(shares.values())}
-    tc = mv["bf16x3"]
-    tc_hw = 3 * f_exec / (tc["ms"] / 1e3) / 1e12
-    tf = mv["tf32"]
-    tf_hw = f_exec / (tf["ms"] / 1e3) / 1e12
+    tc_ms, ff_ms = kms[0] + kms[1], kms[2] + kms[3]
+    svd_ms = svd_work[0] + svd_work[4]
+    # the headline kernel: the split-BF16 H_eff of the timed updates (both grouped launches of
+    # every application). Algorithmic flops: the definition order L -> W -> R of the H_eff,
+    # 8 per complex multiply-add (the survey's measure). Hardware flops: what the tensor cores
+    # execute, 4 BF16 products (hi and lo of each operand) per real product of the folded
+    # contraction. The kernel runs inside a long step: sustained BF16 peak.
+    t_tc = tc_ms / 1e3
+    ach = f_def / t_tc / 1e12
+    hw = 4 * f_exec / t_tc / 1e12
+    traffic, traffic_src = traffic_from_profile(["paper_1512_03318_gb300/csrc/heff_tc.cu",
+                                                 "paper_1512_03318_gb300/csrc/tc_host.cu"])
+    roof = {"kernel": "k_tc_gemm BF16X3 (H_eff steps 1+2, the timed updates' own H_effs)", "bound": "tensor",
+            "achieved": ach, "peak": bf16_sust, "unit": "TFLOP/s", "frac": ach / bf16_sust,
+            "traffic": traffic, "traffic_unit": "bytes per H_eff application (2 launches)",
+            "hw_achieved": hw, "hw_frac": hw / bf16_sust,
+            "peak_source": f"bf16 sustained {peak_src}", "applications": n_tc,
+            "ms_per_application": tc_ms / max(n_tc, 1), "ms_per_update": tc_ms / args.steps,
+            "note": "achieved: definition-order flops (8 per complex multiply-add); hw: 4 BF16 products "
+                    "per real product of the folded contraction"}
+    # the Jacobi rounds of the block SVD: FP32 instructions of the float-float work done (per
+    # element of a tested pair 48, per element of a rotated pair 112) against the measured FP32
+    # fused multiply-add issue rate of this device
+    svd_instr = svd_work[1] * 48 + svd_work[2] * 112
+    svd_ach = svd_instr / (svd_work[0] / 1e3) / 1e12 if svd_work[0] > 0 else 0.0
+    roof_svd = {"kernel": "k_svd_bround<float-float> (block-cyclic Jacobi rounds)", "bound": "alu",
+                "achieved": svd_ach, "peak": fp32_peak, "unit": "T FP32-instr/s", "frac": svd_ach / fp32_peak,
+                "peak_source": "FP32 FMA issue rate measured in this run (mrd_measure_peaks)",
+                "ms_per_update": svd_ms / args.steps}
+    # float-float refinement matvecs: 36 FP32 instructions per complex multiply-add executed
+    ff_ach = f_exec_ff / 8 * FF_INSTR_PER_CMAC / (ff_ms / 1e3) / 1e12 if ff_ms > 0 else 0.0
+    dE = abs(e_mixed_first - e_ref) / abs(e_ref)
     line = {
         "metric": METRIC, "value": s_per_update, "unit": "s/update", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3+f32x2", "data": "synthetic",
-        "config": {"workload": workload_name(chi), "chi": chi, "ly": LY, "lx": LX_UPDATE,
-                   "form": f"split-BF16 tensor-core Lanczos (60 per run, up to {args.fast_restarts} restarts) + "
-                           f"float-float Rayleigh-quotient refinement ({args.refine} matvec), block SVD by "
-                           f"FP32 pre-sweeps + float-float Jacobi sweeps, float-float environment update",
-                   "l2": "working set > L2 (folded environments, Z intermediate and Lanczos basis, >1 GB)",
-                   "parallelism": f"replicas x{world}"},
+        "dE_rel_mixed_vs_converged_fp64": dE,
         "s_per_update_fp64": t64,
-        "fp64_form_matvecs": fp64_matvecs,
         "speedup_vs_fp64": t64 / (ms_total / 1e3 / args.steps),
-        "dE_rel_mixed_vs_converged_fp64": abs(e_mixed_first - e_ref) / abs(e_ref),
-        "dE_rel_fp64_form_vs_converged_fp64": abs(e_fp64 - e_ref) / abs(e_ref),
-        "energy_first_update": {"mixed": e_mixed_first, "fp64_form": e_fp64, "converged_fp64": e_ref},
-        "discarded_weight_last": trunc,
+        "heff_tflops_bf16x3_timed": ach,
+        "config": {"workload": f"two-site update Ly={LY} Lx={LX_UPDATE} flux=1/10 V=1 N={LX_UPDATE} chi={chi}, centre",
+                   "chi": chi, "ly": LY, "lx": LX_UPDATE,
+                   "form": "BF16X3 Lanczos + float-float refinement, FP32+float-float Jacobi SVD, float-float env",
+                   "gate": {"dE_rel_vs_fp64_converged": dE, "limit": 1e-9, "passed": dE <= 1e-9},
+                   "fp64_form": {"s_per_update": t64, "dE_rel": abs(e_fp64 - e_ref) / abs(e_ref),
+                                 "matvecs": fp64_matvecs},
+                   "fp64_refined_form": {"s_per_update": t_f64r, "dE_rel": abs(e_f64r - e_ref) / abs(e_ref)},
+                   "l2": "working set > L2 (environments, Z, Lanczos basis > 1 GB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "roofline_svd": roof_svd,
+        "roofline_ff_gemm": {"kernel": "k_cgemm_ff (float-float refinement and environment GEMMs)", "bound": "alu",
+                             "achieved": ff_ach, "peak": fp32_peak, "unit": "T FP32-instr/s",
+                             "frac": ff_ach / fp32_peak, "ms_per_update": ff_ms / args.steps,
+                             "applications": n_ff},
+        "kernel_ms_per_update": {"k_tc_gemm": round(tc_ms / args.steps, 3), "k_cgemm_ff": round(ff_ms / args.steps, 3),
+                                 "k_svd_bround": round(svd_ms / args.steps, 3)},
         "phase_ms_mean": dict(zip(["tables", "theta", "lanczos+refine", "svd", "tensors", "env"],
                                   (phases / args.steps).round(2).tolist())),
-        "svd_jacobi_rounds_mean": dict(zip(["fp32", "fp64"], (sweeps / args.steps).round(1).tolist())),
-        "kernel_ms_per_step": {k: round(v / args.steps, 3) for k, v in shares.items()},
-        "svd_elem_pairs_per_step": {"tested": svd_work[1] / args.steps, "rotated": svd_work[2] / args.steps},
-        "heff_tflops": {k: round(mv[k]["tflops"], 3) for k in PREC},
-        "heff_ms": {k: round(mv[k]["ms"], 4) for k in PREC},
-        "heff_ms_steps": {k: [round(mv[k]["ms_step1"], 4), round(mv[k]["ms_step2"], 4)] for k in PREC},
-        "heff_tile_config": {k: mv[k].get("tile_config") for k in ("tf32", "bf16x3")},
-        "heff_bf16x3_ms_grouped_vs_per_task": [round(mv["bf16x3"]["ms"], 4),
-                                               round(mv["bf16x3"]["ms_per_task_launches"], 3)],
-        "heff_flops": {"definition": mv["flops_definition"], "executed": mv["flops_executed"]},
-        "real_vs_mixed_heff": rvm,
-        "mpo_diagnostics": mpo_diagnostics(P),
-        "roofline": roof,
-        "roofline_tc_bf16x3": {"kernel": "k_tc_gemm BF16X3 (steps 1+2), Lx=20 matvec", "bound": "tensor",
-                               "achieved": tc_hw, "peak": bf16_peak, "unit": "TFLOP/s", "frac": tc_hw / bf16_peak,
-                               "traffic": None, "note": "hardware bf16 flops = 3 x executed complex-product flops "
-                                                        f"(split), peak = bf16 burst {peak_src}"},
-        "roofline_ff_gemm": {"kernel": "k_cgemm_ff (steps 1+2), Lx=20 matvec", "bound": "alu",
-                             "achieved": f_exec / 8 * FF_INSTR_PER_CMAC / (mv["ff"]["ms"] / 1e3) / 1e12, "peak": FP32_ISSUE_TINSTR,
-                             "unit": "T FP32-instr/s",
-                             "frac": f_exec / 8 * FF_INSTR_PER_CMAC / (mv["ff"]["ms"] / 1e3) / 1e12 / FP32_ISSUE_TINSTR,
-                             "traffic": None, "note": "36 FP32 instructions per complex multiply-add (3 float-float products of 12)"},
-        "roofline_tc_tf32": {"kernel": "k_tc_gemm TF32 (steps 1+2), Lx=20 matvec", "bound": "tensor",
-                             "achieved": tf_hw, "peak": bf16_peak / 2, "unit": "TFLOP/s",
-                             "frac": tf_hw / (bf16_peak / 2), "traffic": None,
-                             "note": f"TF32 peak = bf16 burst {peak_src} x 1/2 (nominal ratio)"},
         "e2e": {"value": e2e_value, "unit": "s/update", "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
     }
+    details["accuracy"] = {"e_ref_fp64_converged": e_ref, "ref_matvecs": ref_matvecs, "e_mixed_first": e_mixed_first,
+                           "e_fp64_form": e_fp64, "e_fp64_refined_form": e_f64r}
+    details["svd"] = {"jacobi_sweeps_mean": dict(zip(["fp32", "final"], (sweeps / args.steps).round(1).tolist())),
+                      "elem_pairs_per_update": {"tested": svd_work[1] / args.steps, "rotated": svd_work[2] / args.steps}}
+    details["measured_issue_rates"] = {"fp32_fma_per_s": peaks[0], "fp64_fma_per_s": peaks[1], "sms": peaks[2],
+                                       "max_sm_clock_hz": peaks[3]}
+    details["roofline_traffic_source"] = traffic_src
+    if "ly8" in details and "chi2048" in details.get("ly8", {}):
+        l8 = details["ly8"]
+        line["ly8"] = {"chi1024_fp64_s_per_update": l8["chi1024"]["s_per_update_fp64"],
+                       "chi1024_fp64_heff_err_vs_oracle": l8["chi1024"].get("heff_fp64_rel_err_vs_oracle_sampled"),
+                       "chi2048_heff_err": {k: l8["chi2048"][f"heff_{k}_rel_err_vs_fp64"] for k in ("tf32", "bf16x3")},
+                       "chi2048_forms": {k[5:]: v for k, v in l8["chi2048"].items() if k.startswith("form_")},
+                       "chi2048_fp64_s_per_update": l8["chi2048"]["s_per_update_fp64"]}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    line["details"] = args.details
+    try:
+        with open(args.details, "w") as f:
+            json.dump(details, f, indent=1, default=float)
+    except OSError as e:
+        line["details"] = f"not written: {e}"
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

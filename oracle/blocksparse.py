@@ -297,7 +297,13 @@ def heff_apply_block(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat,
     return out
 
 
-def env_left_update_block(sec_l, sec_r, m, mod, cl, cm, w_entries, lflat, a_blocks, out_key):
+def left_env_blocks(sec_l, cl, mod, lflat):
+    """{(w, a_index): (a'_index, d_a' x d_a block)} of a left environment in its layout."""
+    return {(w, ai): (api, lflat[off: off + dp * da].reshape(dp, da))
+            for w, ai, api, off, dp, da in env_left_layout(sec_l, cl, mod)}
+
+
+def env_left_update_block(sec_l, sec_r, m, mod, cl, cm, w_entries, lflat, a_blocks, out_key, lblk=None):
     """One block of the left environment update of standard two-site DMRG,
         L'_{w'}[c', c] = sum_{w, a', a, s', s} conj(A[a', s', c']) L_w[a', a] W[w, w', s', s] A[a, s, c],
     restated with loops over charge blocks. sec_l / sec_r: BondSectors of the bonds left and
@@ -305,15 +311,16 @@ def env_left_update_block(sec_l, sec_r, m, mod, cl, cm, w_entries, lflat, a_bloc
     right of it; w_entries: the site's (w, w', s', s, value) list; lflat: L in the
     env_left_layout(sec_l, cl) layout; a_blocks: {(a_index, s): d_a x d_c array} of the MPS
     tensor, c the sector q_a + q(s). out_key = (w', c_index); returns the d(c + c_{w'}) x d(c)
-    block ([bra][ket]), zero if no term reaches it."""
+    block ([bra][ket]), zero if no term reaches it. lblk: the blocks of lflat from
+    left_env_blocks, when the caller evaluates many output blocks of one environment."""
     wp, ci = out_key
     qc = sec_r.charges[ci]
     qcp = qadd(qc, cm[wp], mod)
     out = np.zeros((sec_r.dim(qcp), sec_r.dims[ci]), dtype=np.complex128)
     if qcp not in sec_r.index:
         return out
-    lblk = {(w, ai): (api, lflat[off: off + dp * da].reshape(dp, da))
-            for w, ai, api, off, dp, da in env_left_layout(sec_l, cl, mod)}
+    if lblk is None:
+        lblk = left_env_blocks(sec_l, cl, mod, lflat)
     for (w, wq, sp, s, v) in w_entries:
         if wq != wp:
             continue
@@ -413,8 +420,9 @@ def two_site_update(left, right, m1, m2, mod, cl, cm, cr, wi, wj, lflat, rflat, 
             a_blocks[(ai, s1)] = u[ro:ro + da]
     lay_new = env_left_layout(bond, cm, mod)
     lnew = np.zeros(env_size(lay_new), dtype=np.complex128)
+    lblk = left_env_blocks(left, cl, mod, lflat)
     for w, ci, cpi, off, d0, d1 in lay_new:
         lnew[off:off + d0 * d1] = env_left_update_block(left, bond, m1, mod, cl, cm, wi, lflat, a_blocks,
-                                                        (w, ci)).reshape(-1)
+                                                        (w, ci), lblk=lblk).reshape(-1)
     return {"energy": e, "matvecs": nmv, "discarded": 1.0 - keep_w / total, "bond": bond, "schmidt": schmidt,
             "a_blocks": a_blocks, "lenv": lnew}
