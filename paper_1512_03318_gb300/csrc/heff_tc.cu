@@ -403,6 +403,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
       const int64_t rt = local / tiles_n, nt = local % tiles_n;
       const int64_t npad = ((N + 15) / 16) * 16;
       const int64_t nrow = npad - nt * ntile < ntile ? npad - nt * ntile : ntile;
+      // rows of this A row tile that hold data, rounded up to a swizzle atom of 8 rows: only
+      // these are copied; the stage's other rows keep stale values, which reach only
+      // accumulator rows the epilogue never stores
+      const int64_t mleft = task[0] - rt * 128;
+      const uint32_t mrows = (uint32_t)(((mleft < 128 ? mleft : 128) + 7) / 8 * 8);
       for (int64_t s = 0; s < task[6] && ok; ++s) {
         const int64_t* sg = g.segs + TCS * (task[5] + s);
         const int64_t nkt = sg[2];
@@ -414,8 +419,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
           const uint32_t abytes = aplanes * 128 * 128, bbytes = (uint32_t)(bplanes * nrow * 128);
           const uint32_t sa = smem_u32(smem + stage * stage_bytes);
           const uint32_t sb = sa + abytes;
-          mbar_expect_tx(smem_u32(&bar_full[stage]), abytes + bbytes);
-          bulk_g2s(sa, a + kt * abytes, abytes, smem_u32(&bar_full[stage]));
+          mbar_expect_tx(smem_u32(&bar_full[stage]), (uint32_t)aplanes * mrows * 128 + bbytes);
+          for (int p = 0; p < aplanes; ++p)
+            bulk_g2s(sa + p * 128 * 128, a + kt * abytes + p * 128 * 128, mrows * 128, smem_u32(&bar_full[stage]));
           bulk_g2s(sb, b + kt * (int64_t)bbytes, bbytes, smem_u32(&bar_full[stage]));
           ++fills;
           if (++stage == nstages) { stage = 0; phase ^= 1; }
