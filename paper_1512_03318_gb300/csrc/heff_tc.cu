@@ -286,6 +286,7 @@ struct TcArgs {
   int nstages;             // shared-memory pipeline depth (at most kTcMaxStages)
   int stage_bytes;
   uint64_t wait_ns;        // limit of each pipeline wait (ns); 0: the first wait gives up
+  const int64_t* rowmap;   // mode 2: per output row (Z panel byte offset << 16) | row in that panel
 };
 
 // Task and tile of a work item: one load from the host-built item table, else a binary
@@ -548,6 +549,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
 #pragma unroll
             for (int j = 0; j < 16; ++j)
               if (j < nvalid) dst[j] = make_double2((double)re[j], (double)im[j]);
+          } else if (task[7] == 2) {   // stacked rows: each goes to its own Z panel
+            const int64_t rm = g.rowmap[task[2] + row];
+            put_packed16(g.z_out + (rm >> 16), task[8], aplanes, prec, rm & 0xffff, col, re, im, nvalid);
           } else {
             put_packed16(g.z_out + task[2], task[8], aplanes, prec, row, col, re, im, nvalid);
           }
@@ -587,15 +591,16 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
 }
 
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
-                    const int64_t* prefix, const int2* items, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out,
-                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, uint64_t wait_ns, cudaStream_t s) {
+                    const int64_t* prefix, const int2* items, const int64_t* rowmap, int64_t n_tasks,
+                    int64_t total_tiles, uint8_t* z_out, double2* f_out, int prec, TcCfg cfg, int* err, int n_sm,
+                    uint64_t wait_ns, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   cudaError_t ea = tc_gemm_init();
   if (ea != cudaSuccess) return ea;
   const int smem = tc_smem_bytes(prec, cfg);
   if (!tc_cfg_ok(prec, cfg) || smem > kTcMaxSmem) return cudaErrorInvalidValue;
   TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, items, cfg.ntile, cfg.stages,
-           tc_stage_bytes(prec, cfg.ntile), wait_ns};
+           tc_stage_bytes(prec, cfg.ntile), wait_ns, rowmap};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
   k_tc_gemm<<<(unsigned)grid, 192, smem, s>>>(g);
   mrd::count_launch();

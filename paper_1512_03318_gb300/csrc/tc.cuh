@@ -8,6 +8,9 @@ enum { TC_TF32 = 1, TC_BF16X3 = 2 };
 // task row (int64): M N out0 out1 pad seg0 nseg mode nkt_z pad
 //   mode 0: packed Z output, out0 = byte offset of the Z panel, nkt_z its K-tile count
 //   mode 1: FP64 output, out0 = element offset, out1 = leading dimension
+//   mode 2: packed Z output of stacked rows, out0 = first entry of the task in the row map
+//           ((Z panel byte offset << 16) | row in that panel, one per output row), nkt_z the
+//           K-tile count of those panels
 enum { TCT = 10 };
 // segment row: a_panel_byte_offset b_panel_byte_offset nkt pad
 enum { TCS = 4 };

@@ -14,8 +14,9 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
                     cudaStream_t s);
 cudaError_t tc_gemm_init();
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
-                    const int64_t* prefix, const int2* items, int64_t n_tasks, int64_t total_tiles, uint8_t* z_out,
-                    double2* f_out, int prec, TcCfg cfg, int* err, int n_sm, uint64_t wait_ns, cudaStream_t s);
+                    const int64_t* prefix, const int2* items, const int64_t* rowmap, int64_t n_tasks,
+                    int64_t total_tiles, uint8_t* z_out, double2* f_out, int prec, TcCfg cfg, int* err, int n_sm,
+                    uint64_t wait_ns, cudaStream_t s);
 }  // namespace mrd
 
 struct Tc {
@@ -35,6 +36,7 @@ struct Tc {
   int64_t *pt1 = nullptr, *pt2 = nullptr;
   std::vector<int64_t> tiles1, tiles2;
   int2 *it1 = nullptr, *it2 = nullptr;   // item tables of the grouped launches
+  int64_t* rmap1 = nullptr;               // step-1 row map: (Z panel byte offset << 16) | row in panel
   int* err = nullptr;
 };
 
@@ -77,19 +79,11 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   Tc* T = h->tc;
   const int aplanes = tc_aplanes(prec), bplanes = tc_bplanes(prec), kpt = tc_kpt(prec), ntile = cfg.ntile;
   const int64_t* c = h->counts;
-  PanelIndex lw_map, wr_map, th_map, z_map;
-  lw_map.v.reserve(c[C_NLW]);
+  PanelIndex wr_map, th_map, z_map;
   wr_map.v.reserve(c[C_NWR]);
   std::vector<int64_t> j_lw, j_wr, j_th;
   int64_t lw_b = 0, wr_b = 0, th_b = 0, z_b = 0;
-  // folded left operand LW(w', s1', s1, a): A panel, rows d_a', K d_a
-  for (int64_t k = 0; k < c[C_NLW]; ++k) {
-    const int64_t* r = &h->lw_host[LWF * k];
-    const int64_t rows = r[5], K = r[6], nkt = (K + kpt - 1) / kpt;
-    lw_map.add(r[7], {lw_b, nkt});
-    j_lw.insert(j_lw.end(), {r[7], K, 0, rows, K, lw_b, 128, nkt, round_up(rows, 128), 0, 0, 0, 0});
-    lw_b += a_bytes(rows, nkt, aplanes);
-  }
+  // (the folded left operand LW is packed below, stacked by input middle sector)
   // folded right operand WR(w', s2, s2', b): B panel of its transpose, rows d_b', K d_b
   for (int64_t k = 0; k < c[C_NWR]; ++k) {
     const int64_t* r = &h->wr_host[WRF * k];
@@ -140,7 +134,6 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
       }
     }
   }
-  lw_map.finish();
   wr_map.finish();
   th_map.finish();
   z_map.finish();
@@ -177,27 +170,80 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     std::thread& t;
     ~Join() { if (t.joinable()) t.join(); }
   } join_step2{step2};
-  // step-1 tasks (Z = LW theta), one per (w', m_in, s1', s2) so that each writes one Z panel
-  for (int64_t i = 0; i < c[C_NT1]; ++i) {
-    const int64_t* t = &h->t1_host[TF * i];
-    if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
-    const int64_t* rin = &mid[MIDF * ((i / 2) % nmid)];
-    for (int s2p = 0; s2p < 2; ++s2p) {
-      if (rin[8 + s2p] < 0) continue;
-      const int64_t N = h->right[3 * rin[8 + s2p] + 2], coff = s2p ? rin[10] : 0;
-      if (N == 0) continue;
-      const int64_t seg0 = (int64_t)s1.size() / TCS;
-      for (int64_t k = 0; k < t[5]; ++k) {
-        const int64_t* sg = &h->s1_host[SF * (t[4] + k)];
-        const Panel* a = lw_map.find(sg[0]);
-        const Panel* b = th_map.find(sg[2] + coff);
-        if (!a || !b || a->nkt != b->nkt) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
-        s1.insert(s1.end(), {a->off, b->off, a->nkt, 0});
+  // step-1 tasks (Z = LW theta), stacked: for every input middle sector m_in, the output rows
+  // (w', s1', a') of all its Z blocks are stacked along M into one GEMM per column part s2, so
+  // that small blocks share 128-row tiles instead of each filling one. Rows are grouped in
+  // three classes by the LW blocks that feed them (s1 = 0 only, s1 = 1 only, both), each
+  // class a task of its own with the K segments it needs, so no zero block is multiplied.
+  // The stacked LW of a class and K segment s1 is one A panel; each output row is scattered to
+  // its Z panel through a row map (mode 2).
+  std::vector<int64_t> rowmap;
+  {
+    std::vector<int64_t> zrow_of((size_t)c[C_NMID] > 0 ? (size_t)h->d.d_m * nmid : 0, -1);
+    for (int64_t k = 0; k < c[C_NZ]; ++k) zrow_of[(size_t)(z[ZF * k] * nmid + z[ZF * k + 1])] = k;
+    struct Member { int64_t wp, s1p, rows, row0, lw[2]; };
+    for (int64_t mi = 0; mi < nmid; ++mi) {
+      const int64_t* rin = &mid[MIDF * mi];
+      std::vector<Member> cls[3];
+      for (int64_t wp = 0; wp < h->d.d_m; ++wp)
+        for (int s1p = 0; s1p < 2; ++s1p) {
+          const int64_t ti = (wp * nmid + mi) * 2 + s1p;
+          const int64_t* t = &h->t1_host[TF * ti];
+          if (t[5] == 0 || t[0] == 0 || t[1] == 0) continue;
+          Member mb{wp, s1p, t[0], 0, {-1, -1}};
+          for (int64_t k = 0; k < t[5]; ++k) {
+            const int64_t* sg = &h->s1_host[SF * (t[4] + k)];
+            int q1 = sg[2] == rin[4] + rin[7] * rin[3] ? 1 : 0;   // theta rows of the s1 = 1 part
+            if (rin[5] < 0) q1 = 1;
+            if (rin[6] < 0) q1 = 0;
+            mb.lw[q1] = sg[0];
+          }
+          const int k = mb.lw[0] >= 0 && mb.lw[1] >= 0 ? 2 : (mb.lw[0] >= 0 ? 0 : 1);
+          cls[k].push_back(mb);
+        }
+      for (int k = 0; k < 3; ++k) {
+        if (cls[k].empty()) continue;
+        int64_t R = 0;
+        for (Member& mb : cls[k]) { mb.row0 = R; R += mb.rows; }
+        // the class's stacked A panels, one per K segment s1
+        int64_t aoff[2] = {-1, -1}, ank[2] = {0, 0};
+        for (int q1 = 0; q1 < 2; ++q1) {
+          if (k != 2 && k != q1) continue;
+          if (rin[5 + q1] < 0) return mrd_fail(ctx, MRD_E_STATE, "tc: LW block without its theta rows");
+          const int64_t K = h->left[3 * rin[5 + q1] + 2];
+          ank[q1] = (K + kpt - 1) / kpt;
+          aoff[q1] = lw_b;
+          for (const Member& mb : cls[k])
+            j_lw.insert(j_lw.end(), {mb.lw[q1], K, 0, mb.rows, K, lw_b, 128, ank[q1], round_up(R, 128), 0, 0, mb.row0, 0});
+          lw_b += a_bytes(R, ank[q1], aplanes);
+        }
+        for (int s2p = 0; s2p < 2; ++s2p) {
+          if (rin[8 + s2p] < 0) continue;
+          const int64_t N = h->right[3 * rin[8 + s2p] + 2], coff = s2p ? rin[10] : 0;
+          if (N == 0) continue;
+          const int64_t seg0 = (int64_t)s1.size() / TCS, map0 = (int64_t)rowmap.size();
+          int64_t nseg = 0;
+          for (int q1 = 0; q1 < 2; ++q1) {
+            if (aoff[q1] < 0) continue;
+            const Panel* b = th_map.find(rin[4] + (q1 ? rin[7] : 0) * rin[3] + coff);
+            if (!b || b->nkt != ank[q1]) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
+            s1.insert(s1.end(), {aoff[q1], b->off, ank[q1], 0});
+            ++nseg;
+          }
+          const int64_t nkt_z = (N + kpt - 1) / kpt;
+          for (const Member& mb : cls[k]) {
+            const int64_t zk = zrow_of[(size_t)(mb.wp * nmid + mi)];
+            if (zk < 0) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output block missing");
+            const int64_t* zr = &z[ZF * zk];
+            const int64_t* rout = &mid[MIDF * zr[2]];
+            const Panel* q = z_map.find(zr[5] + (mb.s1p ? rout[7] : 0) * rin[3] + coff);
+            if (!q || q->nkt != nkt_z) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
+            for (int64_t r = 0; r < mb.rows; ++r) rowmap.push_back(q->off << 16 | r);
+          }
+          t1.insert(t1.end(), {R, N, map0, 0, 0, seg0, nseg, 2, nkt_z, 0});
+          p1.push_back(p1.back() + ((R + 127) / 128) * ((N + ntile - 1) / ntile));
+        }
       }
-      const Panel* q = z_map.find(t[2] + coff);
-      if (!q) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
-      t1.insert(t1.end(), {t[0], N, q->off, 0, 0, seg0, t[5], 0, q->nkt, 0});
-      p1.push_back(p1.back() + ((t[0] + 127) / 128) * ((N + ntile - 1) / ntile));
     }
   }
   if (step2.joinable()) step2.join();
@@ -237,8 +283,13 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
           if (q[0] < 0 || q[0] + a_bytes(M, q[2], aplanes) > alen) return false;
           if (q[1] < 0 || q[1] + b_bytes(N, q[2], bplanes) > blen) return false;
         }
-        if (zout && (tk[i + 2] < 0 || tk[i + 2] + a_bytes(M, tk[i + 8], aplanes) > z_b || tk[i + 8] * kpt < N))
-          return false;
+        if (zout) {   // every mapped row lies in a Z panel of this task's K-tile count
+          if (tk[i + 2] < 0 || tk[i + 2] + M > (int64_t)rowmap.size() || tk[i + 8] * kpt < N) return false;
+          for (int64_t r = 0; r < M; ++r) {
+            const int64_t off = rowmap[tk[i + 2] + r] >> 16, zr = rowmap[tk[i + 2] + r] & 0xffff;
+            if (off < 0 || off + (zr / 128 + 1) * tk[i + 8] * aplanes * 128 * 128 > z_b) return false;
+          }
+        }
       }
       return true;
     };
@@ -271,6 +322,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   for (size_t t = 0; t + 1 < p2.size(); ++t)
     for (int64_t l = 0; l < p2[t + 1] - p2[t]; ++l) i2.push_back(make_int2((int)t, (int)l));
   TALLOC(T->it1, i1.size()); TALLOC(T->it2, i2.size());
+  TALLOC(T->rmap1, rowmap.size());
 #undef TALLOC
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: device buffers");
   T->lw_bytes = lw_b; T->wr_bytes = wr_b; T->th_bytes = th_b; T->z_bytes = z_b;
@@ -297,6 +349,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   up(T->pt1, q1); up(T->pt2, q2);
   if (e == cudaSuccess && !i1.empty()) e = cudaMemcpyAsync(T->it1, i1.data(), i1.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !i2.empty()) e = cudaMemcpyAsync(T->it2, i2.data(), i2.size() * 8, cudaMemcpyHostToDevice, s);
+  up(T->rmap1, rowmap);
   T->tiles1.resize(p1.size() - 1);
   T->tiles2.resize(p2.size() - 1);
   for (size_t t = 0; t < T->tiles1.size(); ++t) T->tiles1[t] = q1[2 * t + 1];
@@ -343,10 +396,10 @@ int time_cfg(mrd_heff* h, double* ms) {
   for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
     if (r == 1) e = cudaEventRecord(a, s);
     if (e == cudaSuccess)
-      e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
+      e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->rmap1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
                   h->n_sm, h->wait_ns, s);
     if (e == cudaSuccess)
-      e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
+      e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, nullptr, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
                   h->wait_ns, s);
   }
   float f = 0.f;
@@ -468,18 +521,18 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, T->pc_th, tp, s));
   MRD_CUDA(ctx, record_event(e0, s, cap));
   if (!h->per_task) {
-    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
+    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->rmap1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
                           h->n_sm, h->wait_ns, s));
     MRD_CUDA(ctx, record_event(e1, s, cap));
-    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
+    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, nullptr, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
                           T->err, h->n_sm, h->wait_ns, s));
   } else {   // one launch per task: the per-block baseline of the grouped persistent launch
     for (int64_t t = 0; t < T->n1; ++t)
-      MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, nullptr, 1, T->tiles1[t], T->z, nullptr, tp,
+      MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, nullptr, T->rmap1, 1, T->tiles1[t], T->z, nullptr, tp,
                             T->cfg, T->err, h->n_sm, h->wait_ns, s));
     MRD_CUDA(ctx, record_event(e1, s, cap));
     for (int64_t t = 0; t < T->n2; ++t)
-      MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, nullptr, 1, T->tiles2[t], nullptr,
+      MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, nullptr, nullptr, 1, T->tiles2[t], nullptr,
                             (double2*)out, tp, T->cfg, T->err, h->n_sm, h->wait_ns, s));
   }
   MRD_CUDA(ctx, record_event(e2, s, cap));
