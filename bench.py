@@ -672,7 +672,7 @@ def main():
     barrier()
     phases = np.zeros(6)
     sweeps = np.zeros(2)
-    svd_work = np.zeros(6)   # summed mrd_dmrg_svd_stats of the timed updates
+    svd_work = np.zeros(8)   # summed mrd_dmrg_svd_stats of the timed updates
     bonds, counts = [], []   # outer bonds and matvec counts of each timed update's H_eff
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = P.launch_count()
@@ -856,7 +856,9 @@ def main():
     details["accuracy"] = {"e_ref_fp64_converged": e_ref, "ref_matvecs": ref_matvecs, "e_mixed_first": e_mixed_first,
                            "e_fp64_form": e_fp64, "e_fp64_refined_form": e_f64r}
     details["svd"] = {"jacobi_sweeps_mean": dict(zip(["fp32", "final"], (sweeps / args.steps).round(1).tolist())),
-                      "elem_pairs_per_update": {"tested": svd_work[1] / args.steps, "rotated": svd_work[2] / args.steps}}
+                      "elem_pairs_per_update": {"tested": svd_work[1] / args.steps, "rotated": svd_work[2] / args.steps},
+                      "columns_final_sweeps_per_update": svd_work[6] / args.steps,
+                      "columns_all_per_update": svd_work[7] / args.steps}
     details["measured_issue_rates"] = {"fp32_fma_per_s": peaks[0], "fp64_fma_per_s": peaks[1], "sms": peaks[2],
                                        "max_sm_clock_hz": peaks[3]}
     details["roofline_traffic_source"] = traffic_src

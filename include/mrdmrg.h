@@ -300,11 +300,14 @@ int mrd_dmrg_timing(mrd_dmrg* d, int32_t on, double* kernel_ms4, int64_t* applie
  * [3] block SVD and truncation, [4] new MPS tensors, [5] environment update; then [6] the
  * FP32 and [7] the FP64 Jacobi sweeps of its block SVD. */
 int mrd_dmrg_phase_ms(const mrd_dmrg* d, double* ms8);
-/* Block SVD of the last two-site update: out6 = {ms of the final (float-float or FP64) Jacobi
+/* Block SVD of the last two-site update: out8 = {ms of the final (float-float or FP64) Jacobi
  * sweeps (CUDA events around them), column element-pairs whose overlap was tested (sum of the
  * column length over tested pairs), element-pairs rotated, final sweeps, ms of the FP32
- * pre-sweeps (0 without), svd_mode}. */
-int mrd_dmrg_svd_stats(const mrd_dmrg* d, double* out6);
+ * pre-sweeps (0 without), svd_mode, columns that entered the final sweeps, columns of all
+ * blocks}. With FP32 pre-sweeps and more columns than chi, columns whose norm after the
+ * pre-sweeps is below half the chi-th largest column norm are set aside before the final
+ * sweeps (their Schmidt weight is discarded by the truncation to chi in any case). */
+int mrd_dmrg_svd_stats(const mrd_dmrg* d, double* out8);
 /* Momentum-resolved entanglement spectrum (Sec. III.C): the Schmidt values lambda of the
  * bond cut by the last two-site update (*bond = i + 1 for an update of sites i, i+1), one per
  * kept Schmidt state, with the charges (N, K) of its left part in nk (2 per value). The values

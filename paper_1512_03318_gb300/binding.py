@@ -403,8 +403,9 @@ class DMRG:
         return b.value, {k: np.sort(np.array(v))[::-1] for k, v in out.items()}
 
     def svd_stats(self):
-        """(sweep ms, element-pairs tested, element-pairs rotated, sweeps, FP32 pre-sweep ms, svd_mode)."""
-        f = (C.c_double * 6)()
+        """(sweep ms, element-pairs tested, element-pairs rotated, sweeps, FP32 pre-sweep ms, svd_mode,
+        columns entering the final sweeps, columns of all blocks)."""
+        f = (C.c_double * 8)()
         self.ctx.check(lib().mrd_dmrg_svd_stats(self.h, f))
         return tuple(f)
 

@@ -51,7 +51,14 @@ cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_pre
                          int sweep, unsigned long long* wctr, cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
-enum { SVF = 12 };
+cudaError_t svd_colnorm2(const double2* work, const int64_t* blk, int nblk, double* out, cudaStream_t s);
+cudaError_t svd_gather_cols(double2* work, const double2* src, const int64_t* blk, int nblk, const int* perm,
+                            cudaStream_t s);
+enum { SVF = 13 };
+// After the FP32 pre-sweeps, columns whose norm is below this fraction of the chi-th largest
+// column norm over all blocks are set aside: they hold Schmidt weight that the truncation to
+// chi discards, so the float-float sweeps run on the other columns only (see block_svd)
+constexpr double kSetAsideFrac = 0.5;
 constexpr int64_t kSvdMaxSmemHost = 220 * 1024;   // dynamic shared memory of a Jacobi CTA
 // orthogonality tolerance |x_i^+ x_j| / (|x_i| |x_j|) of the final sweeps: FP64, and float-float
 // (48-bit products: dot products of a few hundred terms carry ~1e-13 relative noise)
@@ -317,7 +324,9 @@ struct mrd_dmrg {
   std::vector<EnvT> L, R;
   Buf gtask, gseg, gpref, gitems, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
       svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, svd_last, svd_ctr, tbuf,
-      zeros;
+      zeros, svd_perm;
+  // columns entering the final Jacobi sweeps and columns of all blocks, last block SVD
+  double svd_cols[2] = {0, 0};
   cudaEvent_t svd_ev[2] = {nullptr, nullptr};
   // last block SVD: [0] ms of the final sweeps, [1] element-pairs tested, [2] rotated, [3] sweeps,
   // [4] ms of the FP32 pre-sweeps, [5] svd_mode
@@ -512,7 +521,7 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     const int64_t m = d[0], n = d[1];
     const bool wide = side == 1;   // X = M^+ (orthonormal V) instead of X = M (orthonormal U)
     const int64_t p = wide ? n : m, r = wide ? m : n;
-    d[2] = p; d[3] = r; d[9] = wide;
+    d[2] = p; d[3] = r; d[9] = wide; d[12] = r;
     d[4] = work; work += p * r;
     d[6] = ulen; ulen += m * r;
     d[7] = vlen; vlen += r * n;
@@ -566,7 +575,8 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     return sc;
   };
   const bool ff_cols = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
-  const Sched s32 = schedule(8, true, pp.data()), s64 = schedule(ff_cols ? 16 : 8, false, pp.data() + nb + 1);
+  const Sched s32 = schedule(8, true, pp.data());
+  Sched s64 = schedule(ff_cols ? 16 : 8, false, pp.data() + nb + 1);
   if (s32.smem > kSvdMaxSmemHost || s64.smem > kSvdMaxSmemHost)
     return mrd_fail(ctx, MRD_E_OOM, "block SVD: a block is too large for the shared-memory Jacobi rounds");
   MRD_CUDA(ctx, D->svd_blk.need(blk.size() * 8));
@@ -652,6 +662,7 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   // (X <- X V32, one grouped GEMM) and float-float or FP64 sweeps finish the job.
   int rc = MRD_OK;
   D->svd_sweeps32 = 0;
+  D->svd_cols[0] = D->svd_cols[1] = (double)slen;
   if (mode == MRD_SVD_F32_FF || mode == MRD_SVD_F32_F64) {
   MRD_CUDA(ctx, svd_to_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
   rc = sweep_until_done(true, kMaxSweeps32, &D->svd_sweeps32);
@@ -669,8 +680,61 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     rc = run_gemm(D, g, D->svd_work.as<double2>(), work, D->svd_work.as<double2>(), work, D->svd_x2.as<double2>(),
                   xlen);
     if (rc != MRD_OK) return rc;
+  }
+  // Columns set aside before the final sweeps. After the pre-sweeps the columns of X = M V32
+  // are orthogonal to ~1e-5 and their norms are the singular values to that accuracy. Only the
+  // chi largest values over all blocks survive the truncation, so columns of norm below
+  // kSetAsideFrac times the chi-th largest norm carry weight that is discarded in any case;
+  // they are dropped from X, the final sweeps orthogonalise the remaining columns (the
+  // dominant singular subspace, perturbed only through the ~1e-5 overlaps with the dropped
+  // columns, a second-order change of the truncated state) and the block keeps r_act values.
+  // The canonical factor stays exactly orthonormal; the other factor is the exact projection.
+  bool set_aside = false;
+  int64_t cols_all = 0, cols_kept = 0;
+  for (int b = 0; b < nb; ++b) cols_all += blk[SVF * b + 3];
+  if (cols_all > chi && chi > 0) {
+    MRD_CUDA(ctx, svd_colnorm2(D->svd_x2.as<double2>(), dblk, nb, D->svd_s.as<double>(), s));
+    std::vector<double> nrm((size_t)slen, 0.0);
+    MRD_CUDA(ctx, cudaMemcpyAsync(nrm.data(), D->svd_s.p, (size_t)slen * 8, cudaMemcpyDeviceToHost, s));
+    MRD_CUDA(ctx, cudaStreamSynchronize(s));
+    std::vector<double> all;
+    all.reserve((size_t)cols_all);
+    for (int b = 0; b < nb; ++b)
+      for (int64_t j = 0; j < blk[SVF * b + 3]; ++j) all.push_back(nrm[(size_t)(blk[SVF * b + 8] + j)]);
+    std::nth_element(all.begin(), all.begin() + (chi - 1), all.end(), std::greater<double>());
+    const double tau2 = kSetAsideFrac * kSetAsideFrac * all[(size_t)(chi - 1)];
+    std::vector<int32_t> perm((size_t)slen, 0);
+    for (int b = 0; b < nb; ++b) {
+      int64_t* d = &blk[SVF * b];
+      int64_t k = 0;
+      for (int pass = 0; pass < 2; ++pass)   // columns that stay first, then those set aside
+        for (int64_t j = 0; j < d[3]; ++j)
+          if ((nrm[(size_t)(d[8] + j)] >= tau2) == (pass == 0)) perm[(size_t)(d[8] + k++)] = (int32_t)j;
+      int64_t act = 0;
+      for (int64_t j = 0; j < d[3]; ++j) act += nrm[(size_t)(d[8] + j)] >= tau2;
+      d[3] = act;
+      cols_kept += act;
+    }
+    MRD_CUDA(ctx, D->svd_perm.need((size_t)std::max<int64_t>(slen, 1) * 4));
+    MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_perm.p, perm.data(), (size_t)slen * 4, cudaMemcpyHostToDevice, s));
+    MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_blk.p, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice, s));
+    // the final sweeps' schedule on the remaining columns, largest blocks first
+    std::stable_sort(order, order + nb, [&](int64_t x, int64_t y) {
+      return blk[SVF * x + 3] * blk[SVF * x + 2] > blk[SVF * y + 3] * blk[SVF * y + 2];
+    });
+    s64 = schedule(s64.W, false, pp.data() + nb + 1);
+    MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_pref.p, pp.data(), pp.size() * 8, cudaMemcpyHostToDevice, s));
+    MRD_CUDA(ctx, svd_gather_cols(D->svd_work.as<double2>(), D->svd_x2.as<double2>(), dblk, nb,
+                                  D->svd_perm.as<int>(), s));
+    MRD_CUDA(ctx, cudaStreamSynchronize(s));   // host tables of the copies above leave scope
+    set_aside = true;
+  } else {
+    cols_kept = cols_all;
     MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_work.p, D->svd_x2.p, (size_t)xlen * 16, cudaMemcpyDeviceToDevice, s));
   }
+  D->svd_cols[0] = (double)cols_kept;
+  D->svd_cols[1] = (double)cols_all;
+  (void)set_aside;
   }
   // float-float sweeps work on a float-float copy of X in svd_x2 (16 bytes per element either way)
   const bool ffm = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
@@ -1353,9 +1417,11 @@ int mrd_dmrg_schmidt(const mrd_dmrg* D, int32_t* bond, int64_t* n, int32_t* nk, 
   return MRD_OK;
 }
 
-int mrd_dmrg_svd_stats(const mrd_dmrg* D, double* out6) {
-  if (!D || !out6) return MRD_E_ARG;
-  for (int k = 0; k < 6; ++k) out6[k] = D->svd_stats[k];
+int mrd_dmrg_svd_stats(const mrd_dmrg* D, double* out8) {
+  if (!D || !out8) return MRD_E_ARG;
+  for (int k = 0; k < 6; ++k) out8[k] = D->svd_stats[k];
+  out8[6] = D->svd_cols[0];
+  out8[7] = D->svd_cols[1];
   return MRD_OK;
 }
 

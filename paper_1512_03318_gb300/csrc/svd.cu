@@ -25,7 +25,9 @@
 namespace mrd {
 
 // Per-block descriptor (int64): m n p r x_off v_off out_u_off out_vh_off s_off wide
-enum { SVF = 12 };   // + field 10: X32 offset, 11: V32 offset (float2 units)
+// + field 10: X32 offset, 11: V32 offset (float2 units), 12: value slots of the block (r before
+// columns were set aside after the FP32 pre-sweeps; the slots past r hold zeros)
+enum { SVF = 13 };
 constexpr int kSvdMaxSmem = 220 * 1024;
 
 namespace {
@@ -483,6 +485,39 @@ __global__ void k_svd_sort_values(const int64_t* __restrict__ blk, int nblk, dou
     }
     o[rank] = v;
   }
+  for (int64_t j = r + threadIdx.x; j < d[12]; j += blockDim.x) o[j] = 0.0;
+}
+
+// Squared norms of the columns of X (FP64, field 4) of every block, one warp per column:
+// out[s_off + j] for j < r.
+__global__ void k_svd_colnorm2(const double2* __restrict__ work, const int64_t* __restrict__ blk, int nblk,
+                               double* __restrict__ out) {
+  const int b = blockIdx.y;
+  if (b >= nblk) return;
+  const int64_t* d = blk + SVF * b;
+  const int64_t p = d[2], r = d[3];
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); j < r; j += (int64_t)gridDim.x * (blockDim.x / 32)) {
+    const double2* x = work + d[4] + j * p;
+    double acc = 0.0;
+    for (int64_t t = lane; t < p; t += 32) acc = fma(x[t].x, x[t].x, fma(x[t].y, x[t].y, acc));
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[d[8] + j] = acc;
+  }
+}
+
+// Columns of every block gathered in a new order: X[:, j] = src[:, perm[s_off + j]] for j < r
+// (X at field 4 of work, src with the same offsets).
+__global__ void k_svd_gather_cols(double2* __restrict__ work, const double2* __restrict__ src,
+                                  const int64_t* __restrict__ blk, int nblk, const int* __restrict__ perm) {
+  const int b = blockIdx.y;
+  if (b >= nblk) return;
+  const int64_t* d = blk + SVF * b;
+  const int64_t p = d[2], r = d[3];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < p * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / p, t = e % p;
+    work[d[4] + j * p + t] = src[d[4] + (int64_t)perm[d[8] + j] * p + t];
+  }
 }
 
 // Global truncation, three launches. keep[b] = number of kept values of block b (the chi
@@ -495,7 +530,7 @@ __global__ void k_trunc_prep(const int64_t* __restrict__ blk, int nblk, const do
   const int b = blockIdx.x;
   if (b >= nblk) return;
   const int64_t* d = blk + SVF * b;
-  for (int64_t k = threadIdx.x; k < d[3]; k += blockDim.x) flat_block[d[8] + k] = b;
+  for (int64_t k = threadIdx.x; k < d[12]; k += blockDim.x) flat_block[d[8] + k] = b;
   if (threadIdx.x == 0) {
     keep[b] = 0;
     if (d[3] > 0)
@@ -662,6 +697,23 @@ cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double
   k_svd_finish<<<nblk, 256, 0, s>>>(work, blk, nblk, U, Vh, S, order_scratch, fro2);
   mrd::count_launch();
   k_svd_sort_values<<<nblk, 256, 0, s>>>(blk, nblk, S, S_sorted);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t svd_colnorm2(const double2* work, const int64_t* blk, int nblk, double* out, cudaStream_t s) {
+  if (nblk == 0) return cudaSuccess;
+  dim3 grid(16, nblk);
+  k_svd_colnorm2<<<grid, 256, 0, s>>>(work, blk, nblk, out);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t svd_gather_cols(double2* work, const double2* src, const int64_t* blk, int nblk, const int* perm,
+                            cudaStream_t s) {
+  if (nblk == 0) return cudaSuccess;
+  dim3 grid(32, nblk);
+  k_svd_gather_cols<<<grid, 256, 0, s>>>(work, src, blk, nblk, perm);
   mrd::count_launch();
   return cudaGetLastError();
 }

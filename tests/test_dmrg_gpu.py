@@ -249,3 +249,27 @@ def test_bench_form_entanglement_spectrum_matches_ed(ctx):
     assert abs(e - w[0]) <= 1e-9 * abs(w[0])
     assert abs(sum(np.sum(v ** 2) for v in got.values()) - 1.0) < 1e-12
     _compare_spectra(got, ref, 1e-5)
+
+
+def test_set_aside_columns_do_not_change_truncated_sweeps(ctx):
+    """Truncating sweeps (4 x 4 cylinder, V = 1, chi = 24): the block SVD with FP32 pre-sweeps
+    sets aside, before its final sweeps, the columns whose norm is below half the chi-th
+    largest (their weight is truncated anyway); the float-float sweeps alone keep every
+    column. Both reach the same energy (to 1e-9 relative) and keep at most chi states."""
+    import paper_1512_03318_gb300 as P
+    lx, ly, n = 4, 4, 4
+    e_ed = [ed_sector(lx, ly, 0.25, 1.0, 1.0, n, k) for k in range(ly)]
+    k0 = int(np.argmin(e_ed))
+    out = {}
+    for mode in (P.MRD_SVD_F32_FF, P.MRD_SVD_FF):
+        p = P.DMRG.params(24, 1e-14, 40, 1e-14, P.MRD_PREC_FP64, svd_mode=mode, refine_prec=P.MRD_PREC_FF)
+        es, d = run_dmrg(ctx, lx, ly, 4, 1.0, 1.0, n, k0, 24, sweeps=6, params=p)
+        st = d.svd_stats()
+        out[mode] = (es[-1], st[6], st[7])
+        assert max(d.bond(b)[:, 2].sum() for b in range(1, 16)) <= 24
+        d.close()
+    e_a, kept_a, all_a = out[P.MRD_SVD_F32_FF]
+    e_b, kept_b, all_b = out[P.MRD_SVD_FF]
+    assert kept_b == all_b and kept_a <= all_a
+    assert abs(e_a - e_b) <= 1e-9 * abs(e_b)
+    assert e_ed[k0] - 1e-10 < e_a
