@@ -565,6 +565,167 @@ def ly8_forms(P, ctx, torch, dev, details):
     return out
 
 
+def free_fermion_k(lx, ly, flux, n, t=T_HOP):
+    """Momentum sector (sum of the occupied m mod Ly) of the free-fermion ground state of the
+    cylinder (Eq. H_kin: per momentum k_m the Lx x Lx tridiagonal with diagonal
+    -2t cos(k_m + x phi) and off-diagonal -t); the interacting ground state is taken in it."""
+    lev = []
+    for m in range(ly):
+        k = 2 * np.pi * m / ly
+        h = np.diag([-2 * t * np.cos(k + x * 2 * np.pi * flux) for x in range(lx)])
+        h += np.diag([-t] * (lx - 1), 1) + np.diag([-t] * (lx - 1), -1)
+        lev += [(e, m) for e in np.linalg.eigvalsh(h)]
+    lev.sort()
+    return sum(m for _, m in lev[:n]) % ly
+
+
+def sweeps_mixed_vs_real(P, ctx, torch, dev, chi=1024, lx=16, ly=8, max_sweeps=14, tol=1e-8, chi0=128):
+    """The paper's basis comparison (Sec. III.B, Fig. 3(c, d)) on this build's own code: finite
+    two-site DMRG sweeps from a seeded random MPS to convergence on the Ly = 8 interacting
+    Hofstadter cylinder (flux 1/8, t = V = 1, one particle per ring), in the mixed basis
+    (charges N, K; K of the free-fermion ground state) and in real space (charge N only), both
+    in the benchmarked reduced-precision form. The kept bond dimension doubles every sweep from
+    chi0 up to chi, then sweeps repeat until the sweep energy changes by less than tol
+    (relative), at most max_sweeps. Reports the time per sweep, the energies and the
+    device-memory high-water mark: total minus the least free memory seen after any sweep,
+    the library's cache released before each basis (the cache keeps what a run allocated, so
+    this includes its transient buffers)."""
+    out = {}
+    kk = free_fermion_k(lx, ly, 1 / 8, lx)
+    for name, basis in (("mixed", P.MRD_BASIS_MIXED), ("real", P.MRD_BASIS_REAL)):
+        ctx.release_cached()
+        torch.cuda.synchronize(dev)
+        free0, total = torch.cuda.mem_get_info(dev)
+        mpo = P.MPO(None, lx, ly, 1, 8, T_HOP, V_INT, basis)
+        st = P.DMRG(ctx, mpo, lx, kk if basis == P.MRD_BASIS_MIXED else 0, chi, seed=21, center=0)
+        free_min = torch.cuda.mem_get_info(dev)[0]
+        es, times, chis = [], [], []
+        c = chi0
+        for _ in range(max_sweeps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            es.append(st.sweep(mixed_params(P, c)))
+            torch.cuda.synchronize(dev)
+            times.append(time.perf_counter() - t0)
+            chis.append(c)
+            free_min = min(free_min, torch.cuda.mem_get_info(dev)[0])
+            if c == chi and len(es) > 1 and chis[-2] == chi and abs(es[-1] - es[-2]) < tol * abs(es[-1]):
+                break
+            c = min(chi, 2 * c)
+        full = [t for t, x in zip(times, chis) if x == chi]
+        out[name] = {"energies": es, "chi_per_sweep": chis, "s_per_sweep": times, "sweeps": len(es),
+                     "converged": len(full) > 1 and abs(es[-1] - es[-2]) < tol * abs(es[-1]),
+                     "s_per_sweep_at_chi": sum(full) / max(len(full), 1), "s_total": sum(times),
+                     "mem_high_water_gb": (free0 - free_min) / 1e9,
+                     "max_bond": int(max(st.bond(b)[:, 2].sum() for b in range(1, lx * ly)))}
+        st.close()
+        mpo.close()
+    m, r = out["mixed"], out["real"]
+    out["ratio_real_over_mixed"] = {"s_per_sweep_at_chi": r["s_per_sweep_at_chi"] / m["s_per_sweep_at_chi"],
+                                    "s_total": r["s_total"] / m["s_total"],
+                                    "mem_high_water": r["mem_high_water_gb"] / max(m["mem_high_water_gb"], 1e-9)}
+    out["dE_rel_real_vs_mixed"] = abs(r["energies"][-1] - m["energies"][-1]) / abs(m["energies"][-1])
+    out["workload"] = (f"Ly={ly} Lx={lx} flux=1/8 t=1 V=1 N={lx} K={kk}, chi {chi0}->{chi}, split-BF16 Lanczos + "
+                       f"float-float refinement, FP32 + float-float SVD, float-float environments")
+    return out
+
+
+def config5(P, ctx, torch, dev, chi=8000, ly=12, lx=4, fp64_matvecs=53):
+    """The memory-bound scale: the Ly = 12 cylinder (flux 1/6, t = V = 1, the lowest band
+    filled: 2 particles per ring), chi = 8000 at the centre bonds, environments stored in
+    complex64 (MRD_DMRG_OPT_ENV_FP32). A 4-ring cylinder whose bond caps double towards the
+    centre (so that the state and its environments can be built in seconds) holds one
+    two-site update with chi = 8000 on both outer bonds of its H_eff. Reported: seconds of that
+    update in the benchmarked reduced-precision form, the split-BF16 H_eff TFLOP/s inside it,
+    the HBM GB/s of one environment update (complex64 in and out), the device memory of the
+    state, the byte estimate of all environments of a 24-ring cylinder at this bond dimension
+    in complex64 and complex128 against the device, and the plain FP64 H_eff matvec time
+    (times the FP64 form's matvec count at chi = 3200: an estimate of its update time)."""
+    seed5 = 1234 + 4
+    n = lx * ly
+    i = (lx // 2) * ly + ly // 2 - 1
+    def cap(j):
+        dist = 0 if i <= j <= i + 2 else (i - j if j < i else j - (i + 2))
+        c = max(512, chi >> dist)
+        return [(q[0], q[1], d) for q, d in synth.bond_sectors(c, ly, round(2 * j / ly), synth.substream(seed5, 7, j))]
+    caps = [cap(j) if 2 <= j <= n - 2 else [] for j in range(n + 1)]
+    mpo = P.MPO(None, lx, ly, 1, 6, T_HOP, V_INT, P.MRD_BASIS_MIXED)
+    out = {"workload": f"Ly={ly} Lx={lx} flux=1/6 t=1 V=1 N={2 * lx}, chi={chi} at the centre bonds, env complex64"}
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st = P.DMRG(ctx, mpo, 2 * lx, 0, chi, seed=seed5, center=i, caps=caps)
+    st.set_option(P.MRD_DMRG_OPT_ENV_FP32, 1)
+    torch.cuda.synchronize(dev)
+    out["state_build_s"] = time.perf_counter() - t0
+    prm = mixed_params(P, chi)
+    st.update(i, +1, prm)                       # tile tuning for this problem class
+    lb, rb = st.bond(i + 1), st.bond(i + 3)
+    out["bond_dims"] = [int(lb[:, 2].sum()), int(rb[:, 2].sum())]
+    st.timing(True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e, trunc = st.update(i + 1, +1, prm)
+    torch.cuda.synchronize(dev)
+    out["s_per_update"] = time.perf_counter() - t0
+    kms, kn = st.timing(False)
+    out["phase_ms"] = dict(zip(["tables", "theta", "lanczos+refine", "svd", "tensors", "env"],
+                               np.round(st.phase_ms(), 1).tolist()))
+    cnt = st.stats()[2]
+    h = heff_of_bonds(P, ctx, mpo, i + 1, lb, rb)
+    fd, fe, _, _ = h.flops()
+    theta_len, lenv_len, renv_len = h.theta_len, h.lenv_len, h.renv_len
+    h.close()
+    ntc = cnt % 1000
+    out["heff_flops_definition"] = fd
+    out["heff_tflops_bf16x3"] = fd * ntc / (kms[0] + kms[1]) / 1e9 if kms[0] + kms[1] > 0 else None
+    out["heff_bf16x3_ms"] = (kms[0] + kms[1]) / max(ntc, 1)
+    out["theta_elems"] = theta_len
+    # one environment update in complex64 storage: read L (8 B), the site tensor (16 B), write L'
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st.env_update(i + 1, +1, PREC["ff"])
+    torch.cuda.synchronize(dev)
+    t_env = time.perf_counter() - t0
+    l_in, l_out, a_len = lenv_len, st.env_len(i + 2, 0), st.site_len(i + 1)
+    env_bytes = 8 * (l_in + l_out) + 16 * a_len
+    out["env_update_ms"] = 1e3 * t_env
+    out["env_update_gbs"] = env_bytes / t_env / 1e9
+    mem = st.memory()
+    out["state_memory_gb"] = {"environments": mem[0] / 1e9, "environments_built": mem[1], "mps": mem[2] / 1e9}
+    # byte estimate of all environments of a 24-ring cylinder (289 bonds, left and right
+    # environments at every bulk bond) at the centre's size
+    per_env = 8.0 * (l_in + l_out) / 2
+    n24 = 24 * ly
+    free, total = torch.cuda.mem_get_info(dev)
+    out["env_estimate_lx24_gb"] = {"complex64": 2 * (n24 - 1) * per_env / 1e9,
+                                   "complex128": 2 * (n24 - 1) * per_env * 2 / 1e9, "device_total": total / 1e9,
+                                   "budget": 180.0}
+    out["energy"], out["discarded_weight"] = e, trunc
+    st.close()
+    # plain FP64 H_eff on the same shapes (seeded random environments)
+    h = heff_of_bonds(P, ctx, mpo, i + 1, lb, rb)
+    s = synth.substream(seed5, 100)
+    L = torch.from_numpy(synth.complex_pm1(synth.substream(s, 8), h.lenv_len)).to(dev)
+    R = torch.from_numpy(synth.complex_pm1(synth.substream(s, 9), h.renv_len)).to(dev)
+    T = torch.from_numpy(synth.complex_pm1(synth.substream(s, 10), h.theta_len)).to(dev)
+    o = torch.empty_like(T)
+    h.set_env(L, R)
+    h.apply(T, o, PREC["fp64"])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    h.apply(T, o, PREC["fp64"])
+    torch.cuda.synchronize(dev)
+    t64 = time.perf_counter() - t0
+    h.close()
+    del L, R, T, o
+    out["fp64_matvec_s"] = t64
+    out["fp64_form_s_per_update_estimate"] = t64 * fp64_matvecs
+    out["speedup_vs_fp64_estimate"] = t64 * fp64_matvecs / out["s_per_update"]
+    mpo.close()
+    ctx.release_cached()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -582,6 +743,12 @@ def main():
                     help="warm-up updates, then one update inside a CUDA profiler range (ncu --profile-from-start off)")
     ap.add_argument("--details", default="bench_details.json", help="file for the per-workload details")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (Ly = 8 forms, real vs mixed)")
+    ap.add_argument("--sweeps", action="store_true",
+                    help="only: converged sweeps in the mixed and the real-space basis (Ly = 8), one JSON line")
+    ap.add_argument("--config5", action="store_true",
+                    help="only: the Ly = 12, chi = 8000 update with complex64 environments, one JSON line")
+    ap.add_argument("--sweeps-chi", type=int, default=1024)
+    ap.add_argument("--sweeps-lx", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -615,6 +782,15 @@ def main():
         done = [k for k in PREC if k in mv]
         print(json.dumps({"only_matvec": True, "chi": chi, "heff_tflops": {k: mv[k]["tflops"] for k in done},
                           "heff_ms_steps": {k: [mv[k]["ms_step1"], mv[k]["ms_step2"]] for k in done}}))
+        return 0
+
+    if args.config5:
+        print(json.dumps({"config5": config5(P, ctx, torch, dev)}, default=float))
+        return 0
+
+    if args.sweeps:
+        res = sweeps_mixed_vs_real(P, ctx, torch, dev, chi=args.sweeps_chi, lx=args.sweeps_lx)
+        print(json.dumps({"sweeps_mixed_vs_real": res}))
         return 0
 
     if args.profile_update:

@@ -76,6 +76,10 @@ typedef struct mrd_dmrg mrd_dmrg;
 int mrd_create(mrd_ctx** out, int device, void* stream);
 int mrd_destroy(mrd_ctx* ctx);
 int mrd_set_stream(mrd_ctx* ctx, void* stream);
+/* Return to the device the memory the library keeps cached for reuse on this context's device
+ * (blocks released by freed handles); waits for the context stream first. Memory of live
+ * handles is not touched. */
+int mrd_release_cached(mrd_ctx* ctx);
 /* Message of the last failing call on this context (static storage of the context). */
 const char* mrd_last_error(const mrd_ctx* ctx);
 /* Library version as major*10000 + minor*100 + patch. */
@@ -276,6 +280,21 @@ int mrd_sweep(mrd_dmrg* d, const mrd_dmrg_params* p, double* energy);
  * MRD_E_ARG for a site outside 0..n-2 (+1) or 1..n-1 (-1), MRD_E_STATE if the input
  * environment has not been built. */
 int mrd_env_update(mrd_dmrg* d, int32_t site, int32_t direction, int32_t prec);
+/* Options of a DMRG state:
+ *   MRD_DMRG_OPT_ENV_FP32   0 (default): environments are stored in complex128; 1: stored in
+ *                           complex64 (half the bytes, for the memory-bound scale of large
+ *                           circumferences and bond dimensions). Setting it converts the
+ *                           environments already built; later environment updates compute in
+ *                           FP64 or float-float as before and round their result to complex64
+ *                           for storage, and an update widens the two environments it reads
+ *                           back to complex128 before folding them with the MPO. The rounding
+ *                           (2^-24 relative per entry) enters the H_eff of later updates.
+ * MRD_E_ARG for an unknown option. */
+#define MRD_DMRG_OPT_ENV_FP32 1
+int mrd_dmrg_set_option(mrd_dmrg* d, int32_t option, int64_t value);
+/* Device memory of a DMRG state: out4 = {bytes of the stored environments, environments
+ * built, bytes of the MPS tensors, 1 if environments are stored in complex64}. */
+int mrd_dmrg_memory(const mrd_dmrg* d, int64_t* out4);
 /* Sectors of MPS bond `bond` (0..n) as (N, K, dim) triplets (sectors may be NULL). */
 int mrd_dmrg_bond(const mrd_dmrg* d, int32_t bond, int32_t* n_sectors, int32_t* sectors);
 /* Copy of MPS tensor `site` to the host (complex128). mode 0: blocks grouped by right

@@ -25,6 +25,7 @@ MRD_SVD_F32_FF = 0
 MRD_SVD_FF = 1
 MRD_SVD_F32_F64 = 2
 MRD_SVD_F64 = 3
+MRD_DMRG_OPT_ENV_FP32 = 1
 
 _LIB = None
 _LIVE = []        # weak references to open handles, closed in creation-reverse order at exit
@@ -86,6 +87,7 @@ _SIGS = {
     "mrd_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     "mrd_destroy": (C.c_int, [C.c_void_p]),
     "mrd_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mrd_release_cached": (C.c_int, [C.c_void_p]),
     "mrd_last_error": (C.c_char_p, [C.c_void_p]),
     "mrd_mpo_build": (C.c_int, [C.c_void_p, C.POINTER(mrd_model), C.POINTER(C.c_void_p)]),
     "mrd_mpo_free": (C.c_int, [C.c_void_p]),
@@ -113,6 +115,8 @@ _SIGS = {
                                       C.POINTER(C.c_double)]),
     "mrd_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_env_update": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "mrd_dmrg_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "mrd_dmrg_memory": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "mrd_dmrg_bond": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mrd_dmrg_site": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_double)]),
@@ -197,6 +201,10 @@ class Context:
     def check(self, rc):
         if rc != 0:
             raise MrdError(rc, lib().mrd_last_error(self.h).decode())
+
+    def release_cached(self):
+        """mrd_release_cached: free the device memory the library holds cached for reuse."""
+        self.check(lib().mrd_release_cached(self.h))
 
     def measure_peaks(self):
         """mrd_measure_peaks: (FP32 FMA instr/s, FP64 FMA instr/s, SMs, max SM clock Hz)."""
@@ -325,6 +333,16 @@ class DMRG:
         self.ctx.check(lib().mrd_sweep(self.h, C.byref(params), C.byref(e)))
         return e.value
 
+    def set_option(self, option, value):
+        """mrd_dmrg_set_option (MRD_DMRG_OPT_ENV_FP32)."""
+        self.ctx.check(lib().mrd_dmrg_set_option(self.h, option, int(value)))
+
+    def memory(self):
+        """(environment bytes, environments built, MPS bytes, complex64 storage) of the state."""
+        out = (C.c_int64 * 4)()
+        self.ctx.check(lib().mrd_dmrg_memory(self.h, out))
+        return tuple(out)
+
     def env_update(self, site, direction, prec=MRD_PREC_FP64):
         """mrd_env_update: rebuild the left environment of bond site+1 (direction +1) or the right
         environment of bond site (direction -1) from the neighbouring one."""
@@ -352,6 +370,12 @@ class DMRG:
         buf = np.zeros(2 * max(ln.value, 1), dtype=np.float64)
         self.ctx.check(lib().mrd_dmrg_env(self.h, b, side, C.byref(ln), _p64f(buf)))
         return (buf[0::2] + 1j * buf[1::2])[: ln.value]
+
+    def env_len(self, b, side):
+        """Length (complex elements) of the environment at bond b (side 0 left, 1 right); -1 if not built."""
+        ln = C.c_int64()
+        self.ctx.check(lib().mrd_dmrg_env(self.h, b, side, C.byref(ln), None))
+        return ln.value
 
     def set_site(self, j, host_ptr):
         """host_ptr: address of complex128 data (e.g. a pinned torch tensor's data_ptr())."""

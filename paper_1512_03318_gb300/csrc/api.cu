@@ -89,6 +89,14 @@ int mrd_destroy(mrd_ctx* ctx) {
   return MRD_OK;
 }
 
+int mrd_release_cached(mrd_ctx* ctx) {
+  if (!ctx) return MRD_E_ARG;
+  Guard g(ctx->device);
+  MRD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  mrd::cache_trim(ctx->device);
+  return MRD_OK;
+}
+
 int mrd_set_stream(mrd_ctx* ctx, void* stream) {
   if (!ctx) return MRD_E_ARG;
   ctx->stream = (cudaStream_t)stream;

@@ -220,6 +220,18 @@ __global__ void __launch_bounds__(256) k_scale_unit(double2* __restrict__ x, int
 
 }  // namespace
 
+// complex128 <-> complex64 copies of environments stored in single precision (round to
+// nearest on the way down, exact on the way up)
+__global__ void k_c128_to_c64(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = make_float2(__double2float_rn(x[e].x), __double2float_rn(x[e].y));
+}
+
+__global__ void k_c64_to_c128(const float2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = make_double2((double)x[e].x, (double)x[e].y);
+}
+
 // ---------------------------------------------------------------- tensors
 
 struct SiteT {
@@ -282,7 +294,8 @@ struct EnvT {
   bool left = true;
   std::vector<int64_t> off;
   int64_t size = 0;
-  Buf data;
+  Buf data;           // complex128, or complex64 when f32
+  bool f32 = false;
   void layout(int mod) {
     off.assign(ch.size() * sec.size(), -1);
     size = 0;
@@ -327,6 +340,10 @@ struct mrd_dmrg {
       zeros, svd_perm;
   // columns entering the final Jacobi sweeps and columns of all blocks, last block SVD
   double svd_cols[2] = {0, 0};
+  // environments stored in complex64 (MRD_DMRG_OPT_ENV_FP32); envx: complex128 working copies
+  // of the two environments an H_eff reads and of an update's output
+  bool env_fp32 = false;
+  Buf envx[3];
   cudaEvent_t svd_ev[2] = {nullptr, nullptr};
   // last block SVD: [0] ms of the final sweeps, [1] element-pairs tested, [2] rotated, [3] sweeps,
   // [4] ms of the FP32 pre-sweeps, [5] svd_mode
@@ -434,6 +451,44 @@ std::vector<std::array<int, 2>> mpo_channels(const HostMPO& m, int bond, int mod
   const auto& v = m.bond_charges[bond];
   for (size_t i = 0; i + 1 < v.size(); i += 2) c.push_back({v[i], kmod(v[i + 1], mod)});
   return c;
+}
+
+cudaError_t conv_c64(const double2* x, float2* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_c128_to_c64<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(x, y, n);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t conv_c128(const float2* x, double2* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_c64_to_c128<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(x, y, n);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+// The complex128 data of an environment: its own buffer, or for single-precision storage a
+// widened copy in working buffer `slot` (valid until the slot is reused).
+int env_fp64(mrd_dmrg* D, EnvT& E, int slot, const double2** out) {
+  if (!E.f32) {
+    *out = E.data.as<double2>();
+    return MRD_OK;
+  }
+  MRD_CUDA(D->ctx, D->envx[slot].need((size_t)std::max<int64_t>(E.size, 1) * 16));
+  MRD_CUDA(D->ctx, conv_c128(E.data.as<float2>(), D->envx[slot].as<double2>(), E.size, D->ctx->stream));
+  *out = D->envx[slot].as<double2>();
+  return MRD_OK;
+}
+
+// Storage of a freshly computed environment: the complex128 result `src` (E.size values)
+// becomes E's data, rounded to complex64 when the state stores environments in single precision.
+int env_store(mrd_dmrg* D, EnvT& E, const double2* src) {
+  mrd_ctx* ctx = D->ctx;
+  E.f32 = D->env_fp32;
+  if (!E.f32) return MRD_OK;   // computed in place
+  MRD_CUDA(ctx, E.data.need((size_t)std::max<int64_t>(E.size, 1) * 8));
+  MRD_CUDA(ctx, conv_c64(src, E.data.as<float2>(), E.size, ctx->stream));
+  return MRD_OK;
 }
 
 // Build the H_eff handle for sites (i, i+1) from the current bonds; env pointers may be the
@@ -807,8 +862,9 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
   E.ch = cm;
   E.left = true;
   E.layout(mod);
-  MRD_CUDA(ctx, E.data.need((size_t)std::max<int64_t>(E.size, 1) * 16));
-  MRD_CUDA(ctx, cudaMemsetAsync(E.data.p, 0, (size_t)std::max<int64_t>(E.size, 1) * 16, ctx->stream));
+  Buf& eout = D->env_fp32 ? D->envx[2] : E.data;   // complex128 result, rounded afterwards in FP32 storage
+  MRD_CUDA(ctx, eout.need((size_t)std::max<int64_t>(E.size, 1) * 16));
+  MRD_CUDA(ctx, cudaMemsetAsync(eout.p, 0, (size_t)std::max<int64_t>(E.size, 1) * 16, ctx->stream));
   GemmList g2;
   for (int w = 0; w < (int)cm.size(); ++w)
     for (int c = 0; c < (int)cs.size(); ++c) {
@@ -828,7 +884,9 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
         g2.seg(ao, ald, it->second.off, cs[c].d, ls[ap].d, 1);
       }
     }
-  return run_gemm(D, g2, A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen, E.data.as<double2>(), E.size);
+  rc = run_gemm(D, g2, A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen, eout.as<double2>(), E.size);
+  if (rc != MRD_OK) return rc;
+  return env_store(D, E, eout.as<double2>());
 }
 
 // R[i+1] = B (W_{i+1} R[i+2]) B^+ with B = D->A[i+1] (mode 1) and the WR fold of h.
@@ -882,8 +940,9 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
   E.ch = cm;
   E.left = false;
   E.layout(mod);
-  MRD_CUDA(ctx, E.data.need((size_t)std::max<int64_t>(E.size, 1) * 16));
-  MRD_CUDA(ctx, cudaMemsetAsync(E.data.p, 0, (size_t)std::max<int64_t>(E.size, 1) * 16, ctx->stream));
+  Buf& eout = D->env_fp32 ? D->envx[2] : E.data;   // complex128 result, rounded afterwards in FP32 storage
+  MRD_CUDA(ctx, eout.need((size_t)std::max<int64_t>(E.size, 1) * 16));
+  MRD_CUDA(ctx, cudaMemsetAsync(eout.p, 0, (size_t)std::max<int64_t>(E.size, 1) * 16, ctx->stream));
   GemmList g2;
   for (int w = 0; w < (int)cm.size(); ++w)
     for (int c = 0; c < (int)cs.size(); ++c) {
@@ -902,7 +961,9 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
         g2.seg(it->second.off, it->second.cols, bo, bld, bs[bp].d, 2);
       }
     }
-  return run_gemm(D, g2, D->tbuf.as<double2>(), tlen, B.data.as<double2>(), B.size, E.data.as<double2>(), E.size);
+  rc = run_gemm(D, g2, D->tbuf.as<double2>(), tlen, B.data.as<double2>(), B.size, eout.as<double2>(), E.size);
+  if (rc != MRD_OK) return rc;
+  return env_store(D, E, eout.as<double2>());
 }
 
 int set_trivial_env(mrd_dmrg* D, EnvT& E, const Secs& sec, int bond, bool left) {
@@ -911,6 +972,7 @@ int set_trivial_env(mrd_dmrg* D, EnvT& E, const Secs& sec, int bond, bool left) 
   E.left = left;
   E.layout(D->mod);
   if (E.size != 1) return mrd_fail(D->ctx, MRD_E_STATE, "boundary environment is not 1 x 1");
+  E.f32 = false;
   MRD_CUDA(D->ctx, E.data.need(16));
   const double2 one = make_double2(1.0, 0.0);
   MRD_CUDA(D->ctx, cudaMemcpy(E.data.p, &one, 16, cudaMemcpyHostToDevice));
@@ -1084,13 +1146,17 @@ int mrd_dmrg_create(mrd_ctx* ctx, const mrd_mpo* mpo, int32_t n_part, int32_t k_
   // left environments up to the centre, right environments down to centre + 2
   for (int j = 0; j < center && rcd == MRD_OK; ++j) {
     mrd_heff* h = nullptr;
-    rcd = make_heff(D, j, D->L[j].data.as<double2>(), nullptr, &h);
+    const double2* lj = nullptr;
+    rcd = env_fp64(D, D->L[j], 0, &lj);
+    if (rcd == MRD_OK) rcd = make_heff(D, j, lj, nullptr, &h);
     if (rcd == MRD_OK) rcd = env_left(D, h, j);
     if (h) mrd_heff_free(h);
   }
   for (int j = n - 1; j >= center + 2 && rcd == MRD_OK; --j) {
     mrd_heff* h = nullptr;
-    rcd = make_heff(D, j - 1, nullptr, D->R[j + 1].data.as<double2>(), &h);
+    const double2* rj = nullptr;
+    rcd = env_fp64(D, D->R[j + 1], 1, &rj);
+    if (rcd == MRD_OK) rcd = make_heff(D, j - 1, nullptr, rj, &h);
     if (rcd == MRD_OK) rcd = env_right(D, h, j - 1);
     if (h) mrd_heff_free(h);
   }
@@ -1141,7 +1207,10 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
     t0 = t1;
   };
   mrd_heff* h = nullptr;
-  int rc = make_heff(D, i, D->L[i].data.as<double2>(), D->R[i + 2].data.as<double2>(), &h);
+  const double2 *le = nullptr, *re = nullptr;
+  int rc = env_fp64(D, D->L[i], 0, &le);
+  if (rc == MRD_OK) rc = env_fp64(D, D->R[i + 2], 1, &re);
+  if (rc == MRD_OK) rc = make_heff(D, i, le, re, &h);
   if (rc != MRD_OK) return rc;
   struct Free { mrd_heff* h; ~Free() { if (h) mrd_heff_free(h); } } guard{h};
   if (D->timing) mrd_heff_timing(h, 1);
@@ -1334,8 +1403,10 @@ int mrd_env_update(mrd_dmrg* D, int32_t site, int32_t direction, int32_t prec) {
   D->gemm_ff = prec == MRD_PREC_FF;
   mrd_heff* h = nullptr;
   const int i = direction > 0 ? site : site - 1;
-  int rc = direction > 0 ? make_heff(D, i, D->L[i].data.as<double2>(), nullptr, &h)
-                         : make_heff(D, i, nullptr, D->R[i + 2].data.as<double2>(), &h);
+  const double2* ein = nullptr;
+  int rc = env_fp64(D, direction > 0 ? D->L[i] : D->R[i + 2], direction > 0 ? 0 : 1, &ein);
+  if (rc == MRD_OK)
+    rc = direction > 0 ? make_heff(D, i, ein, nullptr, &h) : make_heff(D, i, nullptr, ein, &h);
   if (rc != MRD_OK) return rc;
   rc = direction > 0 ? env_left(D, h, i) : env_right(D, h, i);
   mrd_heff_free(h);
@@ -1373,8 +1444,54 @@ int mrd_dmrg_env(mrd_dmrg* D, int32_t bond, int32_t side, int64_t* len, double* 
   if (host && E.data.p && E.size) {
     Guard g(D->ctx->device);
     MRD_CUDA(D->ctx, cudaStreamSynchronize(D->ctx->stream));
-    MRD_CUDA(D->ctx, cudaMemcpy(host, E.data.p, (size_t)E.size * 16, cudaMemcpyDeviceToHost));
+    if (E.f32) {   // complex64 storage, widened on the host
+      std::vector<float> t((size_t)E.size * 2);
+      MRD_CUDA(D->ctx, cudaMemcpy(t.data(), E.data.p, (size_t)E.size * 8, cudaMemcpyDeviceToHost));
+      for (size_t k = 0; k < t.size(); ++k) host[k] = (double)t[k];
+    } else {
+      MRD_CUDA(D->ctx, cudaMemcpy(host, E.data.p, (size_t)E.size * 16, cudaMemcpyDeviceToHost));
+    }
   }
+  return MRD_OK;
+}
+
+int mrd_dmrg_set_option(mrd_dmrg* D, int32_t option, int64_t value) {
+  if (!D) return MRD_E_ARG;
+  mrd_ctx* ctx = D->ctx;
+  if (option != MRD_DMRG_OPT_ENV_FP32) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_set_option: unknown option");
+  Guard g(ctx->device);
+  D->env_fp32 = value != 0;
+  cudaStream_t s = ctx->stream;
+  // convert the stored environments (the 1 x 1 boundary ones stay complex128)
+  for (std::vector<EnvT>* side : {&D->L, &D->R})
+    for (EnvT& E : *side) {
+      if (!E.data.p || E.size <= 1 || E.f32 == D->env_fp32) continue;
+      Buf nb;
+      MRD_CUDA(ctx, nb.need((size_t)E.size * (D->env_fp32 ? 8 : 16)));
+      if (D->env_fp32) MRD_CUDA(ctx, conv_c64(E.data.as<double2>(), nb.as<float2>(), E.size, s));
+      else MRD_CUDA(ctx, conv_c128(E.data.as<float2>(), nb.as<double2>(), E.size, s));
+      MRD_CUDA(ctx, cudaStreamSynchronize(s));
+      std::swap(E.data.p, nb.p);
+      std::swap(E.data.bytes, nb.bytes);
+      E.f32 = D->env_fp32;
+    }
+  return MRD_OK;
+}
+
+int mrd_dmrg_memory(const mrd_dmrg* D, int64_t* out4) {
+  if (!D || !out4) return MRD_E_ARG;
+  int64_t env = 0, nenv = 0, mps = 0;
+  for (const std::vector<EnvT>* side : {&D->L, &D->R})
+    for (const EnvT& E : *side)
+      if (E.data.p) {
+        env += E.size * (E.f32 ? 8 : 16);
+        ++nenv;
+      }
+  for (const SiteT& T : D->A) mps += T.size * 16;
+  out4[0] = env;
+  out4[1] = nenv;
+  out4[2] = mps;
+  out4[3] = D->env_fp32 ? 1 : 0;
   return MRD_OK;
 }
 

@@ -193,3 +193,55 @@ def test_headline_environment_at_production_block_sizes(ctx):
     assert len(sample) >= 8
     compare(d.env(i + 1, 0), oracle_left(d, mpo, i, li, sample), 1e-11)
     d.close()
+
+
+def test_fp32_environment_storage(ctx):
+    """Environments stored in complex64 (MRD_DMRG_OPT_ENV_FP32): the stored values are the
+    complex128 ones rounded (2^-24 relative), they take half the bytes, and an environment
+    update in that storage equals the oracle's update of the stored input within the FP32
+    rounding of its result."""
+    import paper_1512_03318_gb300 as P
+    mpo, d = cylinder(ctx, 64, 6)
+    l4_64 = d.env(4, 0)
+    bytes64, n_env, _, f = d.memory()
+    assert f == 0
+    d.set_option(P.MRD_DMRG_OPT_ENV_FP32, 1)
+    bytes32, n_env2, _, f = d.memory()
+    assert f == 1 and n_env2 == n_env
+    assert bytes32 < 0.52 * bytes64 + 64
+    l4 = d.env(4, 0)
+    assert np.max(np.abs(l4 - l4_64)) <= 2.0 ** -24 * np.max(np.abs(l4_64))
+    d.env_update(4, +1, P.MRD_PREC_FF)
+    compare(d.env(5, 0), oracle_left(d, mpo, 4, l4), 3e-7)
+    r10 = d.env(10, 1)
+    d.env_update(9, -1, P.MRD_PREC_FP64)
+    compare(d.env(9, 1), oracle_right(d, mpo, 9, r10), 3e-7)
+    d.close()
+
+
+def test_fp32_environment_sweeps_reach_ed(ctx):
+    """Sweeps of the benchmarked reduced-precision form with complex64 environment storage on
+    the 4 x 4 cylinder (flux 1/4, V = 1, N = 4, chi = 256): the energy reaches the ED ground
+    energy of the sector within 1e-7 relative, the scale of the single-precision rounding of
+    the environments that every later H_eff inherits."""
+    import paper_1512_03318_gb300 as P
+    from oracle import model
+    lx, ly, n = 4, 4, 4
+    e_ed = []
+    for k in range(ly):
+        basis = model.fock_basis(lx * ly, n)
+        basis = np.array([s for s in basis if model.total_momentum(lx, ly, int(s)) == k], dtype=np.uint64)
+        e_ed.append(float(np.linalg.eigvalsh(model.mixed_space_hamiltonian(lx, ly, 0.25, 1.0, 1.0, n, basis=basis))[0]))
+    k0 = int(np.argmin(e_ed))
+    mpo = P.MPO(None, lx, ly, 1, 4, 1.0, 1.0, P.MRD_BASIS_MIXED)
+    d = P.DMRG(ctx, mpo, n, k0, 256, seed=7, center=0)
+    d.set_option(P.MRD_DMRG_OPT_ENV_FP32, 1)
+    p = headline_params(P, 256)
+    es = []
+    for _ in range(6):
+        es.append(d.sweep(p))
+        if len(es) > 1 and abs(es[-1] - es[-2]) < 1e-12 * abs(es[-1]):
+            break
+    assert d.memory()[3] == 1
+    d.close()
+    assert abs(es[-1] - e_ed[k0]) <= 1e-7 * abs(e_ed[k0]), (es, e_ed[k0])
