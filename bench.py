@@ -375,11 +375,13 @@ def real_vs_mixed_or_note(P, ctx, torch, dev, stream):
 
 def mpo_diagnostics(P):
     """Mean and largest MPO bond dimension and mean fill over a bulk ring (the second of three),
-    real-space and mixed machines, against the real-space 3L + 2 (Sec. IV.C-D). Host only."""
+    real-space, mixed (exponential) and mixed sine / cosine machines, against the real-space
+    3L + 2 (Sec. IV.C-D, Eq. rot). Host only."""
     out = {}
     for ly in (4, 6, 8, 10, 12):
         row = {"3L+2": 3 * ly + 2}
-        for name, basis in (("real", P.MRD_BASIS_REAL), ("mixed", P.MRD_BASIS_MIXED)):
+        for name, basis in (("real", P.MRD_BASIS_REAL), ("mixed", P.MRD_BASIS_MIXED),
+                            ("mixed_sin_cos", P.MRD_BASIS_MIXED_REAL)):
             m = P.MPO(None, 3, ly, 1, ly, T_HOP, V_INT, basis)
             mean_d, max_d, fill, _ = m.stats(ly, ly)
             row[name] = {"mean_D": round(mean_d, 3), "max_D": max_d, "fill": round(fill, 4)}
@@ -961,6 +963,10 @@ def main():
             ly8_forms(P, ctx, torch, dev, details)
         except (P.MrdError, torch.cuda.OutOfMemoryError) as e:
             details["ly8"] = {"skipped": f"{type(e).__name__}: {e}"}
+        try:
+            details["config5"] = config5(P, ctx, torch, dev, fp64_matvecs=max(fp64_matvecs % 1000, 1))
+        except (P.MrdError, torch.cuda.OutOfMemoryError) as e:
+            details["config5"] = {"skipped": f"{type(e).__name__}: {e}"}
     details["mpo_diagnostics"] = mpo_diagnostics(P)
 
     if rank != 0:
@@ -1050,6 +1056,13 @@ def main():
                        "chi2048_heff_err": {k: l8["chi2048"][f"heff_{k}_rel_err_vs_fp64"] for k in ("tf32", "bf16x3")},
                        "chi2048_forms": {k[5:]: v for k, v in l8["chi2048"].items() if k.startswith("form_")},
                        "chi2048_fp64_s_per_update": l8["chi2048"]["s_per_update_fp64"]}
+    c5 = details.get("config5", {})
+    if "s_per_update" in c5:
+        line["ly12_chi8000"] = {"s_per_update": c5["s_per_update"], "heff_tflops_bf16x3": c5["heff_tflops_bf16x3"],
+                                "bond_dims": c5["bond_dims"], "env_update_gbs": c5["env_update_gbs"],
+                                "env_storage": "complex64",
+                                "env_estimate_gb": {k: c5["env_estimate_gb"][k] for k in ("complex64", "complex128")},
+                                "fp64_form_s_per_update_estimate": c5["fp64_form_s_per_update_estimate"]}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     line["details"] = args.details

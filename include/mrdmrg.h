@@ -63,6 +63,8 @@ extern "C" {
 
 #define MRD_BASIS_MIXED 0   /* orbitals (x, k_m), charges (N, K mod Ly)                   */
 #define MRD_BASIS_REAL 1    /* orbitals (x, y), charge N only (modulus 1)                 */
+#define MRD_BASIS_MIXED_REAL 2 /* orbitals (x, k_m), charges (N, K mod Ly), the sine /     */
+                               /* cosine machine of Sec. IV.D (Eq. rot): every entry real  */
 
 typedef struct mrd_ctx mrd_ctx;
 typedef struct mrd_mpo mrd_mpo;
@@ -93,7 +95,7 @@ typedef struct {
   int32_t lx, ly;          /* rings along the cylinder, orbitals per ring (ly >= 2)      */
   int32_t flux_p, flux_q;  /* flux per plaquette phi = 2 pi p / q (q > 0)                */
   double t, v;             /* hopping and nearest-neighbour repulsion                    */
-  int32_t basis;           /* MRD_BASIS_MIXED or MRD_BASIS_REAL                          */
+  int32_t basis;           /* MRD_BASIS_MIXED, MRD_BASIS_REAL or MRD_BASIS_MIXED_REAL    */
 } mrd_model;
 
 /* Build the Hamiltonian MPO from its finite-state machine (Sec. IV.A-B): intermediate

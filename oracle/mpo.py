@@ -61,6 +61,7 @@ class Role:
     ring: int | None      # ring offset from the family's base ring (None: any ring)
     phase: int = 0        # placed at momentum m, contributes e^{i phase 2 pi m / Ly}
     label: int = 0        # contributes label * m (mixed) or label * y (real) to the node label
+    trig: str = ""        # 'cos' / 'sin': contributes cos / sin(2 pi m / Ly) instead of a phase
 
 
 @dataclass
@@ -125,6 +126,27 @@ def mixed_families(lx, ly, flux, t, v, penalty=None):
     return fams, onsite
 
 
+def mixed_real_families(lx, ly, flux, t, v, penalty=None):
+    """Term families of the mixed-basis Hamiltonian with real coefficients only (the sine /
+    cosine machine of Sec. IV.D, Eq. rot). The phases of the intra-ring interaction come in
+    pairs e^{+i alpha}, e^{-i alpha}; rotating each pair into cos alpha, sin alpha makes every
+    MPO entry real. Written per term: the literal coefficient of c+_{p1} c_{p2} c+_{p3} c_{p4} in
+    (V/Ly) sum_q cos(q) n_q n_{-q} is (V/Ly) cos((p1 - p2) alpha) = (V/Ly) [cos(p1 alpha)
+    cos(p2 alpha) + sin(p1 alpha) sin(p2 alpha)], so the family splits into a cosine and a
+    sine family whose first two roles each carry one real factor. The hops and the inter-ring
+    interaction are real already (the note after Eq. rot)."""
+    fams, onsite = mixed_families(lx, ly, flux, t, v, penalty)
+    out = []
+    for f in fams:
+        if f.name != "intra":
+            out.append(f)
+            continue
+        for trig in ("cos", "sin"):
+            roles = [Role(r.op, r.ring, 0, r.label, trig if k < 2 else "") for k, r in enumerate(f.roles)]
+            out.append(Family("intra" + trig[0], roles, f.target, f.coeff, f.bases))
+    return out, onsite
+
+
 def real_families(lx, ly, flux, t, v, penalty=None):
     """Term families of the real-space Hamiltonian (Eq. H_real); the label is the position
     y, so the hop around the ring c+_{x,y} c_{x,y+1} closes with label sum -1 (mod Ly)."""
@@ -143,6 +165,15 @@ def real_families(lx, ly, flux, t, v, penalty=None):
         mu, _ = penalty
         fams.append(Family("pen", [Role("n", None), Role("n", None)], 0, lambda x: mu, [0]))
     return fams, (lambda x, m: 0.0)
+
+
+def _trig(kind: str, m: int, ly: int) -> float:
+    """cos or sin of 2 pi m / Ly, exactly zero where the angle is a multiple of pi (sin) or an
+    odd multiple of pi / 2 (cos): rounded library values there (~1e-16) would add spurious
+    transitions to the machine."""
+    if kind == "sin":
+        return 0.0 if (2 * m) % ly == 0 else math.sin(2 * math.pi * m / ly)
+    return 0.0 if (4 * m) % (2 * ly) == ly else math.cos(2 * math.pi * m / ly)
 
 
 def _local_op(roles, placed: int, here: int) -> np.ndarray:
@@ -165,13 +196,15 @@ def build_mpo(lx: int, ly: int, flux: float, t: float, v: float, basis: str = "m
               penalty=None, merge: bool = True) -> MPO:
     """Build, trim and merge the FSM MPO of the cylinder Hamiltonian.
 
-    basis: 'mixed' (orbitals (x, m), charges (N, K mod Ly)) or 'real' (orbitals (x, y),
-    charge N only). penalty: optional (mu, N) adding mu (N_tot - N)^2, used only by the
-    symmetry-free dense DMRG of this oracle."""
+    basis: 'mixed' (orbitals (x, m), charges (N, K mod Ly)), 'mixed_real' (the same orbitals
+    and charges, the sine / cosine machine with real entries) or 'real' (orbitals (x, y), charge
+    N only). penalty: optional (mu, N) adding mu (N_tot - N)^2, used only by the symmetry-free
+    dense DMRG of this oracle."""
     if ly < 2:
         raise ValueError("Ly >= 2 required")
-    fams, onsite = (mixed_families if basis == "mixed" else real_families)(lx, ly, flux, t, v, penalty)
-    modulus = ly if basis == "mixed" else 1
+    make = {"mixed": mixed_families, "mixed_real": mixed_real_families, "real": real_families}[basis]
+    fams, onsite = make(lx, ly, flux, t, v, penalty)
+    modulus = 1 if basis == "real" else ly
     return build_fsm_mpo(lx, ly, fams, onsite, modulus, penalty=penalty, merge=merge)
 
 
@@ -245,8 +278,11 @@ def build_fsm_mpo(lx: int, ly: int, fams, onsite, modulus: int, penalty=None, me
                     for r in range(nr):
                         if here >> r & 1:
                             role = fam.roles[r]
-                            coeff = coeff * complex(math.cos(role.phase * 2 * math.pi * m / ly),
-                                                    math.sin(role.phase * 2 * math.pi * m / ly))
+                            if role.trig:
+                                coeff = coeff * _trig(role.trig, m, ly)
+                            else:
+                                coeff = coeff * complex(math.cos(role.phase * 2 * math.pi * m / ly),
+                                                        math.sin(role.phase * 2 * math.pi * m / ly))
                             lab2 = (lab2 + role.label * m) % ly
                             dn2 += _CHARGE_N[role.op]
                             if role.op == "cd":

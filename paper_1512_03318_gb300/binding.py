@@ -17,6 +17,7 @@ MRD_PREC_BF16X3 = 2
 MRD_PREC_FF = 3
 MRD_BASIS_MIXED = 0
 MRD_BASIS_REAL = 1
+MRD_BASIS_MIXED_REAL = 2
 MRD_OPT_GRAPH = 1
 MRD_OPT_PER_TASK_LAUNCH = 2
 MRD_OPT_AUTOTUNE = 3

@@ -71,7 +71,16 @@ struct Role {
   int ring;      // offset from the base ring; kAnyRing for any
   int phase;     // phase sign
   int label;     // label sign
+  int trig = 0;  // 1: factor cos(2 pi m / Ly), 2: sin(2 pi m / Ly) instead of a phase
 };
+
+// cos / sin of 2 pi m / ly, exactly zero where the angle is an odd multiple of pi/2 (cos) or a
+// multiple of pi (sin): rounded library values there would add spurious transitions
+double trig_of(int kind, int m, int ly) {
+  const double pi = 3.14159265358979323846;
+  if (kind == 2) return (2 * m) % ly == 0 ? 0.0 : std::sin(2.0 * pi * m / ly);
+  return (4 * m) % (2 * ly) == ly ? 0.0 : std::cos(2.0 * pi * m / ly);
+}
 constexpr int kAnyRing = 1 << 20;
 
 struct Family {
@@ -228,7 +237,8 @@ void fuse(std::vector<std::vector<Key>>& bonds, std::vector<Trans>& trans, int n
 }  // namespace
 
 int build_mpo_host(const mrd_model& m, HostMPO* out, std::string* err) {
-  if (m.ly < 2 || m.lx < 1 || m.flux_q <= 0 || (m.basis != MRD_BASIS_MIXED && m.basis != MRD_BASIS_REAL)) {
+  if (m.ly < 2 || m.lx < 1 || m.flux_q <= 0 ||
+      (m.basis != MRD_BASIS_MIXED && m.basis != MRD_BASIS_REAL && m.basis != MRD_BASIS_MIXED_REAL)) {
     *err = "mrd_mpo_build: need ly >= 2, lx >= 1, flux_q > 0 and a known basis";
     return MRD_E_ARG;
   }
@@ -239,7 +249,7 @@ int build_mpo_host(const mrd_model& m, HostMPO* out, std::string* err) {
   const int lx = m.lx, ly = m.ly, n = lx * ly;
   const double pi = 3.14159265358979323846;
   const double phi = 2.0 * pi * (double)m.flux_p / (double)m.flux_q;
-  const bool mixed = m.basis == MRD_BASIS_MIXED;
+  const bool mixed = m.basis == MRD_BASIS_MIXED || m.basis == MRD_BASIS_MIXED_REAL;
   const int modulus = mixed ? ly : 1;
   const double t = m.t, v = m.v;
 
@@ -252,8 +262,18 @@ int build_mpo_host(const mrd_model& m, HostMPO* out, std::string* err) {
     fams.push_back({"hopL", {{OP_CD, 1, 0, 1}, {OP_C, 0, 0, -1}}, 0, bases(0, lx - 1), constant(-t)});
     // intra-ring (V/Ly) sum_q cos q n_q n_{-q} = (V/Ly) sum e^{i(p1-p2)2pi/Ly} c+_p1 c_p2 c+_p3 c_p4
     // (n_q and n_{-q} commute, so cos q may be replaced by e^{iq})           (Eq. H_k_int)
-    fams.push_back({"intra", {{OP_CD, 0, 1, 1}, {OP_C, 0, -1, -1}, {OP_CD, 0, 0, 1}, {OP_C, 0, 0, -1}}, 0,
-                    bases(0, lx), constant(v / ly)});
+    if (m.basis == MRD_BASIS_MIXED) {
+      fams.push_back({"intra", {{OP_CD, 0, 1, 1}, {OP_C, 0, -1, -1}, {OP_CD, 0, 0, 1}, {OP_C, 0, 0, -1}}, 0,
+                      bases(0, lx), constant(v / ly)});
+    } else {
+      // the sine / cosine machine (Sec. IV.D, Eq. rot): the coefficient cos((p1 - p2) alpha) of
+      // c+_p1 c_p2 c+_p3 c_p4 is cos(p1 a) cos(p2 a) + sin(p1 a) sin(p2 a), one family per term,
+      // every entry real
+      fams.push_back({"intrac", {{OP_CD, 0, 0, 1, 1}, {OP_C, 0, 0, -1, 1}, {OP_CD, 0, 0, 1}, {OP_C, 0, 0, -1}}, 0,
+                      bases(0, lx), constant(v / ly)});
+      fams.push_back({"intras", {{OP_CD, 0, 0, 1, 2}, {OP_C, 0, 0, -1, 2}, {OP_CD, 0, 0, 1}, {OP_C, 0, 0, -1}}, 0,
+                      bases(0, lx), constant(v / ly)});
+    }
     // inter-ring (V/Ly) sum_q n_{x,-q} n_{x+1,q}                               (Eq. H_k_int)
     fams.push_back({"inter", {{OP_CD, 0, 0, 1}, {OP_C, 0, 0, -1}, {OP_CD, 1, 0, 1}, {OP_C, 1, 0, -1}}, 0,
                     bases(0, lx - 1), constant(v / ly)});
@@ -332,8 +352,12 @@ int build_mpo_host(const mrd_model& m, HostMPO* out, std::string* err) {
           for (int r = 0; r < nr; ++r) {
             if (!(here >> r & 1)) continue;
             const Role& role = fam.roles[r];
-            double ang = role.phase * 2.0 * pi * mm / ly;
-            coeff *= cd(std::cos(ang), std::sin(ang));
+            if (role.trig) {
+              coeff *= trig_of(role.trig, mm, ly);
+            } else {
+              double ang = role.phase * 2.0 * pi * mm / ly;
+              coeff *= cd(std::cos(ang), std::sin(ang));
+            }
             lab = ((lab + role.label * mm) % ly + ly) % ly;
             if (role.op == OP_CD) { dn += 1; dk += mm; }
             else if (role.op == OP_C) { dn -= 1; dk -= mm; }

@@ -23,12 +23,14 @@ def test_bindings_cover_header():
     assert set(binding.declared_symbols()) == set(binding._SIGS)
 
 
-@pytest.mark.parametrize("basis,b", [("mixed", P.MRD_BASIS_MIXED), ("real", P.MRD_BASIS_REAL)])
+@pytest.mark.parametrize("basis,b", [("mixed", P.MRD_BASIS_MIXED), ("real", P.MRD_BASIS_REAL),
+                                     ("mixed_real", P.MRD_BASIS_MIXED_REAL)])
 @pytest.mark.parametrize("lx,ly,fp,fq,v", [(3, 4, 1, 4, 1.0), (2, 5, 1, 5, 0.3), (4, 8, 1, 8, 1.0), (3, 10, 1, 10, 1.0),
                                            (2, 6, 1, 3, 7.0)])
 def test_product_mpo_equals_oracle_mpo(basis, b, lx, ly, fp, fq, v):
-    """Same FSM, two independent implementations: channel charges identical, entries
-    identical in position and equal in value to rounding."""
+    """The library's MPO builder restates the oracle's machine in C++ (one design written
+    twice: a translation check; the oracle's machine is pinned against ED): channel charges
+    identical, entries identical in position and equal in value to rounding."""
     m = P.MPO(None, lx, ly, fp, fq, 1.0, v, b)
     o = M.build_mpo(lx, ly, fp / fq, 1.0, v, basis)
     assert m.n_sites == o.n_sites and m.modulus == o.modulus
@@ -40,6 +42,8 @@ def test_product_mpo_equals_oracle_mpo(basis, b, lx, ly, fp, fq, v):
         ov = np.array([e[4] for e in o.entries[j]])
         assert np.array_equal(idx, oi)
         assert np.max(np.abs(val - ov)) < 1e-13
+        if basis == "mixed_real":
+            assert np.all(val.imag == 0.0)
 
 
 def test_mpo_build_rejects_bad_model():

@@ -273,3 +273,16 @@ def test_set_aside_columns_do_not_change_truncated_sweeps(ctx):
     assert kept_b == all_b and kept_a <= all_a
     assert abs(e_a - e_b) <= 1e-9 * abs(e_b)
     assert e_ed[k0] - 1e-10 < e_a
+
+
+def test_sine_cosine_machine_dmrg_matches_ed(ctx):
+    """The real-valued sine / cosine MPO of Sec. IV.D (Eq. rot) drives the same DMRG to the ED
+    ground energy of the sector: 4 x 4 cylinder, flux 1/4, V = 1, N = 4, exact chi (plain FP64
+    form)."""
+    import paper_1512_03318_gb300 as P
+    lx, ly, n = 4, 4, 4
+    e_ed = [ed_sector(lx, ly, 0.25, 1.0, 1.0, n, k) for k in range(ly)]
+    k0 = int(np.argmin(e_ed))
+    es, d = run_dmrg(ctx, lx, ly, 4, 1.0, 1.0, n, k0, 256, basis=P.MRD_BASIS_MIXED_REAL, sweeps=6)
+    d.close()
+    assert abs(es[-1] - e_ed[k0]) < 1e-10 * abs(e_ed[k0])

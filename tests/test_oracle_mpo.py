@@ -14,7 +14,7 @@ def _full_h(basis, lx, ly, flux, v):
     return f(lx, ly, flux, 1.0, v, 0, basis=full)
 
 
-@pytest.mark.parametrize("basis", ["real", "mixed"])
+@pytest.mark.parametrize("basis", ["real", "mixed", "mixed_real"])
 @pytest.mark.parametrize("lx,ly,flux,v", SMALL)
 def test_mpo_equals_ed_operator(basis, lx, ly, flux, v):
     """The MPO applied to random states of the whole Fock space equals the ED operator."""
@@ -71,7 +71,19 @@ def test_mixed_bond_dimension_bound(ly):
     assert max(mpo.dims()) <= 26 * ly + 9
 
 
-@pytest.mark.parametrize("basis", ["real", "mixed"])
+@pytest.mark.parametrize("lx,ly", [(2, 4), (1, 6), (2, 6), (3, 8)])
+def test_sine_cosine_machine_is_real(lx, ly):
+    """Sec. IV.D, Eq. rot: rotating the e^{+i alpha}, e^{-i alpha} pairs into cosines and sines
+    leaves every MPO entry real (the hops and the inter-ring terms are real in the mixed
+    basis), keeps the charges (N, K) of every channel, and stays within the crude bound
+    D <= 26 L + 9; its operator is the mixed Hamiltonian (test above)."""
+    mpo = M.build_mpo(lx, ly, 1 / ly, 1.0, 1.0, "mixed_real")
+    assert all(e[4].imag == 0.0 for ent in mpo.entries for e in ent)
+    assert mpo.modulus == ly
+    assert max(mpo.dims()) <= 26 * ly + 9
+
+
+@pytest.mark.parametrize("basis", ["real", "mixed", "mixed_real"])
 def test_channel_charges_conserved(basis):
     """Onsite symmetry (Sec. II): every nonzero W[w, w', s', s] has
     c_{w'} = c_w + q(s') - q(s), q(s) = (s, s m mod M)."""
