@@ -187,6 +187,14 @@ int mrd_heff_timing(mrd_heff* h, int32_t on);
 #define MRD_OPT_PER_TASK_LAUNCH 2
 #define MRD_OPT_AUTOTUNE 3
 #define MRD_OPT_WAIT_LIMIT_US 4
+/*   MRD_OPT_REAL            0 (default); 1: the operands are real (MPO entries, which must then
+ *                           be real, e.g. from MRD_BASIS_MIXED_REAL; environments; theta):
+ *                           the tensor-core precisions drop the imaginary planes (TF32: one
+ *                           MMA per K step instead of two, split BF16: two of half the width
+ *                           instead of four) and write zero imaginary parts. The float-float and
+ *                           FP64 paths are unchanged (their results are real for real inputs).
+ *                           This is the real arithmetic the paper runs (Sec. IV.D, Eq. rot). */
+#define MRD_OPT_REAL 5
 int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value);
 /* Wait for the context stream and report a device-side wait of a tensor-core GEMM that gave
  * up since the last check: MRD_E_TIMEOUT (the flag is then cleared), else 0. */
@@ -293,6 +301,13 @@ int mrd_env_update(mrd_dmrg* d, int32_t site, int32_t direction, int32_t prec);
  *                           (2^-24 relative per entry) enters the H_eff of later updates.
  * MRD_E_ARG for an unknown option. */
 #define MRD_DMRG_OPT_ENV_FP32 1
+/*   MRD_DMRG_OPT_REAL       1: real arithmetic (Sec. IV.D, Eq. rot): the MPO must be real (e.g.
+ *                           MRD_BASIS_MIXED_REAL; MRD_E_ARG otherwise) and the option set before
+ *                           the first update (MRD_E_STATE otherwise). The seeded random tensors
+ *                           are replaced by their real parts and canonicalised again, the
+ *                           environments rebuilt; every later H_eff is declared real
+ *                           (MRD_OPT_REAL), and all tensors stay real. 0 switches it off. */
+#define MRD_DMRG_OPT_REAL 2
 int mrd_dmrg_set_option(mrd_dmrg* d, int32_t option, int64_t value);
 /* Device memory of a DMRG state: out4 = {bytes of the stored environments, environments
  * built, bytes of the MPS tensors, 1 if environments are stored in complex64}. */

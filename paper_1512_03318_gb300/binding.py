@@ -22,11 +22,13 @@ MRD_OPT_GRAPH = 1
 MRD_OPT_PER_TASK_LAUNCH = 2
 MRD_OPT_AUTOTUNE = 3
 MRD_OPT_WAIT_LIMIT_US = 4
+MRD_OPT_REAL = 5
 MRD_SVD_F32_FF = 0
 MRD_SVD_FF = 1
 MRD_SVD_F32_F64 = 2
 MRD_SVD_F64 = 3
 MRD_DMRG_OPT_ENV_FP32 = 1
+MRD_DMRG_OPT_REAL = 2
 
 _LIB = None
 _LIVE = []        # weak references to open handles, closed in creation-reverse order at exit
@@ -335,7 +337,7 @@ class DMRG:
         return e.value
 
     def set_option(self, option, value):
-        """mrd_dmrg_set_option (MRD_DMRG_OPT_ENV_FP32)."""
+        """mrd_dmrg_set_option (MRD_DMRG_OPT_ENV_FP32, MRD_DMRG_OPT_REAL)."""
         self.ctx.check(lib().mrd_dmrg_set_option(self.h, option, int(value)))
 
     def memory(self):

@@ -736,6 +736,17 @@ int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) {
     h->per_task = value != 0;
     if (h->tc) tc_env_changed(h);   // tensor-core per-task tables are built with the panels
     ++h->gen;
+  } else if (option == MRD_OPT_REAL) {
+    const bool on = value != 0;
+    if (on)   // the MPO entries must be real (the sine / cosine machine)
+      for (const std::vector<double>* v : {&h->wi_v, &h->wj_v})
+        for (size_t k = 1; k < v->size(); k += 2)
+          if ((*v)[k] != 0.0) return mrd_fail(h->ctx, MRD_E_ARG, "mrd_heff_set_option: MRD_OPT_REAL needs real MPO entries");
+    if (on != h->real) {
+      h->real = on;
+      if (h->tc) { tc_free(h->tc); h->tc = nullptr; }   // panels of the other format
+      ++h->gen;
+    }
   } else if (option == MRD_OPT_WAIT_LIMIT_US) {
     if (value < 0 || value > 60000000) return mrd_fail(h->ctx, MRD_E_ARG, "mrd_heff_set_option: wait limit outside 0 .. 60 s");
     h->wait_ns = (uint64_t)value * 1000ull;

@@ -220,6 +220,11 @@ __global__ void __launch_bounds__(256) k_scale_unit(double2* __restrict__ x, int
 
 }  // namespace
 
+__global__ void k_zero_imag(double2* __restrict__ x, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e].y = 0.0;
+}
+
 // complex128 <-> complex64 copies of environments stored in single precision (round to
 // nearest on the way down, exact on the way up)
 __global__ void k_c128_to_c64(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
@@ -344,6 +349,10 @@ struct mrd_dmrg {
   // of the two environments an H_eff reads and of an update's output
   bool env_fp32 = false;
   Buf envx[3];
+  // real arithmetic (MRD_DMRG_OPT_REAL): real MPO and tensors, H_effs declared real
+  bool real = false;
+  int center0 = 0;      // centre given at creation
+  int updates = 0;      // two-site updates run so far
   cudaEvent_t svd_ev[2] = {nullptr, nullptr};
   // last block SVD: [0] ms of the final sweeps, [1] element-pairs tested, [2] rotated, [3] sweeps,
   // [4] ms of the FP32 pre-sweeps, [5] svd_mode
@@ -1014,6 +1023,35 @@ int orthonormalise(mrd_dmrg* D, SiteT& T) {
                     nullptr, nullptr);
 }
 
+// Orthonormalise every tensor but the centre's (left of it left-canonical, right of it
+// right-canonical) and build the left environments up to the centre and the right ones down to
+// centre + 2 (the initial state of mrd_dmrg_create, or its real-valued version).
+int canonicalise_and_build_envs(mrd_dmrg* D, int center) {
+  const int n = D->n;
+  int rcd = MRD_OK;
+  for (int j = 0; j < n && rcd == MRD_OK; ++j)
+    if (j != center) rcd = orthonormalise(D, D->A[j]);
+  if (rcd == MRD_OK) rcd = set_trivial_env(D, D->L[0], D->A[0].left, 0, true);
+  if (rcd == MRD_OK) rcd = set_trivial_env(D, D->R[n], D->A[n - 1].right, n, false);
+  for (int j = 0; j < center && rcd == MRD_OK; ++j) {
+    mrd_heff* h = nullptr;
+    const double2* lj = nullptr;
+    rcd = env_fp64(D, D->L[j], 0, &lj);
+    if (rcd == MRD_OK) rcd = make_heff(D, j, lj, nullptr, &h);
+    if (rcd == MRD_OK) rcd = env_left(D, h, j);
+    if (h) mrd_heff_free(h);
+  }
+  for (int j = n - 1; j >= center + 2 && rcd == MRD_OK; --j) {
+    mrd_heff* h = nullptr;
+    const double2* rj = nullptr;
+    rcd = env_fp64(D, D->R[j + 1], 1, &rj);
+    if (rcd == MRD_OK) rcd = make_heff(D, j - 1, nullptr, rj, &h);
+    if (rcd == MRD_OK) rcd = env_right(D, h, j - 1);
+    if (h) mrd_heff_free(h);
+  }
+  return rcd;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1138,28 +1176,8 @@ int mrd_dmrg_create(mrd_ctx* ctx, const mrd_mpo* mpo, int32_t n_part, int32_t k_
       mrd::count_launch();
     }
   }
-  int rcd = MRD_OK;
-  for (int j = 0; j < n && rcd == MRD_OK; ++j)
-    if (j != center) rcd = orthonormalise(D, D->A[j]);
-  if (rcd == MRD_OK) rcd = set_trivial_env(D, D->L[0], bond[0], 0, true);
-  if (rcd == MRD_OK) rcd = set_trivial_env(D, D->R[n], bond[n], n, false);
-  // left environments up to the centre, right environments down to centre + 2
-  for (int j = 0; j < center && rcd == MRD_OK; ++j) {
-    mrd_heff* h = nullptr;
-    const double2* lj = nullptr;
-    rcd = env_fp64(D, D->L[j], 0, &lj);
-    if (rcd == MRD_OK) rcd = make_heff(D, j, lj, nullptr, &h);
-    if (rcd == MRD_OK) rcd = env_left(D, h, j);
-    if (h) mrd_heff_free(h);
-  }
-  for (int j = n - 1; j >= center + 2 && rcd == MRD_OK; --j) {
-    mrd_heff* h = nullptr;
-    const double2* rj = nullptr;
-    rcd = env_fp64(D, D->R[j + 1], 1, &rj);
-    if (rcd == MRD_OK) rcd = make_heff(D, j - 1, nullptr, rj, &h);
-    if (rcd == MRD_OK) rcd = env_right(D, h, j - 1);
-    if (h) mrd_heff_free(h);
-  }
+  D->center0 = center;
+  int rcd = canonicalise_and_build_envs(D, center);
   if (rcd != MRD_OK) {
     std::string msg = ctx->err;
     mrd_dmrg_free(D);
@@ -1213,6 +1231,8 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   if (rc == MRD_OK) rc = make_heff(D, i, le, re, &h);
   if (rc != MRD_OK) return rc;
   struct Free { mrd_heff* h; ~Free() { if (h) mrd_heff_free(h); } } guard{h};
+  ++D->updates;
+  if (D->real && (rc = mrd_heff_set_option(h, MRD_OPT_REAL, 1)) != MRD_OK) return rc;
   if (D->timing) mrd_heff_timing(h, 1);
   auto collect = [&](int which) {
     if (!D->timing) return;
@@ -1458,6 +1478,24 @@ int mrd_dmrg_env(mrd_dmrg* D, int32_t bond, int32_t side, int64_t* len, double* 
 int mrd_dmrg_set_option(mrd_dmrg* D, int32_t option, int64_t value) {
   if (!D) return MRD_E_ARG;
   mrd_ctx* ctx = D->ctx;
+  if (option == MRD_DMRG_OPT_REAL) {
+    if (value == 0) { D->real = false; return MRD_OK; }
+    if (D->real) return MRD_OK;
+    for (const auto& v : D->mpo.site_val)
+      for (size_t k = 1; k < v.size(); k += 2)
+        if (v[k] != 0.0) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_set_option: MRD_DMRG_OPT_REAL needs a real MPO");
+    if (D->updates > 0) return mrd_fail(ctx, MRD_E_STATE, "mrd_dmrg_set_option: MRD_DMRG_OPT_REAL before the first update");
+    Guard g(ctx->device);
+    for (SiteT& T : D->A)   // the real parts of the seeded random tensors
+      if (T.size > 0) {
+        k_zero_imag<<<(unsigned)std::min<int64_t>((T.size + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+            T.data.as<double2>(), T.size);
+        mrd::count_launch();
+      }
+    MRD_CUDA(ctx, cudaGetLastError());
+    D->real = true;
+    return canonicalise_and_build_envs(D, D->center0);
+  }
   if (option != MRD_DMRG_OPT_ENV_FP32) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_set_option: unknown option");
   Guard g(ctx->device);
   D->env_fp32 = value != 0;

@@ -112,6 +112,7 @@ struct mrd_heff {
   bool per_task = false;     // one GEMM launch per task (MRD_OPT_PER_TASK_LAUNCH)
   bool autotune = true;      // time the tensor-core tile configurations (MRD_OPT_AUTOTUNE)
   uint64_t wait_ns = 1000000000ull;   // limit of each device-side wait (MRD_OPT_WAIT_LIMIT_US)
+  bool real = false;         // operands declared real (MRD_OPT_REAL): tensor cores skip imaginary planes
   // per-task launches: [0, tiles of task t] for every task of step 1 and step 2 (device),
   // tiles per task (host), for the FP64 / float-float tiles and for the tensor-core tiles
   Arena pt_mem;

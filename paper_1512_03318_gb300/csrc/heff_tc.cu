@@ -54,7 +54,7 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t make_idesc(int prec, int n, bool neg_a) {
   uint32_t d = 0;
   d |= 1u << 4;                                        // D: FP32
-  if (prec == TC_TF32) { d |= 2u << 7; d |= 2u << 10; }  // A, B: TF32
+  if (tc_is_tf32(prec)) { d |= 2u << 7; d |= 2u << 10; }  // A, B: TF32
   else { d |= 1u << 7; d |= 1u << 10; }                // A, B: BF16
   if (neg_a) d |= 1u << 13;
   d |= (uint32_t)(n >> 3) << 17;
@@ -138,6 +138,24 @@ __device__ __forceinline__ void mma_cplx_bf16x3(uint32_t tacc, uint64_t a_rh, ui
       ::"r"(tacc), "l"(a_rh), "l"(a_rl), "l"(a_ih), "l"(a_il), "l"(b_s0), "l"(b_s2), "r"(acc), "r"(idesc));
 }
 
+// Real operands: TF32 C[re] += A x B (1 MMA of N = nrow); split BF16 C[hi | lo] +=
+// (A_hi + A_lo) x [B_hi | B_lo] (2 MMAs of N = 2 nrow, the four products of the split).
+__device__ __forceinline__ void mma_real_tf32(uint32_t tacc, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %3, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %4, p;\n}\n"
+      ::"r"(tacc), "l"(a), "l"(b), "r"(acc), "r"(idesc));
+}
+
+__device__ __forceinline__ void mma_real_bf16x3(uint32_t tacc, uint64_t a_hi, uint64_t a_lo, uint64_t b,
+                                                uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %4, 0;\nsetp.eq.b32 q, 0, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, p;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, q;\n}\n"
+      ::"r"(tacc), "l"(a_hi), "l"(a_lo), "l"(b), "r"(acc), "r"(idesc));
+}
+
 // 16 consecutive FP32 columns of the warp's 32 TMEM lanes (one row per lane); the caller waits
 // with tcgen05.wait::ld before reading the registers.
 __device__ __forceinline__ void tmem_ld16(uint32_t* v, uint32_t taddr) {
@@ -185,7 +203,7 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // pipe (2 ops per clock per SM) only converts. Negation is exact in both formats.
 __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ dst, const int64_t* __restrict__ jobs,
                        int njobs, int64_t npieces, int prec) {
-  const bool tf32 = prec == TC_TF32;
+  const bool tf32 = tc_is_tf32(prec), real = tc_is_real(prec);
   const int kc = tf32 ? 4 : 8;                   // K values per 16-byte chunk
   const int kpt = tf32 ? 32 : 64;                // K values per 128-byte row
   for (int64_t pc = blockIdx.x; pc < npieces; pc += gridDim.x) {
@@ -224,7 +242,9 @@ __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ ds
           pre[q] = tf32_rna((float)v.x);
           pim[q] = tf32_rna((float)v.y);
         }
-        if (bfmt) {    // [-im, re, im]
+        if (real) {    // [re]
+          *(float4*)(tile + off) = re;
+        } else if (bfmt) {    // [-im, re, im]
           const float4 nim = make_float4(-im.x, -im.y, -im.z, -im.w);
           *(float4*)(tile + off) = nim;
           *(float4*)(tile + tile_bytes + off) = re;
@@ -255,7 +275,10 @@ __global__ void k_pack(const double2* __restrict__ src, uint8_t* __restrict__ ds
           b[4][q] = __hneg(ih);
           b[5][q] = __hneg(il);
         }
-        if (bfmt) {    // [-im_hi, -im_lo, re_hi, re_lo, im_hi, im_lo]
+        if (real) {    // [re_hi, re_lo]
+          *(uint4*)(tile + off) = pl[0];
+          *(uint4*)(tile + tile_bytes + off) = pl[1];
+        } else if (bfmt) {    // [-im_hi, -im_lo, re_hi, re_lo, im_hi, im_lo]
           const int order[6] = {4, 5, 0, 1, 2, 3};
 #pragma unroll
           for (int q = 0; q < 6; ++q) *(uint4*)(tile + q * tile_bytes + off) = pl[order[q]];
@@ -308,12 +331,13 @@ constexpr int kAccSlots = 2;
 // Write 16 consecutive output values of one row into a packed panel (16-byte chunks).
 __device__ __forceinline__ void put_packed16(uint8_t* base, int64_t nkt, int planes, int prec, int64_t row,
                                              int64_t k0, const float* re, const float* im, int nvalid) {
-  const int kpt = prec == TC_TF32 ? 32 : 64;
+  const int kpt = tc_kpt(prec);
   const int64_t rt = row / 128, kt = k0 / kpt;
   uint8_t* tile = base + (rt * nkt + kt) * planes * (int64_t)(128 * 128);
   const uint32_t r = (uint32_t)(row % 128);
   const int kin = (int)(k0 % kpt);
-  if (prec == TC_TF32) {
+  const bool real = tc_is_real(prec);
+  if (tc_is_tf32(prec)) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {          // 4 chunks of 4 TF32 values
       uint4 vr, vi;
@@ -327,7 +351,7 @@ __device__ __forceinline__ void put_packed16(uint8_t* base, int64_t nkt, int pla
       }
       const uint32_t off = sw128(r, (uint32_t)((kin + 4 * q) * 4));
       *(uint4*)(tile + off) = vr;
-      *(uint4*)(tile + 128 * 128 + off) = vi;
+      if (!real) *(uint4*)(tile + 128 * 128 + off) = vi;
     }
   } else {
 #pragma unroll
@@ -348,7 +372,8 @@ __device__ __forceinline__ void put_packed16(uint8_t* base, int64_t nkt, int pla
       }
       const uint32_t off = sw128(r, (uint32_t)((kin + 8 * q) * 2));
 #pragma unroll
-      for (int pl = 0; pl < 4; ++pl) *(uint4*)(tile + pl * 128 * 128 + off) = v[pl];
+      for (int pl = 0; pl < 4; ++pl)
+        if (!real || pl < 2) *(uint4*)(tile + pl * 128 * 128 + off) = v[pl];   // real: [hi, lo]
     }
   }
 }
@@ -363,7 +388,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
   const int prec = g.prec;
   const int aplanes = tc_aplanes(prec), bplanes = tc_bplanes(prec), groups = tc_groups(prec);
   const int kpt = tc_kpt(prec);                    // K values per 128-byte row
-  const int kstep = prec == TC_TF32 ? 8 : 16;      // K per MMA instruction
+  const int kstep = tc_is_tf32(prec) ? 8 : 16;     // K per MMA instruction
   const int ntile = g.ntile;                       // B rows (output columns) per tile
   const int nstages = g.nstages;
   const int stage_bytes = g.stage_bytes;
@@ -474,9 +499,13 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
             const uint32_t acc = first ? 0u : 1u;
             if (prec == TC_TF32)
               mma_cplx_tf32(tacc, a0 + ko, a0 + pa + ko, b0 + ko, b0 + pb + ko, idesc, acc);
-            else
+            else if (prec == TC_BF16X3)
               mma_cplx_bf16x3(tacc, a0 + ko, a0 + pa + ko, a0 + 2 * pa + ko, a0 + 3 * pa + ko, b0 + ko,
                               b0 + 2 * pb + ko, idesc, acc);
+            else if (prec == TC_TF32_REAL)
+              mma_real_tf32(tacc, a0 + ko, b0 + ko, idesc, acc);
+            else
+              mma_real_bf16x3(tacc, a0 + ko, a0 + pa + ko, b0 + ko, idesc, acc);
             first = false;
           }
           mma_commit(smem_u32(&bar_empty[stage]));
@@ -518,10 +547,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
         // groups of each part
         uint32_t vr[16], vi[16], wr[16], wi[16];
         const uint32_t c = (uint32_t)cb;
-        if (groups == 2) {
+        const bool real = tc_is_real(prec);
+        if (real) {                 // [re] or [re_hi | re_lo]
+          tmem_ld16(vr, tacc + c);
+          if (groups == 2) tmem_ld16(wr, tacc + nrow + c);
+        } else if (groups == 2) {   // [re | im]
           tmem_ld16(vr, tacc + c);
           tmem_ld16(vi, tacc + nrow + c);
-        } else {
+        } else {                    // [re_hi | re_lo | im_hi | im_lo]
           tmem_ld16(vr, tacc + c);
           tmem_ld16(wr, tacc + nrow + c);
           tmem_ld16(vi, tacc + 2 * nrow + c);
@@ -534,9 +567,12 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             re[j] = __uint_as_float(vr[j]);
-            im[j] = __uint_as_float(vi[j]);
+            im[j] = real ? 0.f : __uint_as_float(vi[j]);
           }
-          if (groups == 4) {
+          if (real && groups == 2) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) re[j] = __fadd_rn(re[j], __uint_as_float(wr[j]));
+          } else if (groups == 4) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               re[j] = __fadd_rn(re[j], __uint_as_float(wr[j]));

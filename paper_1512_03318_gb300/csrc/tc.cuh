@@ -4,7 +4,11 @@
 
 namespace mrd {
 
-enum { TC_TF32 = 1, TC_BF16X3 = 2 };
+// Tensor-core precisions: complex operands, or real ones (the sine / cosine machine of Eq. rot
+// with real environments and theta: imaginary planes dropped, the result's imaginary parts 0).
+enum { TC_TF32 = 1, TC_BF16X3 = 2, TC_TF32_REAL = 3, TC_BF16X3_REAL = 4 };
+__host__ __device__ inline bool tc_is_tf32(int prec) { return prec == TC_TF32 || prec == TC_TF32_REAL; }
+__host__ __device__ inline bool tc_is_real(int prec) { return prec == TC_TF32_REAL || prec == TC_BF16X3_REAL; }
 // task row (int64): M N out0 out1 pad seg0 nseg mode nkt_z pad
 //   mode 0: packed Z output, out0 = byte offset of the Z panel, nkt_z its K-tile count
 //   mode 1: FP64 output, out0 = element offset, out1 = leading dimension
@@ -30,11 +34,19 @@ constexpr int kPackPiece = 1024;
 //           C += (A_re_hi + A_re_lo) x S[2..5] + (A_im_hi + A_im_lo) x S[0..3]
 // The accumulator then holds the column groups (re, im) or (re_hi, re_lo, im_hi, im_lo) of
 // the output side by side, and the epilogue adds each part's pieces.
-__host__ __device__ inline int tc_aplanes(int prec) { return prec == TC_TF32 ? 2 : 4; }
-__host__ __device__ inline int tc_bplanes(int prec) { return prec == TC_TF32 ? 3 : 6; }
+// Real operands: A and B both [re] (TF32) or [re_hi, re_lo] (BF16X3), C[hi | lo] += A_hi x
+// [hi | lo] + A_lo x [hi | lo] (2 MMAs of N = 2 nrow; 1 MMA of N = nrow for TF32).
+__host__ __device__ inline int tc_aplanes(int prec) {
+  return prec == TC_TF32 ? 2 : prec == TC_BF16X3 ? 4 : prec == TC_TF32_REAL ? 1 : 2;
+}
+__host__ __device__ inline int tc_bplanes(int prec) {
+  return prec == TC_TF32 ? 3 : prec == TC_BF16X3 ? 6 : prec == TC_TF32_REAL ? 1 : 2;
+}
 // accumulator column groups of one output tile (one per B plane of a window)
-__host__ __device__ inline int tc_groups(int prec) { return prec == TC_TF32 ? 2 : 4; }
-__host__ __device__ inline int tc_kpt(int prec) { return prec == TC_TF32 ? 32 : 64; }   // K per 128-byte row
+__host__ __device__ inline int tc_groups(int prec) {
+  return prec == TC_TF32 ? 2 : prec == TC_BF16X3 ? 4 : prec == TC_TF32_REAL ? 1 : 2;
+}
+__host__ __device__ inline int tc_kpt(int prec) { return tc_is_tf32(prec) ? 32 : 64; }   // K per 128-byte row
 // Tile configuration of the grouped GEMM, picked per problem class by the autotuner
 // (tc_host.cu): B rows (output columns) per tile, pipeline stages, task order (0: charge
 // order, 1: largest work first).
@@ -57,6 +69,8 @@ __host__ __device__ inline bool tc_cfg_ok(int prec, TcCfg c) {
          tc_groups(prec) * c.ntile <= 256 && tc_smem_bytes(prec, c) <= kTcMaxSmem;
 }
 // default configuration (also the first candidate of the autotuner)
-inline TcCfg tc_default_cfg(int prec) { return prec == TC_TF32 ? TcCfg{128, 2, 0} : TcCfg{64, 2, 0}; }
+inline TcCfg tc_default_cfg(int prec) {
+  return prec == TC_TF32 ? TcCfg{128, 2, 0} : prec == TC_BF16X3 ? TcCfg{64, 2, 0} : TcCfg{128, 3, 0};
+}
 
 }  // namespace mrd

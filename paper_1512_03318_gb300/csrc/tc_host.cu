@@ -42,6 +42,13 @@ struct Tc {
 
 void tc_free(Tc* t) { delete t; }
 
+// Tensor-core precision of an application: complex, or real when the H_eff is declared real
+// (MRD_OPT_REAL).
+int tc_prec_of(const mrd_heff* h, int32_t prec) {
+  if (prec == MRD_PREC_TF32) return h->real ? TC_TF32_REAL : TC_TF32;
+  return h->real ? TC_BF16X3_REAL : TC_BF16X3;
+}
+
 namespace {
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -330,7 +337,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   T->n2 = (int64_t)t2.size() / TCT; T->ntiles2 = p2.back();
   T->n_lw = (int)(j_lw.size() / TCJ); T->n_wr = (int)(j_wr.size() / TCJ); T->n_th = (int)(j_th.size() / TCJ);
   // first piece of every pack job (field 9) and the pieces of each list
-  const int kc = prec == TC_TF32 ? 4 : 8;
+  const int kc = tc_is_tf32(prec) ? 4 : 8;
   auto pieces = [&](std::vector<int64_t>& j) {
     int64_t n = 0;
     for (size_t k = 0; k < j.size(); k += TCJ) {
@@ -371,7 +378,8 @@ namespace {
 // Candidate tile configurations per precision (all fit the 227 KB of shared memory).
 std::vector<TcCfg> candidates(int prec) {
   if (prec == TC_TF32) return {{128, 2, 0}, {64, 4, 0}, {128, 2, 1}, {64, 4, 1}};
-  return {{64, 2, 0}, {48, 2, 0}, {64, 2, 1}, {48, 2, 1}};
+  if (prec == TC_BF16X3) return {{64, 2, 0}, {48, 2, 0}, {64, 2, 1}, {48, 2, 1}};
+  return {{128, 3, 0}, {64, 4, 0}, {128, 3, 1}, {64, 4, 1}};   // real operands: 1 or 2 planes
 }
 
 // Problem class of an H_eff for the tuning cache: precision, size of theta (powers of two)
@@ -476,7 +484,7 @@ int tc_status(mrd_heff* h) {
 // environments; a no-op when both are current.
 int tc_prepare(mrd_heff* h, int32_t prec) {
   mrd_ctx* ctx = h->ctx;
-  const int tp = prec == MRD_PREC_TF32 ? TC_TF32 : TC_BF16X3;
+  const int tp = tc_prec_of(h, prec);
   int rc;
   MRD_CUDA(ctx, tc_gemm_init());
   if (!h->tc || h->tc->prec != tp) {
@@ -508,7 +516,7 @@ int tc_config(const mrd_heff* h, int32_t* cfg4) {
 
 int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   mrd_ctx* ctx = h->ctx;
-  const int tp = prec == MRD_PREC_TF32 ? TC_TF32 : TC_BF16X3;
+  const int tp = tc_prec_of(h, prec);
   int rc = tc_prepare(h, prec);
   if (rc != MRD_OK) return rc;
   Tc* T = h->tc;

@@ -140,3 +140,44 @@ def test_wait_limit_reports_timeout_and_context_recovers(ctx, prec):
     h.status()
     err = np.max(np.abs(out.cpu().numpy() - ref)) / np.max(np.abs(ref))
     assert err < TOL[prec], err
+
+
+def _real_case(case):
+    """The same case with every operand real: MPO entries, environments and theta replaced by
+    their real parts (the structure of the sine / cosine machine's real arithmetic)."""
+    out = dict(case)
+    out["wi"] = [(a, b, c, d, complex(v.real, 0.0)) for a, b, c, d, v in case["wi"]]
+    out["wj"] = [(a, b, c, d, complex(v.real, 0.0)) for a, b, c, d, v in case["wj"]]
+    for k in ("lflat", "rflat", "tflat"):
+        out[k] = case[k].real.astype(np.complex128)
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("seed,ly,chi_l,chi_r,m1,m2,dl,dm,dr", CASES[:3])
+def test_real_operands_match_oracle(ctx, prec, seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr):
+    """Real arithmetic (MRD_OPT_REAL, Sec. IV.D Eq. rot): with real MPO entries, environments
+    and theta the tensor cores drop the imaginary planes; the product equals the oracle's
+    within the same bounds as the complex form and its imaginary parts are exactly zero. An
+    H_eff with complex MPO entries refuses the option."""
+    import paper_1512_03318_gb300 as P
+    case = _real_case(G.random_case(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr))
+    ref = B.heff_apply(case["left"], case["right"], case["m1"], case["m2"], case["mod"], case["cl"], case["cm"],
+                       case["cr"], case["wi"], case["wj"], case["lflat"], case["rflat"], case["tflat"])
+    h = P.Heff(ctx, **G.heff_args(case))
+    h.set_option(P.MRD_OPT_REAL, 1)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    h.set_env(dev(case["lflat"]), dev(case["rflat"]))
+    T = dev(case["tflat"])
+    out = torch.empty_like(T)
+    for _ in range(2):
+        h.apply(T, out, prec=prec)
+        got = out.cpu().numpy()
+        assert np.all(got.imag == 0.0)
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err < TOL[prec], err
+    h.close()
+    hc = P.Heff(ctx, **G.heff_args(G.random_case(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr)))
+    with pytest.raises(P.MrdError):
+        hc.set_option(P.MRD_OPT_REAL, 1)
+    hc.close()
