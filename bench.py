@@ -373,6 +373,72 @@ def real_vs_mixed_or_note(P, ctx, torch, dev, stream):
         return {"skipped": f"{type(e).__name__}: {e}"}
 
 
+def real_arithmetic_update(P, ctx, torch, dev, stream, chi, steps, warmup, refine=1, restarts=8):
+    """The timed update in real arithmetic (Sec. IV.D, Eq. rot): the sine / cosine MPO of the same
+    cylinder, real site tensors and environments (MRD_DMRG_OPT_REAL), real tensor-core and
+    float-float GEMMs. Timed like the complex form (a tuning pass over the same sites on a
+    throwaway state, then device-resident updates between CUDA events), gated against the FP64
+    form converged on the same real state. Flops: a real multiply-add is 2 definition flops (8 for
+    a complex one) and 4 BF16 products on the tensor cores."""
+    mpo = P.MPO(None, LX_UPDATE, LY, FLUX_P, FLUX_Q, T_HOP, V_INT, P.MRD_BASIS_MIXED_REAL)
+    caps = update_caps(LX_UPDATE, chi)
+    centre = update_centre(LX_UPDATE)
+    form = mixed_params(P, chi, refine, restarts)
+
+    def state():
+        st = make_state(P, ctx, mpo, chi, caps, replica_seed(0))
+        st.set_option(P.MRD_DMRG_OPT_REAL, 1)
+        return st
+
+    st = state()
+    e_ref, _ = st.update(centre, +1, fp64_params(P, chi, tol=1e-14, restarts=8))
+    st.close()
+    st = state()
+    for k in range(warmup + steps):
+        st.update(centre + k, +1, form)
+    st.close()
+    st = state()
+    e_first = None
+    for k in range(warmup):
+        e, _ = st.update(centre + k, +1, form)
+        e_first = e if e_first is None else e_first
+    torch.cuda.synchronize(dev)
+    st.timing(True)
+    bonds, counts = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        i = centre + warmup + k
+        bonds.append((i, st.bond(i), st.bond(i + 2)))
+        st.update(i, +1, form)
+        counts.append(st.stats()[2])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    kms, _ = st.timing(False)
+    real_tensors = all(np.all(st.site(j)[1].imag == 0.0) for j in range(centre, centre + warmup + steps + 1))
+    st.close()
+    f_def = f_exec = 0.0
+    n_tc = 0
+    for (i, lb, rb), cnt in zip(bonds, counts):
+        h = heff_of_bonds(P, ctx, mpo, i, lb, rb)
+        fd, fe, _, _ = h.flops()
+        h.close()
+        f_def += fd / 4 * (cnt % 1000)
+        f_exec += fe / 4 * (cnt % 1000)
+        n_tc += cnt % 1000
+    mpo.close()
+    tc_ms, ff_ms = kms[0] + kms[1], kms[2] + kms[3]
+    dE = abs(e_first - e_ref) / abs(e_ref)
+    return {"s_per_update": ms / 1e3 / steps, "steps": steps,
+            "basis": "mixed sine/cosine (Eq. rot), real tensors", "dE_rel_vs_fp64_converged": dE,
+            "gate_passed": dE <= 1e-9, "site_tensors_real": bool(real_tensors),
+            "heff_tflops_bf16x3_real": f_def / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None,
+            "heff_hw_tflops": 4 * f_exec / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None,
+            "kernel_ms_per_update": {"k_tc_gemm": tc_ms / steps, "k_cgemm_ff": ff_ms / steps},
+            "heff_applications": n_tc, "e_fp64_converged": e_ref, "e_first": e_first}
+
+
 def mpo_diagnostics(P):
     """Mean and largest MPO bond dimension and mean fill over a bulk ring (the second of three),
     real-space, mixed (exponential) and mixed sine / cosine machines, against the real-space
@@ -964,6 +1030,11 @@ def main():
         except (P.MrdError, torch.cuda.OutOfMemoryError) as e:
             details["ly8"] = {"skipped": f"{type(e).__name__}: {e}"}
         try:
+            details["real_arithmetic"] = real_arithmetic_update(P, ctx, torch, dev, stream, chi, args.steps,
+                                                                args.warmup, args.refine, args.fast_restarts)
+        except (P.MrdError, torch.cuda.OutOfMemoryError) as e:
+            details["real_arithmetic"] = {"skipped": f"{type(e).__name__}: {e}"}
+        try:
             details["config5"] = config5(P, ctx, torch, dev, fp64_matvecs=max(fp64_matvecs % 1000, 1))
         except (P.MrdError, torch.cuda.OutOfMemoryError) as e:
             details["config5"] = {"skipped": f"{type(e).__name__}: {e}"}
@@ -1056,6 +1127,11 @@ def main():
                        "chi2048_heff_err": {k: l8["chi2048"][f"heff_{k}_rel_err_vs_fp64"] for k in ("tf32", "bf16x3")},
                        "chi2048_forms": {k[5:]: v for k, v in l8["chi2048"].items() if k.startswith("form_")},
                        "chi2048_fp64_s_per_update": l8["chi2048"]["s_per_update_fp64"]}
+    ra = details.get("real_arithmetic", {})
+    if "s_per_update" in ra:
+        line["real_arithmetic"] = {k: ra[k] for k in ("s_per_update", "dE_rel_vs_fp64_converged", "gate_passed",
+                                                       "heff_tflops_bf16x3_real", "kernel_ms_per_update")}
+        line["real_arithmetic"]["speedup_vs_complex"] = s_per_update / ra["s_per_update"]
     c5 = details.get("config5", {})
     if "s_per_update" in c5:
         line["ly12_chi8000"] = {"s_per_update": c5["s_per_update"], "heff_tflops_bf16x3": c5["heff_tflops_bf16x3"],

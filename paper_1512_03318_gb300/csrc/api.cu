@@ -16,6 +16,9 @@ cudaError_t launch_plan(const PlanDims& d, const PlanPtrs& p, cudaStream_t s);
 cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
                                    const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
                                    int n_sm, cudaStream_t s, const int2* items = nullptr);
+cudaError_t launch_rgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
+                                   const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                                   int n_sm, cudaStream_t s, const int2* items = nullptr);
 std::vector<int2> ff_item_order(const int64_t* tasks, const int64_t* segs, int64_t n_tasks);
 cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
@@ -520,26 +523,28 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   cudaError_t e = cudaMemsetAsync(theta_out_dev, 0, (size_t)n * 16, s);
   if (prec == MRD_PREC_FF) {
     float4* z_ff = (float4*)h->z;
+    // real operands (MRD_OPT_REAL): one float-float product per multiply-add instead of three
+    auto gemm = h->real ? launch_rgemm_ff_packed : launch_cgemm_ff_packed;
     if (e == cudaSuccess) e = to_ff((const double2*)theta_in_dev, h->th_ff, n, s);
     if (e == cudaSuccess && e0) e = record_event(e0, s, cap);
     if (!h->per_task) {
       if (e == cudaSuccess)
-        e = launch_cgemm_ff_packed(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1, h->p.seg1, h->p.tile1,
-                                   h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s, h->ff_it1);
+        e = gemm(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1, h->p.seg1, h->p.tile1,
+                 h->counts[C_NT1], h->counts[C_TILES1], h->n_sm, s, h->ff_it1);
       if (e == cudaSuccess && e1) e = record_event(e1, s, cap);
       if (e == cudaSuccess)
-        e = launch_cgemm_ff_packed(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
-                                   h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s, h->ff_it2);
+        e = gemm(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2, h->p.seg2, h->p.tile2,
+                 h->counts[C_NT2], h->counts[C_TILES2], h->n_sm, s, h->ff_it2);
     } else {
       for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT1]; ++t)
         if (h->pt_tiles1[t])
-          e = launch_cgemm_ff_packed(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1 + TF * t, h->p.seg1,
-                                     h->pt_pref1 + 2 * t, 1, h->pt_tiles1[t], h->n_sm, s);
+          e = gemm(h->lw_ff, h->th_ff, z_ff, nullptr, h->p.t1 + TF * t, h->p.seg1, h->pt_pref1 + 2 * t, 1,
+                   h->pt_tiles1[t], h->n_sm, s, nullptr);
       if (e == cudaSuccess && e1) e = record_event(e1, s, cap);
       for (int64_t t = 0; e == cudaSuccess && t < h->counts[C_NT2]; ++t)
         if (h->pt_tiles2[t])
-          e = launch_cgemm_ff_packed(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2 + TF * t, h->p.seg2,
-                                     h->pt_pref2 + 2 * t, 1, h->pt_tiles2[t], h->n_sm, s);
+          e = gemm(z_ff, h->wr_ff, nullptr, (double2*)theta_out_dev, h->p.t2 + TF * t, h->p.seg2,
+                   h->pt_pref2 + 2 * t, 1, h->pt_tiles2[t], h->n_sm, s, nullptr);
     }
   } else {
     if (e == cudaSuccess && e0) e = record_event(e0, s, cap);

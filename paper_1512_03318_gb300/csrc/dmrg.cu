@@ -28,6 +28,9 @@ namespace mrd {
 cudaError_t launch_cgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
                                    const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
                                    int n_sm, cudaStream_t s, const int2* items = nullptr);
+cudaError_t launch_rgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
+                                   const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                                   int n_sm, cudaStream_t s, const int2* items = nullptr);
 std::vector<int2> ff_item_order(const int64_t* tasks, const int64_t* segs, int64_t n_tasks);
 cudaError_t to_ff(const double2* x, float4* y, int64_t n, cudaStream_t s);
 cudaError_t launch_cgemm_fp64(const double2* A, const double2* B, double2* C, const int64_t* tasks,
@@ -431,8 +434,11 @@ int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const d
       MRD_CUDA(ctx, cudaMemcpyAsync(D->gitems.p, items.data(), items.size() * 8, cudaMemcpyHostToDevice, s));
       it = D->gitems.as<int2>();
     }
-    MRD_CUDA(ctx, launch_cgemm_ff_packed(a_ff, b_ff, nullptr, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(),
-                                         D->gpref.as<int64_t>(), nt, pref[nt], D->n_sm, s, it));
+    // a real state (MRD_DMRG_OPT_REAL): every operand is real, one float-float product per
+    // multiply-add instead of three
+    auto gemm = D->real ? launch_rgemm_ff_packed : launch_cgemm_ff_packed;
+    MRD_CUDA(ctx, gemm(a_ff, b_ff, nullptr, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
+                       nt, pref[nt], D->n_sm, s, it));
   } else {
     MRD_CUDA(ctx, launch_cgemm_fp64(Aop, Bop, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
                                     nt, pref[nt], D->n_sm, s));

@@ -78,6 +78,16 @@ __device__ __forceinline__ void st_out(float4* c, int64_t i, const CAcc& a) {
   c[i] = make_float4(re.hi, im.hi, re.lo, im.lo);
 }
 
+// real result (Re = the accumulated real products, Im = 0)
+__device__ __forceinline__ void st_out_real(double2* c, int64_t i, const FFAcc& a) {
+  const FF re = ff_norm(a);
+  c[i] = make_double2((double)re.hi + (double)re.lo, 0.0);
+}
+__device__ __forceinline__ void st_out_real(float4* c, int64_t i, const FFAcc& a) {
+  const FF re = ff_norm(a);
+  c[i] = make_float4(re.hi, 0.f, re.lo, 0.f);
+}
+
 // a_r + a_i of a staged element (float-float), for the third product
 __device__ __forceinline__ float2 cff_sum(float4 a) {
   const FF s = ff_add(FF{a.x, a.z}, FF{a.y, a.w});
@@ -101,7 +111,10 @@ __device__ __forceinline__ FFAcc ff_renorm(FFAcc a) {
 // items (optional): (task, tile within task) of every tile in launch order, longest K first
 // (ff_item_order), so that no long tile starts at the end of the grid; without it tiles run in
 // task order and the task is found by binary search over the tile prefix.
-template <class TA, class TB, class TC>
+// REAL: the operands are real (their imaginary parts zero, e.g. the sine / cosine machine's
+// real arithmetic); only Re = sum a_r b_r is formed, one float-float product per multiply-add
+// instead of three, and the result's imaginary parts are written as zero.
+template <class TA, class TB, class TC, bool REAL>
 __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, const TB* __restrict__ B,
                                                   TC* __restrict__ C, const int64_t* __restrict__ tasks,
                                                   const int64_t* __restrict__ segs,
@@ -157,26 +170,26 @@ __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, c
             const int64_t gr = m0 + ar, gk = k0 + ak;
             const float4 v = ld_op(A, (gr < M && gk < K) ? a_off + gr * lda + gk : -1, false);
             As[ar][ak] = v;
-            Ass[ar][ak] = cff_sum(v);
+            if (!REAL) Ass[ar][ak] = cff_sum(v);
           } else {                                      // A[m, k] = conj(A[a_off + k * lda + m])
             const int ar = e & 31, ak = e >> 5;
             const int64_t gr = m0 + ar, gk = k0 + ak;
             const float4 v = ld_op(A, (gr < M && gk < K) ? a_off + gk * lda + gr : -1, true);
             As[ar][ak] = v;
-            Ass[ar][ak] = cff_sum(v);
+            if (!REAL) Ass[ar][ak] = cff_sum(v);
           }
           if (!(flags & 2)) {                           // B[k, n] at b_off + k * ldb + n
             const int bk = e >> 5, bc = e & 31;
             const int64_t gk2 = k0 + bk, gc = n0 + bc;
             const float4 v = ld_op(B, (gk2 < K && gc < N) ? b_off + gk2 * ldb + gc : -1, false);
             Bs[bk][bc] = v;
-            Bss[bk][bc] = cff_sum(v);
+            if (!REAL) Bss[bk][bc] = cff_sum(v);
           } else {                                      // B[k, n] = conj(B[b_off + n * ldb + k])
             const int bk = e & 15, bc = e >> 4;
             const int64_t gk2 = k0 + bk, gc = n0 + bc;
             const float4 v = ld_op(B, (gk2 < K && gc < N) ? b_off + gc * ldb + gk2 : -1, true);
             Bs[bk][bc] = v;
-            Bss[bk][bc] = cff_sum(v);
+            if (!REAL) Bss[bk][bc] = cff_sum(v);
           }
         }
         __syncthreads();
@@ -184,12 +197,19 @@ __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, c
         for (int k = 0; k < kn; ++k) {
           const float4 a0 = As[r0][k], a1 = As[r0 + 1][k];
           const float4 b0 = Bs[k][c0], b1 = Bs[k][c0 + 1];
-          const float2 sa0 = Ass[r0][k], sa1 = Ass[r0 + 1][k];
-          const float2 sb0 = Bss[k][c0], sb1 = Bss[k][c0 + 1];
-          cff_mac(acc[0][0], a0, sa0, b0, sb0);
-          cff_mac(acc[0][1], a0, sa0, b1, sb1);
-          cff_mac(acc[1][0], a1, sa1, b0, sb0);
-          cff_mac(acc[1][1], a1, sa1, b1, sb1);
+          if (REAL) {
+            ff_mac(acc[0][0].rr, FF{a0.x, a0.z}, FF{b0.x, b0.z});
+            ff_mac(acc[0][1].rr, FF{a0.x, a0.z}, FF{b1.x, b1.z});
+            ff_mac(acc[1][0].rr, FF{a1.x, a1.z}, FF{b0.x, b0.z});
+            ff_mac(acc[1][1].rr, FF{a1.x, a1.z}, FF{b1.x, b1.z});
+          } else {
+            const float2 sa0 = Ass[r0][k], sa1 = Ass[r0 + 1][k];
+            const float2 sb0 = Bss[k][c0], sb1 = Bss[k][c0 + 1];
+            cff_mac(acc[0][0], a0, sa0, b0, sb0);
+            cff_mac(acc[0][1], a0, sa0, b1, sb1);
+            cff_mac(acc[1][0], a1, sa1, b0, sb0);
+            cff_mac(acc[1][1], a1, sa1, b1, sb1);
+          }
         }
         // renormalise every accumulator (s, c) <- FastTwoSum(s, c) once per K chunk: the
         // error term c then holds at most 16 products' residuals, and its own FP32 rounding
@@ -199,8 +219,10 @@ __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, c
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             acc[i][j].rr = ff_renorm(acc[i][j].rr);
-            acc[i][j].ii = ff_renorm(acc[i][j].ii);
-            acc[i][j].ss = ff_renorm(acc[i][j].ss);
+            if (!REAL) {
+              acc[i][j].ii = ff_renorm(acc[i][j].ii);
+              acc[i][j].ss = ff_renorm(acc[i][j].ss);
+            }
           }
         __syncthreads();
       }
@@ -210,7 +232,10 @@ __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, c
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int64_t r = m0 + r0 + i, c = n0 + c0 + j;
-        if (r < M && c < N) st_out(C, c_off + r * ldc + c, acc[i][j]);
+        if (r < M && c < N) {
+          if (REAL) st_out_real(C, c_off + r * ldc + c, acc[i][j].rr);
+          else st_out(C, c_off + r * ldc + c, acc[i][j]);
+        }
       }
   }
 }
@@ -224,11 +249,14 @@ __global__ void k_to_ff(const double2* __restrict__ x, float4* __restrict__ y, i
 template <class TA, class TB, class TC>
 static cudaError_t launch_ff(const TA* A, const TB* B, TC* C, const int64_t* tasks, const int64_t* segs,
                              const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s,
-                             const int2* items) {
+                             const int2* items, bool real = false) {
   if (total_tiles <= 0) return cudaSuccess;
   int64_t grid = (int64_t)n_sm * 8;
   if (grid > total_tiles) grid = total_tiles;
-  k_cgemm_ff<TA, TB, TC><<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks, items);
+  if (real)
+    k_cgemm_ff<TA, TB, TC, true><<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks, items);
+  else
+    k_cgemm_ff<TA, TB, TC, false><<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks, items);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -236,6 +264,14 @@ static cudaError_t launch_ff(const TA* A, const TB* B, TC* C, const int64_t* tas
 cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
                             const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
   return launch_ff(A, B, C, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s, nullptr);
+}
+
+// real operands already in float-float layout (imaginary parts zero): Re only, Im written 0
+cudaError_t launch_rgemm_ff_packed(const float4* A, const float4* B, float4* c_ff, double2* c64, const int64_t* tasks,
+                                   const int64_t* segs, const int64_t* prefix, int64_t n_tasks, int64_t total_tiles,
+                                   int n_sm, cudaStream_t s, const int2* items) {
+  if (c_ff) return launch_ff(A, B, c_ff, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s, items, true);
+  return launch_ff(A, B, c64, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s, items, true);
 }
 
 // operands already in float-float layout; result in float-float (c_ff) or FP64 (c64)

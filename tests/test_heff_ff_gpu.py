@@ -75,3 +75,28 @@ def test_ff_heff_model_mpo_ly10_chi3200(ctx):
     torch.cuda.synchronize()
     o64 = o64.cpu().numpy()
     assert np.max(np.abs(got - o64)) <= TOL_FF * np.max(np.abs(o64))
+
+
+@pytest.mark.parametrize("seed,ly,chi_l,chi_r,m1,m2,dl,dm,dr", RANDOM_CASES[:3])
+def test_ff_heff_real_operands_match_oracle(ctx, seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr):
+    """Real arithmetic of the float-float GEMM (MRD_OPT_REAL, Sec. IV.D Eq. rot): with real MPO
+    entries, environments and theta each multiply-add is one float-float product; the result
+    equals the oracle's within the complex form's bound and its imaginary parts are zero."""
+    import paper_1512_03318_gb300 as P
+    from tests.test_heff_tc_gpu import _real_case
+    case = _real_case(G.random_case(seed, ly, chi_l, chi_r, m1, m2, dl, dm, dr))
+    ref = B.heff_apply(case["left"], case["right"], case["m1"], case["m2"], case["mod"], case["cl"], case["cm"],
+                       case["cr"], case["wi"], case["wj"], case["lflat"], case["rflat"], case["tflat"])
+    assert np.all(ref.imag == 0.0)
+    h = P.Heff(ctx, **G.heff_args(case))
+    h.set_option(P.MRD_OPT_REAL, 1)
+    h.set_env(_dev(case["lflat"]), _dev(case["rflat"]))
+    T = _dev(case["tflat"])
+    out = torch.empty_like(T)
+    h.apply(T, out, P.MRD_PREC_FF)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(got.imag == 0.0)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= TOL_FF, err
+    h.close()
