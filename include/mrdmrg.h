@@ -308,6 +308,12 @@ int mrd_env_update(mrd_dmrg* d, int32_t site, int32_t direction, int32_t prec);
  *                           environments rebuilt; every later H_eff is declared real
  *                           (MRD_OPT_REAL), and all tensors stay real. 0 switches it off. */
 #define MRD_DMRG_OPT_REAL 2
+/*   MRD_DMRG_OPT_SVD_PRESWEEPS  0 .. 64 (default 8): the largest number of FP32 Jacobi
+ *                           pre-sweeps of the block SVD modes MRD_SVD_F32_* (they stop earlier
+ *                           once no pair rotates); 0 leaves all work to the final sweeps.
+ *                           Columns are set aside before the final sweeps (mrd_dmrg_svd_stats)
+ *                           only after at least 8 pre-sweeps or converged ones. */
+#define MRD_DMRG_OPT_SVD_PRESWEEPS 3
 int mrd_dmrg_set_option(mrd_dmrg* d, int32_t option, int64_t value);
 /* Device memory of a DMRG state: out4 = {bytes of the stored environments, environments
  * built, bytes of the MPS tensors, 1 if environments are stored in complex64}. */
@@ -344,6 +350,11 @@ int mrd_dmrg_phase_ms(const mrd_dmrg* d, double* ms8);
  * pre-sweeps is below half the chi-th largest column norm are set aside before the final
  * sweeps (their Schmidt weight is discarded by the truncation to chi in any case). */
 int mrd_dmrg_svd_stats(const mrd_dmrg* d, double* out8);
+/* Column pairs rotated in each Jacobi sweep of the last block SVD: n2[0] FP32 pre-sweeps, then
+ * n2[1] final sweeps; the first cap counts (pre-sweeps first) are copied to out and, when ms
+ * is not NULL, the host wall time of each sweep in ms (its launches up to the read-back of its
+ * rotation count) to ms. */
+int mrd_dmrg_svd_trace(const mrd_dmrg* d, int32_t cap, int32_t* out, double* ms, int32_t* n2);
 /* Momentum-resolved entanglement spectrum (Sec. III.C): the Schmidt values lambda of the
  * bond cut by the last two-site update (*bond = i + 1 for an update of sites i, i+1), one per
  * kept Schmidt state, with the charges (N, K) of its left part in nk (2 per value). The values

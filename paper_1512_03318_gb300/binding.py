@@ -29,6 +29,7 @@ MRD_SVD_F32_F64 = 2
 MRD_SVD_F64 = 3
 MRD_DMRG_OPT_ENV_FP32 = 1
 MRD_DMRG_OPT_REAL = 2
+MRD_DMRG_OPT_SVD_PRESWEEPS = 3
 
 _LIB = None
 _LIVE = []        # weak references to open handles, closed in creation-reverse order at exit
@@ -134,6 +135,8 @@ _SIGS = {
     "mrd_measure_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrd_heff_tc_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "mrd_dmrg_svd_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mrd_dmrg_svd_trace": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int32)]),
     "mrd_dmrg_schmidt": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_double)]),
     "mrd_heff_timing_collect": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -337,7 +340,7 @@ class DMRG:
         return e.value
 
     def set_option(self, option, value):
-        """mrd_dmrg_set_option (MRD_DMRG_OPT_ENV_FP32, MRD_DMRG_OPT_REAL)."""
+        """mrd_dmrg_set_option (MRD_DMRG_OPT_ENV_FP32, MRD_DMRG_OPT_REAL, MRD_DMRG_OPT_SVD_PRESWEEPS)."""
         self.ctx.check(lib().mrd_dmrg_set_option(self.h, option, int(value)))
 
     def memory(self):
@@ -435,6 +438,17 @@ class DMRG:
         f = (C.c_double * 8)()
         self.ctx.check(lib().mrd_dmrg_svd_stats(self.h, f))
         return tuple(f)
+
+    def svd_trace(self, cap=256, times=False):
+        """Column pairs rotated per Jacobi sweep of the last block SVD: (FP32 pre-sweeps, final);
+        with times=True also the host ms of each sweep, in the same two lists."""
+        out, ms, n2 = (C.c_int32 * cap)(), (C.c_double * cap)(), (C.c_int32 * 2)()
+        self.ctx.check(lib().mrd_dmrg_svd_trace(self.h, cap, out, ms, n2))
+        k = min(cap, n2[0] + n2[1])
+        v, t = list(out)[:k], list(ms)[:k]
+        if times:
+            return v[:n2[0]], v[n2[0]:], t[:n2[0]], t[n2[0]:]
+        return v[:n2[0]], v[n2[0]:]
 
     def stats(self):
         e, t, it = C.c_double(), C.c_double(), C.c_int32()

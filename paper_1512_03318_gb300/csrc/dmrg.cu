@@ -40,8 +40,9 @@ cudaError_t svd_load(const double2* theta, const int64_t* blk, const int64_t* sr
                      double* fro2, cudaStream_t s);
 int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
-                       const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
-                       int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s);
+                       const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol,
+                       const double* fro2, int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
+                       cudaStream_t s);
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
                       cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
@@ -49,9 +50,8 @@ cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double
 cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, int64_t total, int chi, double cutoff,
                          int* keep, double* info, int* flat_block, cudaStream_t s);
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
-                         int64_t ncta,
-                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
-                         int sweep, unsigned long long* wctr, cudaStream_t s);
+                         int64_t ncta, int round, int W, int64_t smem, float tol, const double* fro2,
+                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_colnorm2(const double2* work, const int64_t* blk, int nblk, double* out, cudaStream_t s);
@@ -361,6 +361,10 @@ struct mrd_dmrg {
   // [4] ms of the FP32 pre-sweeps, [5] svd_mode
   double svd_stats[6] = {0, 0, 0, 0, 0, 0};
   int svd_sweeps32 = 0, svd_sweeps64 = 0;
+  // column pairs rotated in each sweep of the last block SVD: the FP32 pre-sweeps, then the final
+  std::vector<int32_t> svd_trace32, svd_trace64;
+  std::vector<double> svd_tms32, svd_tms64;   // host ms of each sweep (launches to the count read back)
+  int svd_presweeps = kMaxSweeps32;   // MRD_DMRG_OPT_SVD_PRESWEEPS
   bool gemm_ff = false;   // grouped GEMMs of the update in float-float (refine_prec MRD_PREC_FF)
   double last_energy = 0.0, last_trunc = 0.0;
   // Schmidt values of the bond cut by the last update: bond index, (N, K) and value per state
@@ -609,8 +613,9 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     blk[SVF * b + 11] = w32;
     w32 += blk[SVF * b + 3] * blk[SVF * b + 3];
   }
-  // block-cyclic Jacobi schedules: column groups of W (FP32 with V: 16, FP64: 8), halved
-  // while a group pair does not fit in shared memory
+  // block-cyclic Jacobi schedules: column groups of W = 8 (256 threads a CTA; measured faster
+  // than 16 for the float-float sweeps at chi = 3200, whose largest blocks bound each round),
+  // halved while a group pair does not fit in shared memory
   struct Sched {
     int W = 0, rounds = 0;
     int64_t ncta = 0, smem = 0;
@@ -644,9 +649,8 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     sc.ncta = pre[nb];
     return sc;
   };
-  const bool ff_cols = mode == MRD_SVD_F32_FF || mode == MRD_SVD_FF;
   const Sched s32 = schedule(8, true, pp.data());
-  Sched s64 = schedule(ff_cols ? 16 : 8, false, pp.data() + nb + 1);
+  Sched s64 = schedule(8, false, pp.data() + nb + 1);
   if (s32.smem > kSvdMaxSmemHost || s64.smem > kSvdMaxSmemHost)
     return mrd_fail(ctx, MRD_E_OOM, "block SVD: a block is too large for the shared-memory Jacobi rounds");
   MRD_CUDA(ctx, D->svd_blk.need(blk.size() * 8));
@@ -694,20 +698,31 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     MRD_CUDA(ctx, cudaMemsetAsync(wctr, 0, 2 * 8, s));
     MRD_CUDA(ctx, cudaEventRecord(D->svd_ev[0], s));
     bool done = false;
+    std::vector<int32_t>& trace = f32 ? D->svd_trace32 : D->svd_trace64;
+    std::vector<double>& tms = f32 ? D->svd_tms32 : D->svd_tms64;
+    trace.clear();
+    tms.clear();
+    MRD_CUDA(ctx, cudaStreamSynchronize(s));
+    auto t_last = std::chrono::steady_clock::now();
     for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
       MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
       for (int rd = 0; rd < sc.rounds; ++rd) {
         if (f32)
-          MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, ord, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f, fro,
-                                     rot, last, sweep, wctr, s));
+          MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, ord, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f,
+                                     fro, rot, last, sweep, wctr, s));
         else
           MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, ord, nb,
-                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, wctr, s));
+                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, wctr,
+                                   s));
       }
       int hrot = 0;
       MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
       MRD_CUDA(ctx, cudaStreamSynchronize(s));
       *used = sweep + 1;
+      trace.push_back(hrot);
+      const auto t_now = std::chrono::steady_clock::now();
+      tms.push_back(std::chrono::duration<double, std::milli>(t_now - t_last).count());
+      t_last = t_now;
       done = hrot == 0;
     }
     MRD_CUDA(ctx, cudaEventRecord(D->svd_ev[1], s));
@@ -732,10 +747,12 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   // (X <- X V32, one grouped GEMM) and float-float or FP64 sweeps finish the job.
   int rc = MRD_OK;
   D->svd_sweeps32 = 0;
+  D->svd_trace32.clear();
+  D->svd_tms32.clear();
   D->svd_cols[0] = D->svd_cols[1] = (double)slen;
   if (mode == MRD_SVD_F32_FF || mode == MRD_SVD_F32_F64) {
   MRD_CUDA(ctx, svd_to_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
-  rc = sweep_until_done(true, kMaxSweeps32, &D->svd_sweeps32);
+  rc = sweep_until_done(true, D->svd_presweeps, &D->svd_sweeps32);
   if (rc != MRD_OK) return rc;
   MRD_CUDA(ctx, svd_v_from_f32(D->svd_work.as<double2>(), D->svd_w32.as<float2>(), dblk, nb, s));
   {
@@ -759,10 +776,13 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   // dominant singular subspace, perturbed only through the ~1e-5 overlaps with the dropped
   // columns, a second-order change of the truncated state) and the block keeps r_act values.
   // The canonical factor stays exactly orthonormal; the other factor is the exact projection.
+  // The column norms stand for singular values only once the pre-sweeps have run their default
+  // budget (or converged): with fewer, no column is set aside.
   bool set_aside = false;
   int64_t cols_all = 0, cols_kept = 0;
   for (int b = 0; b < nb; ++b) cols_all += blk[SVF * b + 3];
-  if (cols_all > chi && chi > 0) {
+  const bool pre_done = D->svd_sweeps32 >= kMaxSweeps32 || (!D->svd_trace32.empty() && D->svd_trace32.back() == 0);
+  if (cols_all > chi && chi > 0 && pre_done) {
     MRD_CUDA(ctx, svd_colnorm2(D->svd_x2.as<double2>(), dblk, nb, D->svd_s.as<double>(), s));
     std::vector<double> nrm((size_t)slen, 0.0);
     MRD_CUDA(ctx, cudaMemcpyAsync(nrm.data(), D->svd_s.p, (size_t)slen * 8, cudaMemcpyDeviceToHost, s));
@@ -782,6 +802,11 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
           if ((nrm[(size_t)(d[8] + j)] >= tau2) == (pass == 0)) perm[(size_t)(d[8] + k++)] = (int32_t)j;
       int64_t act = 0;
       for (int64_t j = 0; j < d[3]; ++j) act += nrm[(size_t)(d[8] + j)] >= tau2;
+      // the columns that stay by decreasing norm: groups of similar norms, which the final
+      // sweeps orthogonalise in fewer sweeps (de Rijk's ordering, applied once)
+      const double* nb0 = &nrm[(size_t)d[8]];
+      std::stable_sort(&perm[(size_t)d[8]], &perm[(size_t)d[8]] + act,
+                       [&](int32_t x, int32_t y) { return nb0[x] > nb0[y]; });
       d[3] = act;
       cols_kept += act;
     }
@@ -1502,6 +1527,11 @@ int mrd_dmrg_set_option(mrd_dmrg* D, int32_t option, int64_t value) {
     D->real = true;
     return canonicalise_and_build_envs(D, D->center0);
   }
+  if (option == MRD_DMRG_OPT_SVD_PRESWEEPS) {
+    if (value < 0 || value > 64) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_set_option: pre-sweeps outside 0 .. 64");
+    D->svd_presweeps = (int)value;
+    return MRD_OK;
+  }
   if (option != MRD_DMRG_OPT_ENV_FP32) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_set_option: unknown option");
   Guard g(ctx->device);
   D->env_fp32 = value != 0;
@@ -1575,6 +1605,22 @@ int mrd_dmrg_schmidt(const mrd_dmrg* D, int32_t* bond, int64_t* n, int32_t* nk, 
   *n = (int64_t)D->schmidt_val.size();
   if (nk && !D->schmidt_nk.empty()) std::copy(D->schmidt_nk.begin(), D->schmidt_nk.end(), nk);
   if (values && !D->schmidt_val.empty()) std::copy(D->schmidt_val.begin(), D->schmidt_val.end(), values);
+  return MRD_OK;
+}
+
+int mrd_dmrg_svd_trace(const mrd_dmrg* D, int32_t cap, int32_t* out, double* ms, int32_t* n2) {
+  if (!D || cap < 0 || (cap > 0 && !out) || !n2) return MRD_E_ARG;
+  n2[0] = (int32_t)D->svd_trace32.size();
+  n2[1] = (int32_t)D->svd_trace64.size();
+  int32_t k = 0;
+  for (int ph = 0; ph < 2; ++ph) {
+    const std::vector<int32_t>& v = ph ? D->svd_trace64 : D->svd_trace32;
+    const std::vector<double>& t = ph ? D->svd_tms64 : D->svd_tms32;
+    for (size_t j = 0; j < v.size() && k < cap; ++j, ++k) {
+      out[k] = v[j];
+      if (ms) ms[k] = j < t.size() ? t[j] : 0.0;
+    }
+  }
   return MRD_OK;
 }
 

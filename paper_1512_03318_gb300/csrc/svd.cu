@@ -63,6 +63,19 @@ __global__ void k_svd_load(const double2* __restrict__ theta, const int64_t* __r
     V[e] = make_double2((e / r) == (e % r) ? 1.0 : 0.0, 0.0);
 }
 
+// Asynchronous copy global -> shared of one 8- or 16-byte element (the columns of a round are
+// staged with these, all in flight at once, then awaited together).
+template <class S2>
+__device__ __forceinline__ void stage_elem(S2* dst, const S2* src) {
+  static_assert(sizeof(S2) == 8 || sizeof(S2) == 16, "8- or 16-byte elements");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(S2) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Rotate the column pair (x_i, x_j) (and the matching columns of V, when given) so that they
 // become orthogonal; one warp, columns of length p (V: r). Returns whether it rotated.
 // A column whose norm is negligible against the block (|x|^2 <= floor2 = zero_rel |M|_F^2)
@@ -94,16 +107,16 @@ __device__ __forceinline__ bool jacobi_pair(T2* xi, T2* xj, int p, T2* vi, T2* v
   const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
   const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
   auto rot = [&](T2* ci, T2* cj, int n) {
-    for (int q = lane; q < n; q += 32) {
-      const T2 u = ci[q], v0 = cj[q];
+    for (int k = lane; k < n; k += 32) {
+      const T2 u = ci[k], v0 = cj[k];
       T2 v;
       v.x = v0.x * ph_r - v0.y * ph_i;
       v.y = v0.x * ph_i + v0.y * ph_r;
       T2 o1, o2;
       o1.x = c * u.x - sn * v.x; o1.y = c * u.y - sn * v.y;
       o2.x = sn * u.x + c * v.x; o2.y = sn * u.y + c * v.y;
-      ci[q] = o1;
-      cj[q] = o2;
+      ci[k] = o1;
+      cj[k] = o2;
     }
   };
   rot(xi, xj, p);
@@ -147,8 +160,8 @@ __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, fl
   const float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
   // x_i' = c u - sigma v, x_j' = s u + kappa v with sigma = s e^{-i phi}, kappa = c e^{-i phi}
   const float sr = sn * ph_r, si = sn * ph_i, kr = c * ph_r, ki = c * ph_i;
-  for (int q = lane; q < p; q += 32) {
-    const float4 u4 = xi[q], v4 = xj[q];
+  for (int k = lane; k < p; k += 32) {
+    const float4 u4 = xi[k], v4 = xj[k];
     const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
     FFAcc o1r = ff_prod1(ur, c), o1i = ff_prod1(ui, c), o2r = ff_prod1(ur, sn), o2i = ff_prod1(ui, sn);
     ff_mac1(o1r, vr, -sr); ff_mac1(o1r, vi, si);    // c u_r - (s_r v_r - s_i v_i)
@@ -156,8 +169,8 @@ __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, fl
     ff_mac1(o2r, vr, kr); ff_mac1(o2r, vi, -ki);    // s u_r + k_r v_r - k_i v_i
     ff_mac1(o2i, vi, kr); ff_mac1(o2i, vr, ki);     // s u_i + k_r v_i + k_i v_r
     const FF a1 = ff_norm(o1r), b1 = ff_norm(o1i), a3 = ff_norm(o2r), b3 = ff_norm(o2i);
-    xi[q] = make_float4(a1.hi, b1.hi, a1.lo, b1.lo);
-    xj[q] = make_float4(a3.hi, b3.hi, a3.lo, b3.lo);
+    xi[k] = make_float4(a1.hi, b1.hi, a1.lo, b1.lo);
+    xj[k] = make_float4(a3.hi, b3.hi, a3.lo, b3.lo);
   }
   // Norms of the rotated columns from the pair's own values, with the coefficients that were
   // applied (exact FP32 numbers, whether or not they form an exactly unitary rotation), g =
@@ -228,23 +241,26 @@ __device__ __forceinline__ void rr_pair(int n, int s, int q, int& i, int& j) {
 // One round of the block-cyclic schedule for every block. The r columns of a block form
 // G = ceil(r / W) groups of W (padded to an even count Gp with an empty group); round
 // `round` pairs the groups round-robin and CTA k of the block takes group pair k: it stages
-// the (up to) 2W columns of X, and of V when vf >= 0, in shared memory, rotates every cross
-// pair (one pair per warp, W disjoint pairs per step, W steps), in round 0 first every pair
-// inside each of the two groups, and writes the columns back. Over Gp - 1 rounds each
-// column pair is rotated once (one sweep). T is float (pre-sweeps) or double.
+// the (up to) 2W columns of X, and of V when vf >= 0, in shared memory (asynchronous copies,
+// all in flight together), rotates every cross pair (one pair per warp, W disjoint pairs per
+// step, W steps), in round 0 first every pair inside each of the two groups, and
+// writes the columns back. Over Gp - 1 rounds each column pair is rotated once (one sweep).
+// T is float (pre-sweeps) or double.
 // MODE 0: FP32 columns and V (T2 = float2); 1: FP64 (double2); 2: float-float columns
 // (float4, scaled by ff_scale).
 template <int MODE, class T, class T2, class S2>
-__global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf, int vf,
-                             const int64_t* __restrict__ grp_prefix, const int64_t* __restrict__ order, int nblk,
-                             int round, int W, T tol,
-                             const double* __restrict__ fro2, double zero_rel, int* __restrict__ rotated,
-                             int* __restrict__ last_rot, int sweep, unsigned long long* __restrict__ wctr) {
+__global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf,
+                                                    int vf, const int64_t* __restrict__ grp_prefix,
+                                                    const int64_t* __restrict__ order, int nblk, int round, int W,
+                                                    T tol, const double* __restrict__ fro2, double zero_rel,
+                                                    int* __restrict__ rotated, int* __restrict__ last_rot, int sweep,
+                                                    unsigned long long* __restrict__ wctr) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ int n_rot;
   __shared__ unsigned long long n_tested, n_rotated;   // element-pairs tested / rotated
   __shared__ int s_last[32];   // sweep in which each staged column last rotated
   __shared__ FF s_norm[32];    // float-float column norms (MODE 2)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int64_t cta = blockIdx.x;
   int lo = 0, hi = nblk - 1;   // largest k with grp_prefix[k] <= cta; the CTAs run over the
   while (lo < hi) {            // blocks in the order `order` (longest sweeps first)
@@ -261,17 +277,28 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
   rr_pair(Gp, round, k, gI, gJ);
   const int nI = gI < G ? min(W, r - gI * W) : 0, nJ = gJ < G ? min(W, r - gJ * W) : 0;
   if (nI + nJ < 2) return;
-  T2* X = work + d[xf];
-  T2* V = vf >= 0 ? work + d[vf] : nullptr;
-  S2* sx = (S2*)smem_raw;                      // 2W columns of length p
-  S2* sv = sx + (int64_t)2 * W * p;            // 2W columns of length r (V, MODE 0)
+  // From the third sweep on, a pair is tested only if one of its columns rotated in this or
+  // the previous sweep (see do_pair); a group pair none of whose columns did has nothing to do.
+  if (sweep >= 2) {
+    bool live = false;
+    if (warp == 0)
+      for (int cc = lane; cc < nI + nJ; cc += 32) {
+        const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
+        live = live || last_rot[d[8] + gc] >= sweep - 1;
+      }
+    if (__syncthreads_or(live) == 0) return;
+  }
   if (threadIdx.x == 0) {
     n_rot = 0;
     n_tested = n_rotated = 0;
   }
+  int mine = 0;
+  T2* X = work + d[xf];
+  T2* V = vf >= 0 ? work + d[vf] : nullptr;
+  S2* sx = (S2*)smem_raw;                      // 2W columns of length p
+  S2* sv = sx + (int64_t)2 * W * p;            // 2W columns of length r (V, MODE 0)
   // float-float columns are held scaled by ff_scale(fro2) (svd_ff_io)
   const double up = MODE == 2 ? ff_scale(fro2[b]) : 1.0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   // stage: local column c < W is column gI*W + c, c >= W is column gJ*W + c - W (one warp
   // per column, lanes along it)
   for (int cc = warp; cc < nI + nJ; cc += nwarp) {
@@ -279,12 +306,12 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
     const T2* src = X + (int64_t)gc * p;
     S2* dst = sx + (int64_t)lc * p;
-    for (int t = lane; t < p; t += 32) dst[t] = src[t];
+    for (int t = lane; t < p; t += 32) stage_elem<S2>(dst + t, (const S2*)(src + t));
     if constexpr (MODE == 0)
       if (V != nullptr) {
         const T2* vs = V + (int64_t)gc * r;
         S2* vd = sv + (int64_t)lc * r;
-        for (int t = lane; t < r; t += 32) vd[t] = vs[t];
+        for (int t = lane; t < r; t += 32) stage_elem<S2>(vd + t, (const S2*)(vs + t));
       }
   }
   for (int cc = threadIdx.x; cc < nI + nJ; cc += blockDim.x) {
@@ -292,9 +319,10 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
     s_last[lc] = last_rot[d[8] + gc];
   }
+  stage_wait();
   __syncthreads();
   if constexpr (MODE == 2) {   // norms of the staged columns, one warp per column
-    for (int cc = warp; cc < nI + nJ; cc += blockDim.x >> 5) {
+    for (int cc = warp; cc < nI + nJ; cc += nwarp) {
       const int lc = cc < nI ? cc : W + cc - nI;
       const float4* x = sx + (int64_t)lc * p;
       FFAcc A = {0.f, 0.f};
@@ -309,7 +337,6 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     __syncthreads();
   }
   const double floor2 = zero_rel * fro2[b];
-  int mine = 0;
   // A pair found orthogonal in the previous sweep stays orthogonal while neither column
   // rotates: pairs whose columns last rotated before the previous sweep are skipped (the
   // first two sweeps test every pair, last_rot starting at 0).
@@ -354,7 +381,6 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     if (i < nI && j < nJ) do_pair(i, W + j);
     __syncthreads();
   }
-  if (lane == 0 && mine) atomicAdd(&n_rot, mine);
   for (int cc = warp; cc < nI + nJ; cc += nwarp) {
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
@@ -373,6 +399,7 @@ __global__ void k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ 
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
     last_rot[d[8] + gc] = s_last[lc];
   }
+  if (lane == 0 && mine) atomicAdd(&n_rot, mine);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (n_rot) atomicAdd(rotated, n_rot);
@@ -622,30 +649,37 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32) {
   return (int64_t)2 * W * (p + r_v) * (f32 ? 8 : 16);
 }
 
-// FP64 rounds on X (field 4 of work) or, with xff != nullptr, float-float rounds on the
-// float-float copy xff (same offsets, see svd_ff_io).
-cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
-                       const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol, const double* fro2, int* rotated,
-                       int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s) {
+template <int MODE, class T, class T2>
+static cudaError_t launch_bround(T2* work, const int64_t* blk, int xf, int vf, const int64_t* grp_prefix,
+                                 const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, T tol,
+                                 const double* fro2, double zero_rel, int* rotated, int* last_rot, int sweep,
+                                 unsigned long long* wctr, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
+  if (W < 2 || W > 16 || (W & 1)) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_svd_bround<1, double, double2, double2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdMaxSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_svd_bround<2, double, float4, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kSvdMaxSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_svd_bround<MODE, T, T2, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSvdMaxSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (xff)
-    k_svd_bround<2, double, float4, float4><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        xff, blk, 4, -1, grp_prefix, order, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
-  else
-    k_svd_bround<1, double, double2, double2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-        work, blk, 4, -1, grp_prefix, order, nblk, round, W, tol, fro2, 1e-28, rotated, last_rot, sweep, wctr);
+  k_svd_bround<MODE, T, T2, T2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
+      work, blk, xf, vf, grp_prefix, order, nblk, round, W, tol, fro2, zero_rel, rotated, last_rot, sweep, wctr);
   mrd::count_launch();
   return cudaGetLastError();
+}
+
+// FP64 rounds on X (field 4 of work) or, with xff != nullptr, float-float rounds on the
+// float-float copy xff (same offsets, see svd_ff_io).
+cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
+                       const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol,
+                       const double* fro2, int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
+                       cudaStream_t s) {
+  if (xff)
+    return launch_bround<2, double, float4>(xff, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem, tol,
+                                            fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
+  return launch_bround<1, double, double2>(work, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem, tol,
+                                           fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
 }
 
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
@@ -658,21 +692,10 @@ cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, 
 }
 
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
-                         int64_t ncta,
-                         int round, int W, int64_t smem, float tol, const double* fro2, int* rotated, int* last_rot,
-                         int sweep, unsigned long long* wctr, cudaStream_t s) {
-  if (ncta == 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_svd_bround<0, float, float2, float2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdMaxSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  k_svd_bround<0, float, float2, float2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-      w32, blk, 10, 11, grp_prefix, order, nblk, round, W, tol, fro2, 1e-12, rotated, last_rot, sweep, wctr);
-  mrd::count_launch();
-  return cudaGetLastError();
+                         int64_t ncta, int round, int W, int64_t smem, float tol, const double* fro2,
+                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s) {
+  return launch_bround<0, float, float2>(w32, blk, 10, 11, grp_prefix, order, nblk, ncta, round, W, smem, tol,
+                                         fro2, 1e-12, rotated, last_rot, sweep, wctr, s);
 }
 
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s) {
