@@ -55,6 +55,7 @@ cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_pre
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_colnorm2(const double2* work, const int64_t* blk, int nblk, double* out, cudaStream_t s);
+cudaError_t svd_fix_phases(double2* U, double2* Vh, const int64_t* blk, int nblk, int side, cudaStream_t s);
 cudaError_t svd_gather_cols(double2* work, const double2* src, const int64_t* blk, int nblk, const int* perm,
                             cudaStream_t s);
 enum { SVF = 13 };
@@ -1038,6 +1039,11 @@ int orthonormalise(mrd_dmrg* D, SiteT& T) {
   double info[3];
   int rc = block_svd(D, blk, src, T.data.as<double2>(), T.mode == 1 ? 1 : 0, 1 << 30, 0.0, MRD_SVD_FF, keep, info);
   if (rc != MRD_OK) return rc;
+  // The factor replaces the tensor without its partner (S V^+ or U S is not carried to the
+  // neighbour), so the phase of each singular vector would enter the state: fix it by a
+  // convention, which makes the orthonormalised state independent of the Jacobi rotation order.
+  MRD_CUDA(D->ctx, svd_fix_phases(D->svd_u.as<double2>(), D->svd_vh.as<double2>(), D->svd_blk.as<int64_t>(),
+                                  (int)gi.size(), T.mode == 1 ? 1 : 0, D->ctx->stream));
   std::vector<int64_t> cp;
   for (size_t b = 0; b < gi.size(); ++b) {
     const int64_t* d = &blk[SVF * b];

@@ -495,6 +495,36 @@ __global__ void k_svd_finish(const double2* __restrict__ work, const int64_t* __
 }
 
 // Values are sorted in place after the vectors were written.
+// Phase convention of the orthonormal factor (the singular vectors are fixed only up to a phase
+// each): every column of U (side 0) or row of V^+ (side 1) is multiplied by the conjugate phase
+// of its entry of largest modulus (the first such entry), which makes that entry real and
+// positive. One CTA per block, one thread per vector.
+__global__ void k_svd_fix_phases(double2* __restrict__ U, double2* __restrict__ Vh, const int64_t* __restrict__ blk,
+                                 int nblk, int side) {
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int64_t* d = blk + SVF * b;
+  const int64_t m = d[0], n = d[1], r = d[3];
+  for (int64_t k = threadIdx.x; k < r; k += blockDim.x) {
+    double2* v = side == 0 ? U + d[6] + k : Vh + d[7] + k * n;   // column k of U or row k of V^+
+    const int64_t len = side == 0 ? m : n, stride = side == 0 ? r : 1;
+    double best = -1.0;
+    double2 at = make_double2(0.0, 0.0);
+    for (int64_t i = 0; i < len; ++i) {
+      const double2 x = v[i * stride];
+      const double a = x.x * x.x + x.y * x.y;
+      if (a > best) { best = a; at = x; }
+    }
+    if (!(best > 0.0)) continue;
+    const double inv = 1.0 / sqrt(best);
+    const double pr = at.x * inv, pi = -at.y * inv;   // conj(phase)
+    for (int64_t i = 0; i < len; ++i) {
+      const double2 x = v[i * stride];
+      v[i * stride] = make_double2(x.x * pr - x.y * pi, x.x * pi + x.y * pr);
+    }
+  }
+}
+
 __global__ void k_svd_sort_values(const int64_t* __restrict__ blk, int nblk, double* __restrict__ S,
                                   double* __restrict__ S_sorted) {
   const int b = blockIdx.x;
@@ -720,6 +750,13 @@ cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double
   k_svd_finish<<<nblk, 256, 0, s>>>(work, blk, nblk, U, Vh, S, order_scratch, fro2);
   mrd::count_launch();
   k_svd_sort_values<<<nblk, 256, 0, s>>>(blk, nblk, S, S_sorted);
+  mrd::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t svd_fix_phases(double2* U, double2* Vh, const int64_t* blk, int nblk, int side, cudaStream_t s) {
+  if (nblk == 0) return cudaSuccess;
+  k_svd_fix_phases<<<nblk, 128, 0, s>>>(U, Vh, blk, nblk, side);
   mrd::count_launch();
   return cudaGetLastError();
 }
