@@ -20,7 +20,8 @@ namespace mrd {
 namespace {
 
 constexpr int kT = 32;   // output tile (complex elements per side), 2 x 2 per thread
-constexpr int kK = 16;   // K chunk
+constexpr int kK = 16;   // K chunk (kT kK a multiple of the 256 threads)
+static_assert(kT * kK % 256 == 0, "tile loads: whole rounds of 256 threads");
 
 __device__ __forceinline__ int64_t find_task_ff(const int64_t* prefix, int64_t n, int64_t item) {
   int64_t lo = 0, hi = n - 1;
@@ -163,29 +164,29 @@ __global__ void __launch_bounds__(256, 3) k_cgemm_ff(const TA* __restrict__ A, c
       const int64_t flags = sg[5];
       for (int64_t k0 = 0; k0 < K; k0 += kK) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < kT * kK / 256; ++r) {
           const int e = tid + r * 256;
           if (!(flags & 1)) {                           // A[m, k] at a_off + m * lda + k
-            const int ar = e >> 4, ak = e & 15;
+            const int ar = e / kK, ak = e % kK;
             const int64_t gr = m0 + ar, gk = k0 + ak;
             const float4 v = ld_op(A, (gr < M && gk < K) ? a_off + gr * lda + gk : -1, false);
             As[ar][ak] = v;
             if (!REAL) Ass[ar][ak] = cff_sum(v);
           } else {                                      // A[m, k] = conj(A[a_off + k * lda + m])
-            const int ar = e & 31, ak = e >> 5;
+            const int ar = e % kT, ak = e / kT;
             const int64_t gr = m0 + ar, gk = k0 + ak;
             const float4 v = ld_op(A, (gr < M && gk < K) ? a_off + gk * lda + gr : -1, true);
             As[ar][ak] = v;
             if (!REAL) Ass[ar][ak] = cff_sum(v);
           }
           if (!(flags & 2)) {                           // B[k, n] at b_off + k * ldb + n
-            const int bk = e >> 5, bc = e & 31;
+            const int bk = e / kT, bc = e % kT;
             const int64_t gk2 = k0 + bk, gc = n0 + bc;
             const float4 v = ld_op(B, (gk2 < K && gc < N) ? b_off + gk2 * ldb + gc : -1, false);
             Bs[bk][bc] = v;
             if (!REAL) Bss[bk][bc] = cff_sum(v);
           } else {                                      // B[k, n] = conj(B[b_off + n * ldb + k])
-            const int bk = e & 15, bc = e >> 4;
+            const int bk = e % kK, bc = e / kK;
             const int64_t gk2 = k0 + bk, gc = n0 + bc;
             const float4 v = ld_op(B, (gk2 < K && gc < N) ? b_off + gc * ldb + gk2 : -1, true);
             Bs[bk][bc] = v;
