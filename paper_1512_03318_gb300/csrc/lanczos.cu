@@ -353,103 +353,42 @@ __device__ int sturm_count(const double* a, const double* b2, int k, double x) {
   return cnt;
 }
 
-// Lowest eigenpair of the k x k tridiagonal Lanczos matrix, k = j + 1; one warp.
-__global__ void k_tridiag_lowest(LzState* st) {
-  const int k = st->j + 1;
-  const double* a = st->alpha;
-  const double* b = st->beta;
-  const int lane = threadIdx.x;
-  __shared__ double lo_s, hi_s;
-  __shared__ double a_s[MRD_LANCZOS_MAX_ITER + 1], b2_s[MRD_LANCZOS_MAX_ITER + 1];
-  for (int i = lane; i < k; i += 32) {
-    a_s[i] = a[i];
-    b2_s[i] = b[i] * b[i];
-  }
-  __syncwarp();
-  if (lane == 0) {
-    // the lowest eigenvalue lies between the lowest Gershgorin bound and the smallest
-    // diagonal element (a Rayleigh quotient of a unit vector)
-    double lo = 1e300, hi = 1e300;
-    for (int i = 0; i < k; ++i) {
-      double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
-      lo = fmin(lo, a[i] - r);
-      hi = fmin(hi, a[i]);
-    }
-    double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
-    lo -= pad;
-    hi += pad;
-    // warm start: by interlacing the lowest eigenvalue of T_k is at most that of T_{k-1};
-    // late in a run it moves little, so try [E_{k-1} - 4|E_{k-1} - E_{k-2}|, E_{k-1}], padded,
-    // and keep it where Sturm counts confirm it (no eigenvalue below, at least one below the
-    // top); otherwise the Gershgorin bracket
-    if (k >= 3) {
-      const double e1 = st->ritz[k - 2], e2 = st->ritz[k - 3];
-      const double tol = 1e-13 * fmax(fabs(e1), 1.0);
-      const double wlo = e1 - 4.0 * fabs(e1 - e2) - tol, whi = e1 + tol;
-      if (wlo > lo && whi < hi && sturm_count(a_s, b2_s, k, wlo) == 0 && sturm_count(a_s, b2_s, k, whi) >= 1) {
-        lo = wlo;
-        hi = whi;
-      }
-    }
-    lo_s = lo;
-    hi_s = hi;
-  }
-  __syncwarp();
-  // multisection to 1e-14 relative width (the Ritz value is compared to 1e-10 and refined
-  // afterwards), or until a subdivision no longer shrinks the interval in FP64
-  double prev_w = 0.0;
-  for (int it = 0; it < 40; ++it) {
-    const double lo = lo_s, hi = hi_s;
-    if (!(hi - lo > 1e-14 * fmax(fabs(lo), fabs(hi))) || hi - lo == prev_w) break;
-    prev_w = hi - lo;
-    const double x = lo + (hi - lo) * (lane + 1) / 33.0;
-    const int c = sturm_count(a_s, b2_s, k, x);
-    const unsigned m = __ballot_sync(0xffffffffu, c >= 1);
-    __syncwarp();
-    if (lane == 0) {
-      if (m == 0) {
-        lo_s = lo + (hi - lo) * 32.0 / 33.0;
-      } else {
-        const int f = __ffs(m) - 1;  // first point with at least one eigenvalue below
-        hi_s = lo + (hi - lo) * (f + 1) / 33.0;
-        lo_s = f > 0 ? lo + (hi - lo) * f / 33.0 : lo;
-      }
-    }
-    __syncwarp();
-  }
-  if (lane != 0) return;
-  const double lam = 0.5 * (lo_s + hi_s);
-  st->energy = lam;
-  st->ritz[k - 1] = lam;
-  // inverse iteration: (T - lam I) y = y_prev with a pivoted LU of the tridiagonal matrix. One
-  // thread: the factors and y live in shared memory (not the thread's stack or global memory,
-  // whose latency the serial recurrences would pay on every access), and the k pivots are
-  // inverted once instead of dividing in each of the three solves
-  __shared__ double d[MRD_LANCZOS_MAX_ITER + 1], du[MRD_LANCZOS_MAX_ITER + 1], du2[MRD_LANCZOS_MAX_ITER + 1];
-  __shared__ double dl[MRD_LANCZOS_MAX_ITER + 1], y[MRD_LANCZOS_MAX_ITER + 1];
+// Inverse iteration for the eigenvector of the k x k tridiagonal matrix (diagonal a, off-diagonal
+// b) at the eigenvalue lam: (T - lam I) y = y_prev with a pivoted LU of the tridiagonal matrix,
+// `passes` times from the uniform vector, normalised; the sign is fixed so that the first
+// nonzero component is positive (a deterministic ground vector). One thread; the factors and y
+// live in shared memory (not the thread's stack or global memory, whose latency the serial
+// recurrences would pay on every access), and the k pivots are inverted once instead of
+// dividing in each of the solves. T is double, or float where the Lanczos matvecs carry ~1e-5
+// relative error and the vector only needs single precision.
+template <class T>
+__device__ void tridiag_inverse_iteration(const double* a_s, const double* b_s, int k, double lam, int passes,
+                                          double* y_out) {
+  __shared__ T d[MRD_LANCZOS_MAX_ITER + 1], du[MRD_LANCZOS_MAX_ITER + 1], du2[MRD_LANCZOS_MAX_ITER + 1];
+  __shared__ T dl[MRD_LANCZOS_MAX_ITER + 1], y[MRD_LANCZOS_MAX_ITER + 1];
   __shared__ int piv[MRD_LANCZOS_MAX_ITER + 1];
-  const double shift = lam + 1e-14 * fmax(1.0, fabs(lam));
-  const double y0 = 1.0 / sqrt((double)k);
+  const T shift = (T)(lam + 1e-14 * fmax(1.0, fabs(lam)));
+  const T y0 = (T)(1.0 / sqrt((double)k));
   for (int i = 0; i < k; ++i) {
-    d[i] = a_s[i] - shift;
-    du[i] = i + 1 < k ? b[i] : 0.0;
+    d[i] = (T)a_s[i] - shift;
+    du[i] = i + 1 < k ? (T)b_s[i] : T(0);
     dl[i] = du[i];
-    du2[i] = 0.0;
+    du2[i] = T(0);
     y[i] = y0;
   }
   for (int i = 0; i + 1 < k; ++i) {  // LU with partial pivoting (LAPACK gttrf layout)
     if (fabs(d[i]) >= fabs(dl[i])) {
       piv[i] = i;
-      const double f = d[i] != 0.0 ? dl[i] / d[i] : 0.0;
+      const T f = d[i] != T(0) ? dl[i] / d[i] : T(0);
       dl[i] = f;
       d[i + 1] -= f * du[i];
-      du2[i] = 0.0;
+      du2[i] = T(0);
     } else {
       piv[i] = i + 1;
-      const double f = d[i] / dl[i];
+      const T f = d[i] / dl[i];
       d[i] = dl[i];
       dl[i] = f;
-      const double t = du[i];
+      const T t = du[i];
       du[i] = d[i + 1];
       d[i + 1] = t - f * d[i + 1];
       if (i + 2 < k) {
@@ -459,34 +398,129 @@ __global__ void k_tridiag_lowest(LzState* st) {
     }
   }
   piv[k - 1] = k - 1;
-  const double tiny = 1e-300;
-  for (int i = 0; i < k; ++i) d[i] = 1.0 / (fabs(d[i]) > tiny ? d[i] : tiny);   // pivots, inverted
-  for (int rep = 0; rep < 3; ++rep) {
+  // floor of a pivot: FP64 keeps the smallest normal scale; FP32 floors it at 2^-24 of the
+  // matrix's largest entry (a perturbed pivot, as in LAPACK's inverse iteration), so that one
+  // solve grows the vector by 2^24 at most and no square below overflows
+  T tiny = (T)1e-300;
+  if (sizeof(T) == 4) {
+    double mx = 0.0;
+    for (int i = 0; i < k; ++i) mx = fmax(mx, fmax(fabs(a_s[i] - lam), i + 1 < k ? fabs(b_s[i]) : 0.0));
+    tiny = (T)fmax(mx * 0x1p-24, 1e-30);
+  }
+  for (int i = 0; i < k; ++i)   // pivots, inverted
+    d[i] = T(1) / (fabs(d[i]) > tiny ? d[i] : (sizeof(T) == 4 && d[i] < T(0) ? -tiny : tiny));
+  for (int rep = 0; rep < passes; ++rep) {
     for (int i = 0; i + 1 < k; ++i) {  // forward: L
       if (piv[i] == i) {
         y[i + 1] -= dl[i] * y[i];
       } else {
-        const double t = y[i];
+        const T t = y[i];
         y[i] = y[i + 1];
         y[i + 1] = t - dl[i] * y[i + 1];
       }
     }
     for (int i = k - 1; i >= 0; --i) {  // backward: U
-      double v = y[i];
+      T v = y[i];
       if (i + 1 < k) v -= du[i] * y[i + 1];
       if (i + 2 < k) v -= du2[i] * y[i + 2];
       y[i] = v * d[i];
     }
-    double sq = 0.0;
+    T sq = T(0);
+    if (sizeof(T) == 4) {   // scale by the largest component first: the squares stay in range
+      T mx = T(0);
+      for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(y[i]));
+      mx = mx > T(0) ? T(1) / mx : T(1);
+      for (int i = 0; i < k; ++i) y[i] *= mx;
+    }
     for (int i = 0; i < k; ++i) sq += y[i] * y[i];
-    sq = 1.0 / sqrt(sq);
+    sq = T(1) / sqrt(sq);
     for (int i = 0; i < k; ++i) y[i] *= sq;
   }
-  // fix the sign: first nonzero component positive (deterministic ground vector)
   double sg = 1.0;
   for (int i = 0; i < k; ++i)
-    if (y[i] != 0.0) { sg = y[i] > 0 ? 1.0 : -1.0; break; }
-  for (int i = 0; i < k; ++i) st->y[i] = y[i] * sg;
+    if (y[i] != T(0)) { sg = y[i] > T(0) ? 1.0 : -1.0; break; }
+  if (sizeof(T) == 8) {
+    for (int i = 0; i < k; ++i) y_out[i] = (double)y[i] * sg;
+  } else {   // renormalise in FP64 so that the vector's norm is exact to FP64
+    double sq = 0.0;
+    for (int i = 0; i < k; ++i) sq += (double)y[i] * (double)y[i];
+    sg /= sqrt(sq);
+    for (int i = 0; i < k; ++i) y_out[i] = (double)y[i] * sg;
+  }
+}
+
+// Lowest eigenpair of the k x k tridiagonal Lanczos matrix, k = j + 1; one warp. The Ritz value
+// is FP64 (it decides convergence); the vector comes from FP64 inverse iteration, or FP32
+// (vec32) when the Lanczos matvecs are reduced-precision.
+__global__ void k_tridiag_lowest(LzState* st, int vec32) {
+  const int k = st->j + 1;
+  const int lane = threadIdx.x;
+  __shared__ double a_s[MRD_LANCZOS_MAX_ITER + 1], b_s[MRD_LANCZOS_MAX_ITER + 1], b2_s[MRD_LANCZOS_MAX_ITER + 1];
+  for (int i = lane; i < k; i += 32) {
+    a_s[i] = st->alpha[i];
+    b_s[i] = st->beta[i];
+    b2_s[i] = st->beta[i] * st->beta[i];
+  }
+  __syncwarp();
+  // the lowest eigenvalue lies between the lowest Gershgorin bound and the smallest diagonal
+  // element (a Rayleigh quotient of a unit vector); every lane holds the same bracket
+  double lo = 1e300, hi = 1e300;
+  for (int i = lane; i < k; i += 32) {
+    const double r = (i > 0 ? fabs(b_s[i - 1]) : 0.0) + (i + 1 < k ? fabs(b_s[i]) : 0.0);
+    lo = fmin(lo, a_s[i] - r);
+    hi = fmin(hi, a_s[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmin(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+  lo -= pad;
+  hi += pad;
+  // warm start: by interlacing the lowest eigenvalue of T_k is at most that of T_{k-1}; late
+  // in a run it moves little, so try [E_{k-1} - 4|E_{k-1} - E_{k-2}|, E_{k-1}], padded, and
+  // keep it where Sturm counts confirm it (no eigenvalue below, at least one below the top),
+  // the two counts on lanes 0 and 1; otherwise the Gershgorin bracket
+  if (k >= 3) {
+    const double e1 = st->ritz[k - 2], e2 = st->ritz[k - 3];
+    const double tol = 1e-13 * fmax(fabs(e1), 1.0);
+    const double wlo = e1 - 4.0 * fabs(e1 - e2) - tol, whi = e1 + tol;
+    if (wlo > lo && whi < hi) {
+      const int c = lane < 2 ? sturm_count(a_s, b2_s, k, lane == 0 ? wlo : whi) : 0;
+      const int c_lo = __shfl_sync(0xffffffffu, c, 0), c_hi = __shfl_sync(0xffffffffu, c, 1);
+      if (c_lo == 0 && c_hi >= 1) {
+        lo = wlo;
+        hi = whi;
+      }
+    }
+  }
+  // multisection to 1e-14 relative width (the Ritz value is compared to 1e-10 and refined
+  // afterwards), or until a subdivision no longer shrinks the interval in FP64
+  double prev_w = 0.0;
+  for (int it = 0; it < 40; ++it) {
+    if (!(hi - lo > 1e-14 * fmax(fabs(lo), fabs(hi))) || hi - lo == prev_w) break;
+    prev_w = hi - lo;
+    const double x = lo + (hi - lo) * (lane + 1) / 33.0;
+    const int c = sturm_count(a_s, b2_s, k, x);
+    const unsigned m = __ballot_sync(0xffffffffu, c >= 1);
+    if (m == 0) {
+      lo = lo + (hi - lo) * 32.0 / 33.0;
+    } else {
+      const int f = __ffs(m) - 1;  // first point with at least one eigenvalue below
+      const double nlo = f > 0 ? lo + (hi - lo) * f / 33.0 : lo;
+      hi = lo + (hi - lo) * (f + 1) / 33.0;
+      lo = nlo;
+    }
+  }
+  if (lane != 0) return;
+  const double lam = 0.5 * (lo + hi);
+  st->energy = lam;
+  st->ritz[k - 1] = lam;
+  if (vec32)
+    tridiag_inverse_iteration<float>(a_s, b_s, k, lam, 3, st->y);
+  else
+    tridiag_inverse_iteration<double>(a_s, b_s, k, lam, 3, st->y);
 }
 
 }  // namespace
@@ -619,7 +653,7 @@ static int lanczos_step(Lanczos* L, mrd_ctx* ctx, int (*apply)(void*, const doub
   MRD_CUDA(ctx, dots(L, L->w, 1, L->w, L->scal, s));
   k_record_beta<<<1, 1, 0, s>>>(L->st, L->scal);
   mrd::count_launch();
-  k_tridiag_lowest<<<1, 32, 0, s>>>(L->st);
+  k_tridiag_lowest<<<1, 32, 0, s>>>(L->st, L->fp32_full ? 1 : 0);
   mrd::count_launch();
   k_scale_next<<<grid_for(n), 256, 0, s>>>(L->w, L->V, n, L->st, L->fp32_full ? L->V32 : nullptr);
   mrd::count_launch();
