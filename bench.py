@@ -405,6 +405,8 @@ def real_arithmetic_update(P, ctx, torch, dev, stream, chi, steps, warmup, refin
     torch.cuda.synchronize(dev)
     st.timing(True)
     bonds, counts = [], []
+    phases = np.zeros(6)
+    svd_ms = 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(steps):
@@ -412,6 +414,9 @@ def real_arithmetic_update(P, ctx, torch, dev, stream, chi, steps, warmup, refin
         bonds.append((i, st.bond(i), st.bond(i + 2)))
         st.update(i, +1, form)
         counts.append(st.stats()[2])
+        phases += np.array(st.phase_ms())
+        ss = st.svd_stats()
+        svd_ms += ss[0] + ss[4]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
@@ -435,7 +440,10 @@ def real_arithmetic_update(P, ctx, torch, dev, stream, chi, steps, warmup, refin
             "gate_passed": dE <= 1e-9, "site_tensors_real": bool(real_tensors),
             "heff_tflops_bf16x3_real": f_def / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None,
             "heff_hw_tflops": 4 * f_exec / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None,
-            "kernel_ms_per_update": {"k_tc_gemm": tc_ms / steps, "k_cgemm_ff": ff_ms / steps},
+            "kernel_ms_per_update": {"k_tc_gemm": tc_ms / steps, "k_cgemm_ff": ff_ms / steps,
+                                     "k_svd_bround": svd_ms / steps},
+            "phase_ms_mean": dict(zip(["tables", "theta", "lanczos+refine", "svd", "tensors", "env"],
+                                      (phases / steps).round(2).tolist())),
             "heff_applications": n_tc, "e_fp64_converged": e_ref, "e_first": e_first}
 
 

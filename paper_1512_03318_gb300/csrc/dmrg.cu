@@ -42,7 +42,7 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
                        const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol,
                        const double* fro2, int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
-                       cudaStream_t s);
+                       bool real, cudaStream_t s);
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
                       cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
@@ -51,7 +51,8 @@ cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, i
                          int* keep, double* info, int* flat_block, cudaStream_t s);
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
                          int64_t ncta, int round, int W, int64_t smem, float tol, const double* fro2,
-                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s);
+                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, bool real,
+                         cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_colnorm2(const double2* work, const int64_t* blk, int nblk, double* out, cudaStream_t s);
@@ -710,11 +711,11 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
       for (int rd = 0; rd < sc.rounds; ++rd) {
         if (f32)
           MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, ord, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f,
-                                     fro, rot, last, sweep, wctr, s));
+                                     fro, rot, last, sweep, wctr, D->real, s));
         else
           MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, ord, nb,
                                    sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, wctr,
-                                   s));
+                                   D->real, s));
       }
       int hrot = 0;
       MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));

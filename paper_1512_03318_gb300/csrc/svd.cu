@@ -80,41 +80,70 @@ __device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;"
 // become orthogonal; one warp, columns of length p (V: r). Returns whether it rotated.
 // A column whose norm is negligible against the block (|x|^2 <= floor2 = zero_rel |M|_F^2)
 // is a numerical zero (rank deficiency): it is neither rotated nor counted as unconverged.
-template <class T, class T2>
+// REAL: the columns are real (imaginary parts zero, the real-arithmetic mode): only the real
+// parts enter the dot products and the rotation, whose phase is a sign.
+template <class T, class T2, bool REAL>
 __device__ __forceinline__ bool jacobi_pair(T2* xi, T2* xj, int p, T2* vi, T2* vj, int r, T tol, double floor2,
                                             int lane) {
   T a = 0, bb = 0, gr = 0, gi = 0;
   for (int t = lane; t < p; t += 32) {
     const T2 u = xi[t], v = xj[t];
-    a = fma(u.x, u.x, fma(u.y, u.y, a));
-    bb = fma(v.x, v.x, fma(v.y, v.y, bb));
-    gr = fma(u.x, v.x, fma(u.y, v.y, gr));     // Re(conj(u) v)
-    gi = fma(u.x, v.y, fma(-u.y, v.x, gi));    // Im(conj(u) v)
+    if (REAL) {
+      a = fma(u.x, u.x, a);
+      bb = fma(v.x, v.x, bb);
+      gr = fma(u.x, v.x, gr);
+    } else {
+      a = fma(u.x, u.x, fma(u.y, u.y, a));
+      bb = fma(v.x, v.x, fma(v.y, v.y, bb));
+      gr = fma(u.x, v.x, fma(u.y, v.y, gr));     // Re(conj(u) v)
+      gi = fma(u.x, v.y, fma(-u.y, v.x, gi));    // Im(conj(u) v)
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     bb += __shfl_xor_sync(0xffffffffu, bb, o);
     gr += __shfl_xor_sync(0xffffffffu, gr, o);
-    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+    if (!REAL) gi += __shfl_xor_sync(0xffffffffu, gi, o);
   }
-  const T g = sqrt(gr * gr + gi * gi);
+  const T g = REAL ? fabs(gr) : sqrt(gr * gr + gi * gi);
   if ((double)a <= floor2 || (double)bb <= floor2) return false;
   if (!(g > tol * sqrt(a * bb))) return false;
   // phase-free real rotation on (x_i, e^{-i phi} x_j), phi = arg(gamma)
-  const T ph_r = gr / g, ph_i = -gi / g;          // e^{-i phi}
-  const T zeta = (bb - a) / (T(2) * g);
-  const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-  const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
+  T ph_r, ph_i, c, sn;
+  if constexpr (sizeof(T) == 4) {   // FP32 pre-sweeps: fast reciprocal and rsqrt (a few ulp)
+    const float ig = 1.f / g;
+    ph_r = gr * ig;
+    ph_i = -gi * ig;
+    const float zeta = 0.5f * (bb - a) * ig, q = 1.f + zeta * zeta;
+    // very different norms: t = 1 / (2 zeta), as zeta^2 would overflow
+    const float t = fabsf(zeta) > 1e4f ? __fdividef(0.5f, zeta)
+                                       : __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + q * rsqrtf(q));
+    c = rsqrtf(1.f + t * t);
+    sn = c * t;
+  } else {
+    ph_r = gr / g;
+    ph_i = -gi / g;                               // e^{-i phi}
+    const T zeta = (bb - a) / (T(2) * g);
+    const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    c = T(1) / sqrt(T(1) + t * t);
+    sn = c * t;
+  }
   auto rot = [&](T2* ci, T2* cj, int n) {
     for (int k = lane; k < n; k += 32) {
       const T2 u = ci[k], v0 = cj[k];
-      T2 v;
-      v.x = v0.x * ph_r - v0.y * ph_i;
-      v.y = v0.x * ph_i + v0.y * ph_r;
       T2 o1, o2;
-      o1.x = c * u.x - sn * v.x; o1.y = c * u.y - sn * v.y;
-      o2.x = sn * u.x + c * v.x; o2.y = sn * u.y + c * v.y;
+      if (REAL) {
+        const T vx = v0.x * ph_r;
+        o1.x = c * u.x - sn * vx; o1.y = T(0);
+        o2.x = sn * u.x + c * vx; o2.y = T(0);
+      } else {
+        T2 v;
+        v.x = v0.x * ph_r - v0.y * ph_i;
+        v.y = v0.x * ph_i + v0.y * ph_r;
+        o1.x = c * u.x - sn * v.x; o1.y = c * u.y - sn * v.y;
+        o2.x = sn * u.x + c * v.x; o2.y = sn * u.y + c * v.y;
+      }
       ci[k] = o1;
       cj[k] = o2;
     }
@@ -133,6 +162,7 @@ __device__ __forceinline__ bool jacobi_pair(T2* xi, T2* xj, int p, T2* vi, T2* v
 // previous overlap (the next sweep removes the rest) and the column norms drift by ~1e-7,
 // which the caller absorbs because it takes the singular vectors of one side from the
 // orthogonalised columns and the other factor by projection.
+template <bool REAL>
 __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, float tol, float floor2, FF& na, FF& nb,
                                                int lane) {
   FFAcc GR = {0.f, 0.f}, GI = {0.f, 0.f};
@@ -140,29 +170,46 @@ __device__ __forceinline__ bool jacobi_pair_ff(float4* xi, float4* xj, int p, fl
     const float4 u4 = xi[t], v4 = xj[t];
     const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
     ff_mac(GR, ur, vr);                        // Re(conj(u) v)
-    ff_mac(GR, ui, vi);
-    ff_mac(GI, ur, vi);                        // Im(conj(u) v)
-    ff_mac(GI, ff_neg(ui), vr);
+    if (!REAL) {
+      ff_mac(GR, ui, vi);
+      ff_mac(GI, ur, vi);                      // Im(conj(u) v)
+      ff_mac(GI, ff_neg(ui), vr);
+    }
   }
-  const FF gr2 = ff_warp_sum(ff_norm(GR)), gi2 = ff_warp_sum(ff_norm(GI));
+  const FF gr2 = ff_warp_sum(ff_norm(GR)), gi2 = REAL ? FF{0.f, 0.f} : ff_warp_sum(ff_norm(GI));
   const float a = na.hi, bb = nb.hi, gr = gr2.hi, gi = gi2.hi;
   const float g = hypotf(gr, gi);               // no intermediate underflow
   if (a <= floor2 || bb <= floor2) return false;
   if (!(g > tol * (sqrtf(a) * sqrtf(bb)))) return false;
   const FF dba = ff_add(nb, ff_neg(na));
-  const float ph_r = gr / g, ph_i = -gi / g;    // e^{-i phi}
+  // The coefficients only need to be good FP32 numbers (the rotation is applied exactly with
+  // whatever c, s it gets), so they use the fast reciprocal and reciprocal square root: a few
+  // ulp, the same order as the FP32 rounding of the exact formulas, on the latency chain of
+  // every pair step.
+  const float ig = 1.f / g;                      // g > 0 here
+  const float ph_r = gr * ig, ph_i = -gi * ig;   // e^{-i phi}
   // columns of very different norms give |zeta| up to ~1e26: take t = 1 / (2 zeta) there
   // (relative error 1 / (4 zeta^2)) instead of squaring zeta
-  const float zeta = dba.hi / (2.f * g);
-  const float t = fabsf(zeta) > 1e4f ? 0.5f / zeta
-                                     : (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float zeta = 0.5f * dba.hi * ig;
+  const float q = 1.f + zeta * zeta;
+  const float t = fabsf(zeta) > 1e4f ? __fdividef(0.5f, zeta)
+                                     : __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + q * rsqrtf(q));
   if (!(fabsf(t) > 0.f) || !isfinite(t)) return false;   // no representable rotation
-  const float c = 1.f / sqrtf(1.f + t * t), sn = c * t;
+  const float c = rsqrtf(1.f + t * t), sn = c * t;
   // x_i' = c u - sigma v, x_j' = s u + kappa v with sigma = s e^{-i phi}, kappa = c e^{-i phi}
   const float sr = sn * ph_r, si = sn * ph_i, kr = c * ph_r, ki = c * ph_i;
   for (int k = lane; k < p; k += 32) {
     const float4 u4 = xi[k], v4 = xj[k];
     const FF ur = {u4.x, u4.z}, ui = {u4.y, u4.w}, vr = {v4.x, v4.z}, vi = {v4.y, v4.w};
+    if (REAL) {   // si = ki = 0: x_i' = c u - s_r v, x_j' = s u + k_r v, imaginary parts stay 0
+      FFAcc o1r = ff_prod1(ur, c), o2r = ff_prod1(ur, sn);
+      ff_mac1(o1r, vr, -sr);
+      ff_mac1(o2r, vr, kr);
+      const FF a1 = ff_norm(o1r), a3 = ff_norm(o2r);
+      xi[k] = make_float4(a1.hi, 0.f, a1.lo, 0.f);
+      xj[k] = make_float4(a3.hi, 0.f, a3.lo, 0.f);
+      continue;
+    }
     FFAcc o1r = ff_prod1(ur, c), o1i = ff_prod1(ui, c), o2r = ff_prod1(ur, sn), o2i = ff_prod1(ui, sn);
     ff_mac1(o1r, vr, -sr); ff_mac1(o1r, vi, si);    // c u_r - (s_r v_r - s_i v_i)
     ff_mac1(o1i, vi, -sr); ff_mac1(o1i, vr, -si);   // c u_i - (s_r v_i + s_i v_r)
@@ -248,7 +295,7 @@ __device__ __forceinline__ void rr_pair(int n, int s, int q, int& i, int& j) {
 // T is float (pre-sweeps) or double.
 // MODE 0: FP32 columns and V (T2 = float2); 1: FP64 (double2); 2: float-float columns
 // (float4, scaled by ff_scale).
-template <int MODE, class T, class T2, class S2>
+template <int MODE, bool REAL, class T, class T2, class S2>
 __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const int64_t* __restrict__ blk, int xf,
                                                     int vf, const int64_t* __restrict__ grp_prefix,
                                                     const int64_t* __restrict__ order, int nblk, int round, int W,
@@ -293,6 +340,7 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
     n_tested = n_rotated = 0;
   }
   int mine = 0;
+  unsigned long long my_tested = 0, my_rotated = 0;   // this warp's element-pairs (counters)
   T2* X = work + d[xf];
   T2* V = vf >= 0 ? work + d[vf] : nullptr;
   S2* sx = (S2*)smem_raw;                      // 2W columns of length p
@@ -329,7 +377,7 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
       for (int t = lane; t < p; t += 32) {
         const float4 u = x[t];
         ff_mac(A, FF{u.x, u.z}, FF{u.x, u.z});
-        ff_mac(A, FF{u.y, u.w}, FF{u.y, u.w});
+        if (!REAL) ff_mac(A, FF{u.y, u.w}, FF{u.y, u.w});
       }
       const FF nrm = ff_warp_sum(ff_norm(A));
       if (lane == 0) s_norm[lc] = nrm;
@@ -345,23 +393,21 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
     bool rot;
     if constexpr (MODE == 2) {
       FF na = s_norm[i], nb = s_norm[j];
-      rot = jacobi_pair_ff(sx + (int64_t)i * p, sx + (int64_t)j * p, p, (float)tol, (float)(floor2 * up * up), na,
+      rot = jacobi_pair_ff<REAL>(sx + (int64_t)i * p, sx + (int64_t)j * p, p, (float)tol, (float)(floor2 * up * up), na,
                            nb, lane);
       if (rot && lane == 0) {
         s_norm[i] = na;
         s_norm[j] = nb;
       }
     } else {
-      rot = jacobi_pair<T, T2>(sx + (int64_t)i * p, sx + (int64_t)j * p, p, V ? sv + (int64_t)i * r : nullptr,
+      rot = jacobi_pair<T, T2, REAL>(sx + (int64_t)i * p, sx + (int64_t)j * p, p, V ? sv + (int64_t)i * r : nullptr,
                                V ? sv + (int64_t)j * r : nullptr, r, tol, floor2, lane);
     }
-    if (lane == 0) atomicAdd(&n_tested, (unsigned long long)p);
+    my_tested += p;
     if (rot) {
       ++mine;
-      if (lane == 0) {
-        s_last[i] = s_last[j] = sweep;
-        atomicAdd(&n_rotated, (unsigned long long)p);
-      }
+      my_rotated += p;
+      if (lane == 0) s_last[i] = s_last[j] = sweep;
     }
     __syncwarp();
   };
@@ -400,6 +446,8 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
     last_rot[d[8] + gc] = s_last[lc];
   }
   if (lane == 0 && mine) atomicAdd(&n_rot, mine);
+  if (lane == 0 && my_tested) atomicAdd(&n_tested, my_tested);
+  if (lane == 0 && my_rotated) atomicAdd(&n_rotated, my_rotated);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (n_rot) atomicAdd(rotated, n_rot);
@@ -679,7 +727,7 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32) {
   return (int64_t)2 * W * (p + r_v) * (f32 ? 8 : 16);
 }
 
-template <int MODE, class T, class T2>
+template <int MODE, bool REAL, class T, class T2>
 static cudaError_t launch_bround(T2* work, const int64_t* blk, int xf, int vf, const int64_t* grp_prefix,
                                  const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, T tol,
                                  const double* fro2, double zero_rel, int* rotated, int* last_rot, int sweep,
@@ -688,28 +736,31 @@ static cudaError_t launch_bround(T2* work, const int64_t* blk, int xf, int vf, c
   if (W < 2 || W > 16 || (W & 1)) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_svd_bround<MODE, T, T2, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_svd_bround<MODE, REAL, T, T2, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSvdMaxSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_svd_bround<MODE, T, T2, T2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
+  k_svd_bround<MODE, REAL, T, T2, T2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
       work, blk, xf, vf, grp_prefix, order, nblk, round, W, tol, fro2, zero_rel, rotated, last_rot, sweep, wctr);
   mrd::count_launch();
   return cudaGetLastError();
 }
 
 // FP64 rounds on X (field 4 of work) or, with xff != nullptr, float-float rounds on the
-// float-float copy xff (same offsets, see svd_ff_io).
+// float-float copy xff (same offsets, see svd_ff_io); real: real columns (float-float only).
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
                        const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol,
                        const double* fro2, int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
-                       cudaStream_t s) {
+                       bool real, cudaStream_t s) {
+  if (xff && real)
+    return launch_bround<2, true, double, float4>(xff, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem,
+                                                  tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
   if (xff)
-    return launch_bround<2, double, float4>(xff, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem, tol,
-                                            fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
-  return launch_bround<1, double, double2>(work, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem, tol,
-                                           fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
+    return launch_bround<2, false, double, float4>(xff, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem,
+                                                   tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
+  return launch_bround<1, false, double, double2>(work, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem,
+                                                  tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
 }
 
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
@@ -723,9 +774,13 @@ cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, 
 
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
                          int64_t ncta, int round, int W, int64_t smem, float tol, const double* fro2,
-                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, cudaStream_t s) {
-  return launch_bround<0, float, float2>(w32, blk, 10, 11, grp_prefix, order, nblk, ncta, round, W, smem, tol,
-                                         fro2, 1e-12, rotated, last_rot, sweep, wctr, s);
+                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, bool real,
+                         cudaStream_t s) {
+  if (real)
+    return launch_bround<0, true, float, float2>(w32, blk, 10, 11, grp_prefix, order, nblk, ncta, round, W, smem,
+                                                 tol, fro2, 1e-12, rotated, last_rot, sweep, wctr, s);
+  return launch_bround<0, false, float, float2>(w32, blk, 10, 11, grp_prefix, order, nblk, ncta, round, W, smem, tol,
+                                                fro2, 1e-12, rotated, last_rot, sweep, wctr, s);
 }
 
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s) {
