@@ -305,6 +305,8 @@ struct TcArgs {
   int prec;
   int* err;
   const int2* items;       // per tile item: (task, tile within the task), or null: search the prefix
+  const int32_t* cta_off;  // with items: CTA c runs items cta_off[c] .. cta_off[c + 1] - 1; null:
+                           // items blockIdx.x, + gridDim.x, ...
   int ntile;               // B rows per tile (multiple of 16, at most 128)
   int nstages;             // shared-memory pipeline depth (at most kTcMaxStages)
   int stage_bytes;
@@ -413,6 +415,12 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const int64_t total = g.prefix[g.n_tasks];
+  // this CTA's work items: its own list (host-balanced deal) or every gridDim.x-th item; the
+  // producer, the MMA thread and the epilogue walk the same sequence
+  const bool listed = g.items != nullptr && g.cta_off != nullptr;
+  const int64_t it_first = listed ? (int64_t)g.cta_off[blockIdx.x] : (int64_t)blockIdx.x;
+  const int64_t it_last = listed ? (int64_t)g.cta_off[blockIdx.x + 1] : total;
+  const int64_t it_step = listed ? 1 : (int64_t)gridDim.x;
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
     uint32_t phase = 0;
     bool ok = true;
     int64_t fills = 0;   // stage fills issued
-    for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+    for (int64_t item = it_first, it_end = it_last; item < it_end && ok; item += it_step) {
       int64_t t, local;
       item_of(g, item, t, local);
       const int64_t* task = g.tasks + TCT * t;
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
     uint32_t acc_phase = 0;   // bit b: phase of slot b
     int slot = 0;
     bool ok = true;
-    for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+    for (int64_t item = it_first, it_end = it_last; item < it_end && ok; item += it_step) {
       int64_t t, local;
       item_of(g, item, t, local);
       const int64_t* task = g.tasks + TCT * t;
@@ -525,7 +533,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(TcArgs g) {
     uint32_t acc_phase = 0;   // bit b: phase of slot b
     int slot = 0;
     bool ok = true;
-    for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+    for (int64_t item = it_first, it_end = it_last; item < it_end && ok; item += it_step) {
       int64_t t, local;
       item_of(g, item, t, local);
       const int64_t* task = g.tasks + TCT * t;
@@ -627,15 +635,15 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
 }
 
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
-                    const int64_t* prefix, const int2* items, const int64_t* rowmap, int64_t n_tasks,
-                    int64_t total_tiles, uint8_t* z_out, double2* f_out, int prec, TcCfg cfg, int* err, int n_sm,
-                    uint64_t wait_ns, cudaStream_t s) {
+                    const int64_t* prefix, const int2* items, const int32_t* cta_off, const int64_t* rowmap,
+                    int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out, int prec, TcCfg cfg,
+                    int* err, int n_sm, uint64_t wait_ns, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   cudaError_t ea = tc_gemm_init();
   if (ea != cudaSuccess) return ea;
   const int smem = tc_smem_bytes(prec, cfg);
   if (!tc_cfg_ok(prec, cfg) || smem > kTcMaxSmem) return cudaErrorInvalidValue;
-  TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, items, cfg.ntile, cfg.stages,
+  TcArgs g{a_base, b_base, tasks, segs, prefix, n_tasks, z_out, f_out, prec, err, items, cta_off, cfg.ntile, cfg.stages,
            tc_stage_bytes(prec, cfg.ntile), wait_ns, rowmap};
   const int64_t grid = total_tiles < n_sm ? total_tiles : n_sm;
   k_tc_gemm<<<(unsigned)grid, 192, smem, s>>>(g);

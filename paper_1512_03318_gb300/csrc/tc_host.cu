@@ -3,6 +3,7 @@
 // and the two grouped-GEMM launches.
 #include <algorithm>
 #include <map>
+#include <queue>
 #include <thread>
 #include <vector>
 
@@ -14,9 +15,9 @@ cudaError_t tc_pack(const double2* src, uint8_t* dst, const int64_t* jobs, int n
                     cudaStream_t s);
 cudaError_t tc_gemm_init();
 cudaError_t tc_gemm(const uint8_t* a_base, const uint8_t* b_base, const int64_t* tasks, const int64_t* segs,
-                    const int64_t* prefix, const int2* items, const int64_t* rowmap, int64_t n_tasks,
-                    int64_t total_tiles, uint8_t* z_out, double2* f_out, int prec, TcCfg cfg, int* err, int n_sm,
-                    uint64_t wait_ns, cudaStream_t s);
+                    const int64_t* prefix, const int2* items, const int32_t* cta_off, const int64_t* rowmap,
+                    int64_t n_tasks, int64_t total_tiles, uint8_t* z_out, double2* f_out, int prec, TcCfg cfg,
+                    int* err, int n_sm, uint64_t wait_ns, cudaStream_t s);
 }  // namespace mrd
 
 struct Tc {
@@ -36,6 +37,7 @@ struct Tc {
   int64_t *pt1 = nullptr, *pt2 = nullptr;
   std::vector<int64_t> tiles1, tiles2;
   int2 *it1 = nullptr, *it2 = nullptr;   // item tables of the grouped launches
+  int32_t *co1 = nullptr, *co2 = nullptr; // first item of each CTA in them (grid + 1 entries)
   int64_t* rmap1 = nullptr;               // step-1 row map: (Z panel byte offset << 16) | row in panel
   int* err = nullptr;
 };
@@ -322,13 +324,55 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   for (size_t t = 0; t + 1 < p1.size(); ++t) q1[2 * t + 1] = p1[t + 1] - p1[t];
   for (size_t t = 0; t + 1 < p2.size(); ++t) q2[2 * t + 1] = p2[t + 1] - p2[t];
   TALLOC(T->pt1, q1.size()); TALLOC(T->pt2, q2.size());
-  // item tables: (task, tile within task) of every tile, in launch order
+  // Item tables: (task, tile within task) of every tile, dealt to the persistent CTAs by
+  // longest-processing-time-first: items by decreasing cost (the task's K tiles plus two for the
+  // pipeline fill and the epilogue), each to the CTA with the least work so far. Each CTA's
+  // items are stored together, co[c] .. co[c + 1]. A static deal in item order left step 2's
+  // SMs between 25% and 91% busy (ncu) because the tiles' K lengths differ by orders of
+  // magnitude.
+  const int grid_sm = std::max(h->n_sm, 1);
+  auto deal = [&](const std::vector<int64_t>& tk, const std::vector<int64_t>& sg, const std::vector<int64_t>& pf,
+                  std::vector<int2>& items, std::vector<int32_t>& co) {
+    const size_t nt = tk.size() / TCT;
+    const int64_t total = pf.back();
+    const int G = (int)std::min<int64_t>(total, grid_sm);
+    co.assign((size_t)G + 1, 0);
+    if (total <= 0) return;
+    std::vector<int64_t> cost(nt, 0);
+    for (size_t t = 0; t < nt; ++t) {
+      int64_t kt = 0;
+      for (int64_t k = 0; k < tk[TCT * t + 6]; ++k) kt += sg[TCS * (tk[TCT * t + 5] + k) + 2];
+      cost[t] = kt + 2;
+    }
+    std::vector<int2> all;
+    all.reserve((size_t)total);
+    for (size_t t = 0; t < nt; ++t)
+      for (int64_t l = 0; l < pf[t + 1] - pf[t]; ++l) all.push_back(make_int2((int)t, (int)l));
+    std::stable_sort(all.begin(), all.end(), [&](int2 a, int2 b) { return cost[a.x] > cost[b.x]; });
+    using Load = std::pair<int64_t, int>;   // (work so far, CTA): least work, then lowest index
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < G; ++c) heap.push({0, c});
+    std::vector<int> owner(all.size());
+    std::vector<int32_t> count((size_t)G, 0);
+    for (size_t i = 0; i < all.size(); ++i) {
+      Load l = heap.top();
+      heap.pop();
+      owner[i] = l.second;
+      ++count[(size_t)l.second];
+      l.first += cost[all[i].x];
+      heap.push(l);
+    }
+    for (int c = 0; c < G; ++c) co[(size_t)c + 1] = co[(size_t)c] + count[(size_t)c];
+    items.assign(all.size(), make_int2(0, 0));
+    std::vector<int32_t> fill(co.begin(), co.end() - 1);
+    for (size_t i = 0; i < all.size(); ++i) items[(size_t)fill[(size_t)owner[i]]++] = all[i];
+  };
   std::vector<int2> i1, i2;
-  for (size_t t = 0; t + 1 < p1.size(); ++t)
-    for (int64_t l = 0; l < p1[t + 1] - p1[t]; ++l) i1.push_back(make_int2((int)t, (int)l));
-  for (size_t t = 0; t + 1 < p2.size(); ++t)
-    for (int64_t l = 0; l < p2[t + 1] - p2[t]; ++l) i2.push_back(make_int2((int)t, (int)l));
+  std::vector<int32_t> co1, co2;
+  deal(t1, s1, p1, i1, co1);
+  deal(t2, s2, p2, i2, co2);
   TALLOC(T->it1, i1.size()); TALLOC(T->it2, i2.size());
+  TALLOC(T->co1, co1.size()); TALLOC(T->co2, co2.size());
   TALLOC(T->rmap1, rowmap.size());
 #undef TALLOC
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: device buffers");
@@ -356,6 +400,8 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   up(T->pt1, q1); up(T->pt2, q2);
   if (e == cudaSuccess && !i1.empty()) e = cudaMemcpyAsync(T->it1, i1.data(), i1.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !i2.empty()) e = cudaMemcpyAsync(T->it2, i2.data(), i2.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T->co1, co1.data(), co1.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T->co2, co2.data(), co2.size() * 4, cudaMemcpyHostToDevice, s);
   up(T->rmap1, rowmap);
   T->tiles1.resize(p1.size() - 1);
   T->tiles2.resize(p2.size() - 1);
@@ -404,10 +450,10 @@ int time_cfg(mrd_heff* h, double* ms) {
   for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
     if (r == 1) e = cudaEventRecord(a, s);
     if (e == cudaSuccess)
-      e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->rmap1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
+      e = tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->co1, T->rmap1, T->n1, T->ntiles1, T->z, nullptr, T->prec, T->cfg, T->err,
                   h->n_sm, h->wait_ns, s);
     if (e == cudaSuccess)
-      e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, nullptr, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
+      e = tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->co2, nullptr, T->n2, T->ntiles2, nullptr, out, T->prec, T->cfg, T->err, h->n_sm,
                   h->wait_ns, s);
   }
   float f = 0.f;
@@ -529,18 +575,18 @@ int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec) {
   MRD_CUDA(ctx, tc_pack((const double2*)in, T->th, T->j_th, T->n_th, T->pc_th, tp, s));
   MRD_CUDA(ctx, record_event(e0, s, cap));
   if (!h->per_task) {
-    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->rmap1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
+    MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1, T->s1, T->p1, T->it1, T->co1, T->rmap1, T->n1, T->ntiles1, T->z, nullptr, tp, T->cfg, T->err,
                           h->n_sm, h->wait_ns, s));
     MRD_CUDA(ctx, record_event(e1, s, cap));
-    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, nullptr, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
+    MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2, T->s2, T->p2, T->it2, T->co2, nullptr, T->n2, T->ntiles2, nullptr, (double2*)out, tp, T->cfg,
                           T->err, h->n_sm, h->wait_ns, s));
   } else {   // one launch per task: the per-block baseline of the grouped persistent launch
     for (int64_t t = 0; t < T->n1; ++t)
-      MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, nullptr, T->rmap1, 1, T->tiles1[t], T->z, nullptr, tp,
+      MRD_CUDA(ctx, tc_gemm(T->lw, T->th, T->t1 + TCT * t, T->s1, T->pt1 + 2 * t, nullptr, nullptr, T->rmap1, 1, T->tiles1[t], T->z, nullptr, tp,
                             T->cfg, T->err, h->n_sm, h->wait_ns, s));
     MRD_CUDA(ctx, record_event(e1, s, cap));
     for (int64_t t = 0; t < T->n2; ++t)
-      MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, nullptr, nullptr, 1, T->tiles2[t], nullptr,
+      MRD_CUDA(ctx, tc_gemm(T->z, T->wr, T->t2 + TCT * t, T->s2, T->pt2 + 2 * t, nullptr, nullptr, nullptr, 1, T->tiles2[t], nullptr,
                             (double2*)out, tp, T->cfg, T->err, h->n_sm, h->wait_ns, s));
   }
   MRD_CUDA(ctx, record_event(e2, s, cap));
