@@ -71,6 +71,20 @@ def update_caps(lx, chi):
             if 2 <= j <= n - 2 else [] for j in range(n + 1)]
 
 
+def small_profile_caps(lx, chi):
+    """Bond caps of the small-footprint profiling state: the synthetic sectors at chi on the
+    bonds from 4 left to 12 right of the centre (the profiled updates' bonds, with room for the
+    ranks the right end allows), halved per further bond (floor 512), so that the state and its
+    environments hold a few GB instead of tens."""
+    n, i = lx * LY, update_centre(lx)
+    def cap(j):
+        dist = 0 if i - 4 <= j <= i + 12 else (i - 4 - j if j < i else j - (i + 12))
+        c = chi if dist == 0 else max(512, chi >> dist)
+        return [(q[0], q[1], d) for q, d in synth.bond_sectors(c, LY, round(j / LY), synth.substream(SEED, 7, j),
+                                                               min_dim=4 if c == chi else 1)]
+    return [cap(j) if 2 <= j <= n - 2 else [] for j in range(n + 1)]
+
+
 def workload_name(chi):
     return (f"two-site update, mixed-space Hofstadter cylinder Ly={LY} Lx={LX_UPDATE} flux={FLUX_P}/{FLUX_Q} "
             f"t={T_HOP} V={V_INT} N={LX_UPDATE}, chi={chi}, random canonical MPS with synthetic sectors")
@@ -314,6 +328,8 @@ def matvec_throughput(P, ctx, torch, dev, stream, reps=10, precs=None):
     res["flops_executed"] = f_exec
     res["flops_step1"], res["flops_step2"] = f1, f2
     res["theta_len"] = h.theta_len
+    free, total = torch.cuda.mem_get_info(dev)   # device memory in use with the H_eff built
+    res["device_used_gb"] = (total - free) / 1e9
     h.close()
     return res
 
@@ -822,6 +838,8 @@ def main():
     ap.add_argument("--precs", default="", help="with --only-matvec: comma-separated precisions (default all)")
     ap.add_argument("--profile-update", action="store_true",
                     help="warm-up updates, then one update inside a CUDA profiler range (ncu --profile-from-start off)")
+    ap.add_argument("--small", action="store_true",
+                    help="with --profile-update: the small-footprint state (full chi only near the centre)")
     ap.add_argument("--details", default="bench_details.json", help="file for the per-workload details")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements (Ly = 8 forms, real vs mixed)")
     ap.add_argument("--sweeps", action="store_true",
@@ -862,7 +880,8 @@ def main():
         mv = matvec_throughput(P, ctx, torch, dev, stream, precs=precs)
         done = [k for k in PREC if k in mv]
         print(json.dumps({"only_matvec": True, "chi": chi, "heff_tflops": {k: mv[k]["tflops"] for k in done},
-                          "heff_ms_steps": {k: [mv[k]["ms_step1"], mv[k]["ms_step2"]] for k in done}}))
+                          "heff_ms_steps": {k: [mv[k]["ms_step1"], mv[k]["ms_step2"]] for k in done},
+                          "device_used_gb": mv["device_used_gb"]}))
         return 0
 
     if args.config5:
@@ -875,6 +894,8 @@ def main():
         return 0
 
     if args.profile_update:
+        if args.small:
+            caps = small_profile_caps(LX_UPDATE, chi)
         st = make_state(P, ctx, mpo, chi, caps, seed)   # tuning pass, as before the timed updates
         for k in range(args.warmup + 1):
             st.update(centre + k, +1, mixed)
@@ -887,8 +908,14 @@ def main():
         e, trunc = st.update(centre + args.warmup, +1, mixed)
         torch.cuda.synchronize(dev)
         torch.cuda.cudart().cudaProfilerStop()
-        print(json.dumps({"profile_update": True, "chi": chi, "energy": e, "discarded_weight": trunc,
-                          "phase_ms": st.phase_ms(), "svd_stats": st.svd_stats(), "lanczos_stats": st.stats()}))
+        t32, t64 = st.svd_trace()
+        free, total = torch.cuda.mem_get_info(dev)   # the device memory in use (state, caches, context)
+        print(json.dumps({"profile_update": True, "chi": chi, "small": args.small, "energy": e,
+                          "device_used_gb": (total - free) / 1e9,
+                          "discarded_weight": trunc, "bonds": [int(st.bond(centre + args.warmup)[:, 2].sum()),
+                                                               int(st.bond(centre + args.warmup + 2)[:, 2].sum())],
+                          "phase_ms": st.phase_ms(), "svd_stats": st.svd_stats(), "svd_sweeps": [len(t32), len(t64)],
+                          "lanczos_stats": st.stats()}))
         st.close()
         return 0
 
