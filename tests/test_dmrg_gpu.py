@@ -349,3 +349,52 @@ def test_svd_presweeps_and_trace(ctx, presweeps):
         d.set_option(P.MRD_DMRG_OPT_SVD_PRESWEEPS, 65)
     d.close()
     assert abs(es[-1] - e_ed[k0]) <= 1e-9 * abs(e_ed[k0]), (presweeps, es, e_ed[k0])
+
+
+def _orthonormal_vectors(site, mode, left, right, m, ly):
+    """The singular vectors a site tensor holds after orthonormalisation: the columns of every
+    right-sector block of a mode-0 tensor (rows (s, l)), the rows of every left-sector block of a
+    mode-1 tensor (columns (s, r))."""
+    dl = {(int(a), int(b)): int(c) for a, b, c in left}
+    dr = {(int(a), int(b)): int(c) for a, b, c in right}
+    off, out = 0, []
+    if mode == 0:
+        for n_r, k_r, d_r in right:
+            rows = sum(dl.get((int(n_r) - s, (int(k_r) - s * m) % ly), 0) for s in (0, 1))
+            blk = site[off:off + rows * d_r].reshape(rows, d_r)
+            off += rows * d_r
+            out += [blk[:, c] for c in range(d_r)]
+    else:
+        for n_l, k_l, d_l in left:
+            cols = sum(dr.get((int(n_l) + s, (int(k_l) + s * m) % ly), 0) for s in (0, 1))
+            blk = site[off:off + d_l * cols].reshape(d_l, cols)
+            off += d_l * cols
+            out += [blk[r, :] for r in range(d_l)]
+    assert off == site.size
+    return out
+
+
+def test_random_state_phase_convention(ctx):
+    """The seeded random MPS is orthonormalised tensor by tensor with the block SVD, whose
+    singular vectors are fixed only up to a phase each; the state must not depend on the
+    rotation order that picks it. Every singular vector of every tensor but the centre's has its
+    entry of largest modulus real and positive (4 x 4 cylinder, chi = 64, centre 7), and the
+    tensors are isometries."""
+    import paper_1512_03318_gb300 as P
+    lx, ly, n, centre = 4, 4, 4, 7
+    mpo = P.MPO(None, lx, ly, 1, 4, 1.0, 1.0)
+    d = P.DMRG(ctx, mpo, n, 0, 64, seed=7, center=centre)
+    checked = 0
+    for j in range(lx * ly):
+        if j == centre:
+            continue
+        mode, data = d.site(j)
+        for v in _orthonormal_vectors(data, mode, d.bond(j), d.bond(j + 1), j % ly, ly):
+            if v.size == 0:
+                continue
+            x = v[int(np.argmax(v.real ** 2 + v.imag ** 2))]
+            assert x.real > 0 and abs(x.imag) <= 1e-13 * abs(x), (j, x)
+            assert abs(np.vdot(v, v) - 1.0) < 1e-12
+            checked += 1
+    d.close()
+    assert checked > 100
