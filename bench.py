@@ -335,7 +335,7 @@ def matvec_throughput(P, ctx, torch, dev, stream, reps=10, precs=None):
 
 
 def real_vs_mixed(P, ctx, torch, dev, stream):
-    """The paper's comparison of the two bases (Sec. III.B, Fig. 3) on this build's own code:
+    """The paper's comparison of the two bases (Sec. III.B, Fig. 3) on the library's own code:
     the same Hofstadter cylinder (Lx = 20, mid-ring sites) at the same chi, with the mixed
     basis (charges N and K mod Ly, the library's mixed-space MPO) and with the real-space basis
     (charge N only, the real-space MPO, D = 3 Ly + 2). Reports the H_eff time per application
@@ -674,7 +674,7 @@ def free_fermion_k(lx, ly, flux, n, t=T_HOP):
 
 
 def sweeps_mixed_vs_real(P, ctx, torch, dev, chi=1024, lx=16, ly=8, max_sweeps=14, tol=1e-8, chi0=128):
-    """The paper's basis comparison (Sec. III.B, Fig. 3(c, d)) on this build's own code: finite
+    """The paper's basis comparison (Sec. III.B, Fig. 3(c, d)) on the library's own code: finite
     two-site DMRG sweeps from a seeded random MPS to convergence on the Ly = 8 interacting
     Hofstadter cylinder (flux 1/8, t = V = 1, one particle per ring), in the mixed basis
     (charges N, K; K of the free-fermion ground state) and in real space (charge N only), both
