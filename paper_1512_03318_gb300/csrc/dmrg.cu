@@ -42,7 +42,7 @@ int64_t svd_bround_smem(int W, int64_t p, int64_t r_v, bool f32);
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
                        const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol,
                        const double* fro2, int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
-                       bool real, cudaStream_t s);
+                       const int* prev_rotated, bool real, cudaStream_t s);
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
                       cudaStream_t s);
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
@@ -51,8 +51,8 @@ cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, i
                          int* keep, double* info, int* flat_block, cudaStream_t s);
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
                          int64_t ncta, int round, int W, int64_t smem, float tol, const double* fro2,
-                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, bool real,
-                         cudaStream_t s);
+                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
+                         const int* prev_rotated, bool real, cudaStream_t s);
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk, int nblk, cudaStream_t s);
 cudaError_t svd_colnorm2(const double2* work, const int64_t* blk, int nblk, double* out, cudaStream_t s);
@@ -346,7 +346,7 @@ struct mrd_dmrg {
   std::vector<SiteT> A;
   std::vector<EnvT> L, R;
   Buf gtask, gseg, gpref, gitems, ctask, theta, theta2, svd_blk, svd_src, svd_pref, svd_work, svd_u, svd_vh, svd_s,
-      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_rot, svd_w32, svd_x2, svd_fro, svd_last, svd_ctr, tbuf,
+      svd_ss, svd_ord, svd_flat, svd_keep, svd_info, svd_w32, svd_x2, svd_fro, svd_last, svd_ctr, tbuf,
       zeros, svd_perm;
   // columns entering the final Jacobi sweeps and columns of all blocks, last block SVD
   double svd_cols[2] = {0, 0};
@@ -367,6 +367,9 @@ struct mrd_dmrg {
   std::vector<int32_t> svd_trace32, svd_trace64;
   std::vector<double> svd_tms32, svd_tms64;   // host ms of each sweep (launches to the count read back)
   int svd_presweeps = kMaxSweeps32;   // MRD_DMRG_OPT_SVD_PRESWEEPS
+  Buf svd_rotv;                       // rotation count of each sweep of a phase
+  int* svd_hcnt = nullptr;            // pinned host copies of them
+  cudaEvent_t svd_sev[2] = {nullptr, nullptr};
   bool gemm_ff = false;   // grouped GEMMs of the update in float-float (refine_prec MRD_PREC_FF)
   double last_energy = 0.0, last_trunc = 0.0;
   // Schmidt values of the bond cut by the last update: bond index, (N, K) and value per state
@@ -670,7 +673,6 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   MRD_CUDA(ctx, D->svd_last.need((size_t)std::max<int64_t>(slen, 1) * 4));
   MRD_CUDA(ctx, D->svd_keep.need((size_t)nb * 4));
   MRD_CUDA(ctx, D->svd_info.need(4 * 8));
-  MRD_CUDA(ctx, D->svd_rot.need(8));
   MRD_CUDA(ctx, D->svd_fro.need((size_t)nb * 8));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_blk.p, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice, s));
   MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_src.p, src_off.data(), src_off.size() * 8, cudaMemcpyHostToDevice, s));
@@ -678,7 +680,6 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   const int64_t* dblk = D->svd_blk.as<int64_t>();
   const double* fro = D->svd_fro.as<double>();
   MRD_CUDA(ctx, svd_load(src, dblk, D->svd_src.as<int64_t>(), nb, D->svd_work.as<double2>(), D->svd_fro.as<double>(), s));
-  int* rot = D->svd_rot.as<int>();
   const int64_t* pre32 = D->svd_pref.as<int64_t>();
   const int64_t* pre64 = pre32 + nb + 1;
   const int64_t* ord = pre32 + 2 * (nb + 1);
@@ -704,22 +705,38 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     std::vector<double>& tms = f32 ? D->svd_tms32 : D->svd_tms64;
     trace.clear();
     tms.clear();
-    MRD_CUDA(ctx, cudaStreamSynchronize(s));
-    auto t_last = std::chrono::steady_clock::now();
-    for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
-      MRD_CUDA(ctx, cudaMemsetAsync(rot, 0, 4, s));
+    // One rotation counter per sweep. Sweep s + 1 is enqueued before the host reads sweep s's
+    // count (from pinned memory, after an event), so the device runs on while the host waits;
+    // a sweep whose predecessor rotated nothing returns at once (the kernels check).
+    MRD_CUDA(ctx, D->svd_rotv.need((size_t)(max_sweeps + 1) * 4));
+    int* rotv = D->svd_rotv.as<int>();
+    MRD_CUDA(ctx, cudaMemsetAsync(rotv, 0, (size_t)(max_sweeps + 1) * 4, s));
+    if (!D->svd_hcnt) MRD_CUDA(ctx, cudaHostAlloc((void**)&D->svd_hcnt, 4 * (kMaxSweeps64 + 65), cudaHostAllocDefault));
+    for (cudaEvent_t& ev : D->svd_sev)
+      if (!ev) MRD_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    auto enqueue_sweep = [&](int sweep) -> int {
+      const int* prev = sweep > 0 ? rotv + sweep - 1 : nullptr;
       for (int rd = 0; rd < sc.rounds; ++rd) {
         if (f32)
           MRD_CUDA(ctx, svd_bround32(D->svd_w32.as<float2>(), dblk, pre32, ord, nb, sc.ncta, rd, sc.W, sc.smem, 1e-5f,
-                                     fro, rot, last, sweep, wctr, D->real, s));
+                                     fro, rotv + sweep, last, sweep, wctr, prev, D->real, s));
         else
           MRD_CUDA(ctx, svd_bround(D->svd_work.as<double2>(), ff ? D->svd_x2.as<float4>() : nullptr, dblk, pre64, ord, nb,
-                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rot, last, sweep, wctr,
-                                   D->real, s));
+                                   sc.ncta, rd, sc.W, sc.smem, ff ? kTolFF : kTolF64, fro, rotv + sweep, last, sweep,
+                                   wctr, prev, D->real, s));
       }
-      int hrot = 0;
-      MRD_CUDA(ctx, cudaMemcpyAsync(&hrot, rot, 4, cudaMemcpyDeviceToHost, s));
-      MRD_CUDA(ctx, cudaStreamSynchronize(s));
+      MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_hcnt + sweep, rotv + sweep, 4, cudaMemcpyDeviceToHost, s));
+      MRD_CUDA(ctx, cudaEventRecord(D->svd_sev[sweep & 1], s));
+      return MRD_OK;
+    };
+    MRD_CUDA(ctx, cudaStreamSynchronize(s));
+    auto t_last = std::chrono::steady_clock::now();
+    int rc0 = max_sweeps > 0 ? enqueue_sweep(0) : MRD_OK;
+    if (rc0 != MRD_OK) return rc0;
+    for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
+      if (sweep + 1 < max_sweeps && (rc0 = enqueue_sweep(sweep + 1)) != MRD_OK) return rc0;
+      MRD_CUDA(ctx, cudaEventSynchronize(D->svd_sev[sweep & 1]));
+      const int hrot = D->svd_hcnt[sweep];
       *used = sweep + 1;
       trace.push_back(hrot);
       const auto t_now = std::chrono::steady_clock::now();
@@ -1233,6 +1250,9 @@ int mrd_dmrg_free(mrd_dmrg* D) {
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : D->svd_ev)
       if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : D->svd_sev)
+      if (e) cudaEventDestroy(e);
+    if (D->svd_hcnt) cudaFreeHost(D->svd_hcnt);
     delete D;
   }
   mrd_ctx_release(ctx);

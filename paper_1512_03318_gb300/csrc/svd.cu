@@ -301,12 +301,16 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
                                                     const int64_t* __restrict__ order, int nblk, int round, int W,
                                                     T tol, const double* __restrict__ fro2, double zero_rel,
                                                     int* __restrict__ rotated, int* __restrict__ last_rot, int sweep,
-                                                    unsigned long long* __restrict__ wctr) {
+                                                    unsigned long long* __restrict__ wctr,
+                                                    const int* __restrict__ prev_rotated) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ int n_rot;
   __shared__ unsigned long long n_tested, n_rotated;   // element-pairs tested / rotated
   __shared__ int s_last[32];   // sweep in which each staged column last rotated
   __shared__ FF s_norm[32];    // float-float column norms (MODE 2)
+  // the host enqueues each sweep before it has read the previous sweep's rotation count: a
+  // sweep that follows one in which nothing rotated (the phase converged) does nothing
+  if (prev_rotated != nullptr && *prev_rotated == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int64_t cta = blockIdx.x;
   int lo = 0, hi = nblk - 1;   // largest k with grp_prefix[k] <= cta; the CTAs run over the
@@ -731,7 +735,7 @@ template <int MODE, bool REAL, class T, class T2>
 static cudaError_t launch_bround(T2* work, const int64_t* blk, int xf, int vf, const int64_t* grp_prefix,
                                  const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, T tol,
                                  const double* fro2, double zero_rel, int* rotated, int* last_rot, int sweep,
-                                 unsigned long long* wctr, cudaStream_t s) {
+                                 unsigned long long* wctr, const int* prev_rotated, cudaStream_t s) {
   if (ncta == 0) return cudaSuccess;
   if (W < 2 || W > 16 || (W & 1)) return cudaErrorInvalidValue;
   static bool attr = false;
@@ -742,7 +746,8 @@ static cudaError_t launch_bround(T2* work, const int64_t* blk, int xf, int vf, c
     attr = true;
   }
   k_svd_bround<MODE, REAL, T, T2, T2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-      work, blk, xf, vf, grp_prefix, order, nblk, round, W, tol, fro2, zero_rel, rotated, last_rot, sweep, wctr);
+      work, blk, xf, vf, grp_prefix, order, nblk, round, W, tol, fro2, zero_rel, rotated, last_rot, sweep, wctr,
+      prev_rotated);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -752,15 +757,15 @@ static cudaError_t launch_bround(T2* work, const int64_t* blk, int xf, int vf, c
 cudaError_t svd_bround(double2* work, float4* xff, const int64_t* blk, const int64_t* grp_prefix,
                        const int64_t* order, int nblk, int64_t ncta, int round, int W, int64_t smem, double tol,
                        const double* fro2, int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
-                       bool real, cudaStream_t s) {
+                       const int* prev_rotated, bool real, cudaStream_t s) {
   if (xff && real)
     return launch_bround<2, true, double, float4>(xff, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem,
-                                                  tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
+                                                  tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, prev_rotated, s);
   if (xff)
     return launch_bround<2, false, double, float4>(xff, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem,
-                                                   tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
+                                                   tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, prev_rotated, s);
   return launch_bround<1, false, double, double2>(work, blk, 4, -1, grp_prefix, order, nblk, ncta, round, W, smem,
-                                                  tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, s);
+                                                  tol, fro2, 1e-28, rotated, last_rot, sweep, wctr, prev_rotated, s);
 }
 
 cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, const double* fro2, bool to_ff,
@@ -774,13 +779,13 @@ cudaError_t svd_ff_io(double2* work, float4* xff, const int64_t* blk, int nblk, 
 
 cudaError_t svd_bround32(float2* w32, const int64_t* blk, const int64_t* grp_prefix, const int64_t* order, int nblk,
                          int64_t ncta, int round, int W, int64_t smem, float tol, const double* fro2,
-                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr, bool real,
-                         cudaStream_t s) {
+                         int* rotated, int* last_rot, int sweep, unsigned long long* wctr,
+                         const int* prev_rotated, bool real, cudaStream_t s) {
   if (real)
     return launch_bround<0, true, float, float2>(w32, blk, 10, 11, grp_prefix, order, nblk, ncta, round, W, smem,
-                                                 tol, fro2, 1e-12, rotated, last_rot, sweep, wctr, s);
+                                                 tol, fro2, 1e-12, rotated, last_rot, sweep, wctr, prev_rotated, s);
   return launch_bround<0, false, float, float2>(w32, blk, 10, 11, grp_prefix, order, nblk, ncta, round, W, smem, tol,
-                                                fro2, 1e-12, rotated, last_rot, sweep, wctr, s);
+                                                fro2, 1e-12, rotated, last_rot, sweep, wctr, prev_rotated, s);
 }
 
 cudaError_t svd_to_f32(const double2* work, float2* w32, const int64_t* blk, int nblk, cudaStream_t s) {
