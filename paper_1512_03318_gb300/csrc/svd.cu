@@ -308,9 +308,6 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
   __shared__ unsigned long long n_tested, n_rotated;   // element-pairs tested / rotated
   __shared__ int s_last[32];   // sweep in which each staged column last rotated
   __shared__ FF s_norm[32];    // float-float column norms (MODE 2)
-  // the host enqueues each sweep before it has read the previous sweep's rotation count: a
-  // sweep that follows one in which nothing rotated (the phase converged) does nothing
-  if (prev_rotated != nullptr && *prev_rotated == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int64_t cta = blockIdx.x;
   int lo = 0, hi = nblk - 1;   // largest k with grp_prefix[k] <= cta; the CTAs run over the
@@ -323,6 +320,13 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
   const int p = (int)d[2], r = (int)d[3];
   const int G = (r + W - 1) / W, Gp = G + (G & 1) < 2 ? 2 : G + (G & 1);
   if (r == 0 || round >= Gp - 1) return;
+  // Rounds are launched as programmatic dependents of the previous launch: everything above
+  // reads only the tables the host wrote before the sweeps; the columns, the last-rotation
+  // sweeps and the rotation counts are read after the previous round has completed.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the host enqueues each sweep before it has read the previous sweep's rotation count: a
+  // sweep that follows one in which nothing rotated (the phase converged) does nothing
+  if (prev_rotated != nullptr && *prev_rotated == 0) return;
   const int k = (int)(cta - grp_prefix[lo]);
   int gI, gJ;
   rr_pair(Gp, round, k, gI, gJ);
@@ -431,6 +435,8 @@ __global__ void __launch_bounds__(512) k_svd_bround(T2* __restrict__ work, const
     if (i < nI && j < nJ) do_pair(i, W + j);
     __syncthreads();
   }
+  // the next round may be scheduled now; it waits for this one's write-back to complete
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (int cc = warp; cc < nI + nJ; cc += nwarp) {
     const int lc = cc < nI ? cc : W + cc - nI;
     const int gc = cc < nI ? gI * W + cc : gJ * W + cc - nI;
@@ -745,11 +751,22 @@ static cudaError_t launch_bround(T2* work, const int64_t* blk, int xf, int vf, c
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_svd_bround<MODE, REAL, T, T2, T2><<<(unsigned)ncta, W * 32, (size_t)smem, s>>>(
-      work, blk, xf, vf, grp_prefix, order, nblk, round, W, tol, fro2, zero_rel, rotated, last_rot, sweep, wctr,
-      prev_rotated);
+  // programmatic dependent launch: the round's CTAs are scheduled while the previous round
+  // writes back, and wait (griddepcontrol.wait) before reading anything it wrote
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)ncta);
+  lc.blockDim = dim3((unsigned)(W * 32));
+  lc.dynamicSmemBytes = (size_t)smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&lc, k_svd_bround<MODE, REAL, T, T2, T2>, work, blk, xf, vf, grp_prefix, order,
+                                     nblk, round, W, tol, fro2, zero_rel, rotated, last_rot, sweep, wctr, prev_rotated);
   mrd::count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 // FP64 rounds on X (field 4 of work) or, with xff != nullptr, float-float rounds on the
