@@ -631,9 +631,21 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
   std::vector<int64_t> pp(3 * nb + 2, 0);
   int64_t* order = pp.data() + 2 * (nb + 1);
   for (int b = 0; b < nb; ++b) order[b] = b;
-  std::stable_sort(order, order + nb, [&](int64_t x, int64_t y) {
-    return blk[SVF * x + 3] * blk[SVF * x + 2] > blk[SVF * y + 3] * blk[SVF * y + 2];
-  });
+  // Largest blocks first, then the rest in reverse: once the first CTAs hold one SM each, the
+  // CTAs that share an SM with the largest blocks' are the smallest ones (snake order).
+  auto order_blocks = [&](int W) {
+    std::stable_sort(order, order + nb, [&](int64_t x, int64_t y) {
+      return blk[SVF * x + 3] * blk[SVF * x + 2] > blk[SVF * y + 3] * blk[SVF * y + 2];
+    });
+    int64_t cum = 0;
+    int k = 0;
+    for (; k < nb && cum < D->n_sm; ++k) {
+      const int64_t r = blk[SVF * order[k] + 3], G = (r + W - 1) / W;
+      cum += r > 0 ? std::max<int64_t>(2, G + (G & 1)) / 2 : 0;
+    }
+    std::reverse(order + k, order + nb);
+  };
+  order_blocks(8);
   auto schedule = [&](int W, bool f32, int64_t* pre) -> Sched {
     Sched sc;
     for (;;) {
@@ -833,9 +845,7 @@ int block_svd(mrd_dmrg* D, std::vector<int64_t>& blk, const std::vector<int64_t>
     MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_perm.p, perm.data(), (size_t)slen * 4, cudaMemcpyHostToDevice, s));
     MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_blk.p, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice, s));
     // the final sweeps' schedule on the remaining columns, largest blocks first
-    std::stable_sort(order, order + nb, [&](int64_t x, int64_t y) {
-      return blk[SVF * x + 3] * blk[SVF * x + 2] > blk[SVF * y + 3] * blk[SVF * y + 2];
-    });
+    order_blocks(s64.W);
     s64 = schedule(s64.W, false, pp.data() + nb + 1);
     MRD_CUDA(ctx, cudaMemcpyAsync(D->svd_pref.p, pp.data(), pp.size() * 8, cudaMemcpyHostToDevice, s));
     MRD_CUDA(ctx, svd_gather_cols(D->svd_work.as<double2>(), D->svd_x2.as<double2>(), dblk, nb,
