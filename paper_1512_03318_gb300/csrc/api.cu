@@ -313,6 +313,7 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
     dl(t2, p.t2, (size_t)TF * c[C_NT2]); dl(s2, p.seg2, (size_t)SF * c[C_NT2] * d.seg2_stride);
     dl(lw, p.lw, (size_t)LWF * c[C_NLW]); dl(wr, p.wr, (size_t)WRF * c[C_NWR]);
     dl(lmap, p.lmap, (size_t)d.d_l * d.n_l); dl(rmap, p.rmap, (size_t)d.d_r * d.n_r);
+    dl(h->z_host, p.z, (size_t)ZF * std::min(c[C_NZ], d.z_cap));   // Z blocks, for the tensor-core panel tables
     if (e == cudaSuccess && d.nnz_i) e = cudaMemcpy(wperm_i.data(), p.wi_perm, d.nnz_i * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && d.nnz_j) e = cudaMemcpy(wperm_j.data(), p.wj_perm, d.nnz_j * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { delete h; mrd_ctx_release(ctx); return mrd_cuda_fail(ctx, e, "mrd_heff_create: table download"); }

@@ -1302,6 +1302,10 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   ++D->updates;
   if (D->real && (rc = mrd_heff_set_option(h, MRD_OPT_REAL, 1)) != MRD_OK) return rc;
   if (D->timing) mrd_heff_timing(h, 1);
+  // the tensor-core tables of the Lanczos matvecs are host work: built on a host thread while
+  // the device folds the environments, forms theta and converts the refinement's operands
+  const bool tc = p->prec == MRD_PREC_TF32 || p->prec == MRD_PREC_BF16X3;
+  if (tc) tc_prebuild(h, p->prec);
   auto collect = [&](int which) {
     if (!D->timing) return;
     double a = 0, b = 0;
@@ -1319,9 +1323,6 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   lap(1);
   double e = 0.0;
   int32_t it = 0;
-  // the float-float refinement's operand conversion runs on the device while the host builds
-  // the tensor-core tables of the Lanczos matvecs
-  const bool tc = p->prec == MRD_PREC_TF32 || p->prec == MRD_PREC_BF16X3;
   if (tc && p->refine_iter > 0 && p->refine_prec == MRD_PREC_FF && (rc = heff_prefetch_ff(h)) != MRD_OK) return rc;
   if ((rc = mrd_lanczos(h, (double*)theta, p->lanczos_max_iter, p->lanczos_tol, p->prec, &e, &it)) != MRD_OK) return rc;
   D->last_iters = it;

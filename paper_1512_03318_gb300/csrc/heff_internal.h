@@ -11,9 +11,12 @@ void lanczos_free(Lanczos* L);
 }  // namespace mrd
 struct Tc;
 void tc_free(Tc* t);
+struct TcPre;
+void tc_pre_free(TcPre* t);
 struct mrd_heff;
 int tc_apply(mrd_heff* h, const double* in, double* out, int32_t prec);
 int tc_prepare(mrd_heff* h, int32_t prec);
+void tc_prebuild(mrd_heff* h, int32_t prec);
 int tc_config(const mrd_heff* h, int32_t* cfg4);
 int autotune(mrd_heff* h, int prec);
 void tc_env_changed(mrd_heff* h);
@@ -97,9 +100,10 @@ struct mrd_heff {
   int32_t gcalls = 0;
   Lanczos* lz = nullptr;
   // host copies of the device-built tables (downloaded once at creation)
-  std::vector<int64_t> mid_host, lw_host, wr_host, lmap_host, rmap_host, t1_host, s1_host, t2_host, s2_host;
+  std::vector<int64_t> mid_host, lw_host, wr_host, lmap_host, rmap_host, t1_host, s1_host, t2_host, s2_host, z_host;
   // tensor-core path state (tc_host.cu)
   struct Tc* tc = nullptr;
+  struct TcPre* tc_pre = nullptr;   // panel tables being built on a host thread (tc_prebuild)
   // float-float path: LW, WR in float-float layout (prepared after each environment load) and
   // theta staging
   Arena ff_mem;
@@ -120,6 +124,7 @@ struct mrd_heff {
   int64_t* pt_pref2 = nullptr;
   std::vector<int64_t> pt_tiles1, pt_tiles2;
   ~mrd_heff() {
+    tc_pre_free(tc_pre);   // joins the thread, which reads the host tables
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : gev)

@@ -3,6 +3,7 @@
 // and the two grouped-GEMM launches.
 #include <algorithm>
 #include <map>
+#include <new>
 #include <queue>
 #include <thread>
 #include <vector>
@@ -83,15 +84,31 @@ struct PanelIndex {
 int64_t a_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 128) * nkt * planes * 128; }
 int64_t b_bytes(int64_t rows, int64_t nkt, int planes) { return round_up(rows, 16) * nkt * planes * 128; }
 
-int build(mrd_heff* h, int prec, TcCfg cfg) {
-  mrd_ctx* ctx = h->ctx;
-  Tc* T = h->tc;
+// Host tables of the tensor-core path for one precision and tile configuration: panel
+// layouts, pack jobs, tasks, segments, row map and the per-CTA item deal. Built without any
+// device call, so that a host thread can build them while the device works (tc_prebuild).
+struct TcTables {
+  int prec = 0;
+  TcCfg cfg{0, 0, 0};
+  int n_sm = 0;
+  std::vector<int64_t> j_lw, j_wr, j_th, t1, s1, p1, t2, s2, p2, q1, q2, rowmap;
+  std::vector<int2> i1, i2;
+  std::vector<int32_t> co1, co2;
+  int64_t lw_b = 0, wr_b = 0, th_b = 0, z_b = 0, pc_lw = 0, pc_wr = 0, pc_th = 0;
+  const char* err = nullptr;   // why the tables could not be built
+};
+
+bool tables(const mrd_heff* h, int prec, TcCfg cfg, TcTables& o) {
+  auto fail = [&](const char* m) { o.err = m; return false; };
+  o.prec = prec;
+  o.cfg = cfg;
+  o.n_sm = h->n_sm;
   const int aplanes = tc_aplanes(prec), bplanes = tc_bplanes(prec), kpt = tc_kpt(prec), ntile = cfg.ntile;
   const int64_t* c = h->counts;
   PanelIndex wr_map, th_map, z_map;
   wr_map.v.reserve(c[C_NWR]);
-  std::vector<int64_t> j_lw, j_wr, j_th;
-  int64_t lw_b = 0, wr_b = 0, th_b = 0, z_b = 0;
+  std::vector<int64_t>&j_lw = o.j_lw, &j_wr = o.j_wr, &j_th = o.j_th;
+  int64_t &lw_b = o.lw_b, &wr_b = o.wr_b, &th_b = o.th_b, &z_b = o.z_b;
   // (the folded left operand LW is packed below, stacked by input middle sector)
   // folded right operand WR(w', s2, s2', b): B panel of its transpose, rows d_b', K d_b
   for (int64_t k = 0; k < c[C_NWR]; ++k) {
@@ -119,11 +136,8 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     }
   }
   // Z(w', m_in) rows (s1') x columns (s2): A panels keyed by their FP64 element offset
-  std::vector<int64_t> z(ZF * c[C_NZ]);
-  if (c[C_NZ]) {
-    cudaError_t e = cudaMemcpy(z.data(), h->p.z, z.size() * 8, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: table download");
-  }
+  const std::vector<int64_t>& z = h->z_host;   // downloaded with the other tables at creation
+  if ((int64_t)z.size() < ZF * c[C_NZ]) return fail("tc: Z table missing");
   const int64_t nmid = c[C_NMID];
   for (int64_t k = 0; k < c[C_NZ]; ++k) {
     const int64_t* zr = &z[ZF * k];
@@ -146,7 +160,9 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   wr_map.finish();
   th_map.finish();
   z_map.finish();
-  std::vector<int64_t> t1, s1, p1{0}, t2, s2, p2{0};
+  std::vector<int64_t>&t1 = o.t1, &s1 = o.s1, &p1 = o.p1, &t2 = o.t2, &s2 = o.s2, &p2 = o.p2;
+  p1.assign(1, 0);
+  p2.assign(1, 0);
   // step-2 tasks (theta' = sum Z WR), built on a second host thread while this one builds the
   // step-1 tasks: the two loops share only the finished (read-only) panel indexes
   bool step2_ok = true;
@@ -171,7 +187,13 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   };
   std::thread step2;
   try {
-    step2 = std::thread(build_step2);
+    step2 = std::thread([&] {
+      try {
+        build_step2();
+      } catch (...) {   // out of host memory
+        step2_ok = false;
+      }
+    });
   } catch (...) {   // no thread to be had: build it here, before step 1
     build_step2();
   }
@@ -186,7 +208,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
   // class a task of its own with the K segments it needs, so no zero block is multiplied.
   // The stacked LW of a class and K segment s1 is one A panel; each output row is scattered to
   // its Z panel through a row map (mode 2).
-  std::vector<int64_t> rowmap;
+  std::vector<int64_t>& rowmap = o.rowmap;
   {
     std::vector<int64_t> zrow_of((size_t)c[C_NMID] > 0 ? (size_t)h->d.d_m * nmid : 0, -1);
     for (int64_t k = 0; k < c[C_NZ]; ++k) zrow_of[(size_t)(z[ZF * k] * nmid + z[ZF * k + 1])] = k;
@@ -218,7 +240,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
         int64_t aoff[2] = {-1, -1}, ank[2] = {0, 0};
         for (int q1 = 0; q1 < 2; ++q1) {
           if (k != 2 && k != q1) continue;
-          if (rin[5 + q1] < 0) return mrd_fail(ctx, MRD_E_STATE, "tc: LW block without its theta rows");
+          if (rin[5 + q1] < 0) return fail("tc: LW block without its theta rows");
           const int64_t K = h->left[3 * rin[5 + q1] + 2];
           ank[q1] = (K + kpt - 1) / kpt;
           aoff[q1] = lw_b;
@@ -235,18 +257,18 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
           for (int q1 = 0; q1 < 2; ++q1) {
             if (aoff[q1] < 0) continue;
             const Panel* b = th_map.find(rin[4] + (q1 ? rin[7] : 0) * rin[3] + coff);
-            if (!b || b->nkt != ank[q1]) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 operand not packed");
+            if (!b || b->nkt != ank[q1]) return fail("tc: step-1 operand not packed");
             s1.insert(s1.end(), {aoff[q1], b->off, ank[q1], 0});
             ++nseg;
           }
           const int64_t nkt_z = (N + kpt - 1) / kpt;
           for (const Member& mb : cls[k]) {
             const int64_t zk = zrow_of[(size_t)(mb.wp * nmid + mi)];
-            if (zk < 0) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output block missing");
+            if (zk < 0) return fail("tc: step-1 output block missing");
             const int64_t* zr = &z[ZF * zk];
             const int64_t* rout = &mid[MIDF * zr[2]];
             const Panel* q = z_map.find(zr[5] + (mb.s1p ? rout[7] : 0) * rin[3] + coff);
-            if (!q || q->nkt != nkt_z) return mrd_fail(ctx, MRD_E_STATE, "tc: step-1 output panel missing");
+            if (!q || q->nkt != nkt_z) return fail("tc: step-1 output panel missing");
             for (int64_t r = 0; r < mb.rows; ++r) rowmap.push_back(q->off << 16 | r);
           }
           t1.insert(t1.end(), {R, N, map0, 0, 0, seg0, nseg, 2, nkt_z, 0});
@@ -256,7 +278,7 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     }
   }
   if (step2.joinable()) step2.join();
-  if (!step2_ok) return mrd_fail(ctx, MRD_E_STATE, "tc: step-2 operand not packed");
+  if (!step2_ok) return fail("tc: step-2 operand not packed");
   // block schedule: tiles are dealt to the persistent CTAs in task order; order 1 puts the
   // tasks with the most work (tiles x K tiles) first so that the long ones start early
   if (cfg.order == 1) {
@@ -303,27 +325,14 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
       return true;
     };
     if (!chk(t1, s1, lw_b, th_b, true) || !chk(t2, s2, z_b, wr_b, false))
-      return mrd_fail(ctx, MRD_E_STATE, "tc: internal panel table check failed");
-    if (!tc_cfg_ok(prec, cfg)) return mrd_fail(ctx, MRD_E_STATE, "tc: tile configuration does not fit");
+      return fail("tc: internal panel table check failed");
+    if (!tc_cfg_ok(prec, cfg)) return fail("tc: tile configuration does not fit");
   }
-  // device buffers
-  delete h->tc;
-  h->tc = T = new Tc();
-  T->prec = prec;
-  T->cfg = cfg;
-  Arena& A = T->mem;
-  A.stream = ctx->stream;
-  cudaError_t e = cudaSuccess;
-#define TALLOC(ptr, n) if (e == cudaSuccess) e = A.alloc(&(ptr), (size_t)std::max<int64_t>((n), 1))
-  TALLOC(T->lw, lw_b); TALLOC(T->wr, wr_b); TALLOC(T->th, th_b); TALLOC(T->z, z_b);
-  TALLOC(T->t1, t1.size()); TALLOC(T->s1, s1.size()); TALLOC(T->p1, p1.size());
-  TALLOC(T->t2, t2.size()); TALLOC(T->s2, s2.size()); TALLOC(T->p2, p2.size());
-  TALLOC(T->j_lw, j_lw.size()); TALLOC(T->j_wr, j_wr.size()); TALLOC(T->j_th, j_th.size());
-  TALLOC(T->err, 1);
-  std::vector<int64_t> q1(2 * std::max<size_t>(p1.size() - 1, 1), 0), q2(2 * std::max<size_t>(p2.size() - 1, 1), 0);
+  std::vector<int64_t>&q1 = o.q1, &q2 = o.q2;
+  q1.assign(2 * std::max<size_t>(p1.size() - 1, 1), 0);
+  q2.assign(2 * std::max<size_t>(p2.size() - 1, 1), 0);
   for (size_t t = 0; t + 1 < p1.size(); ++t) q1[2 * t + 1] = p1[t + 1] - p1[t];
   for (size_t t = 0; t + 1 < p2.size(); ++t) q2[2 * t + 1] = p2[t + 1] - p2[t];
-  TALLOC(T->pt1, q1.size()); TALLOC(T->pt2, q2.size());
   // Item tables: (task, tile within task) of every tile, dealt to the persistent CTAs by
   // longest-processing-time-first: items by decreasing cost (the task's K tiles plus two for the
   // pipeline fill and the epilogue), each to the CTA with the least work so far. Each CTA's
@@ -367,19 +376,8 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     std::vector<int32_t> fill(co.begin(), co.end() - 1);
     for (size_t i = 0; i < all.size(); ++i) items[(size_t)fill[(size_t)owner[i]]++] = all[i];
   };
-  std::vector<int2> i1, i2;
-  std::vector<int32_t> co1, co2;
-  deal(t1, s1, p1, i1, co1);
-  deal(t2, s2, p2, i2, co2);
-  TALLOC(T->it1, i1.size()); TALLOC(T->it2, i2.size());
-  TALLOC(T->co1, co1.size()); TALLOC(T->co2, co2.size());
-  TALLOC(T->rmap1, rowmap.size());
-#undef TALLOC
-  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: device buffers");
-  T->lw_bytes = lw_b; T->wr_bytes = wr_b; T->th_bytes = th_b; T->z_bytes = z_b;
-  T->n1 = (int64_t)t1.size() / TCT; T->ntiles1 = p1.back();
-  T->n2 = (int64_t)t2.size() / TCT; T->ntiles2 = p2.back();
-  T->n_lw = (int)(j_lw.size() / TCJ); T->n_wr = (int)(j_wr.size() / TCJ); T->n_th = (int)(j_th.size() / TCJ);
+  deal(t1, s1, p1, o.i1, o.co1);
+  deal(t2, s2, p2, o.i2, o.co2);
   // first piece of every pack job (field 9) and the pieces of each list
   const int kc = tc_is_tf32(prec) ? 4 : 8;
   auto pieces = [&](std::vector<int64_t>& j) {
@@ -390,31 +388,71 @@ int build(mrd_heff* h, int prec, TcCfg cfg) {
     }
     return n;
   };
-  T->pc_lw = pieces(j_lw); T->pc_wr = pieces(j_wr); T->pc_th = pieces(j_th);
+  o.pc_lw = pieces(j_lw);
+  o.pc_wr = pieces(j_wr);
+  o.pc_th = pieces(j_th);
+  return true;
+}
+
+// Device buffers of the tables in `o` (which must have been built for this H_eff): allocation,
+// upload and zeroed panels; replaces the H_eff's tensor-core state. Synchronises the stream.
+int upload(mrd_heff* h, const TcTables& o) {
+  mrd_ctx* ctx = h->ctx;
+  delete h->tc;
+  Tc* T = h->tc = new Tc();
+  T->prec = o.prec;
+  T->cfg = o.cfg;
+  Arena& A = T->mem;
+  A.stream = ctx->stream;
+  cudaError_t e = cudaSuccess;
+#define TALLOC(ptr, n) if (e == cudaSuccess) e = A.alloc(&(ptr), (size_t)std::max<int64_t>((n), 1))
+  TALLOC(T->lw, o.lw_b); TALLOC(T->wr, o.wr_b); TALLOC(T->th, o.th_b); TALLOC(T->z, o.z_b);
+  TALLOC(T->t1, o.t1.size()); TALLOC(T->s1, o.s1.size()); TALLOC(T->p1, o.p1.size());
+  TALLOC(T->t2, o.t2.size()); TALLOC(T->s2, o.s2.size()); TALLOC(T->p2, o.p2.size());
+  TALLOC(T->j_lw, o.j_lw.size()); TALLOC(T->j_wr, o.j_wr.size()); TALLOC(T->j_th, o.j_th.size());
+  TALLOC(T->err, 1);
+  TALLOC(T->pt1, o.q1.size()); TALLOC(T->pt2, o.q2.size());
+  TALLOC(T->it1, o.i1.size()); TALLOC(T->it2, o.i2.size());
+  TALLOC(T->co1, o.co1.size()); TALLOC(T->co2, o.co2.size());
+  TALLOC(T->rmap1, o.rowmap.size());
+#undef TALLOC
+  if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: device buffers");
+  T->lw_bytes = o.lw_b; T->wr_bytes = o.wr_b; T->th_bytes = o.th_b; T->z_bytes = o.z_b;
+  T->n1 = (int64_t)o.t1.size() / TCT; T->ntiles1 = o.p1.back();
+  T->n2 = (int64_t)o.t2.size() / TCT; T->ntiles2 = o.p2.back();
+  T->n_lw = (int)(o.j_lw.size() / TCJ); T->n_wr = (int)(o.j_wr.size() / TCJ); T->n_th = (int)(o.j_th.size() / TCJ);
+  T->pc_lw = o.pc_lw; T->pc_wr = o.pc_wr; T->pc_th = o.pc_th;
   cudaStream_t s = ctx->stream;
-  auto up = [&](int64_t* d, const std::vector<int64_t>& v) {
-    if (e == cudaSuccess && !v.empty()) e = cudaMemcpyAsync(d, v.data(), v.size() * 8, cudaMemcpyHostToDevice, s);
+  auto up = [&](void* d, const void* v, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, v, bytes, cudaMemcpyHostToDevice, s);
   };
-  up(T->t1, t1); up(T->s1, s1); up(T->p1, p1); up(T->t2, t2); up(T->s2, s2); up(T->p2, p2);
-  up(T->j_lw, j_lw); up(T->j_wr, j_wr); up(T->j_th, j_th);
-  up(T->pt1, q1); up(T->pt2, q2);
-  if (e == cudaSuccess && !i1.empty()) e = cudaMemcpyAsync(T->it1, i1.data(), i1.size() * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && !i2.empty()) e = cudaMemcpyAsync(T->it2, i2.data(), i2.size() * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(T->co1, co1.data(), co1.size() * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(T->co2, co2.data(), co2.size() * 4, cudaMemcpyHostToDevice, s);
-  up(T->rmap1, rowmap);
-  T->tiles1.resize(p1.size() - 1);
-  T->tiles2.resize(p2.size() - 1);
-  for (size_t t = 0; t < T->tiles1.size(); ++t) T->tiles1[t] = q1[2 * t + 1];
-  for (size_t t = 0; t < T->tiles2.size(); ++t) T->tiles2[t] = q2[2 * t + 1];
+  for (auto pr : {std::make_pair(T->t1, &o.t1), std::make_pair(T->s1, &o.s1), std::make_pair(T->p1, &o.p1),
+                  std::make_pair(T->t2, &o.t2), std::make_pair(T->s2, &o.s2), std::make_pair(T->p2, &o.p2),
+                  std::make_pair(T->j_lw, &o.j_lw), std::make_pair(T->j_wr, &o.j_wr), std::make_pair(T->j_th, &o.j_th),
+                  std::make_pair(T->pt1, &o.q1), std::make_pair(T->pt2, &o.q2), std::make_pair(T->rmap1, &o.rowmap)})
+    up(pr.first, pr.second->data(), pr.second->size() * 8);
+  up(T->it1, o.i1.data(), o.i1.size() * 8);
+  up(T->it2, o.i2.data(), o.i2.size() * 8);
+  up(T->co1, o.co1.data(), o.co1.size() * 4);
+  up(T->co2, o.co2.data(), o.co2.size() * 4);
+  T->tiles1.resize(o.p1.size() - 1);
+  T->tiles2.resize(o.p2.size() - 1);
+  for (size_t t = 0; t < T->tiles1.size(); ++t) T->tiles1[t] = o.q1[2 * t + 1];
+  for (size_t t = 0; t < T->tiles2.size(); ++t) T->tiles2[t] = o.q2[2 * t + 1];
   // zero padding everywhere (packing and the Z epilogue only write valid elements)
-  for (auto pr : {std::make_pair(T->lw, lw_b), std::make_pair(T->wr, wr_b), std::make_pair(T->th, th_b),
-                  std::make_pair(T->z, z_b)})
+  for (auto pr : {std::make_pair(T->lw, o.lw_b), std::make_pair(T->wr, o.wr_b), std::make_pair(T->th, o.th_b),
+                  std::make_pair(T->z, o.z_b)})
     if (e == cudaSuccess && pr.second) e = cudaMemsetAsync(pr.first, 0, (size_t)pr.second, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(T->err, 0, 4, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors leave scope
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host tables may be released after this
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "tc: upload");
   return MRD_OK;
+}
+
+int build(mrd_heff* h, int prec, TcCfg cfg) {
+  TcTables o;
+  if (!tables(h, prec, cfg, o)) return mrd_fail(h->ctx, MRD_E_STATE, o.err);
+  return upload(h, o);
 }
 
 }  // namespace
@@ -470,21 +508,93 @@ int time_cfg(mrd_heff* h, double* ms) {
 
 }  // namespace
 
+// Tables being built on a host thread for a known configuration (tc_prebuild).
+struct TcPre {
+  std::thread th;
+  TcTables tab;
+  bool ok = false;
+  ~TcPre() {
+    if (th.joinable()) th.join();
+  }
+};
+
+void tc_pre_free(TcPre* t) { delete t; }
+
+namespace {
+
+// The configuration a build of `prec` would use without timing anything: the default when
+// tuning is off, the tuned one when this problem class is in the context's cache; false when
+// it would have to be tuned.
+bool known_cfg(const mrd_heff* h, int prec, TcCfg* cfg) {
+  if (!h->autotune) {
+    *cfg = tc_default_cfg(prec);
+    return true;
+  }
+  auto it = h->ctx->tc_tuned.find(tune_key(h, prec));
+  if (it == h->ctx->tc_tuned.end()) return false;
+  *cfg = TcCfg{it->second[0], it->second[1], it->second[2]};
+  return true;
+}
+
+// Build for (prec, cfg), from the host thread's tables when it built exactly these (its thread
+// is joined and its tables released either way).
+int build_known(mrd_heff* h, int prec, TcCfg cfg) {
+  if (TcPre* pre = h->tc_pre) {
+    h->tc_pre = nullptr;
+    if (pre->th.joinable()) pre->th.join();
+    const TcTables& o = pre->tab;
+    const bool same = pre->ok && o.prec == prec && o.n_sm == h->n_sm && o.cfg.ntile == cfg.ntile &&
+                      o.cfg.stages == cfg.stages && o.cfg.order == cfg.order;
+    int rc = same ? upload(h, o) : MRD_OK;
+    delete pre;
+    if (same) return rc;
+  }
+  return build(h, prec, cfg);
+}
+
+}  // namespace
+
+// Starts building the tensor-core tables of `prec` on a host thread when their configuration
+// is known without timing (tuning off, or this problem class tuned earlier on the context),
+// so that the host work (milliseconds at large bond dimension) overlaps device work queued
+// meanwhile; the next tc_prepare joins it. Does nothing otherwise, or when the thread cannot be
+// started (tc_prepare then builds the tables itself). The host tables of h must not change
+// until the thread is joined (tc_prepare, or freeing h).
+void tc_prebuild(mrd_heff* h, int32_t prec) {
+  const int tp = tc_prec_of(h, prec);
+  TcCfg cfg{0, 0, 0};
+  if ((h->tc && h->tc->prec == tp) || h->tc_pre || !known_cfg(h, tp, &cfg)) return;
+  TcPre* pre = new (std::nothrow) TcPre();
+  if (!pre) return;
+  try {
+    pre->th = std::thread([h, pre, tp, cfg] {
+      try {
+        pre->ok = tables(h, tp, cfg, pre->tab);
+      } catch (...) {   // out of host memory: tc_prepare builds the tables itself
+        pre->ok = false;
+      }
+    });
+  } catch (...) {
+    delete pre;
+    return;
+  }
+  h->tc_pre = pre;
+}
+
 // Pick the tile configuration: from the context's tuning cache for this problem class, else
 // by timing every candidate on this H_eff (MRD_OPT_AUTOTUNE, default on), else the default.
 int autotune(mrd_heff* h, int prec) {
   mrd_ctx* ctx = h->ctx;
   const uint64_t key = tune_key(h, prec);
-  if (!h->autotune) {
-    int rc = build(h, prec, tc_default_cfg(prec));
-    if (rc == MRD_OK) h->tc->cfg_source = 0;
+  TcCfg known{0, 0, 0};
+  if (known_cfg(h, prec, &known)) {
+    int rc = build_known(h, prec, known);
+    if (rc == MRD_OK) h->tc->cfg_source = h->autotune ? 2 : 0;
     return rc;
   }
-  auto it = ctx->tc_tuned.find(key);
-  if (it != ctx->tc_tuned.end()) {
-    int rc = build(h, prec, TcCfg{it->second[0], it->second[1], it->second[2]});
-    if (rc == MRD_OK) h->tc->cfg_source = 2;
-    return rc;
+  if (h->tc_pre) {   // tables of another precision
+    tc_pre_free(h->tc_pre);
+    h->tc_pre = nullptr;
   }
   TcCfg best{0, 0, 0};
   double best_ms = 1e300;
