@@ -393,7 +393,7 @@ namespace {
 // tables are copied from pageable host memory (consumed when the copy call returns) into
 // device buffers that later calls reuse in stream order.
 int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const double2* Bop, int64_t blen, double2* C,
-             int64_t clen, const float4* a_ff = nullptr, const float4* b_ff = nullptr) {
+             int64_t clen, const float4* a_ff = nullptr, const float4* b_ff = nullptr, float4* c_ff = nullptr) {
   mrd_ctx* ctx = D->ctx;
   g.drop_empty_last();
   const int64_t nt = (int64_t)g.t.size() / TF;
@@ -446,8 +446,8 @@ int run_gemm(mrd_dmrg* D, GemmList& g, const double2* Aop, int64_t alen, const d
     // a real state (MRD_DMRG_OPT_REAL): every operand is real, one float-float product per
     // multiply-add instead of three
     auto gemm = D->real ? launch_rgemm_ff_packed : launch_cgemm_ff_packed;
-    MRD_CUDA(ctx, gemm(a_ff, b_ff, nullptr, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
-                       nt, pref[nt], D->n_sm, s, it));
+    MRD_CUDA(ctx, gemm(a_ff, b_ff, c_ff, c_ff ? nullptr : C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(),
+                       D->gpref.as<int64_t>(), nt, pref[nt], D->n_sm, s, it));
   } else {
     MRD_CUDA(ctx, launch_cgemm_fp64(Aop, Bop, C, D->gtask.as<int64_t>(), D->gseg.as<int64_t>(), D->gpref.as<int64_t>(),
                                     nt, pref[nt], D->n_sm, s));
@@ -922,8 +922,10 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
       }
     }
   MRD_CUDA(ctx, D->tbuf.need((size_t)std::max<int64_t>(tlen, 1) * 16));
+  // with float-float GEMMs T stays in float-float (the same 16 bytes per element) for step 2
+  float4* t_ff = D->gemm_ff ? D->tbuf.as<float4>() : nullptr;
   int rc = run_gemm(D, g1, h->lw, h->counts[C_LWLEN], A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen,
-                    heff_ff_lw(h));
+                    heff_ff_lw(h), nullptr, t_ff);
   if (rc != MRD_OK) return rc;
   // step 2: L'(w', c) = sum_s' A(a', s' -> c')^+ T(w', c, s')
   EnvT& E = D->L[i + 1];
@@ -953,7 +955,8 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
         g2.seg(ao, ald, it->second.off, cs[c].d, ls[ap].d, 1);
       }
     }
-  rc = run_gemm(D, g2, A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen, eout.as<double2>(), E.size);
+  rc = run_gemm(D, g2, A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen, eout.as<double2>(), E.size, nullptr,
+                t_ff);
   if (rc != MRD_OK) return rc;
   return env_store(D, E, eout.as<double2>());
 }
@@ -1001,8 +1004,9 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
       }
     }
   MRD_CUDA(ctx, D->tbuf.need((size_t)std::max<int64_t>(tlen, 1) * 16));
+  float4* t_ff = D->gemm_ff ? D->tbuf.as<float4>() : nullptr;   // T in float-float for step 2
   int rc = run_gemm(D, g1, B.data.as<double2>(), B.size, h->wr, h->counts[C_WRLEN], D->tbuf.as<double2>(), tlen,
-                    nullptr, heff_ff_wr(h));
+                    nullptr, heff_ff_wr(h), t_ff);
   if (rc != MRD_OK) return rc;
   EnvT& E = D->R[i + 1];
   E.sec = cs;
@@ -1030,7 +1034,7 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
         g2.seg(it->second.off, it->second.cols, bo, bld, bs[bp].d, 2);
       }
     }
-  rc = run_gemm(D, g2, D->tbuf.as<double2>(), tlen, B.data.as<double2>(), B.size, eout.as<double2>(), E.size);
+  rc = run_gemm(D, g2, D->tbuf.as<double2>(), tlen, B.data.as<double2>(), B.size, eout.as<double2>(), E.size, t_ff);
   if (rc != MRD_OK) return rc;
   return env_store(D, E, eout.as<double2>());
 }

@@ -24,33 +24,38 @@ namespace {
 constexpr int kTile = 32;
 
 __device__ int64_t block_scan(int64_t* v, int64_t n, int64_t* smem) {
-  // exclusive prefix sum in place over v[0..n); returns the total. All threads call it.
-  const int tid = threadIdx.x, nt = blockDim.x;
+  // exclusive prefix sum in place over v[0..n); returns the total. All threads call it; the
+  // CTA has a multiple of 32 threads, at most 1024. Each thread sums a contiguous chunk; the
+  // chunk sums are scanned by shuffles within each warp and then over the warps' totals.
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int64_t chunk = (n + nt - 1) / nt;
   const int64_t b = tid * chunk;
   const int64_t e = b + chunk < n ? b + chunk : n;
   int64_t s = 0;
   for (int64_t i = b; i < e; ++i) s += v[i];
-  smem[tid] = s;
+  int64_t x = s;   // inclusive prefix of the chunk sums within the warp
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem[wid] = x;
   __syncthreads();
-  if (tid == 0) {
-    int64_t acc = 0;
-    for (int i = 0; i < nt; ++i) {
-      int64_t x = smem[i];
-      smem[i] = acc;
-      acc += x;
+  if (wid == 0) {   // inclusive prefix of the warps' totals
+    int64_t t = lane < nw ? smem[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
     }
-    smem[nt] = acc;
+    smem[32 + lane] = t;
   }
   __syncthreads();
-  int64_t acc = smem[tid];
+  int64_t acc = (wid > 0 ? smem[32 + wid - 1] : 0) + x - s;
+  const int64_t total = smem[32 + nw - 1];
   for (int64_t i = b; i < e; ++i) {
-    int64_t x = v[i];
+    const int64_t y = v[i];
     v[i] = acc;
-    acc += x;
+    acc += y;
   }
-  __syncthreads();
-  int64_t total = smem[nt];
   __syncthreads();
   return total;
 }
@@ -82,12 +87,28 @@ __device__ int find_mid(const int64_t* mid, int n, int N, int K) {
   return -1;
 }
 
+// Binary search of a key in a sorted key array; -1 if absent.
+__device__ int find_key(const int64_t* keys, int n, int64_t key) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    const int m = (lo + hi) >> 1;
+    const int64_t k = keys[m];
+    if (k == key) return m;
+    if (k < key) lo = m + 1; else hi = m - 1;
+  }
+  return -1;
+}
+
+// middle-sector keys kept in shared memory for the lookups of steps 5 and 7 (global otherwise)
+constexpr int kMidKeys = 2048;
+
 __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace
 
 __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
   __shared__ int64_t smem[1025];
+  __shared__ int64_t mkey[kMidKeys];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int M = d.mod;
   const int32_t *L = p.left, *Rs = p.right;
@@ -144,28 +165,33 @@ __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
   __syncthreads();
 
   // ---- P2: fused middle sectors
+  // candidate i = (a, s1) carries the charge q_a + q1(s1); the distinct charges, in increasing
+  // order, are the middle sectors. A candidate that is the first of its charge gets the number
+  // of distinct smaller charges as its slot, the others -1. The keys and first-occurrence flags
+  // are staged in p.mid, whose rows are written only after this.
   const int ncand = 2 * d.n_l;
+  int64_t* ckey = p.mid;
+  int64_t* cfirst = p.mid + ncand;
   for (int i = tid; i < ncand; i += nt) {
-    int a = i >> 1, s1 = i & 1;
-    int N = L[3 * a] + s1, K = kmod(L[3 * a + 1] + s1 * d.m1, M);
-    int64_t key = qkey(N, K);
-    bool first = true;
-    int rank = 0;
-    for (int j = 0; j < ncand; ++j) {
-      int b = j >> 1, t1 = j & 1;
-      int64_t kj = qkey(L[3 * b] + t1, kmod(L[3 * b + 1] + t1 * d.m1, M));
-      if (kj == key && j < i) first = false;
-      // count distinct smaller keys: j must be the first occurrence of its key
-      if (kj < key) {
-        bool jfirst = true;
-        for (int q = 0; q < j; ++q) {
-          int c = q >> 1, t2 = q & 1;
-          if (qkey(L[3 * c] + t2, kmod(L[3 * c + 1] + t2 * d.m1, M)) == kj) { jfirst = false; break; }
-        }
-        rank += jfirst;
-      }
+    const int a = i >> 1, s1 = i & 1;
+    ckey[i] = qkey(L[3 * a] + s1, kmod(L[3 * a + 1] + s1 * d.m1, M));
+  }
+  __syncthreads();
+  for (int i = tid; i < ncand; i += nt) {
+    const int64_t key = ckey[i];
+    int64_t first = 1;
+    for (int j = 0; j < i && first; ++j) first = ckey[j] != key;
+    cfirst[i] = first;
+  }
+  __syncthreads();
+  for (int i = tid; i < ncand; i += nt) {
+    int64_t slot = -1;
+    if (cfirst[i]) {
+      const int64_t key = ckey[i];
+      slot = 0;
+      for (int j = 0; j < ncand; ++j) slot += cfirst[j] && ckey[j] < key;
     }
-    p.scr_a[i] = first ? rank : -1;
+    p.scr_a[i] = slot;
   }
   __syncthreads();
   // candidate slot -> sector data (in scr_b, MIDF per slot; valid flag in scr_a reused)
@@ -198,19 +224,26 @@ __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
     p.scr_a[i] = keep ? p.scr_b[i] : -1;
   }
   __syncthreads();
-  if (tid == 0) {  // ordered in-place compaction (destination index never exceeds source)
-    for (int64_t i = 0; i < ndist; ++i) {
-      int64_t dst = p.scr_a[i];
-      if (dst < 0 || dst == i) continue;
-      for (int f = 0; f < MIDF; ++f) p.mid[MIDF * dst + f] = p.mid[MIDF * i + f];
-    }
+  // compaction through a staging copy in p.t1 (12 x its capacity of middle sectors, written
+  // only in step 6)
+  for (int64_t q = tid; q < ndist * MIDF; q += nt) {
+    const int64_t dst = p.scr_a[q / MIDF];
+    if (dst >= 0) p.t1[MIDF * dst + q % MIDF] = p.mid[q];
   }
+  __syncthreads();
+  for (int64_t q = tid; q < nmid * MIDF; q += nt) p.mid[q] = p.t1[q];
   __syncthreads();
   for (int i = tid; i < nmid; i += nt) p.scr_b[i] = p.mid[MIDF * i + 2] * p.mid[MIDF * i + 3];
   __syncthreads();
   const int64_t theta_len = block_scan(p.scr_b, nmid, smem);
   for (int i = tid; i < nmid; i += nt) p.mid[MIDF * i + 4] = p.scr_b[i];
+  const bool mkey_ok = nmid <= kMidKeys;
+  if (mkey_ok)
+    for (int i = tid; i < nmid; i += nt) mkey[i] = qkey((int32_t)p.mid[MIDF * i], (int32_t)p.mid[MIDF * i + 1]);
   __syncthreads();
+  auto mid_of = [&](int N, int K) {
+    return mkey_ok ? find_key(mkey, (int)nmid, qkey(N, K)) : find_mid(p.mid, (int)nmid, N, K);
+  };
 
   // ---- P3: environment layouts
   for (int64_t i = tid; i < (int64_t)d.d_l * d.n_l; i += nt) {
@@ -307,7 +340,7 @@ __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
   for (int64_t i = tid; i < n_z_items; i += nt) {
     int wp = (int)(i / nmid), mi = (int)(i % nmid);
     const int64_t* min_ = p.mid + MIDF * mi;
-    int mo = find_mid(p.mid, (int)nmid, (int)min_[0] + p.cm[2 * wp], kmod((int)min_[1] + p.cm[2 * wp + 1], M));
+    int mo = mid_of((int)min_[0] + p.cm[2 * wp], kmod((int)min_[1] + p.cm[2 * wp + 1], M));
     int mask = 0;
     if (mo >= 0) {
       const int64_t* mout = p.mid + MIDF * mo;
@@ -403,7 +436,7 @@ __global__ void __launch_bounds__(1024) k_plan(PlanDims d, PlanPtrs p) {
       task[2] = mout[4] + rowoff_out * mout[3] + coloff_out;
       task[3] = mout[3];
       for (int wp = 0; wp < d.d_m; ++wp) {
-        int mi = find_mid(p.mid, (int)nmid, (int)mout[0] - p.cm[2 * wp], kmod((int)mout[1] - p.cm[2 * wp + 1], M));
+        int mi = mid_of((int)mout[0] - p.cm[2 * wp], kmod((int)mout[1] - p.cm[2 * wp + 1], M));
         if (mi < 0) continue;
         int64_t zi = (int64_t)wp * nmid + mi;
         int64_t zid = p.zmap[zi];

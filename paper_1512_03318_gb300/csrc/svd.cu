@@ -495,13 +495,24 @@ __global__ void k_svd_v_from_f32(double2* __restrict__ work, const float2* __res
     V[e] = make_double2((double)V32[e].x, (double)V32[e].y);
 }
 
+// Ordering key of a non-negative double: its bit pattern, which orders like the value (the sign
+// bit is cleared, so -0 and +0 are equal). Integer compares run on the integer pipe, where FP64
+// compares would share the GPU's few FP64 units; keys with ties broken by index also give a
+// strict total order, so ranks are a permutation whatever the values.
+__device__ __forceinline__ long long order_key(double v) {
+  return __double_as_longlong(v) & 0x7fffffffffffffffll;
+}
+
 // Per block: singular values (column norms of X) sorted descending (ties by column index),
 // and the orthonormal factor of the block's side: side 0 (X = M): U (m x r, row-major) with
 // column k = X column ord[k] / sigma; side 1 (X = M^+): V^+ (r x n, row-major) with row k =
-// conj(X column ord[k]) / sigma. Columns with sigma = 0 are written as zero.
+// conj(X column ord[k]) / sigma. Columns with sigma = 0 are written as zero. S holds the values
+// in column order, S_sorted in decreasing order, zero-padded to the block's slot length; the
+// reciprocals 1 / sigma are staged in S_sorted while the vectors are written.
 __global__ void k_svd_finish(const double2* __restrict__ work, const int64_t* __restrict__ blk, int nblk,
                              double2* __restrict__ U, double2* __restrict__ Vh, double* __restrict__ S,
-                             int* __restrict__ order_scratch, const double* __restrict__ fro2) {
+                             double* __restrict__ S_sorted, int* __restrict__ order_scratch,
+                             const double* __restrict__ fro2) {
   const int b = blockIdx.x;
   if (b >= nblk) return;
   const int64_t* d = blk + SVF * b;
@@ -509,6 +520,7 @@ __global__ void k_svd_finish(const double2* __restrict__ work, const int64_t* __
   const bool wide = d[9] != 0;
   const double2* X = work + d[4];
   double* s = S + d[8];
+  double* so = S_sorted + d[8];
   int* ord = order_scratch + d[8];
   for (int64_t j = threadIdx.x; j < r; j += blockDim.x) {
     double acc = 0.0;
@@ -520,39 +532,42 @@ __global__ void k_svd_finish(const double2* __restrict__ work, const int64_t* __
   }
   __syncthreads();
   for (int64_t j = threadIdx.x; j < r; j += blockDim.x) {
-    const double v = s[j];
+    const long long v = order_key(s[j]);
     int rank = 0;
     for (int64_t k = 0; k < r; ++k) {
-      const double w = s[k];
+      const long long w = order_key(s[k]);
       rank += (w > v) || (w == v && k < j);
     }
     ord[rank] = (int)j;
+  }
+  __syncthreads();
+  for (int64_t kk = threadIdx.x; kk < r; kk += blockDim.x) {
+    const double sig = s[ord[kk]];
+    so[kk] = sig > 0 ? 1.0 / sig : 0.0;
   }
   __syncthreads();
   if (!wide) {
     double2* u = U + d[6];
     for (int64_t e = threadIdx.x; e < m * r; e += blockDim.x) {
       const int64_t row = e / r, kk = e % r;
-      const int j = ord[kk];
-      const double sig = s[j];
-      const double2 x = X[(int64_t)j * p + row];
-      const double inv = sig > 0 ? 1.0 / sig : 0.0;
+      const double2 x = X[(int64_t)ord[kk] * p + row];
+      const double inv = so[kk];
       u[row * r + kk] = make_double2(x.x * inv, x.y * inv);
     }
   } else {
     double2* vh = Vh + d[7];
     for (int64_t e = threadIdx.x; e < r * n; e += blockDim.x) {
       const int64_t kk = e / n, col = e % n;
-      const int j = ord[kk];
-      const double sig = s[j];
-      const double2 x = X[(int64_t)j * p + col];
-      const double inv = sig > 0 ? 1.0 / sig : 0.0;
+      const double2 x = X[(int64_t)ord[kk] * p + col];
+      const double inv = so[kk];
       vh[kk * n + col] = make_double2(x.x * inv, -x.y * inv);
     }
   }
+  __syncthreads();
+  for (int64_t kk = threadIdx.x; kk < r; kk += blockDim.x) so[kk] = s[ord[kk]];
+  for (int64_t j = r + threadIdx.x; j < d[12]; j += blockDim.x) so[j] = 0.0;
 }
 
-// Values are sorted in place after the vectors were written.
 // Phase convention of the orthonormal factor (the singular vectors are fixed only up to a phase
 // each): every column of U (side 0) or row of V^+ (side 1) is multiplied by the conjugate phase
 // of its entry of largest modulus (the first such entry), which makes that entry real and
@@ -581,26 +596,6 @@ __global__ void k_svd_fix_phases(double2* __restrict__ U, double2* __restrict__ 
       v[i * stride] = make_double2(x.x * pr - x.y * pi, x.x * pi + x.y * pr);
     }
   }
-}
-
-__global__ void k_svd_sort_values(const int64_t* __restrict__ blk, int nblk, double* __restrict__ S,
-                                  double* __restrict__ S_sorted) {
-  const int b = blockIdx.x;
-  if (b >= nblk) return;
-  const int64_t* d = blk + SVF * b;
-  const int64_t r = d[3];
-  const double* s = S + d[8];
-  double* o = S_sorted + d[8];
-  for (int64_t j = threadIdx.x; j < r; j += blockDim.x) {
-    const double v = s[j];
-    int rank = 0;
-    for (int64_t k = 0; k < r; ++k) {
-      const double w = s[k];
-      rank += (w > v) || (w == v && k < j);
-    }
-    o[rank] = v;
-  }
-  for (int64_t j = r + threadIdx.x; j < d[12]; j += blockDim.x) o[j] = 0.0;
 }
 
 // Squared norms of the columns of X (FP64, field 4) of every block, one warp per column:
@@ -653,40 +648,65 @@ __global__ void k_trunc_prep(const int64_t* __restrict__ blk, int nblk, const do
   }
 }
 
-constexpr int kRankTile = 256;
+constexpr int kRankTile = 256;    // threads of a rank CTA, and values staged per tile
+constexpr int kRankPerWarp = 4;   // values ranked by each warp
+constexpr int kRankPerCta = kRankTile / 32 * kRankPerWarp;
 
-// rank of every value among all values (one thread per value, values staged through shared
-// memory in tiles); a value of rank < chi above the cutoff is kept
+// Rank of every value among all values (ties: lower block, then lower position first); a value
+// of rank < chi above the cutoff is kept. Each warp ranks kRankPerWarp values: the CTA stages
+// the values' order keys and blocks through shared memory in tiles, each lane compares its
+// warp's values with every 32nd staged entry, and the lanes' counts are summed by shuffles, so
+// the all-pairs comparison is spread over the whole GPU.
 __global__ void __launch_bounds__(kRankTile) k_trunc_rank(const double* __restrict__ S_sorted, int64_t total, int chi,
                                                           double cutoff, int* __restrict__ keep,
                                                           const double* __restrict__ info,
                                                           const int* __restrict__ flat_block) {
-  __shared__ double sv[kRankTile];
+  __shared__ long long sv[kRankTile];
   __shared__ int sb[kRankTile];
-  const int64_t e = blockIdx.x * (int64_t)kRankTile + threadIdx.x;
-  const bool live = e < total;
-  const double v = live ? S_sorted[e] : 0.0;
-  const int be = live ? flat_block[e] : 0;
-  const double smax = __longlong_as_double((long long)__double_as_longlong(info[3]));
-  int64_t rank = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e0 = blockIdx.x * (int64_t)kRankPerCta + warp * kRankPerWarp;
+  long long v[kRankPerWarp];
+  int be[kRankPerWarp], cnt[kRankPerWarp];
+#pragma unroll
+  for (int u = 0; u < kRankPerWarp; ++u) {
+    const bool live = e0 + u < total;
+    v[u] = order_key(live ? S_sorted[e0 + u] : 0.0);
+    be[u] = live ? flat_block[e0 + u] : 0;
+    cnt[u] = 0;
+  }
   for (int64_t f0 = 0; f0 < total; f0 += kRankTile) {
     const int64_t f = f0 + threadIdx.x;
     __syncthreads();
     if (f < total) {
-      sv[threadIdx.x] = S_sorted[f];
+      sv[threadIdx.x] = order_key(S_sorted[f]);
       sb[threadIdx.x] = flat_block[f];
     }
     __syncthreads();
     const int n = total - f0 < kRankTile ? (int)(total - f0) : kRankTile;
-    if (live && rank < chi) {
-      for (int q = 0; q < n; ++q) {
-        const double w = sv[q];
-        const int bf = sb[q];
-        rank += (w > v) || (w == v && (bf < be || (bf == be && f0 + q < e)));
-      }
+    for (int q = lane; q < n; q += 32) {
+      const long long w = sv[q];
+      const int bf = sb[q];
+      const int64_t fq = f0 + q;
+#pragma unroll
+      for (int u = 0; u < kRankPerWarp; ++u)
+        cnt[u] += (w > v[u]) || (w == v[u] && (bf < be[u] || (bf == be[u] && fq < e0 + u)));
     }
   }
-  if (live && rank < chi && v > cutoff * smax) atomicAdd(&keep[be], 1);
+#pragma unroll
+  for (int u = 0; u < kRankPerWarp; ++u)
+    for (int o = 16; o > 0; o >>= 1) cnt[u] += __shfl_xor_sync(0xffffffffu, cnt[u], o);
+  if (lane < kRankPerWarp) {
+    int rank = cnt[0], b = be[0];
+    const int64_t e = e0 + lane;
+#pragma unroll
+    for (int u = 1; u < kRankPerWarp; ++u)
+      if (lane == u) { rank = cnt[u]; b = be[u]; }
+    if (e < total) {
+      const double x = S_sorted[e];
+      const double smax = __longlong_as_double((long long)__double_as_longlong(info[3]));
+      if (rank < chi && x > cutoff * smax) atomicAdd(&keep[b], 1);
+    }
+  }
 }
 
 // kept and total weight with a fixed reduction order (one CTA of 1024 threads)
@@ -824,9 +844,7 @@ cudaError_t svd_v_from_f32(double2* work, const float2* w32, const int64_t* blk,
 cudaError_t svd_finish(const double2* work, const int64_t* blk, int nblk, double2* U, double2* Vh, double* S,
                        double* S_sorted, int* order_scratch, const double* fro2, cudaStream_t s) {
   if (nblk == 0) return cudaSuccess;
-  k_svd_finish<<<nblk, 256, 0, s>>>(work, blk, nblk, U, Vh, S, order_scratch, fro2);
-  mrd::count_launch();
-  k_svd_sort_values<<<nblk, 256, 0, s>>>(blk, nblk, S, S_sorted);
+  k_svd_finish<<<nblk, 256, 0, s>>>(work, blk, nblk, U, Vh, S, S_sorted, order_scratch, fro2);
   mrd::count_launch();
   return cudaGetLastError();
 }
@@ -863,7 +881,7 @@ cudaError_t svd_truncate(const int64_t* blk, int nblk, const double* S_sorted, i
   k_trunc_prep<<<nblk, 256, 0, s>>>(blk, nblk, S_sorted, keep, info, flat_block);
   mrd::count_launch();
   if (total > 0) {
-    k_trunc_rank<<<(unsigned)((total + kRankTile - 1) / kRankTile), kRankTile, 0, s>>>(S_sorted, total, chi, cutoff,
+    k_trunc_rank<<<(unsigned)((total + kRankPerCta - 1) / kRankPerCta), kRankTile, 0, s>>>(S_sorted, total, chi, cutoff,
                                                                                      keep, info, flat_block);
     mrd::count_launch();
   }
