@@ -54,6 +54,9 @@ extern "C" {
 #define MRD_E_NAN (-6)      /* a non-finite value was produced                            */
 #define MRD_E_TIMEOUT (-7)  /* a bounded device wait gave up                              */
 #define MRD_E_STATE (-8)    /* call out of order (e.g. apply before set_env)              */
+#define MRD_E_HOST (-9)     /* host memory or threads exhausted (no C++ exception leaves  */
+                            /* the library; the handles of the failed call may be stale:  */
+                            /* destroy them)                                              */
 
 #define MRD_PREC_FP64 0     /* complex128 operands, FP64 arithmetic                       */
 #define MRD_PREC_TF32 1     /* tcgen05 tensor cores, TF32 operands, FP32 accumulation     */

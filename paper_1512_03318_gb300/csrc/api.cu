@@ -73,7 +73,7 @@ int mrd_version(void) { return 100; }
 
 int64_t mrd_launch_count(void) { return mrd::g_launches.load(); }
 
-int mrd_create(mrd_ctx** out, int device, void* stream) {
+int mrd_create(mrd_ctx** out, int device, void* stream) try {
   if (!out) return MRD_E_ARG;
   *out = nullptr;
   int n = 0;
@@ -83,34 +83,42 @@ int mrd_create(mrd_ctx** out, int device, void* stream) {
   c->stream = (cudaStream_t)stream;
   *out = c;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_destroy(mrd_ctx* ctx) {
+int mrd_destroy(mrd_ctx* ctx) try {
   if (!ctx) return MRD_OK;
   ctx->destroyed = true;
   if (ctx->refs == 0) delete ctx;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_release_cached(mrd_ctx* ctx) {
+int mrd_release_cached(mrd_ctx* ctx) try {
   if (!ctx) return MRD_E_ARG;
   Guard g(ctx->device);
   MRD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   mrd::cache_trim(ctx->device);
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_set_stream(mrd_ctx* ctx, void* stream) {
+int mrd_set_stream(mrd_ctx* ctx, void* stream) try {
   if (!ctx) return MRD_E_ARG;
   ctx->stream = (cudaStream_t)stream;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 const char* mrd_last_error(const mrd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 // ------------------------------------------------------------------ MPO
 
-int mrd_mpo_build(mrd_ctx* ctx, const mrd_model* model, mrd_mpo** out) {
+int mrd_mpo_build(mrd_ctx* ctx, const mrd_model* model, mrd_mpo** out) try {
   // host-only: ctx may be NULL (then no message is recorded)
   if (!model || !out) return mrd_fail(ctx, MRD_E_ARG, "mrd_mpo_build: null argument");
   *out = nullptr;
@@ -124,29 +132,37 @@ int mrd_mpo_build(mrd_ctx* ctx, const mrd_model* model, mrd_mpo** out) {
   }
   *out = m;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_mpo_free(mrd_mpo* mpo) {
+int mrd_mpo_free(mrd_mpo* mpo) try {
   delete mpo;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_mpo_info(const mrd_mpo* mpo, int32_t* n_sites, int32_t* modulus) {
+int mrd_mpo_info(const mrd_mpo* mpo, int32_t* n_sites, int32_t* modulus) try {
   if (!mpo) return MRD_E_ARG;
   if (n_sites) *n_sites = mpo->h.n_sites;
   if (modulus) *modulus = mpo->h.modulus;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_mpo_bond(const mrd_mpo* mpo, int32_t bond, int32_t* dim, int32_t* charges) {
+int mrd_mpo_bond(const mrd_mpo* mpo, int32_t bond, int32_t* dim, int32_t* charges) try {
   if (!mpo || !dim || bond < 0 || bond > mpo->h.n_sites) return MRD_E_ARG;
   const auto& c = mpo->h.bond_charges[bond];
   *dim = (int32_t)(c.size() / 2);
   if (charges) std::memcpy(charges, c.data(), c.size() * sizeof(int32_t));
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_mpo_site(const mrd_mpo* mpo, int32_t site, int32_t* nnz, int32_t* idx, double* val) {
+int mrd_mpo_site(const mrd_mpo* mpo, int32_t site, int32_t* nnz, int32_t* idx, double* val) try {
   if (!mpo || !nnz || site < 0 || site >= mpo->h.n_sites) return MRD_E_ARG;
   const auto& i = mpo->h.site_idx[site];
   const auto& v = mpo->h.site_val[site];
@@ -154,9 +170,11 @@ int mrd_mpo_site(const mrd_mpo* mpo, int32_t site, int32_t* nnz, int32_t* idx, d
   if (idx) std::memcpy(idx, i.data(), i.size() * sizeof(int32_t));
   if (val) std::memcpy(val, v.data(), v.size() * sizeof(double));
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_mpo_stats(const mrd_mpo* mpo, int32_t first, int32_t count, double* out4) {
+int mrd_mpo_stats(const mrd_mpo* mpo, int32_t first, int32_t count, double* out4) try {
   if (!mpo || !out4 || first < 0 || count < 1 || first > mpo->h.n_sites - count) return MRD_E_ARG;
   double dsum = 0.0, fsum = 0.0, nnz = 0.0;
   int64_t dmax = 0;
@@ -173,6 +191,8 @@ int mrd_mpo_stats(const mrd_mpo* mpo, int32_t first, int32_t count, double* out4
   out4[2] = fsum / count;
   out4[3] = nnz;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 // ------------------------------------------------------------------ H_eff
@@ -208,7 +228,7 @@ static int validate_entries(mrd_ctx* ctx, const int32_t* idx, const double* val,
   return MRD_OK;
 }
 
-int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
+int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) try {
   if (!ctx || !desc || !out) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_create: null argument");
   *out = nullptr;
   const mrd_heff_desc& D = *desc;
@@ -380,9 +400,11 @@ int mrd_heff_create(mrd_ctx* ctx, const mrd_heff_desc* desc, mrd_heff** out) {
   }
   *out = h;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_free(mrd_heff* h) {
+int mrd_heff_free(mrd_heff* h) try {
   if (!h) return MRD_OK;
   mrd_ctx* ctx = h->ctx;
   {
@@ -392,17 +414,21 @@ int mrd_heff_free(mrd_heff* h) {
   }
   mrd_ctx_release(ctx);
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_sizes(const mrd_heff* h, int64_t* theta_len, int64_t* lenv_len, int64_t* renv_len) {
+int mrd_heff_sizes(const mrd_heff* h, int64_t* theta_len, int64_t* lenv_len, int64_t* renv_len) try {
   if (!h) return MRD_E_ARG;
   if (theta_len) *theta_len = h->counts[C_THETA];
   if (lenv_len) *lenv_len = h->counts[C_LENV];
   if (renv_len) *renv_len = h->counts[C_RENV];
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev) {
+int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev) try {
   if (!h) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   if ((!lenv_dev && h->counts[C_LENV] > 0) || (!renv_dev && h->counts[C_RENV] > 0))
@@ -418,6 +444,8 @@ int mrd_heff_set_env(mrd_heff* h, const double* lenv_dev, const double* renv_dev
   tc_env_changed(h);
   h->ff_dirty = true;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 // Per-task launch tables of the FP64 / float-float GEMM steps (32 x 32 tiles).
@@ -501,7 +529,7 @@ static int heff_prepare(mrd_heff* h, int32_t prec) {
   return MRD_OK;
 }
 
-int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev, int32_t prec) {
+int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev, int32_t prec) try {
   if (!h) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   if (!h->env_loaded) return mrd_fail(ctx, MRD_E_STATE, "mrd_heff_apply: environments not loaded");
@@ -572,6 +600,8 @@ int mrd_heff_apply(mrd_heff* h, const double* theta_in_dev, double* theta_out_de
   if (e == cudaSuccess && e2) e = record_event(e2, s, cap);
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply");
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 // Flops of one application in the order of the definition (L, then W_i W_{i+1}, then R, as
@@ -631,7 +661,7 @@ static double definition_flops(const mrd_heff* h) {
   return fl;
 }
 
-int mrd_heff_flops(const mrd_heff* h, double* flops4) {
+int mrd_heff_flops(const mrd_heff* h, double* flops4) try {
   if (!h || !flops4) return MRD_E_ARG;
   if (!h->def_flops_done) {
     h->def_flops = definition_flops(h);
@@ -642,6 +672,8 @@ int mrd_heff_flops(const mrd_heff* h, double* flops4) {
   flops4[2] = (double)h->counts[C_FLOPS1];
   flops4[3] = (double)h->counts[C_FLOPS2];
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 struct ApplyArg {
@@ -674,7 +706,7 @@ static int ensure_lanczos(mrd_heff* h) {
 }
 
 int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, int32_t prec, double* energy,
-                int32_t* iters) {
+                int32_t* iters) try {
   if (!h || !energy || !iters) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   if (!h->env_loaded) return mrd_fail(ctx, MRD_E_STATE, "mrd_lanczos: environments not loaded");
@@ -703,9 +735,11 @@ int mrd_lanczos(mrd_heff* h, double* theta_dev, int32_t max_iter, double tol, in
   *iters = it;
   if (rc == MRD_OK && (prec == MRD_PREC_TF32 || prec == MRD_PREC_BF16X3)) rc = tc_status(h);
   return rc;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double* energy, double* residual) {
+int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double* energy, double* residual) try {
   if (!h || !energy) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   if (!theta_dev || h->counts[C_THETA] == 0) return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_rayleigh: empty theta");
@@ -730,9 +764,11 @@ int mrd_heff_rayleigh(mrd_heff* h, const double* theta_dev, int32_t prec, double
     *residual = std::sqrt(r2 > 0 ? r2 : 0.0) / std::sqrt(nn);
   }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) {
+int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) try {
   if (!h) return MRD_E_ARG;
   if (option == MRD_OPT_GRAPH) {
     h->use_graph = value != 0;
@@ -761,27 +797,35 @@ int mrd_heff_set_option(mrd_heff* h, int32_t option, int64_t value) {
     return mrd_fail(h->ctx, MRD_E_ARG, "mrd_heff_set_option: unknown option");
   }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_status(mrd_heff* h) {
+int mrd_heff_status(mrd_heff* h) try {
   if (!h) return MRD_E_ARG;
   Guard g(h->ctx->device);
   MRD_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
   return tc_status(h);
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_tc_config(const mrd_heff* h, int32_t* cfg4) {
+int mrd_heff_tc_config(const mrd_heff* h, int32_t* cfg4) try {
   if (!h || !cfg4) return MRD_E_ARG;
   return tc_config(h, cfg4);
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_timing(mrd_heff* h, int32_t on) {
+int mrd_heff_timing(mrd_heff* h, int32_t on) try {
   if (!h) return MRD_E_ARG;
   h->timing = on != 0;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls) {
+int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int32_t* n_calls) try {
   if (!h) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   Guard g(ctx->device);
@@ -806,9 +850,11 @@ int mrd_heff_timing_collect(mrd_heff* h, double* ms_step1, double* ms_step2, int
   if (ms_step2) *ms_step2 = b;
   if (n_calls) *n_calls = calls;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_heff_table(const mrd_heff* h, int32_t which, int64_t* rows, int64_t* count) {
+int mrd_heff_table(const mrd_heff* h, int32_t which, int64_t* rows, int64_t* count) try {
   if (!h || !count) return MRD_E_ARG;
   mrd_ctx* ctx = h->ctx;
   Guard g(ctx->device);
@@ -854,6 +900,8 @@ int mrd_heff_table(const mrd_heff* h, int32_t which, int64_t* rows, int64_t* cou
     return MRD_OK;
   }
   return mrd_fail(ctx, MRD_E_ARG, "mrd_heff_table: unknown table");
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 }  // extern "C"

@@ -1126,7 +1126,7 @@ int canonicalise_and_build_envs(mrd_dmrg* D, int center) {
 extern "C" {
 
 int mrd_dmrg_create(mrd_ctx* ctx, const mrd_mpo* mpo, int32_t n_part, int32_t k_tot, int32_t chi, uint64_t seed,
-                    int32_t center, const int32_t* caps, const int64_t* caps_off, mrd_dmrg** out) {
+                    int32_t center, const int32_t* caps, const int64_t* caps_off, mrd_dmrg** out) try {
   if (!ctx || !mpo || !out || chi < 1) return mrd_fail(ctx, MRD_E_ARG, "mrd_dmrg_create: bad argument");
   *out = nullptr;
   const HostMPO& H = mpo->h;
@@ -1254,9 +1254,11 @@ int mrd_dmrg_create(mrd_ctx* ctx, const mrd_mpo* mpo, int32_t n_part, int32_t k_
   }
   *out = D;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_free(mrd_dmrg* D) {
+int mrd_dmrg_free(mrd_dmrg* D) try {
   if (!D) return MRD_OK;
   mrd_ctx* ctx = D->ctx;
   {
@@ -1271,10 +1273,12 @@ int mrd_dmrg_free(mrd_dmrg* D) {
   }
   mrd_ctx_release(ctx);
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmrg_params* p, double* energy,
-                        double* trunc_err) {
+                        double* trunc_err) try {
   if (!D || !p) return MRD_E_ARG;
   mrd_ctx* ctx = D->ctx;
   if (i < 0 || i > D->n - 2) return mrd_fail(ctx, MRD_E_ARG, "mrd_two_site_update: site out of range");
@@ -1464,9 +1468,11 @@ int mrd_two_site_update(mrd_dmrg* D, int32_t i, int32_t direction, const mrd_dmr
   if (energy) *energy = e;
   if (trunc_err) *trunc_err = info[1];
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_sweep(mrd_dmrg* D, const mrd_dmrg_params* p, double* energy) {
+int mrd_sweep(mrd_dmrg* D, const mrd_dmrg_params* p, double* energy) try {
   if (!D || !p) return MRD_E_ARG;
   int rc;
   double e = 0.0;
@@ -1476,9 +1482,11 @@ int mrd_sweep(mrd_dmrg* D, const mrd_dmrg_params* p, double* energy) {
     if ((rc = mrd_two_site_update(D, i, -1, p, &e, nullptr)) != MRD_OK) return rc;
   if (energy) *energy = e;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_env_update(mrd_dmrg* D, int32_t site, int32_t direction, int32_t prec) {
+int mrd_env_update(mrd_dmrg* D, int32_t site, int32_t direction, int32_t prec) try {
   if (!D) return MRD_E_ARG;
   mrd_ctx* ctx = D->ctx;
   if (direction != 1 && direction != -1) return mrd_fail(ctx, MRD_E_ARG, "mrd_env_update: direction must be +1 or -1");
@@ -1504,9 +1512,11 @@ int mrd_env_update(mrd_dmrg* D, int32_t site, int32_t direction, int32_t prec) {
   rc = direction > 0 ? env_left(D, h, i) : env_right(D, h, i);
   mrd_heff_free(h);
   return rc;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_bond(const mrd_dmrg* D, int32_t bond, int32_t* n_sectors, int32_t* sectors) {
+int mrd_dmrg_bond(const mrd_dmrg* D, int32_t bond, int32_t* n_sectors, int32_t* sectors) try {
   if (!D || !n_sectors || bond < 0 || bond > D->n) return MRD_E_ARG;
   const Secs& s = bond < D->n ? D->A[bond].left : D->A[D->n - 1].right;
   *n_sectors = (int32_t)s.size();
@@ -1515,9 +1525,11 @@ int mrd_dmrg_bond(const mrd_dmrg* D, int32_t bond, int32_t* n_sectors, int32_t* 
       sectors[3 * k] = s[k].N; sectors[3 * k + 1] = s[k].K; sectors[3 * k + 2] = s[k].d;
     }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_site(mrd_dmrg* D, int32_t site, int32_t* mode, int64_t* len, double* host) {
+int mrd_dmrg_site(mrd_dmrg* D, int32_t site, int32_t* mode, int64_t* len, double* host) try {
   if (!D || !len || site < 0 || site >= D->n) return MRD_E_ARG;
   const SiteT& T = D->A[site];
   if (mode) *mode = T.mode;
@@ -1528,9 +1540,11 @@ int mrd_dmrg_site(mrd_dmrg* D, int32_t site, int32_t* mode, int64_t* len, double
     MRD_CUDA(D->ctx, cudaMemcpy(host, T.data.p, (size_t)T.size * 16, cudaMemcpyDeviceToHost));
   }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_env(mrd_dmrg* D, int32_t bond, int32_t side, int64_t* len, double* host) {
+int mrd_dmrg_env(mrd_dmrg* D, int32_t bond, int32_t side, int64_t* len, double* host) try {
   if (!D || !len || bond < 0 || bond > D->n) return MRD_E_ARG;
   EnvT& E = side == 0 ? D->L[bond] : D->R[bond];
   *len = E.data.p ? E.size : -1;
@@ -1546,9 +1560,11 @@ int mrd_dmrg_env(mrd_dmrg* D, int32_t bond, int32_t side, int64_t* len, double* 
     }
   }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_set_option(mrd_dmrg* D, int32_t option, int64_t value) {
+int mrd_dmrg_set_option(mrd_dmrg* D, int32_t option, int64_t value) try {
   if (!D) return MRD_E_ARG;
   mrd_ctx* ctx = D->ctx;
   if (option == MRD_DMRG_OPT_REAL) {
@@ -1592,9 +1608,11 @@ int mrd_dmrg_set_option(mrd_dmrg* D, int32_t option, int64_t value) {
       E.f32 = D->env_fp32;
     }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_memory(const mrd_dmrg* D, int64_t* out4) {
+int mrd_dmrg_memory(const mrd_dmrg* D, int64_t* out4) try {
   if (!D || !out4) return MRD_E_ARG;
   int64_t env = 0, nenv = 0, mps = 0;
   for (const std::vector<EnvT>* side : {&D->L, &D->R})
@@ -1609,9 +1627,11 @@ int mrd_dmrg_memory(const mrd_dmrg* D, int64_t* out4) {
   out4[2] = mps;
   out4[3] = D->env_fp32 ? 1 : 0;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_timing(mrd_dmrg* D, int32_t on, double* kernel_ms4, int64_t* applies2) {
+int mrd_dmrg_timing(mrd_dmrg* D, int32_t on, double* kernel_ms4, int64_t* applies2) try {
   if (!D) return MRD_E_ARG;
   if (kernel_ms4)
     for (int k = 0; k < 4; ++k) kernel_ms4[k] = D->kms[k];
@@ -1620,9 +1640,11 @@ int mrd_dmrg_timing(mrd_dmrg* D, int32_t on, double* kernel_ms4, int64_t* applie
   D->kcount[0] = D->kcount[1] = 0;
   D->timing = on != 0;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_set_site(mrd_dmrg* D, int32_t site, const double* host) {
+int mrd_dmrg_set_site(mrd_dmrg* D, int32_t site, const double* host) try {
   if (!D || site < 0 || site >= D->n) return MRD_E_ARG;
   SiteT& T = D->A[site];
   if (T.size && !host) return mrd_fail(D->ctx, MRD_E_ARG, "mrd_dmrg_set_site: null data");
@@ -1631,26 +1653,32 @@ int mrd_dmrg_set_site(mrd_dmrg* D, int32_t site, const double* host) {
     MRD_CUDA(D->ctx, cudaMemcpyAsync(T.data.p, host, (size_t)T.size * 16, cudaMemcpyHostToDevice, D->ctx->stream));
   }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_phase_ms(const mrd_dmrg* D, double* ms8) {
+int mrd_dmrg_phase_ms(const mrd_dmrg* D, double* ms8) try {
   if (!D || !ms8) return MRD_E_ARG;
   for (int k = 0; k < 6; ++k) ms8[k] = D->phase_ms[k];
   ms8[6] = D->svd_sweeps32;
   ms8[7] = D->svd_sweeps64;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_schmidt(const mrd_dmrg* D, int32_t* bond, int64_t* n, int32_t* nk, double* values) {
+int mrd_dmrg_schmidt(const mrd_dmrg* D, int32_t* bond, int64_t* n, int32_t* nk, double* values) try {
   if (!D || !n) return MRD_E_ARG;
   if (bond) *bond = D->schmidt_bond;
   *n = (int64_t)D->schmidt_val.size();
   if (nk && !D->schmidt_nk.empty()) std::copy(D->schmidt_nk.begin(), D->schmidt_nk.end(), nk);
   if (values && !D->schmidt_val.empty()) std::copy(D->schmidt_val.begin(), D->schmidt_val.end(), values);
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_svd_trace(const mrd_dmrg* D, int32_t cap, int32_t* out, double* ms, int32_t* n2) {
+int mrd_dmrg_svd_trace(const mrd_dmrg* D, int32_t cap, int32_t* out, double* ms, int32_t* n2) try {
   if (!D || cap < 0 || (cap > 0 && !out) || !n2) return MRD_E_ARG;
   n2[0] = (int32_t)D->svd_trace32.size();
   n2[1] = (int32_t)D->svd_trace64.size();
@@ -1664,22 +1692,28 @@ int mrd_dmrg_svd_trace(const mrd_dmrg* D, int32_t cap, int32_t* out, double* ms,
     }
   }
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_svd_stats(const mrd_dmrg* D, double* out8) {
+int mrd_dmrg_svd_stats(const mrd_dmrg* D, double* out8) try {
   if (!D || !out8) return MRD_E_ARG;
   for (int k = 0; k < 6; ++k) out8[k] = D->svd_stats[k];
   out8[6] = D->svd_cols[0];
   out8[7] = D->svd_cols[1];
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
-int mrd_dmrg_stats(const mrd_dmrg* D, double* energy, double* trunc_err, int32_t* lanczos_iters) {
+int mrd_dmrg_stats(const mrd_dmrg* D, double* energy, double* trunc_err, int32_t* lanczos_iters) try {
   if (!D) return MRD_E_ARG;
   if (energy) *energy = D->last_energy;
   if (trunc_err) *trunc_err = D->last_trunc;
   if (lanczos_iters) *lanczos_iters = D->last_iters + 1000 * D->last_refine;
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
 
 }  // extern "C"

@@ -54,7 +54,7 @@ int mrd_heff_internal_noalloc_view(const mrd_heff* h, PlanPtrs* p, int64_t* coun
                                    const double2** wr, int* n_sm, mrd_ctx** ctx, bool* env_loaded);
 }  // namespace mrd
 
-extern "C" int mrd_heff_apply_noalloc(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev) {
+extern "C" int mrd_heff_apply_noalloc(mrd_heff* h, const double* theta_in_dev, double* theta_out_dev) try {
   if (!h) return MRD_E_ARG;
   mrd::PlanPtrs p;
   int64_t c[mrd::C_NCOUNTS];
@@ -95,4 +95,6 @@ extern "C" int mrd_heff_apply_noalloc(mrd_heff* h, const double* theta_in_dev, d
   if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return mrd_cuda_fail(ctx, e, "mrd_heff_apply_noalloc");
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }

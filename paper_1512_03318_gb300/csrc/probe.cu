@@ -57,7 +57,7 @@ int fma_rate(mrd_ctx* ctx, int n_sm, double* instr_per_s) {
 
 }  // namespace
 
-extern "C" int mrd_measure_peaks(mrd_ctx* ctx, double* out4) {
+extern "C" int mrd_measure_peaks(mrd_ctx* ctx, double* out4) try {
   if (!ctx || !out4) return MRD_E_ARG;
   Guard g(ctx->device);
   int n_sm = 0;
@@ -73,4 +73,6 @@ extern "C" int mrd_measure_peaks(mrd_ctx* ctx, double* out4) {
   out4[2] = (double)n_sm;
   out4[3] = (double)clk_khz * 1e3;   // the device's reported maximum SM clock (Hz)
   return MRD_OK;
+} catch (...) {   // host memory or threads exhausted: no exception crosses the C ABI
+  return MRD_E_HOST;
 }
