@@ -335,10 +335,14 @@ bool tables(const mrd_heff* h, int prec, TcCfg cfg, TcTables& o) {
   for (size_t t = 0; t + 1 < p2.size(); ++t) q2[2 * t + 1] = p2[t + 1] - p2[t];
   // Item tables: (task, tile within task) of every tile, dealt to the persistent CTAs by
   // longest-processing-time-first: items by decreasing cost (the task's K tiles plus two for the
-  // pipeline fill and the epilogue), each to the CTA with the least work so far. Each CTA's
-  // items are stored together, co[c] .. co[c + 1]. A static deal in item order left step 2's
-  // SMs between 25% and 91% busy (ncu) because the tiles' K lengths differ by orders of
-  // magnitude.
+  // pipeline fill and the epilogue; equal costs in task order), each to the CTA with the least
+  // work so far (the lowest-numbered of those). Each CTA's items are stored together,
+  // co[c] .. co[c + 1]. A static deal in item order left step 2's SMs between 25% and 91% busy
+  // (ncu) because the tiles' K lengths differ by orders of magnitude.
+  // Tasks are ordered by a counting sort of their costs, and the least-loaded CTA is found in a
+  // bucket queue: bit sets of the CTAs per amount of work, in a ring of cmax + 1 buckets (every
+  // CTA's work lies within cmax of the least), so tens of thousands of items cost no sort and
+  // no heap operations.
   const int grid_sm = std::max(h->n_sm, 1);
   auto deal = [&](const std::vector<int64_t>& tk, const std::vector<int64_t>& sg, const std::vector<int64_t>& pf,
                   std::vector<int2>& items, std::vector<int32_t>& co) {
@@ -348,33 +352,58 @@ bool tables(const mrd_heff* h, int prec, TcCfg cfg, TcTables& o) {
     co.assign((size_t)G + 1, 0);
     if (total <= 0) return;
     std::vector<int64_t> cost(nt, 0);
+    int64_t cmax = 0;
     for (size_t t = 0; t < nt; ++t) {
+      if (pf[t + 1] == pf[t]) continue;   // no tiles
       int64_t kt = 0;
       for (int64_t k = 0; k < tk[TCT * t + 6]; ++k) kt += sg[TCS * (tk[TCT * t + 5] + k) + 2];
       cost[t] = kt + 2;
+      cmax = std::max(cmax, cost[t]);
     }
-    std::vector<int2> all;
-    all.reserve((size_t)total);
+    std::vector<int64_t> first((size_t)cmax + 1, 0);   // first slot of each cost, decreasing costs
     for (size_t t = 0; t < nt; ++t)
-      for (int64_t l = 0; l < pf[t + 1] - pf[t]; ++l) all.push_back(make_int2((int)t, (int)l));
-    std::stable_sort(all.begin(), all.end(), [&](int2 a, int2 b) { return cost[a.x] > cost[b.x]; });
-    using Load = std::pair<int64_t, int>;   // (work so far, CTA): least work, then lowest index
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int c = 0; c < G; ++c) heap.push({0, c});
-    std::vector<int> owner(all.size());
-    std::vector<int32_t> count((size_t)G, 0);
-    for (size_t i = 0; i < all.size(); ++i) {
-      Load l = heap.top();
-      heap.pop();
-      owner[i] = l.second;
-      ++count[(size_t)l.second];
-      l.first += cost[all[i].x];
-      heap.push(l);
+      if (pf[t + 1] > pf[t]) ++first[(size_t)cost[t]];
+    for (int64_t c = cmax, acc = 0; c >= 0; --c) {
+      const int64_t n = first[(size_t)c];
+      first[(size_t)c] = acc;
+      acc += n;
+    }
+    size_t n_ord = 0;   // tasks with tiles
+    for (size_t t = 0; t < nt; ++t)
+      if (pf[t + 1] > pf[t]) ++n_ord;
+    std::vector<int32_t> ord(n_ord);
+    for (size_t t = 0; t < nt; ++t)
+      if (pf[t + 1] > pf[t]) ord[(size_t)first[(size_t)cost[t]]++] = (int32_t)t;
+    const int W = (G + 63) / 64;
+    const int64_t R = cmax + 1;
+    std::vector<uint64_t> bits((size_t)(R * W), 0);   // bucket (work mod R): the CTAs with that work
+    for (int c = 0; c < G; ++c) bits[(size_t)(c >> 6)] |= 1ull << (c & 63);
+    int64_t lo = 0;   // least work of any CTA
+    std::vector<int32_t> owner((size_t)total), count((size_t)G, 0);
+    size_t i = 0;
+    for (const int32_t t : ord) {
+      const int64_t add = cost[(size_t)t];
+      for (int64_t l = pf[(size_t)t]; l < pf[(size_t)t + 1]; ++l, ++i) {
+        int c = -1;
+        for (;; ++lo) {
+          const uint64_t* bk = &bits[(size_t)((lo % R) * W)];
+          for (int w = 0; w < W && c < 0; ++w)
+            if (bk[w]) c = w * 64 + __builtin_ctzll(bk[w]);
+          if (c >= 0) break;
+        }
+        bits[(size_t)((lo % R) * W + (c >> 6))] &= ~(1ull << (c & 63));
+        bits[(size_t)(((lo + add) % R) * W + (c >> 6))] |= 1ull << (c & 63);
+        owner[i] = c;
+        ++count[(size_t)c];
+      }
     }
     for (int c = 0; c < G; ++c) co[(size_t)c + 1] = co[(size_t)c] + count[(size_t)c];
-    items.assign(all.size(), make_int2(0, 0));
+    items.assign((size_t)total, make_int2(0, 0));
     std::vector<int32_t> fill(co.begin(), co.end() - 1);
-    for (size_t i = 0; i < all.size(); ++i) items[(size_t)fill[(size_t)owner[i]]++] = all[i];
+    i = 0;
+    for (const int32_t t : ord)
+      for (int64_t l = 0; l < pf[(size_t)t + 1] - pf[(size_t)t]; ++l, ++i)
+        items[(size_t)fill[(size_t)owner[i]]++] = make_int2(t, (int)l);
   };
   deal(t1, s1, p1, o.i1, o.co1);
   deal(t2, s2, p2, o.i2, o.co2);
