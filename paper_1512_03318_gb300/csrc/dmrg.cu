@@ -884,16 +884,19 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
   const Secs& cs = A.right;  // bond i+1
   auto cm = mpo_channels(D->mpo, i + 1, D->mod);
   const int m1 = A.m, mod = D->mod;
-  // LW blocks (w', s', s, a) -> offset
-  std::map<std::array<int64_t, 4>, int64_t> lw;
+  // LW blocks (w', s', s, a) -> offset, in a flat index over all (w', s', s, a)
+  const int64_t nls = (int64_t)ls.size(), ncs = (int64_t)cs.size(), nw = (int64_t)cm.size();
+  std::vector<int64_t> lw((size_t)(nw * 4 * nls), -1);
   for (int64_t k = 0; k < h->counts[C_NLW]; ++k) {
     const int64_t* r = &h->lw_host[LWF * k];
-    lw[{r[0], r[1], r[2], r[3]}] = r[7];
+    if (r[0] < 0 || r[0] >= nw || r[1] < 0 || r[1] > 1 || r[2] < 0 || r[2] > 1 || r[3] < 0 || r[3] >= nls)
+      return mrd_fail(ctx, MRD_E_STATE, "internal: LW block outside the bond's channels or sectors");
+    lw[(size_t)(((r[0] * 2 + r[1]) * 2 + r[2]) * nls + r[3])] = r[7];
   }
   // step 1: T(w', c, s') = sum_s LW(w', s', s, a) A(a, s -> c)
   GemmList g1;
   struct TB { int64_t off, rows; };
-  std::map<std::array<int, 3>, TB> tblk;
+  std::vector<TB> tblk((size_t)(nw * ncs * 2), TB{-1, 0});   // (w', c, s') -> block of T
   int64_t tlen = 0;
   for (int w = 0; w < (int)cm.size(); ++w)
     for (int c = 0; c < (int)cs.size(); ++c) {
@@ -906,18 +909,18 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
         for (int s = 0; s < 2; ++s) {
           const int a = find_sec(ls, cs[c].N - s, kmod(cs[c].K - s * m1, mod));
           if (a < 0) continue;
-          auto it = lw.find({w, sp, s, a});
-          if (it == lw.end()) continue;
+          const int64_t lwo = lw[(size_t)((((int64_t)w * 2 + sp) * 2 + s) * nls + a)];
+          if (lwo < 0) continue;
           int64_t ao, ald;
           int rr;
           if (!A.subblock(a, s, &ao, &ald, &rr) || rr != c) continue;
           if (!started) {
-            tblk[{w, c, sp}] = {tlen, ls[ap].d};
+            tblk[(size_t)(((int64_t)w * ncs + c) * 2 + sp)] = {tlen, ls[ap].d};
             g1.task(ls[ap].d, cs[c].d, tlen, cs[c].d);
             tlen += (int64_t)ls[ap].d * cs[c].d;
             started = true;
           }
-          g1.seg(it->second, ls[a].d, ao, ald, ls[a].d, 0);
+          g1.seg(lwo, ls[a].d, ao, ald, ls[a].d, 0);
         }
       }
     }
@@ -944,15 +947,15 @@ int env_left(mrd_dmrg* D, mrd_heff* h, int i) {
       const int cp = find_sec(cs, cs[c].N + cm[w][0], kmod(cs[c].K + cm[w][1], mod));
       bool started = false;
       for (int sp = 0; sp < 2; ++sp) {
-        auto it = tblk.find({w, c, sp});
-        if (it == tblk.end()) continue;
+        const TB& tb = tblk[(size_t)(((int64_t)w * ncs + c) * 2 + sp)];
+        if (tb.off < 0) continue;
         const int ap = find_sec(ls, cs[cp].N - sp, kmod(cs[cp].K - sp * m1, mod));
         int64_t ao, ald;
         int rr;
         if (!A.subblock(ap, sp, &ao, &ald, &rr) || rr != cp) continue;
         if (!started) { g2.task(cs[cp].d, cs[c].d, off, cs[c].d); started = true; }
         // A-op: conj-transpose of the d_a' x d_c' sub-block
-        g2.seg(ao, ald, it->second.off, cs[c].d, ls[ap].d, 1);
+        g2.seg(ao, ald, tb.off, cs[c].d, ls[ap].d, 1);
       }
     }
   rc = run_gemm(D, g2, A.data.as<double2>(), A.size, D->tbuf.as<double2>(), tlen, eout.as<double2>(), E.size, nullptr,
@@ -969,15 +972,19 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
   const Secs& bs = B.right;  // bond i+2
   auto cm = mpo_channels(D->mpo, i + 1, D->mod);
   const int m2 = B.m, mod = D->mod;
-  std::map<std::array<int64_t, 4>, int64_t> wr;
+  // WR blocks (w', s, s', b) -> offset, in a flat index over all (w', s, s', b)
+  const int64_t nbs = (int64_t)bs.size(), ncs = (int64_t)cs.size(), nw = (int64_t)cm.size();
+  std::vector<int64_t> wr((size_t)(nw * 4 * nbs), -1);
   for (int64_t k = 0; k < h->counts[C_NWR]; ++k) {
     const int64_t* r = &h->wr_host[WRF * k];
-    wr[{r[0], r[1], r[2], r[3]}] = r[7];
+    if (r[0] < 0 || r[0] >= nw || r[1] < 0 || r[1] > 1 || r[2] < 0 || r[2] > 1 || r[3] < 0 || r[3] >= nbs)
+      return mrd_fail(ctx, MRD_E_STATE, "internal: WR block outside the bond's channels or sectors");
+    wr[(size_t)(((r[0] * 2 + r[1]) * 2 + r[2]) * nbs + r[3])] = r[7];
   }
   // step 1: T(w', c, s') = sum_s B(c, s -> b) WR(w', s, s', b)
   GemmList g1;
   struct TB { int64_t off, cols; };
-  std::map<std::array<int, 3>, TB> tblk;
+  std::vector<TB> tblk((size_t)(nw * ncs * 2), TB{-1, 0});   // (w', c, s') -> block of T
   int64_t tlen = 0;
   for (int w = 0; w < (int)cm.size(); ++w)
     for (int c = 0; c < (int)cs.size(); ++c) {
@@ -991,15 +998,15 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
           int64_t bo, bld;
           int b;
           if (!B.subblock(c, s, &bo, &bld, &b)) continue;
-          auto it = wr.find({w, s, sp, b});
-          if (it == wr.end()) continue;
+          const int64_t wro = wr[(size_t)((((int64_t)w * 2 + s) * 2 + sp) * nbs + b)];
+          if (wro < 0) continue;
           if (!started) {
-            tblk[{w, c, sp}] = {tlen, bs[bp].d};
+            tblk[(size_t)(((int64_t)w * ncs + c) * 2 + sp)] = {tlen, bs[bp].d};
             g1.task(cs[c].d, bs[bp].d, tlen, bs[bp].d);
             tlen += (int64_t)cs[c].d * bs[bp].d;
             started = true;
           }
-          g1.seg(bo, bld, it->second, bs[bp].d, bs[b].d, 0);
+          g1.seg(bo, bld, wro, bs[bp].d, bs[b].d, 0);
         }
       }
     }
@@ -1024,14 +1031,14 @@ int env_right(mrd_dmrg* D, mrd_heff* h, int i) {
       const int cp = find_sec(cs, cs[c].N + cm[w][0], kmod(cs[c].K + cm[w][1], mod));
       bool started = false;
       for (int sp = 0; sp < 2; ++sp) {
-        auto it = tblk.find({w, c, sp});
-        if (it == tblk.end()) continue;
+        const TB& tb = tblk[(size_t)(((int64_t)w * ncs + c) * 2 + sp)];
+        if (tb.off < 0) continue;
         int64_t bo, bld;
         int bp;
         if (!B.subblock(cp, sp, &bo, &bld, &bp)) continue;
         if (!started) { g2.task(cs[c].d, cs[cp].d, off, cs[cp].d); started = true; }
         // B-op: conj-transpose of the d_c' x d_b' sub-block
-        g2.seg(it->second.off, it->second.cols, bo, bld, bs[bp].d, 2);
+        g2.seg(tb.off, tb.cols, bo, bld, bs[bp].d, 2);
       }
     }
   rc = run_gemm(D, g2, D->tbuf.as<double2>(), tlen, B.data.as<double2>(), B.size, eout.as<double2>(), E.size, t_ff);
