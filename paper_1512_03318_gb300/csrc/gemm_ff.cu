@@ -48,14 +48,8 @@ struct CAcc {
   FFAcc rr, ii, ss;
 };
 
-// operand element as staged float-float: FP64 operands are split on load, float-float
-// operands (float4 {re.hi, im.hi, re.lo, im.lo}, prepared once) are read as they are
-__device__ __forceinline__ float4 ld_op(const double2* p, int64_t i, bool conj) {
-  if (i < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
-  double2 v = p[i];
-  if (conj) v.y = -v.y;
-  return cff_from(v);
-}
+// operand element as staged: float-float operands (float4 {re.hi, im.hi, re.lo, im.lo},
+// split from FP64 once by k_to_ff) are read as they are
 __device__ __forceinline__ float4 ld_op(const float4* p, int64_t i, bool conj) {
   if (i < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
   float4 v = p[i];
@@ -260,11 +254,6 @@ static cudaError_t launch_ff(const TA* A, const TB* B, TC* C, const int64_t* tas
     k_cgemm_ff<TA, TB, TC, false><<<(unsigned)grid, 256, 0, s>>>(A, B, C, tasks, segs, prefix, n_tasks, items);
   mrd::count_launch();
   return cudaGetLastError();
-}
-
-cudaError_t launch_cgemm_ff(const double2* A, const double2* B, double2* C, const int64_t* tasks, const int64_t* segs,
-                            const int64_t* prefix, int64_t n_tasks, int64_t total_tiles, int n_sm, cudaStream_t s) {
-  return launch_ff(A, B, C, tasks, segs, prefix, n_tasks, total_tiles, n_sm, s, nullptr);
 }
 
 // real operands already in float-float layout (imaginary parts zero): Re only, Im written 0
