@@ -1087,7 +1087,7 @@ def main():
     svd_ms = svd_work[0] + svd_work[4]
     # the headline kernel: the split-BF16 H_eff of the timed updates (both grouped launches of
     # every application). Algorithmic flops: the definition order L -> W -> R of the H_eff,
-    # 8 per complex multiply-add (the survey's measure). Hardware flops: what the tensor cores
+    # 8 per complex multiply-add (definition-order work). Hardware flops: what the tensor cores
     # execute, 4 BF16 products (hi and lo of each operand) per real product of the folded
     # contraction. The kernel runs inside a long step: sustained BF16 peak.
     t_tc = tc_ms / 1e3
